@@ -1,0 +1,261 @@
+"""FP64 CPU oracle for the MRT/AMRT chemotaxis optimal-control path.
+
+TEST INFRASTRUCTURE.  This package is the plain, slow, obviously-correct
+reference the CUDA library is checked against.  Only ``tests/``,
+``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may import
+it; the product path never does.  It shares no code with the CUDA library.
+
+The arithmetic lives in ``mrt_oracle.c`` (plain C, FP64, one node at a time);
+this module only builds it with gcc and marshals arrays through ctypes.  The
+Armijo gradient-descent driver below follows the paper's discrete-adjoint
+algorithm (Sec. 3.2.1, the optimisation process after eq. JD-H-B) with the
+heuristic first step min(1, 1/||E||_inf) (remark after the continuous gradient
+algorithm, Sec. 2.3).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_SRC = os.path.join(_HERE, "mrt_oracle.c")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (portable flags: x86_64 and aarch64)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < max(
+        os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "mrt_oracle.h"))
+    ):
+        tmp = _SO + f".{os.getpid()}.tmp"
+        subprocess.check_call(
+            ["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-ffp-contract=off", "-o", tmp, _SRC, "-lm"]
+        )
+        os.replace(tmp, _SO)
+    return _SO
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("N", ctypes.c_int), ("Q", ctypes.c_int),
+        ("tau", ctypes.c_double),
+        ("Du", ctypes.c_void_p), ("Dv", ctypes.c_void_p),
+        ("d_u", ctypes.c_double), ("d_v", ctypes.c_double),
+        ("chi", ctypes.c_double), ("r_vu", ctypes.c_double), ("r_vv", ctypes.c_double),
+        ("a", ctypes.c_void_p), ("solid", ctypes.c_void_p),
+        ("cx0", ctypes.c_int), ("cy0", ctypes.c_int), ("cnx", ctypes.c_int), ("cny", ctypes.c_int),
+        ("cmask", ctypes.c_void_p),
+        ("u_tgt", ctypes.c_void_p), ("alpha", ctypes.c_double),
+        ("s", ctypes.c_double * 7),
+        ("source_order", ctypes.c_int),
+        ("u0", ctypes.c_void_p), ("v0", ctypes.c_void_p),
+    ]
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        P = ctypes.POINTER(_Problem)
+        vp, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)
+        lib.or_forward.argtypes = [P, vp, dp, vp, vp]
+        lib.or_forward_trace.argtypes = [P, vp, vp, vp, vp]
+        lib.or_tlm.argtypes = [P, vp, vp, vp, vp, vp, dp]
+        lib.or_adjoint.argtypes = [P, vp, vp, vp, vp, vp, dp]
+        lib.or_lattice.argtypes = [ctypes.c_int, vp, vp, vp, vp]
+        lib.or_feq.argtypes = [ctypes.c_int, ctypes.c_double, vp, ctypes.c_double, vp]
+        lib.or_collide_node.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp,
+                                        ctypes.c_double, ctypes.c_double, vp, vp, dp]
+        _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _u8(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.uint8)
+
+
+@dataclass
+class Problem:
+    """Problem data in the oracle's layout (see mrt_oracle.h).
+
+    Du, Dv: [ny, nx, 3] (Dxx, Dxy, Dyy); a: [ny, nx, 2] or None; solid: [ny, nx]
+    bool or None; window (cx0, cy0, cnx, cny) with optional cmask [cny, cnx].
+    """
+
+    nx: int
+    ny: int
+    N: int
+    Q: int
+    Du: np.ndarray
+    Dv: np.ndarray
+    u0: np.ndarray
+    v0: np.ndarray
+    u_tgt: np.ndarray
+    d_u: float = 1.0
+    d_v: float = 1.0
+    chi: float = 0.0
+    r_vu: float = 0.0
+    r_vv: float = 0.0
+    a: np.ndarray | None = None
+    solid: np.ndarray | None = None
+    window: tuple = None
+    cmask: np.ndarray | None = None
+    alpha: float = 0.0
+    s: tuple = (1.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0)
+    source_order: int = 2
+    tau: float = 1.0
+    _keep: list = field(default_factory=list, repr=False)
+
+    @property
+    def ctrl_shape(self):
+        w = self.window or (0, 0, self.nx, self.ny)
+        return (self.N, w[3], w[2])
+
+    def _struct(self):
+        arrs = dict(
+            Du=_f64(self.Du), Dv=_f64(self.Dv), a=_f64(self.a), solid=_u8(self.solid),
+            cmask=_u8(self.cmask), u_tgt=_f64(self.u_tgt), u0=_f64(self.u0), v0=_f64(self.v0),
+        )
+        self._keep = list(arrs.values())
+        w = self.window or (0, 0, self.nx, self.ny)
+        st = _Problem()
+        st.nx, st.ny, st.N, st.Q = self.nx, self.ny, self.N, self.Q
+        st.tau = self.tau
+        st.Du, st.Dv = _ptr(arrs["Du"]), _ptr(arrs["Dv"])
+        st.d_u, st.d_v = self.d_u, self.d_v
+        st.chi, st.r_vu, st.r_vv = self.chi, self.r_vu, self.r_vv
+        st.a, st.solid = _ptr(arrs["a"]), _ptr(arrs["solid"])
+        st.cx0, st.cy0, st.cnx, st.cny = w
+        st.cmask = _ptr(arrs["cmask"])
+        st.u_tgt = _ptr(arrs["u_tgt"])
+        st.alpha = self.alpha
+        st.s = (ctypes.c_double * 7)(*self.s)
+        st.source_order = self.source_order
+        st.u0, st.v0 = _ptr(arrs["u0"]), _ptr(arrs["v0"])
+        return st
+
+
+def _check(rc, name):
+    if rc != 0:
+        raise RuntimeError(f"oracle {name} failed with code {rc}")
+
+
+def forward(p: Problem, g=None):
+    """Forward MRT solve.  Returns (J, u^N, v^N)."""
+    lib = _load()
+    st = p._struct()
+    g = _f64(g)
+    J = ctypes.c_double(0.0)
+    uN = np.zeros((p.ny, p.nx))
+    vN = np.zeros((p.ny, p.nx))
+    _check(lib.or_forward(ctypes.byref(st), _ptr(g), ctypes.byref(J), _ptr(uN), _ptr(vN)), "forward")
+    return J.value, uN, vN
+
+
+def forward_trace(p: Problem, g=None):
+    """Per-step sums over fluid nodes: (sum u^n, sum v^n, sum Phi^n), each [N]."""
+    lib = _load()
+    st = p._struct()
+    mu, mv, sp = np.zeros(p.N), np.zeros(p.N), np.zeros(p.N)
+    _check(lib.or_forward_trace(ctypes.byref(st), _ptr(_f64(g)), _ptr(mu), _ptr(mv), _ptr(sp)), "trace")
+    return mu, mv, sp
+
+
+def tlm(p: Problem, g, dg, df0=None):
+    """Tangent-linear model.  Returns (dJ, du^N, dv^N)."""
+    lib = _load()
+    st = p._struct()
+    g, dg, df0 = _f64(g), _f64(dg), _f64(df0)
+    dJ = ctypes.c_double(0.0)
+    du = np.zeros((p.ny, p.nx))
+    dv = np.zeros((p.ny, p.nx))
+    _check(lib.or_tlm(ctypes.byref(st), _ptr(g), _ptr(dg), _ptr(df0), _ptr(du), _ptr(dv), ctypes.byref(dJ)), "tlm")
+    return dJ.value, du, dv
+
+
+def adjoint(p: Problem, g=None, seed_u=None, seed_v=None, want_psi0=False):
+    """AMRT adjoint sweep.  Returns (J, dJ/dg [N, cny, cnx], psi0 [ny, nx, 2, Q] or None)."""
+    lib = _load()
+    st = p._struct()
+    g, su, sv = _f64(g), _f64(seed_u), _f64(seed_v)
+    dJdg = np.zeros(p.ctrl_shape)
+    psi0 = np.zeros((p.ny, p.nx, 2, p.Q)) if want_psi0 else None
+    J = ctypes.c_double(0.0)
+    _check(lib.or_adjoint(ctypes.byref(st), _ptr(g), _ptr(su), _ptr(sv), _ptr(dJdg), _ptr(psi0),
+                          ctypes.byref(J)), "adjoint")
+    return J.value, dJdg, psi0
+
+
+def lattice(Q: int):
+    """(e [Q,2] int, w [Q], M [Q,Q], Minv [Q,Q]) as the oracle holds them."""
+    lib = _load()
+    e = np.zeros((Q, 2), dtype=np.int32)
+    w, M, Mi = np.zeros(Q), np.zeros((Q, Q)), np.zeros((Q, Q))
+    _check(lib.or_lattice(Q, _ptr(e), _ptr(w), _ptr(M), _ptr(Mi)), "lattice")
+    return e, w, M, Mi
+
+
+def feq(Q: int, Theta: float, a=(0.0, 0.0), d: float = 1.0):
+    lib = _load()
+    out = np.zeros(Q)
+    av = np.asarray(a, dtype=np.float64)
+    _check(lib.or_feq(Q, float(Theta), _ptr(av), float(d), _ptr(out)), "feq")
+    return out
+
+
+def collide_node(p: Problem, x, y, n, f_u, f_v, g=0.0, phi_prev=0.0):
+    """Local forward collision at node (x, y), step n.  Returns (P_u, P_v, Phi)."""
+    lib = _load()
+    st = p._struct()
+    fu, fv = _f64(f_u), _f64(f_v)
+    Pu, Pv = np.zeros(p.Q), np.zeros(p.Q)
+    phi = ctypes.c_double(0.0)
+    _check(lib.or_collide_node(ctypes.byref(st), x, y, n, _ptr(fu), _ptr(fv), float(g), float(phi_prev),
+                               _ptr(Pu), _ptr(Pv), ctypes.byref(phi)), "collide_node")
+    return Pu, Pv, phi.value
+
+
+def gd_step(p: Problem, g, lam_prev=None, c1=1e-4, max_trials=30):
+    """One gradient-descent iteration with Armijo backtracking (FP64).
+
+    Steps (discrete-adjoint algorithm, Sec. 3.2.1): forward -> adjoint ->
+    gradient E -> trial g - lam E, halving lam until
+    J(g - lam E) <= J(g) - c1 lam ||E||^2.  First trial: min(1, 1/||E||_inf)
+    on the first iteration, 2 lam_prev afterwards.
+    Returns (g_new, info dict).
+    """
+    J0, E, _ = adjoint(p, g)
+    E2 = float(np.sum(E * E))
+    Einf = float(np.max(np.abs(E))) if E.size else 0.0
+    lam = min(1.0, 1.0 / Einf) if lam_prev is None else 2.0 * lam_prev
+    for t in range(max_trials):
+        gt = g - lam * E
+        Jt, _, _ = forward(p, gt)
+        if Jt <= J0 - c1 * lam * E2:
+            return gt, dict(J0=J0, J=Jt, lam=lam, trials=t + 1, E2=E2, Einf=Einf)
+        lam *= 0.5
+    raise RuntimeError("Armijo line search failed")
+
+
+def from_workload(w, N=None) -> Problem:
+    """Oracle problem from a seeded workload (per-node tensor and velocity fields)."""
+    Du, Dv = w.D_fields()
+    return Problem(nx=w.nx, ny=w.ny, N=w.N if N is None else N, Q=w.Q, Du=Du, Dv=Dv, u0=w.u0, v0=w.v0,
+                   u_tgt=w.u_tgt, d_u=w.d_u, d_v=w.d_v, chi=w.chi, r_vu=w.r_vu, r_vv=w.r_vv,
+                   a=w.a_fields(), solid=w.solid, window=w.window, cmask=w.cmask, alpha=w.alpha,
+                   s=tuple(w.s), source_order=w.source_order)

@@ -1,0 +1,94 @@
+/*
+ * mrt_oracle.h -- FP64 CPU oracle for the coupled MRT lattice Boltzmann
+ * forward solve, its tangent-linear (sensitivity) model and its AMRT adjoint,
+ * for the two-species chemotaxis system (u = cells, v = chemical, g = control
+ * acting on v).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This code is the slow, plain reference that the
+ * CUDA path is checked against.  Only the test-suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load it.  It shares no code, header,
+ * table or constant with the CUDA library.
+ *
+ * Every function follows the paper (Belmiloudi, "Optimal control for
+ * chemotaxis systems and adjoint-based optimization with multiple-relaxation-
+ * time lattice Boltzmann models"):
+ *   - forward step:     eq. (LBE)/(LBEG) with (S), (PhiS), (phieq), M0, Pi (Sec. 3.1)
+ *   - sensitivity step: eq. (LIBEG-V) (Sec. 3.2), the tangent of the forward step
+ *   - adjoint step:     AMRT, eqs. (CAE), (AEDs), (AEDsM), (CAEL) (Sec. 3.2.1):
+ *                       streaming along -e_i backward in time, collision with
+ *                       the transposed operator, adjoint equilibrium as the
+ *                       scalar broadcast T = sum_j w_j aleph_j m~_j, plus the
+ *                       coupling terms dR/dphi and the gradient (gradientLattice).
+ *
+ * Array layouts (all row-major, all double unless noted):
+ *   node fields          [ny][nx]
+ *   tensor fields D      [ny][nx][3]  (Dxx, Dxy, Dyy)
+ *   vector field a       [ny][nx][2]
+ *   control g, dJ/dg     [N][cny][cnx]  (window x in [cx0,cx0+cnx), y in [cy0,cy0+cny))
+ *   populations (psi0)   [ny][nx][2][Q]  (species 0 = u, 1 = v)
+ */
+#ifndef MRT_ORACLE_H
+#define MRT_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    int nx, ny, N, Q;            /* grid, time steps, lattice (5 or 9) */
+    double tau;                  /* lattice time step (h = tau = c = 1 in every test) */
+    const double* Du;            /* [ny][nx][3] self-diffusion tensor of u */
+    const double* Dv;            /* [ny][nx][3] self-diffusion tensor of v */
+    double d_u, d_v;             /* d_Theta of the equilibrium (phieq) */
+    double chi;                  /* chemotactic sensitivity: D_{u,1} = chi u I */
+    double r_vu, r_vv;           /* Phi_v = r_vu u + r_vv v + g,  Phi_u = 0 */
+    const double* a;             /* [ny][nx][2] convection velocity (T_Theta = a Theta) or NULL */
+    const unsigned char* solid;  /* [ny][nx] 1 = solid node, or NULL (all fluid, periodic) */
+    int cx0, cy0, cnx, cny;      /* control window */
+    const unsigned char* cmask;  /* [cny][cnx] 1 = controlled node, or NULL (whole window) */
+    const double* u_tgt;         /* [ny][nx] target u(T) */
+    double alpha;                /* control penalty weight */
+    double s[7];                 /* free relaxation rates s0..s6 of Pi */
+    int source_order;            /* 2: keep (tau/2)(Phi^n - Phi^{n-1}); 1: drop it */
+    const double* u0;            /* [ny][nx] initial u */
+    const double* v0;            /* [ny][nx] initial v */
+} or_problem;
+
+/* Lattice tables for unit tests: e [Q][2], w [Q], M [Q][Q], Minv [Q][Q]. */
+int or_lattice(int Q, int* e, double* w, double* M, double* Minv);
+
+/* Equilibrium populations (phieq) at one node: out[Q]. */
+int or_feq(int Q, double Theta, const double a[2], double d, double* out);
+
+/* One forward collision at one node (pre-collision f -> post-collision P),
+ * exposing the local map for unit tests.  f_u, f_v, P_u, P_v are [Q]. */
+int or_collide_node(const or_problem* p, int x, int y, int n,
+                    const double* f_u, const double* f_v, double g, double Phi_prev,
+                    double* P_u, double* P_v, double* Phi_out);
+
+/* Forward solve; uN, vN may be NULL.  Returns 0 on success. */
+int or_forward(const or_problem* p, const double* g, double* J, double* uN, double* vN);
+
+/* Forward solve that also returns, per step, the v-mass before collision and
+ * Phi^n summed over fluid nodes ([N] each); used by the mass-balance pin. */
+int or_forward_trace(const or_problem* p, const double* g, double* mass_u, double* mass_v,
+                     double* sum_phi);
+
+/* Tangent-linear model: perturbation dg of g and df0 ([ny][nx][2][Q], may be
+ * NULL) of the initial populations.  Outputs duN, dvN ([ny][nx]) and the
+ * directional derivative dJ of J. */
+int or_tlm(const or_problem* p, const double* g, const double* dg, const double* df0,
+           double* duN, double* dvN, double* dJ);
+
+/* AMRT adjoint sweep and gradient.  seed_u / seed_v: adjoint of u^N / v^N
+ * ([ny][nx]); seed_u == NULL means u^N - u_tgt (the cost's terminal term),
+ * seed_v == NULL means 0.  With explicit seeds the gradient returned is that
+ * of sum(seed_u*u^N + seed_v*v^N) + alpha*||g||^2.
+ * Outputs dJdg [N][cny][cnx], psi0 [ny][nx][2][Q] (may be NULL), J (may be NULL). */
+int or_adjoint(const or_problem* p, const double* g, const double* seed_u,
+               const double* seed_v, double* dJdg, double* psi0, double* J);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

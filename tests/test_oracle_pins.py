@@ -1,0 +1,386 @@
+"""Pins of the FP64 CPU oracle against what the paper and mathematics fix.
+
+Each test checks the oracle against something other than itself: the paper's
+printed tables and moment listing, lattice isotropy identities, the BGK special
+case, conservation laws, the closed-form anisotropic Gaussian, an independent
+pseudo-spectral solution of the PDE, the tangent/adjoint dot-product identity
+and brute-force finite differences.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1908_03876_gb300 import workloads as W
+from paper_1908_03876_gb300.workloads import rotated_tensor
+
+CS2 = 1.0 / 3.0
+
+
+# ----------------------------------------------------------------- lattice
+
+def test_d2q9_tables_match_paper(golden_dir):
+    with open(os.path.join(golden_dir, "d2q9_lattice.json")) as fh:
+        gold = json.load(fh)
+    e, w, M, Minv = oracle.lattice(9)
+    assert np.array_equal(e, np.array(gold["e"]))
+    assert np.allclose(w * gold["w_den"], gold["w_num"], rtol=0, atol=1e-13)
+    assert np.array_equal(M, np.array(gold["M0"], dtype=float))
+    assert np.allclose(Minv @ M, np.eye(9), atol=1e-13)
+
+
+@pytest.mark.parametrize("Q", [5, 9])
+def test_lattice_isotropy(Q):
+    """sum w = 1, sum w e = 0, sum w e e = Cs^2 I, sum w U = 0 (Sec. 3.1)."""
+    e, w, M, Minv = oracle.lattice(Q)
+    assert abs(w.sum() - 1.0) < 1e-15
+    assert np.allclose((w[:, None] * e).sum(0), 0.0, atol=1e-15)
+    ee = np.einsum("i,ia,ib->ab", w, e, e)
+    assert np.allclose(ee, CS2 * np.eye(2), atol=1e-15)
+    U = np.einsum("ia,ib->iab", e, e) - CS2 * np.eye(2)[None]
+    assert np.allclose(np.einsum("i,iab->ab", w, U), 0.0, atol=1e-15)
+    # moment rows are mutually orthogonal (Gram-Schmidt basis)
+    G = M @ M.T
+    assert np.allclose(G - np.diag(np.diag(G)), 0.0)
+    assert np.allclose(Minv @ M, np.eye(Q), atol=1e-13)
+
+
+def test_equilibrium_moments_match_listing(golden_dir):
+    """M phi^eq equals the paper's listed m^eq for random Theta, a, d."""
+    with open(os.path.join(golden_dir, "meq_d2q9.json")) as fh:
+        rows = np.array(json.load(fh)["rows"], dtype=float)
+    e, w, M, _ = oracle.lattice(9)
+    rng = np.random.default_rng(11)
+    for _ in range(20):
+        Th = rng.uniform(0.1, 3.0)
+        a = rng.uniform(-0.2, 0.2, 2)
+        d = rng.uniform(0.4, 1.5)
+        B = (np.outer(a, a) + d * CS2 * np.eye(2)) * Th
+        basis = np.array([Th, a[0] * Th, a[1] * Th, B[0, 0], B[1, 1], B[0, 1]])
+        m = M @ oracle.feq(9, Th, a, d)
+        assert np.allclose(m, rows @ basis, rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("Q", [5, 9])
+def test_equilibrium_constraints_TF0(Q):
+    """sum phi^eq = Theta, sum e phi^eq = a Theta, sum e e phi^eq = (aa + d Cs^2 I) Theta
+    (eq. TF0).  D2Q5 meets the stress condition only for d = 1, a = 0."""
+    e, w, M, _ = oracle.lattice(Q)
+    rng = np.random.default_rng(3)
+    for _ in range(10):
+        Th = rng.uniform(0.1, 3.0)
+        a = rng.uniform(-0.2, 0.2, 2) if Q == 9 else np.zeros(2)
+        d = rng.uniform(0.5, 1.5) if Q == 9 else 1.0
+        f = oracle.feq(Q, Th, a, d)
+        assert abs(f.sum() - Th) < 1e-13
+        assert np.allclose(e.T @ f, a * Th, atol=1e-13)
+        stress = np.einsum("ia,ib,i->ab", e, e, f)
+        assert np.allclose(stress, (np.outer(a, a) + d * CS2 * np.eye(2)) * Th, atol=1e-13)
+
+
+# ------------------------------------------------------ small problem helper
+
+def _problem(n=12, N=10, Q=9, chi=-0.1, adv=True, solid=False, seed=0, source_order=2, alpha=1e-3):
+    w = W.aniso(n, n, N, seed=seed, precision=64, chi=chi)
+    if not adv:
+        w.adv = "none"
+    if Q == 5:
+        w.Q = 5
+        w.aniso, w.adv = "const", "none"
+    if solid:
+        w.solid = W.disc_mask(n, n, seed + 7, rmin=1.5, rmax=3.0, fraction=0.15)
+        w.window = (2, 3, n - 5, n - 6)
+        x0, y0, cx, cy = w.window
+        w.cmask = (1 - w.solid[y0:y0 + cy, x0:x0 + cx]).astype(np.uint8)
+    w.source_order = source_order
+    w.alpha = alpha
+    return w, oracle.from_workload(w)
+
+
+# ----------------------------------------------------------- special cases
+
+def _bgk_numpy(p, s):
+    """Independent BGK advection-diffusion loop: f <- f - s (f - f^eq), pull-stream."""
+    e, w, _, _ = oracle.lattice(p.Q)
+    n = p.nx
+    a = p.a if p.a is not None else np.zeros((n, n, 2))
+    def feq(Th, d):
+        ea = np.einsum("ia,yxa->yxi", e, a)
+        aa = np.einsum("yxa,yxb->yxab", a, a)
+        U = np.einsum("ia,ib->iab", e, e) - CS2 * np.eye(2)[None]
+        BU = np.einsum("yxab,iab->yxi", aa, U) + (d - 1) * CS2 * np.einsum("iaa->i", U)[None, None]
+        return w[None, None] * Th[..., None] * (1 + ea / CS2 + BU / (2 * CS2 * CS2))
+    fu, fv = feq(p.u0, p.d_u), feq(p.v0, p.d_v)
+    for _ in range(p.N):
+        for f, d in ((fu, p.d_u), (fv, p.d_v)):
+            f -= s * (f - feq(f.sum(-1), d))
+            for i in range(p.Q):
+                f[..., i] = np.roll(np.roll(f[..., i], e[i, 0], axis=1), e[i, 1], axis=0)
+    return fu.sum(-1), fv.sum(-1)
+
+
+@pytest.mark.parametrize("Q", [5, 9])
+def test_mrt_reduces_to_bgk(Q):
+    """K = s I and s_1..s_6 = s: M^-1 Pi M = s I, the MRT is the BGK scheme."""
+    s = 1.3
+    w, p = _problem(n=10, N=15, Q=Q, chi=0.0)
+    p.r_vu = p.r_vv = 0.0
+    D = (1.0 / s - 0.5) * CS2          # K = s I  <=>  D = d Cs^2 tau (1/s - 1/2)
+    p.Du = np.broadcast_to([D, 0.0, D], (10, 10, 3)).copy()
+    p.Dv = p.Du.copy()
+    p.s = (s,) * 7
+    if Q == 9:
+        p.a = np.random.default_rng(1).uniform(-0.05, 0.05, (10, 10, 2))
+    _, u, v = oracle.forward(p)
+    ub, vb = _bgk_numpy(p, s)
+    assert np.abs(u - ub).max() < 1e-13
+    assert np.abs(v - vb).max() < 1e-13
+
+
+@pytest.mark.parametrize("solid", [False, True])
+def test_mass_conservation(solid):
+    """Periodic / bounce-back box, Phi = g = 0, chemotaxis on: sum u and sum v
+    are invariant (sum_i S_i = 0, eq. TF0; collision conserves m0)."""
+    w, p = _problem(n=16, N=40, chi=-0.1, solid=solid)
+    p.r_vu = p.r_vv = 0.0
+    p.v0 = 1.0 + 0.3 * np.sin(np.arange(16) / 3.0)[None, :] * np.ones((16, 1))
+    mu, mv, _ = oracle.forward_trace(p)
+    assert np.abs(mu / mu[0] - 1).max() < 1e-14
+    assert np.abs(mv / mv[0] - 1).max() < 1e-14
+
+
+@pytest.mark.parametrize("source_order", [1, 2])
+def test_source_mass_balance(source_order):
+    """sum v^{n+1} - sum v^n = tau sum [Phi^n + (1/2)(Phi^n - Phi^{n-1})], Phi^{-1} := Phi^0."""
+    w, p = _problem(n=14, N=12, chi=-0.1, source_order=source_order)
+    g = w.random_control(4, 0.05)
+    mu, mv, sp = oracle.forward_trace(p, g)
+    dv = np.diff(mv)
+    prev = np.concatenate([[sp[0]], sp[:-1]])
+    expect = sp + (0.5 * (sp - prev) if source_order == 2 else 0.0)
+    assert np.allclose(dv, expect[:-1], rtol=0, atol=1e-12 * np.abs(mv).max())
+    assert np.abs(mu / mu[0] - 1).max() < 1e-14
+
+
+def _gauss_field(n, mu, Sig, mass):
+    Si = np.linalg.inv(Sig)
+    det = np.linalg.det(Sig)
+    x = np.arange(n)[None, :]
+    y = np.arange(n)[:, None]
+    out = np.zeros((n, n))
+    for ix in (-1, 0, 1):
+        for iy in (-1, 0, 1):
+            dx = x - mu[0] + ix * n
+            dy = y - mu[1] + iy * n
+            out += np.exp(-0.5 * (Si[0, 0] * dx * dx + 2 * Si[0, 1] * dx * dy + Si[1, 1] * dy * dy))
+    return mass * out / (2 * np.pi * np.sqrt(det))
+
+
+def _gauss_run(n, sig0, steps, lam, th, Q, a):
+    D = rotated_tensor(lam, np.array(th))
+    Dm = np.array([[D[0], D[1]], [D[1], D[2]]])
+    mu = np.array([n / 2, n / 2])
+    mass = 100.0 * (n / 32) ** 2
+    u0 = 1.0 + _gauss_field(n, mu, sig0 ** 2 * np.eye(2), mass)
+    Df = np.broadcast_to(D, (n, n, 3)).copy()
+    af = np.broadcast_to(np.array(a, float), (n, n, 2)).copy()
+    p = oracle.Problem(nx=n, ny=n, N=steps, Q=Q, Du=Df, Dv=Df, u0=u0, v0=np.zeros((n, n)),
+                       u_tgt=np.zeros((n, n)), a=af)
+    _, u, _ = oracle.forward(p)
+    exact = 1.0 + _gauss_field(n, mu + np.array(a) * steps, sig0 ** 2 * np.eye(2) + 2 * Dm * steps, mass)
+    return np.linalg.norm(u - exact) / np.linalg.norm(exact - 1.0), abs(u.sum() - u0.sum()) / u0.sum()
+
+
+@pytest.mark.parametrize("Q,lam,th,adv", [(9, (0.08, 0.02), 0.6, 0.0), (9, (0.08, 0.02), 0.6, 0.04),
+                                          (5, (0.1, 0.1), 0.0, 0.0)])
+def test_anisotropic_gaussian_closed_form(Q, lam, th, adv):
+    """chi = 0, no reaction, constant D = R diag(l1, l2) R^T: a Gaussian of
+    covariance S0 evolves to S0 + 2 D t (centre moved by a t).  Pins the
+    D -> K map D = d Cs^2 tau (K^-1 - I/2), M0, Pi and phi^eq: 2nd-order
+    convergence under diffusive refinement (h/2, tau/4, a/2)."""
+    errs = []
+    for k, (n, s0, N) in enumerate([(32, 2.0, 25), (64, 4.0, 100), (128, 8.0, 400)]):
+        a = (adv / 2 ** k, -adv / 2 ** (k + 1))
+        e, dm = _gauss_run(n, s0, N, lam, th, Q, a)
+        errs.append(e)
+        assert dm < 1e-13
+    assert errs[0] < 2.5e-2
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 3.5 < r1 < 4.6 and 3.5 < r2 < 4.6, errs
+
+
+def _spectral_ref(L, T, Du, Dv, chi, rvu, rvv, u0, v0, dt=0.02):
+    """Pseudo-spectral RK4 solution of u_t = div(D_u grad u - chi u grad v),
+    v_t = div(D_v grad v) + r_vu u + r_vv v on a periodic square."""
+    n = u0.shape[0]
+    k = 2 * np.pi * np.fft.fftfreq(n, d=L / n)
+    KX, KY = np.meshgrid(k, k)
+
+    def d(f, K):
+        return np.real(np.fft.ifft2(1j * K * np.fft.fft2(f)))
+
+    def rhs(u, v):
+        ux, uy, vx, vy = d(u, KX), d(u, KY), d(v, KX), d(v, KY)
+        fxu = Du[0] * ux + Du[1] * uy - chi * u * vx
+        fyu = Du[1] * ux + Du[2] * uy - chi * u * vy
+        fxv = Dv[0] * vx + Dv[1] * vy
+        fyv = Dv[1] * vx + Dv[2] * vy
+        return d(fxu, KX) + d(fyu, KY), d(fxv, KX) + d(fyv, KY) + rvu * u + rvv * v
+
+    u, v = u0.copy(), v0.copy()
+    for _ in range(int(round(T / dt))):
+        k1 = rhs(u, v)
+        k2 = rhs(u + dt / 2 * k1[0], v + dt / 2 * k1[1])
+        k3 = rhs(u + dt / 2 * k2[0], v + dt / 2 * k2[1])
+        k4 = rhs(u + dt * k3[0], v + dt * k3[1])
+        u = u + dt / 6 * (k1[0] + 2 * k2[0] + 2 * k3[0] + k4[0])
+        v = v + dt / 6 * (k1[1] + 2 * k2[1] + 2 * k3[1] + k4[1])
+    return u, v
+
+
+@pytest.mark.slow
+def test_chemotaxis_coupling_against_pde():
+    """The coupled scheme (cross-diffusion S_u with A = K D_{u,1}/tau and the
+    local grad v reading) converges at 2nd order to an independent
+    pseudo-spectral solution of the PDE; the opposite chemotaxis sign does not."""
+    L, T = 32, 20
+    Du = rotated_tensor((0.08, 0.02), np.array(0.6))
+    Dv = np.array([0.2, 0.0, 0.2])
+    chi, rvu, rvv = -0.1, 0.02, -0.01
+
+    def init(n):
+        x = np.arange(n)[None, :] * L / n
+        y = np.arange(n)[:, None] * L / n
+        k = 2 * np.pi / L
+        return 1 + 0.2 * np.cos(k * x) * np.sin(k * y) + 0.1 * np.sin(2 * k * x), \
+            1 + 0.3 * np.sin(k * (x + y)) * np.ones_like(x)
+
+    us, vs = _spectral_ref(L, T, Du, Dv, chi, rvu, rvv, *init(L))
+
+    def lb(r, chi_):
+        n = L * r
+        u0, v0 = init(n)
+        p = oracle.Problem(nx=n, ny=n, N=T * r * r, Q=9, Du=np.broadcast_to(Du, (n, n, 3)).copy(),
+                           Dv=np.broadcast_to(Dv, (n, n, 3)).copy(), u0=u0, v0=v0, u_tgt=np.zeros((n, n)),
+                           chi=chi_, r_vu=rvu / r ** 2, r_vv=rvv / r ** 2)
+        _, u, v = oracle.forward(p)
+        return u[::r, ::r], v[::r, ::r]
+
+    errs = []
+    for r in (1, 2, 4):
+        u, v = lb(r, chi)
+        errs.append((np.linalg.norm(u - us) / np.linalg.norm(us - us.mean()),
+                     np.linalg.norm(v - vs) / np.linalg.norm(vs - vs.mean())))
+    for c in range(2):
+        r1, r2 = errs[0][c] / errs[1][c], errs[1][c] / errs[2][c]
+        assert 3.5 < r1 < 4.6 and 3.5 < r2 < 4.6, errs
+    u_flip, _ = lb(1, -chi)
+    assert np.linalg.norm(u_flip - us) / np.linalg.norm(us - us.mean()) > 20 * errs[0][0]
+
+
+# --------------------------------------------------------- adjoint / gradient
+
+@pytest.mark.parametrize("case", [
+    dict(Q=9, adv=True, solid=False, source_order=2),
+    dict(Q=9, adv=True, solid=True, source_order=2),
+    dict(Q=9, adv=False, solid=False, source_order=1),
+    dict(Q=5, adv=False, solid=False, source_order=2),
+])
+def test_dot_product_identity(case):
+    """<w, TLM(dg, df0)> = <ADJ(w), (dg, df0)>: the AMRT sweep is the exact
+    transpose of the sensitivity LBE (LIBEG-V), to roundoff."""
+    n = 12
+    w, p = _problem(n=n, N=9, chi=-0.1, alpha=0.0, **case)
+    rng = np.random.default_rng(5)
+    g = w.random_control(1, 0.05)
+    dg = rng.standard_normal(g.shape)
+    if p.cmask is not None:
+        dg *= p.cmask[None]
+    df0 = rng.standard_normal((n, n, 2, p.Q))
+    if p.solid is not None:
+        df0 *= (1 - p.solid)[:, :, None, None]
+    su, sv = rng.standard_normal((n, n)), rng.standard_normal((n, n))
+    if p.solid is not None:
+        su *= 1 - p.solid
+        sv *= 1 - p.solid
+    _, du, dv = oracle.tlm(p, g, dg, df0)
+    _, E, psi0 = oracle.adjoint(p, g, su, sv, want_psi0=True)
+    lhs = np.sum(su * du) + np.sum(sv * dv)
+    rhs = np.sum(E * dg) + np.sum(psi0 * df0)
+    assert abs(lhs - rhs) <= 1e-12 * (abs(lhs) + abs(rhs)), (lhs, rhs)
+
+
+def test_gradient_every_component_fd():
+    """Every component of dJ/dg against central finite differences (8x8, 10 steps)."""
+    w, p = _problem(n=8, N=10, chi=-0.1, alpha=1e-2)
+    g = w.random_control(2, 0.05)
+    J0, E, _ = oracle.adjoint(p, g)
+    h = 1e-6
+    fd = np.zeros_like(g)
+    for idx in np.ndindex(g.shape):
+        gp = g.copy()
+        gp[idx] += h
+        gm = g.copy()
+        gm[idx] -= h
+        fd[idx] = (oracle.forward(p, gp)[0] - oracle.forward(p, gm)[0]) / (2 * h)
+    assert np.abs(fd - E).max() <= 1e-6 * np.abs(E).max()
+
+
+@pytest.mark.parametrize("Q", [5, 9])
+def test_gradient_fd_16x16(Q):
+    """16x16, 50 steps, plain64 physics (sigma = 2): sampled components and a
+    random direction against central finite differences."""
+    w = W.plain64(16, 16, 50, sigma=2.0, Q=Q)
+    w.chi = -0.05
+    p = oracle.from_workload(w)
+    g = w.random_control(9, 0.02)
+    J0, E, _ = oracle.adjoint(p, g)
+    h = 1e-6
+    rng = np.random.default_rng(4)
+    flat = rng.choice(g.size, 24, replace=False)
+    for k in flat:
+        idx = np.unravel_index(k, g.shape)
+        gp = g.copy()
+        gp[idx] += h
+        gm = g.copy()
+        gm[idx] -= h
+        fd = (oracle.forward(p, gp)[0] - oracle.forward(p, gm)[0]) / (2 * h)
+        assert abs(fd - E[idx]) <= 1e-6 * np.abs(E).max()
+    d = rng.standard_normal(g.shape)
+    fd = (oracle.forward(p, g + h * d)[0] - oracle.forward(p, g - h * d)[0]) / (2 * h)
+    # central-difference roundoff is about eps * J / h
+    assert abs(fd - np.sum(E * d)) <= 1e-7 * abs(fd) + 50 * np.finfo(float).eps * J0 / h
+
+
+def test_gradient_fd_geometry():
+    """Bounce-back, window control with a mask, advection: sampled FD components."""
+    w, p = _problem(n=12, N=10, chi=-0.1, solid=True, alpha=1e-2)
+    g = w.random_control(6, 0.05)
+    J0, E, _ = oracle.adjoint(p, g)
+    h = 1e-6
+    rng = np.random.default_rng(8)
+    for k in rng.choice(g.size, 30, replace=False):
+        idx = np.unravel_index(k, g.shape)
+        gp = g.copy()
+        gp[idx] += h
+        gm = g.copy()
+        gm[idx] -= h
+        fd = (oracle.forward(p, gp)[0] - oracle.forward(p, gm)[0]) / (2 * h)
+        if p.cmask[idx[1], idx[2]] == 0:
+            assert E[idx] == 0.0 and abs(fd) < 1e-12
+        else:
+            assert abs(fd - E[idx]) <= 1e-6 * np.abs(E).max()
+
+
+def test_gd_step_decreases_cost():
+    """One Armijo gradient-descent iteration lowers J (discrete-adjoint algorithm)."""
+    w = W.plain64(16, 16, 30, sigma=2.0, Q=9)
+    w.chi = -0.05
+    p = oracle.from_workload(w)
+    g = np.zeros(w.ctrl_shape)
+    g1, info = oracle.gd_step(p, g)
+    assert info["J"] < info["J0"]
+    g2, info2 = oracle.gd_step(p, g1, lam_prev=info["lam"])
+    assert info2["J"] < info["J"]
