@@ -1,0 +1,290 @@
+"""Benchmark: fwd+adjoint MLUPS of the MRT/AMRT gradient on one GB300.
+
+One step = one gradient evaluation of the anisotropic 1024x1024 D2Q9 FP32
+problem (2000 time steps, checkpoint every 100): the forward MRT solve writing
+checkpoints, the segment recompute writing the adjoint tape, the AMRT adjoint
+sweep with the fused gradient, and the FP64 reductions of J and ||dJ/dg||.
+MLUPS = nodes x time steps / seconds per gradient evaluation.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun each rank runs an independent problem (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(name="aniso1024", nx=1024, ny=1024, N=2000, k=100)
+# algorithmic bytes per node and step (FP32, D2Q9, two species):
+#   forward   18 pulls + 18 stores (144) + angle (4) + g (4) + Phi in/out (8)  = 160
+#   recompute forward + tape (u, G_x, G_y) store (12)                           = 172
+#   adjoint   144 + tape read (12) + angle (4) + sigma in/out (8) + g (4) + dJ/dg (4) = 176
+BYTES = dict(forward=160, recompute=172, adjoint=176)
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            pk = json.load(fh)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self):
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self, device_index=0):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9 or f[0] != str(device_index):
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    smax = float(f[2])
+                except ValueError:
+                    continue
+                for nm, val in zip(names, f[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(nsteps=8):
+    """The FP64 CPU oracle, as it stands, on a bounded sample of the workload:
+    the full 1024x1024 lattice for `nsteps` time steps, forward + adjoint."""
+    import numpy as np  # noqa: F401
+
+    import oracle
+    from paper_1908_03876_gb300 import workloads as W
+
+    oracle.build()
+    w = W.aniso(WORKLOAD["nx"], WORKLOAD["ny"], nsteps, seed=1, precision=64, ckpt_every=nsteps)
+    p = oracle.from_workload(w)
+    g = w.random_control(0, 0.01)
+    t0 = time.perf_counter()
+    oracle.adjoint(p, g)  # runs the forward and the AMRT sweep
+    dt = time.perf_counter() - t0
+    mlups = w.nx * w.ny * nsteps / dt / 1e6
+    return {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"{w.nx}x{w.ny} D2Q9 FP64, {nsteps} of {WORKLOAD['N']} time steps, forward + AMRT adjoint, "
+                      f"{dt:.1f} s, single-threaded C"}
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the CPU oracle timed on this machine's host cores."""
+    if rank != 0:
+        return
+    steps, warm = max(1, args.steps), max(0, args.warmup)
+    nsteps = 4
+    times = []
+    base = None
+    for i in range(warm + steps):
+        b = cpu_baseline(nsteps)
+        if i >= warm:
+            times.append(b)
+        base = b
+    val = statistics.mean(t["value"] for t in times)
+    base["value"] = val
+    line = {"metric": "fwd+adjoint MLUPS", "value": val, "unit": "MLUPS", "n_gpus": args.gpus, "steps": steps,
+            "warmup": warm, "ms_per_step": WORKLOAD["nx"] * WORKLOAD["ny"] * WORKLOAD["N"] / val / 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded)", "impl": "reference",
+            "config": {"workload": "aniso1024: 1024x1024 D2Q9, 2000 steps, k=100 (oracle timed on a "
+                                   f"{nsteps}-step sample per bench step)", "l2": "inputs larger than L2"},
+            "cpu_baseline": base,
+            "e2e": {"value": val, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import numpy as np
+    import torch
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_1908_03876_gb300.build import build
+
+    if rank == 0:
+        build()
+    if dist:
+        dist.barrier()
+    from paper_1908_03876_gb300 import workloads as W
+    from paper_1908_03876_gb300.problem import Problem
+
+    wl = WORKLOAD
+    w = W.aniso(wl["nx"], wl["ny"], wl["N"], seed=1 + rank, precision=32, ckpt_every=wl["k"])
+    prob = Problem(w, device=dev)
+    g = torch.as_tensor(w.random_control(100 + rank, 0.01), dtype=torch.float32, device=dev).contiguous()
+    E = torch.empty_like(g)
+    nodes = w.nx * w.ny
+
+    def grad_step():
+        prob.gradient(g, out=E)
+
+    for _ in range(args.warmup):
+        grad_step()
+    torch.cuda.synchronize()
+
+    # ---- timed region (device events on the problem's stream)
+    clocks = Clocks()
+    if rank == 0:
+        clocks.start()
+    prob.set_timing(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    stream = prob.stream
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        grad_step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms_total = ev0.elapsed_time(ev1)
+    phases = prob.timing()
+    prob.set_timing(False)
+    J, gsq, ginf = prob.norms()
+    clk = clocks.stop(local) if rank == 0 else None
+    t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_step = float(t.item()) / args.steps
+    mlups = world * nodes * w.N / (ms_step * 1e-3) / 1e6
+
+    # ---- roofline of the kernels, from the same timed region
+    hbm, peak_kind = _peaks()
+    roof = {}
+    for ph in ("forward", "recompute", "adjoint"):
+        ms, launches = phases[ph]
+        if launches <= 0:
+            continue
+        per_launch_s = ms * 1e-3 / launches
+        traffic = BYTES[ph] * nodes
+        ach = traffic / per_launch_s / 1e9
+        roof[ph] = {"achieved": ach, "frac": ach / hbm, "ms_total": ms, "launches": launches,
+                    "us_per_launch": per_launch_s * 1e6, "bytes_per_node": BYTES[ph]}
+    dom = max(roof, key=lambda k: roof[k]["ms_total"]) if roof else "forward"
+    kern = {"forward": "k_forward", "recompute": "k_forward (tape)", "adjoint": "k_adjoint"}[dom]
+    roofline = {"bound": "hbm", "achieved": roof[dom]["achieved"], "peak": hbm, "unit": "GB/s",
+                "frac": roof[dom]["frac"], "traffic": None, "kernel": kern, "peak_source": peak_kind,
+                "bytes_per_launch": BYTES[dom] * nodes}
+
+    # ---- end to end: host control in, host gradient and cost out, every step
+    e2e = None
+    if rank == 0:
+        try:
+            g_host = torch.empty(g.shape, dtype=g.dtype, pin_memory=True)
+            g_host.copy_(g.cpu())
+            E_host = torch.empty_like(g_host, pin_memory=True)
+            J_host = torch.empty(1, dtype=torch.float64, pin_memory=True)
+            torch.cuda.synchronize()
+            ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ne = max(1, min(args.steps, 3))
+            ea.record(stream)
+            for _ in range(ne):
+                g.copy_(g_host, non_blocking=True)
+                Jd, _ = prob.gradient(g, out=E)
+                E_host.copy_(E, non_blocking=True)
+                J_host.copy_(Jd, non_blocking=True)
+            eb.record(stream)
+            torch.cuda.synchronize()
+            ms_e2e = ea.elapsed_time(eb) / ne
+            e2e = {"value": nodes * w.N / (ms_e2e * 1e-3) / 1e6, "unit": "MLUPS",
+                   "h2d_bytes_per_step": g.numel() * g.element_size(),
+                   "d2h_bytes_per_step": E.numel() * E.element_size() + 8, "ms_per_step": ms_e2e}
+        except Exception as exc:  # pinned memory can fail on small hosts
+            e2e = {"value": None, "unit": "MLUPS", "error": str(exc)[:200]}
+
+    launches_per_step = 3 * w.N - wl["k"] + 3
+    if rank == 0:
+        cpu = None if args.no_cpu_baseline else cpu_baseline()
+        line = {
+            "metric": "fwd+adjoint MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 (FP64 reductions)", "data": "synthetic (seeded)",
+            "config": {"workload": "aniso1024: 1024x1024 D2Q9 FP32, 2000 steps, checkpoint every 100, "
+                                   "rotated anisotropic D_u = D_v, shear convection, chemotaxis chi=-0.1",
+                       "step": "one gradient evaluation (forward + recompute + AMRT adjoint + FP64 reductions)",
+                       "l2": "inputs larger than L2 (8.4 GB control, 1.5 GB checkpoints per step)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roofline,
+            "kernels": roof,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "e2e": e2e,
+            "gpu_launches": launches_per_step * args.steps,
+            "J": J, "grad_norm": float(np.sqrt(gsq)),
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

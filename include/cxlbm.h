@@ -1,0 +1,194 @@
+/*
+ * cxlbm.h -- C ABI of the GB300 (sm_103a) MRT / AMRT lattice Boltzmann
+ * optimal-control library for the two-species chemotaxis system
+ *
+ *     du/dt = div(D_u grad u - chi u grad v) - div(a u)
+ *     dv/dt = div(D_v grad v) - div(a v) + r_vu u + r_vv v + g
+ *
+ * (the paper's system (eq:ReacDiff) with Theta in {u, v}, D_{u,1} = chi u I,
+ * convective flux T_Theta = a Theta, and the distributed control g acting on
+ * the v equation; Sec. 2.1 states the control problem (EPS) and Sec. 3.2.1 the
+ * discrete-adjoint optimisation process that the calls below follow).
+ *
+ * Discrete problem solved (Sec. 3.1 and 3.2):
+ *   forward   eq. (LBE)/(LBEG): per species, MRT collision in moment space
+ *             with M0 and the block relaxation matrix Pi (K block from
+ *             D = d C_s^2 tau (K^-1 - I/2)), cross-diffusion source S_u (eq. S),
+ *             reaction/control source (eq. PhiS) with the tau/2 time-derivative
+ *             term, pull streaming with halfway bounce-back at solid nodes.
+ *   adjoint   AMRT (eqs. CAE, AEDs, AEDsM, CAEL): reverse-time sweep streaming
+ *             along -e_i, transposed collision, adjoint equilibrium broadcast,
+ *             coupling terms; the gradient (gradientLattice / JD-H-B) is
+ *             assembled inside the same kernel.
+ *   cost      J = 1/2 sum_x (u^N - u_target)^2 + alpha sum_{n<N} sum_x g^n(x)^2.
+ *
+ * Conventions for every call:
+ *   - Pointers documented as "device" are CUDA device pointers owned by the
+ *     caller; the library never allocates device memory (the caller passes
+ *     one workspace) and never frees caller memory.  It keeps no input pointer
+ *     past the call that receives it.
+ *   - "T" is float when precision == 32 and double when precision == 64.
+ *   - Node fields are row-major [ny][nx]; control and gradient buffers are
+ *     [n_steps][ctrl_ny][ctrl_nx]; population buffers are [2][Q][ny][nx]
+ *     (species u then v).
+ *   - All calls are ordered on the problem's stream and asynchronous unless
+ *     stated otherwise; cx_step, cx_get_norms and cx_get_timing synchronise.
+ *   - Every call returns a cx_status; CX_OK is 0.  A CUDA error (launch or a
+ *     failed runtime call) returns CX_ERR_CUDA.  Errors a kernel detects (a
+ *     non-finite cost or gradient) are recorded in a device status word and
+ *     reported by the next synchronising call.
+ */
+#ifndef CXLBM_H
+#define CXLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* cudaStream_t; /* the CUDA runtime's stream handle */
+
+typedef enum {
+    CX_OK = 0,
+    CX_ERR_INVALID_ARG = 1, /* bad descriptor or argument (checked on the host) */
+    CX_ERR_WORKSPACE = 2,   /* workspace missing, too small or misaligned      */
+    CX_ERR_CUDA = 3,        /* a CUDA runtime call or kernel launch failed     */
+    CX_ERR_STATE = 4,       /* call out of order (e.g. adjoint before forward) */
+    CX_ERR_UNSTABLE = 5,    /* non-finite cost or gradient                     */
+    CX_ERR_LINESEARCH = 6,  /* Armijo backtracking found no acceptable step    */
+    CX_ERR_TIMEOUT = 7,     /* a bounded device-side wait ran out              */
+    CX_ERR_INTERNAL = 8
+} cx_status;
+
+enum { CX_ANISO_CONST = 0, CX_ANISO_ROTATED = 1, CX_ANISO_FIELD = 2 };
+enum { CX_ADV_NONE = 0, CX_ADV_ROW = 1, CX_ADV_FIELD = 2 };
+
+/* Problem descriptor.  Read once by cx_workspace_size / cx_create. */
+typedef struct {
+    int nx, ny;          /* lattice nodes (h = 1), 3 <= nx, ny                       */
+    int n_steps;         /* N time steps (tau = T/N), >= 1                            */
+    int lattice;         /* 9 (D2Q9, Sec. 3.1) or 5 (D2Q5)                            */
+    int precision;       /* 32 or 64: type T of populations, controls and gradients  */
+    int ckpt_every;      /* k: checkpoint interval of the forward; 0 means N          */
+    double tau;          /* lattice time step, 1 in lattice units (c = h/tau = 1)     */
+    /* self-diffusion tensors D_u, D_v (symmetric) */
+    int aniso;           /* CX_ANISO_*                                                */
+    double D_u[3], D_v[3];       /* CONST: (Dxx, Dxy, Dyy)                             */
+    double lam_u[2], lam_v[2];   /* ROTATED: eigenvalues along (cos t, sin t) and its normal */
+    const double* theta;         /* ROTATED: device [ny][nx] angle t(x)                */
+    const double* D_u_field;     /* FIELD: device [ny][nx][3]                          */
+    const double* D_v_field;     /* FIELD: device [ny][nx][3]                          */
+    double d_u, d_v;     /* d_Theta of the equilibrium (eq. phieq), > 0               */
+    double chi;          /* chemotactic sensitivity (signed)                         */
+    double r_vu, r_vv;   /* Phi_v = r_vu u + r_vv v + g                               */
+    int adv;             /* CX_ADV_*                                                  */
+    const double* a;     /* ROW: device [ny][2]; FIELD: device [ny][nx][2]; else NULL */
+    const uint8_t* solid;     /* device [ny][nx], 1 = solid (bounce-back), or NULL   */
+    int ctrl_x0, ctrl_y0, ctrl_nx, ctrl_ny; /* control window; ctrl_nx = 0: whole grid */
+    const uint8_t* ctrl_mask; /* device [ctrl_ny][ctrl_nx], 1 = controlled, or NULL   */
+    const double* u_target;   /* device [ny][nx]                                     */
+    double alpha;             /* control penalty weight, >= 0                        */
+    double s[7];              /* free relaxation rates s0..s6 of Pi, in (0, 2)       */
+    int source_order;         /* 2: keep (tau/2)(Phi^n - Phi^{n-1}); 1: drop it      */
+} cx_problem_desc;
+
+typedef struct cx_problem cx_problem; /* opaque, library-owned host object */
+
+typedef struct {
+    double J0;      /* cost at the incoming control                  */
+    double J;       /* cost at the accepted control                  */
+    double lam;     /* accepted step length                          */
+    double grad_sq; /* ||dJ/dg||^2 at the incoming control           */
+    double grad_inf;/* max |dJ/dg| at the incoming control           */
+    int trials;     /* forward solves spent in the line search       */
+} cx_step_info;
+
+/* Bytes of device workspace the problem needs (host call, no device work).
+ * Errors: CX_ERR_INVALID_ARG for an inconsistent descriptor. */
+cx_status cx_workspace_size(const cx_problem_desc* desc, size_t* bytes);
+
+/* Create a problem bound to a caller-owned device workspace of at least
+ * cx_workspace_size bytes (256-byte aligned) and to `stream`.  Copies and
+ * converts every descriptor field (tensor, velocity, mask and target fields)
+ * into the workspace, then synchronises the stream once.  The descriptor's
+ * device arrays may be freed after the call.  Checks the relaxation blocks
+ * K (eigenvalues in (0, 2), the stability remark after (UGS)).
+ * Errors: CX_ERR_INVALID_ARG, CX_ERR_WORKSPACE, CX_ERR_CUDA. */
+cx_status cx_create(const cx_problem_desc* desc, void* workspace, size_t bytes, cudaStream_t stream,
+                    cx_problem** out);
+
+/* Initial populations phi^eq(u0), phi^eq(v0) (device T [ny][nx] each),
+ * the initial condition of the forward solve.  Errors: CX_ERR_INVALID_ARG. */
+cx_status cx_set_initial(cx_problem* p, const void* u0, const void* v0);
+
+/* Forward MRT solve over N steps with control g (device T [N][ctrl_ny][ctrl_nx])
+ * (step 2 of the discrete-adjoint algorithm, Sec. 3.2.1).  Stores every k-th
+ * state as a checkpoint and the last segment's adjoint tape, then writes the
+ * FP64 cost J to J_dev (device double, may be NULL).  Needs cx_set_initial.
+ * Errors: CX_ERR_STATE (no initial state), CX_ERR_INVALID_ARG, CX_ERR_CUDA. */
+cx_status cx_forward(cx_problem* p, const void* g, double* J_dev);
+
+/* AMRT adjoint sweep with fused gradient assembly (steps 3-4 of the
+ * algorithm, eqs. CAE/CAEL and gradientLattice): reverse-time, segment by
+ * segment, recomputing each segment's forward from its checkpoint.
+ * g must be the control of the preceding cx_forward.  seed_u / seed_v
+ * (device T [ny][nx]) are the adjoint of u^N / v^N; seed_u == NULL uses
+ * u^N - u_target (the cost's own terminal term), seed_v == NULL uses 0.
+ * Writes dJdg (device T [N][ctrl_ny][ctrl_nx]): the gradient of
+ * sum(seed_u u^N + seed_v v^N) + alpha ||g||^2 -- of J itself when both seeds
+ * are NULL -- with zeros at uncontrolled nodes.
+ * Errors: CX_ERR_STATE (no forward since the last cx_create / cx_set_initial). */
+cx_status cx_adjoint(cx_problem* p, const void* g, const void* seed_u, const void* seed_v, void* dJdg);
+
+/* cx_forward followed by cx_adjoint with NULL seeds: J (device double, may be
+ * NULL) and dJ/dg. */
+cx_status cx_gradient(cx_problem* p, const void* g, void* dJdg, double* J_dev);
+
+/* One steepest-descent iteration with Armijo backtracking (step 5 of the
+ * algorithm; first trial min(1, 1/||E||_inf), the heuristic of the remark
+ * after the continuous gradient algorithm, then twice the previous step).
+ * g_inout (device T [N][ctrl_ny][ctrl_nx]) is updated in place to g - lam E
+ * when J(g - lam E) <= J(g) - 1e-4 lam ||E||^2 (FP64 test); lam halves up to
+ * 30 times.  E_work (device T, same shape, caller-owned) receives the
+ * gradient E = dJ/dg at the incoming g.  Runs a forward first unless the
+ * previous cx_forward / accepted cx_step left its state at g_inout (the
+ * accepted trial's forward is reused, so each iteration costs one adjoint
+ * plus its trial forwards).  Synchronises once per trial.  info (host) may be
+ * NULL.  Errors: CX_ERR_LINESEARCH (g_inout unchanged), CX_ERR_UNSTABLE. */
+cx_status cx_step(cx_problem* p, void* g_inout, void* E_work, cx_step_info* info);
+
+/* u^N and v^N of the last forward (device T [ny][nx] each, either may be NULL). */
+cx_status cx_get_fields(cx_problem* p, void* u_out, void* v_out);
+
+/* Adjoint populations psi^0 of the last cx_adjoint: the sensitivity of the
+ * seeded functional to the initial populations (device T [2][Q][ny][nx]). */
+cx_status cx_get_psi0(cx_problem* p, void* out);
+
+/* Synchronising: cost of the last forward, ||dJ/dg||^2 and max |dJ/dg| of the
+ * last adjoint (host doubles, any may be NULL); returns any recorded device
+ * error (CX_ERR_UNSTABLE for a non-finite value). */
+cx_status cx_get_norms(cx_problem* p, double* J, double* grad_sq, double* grad_inf);
+
+/* Launch shape of the lattice kernels (threads per block in x and y; bx a
+ * multiple of 32, bx * by <= 1024).  Errors: CX_ERR_INVALID_ARG. */
+cx_status cx_set_launch(cx_problem* p, int bx, int by);
+
+/* Per-phase timing with CUDA events on the problem's stream: enable != 0
+ * starts accumulating.  cx_get_timing (synchronising) returns milliseconds
+ * and kernel-launch counts for the phases [forward, recompute, adjoint,
+ * other] (ms[4], launches[4]; either may be NULL) and resets them. */
+cx_status cx_set_timing(cx_problem* p, int enable);
+cx_status cx_get_timing(cx_problem* p, double* ms, long long* launches);
+
+/* Release the host object (the workspace stays the caller's). */
+cx_status cx_destroy(cx_problem* p);
+
+/* Static text for a status code. */
+const char* cx_status_string(cx_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CXLBM_H */

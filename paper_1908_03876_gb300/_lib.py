@@ -1,0 +1,103 @@
+"""ctypes view of the C ABI in include/cxlbm.h (argument marshalling only).
+
+Loading fails loudly if libcxlbm.so is missing: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcxlbm.so")
+
+CX_ANISO_CONST, CX_ANISO_ROTATED, CX_ANISO_FIELD = 0, 1, 2
+CX_ADV_NONE, CX_ADV_ROW, CX_ADV_FIELD = 0, 1, 2
+
+STATUS = {
+    0: "CX_OK", 1: "CX_ERR_INVALID_ARG", 2: "CX_ERR_WORKSPACE", 3: "CX_ERR_CUDA", 4: "CX_ERR_STATE",
+    5: "CX_ERR_UNSTABLE", 6: "CX_ERR_LINESEARCH", 7: "CX_ERR_TIMEOUT", 8: "CX_ERR_INTERNAL",
+}
+
+# every exported symbol of include/cxlbm.h
+EXPORTS = [
+    "cx_workspace_size", "cx_create", "cx_set_initial", "cx_forward", "cx_adjoint", "cx_gradient", "cx_step",
+    "cx_get_fields", "cx_get_psi0", "cx_get_norms", "cx_set_launch", "cx_set_timing", "cx_get_timing",
+    "cx_destroy", "cx_status_string",
+]
+
+
+class CxError(RuntimeError):
+    def __init__(self, code: int, call: str):
+        self.code = code
+        super().__init__(f"{call} failed: {STATUS.get(code, code)}")
+
+
+class Desc(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("n_steps", ctypes.c_int), ("lattice", ctypes.c_int),
+        ("precision", ctypes.c_int), ("ckpt_every", ctypes.c_int), ("tau", ctypes.c_double),
+        ("aniso", ctypes.c_int),
+        ("D_u", ctypes.c_double * 3), ("D_v", ctypes.c_double * 3),
+        ("lam_u", ctypes.c_double * 2), ("lam_v", ctypes.c_double * 2),
+        ("theta", ctypes.c_void_p), ("D_u_field", ctypes.c_void_p), ("D_v_field", ctypes.c_void_p),
+        ("d_u", ctypes.c_double), ("d_v", ctypes.c_double),
+        ("chi", ctypes.c_double), ("r_vu", ctypes.c_double), ("r_vv", ctypes.c_double),
+        ("adv", ctypes.c_int), ("a", ctypes.c_void_p),
+        ("solid", ctypes.c_void_p),
+        ("ctrl_x0", ctypes.c_int), ("ctrl_y0", ctypes.c_int), ("ctrl_nx", ctypes.c_int), ("ctrl_ny", ctypes.c_int),
+        ("ctrl_mask", ctypes.c_void_p),
+        ("u_target", ctypes.c_void_p), ("alpha", ctypes.c_double),
+        ("s", ctypes.c_double * 7),
+        ("source_order", ctypes.c_int),
+    ]
+
+
+class StepInfo(ctypes.Structure):
+    _fields_ = [("J0", ctypes.c_double), ("J", ctypes.c_double), ("lam", ctypes.c_double),
+                ("grad_sq", ctypes.c_double), ("grad_inf", ctypes.c_double), ("trials", ctypes.c_int)]
+
+
+_lib = None
+
+
+def load():
+    """Load libcxlbm.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(
+            f"CUDA library {LIB_PATH} is missing; build it with "
+            "`python -c 'import __graft_entry__ as g; g.build()'` (no CPU fallback exists)")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, cint, dp = ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)
+    D = ctypes.POINTER(Desc)
+    sig = {
+        "cx_workspace_size": [D, ctypes.POINTER(ctypes.c_size_t)],
+        "cx_create": [D, vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)],
+        "cx_set_initial": [vp, vp, vp],
+        "cx_forward": [vp, vp, vp],
+        "cx_adjoint": [vp, vp, vp, vp, vp],
+        "cx_gradient": [vp, vp, vp, vp],
+        "cx_step": [vp, vp, vp, ctypes.POINTER(StepInfo)],
+        "cx_get_fields": [vp, vp, vp],
+        "cx_get_psi0": [vp, vp],
+        "cx_get_norms": [vp, dp, dp, dp],
+        "cx_set_launch": [vp, cint, cint],
+        "cx_set_timing": [vp, cint],
+        "cx_get_timing": [vp, dp, ctypes.POINTER(ctypes.c_longlong)],
+        "cx_destroy": [vp],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = cint
+    lib.cx_status_string.argtypes = [cint]
+    lib.cx_status_string.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def check(code: int, call: str):
+    if code != 0:
+        raise CxError(code, call)

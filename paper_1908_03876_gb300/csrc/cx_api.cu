@@ -1,0 +1,600 @@
+// cx_api.cu -- host side of the C ABI declared in include/cxlbm.h.
+//
+// The host code only validates descriptors, lays out the caller's workspace,
+// orders kernel launches on the problem's stream and reads back FP64 scalars
+// where a call is documented to synchronise.  All arithmetic of the method runs
+// in the kernels of cx_forward.cu, cx_adjoint.cu and cx_misc.cu.
+//
+// Time schedule of a gradient evaluation (discrete-adjoint algorithm, Sec. 3.2.1):
+//   forward  n = 0..N-1: the output of step s*k - 1 goes straight into
+//            checkpoint slot s (no extra copy), Phi^{s*k-1} into its slot; the
+//            last segment writes the adjoint tape (u, G) as it goes;
+//   adjoint  segments s = S-1..0: recompute steps s*k..s*k+k-1 from slot s
+//            writing the tape (skipped for the last segment), then run the
+//            AMRT steps of the segment backward in time.
+// Storage is O(N/k) lattices plus k tape planes of 3 scalars.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "cx_internal.h"
+
+using namespace cx;
+
+namespace {
+
+constexpr size_t ALIGN = 256;
+inline size_t up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+enum { PH_FWD = 0, PH_REC = 1, PH_ADJ = 2, PH_OTHER = 3 };
+enum { ST_UNSTABLE = 1 };
+
+struct Layout {
+    size_t plane, nctrl, esz;
+    int Q, N, k, S, nparts;
+    size_t off_popA, off_popB, off_adjA, off_adjB, off_ckpt, off_ckpt_phi, off_phi, off_sigma, off_tape;
+    size_t off_uN, off_vN, off_wu, off_theta, off_K, off_a, off_ut, off_solid, off_cmask, off_part, off_scal,
+        off_status, total;
+};
+
+struct TimedRange {
+    int phase;
+    long long launches;
+    cudaEvent_t a, b;
+};
+
+} // namespace
+
+struct cx_problem {
+    cx_problem_desc d;
+    CxConst C;
+    Layout lay;
+    cudaStream_t stream;
+    char* ws;
+    Launch L;
+    int nblocks;
+    bool has_init = false, fwd_valid = false, adj_valid = false;
+    bool tape_last_valid = false; // tape holds the last segment (written by the forward)
+    bool have_lam = false;
+    double lam_prev = 0.0;
+    void* psi0 = nullptr;
+    bool timing = false;
+    std::vector<TimedRange> ranges;
+    size_t n_ranges = 0;
+    double ms[4] = {0, 0, 0, 0};
+    long long launches[4] = {0, 0, 0, 0};
+
+    template <typename P> P* at(size_t off) const { return reinterpret_cast<P*>(ws + off); }
+    size_t pop_bytes() const { return (size_t)2 * lay.Q * lay.plane * lay.esz; }
+    char* ckpt_slot(int s) const { return ws + lay.off_ckpt + (size_t)s * pop_bytes(); }
+    char* ckpt_phi_slot(int s) const { return ws + lay.off_ckpt_phi + (size_t)s * lay.plane * lay.esz; }
+    char* tape_slot(int j) const { return ws + lay.off_tape + (size_t)j * 3 * lay.plane * lay.esz; }
+};
+
+// ------------------------------------------------------------ validation
+
+static cx_status validate(const cx_problem_desc* d) {
+    if (!d) return CX_ERR_INVALID_ARG;
+    if (d->nx < 3 || d->ny < 3 || d->n_steps < 1) return CX_ERR_INVALID_ARG;
+    if ((long long)d->nx * d->ny > (1LL << 31) - 1) return CX_ERR_INVALID_ARG;
+    if (d->lattice != 9 && d->lattice != 5) return CX_ERR_INVALID_ARG;
+    if (d->precision != 32 && d->precision != 64) return CX_ERR_INVALID_ARG;
+    if (d->ckpt_every < 0) return CX_ERR_INVALID_ARG;
+    if (!(d->tau > 0.0) || !(d->d_u > 0.0) || !(d->d_v > 0.0) || !(d->alpha >= 0.0)) return CX_ERR_INVALID_ARG;
+    if (!std::isfinite(d->chi) || !std::isfinite(d->r_vu) || !std::isfinite(d->r_vv)) return CX_ERR_INVALID_ARG;
+    for (int i = 0; i < 7; ++i)
+        if (!(d->s[i] > 0.0 && d->s[i] < 2.0)) return CX_ERR_INVALID_ARG;
+    if (d->source_order != 1 && d->source_order != 2) return CX_ERR_INVALID_ARG;
+    if (d->aniso == CX_ANISO_ROTATED && !d->theta) return CX_ERR_INVALID_ARG;
+    if (d->aniso == CX_ANISO_FIELD && (!d->D_u_field || !d->D_v_field)) return CX_ERR_INVALID_ARG;
+    if (d->aniso < 0 || d->aniso > 2 || d->adv < 0 || d->adv > 2) return CX_ERR_INVALID_ARG;
+    if (d->adv != CX_ADV_NONE && !d->a) return CX_ERR_INVALID_ARG;
+    if (d->lattice == 5 && d->adv != CX_ADV_NONE) return CX_ERR_INVALID_ARG; // D2Q5 lacks the a-a moments
+    if (!d->u_target) return CX_ERR_INVALID_ARG;
+    if (d->ctrl_nx < 0 || d->ctrl_ny < 0) return CX_ERR_INVALID_ARG;
+    if (d->ctrl_nx > 0) {
+        if (d->ctrl_ny <= 0 || d->ctrl_x0 < 0 || d->ctrl_y0 < 0 || d->ctrl_x0 + d->ctrl_nx > d->nx ||
+            d->ctrl_y0 + d->ctrl_ny > d->ny)
+            return CX_ERR_INVALID_ARG;
+    }
+    return CX_OK;
+}
+
+static Layout make_layout(const cx_problem_desc* d) {
+    Layout L{};
+    L.esz = d->precision == 64 ? 8 : 4;
+    L.Q = d->lattice;
+    L.N = d->n_steps;
+    L.k = d->ckpt_every > 0 ? std::min(d->ckpt_every, d->n_steps) : d->n_steps;
+    L.S = (L.N + L.k - 1) / L.k;
+    L.plane = up((size_t)d->nx * d->ny, 64);
+    const int cnx = d->ctrl_nx > 0 ? d->ctrl_nx : d->nx, cny = d->ctrl_nx > 0 ? d->ctrl_ny : d->ny;
+    L.nctrl = (size_t)cnx * cny;
+    // partial buffers sized for the smallest admissible block (32 x 1)
+    L.nparts = ((d->nx + 31) / 32) * d->ny;
+    const size_t pop = (size_t)2 * L.Q * L.plane * L.esz, fld = L.plane * L.esz;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t r = o;
+        o = up(o + bytes, ALIGN);
+        return r;
+    };
+    L.off_popA = take(pop);
+    L.off_popB = take(pop);
+    L.off_adjA = take(pop);
+    L.off_adjB = take(pop);
+    L.off_ckpt = take(pop * L.S);
+    L.off_ckpt_phi = take(fld * L.S);
+    L.off_phi = take(fld);
+    L.off_sigma = take(fld);
+    L.off_tape = take(fld * 3 * L.k);
+    L.off_uN = take(fld);
+    L.off_vN = take(fld);
+    L.off_wu = take(fld);
+    L.off_theta = take(d->aniso == CX_ANISO_ROTATED ? fld : 0);
+    L.off_K = take(d->aniso == CX_ANISO_FIELD ? 6 * fld : 0);
+    L.off_a = take(d->adv == CX_ADV_FIELD ? 2 * fld : (d->adv == CX_ADV_ROW ? 2 * (size_t)d->ny * L.esz : 0));
+    L.off_ut = take(fld);
+    L.off_solid = take(d->solid ? L.plane : 0);
+    L.off_cmask = take((d->solid || d->ctrl_mask) ? L.nctrl : 0);
+    L.off_part = take(sizeof(double) * 4 * (size_t)L.nparts);
+    L.off_scal = take(sizeof(double) * 16);
+    L.off_status = take(sizeof(int) * 4);
+    L.total = o;
+    return L;
+}
+
+// K = (D / (d Cs^2 tau) + I/2)^-1 for a constant tensor; eigenvalues checked in (0, 2).
+static bool K_const(const double D[3], double dd, double tau, double K[3]) {
+    const double sc = 1.0 / (dd * (1.0 / 3.0) * tau);
+    const double a = D[0] * sc + 0.5, b = D[1] * sc, c = D[2] * sc + 0.5;
+    const double det = a * c - b * b;
+    if (!(det > 0.0)) return false;
+    K[0] = c / det;
+    K[1] = -b / det;
+    K[2] = a / det;
+    const double tr = K[0] + K[2], dt = K[0] * K[2] - K[1] * K[1];
+    const double disc = std::sqrt(std::max(0.0, tr * tr / 4 - dt));
+    const double e1 = tr / 2 + disc, e2 = tr / 2 - disc;
+    return e2 > 0.0 && e1 < 2.0;
+}
+
+static bool k_rot(double lam, double dd, double tau, double* k) {
+    *k = 1.0 / (lam / (dd * (1.0 / 3.0) * tau) + 0.5);
+    return *k > 0.0 && *k < 2.0 && lam >= 0.0;
+}
+
+#define CX_CUDA(x)                                                                                                   \
+    do {                                                                                                             \
+        if ((x) != cudaSuccess) return CX_ERR_CUDA;                                                                  \
+    } while (0)
+
+// --------------------------------------------------------------- timing
+
+static void range_begin(cx_problem* p, int phase, TimedRange** r) {
+    *r = nullptr;
+    if (!p->timing) return;
+    if (p->n_ranges == p->ranges.size()) {
+        TimedRange t{};
+        if (cudaEventCreate(&t.a) != cudaSuccess || cudaEventCreate(&t.b) != cudaSuccess) return;
+        p->ranges.push_back(t);
+    }
+    TimedRange* t = &p->ranges[p->n_ranges++];
+    t->phase = phase;
+    t->launches = 0;
+    cudaEventRecord(t->a, p->stream);
+    *r = t;
+}
+static void range_end(cx_problem* p, TimedRange* r, long long launches) {
+    if (!r) return;
+    r->launches = launches;
+    cudaEventRecord(r->b, p->stream);
+}
+
+// ----------------------------------------------------------- templated core
+
+template <typename T> static cx_status run_forward(cx_problem* p, const T* g, const T* E, double lam, double* J_dev,
+                                                  bool flag_unstable) {
+    const Layout& Ly = p->lay;
+    const CxConst& C = p->C;
+    double* part = p->at<double>(Ly.off_part);
+    double* gsq = part + Ly.nparts;
+    CX_CUDA(cudaMemsetAsync(gsq, 0, sizeof(double) * p->nblocks, p->stream));
+    TimedRange* r;
+    range_begin(p, PH_FWD, &r);
+    const T* in = reinterpret_cast<const T*>(p->ckpt_slot(0));
+    T* phi = p->at<T>(Ly.off_phi);
+    for (int n = 0; n < Ly.N; ++n) {
+        const int seg = n / Ly.k;
+        FwdArgs<T> A{};
+        A.Pin = in;
+        if (n + 1 < Ly.N && (n + 1) % Ly.k == 0) {
+            A.Pout = reinterpret_cast<T*>(p->ckpt_slot((n + 1) / Ly.k));
+            A.phi_ckpt = reinterpret_cast<T*>(p->ckpt_phi_slot((n + 1) / Ly.k));
+        } else {
+            A.Pout = p->at<T>((n % 2) ? Ly.off_popB : Ly.off_popA);
+            A.phi_ckpt = nullptr;
+        }
+        A.phi = phi;
+        A.g = g ? g + (size_t)n * Ly.nctrl : nullptr;
+        A.E = E ? E + (size_t)n * Ly.nctrl : nullptr;
+        A.lam = lam;
+        A.tape = (seg == Ly.S - 1) ? reinterpret_cast<T*>(p->tape_slot(n - seg * Ly.k)) : nullptr;
+        A.gsq_part = gsq;
+        A.n = n;
+        CX_CUDA(launch_forward<T>(C, A, p->L, p->stream));
+        in = A.Pout;
+    }
+    double* cost = part;
+    CX_CUDA(launch_final<T>(C, in, p->at<T>(Ly.off_ut), p->at<T>(Ly.off_uN), p->at<T>(Ly.off_vN), p->at<T>(Ly.off_wu),
+                            cost, p->L, p->stream));
+    double* scal = p->at<double>(Ly.off_scal);
+    CX_CUDA(launch_finalize(cost, gsq, p->nblocks, C.alpha, scal, p->at<int>(Ly.off_status),
+                            flag_unstable ? ST_UNSTABLE : 0, 0, p->stream));
+    range_end(p, r, Ly.N);
+    if (J_dev) CX_CUDA(cudaMemcpyAsync(J_dev, scal, sizeof(double), cudaMemcpyDeviceToDevice, p->stream));
+    p->fwd_valid = true;
+    p->adj_valid = false;
+    p->tape_last_valid = true;
+    return CX_OK;
+}
+
+template <typename T>
+static cx_status run_adjoint(cx_problem* p, const T* g, const T* seed_u, const T* seed_v, T* dJdg) {
+    const Layout& Ly = p->lay;
+    const CxConst& C = p->C;
+    double* part = p->at<double>(Ly.off_part);
+    double* e2 = part + 2 * (size_t)Ly.nparts;
+    double* emax = part + 3 * (size_t)Ly.nparts;
+    CX_CUDA(cudaMemsetAsync(e2, 0, sizeof(double) * 2 * Ly.nparts, p->stream));
+    T* sigma = p->at<T>(Ly.off_sigma);
+    CX_CUDA(cudaMemsetAsync(sigma, 0, Ly.plane * sizeof(T), p->stream));
+    T* phi = p->at<T>(Ly.off_phi);
+    const T* psi_in = nullptr;
+    for (int s = Ly.S - 1; s >= 0; --s) {
+        const int n0 = s * Ly.k, n1 = std::min(Ly.N, n0 + Ly.k);
+        if (s < Ly.S - 1 || !p->tape_last_valid) {
+            TimedRange* r;
+            range_begin(p, PH_REC, &r);
+            if (s >= 1)
+                CX_CUDA(cudaMemcpyAsync(phi, p->ckpt_phi_slot(s), Ly.plane * sizeof(T), cudaMemcpyDeviceToDevice,
+                                        p->stream));
+            const T* in = reinterpret_cast<const T*>(p->ckpt_slot(s));
+            for (int n = n0; n < n1; ++n) {
+                FwdArgs<T> A{};
+                A.Pin = in;
+                A.Pout = p->at<T>((n % 2) ? Ly.off_popB : Ly.off_popA);
+                A.phi = phi;
+                A.phi_ckpt = nullptr;
+                A.g = g ? g + (size_t)n * Ly.nctrl : nullptr;
+                A.tape = reinterpret_cast<T*>(p->tape_slot(n - n0));
+                A.gsq_part = nullptr;
+                A.n = n;
+                CX_CUDA(launch_forward<T>(C, A, p->L, p->stream));
+                in = A.Pout;
+            }
+            range_end(p, r, n1 - n0);
+        }
+        TimedRange* r;
+        range_begin(p, PH_ADJ, &r);
+        for (int n = n1 - 1; n >= n0; --n) {
+            AdjArgs<T> A{};
+            A.terminal = (n == Ly.N - 1);
+            A.Rin = psi_in;
+            A.wu = seed_u ? seed_u : p->at<T>(Ly.off_wu);
+            A.wv = seed_v;
+            A.Rout = p->at<T>((n % 2) ? Ly.off_adjB : Ly.off_adjA);
+            A.tape = reinterpret_cast<const T*>(p->tape_slot(n - n0));
+            A.sigma = sigma;
+            A.g = g ? g + (size_t)n * Ly.nctrl : nullptr;
+            A.dJdg = dJdg + (size_t)n * Ly.nctrl;
+            A.e2_part = e2;
+            A.emax_part = emax;
+            A.n = n;
+            CX_CUDA(launch_adjoint<T>(C, A, p->L, p->stream));
+            psi_in = A.Rout;
+        }
+        range_end(p, r, n1 - n0);
+    }
+    double* scal = p->at<double>(Ly.off_scal);
+    CX_CUDA(launch_finalize(e2, emax, p->nblocks, 0.0, scal + 2, p->at<int>(Ly.off_status), ST_UNSTABLE, 1,
+                            p->stream));
+    p->psi0 = const_cast<T*>(psi_in);
+    p->adj_valid = true;
+    if (Ly.S > 1) p->tape_last_valid = false; // recomputed segments overwrote the tape
+    return CX_OK;
+}
+
+static cx_status read_scalars(cx_problem* p, double* out4, int* status) {
+    double h[4];
+    int st = 0;
+    CX_CUDA(cudaMemcpyAsync(h, p->at<double>(p->lay.off_scal), sizeof(h), cudaMemcpyDeviceToHost, p->stream));
+    CX_CUDA(cudaMemcpyAsync(&st, p->at<int>(p->lay.off_status), sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+    CX_CUDA(cudaStreamSynchronize(p->stream));
+    if (out4) std::memcpy(out4, h, sizeof(h));
+    if (status) *status = st;
+    return CX_OK;
+}
+
+template <typename T> static cx_status run_step(cx_problem* p, T* g, T* E, cx_step_info* info) {
+    cx_status rc;
+    if (!p->fwd_valid) {
+        rc = run_forward<T>(p, g, nullptr, 0.0, nullptr, true);
+        if (rc) return rc;
+    }
+    rc = run_adjoint<T>(p, g, nullptr, nullptr, E);
+    if (rc) return rc;
+    double s4[4];
+    int st = 0;
+    rc = read_scalars(p, s4, &st);
+    if (rc) return rc;
+    if (st & ST_UNSTABLE) return CX_ERR_UNSTABLE;
+    const double J0 = s4[0], e2 = s4[2], einf = s4[3];
+    double lam = p->have_lam ? 2.0 * p->lam_prev : std::min(1.0, einf > 0.0 ? 1.0 / einf : 1.0);
+    for (int t = 0; t < 30; ++t) {
+        rc = run_forward<T>(p, g, E, lam, nullptr, false);
+        if (rc) return rc;
+        double j4[4];
+        rc = read_scalars(p, j4, nullptr);
+        if (rc) return rc;
+        const double Jt = j4[0];
+        if (std::isfinite(Jt) && Jt <= J0 - 1e-4 * lam * e2) {
+            CX_CUDA(launch_axpy<T>(g, E, lam, (size_t)p->lay.N * p->lay.nctrl, p->stream));
+            p->fwd_valid = true; // the accepted trial's forward state is the new control's
+            p->adj_valid = false;
+            p->lam_prev = lam;
+            p->have_lam = true;
+            if (info) {
+                info->J0 = J0;
+                info->J = Jt;
+                info->lam = lam;
+                info->grad_sq = e2;
+                info->grad_inf = einf;
+                info->trials = t + 1;
+            }
+            return CX_OK;
+        }
+        lam *= 0.5;
+    }
+    p->fwd_valid = false;
+    return CX_ERR_LINESEARCH;
+}
+
+// ------------------------------------------------------------------- C ABI
+
+extern "C" {
+
+cx_status cx_workspace_size(const cx_problem_desc* desc, size_t* bytes) {
+    cx_status rc = validate(desc);
+    if (rc) return rc;
+    if (!bytes) return CX_ERR_INVALID_ARG;
+    *bytes = make_layout(desc).total;
+    return CX_OK;
+}
+
+cx_status cx_set_launch(cx_problem* p, int bx, int by) {
+    if (!p || bx < 32 || bx % 32 != 0 || by < 1 || bx * by > 1024 || bx * by < 32) return CX_ERR_INVALID_ARG;
+    p->L.block = dim3(bx, by);
+    p->L.grid = dim3((p->d.nx + bx - 1) / bx, (p->d.ny + by - 1) / by);
+    p->nblocks = (int)(p->L.grid.x * p->L.grid.y);
+    return CX_OK;
+}
+
+cx_status cx_create(const cx_problem_desc* desc, void* workspace, size_t bytes, cudaStream_t stream,
+                    cx_problem** out) {
+    if (!out) return CX_ERR_INVALID_ARG;
+    *out = nullptr;
+    cx_status rc = validate(desc);
+    if (rc) return rc;
+    Layout Ly = make_layout(desc);
+    if (!workspace || bytes < Ly.total || (reinterpret_cast<uintptr_t>(workspace) % ALIGN) != 0)
+        return CX_ERR_WORKSPACE;
+    CxConst C{};
+    C.nx = desc->nx;
+    C.ny = desc->ny;
+    C.plane = (long long)Ly.plane;
+    C.Q = desc->lattice;
+    C.n_steps = desc->n_steps;
+    C.aniso = desc->aniso;
+    C.adv = desc->adv;
+    C.has_solid = desc->solid ? 1 : 0;
+    if (desc->ctrl_nx > 0) {
+        C.cx0 = desc->ctrl_x0;
+        C.cy0 = desc->ctrl_y0;
+        C.cnx = desc->ctrl_nx;
+        C.cny = desc->ctrl_ny;
+    } else {
+        C.cx0 = C.cy0 = 0;
+        C.cnx = desc->nx;
+        C.cny = desc->ny;
+    }
+    C.source_order = desc->source_order;
+    C.tau = desc->tau;
+    C.d_u = desc->d_u;
+    C.d_v = desc->d_v;
+    C.chi = desc->chi;
+    C.r_vu = desc->r_vu;
+    C.r_vv = desc->r_vv;
+    C.alpha = desc->alpha;
+    for (int i = 0; i < 7; ++i) C.s[i] = desc->s[i];
+    if (desc->aniso == CX_ANISO_CONST) {
+        if (!K_const(desc->D_u, desc->d_u, desc->tau, C.Ku) || !K_const(desc->D_v, desc->d_v, desc->tau, C.Kv))
+            return CX_ERR_INVALID_ARG;
+    } else if (desc->aniso == CX_ANISO_ROTATED) {
+        double k1, k2;
+        if (!k_rot(desc->lam_u[0], desc->d_u, desc->tau, &k1) || !k_rot(desc->lam_u[1], desc->d_u, desc->tau, &k2))
+            return CX_ERR_INVALID_ARG;
+        C.ku_bar = 0.5 * (k1 + k2);
+        C.ku_d = 0.5 * (k1 - k2);
+        if (!k_rot(desc->lam_v[0], desc->d_v, desc->tau, &k1) || !k_rot(desc->lam_v[1], desc->d_v, desc->tau, &k2))
+            return CX_ERR_INVALID_ARG;
+        C.kv_bar = 0.5 * (k1 + k2);
+        C.kv_d = 0.5 * (k1 - k2);
+    }
+    cx_problem* p = new (std::nothrow) cx_problem();
+    if (!p) return CX_ERR_INTERNAL;
+    p->d = *desc;
+    p->lay = Ly;
+    p->stream = stream;
+    p->ws = reinterpret_cast<char*>(workspace);
+    char* ws = p->ws;
+    C.theta = desc->aniso == CX_ANISO_ROTATED ? ws + Ly.off_theta : nullptr;
+    C.Kfield = desc->aniso == CX_ANISO_FIELD ? ws + Ly.off_K : nullptr;
+    C.a = desc->adv != CX_ADV_NONE ? ws + Ly.off_a : nullptr;
+    C.solid = desc->solid ? reinterpret_cast<uint8_t*>(ws + Ly.off_solid) : nullptr;
+    C.cmask = (desc->solid || desc->ctrl_mask) ? reinterpret_cast<uint8_t*>(ws + Ly.off_cmask) : nullptr;
+    p->C = C;
+    const int bx = desc->nx >= 128 ? 128 : (desc->nx >= 64 ? 64 : 32);
+    cx_set_launch(p, bx, 256 / bx);
+    cudaError_t e;
+    if (desc->precision == 64)
+        e = launch_setup_fields<double>(C, *desc, (double*)C.theta, (double*)C.Kfield, (double*)C.a,
+                                        reinterpret_cast<double*>(ws + Ly.off_ut), (uint8_t*)C.solid,
+                                        (uint8_t*)C.cmask, stream);
+    else
+        e = launch_setup_fields<float>(C, *desc, (float*)C.theta, (float*)C.Kfield, (float*)C.a,
+                                       reinterpret_cast<float*>(ws + Ly.off_ut), (uint8_t*)C.solid,
+                                       (uint8_t*)C.cmask, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws + Ly.off_status, 0, sizeof(int) * 4, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) {
+        delete p;
+        return CX_ERR_CUDA;
+    }
+    // the descriptor's device pointers are not kept
+    p->d.theta = p->d.D_u_field = p->d.D_v_field = p->d.a = p->d.u_target = nullptr;
+    p->d.solid = p->d.ctrl_mask = nullptr;
+    *out = p;
+    return CX_OK;
+}
+
+cx_status cx_set_initial(cx_problem* p, const void* u0, const void* v0) {
+    if (!p || !u0 || !v0) return CX_ERR_INVALID_ARG;
+    cudaError_t e;
+    if (p->lay.esz == 8)
+        e = launch_init<double>(p->C, nullptr, nullptr, (const double*)u0, (const double*)v0,
+                                reinterpret_cast<double*>(p->ckpt_slot(0)), p->L, p->stream);
+    else
+        e = launch_init<float>(p->C, nullptr, nullptr, (const float*)u0, (const float*)v0,
+                               reinterpret_cast<float*>(p->ckpt_slot(0)), p->L, p->stream);
+    if (e != cudaSuccess) return CX_ERR_CUDA;
+    p->has_init = true;
+    p->fwd_valid = p->adj_valid = false;
+    p->have_lam = false;
+    return CX_OK;
+}
+
+cx_status cx_forward(cx_problem* p, const void* g, double* J_dev) {
+    if (!p) return CX_ERR_INVALID_ARG;
+    if (!p->has_init) return CX_ERR_STATE;
+    if (p->lay.esz == 8) return run_forward<double>(p, (const double*)g, nullptr, 0.0, J_dev, true);
+    return run_forward<float>(p, (const float*)g, nullptr, 0.0, J_dev, true);
+}
+
+cx_status cx_adjoint(cx_problem* p, const void* g, const void* seed_u, const void* seed_v, void* dJdg) {
+    if (!p || !dJdg) return CX_ERR_INVALID_ARG;
+    if (!p->fwd_valid) return CX_ERR_STATE;
+    if (p->lay.esz == 8)
+        return run_adjoint<double>(p, (const double*)g, (const double*)seed_u, (const double*)seed_v, (double*)dJdg);
+    return run_adjoint<float>(p, (const float*)g, (const float*)seed_u, (const float*)seed_v, (float*)dJdg);
+}
+
+cx_status cx_gradient(cx_problem* p, const void* g, void* dJdg, double* J_dev) {
+    cx_status rc = cx_forward(p, g, J_dev);
+    if (rc) return rc;
+    return cx_adjoint(p, g, nullptr, nullptr, dJdg);
+}
+
+cx_status cx_step(cx_problem* p, void* g_inout, void* E_work, cx_step_info* info) {
+    if (!p || !g_inout || !E_work) return CX_ERR_INVALID_ARG;
+    if (!p->has_init) return CX_ERR_STATE;
+    if (p->lay.esz == 8) return run_step<double>(p, (double*)g_inout, (double*)E_work, info);
+    return run_step<float>(p, (float*)g_inout, (float*)E_work, info);
+}
+
+cx_status cx_get_fields(cx_problem* p, void* u_out, void* v_out) {
+    if (!p) return CX_ERR_INVALID_ARG;
+    if (!p->fwd_valid) return CX_ERR_STATE;
+    const size_t b = (size_t)p->d.nx * p->d.ny * p->lay.esz;
+    if (u_out) CX_CUDA(cudaMemcpyAsync(u_out, p->ws + p->lay.off_uN, b, cudaMemcpyDeviceToDevice, p->stream));
+    if (v_out) CX_CUDA(cudaMemcpyAsync(v_out, p->ws + p->lay.off_vN, b, cudaMemcpyDeviceToDevice, p->stream));
+    return CX_OK;
+}
+
+cx_status cx_get_psi0(cx_problem* p, void* out) {
+    if (!p || !out) return CX_ERR_INVALID_ARG;
+    if (!p->adj_valid || !p->psi0) return CX_ERR_STATE;
+    const size_t nn = (size_t)p->d.nx * p->d.ny;
+    // [2][Q][plane] -> [2][Q][ny][nx]
+    for (int j = 0; j < 2 * p->lay.Q; ++j)
+        CX_CUDA(cudaMemcpyAsync(static_cast<char*>(out) + j * nn * p->lay.esz,
+                                static_cast<char*>(p->psi0) + j * p->lay.plane * p->lay.esz, nn * p->lay.esz,
+                                cudaMemcpyDeviceToDevice, p->stream));
+    return CX_OK;
+}
+
+cx_status cx_get_norms(cx_problem* p, double* J, double* grad_sq, double* grad_inf) {
+    if (!p) return CX_ERR_INVALID_ARG;
+    double s4[4];
+    int st = 0;
+    cx_status rc = read_scalars(p, s4, &st);
+    if (rc) return rc;
+    if (J) *J = s4[0];
+    if (grad_sq) *grad_sq = s4[2];
+    if (grad_inf) *grad_inf = s4[3];
+    if (st & ST_UNSTABLE) return CX_ERR_UNSTABLE;
+    return CX_OK;
+}
+
+cx_status cx_set_timing(cx_problem* p, int enable) {
+    if (!p) return CX_ERR_INVALID_ARG;
+    p->timing = enable != 0;
+    return CX_OK;
+}
+
+cx_status cx_get_timing(cx_problem* p, double* ms, long long* launches) {
+    if (!p) return CX_ERR_INVALID_ARG;
+    CX_CUDA(cudaStreamSynchronize(p->stream));
+    double acc[4] = {0, 0, 0, 0};
+    long long cnt[4] = {0, 0, 0, 0};
+    for (size_t i = 0; i < p->n_ranges; ++i) {
+        float t = 0.0f;
+        if (cudaEventElapsedTime(&t, p->ranges[i].a, p->ranges[i].b) != cudaSuccess) return CX_ERR_CUDA;
+        acc[p->ranges[i].phase] += t;
+        cnt[p->ranges[i].phase] += p->ranges[i].launches;
+    }
+    p->n_ranges = 0;
+    if (ms) std::memcpy(ms, acc, sizeof(acc));
+    if (launches) std::memcpy(launches, cnt, sizeof(cnt));
+    return CX_OK;
+}
+
+cx_status cx_destroy(cx_problem* p) {
+    if (!p) return CX_ERR_INVALID_ARG;
+    for (auto& r : p->ranges) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    delete p;
+    return CX_OK;
+}
+
+const char* cx_status_string(cx_status s) {
+    switch (s) {
+    case CX_OK: return "ok";
+    case CX_ERR_INVALID_ARG: return "invalid argument";
+    case CX_ERR_WORKSPACE: return "workspace missing, too small or misaligned";
+    case CX_ERR_CUDA: return "CUDA runtime error";
+    case CX_ERR_STATE: return "call out of order";
+    case CX_ERR_UNSTABLE: return "non-finite cost or gradient";
+    case CX_ERR_LINESEARCH: return "line search failed";
+    case CX_ERR_TIMEOUT: return "device wait timed out";
+    case CX_ERR_INTERNAL: return "internal error";
+    }
+    return "unknown status";
+}
+
+} // extern "C"

@@ -1,0 +1,82 @@
+// cx_internal.h -- shared definitions of the library's host code and kernels.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/cxlbm.h"
+
+namespace cx {
+
+// Per-problem constants, passed by value to every kernel.
+struct CxConst {
+    int nx, ny;
+    long long plane;      // elements per node plane (nx*ny rounded up to 64)
+    int Q, n_steps;
+    int aniso, adv, has_solid;
+    int cx0, cy0, cnx, cny;
+    int source_order;
+    double tau, d_u, d_v, chi, r_vu, r_vv, alpha;
+    double s[7];
+    double Ku[3], Kv[3];              // CONST tensors -> K (k11, k12, k22)
+    double ku_bar, ku_d, kv_bar, kv_d; // ROTATED: K = kbar I + kd R(2t)-reflection
+    const void* theta;                // T [plane]           (ROTATED)
+    const void* Kfield;               // T [6][plane]        (FIELD)
+    const void* a;                    // T [ny][2] or [2][plane]
+    const uint8_t* solid;             // [plane] or null
+    const uint8_t* cmask;             // [cny*cnx] window & mask & fluid, or null
+};
+
+template <typename T> struct FwdArgs {
+    const T* Pin;        // [2][Q][plane] populations read (pull) or, at n = 0, f^0 read locally
+    T* Pout;             // [2][Q][plane] post-collision populations of step n
+    T* phi;              // [plane] Phi^{n-1} in, Phi^n out (node-local, in place)
+    T* phi_ckpt;         // [plane] copy of Phi^n when Pout is a checkpoint slot, else null
+    const T* g;          // [cny*cnx] control g^n, or null (zero control)
+    const T* E;          // [cny*cnx] gradient for trial controls g - lam E, or null
+    double lam;
+    T* tape;             // [3][plane] (u^n, G_x^n, G_y^n) or null
+    double* gsq_part;    // per-block partial of sum (g^n)^2 (accumulated), or null
+    int n;               // time step index
+};
+
+template <typename T> struct AdjArgs {
+    const T* Rin;        // [2][Q][plane] psi^{n+1}, or null at the terminal step
+    const T* wu;         // terminal seeds psi^N_u,i = wu(x), psi^N_v,i = wv(x) (terminal step only)
+    const T* wv;
+    T* Rout;             // [2][Q][plane] psi^n
+    const T* tape;       // [3][plane] (u^n, G_x^n, G_y^n)
+    T* sigma;            // [plane] sigma^{n+1} in, sigma^n out
+    const T* g;          // [cny*cnx] g^n or null
+    T* dJdg;             // [cny*cnx] output dJ/dg^n
+    double* e2_part;     // per-block partial of sum E^2 (accumulated)
+    double* emax_part;   // per-block partial of max |E| (accumulated)
+    int n;
+    int terminal;        // n == N-1: psi^{n+1} is the broadcast seed
+};
+
+struct Launch {
+    dim3 grid, block;
+};
+
+// kernel launchers (cx_forward.cu / cx_adjoint.cu / cx_misc.cu), one per precision
+template <typename T> cudaError_t launch_forward(const CxConst& C, const FwdArgs<T>& A, const Launch& L, cudaStream_t s);
+template <typename T> cudaError_t launch_adjoint(const CxConst& C, const AdjArgs<T>& A, const Launch& L, cudaStream_t s);
+template <typename T>
+cudaError_t launch_init(const CxConst& C, const double* u0d, const double* v0d, const T* u0, const T* v0, T* P,
+                        const Launch& L, cudaStream_t s);
+template <typename T>
+cudaError_t launch_final(const CxConst& C, const T* Pin, const T* u_tgt, T* uN, T* vN, T* wu, double* cost_part,
+                         const Launch& L, cudaStream_t s);
+cudaError_t launch_finalize(const double* part_a, const double* part_b, int nparts, double scale_b, double* out,
+                            int* status, int status_bit, int mode, cudaStream_t s);
+template <typename T>
+cudaError_t launch_axpy(T* g, const T* E, double lam, size_t n, cudaStream_t s);
+template <typename T>
+cudaError_t launch_convert(const double* in, T* out, size_t n, cudaStream_t s);
+template <typename T>
+cudaError_t launch_setup_fields(const CxConst& C, const cx_problem_desc& d, T* theta, T* Kfield, T* a, T* u_tgt,
+                                uint8_t* solid, uint8_t* cmask, cudaStream_t s);
+
+} // namespace cx

@@ -1,0 +1,236 @@
+// cx_misc.cu -- initial equilibrium, final moments and cost, fixed-order
+// FP64 reductions, control update and field set-up kernels.
+#include <cmath>
+
+#include "cx_device.cuh"
+
+namespace cx {
+
+// f^0 = phi^eq(Theta_0) for both species (eq. phieq; the initial condition of
+// the forward solve).  Reads FP64 (u0d) or T (u0) initial fields.
+template <typename T, int Q>
+__global__ void k_init(const CxConst C, const double* u0d, const double* v0d, const T* u0, const T* v0, T* P) {
+    using L = Lat<Q>;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= C.nx || y >= C.ny) return;
+    const int k = y * C.nx + x;
+    const size_t pl = (size_t)C.plane;
+    const bool solid = C.has_solid && C.solid[k];
+    NodeCoef<T> nc;
+    node_coef<T>(C, x, y, k, nc);
+    const T Tu = solid ? T(0) : (u0d ? T(u0d[k]) : u0[k]);
+    const T Tv = solid ? T(0) : (v0d ? T(v0d[k]) : v0[k]);
+    const T a2 = nc.ax * nc.ax + nc.ay * nc.ay;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const T ea = nc.ax * T(L::ex(i)) + nc.ay * T(L::ey(i));
+        const T e2 = T(L::ex(i) * L::ex(i) + L::ey(i) * L::ey(i));
+        const T base = T(1) + T(3) * ea + T(4.5) * (ea * ea - a2 * T(1.0 / 3.0));
+        const T au = base + T(4.5) * (T(C.d_u) - T(1)) * (e2 - T(2.0 / 3.0)) * T(1.0 / 3.0);
+        const T av = base + T(4.5) * (T(C.d_v) - T(1)) * (e2 - T(2.0 / 3.0)) * T(1.0 / 3.0);
+        P[i * pl + k] = T(L::w(i)) * au * Tu;
+        P[(Q + i) * pl + k] = T(L::w(i)) * av * Tv;
+    }
+}
+
+template <typename T>
+cudaError_t launch_init(const CxConst& C, const double* u0d, const double* v0d, const T* u0, const T* v0, T* P,
+                        const Launch& L, cudaStream_t s) {
+    if (C.Q == 9)
+        k_init<T, 9><<<L.grid, L.block, 0, s>>>(C, u0d, v0d, u0, v0, P);
+    else
+        k_init<T, 5><<<L.grid, L.block, 0, s>>>(C, u0d, v0d, u0, v0, P);
+    return cudaGetLastError();
+}
+
+// u^N = sum_i f^N_u,i, v^N likewise (UGS), with f^N pulled from P^{N-1};
+// wu = u^N - u_target seeds the adjoint (final condition of CAE); the block
+// partial of 1/2 sum (u^N - u_target)^2 goes to cost_part in FP64.
+template <typename T, int Q>
+__global__ void __launch_bounds__(256) k_final(const CxConst C, const T* Pin, const T* u_tgt, T* uN, T* vN, T* wu,
+                                                double* cost_part) {
+    using L = Lat<Q>;
+    __shared__ double red[32];
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    double cst = 0.0;
+    if (x < C.nx && y < C.ny) {
+        const int k = y * C.nx + x;
+        const size_t pl = (size_t)C.plane;
+        T su = T(0), sv = T(0), w = T(0);
+        if (!(C.has_solid && C.solid[k])) {
+            const int xm = x == 0 ? C.nx - 1 : x - 1, xp = x == C.nx - 1 ? 0 : x + 1;
+            const int ym = y == 0 ? C.ny - 1 : y - 1, yp = y == C.ny - 1 ? 0 : y + 1;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const int xs = L::ex(i) > 0 ? xm : (L::ex(i) < 0 ? xp : x);
+                const int ys = L::ey(i) > 0 ? ym : (L::ey(i) < 0 ? yp : y);
+                const int ks = ys * C.nx + xs;
+                if (C.has_solid && i != 0 && C.solid[ks]) {
+                    su += Pin[L::opp(i) * pl + k];
+                    sv += Pin[(Q + L::opp(i)) * pl + k];
+                } else {
+                    su += Pin[i * pl + ks];
+                    sv += Pin[(Q + i) * pl + ks];
+                }
+            }
+            w = su - u_tgt[k];
+            cst = 0.5 * (double)w * (double)w;
+        }
+        uN[k] = su;
+        vN[k] = sv;
+        wu[k] = w;
+    }
+    const double b = block_sum(cst, red);
+    if (threadIdx.x == 0 && threadIdx.y == 0) cost_part[blockIdx.x + gridDim.x * blockIdx.y] = b;
+}
+
+template <typename T>
+cudaError_t launch_final(const CxConst& C, const T* Pin, const T* u_tgt, T* uN, T* vN, T* wu, double* cost_part,
+                         const Launch& L, cudaStream_t s) {
+    if (C.Q == 9)
+        k_final<T, 9><<<L.grid, L.block, 0, s>>>(C, Pin, u_tgt, uN, vN, wu, cost_part);
+    else
+        k_final<T, 5><<<L.grid, L.block, 0, s>>>(C, Pin, u_tgt, uN, vN, wu, cost_part);
+    return cudaGetLastError();
+}
+
+// One block, fixed order: thread t sums parts t, t+256, ... then a fixed tree.
+// mode 0: out = sum(a) + scale_b * sum(b)          (cost J)
+// mode 1: out[0] = sum(a), out[1] = max(b)         (gradient norms)
+// A non-finite result sets status_bit in *status.
+__global__ void __launch_bounds__(256) k_finalize(const double* a, const double* b, int n, double scale_b,
+                                                   double* out, int* status, int status_bit, int mode) {
+    __shared__ double sa[256], sb[256];
+    const int t = threadIdx.x;
+    double ra = 0.0, rb = 0.0;
+    for (int i = t; i < n; i += 256) {
+        ra += a[i];
+        if (b) rb = (mode == 1) ? fmax(rb, b[i]) : rb + b[i];
+    }
+    sa[t] = ra;
+    sb[t] = rb;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (t < h) {
+            sa[t] += sa[t + h];
+            sb[t] = (mode == 1) ? fmax(sb[t], sb[t + h]) : sb[t] + sb[t + h];
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        if (mode == 0) {
+            const double J = sa[0] + scale_b * sb[0];
+            out[0] = J;
+            if (!isfinite(J)) atomicOr(status, status_bit);
+        } else {
+            out[0] = sa[0];
+            out[1] = sb[0];
+            if (!isfinite(sa[0]) || !isfinite(sb[0])) atomicOr(status, status_bit);
+        }
+    }
+}
+
+cudaError_t launch_finalize(const double* a, const double* b, int n, double scale_b, double* out, int* status,
+                            int status_bit, int mode, cudaStream_t s) {
+    k_finalize<<<1, 256, 0, s>>>(a, b, n, scale_b, out, status, status_bit, mode);
+    return cudaGetLastError();
+}
+
+// g <- g - lam E (accepted Armijo step)
+template <typename T> __global__ void k_axpy(T* g, const T* E, double lam, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        g[i] = fma(-T(lam), E[i], g[i]); // bit-identical to the trial control of the forward
+}
+
+template <typename T> cudaError_t launch_axpy(T* g, const T* E, double lam, size_t n, cudaStream_t s) {
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    k_axpy<T><<<blocks, 256, 0, s>>>(g, E, lam, n);
+    return cudaGetLastError();
+}
+
+template <typename T> __global__ void k_convert(const double* in, T* out, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = T(in[i]);
+}
+
+template <typename T> cudaError_t launch_convert(const double* in, T* out, size_t n, cudaStream_t s) {
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    k_convert<T><<<blocks, 256, 0, s>>>(in, out, n);
+    return cudaGetLastError();
+}
+
+// Per-node set-up: angle / K fields, convection, target, solid copy, and the
+// combined control mask (window & ctrl_mask & fluid).
+// K from D = d Cs^2 tau (K^-1 - I/2): K = (D / (d Cs^2 tau) + I/2)^-1 (2x2 inverse).
+template <typename T>
+__global__ void k_setup(const CxConst C, const double* theta_in, const double* Du_in, const double* Dv_in,
+                        const double* a_in, const double* ut_in, const uint8_t* solid_in, const uint8_t* cmask_in,
+                        T* theta, T* Kfield, T* a, T* u_tgt, uint8_t* solid, uint8_t* cmask) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= C.nx || y >= C.ny) return;
+    const int k = y * C.nx + x;
+    const size_t pl = (size_t)C.plane;
+    if (theta) theta[k] = T(theta_in[k]);
+    if (Kfield) {
+        const double* Ds[2] = {Du_in, Dv_in};
+        const double dd[2] = {C.d_u, C.d_v};
+        for (int sp = 0; sp < 2; ++sp) {
+            const double sc = 1.0 / (dd[sp] * (1.0 / 3.0) * C.tau);
+            const double A00 = Ds[sp][3 * k] * sc + 0.5, A01 = Ds[sp][3 * k + 1] * sc, A11 = Ds[sp][3 * k + 2] * sc + 0.5;
+            const double det = A00 * A11 - A01 * A01;
+            Kfield[(3 * sp + 0) * pl + k] = T(A11 / det);
+            Kfield[(3 * sp + 1) * pl + k] = T(-A01 / det);
+            Kfield[(3 * sp + 2) * pl + k] = T(A00 / det);
+        }
+    }
+    if (a && C.adv == CX_ADV_FIELD) {
+        a[k] = T(a_in[2 * k]);
+        a[pl + k] = T(a_in[2 * k + 1]);
+    }
+    if (a && C.adv == CX_ADV_ROW && x == 0) {
+        a[2 * y] = T(a_in[2 * y]);
+        a[2 * y + 1] = T(a_in[2 * y + 1]);
+    }
+    u_tgt[k] = T(ut_in[k]);
+    if (solid) solid[k] = solid_in[k] ? 1 : 0;
+    if (cmask) {
+        const int cx = x - C.cx0, cy = y - C.cy0;
+        if (cx >= 0 && cy >= 0 && cx < C.cnx && cy < C.cny) {
+            const int c = cy * C.cnx + cx;
+            uint8_t m = 1;
+            if (cmask_in && !cmask_in[c]) m = 0;
+            if (solid_in && solid_in[k]) m = 0;
+            cmask[c] = m;
+        }
+    }
+}
+
+template <typename T>
+cudaError_t launch_setup_fields(const CxConst& C, const cx_problem_desc& d, T* theta, T* Kfield, T* a, T* u_tgt,
+                                uint8_t* solid, uint8_t* cmask, cudaStream_t s) {
+    dim3 block(32, 8), grid((C.nx + 31) / 32, (C.ny + 7) / 8);
+    k_setup<T><<<grid, block, 0, s>>>(C, d.theta, d.D_u_field, d.D_v_field, d.a, d.u_target, d.solid, d.ctrl_mask,
+                                      theta, Kfield, a, u_tgt, solid, cmask);
+    return cudaGetLastError();
+}
+
+#define CX_INST(T)                                                                                                   \
+    template cudaError_t launch_init<T>(const CxConst&, const double*, const double*, const T*, const T*, T*,        \
+                                        const Launch&, cudaStream_t);                                                 \
+    template cudaError_t launch_final<T>(const CxConst&, const T*, const T*, T*, T*, T*, double*, const Launch&,      \
+                                         cudaStream_t);                                                               \
+    template cudaError_t launch_axpy<T>(T*, const T*, double, size_t, cudaStream_t);                                 \
+    template cudaError_t launch_convert<T>(const double*, T*, size_t, cudaStream_t);                                 \
+    template cudaError_t launch_setup_fields<T>(const CxConst&, const cx_problem_desc&, T*, T*, T*, T*, uint8_t*,    \
+                                                uint8_t*, cudaStream_t);
+CX_INST(float)
+CX_INST(double)
+
+} // namespace cx

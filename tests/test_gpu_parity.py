@@ -1,0 +1,216 @@
+"""GPU path (CUDA library through the C ABI) against the FP64 CPU oracle.
+
+Tolerances (relative L2 against the oracle, from the project's accuracy bar):
+  FP64 GPU: 1e-12 on u^N, v^N, psi^0 and dJ/dg, and on J;
+  FP32 GPU: 1e-4 on fields, 1e-3 on dJ/dg.
+Every comparison prints its measured error.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+from paper_1908_03876_gb300 import workloads as W  # noqa: E402
+
+TOL64 = 1e-12
+TOL32_FIELD = 1e-4
+TOL32_GRAD = 1e-3
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1908_03876_gb300.build import build
+
+    build()
+    oracle.build()
+
+
+def rel(a, b):
+    a = a.detach().cpu().numpy() if hasattr(a, "detach") else np.asarray(a)
+    b = np.asarray(b)
+    den = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / (den if den > 0 else 1.0))
+
+
+def run_both(w, g, seeds=None, launch=None):
+    from paper_1908_03876_gb300.problem import Problem
+
+    p = Problem(w)
+    if launch:
+        p.set_launch(*launch)
+    J = p.forward(g)
+    su, sv = (None, None) if seeds is None else seeds
+    E = p.adjoint(g, su, sv)
+    u, v = p.fields()
+    psi0 = p.psi0()
+    torch.cuda.synchronize()
+    po = oracle.from_workload(w)
+    Jo, uo, vo = oracle.forward(po, g)
+    _, Eo, psio = oracle.adjoint(po, g, su, sv, want_psi0=True)
+    # oracle psi0 is [ny][nx][2][Q]; the GPU's is [2][Q][ny][nx]
+    psio = np.transpose(psio, (2, 3, 0, 1))
+    if w.solid is not None:  # solid nodes hold no populations
+        solid = torch.as_tensor(w.solid, device=psi0.device).bool()[None, None]
+        psi0 = torch.where(solid, torch.zeros_like(psi0), psi0)
+    return dict(J=(float(J.item()), Jo), u=(u, uo), v=(v, vo), E=(E, Eo), psi0=(psi0, psio), p=p)
+
+
+def check(res, tol_field, tol_grad, label):
+    eJ = abs(res["J"][0] - res["J"][1]) / abs(res["J"][1])
+    eu, ev = rel(*res["u"]), rel(*res["v"])
+    eE, ep = rel(*res["E"]), rel(*res["psi0"])
+    print(f"[{label}] rel err: J {eJ:.2e} u {eu:.2e} v {ev:.2e} dJ/dg {eE:.2e} psi0 {ep:.2e}")
+    assert eJ < tol_field and eu < tol_field and ev < tol_field
+    assert eE < tol_grad and ep < tol_grad
+
+
+# ---------------------------------------------------------------- FP64 parity
+
+def test_plain64_d2q5_fp64_full():
+    """The 64x64 D2Q5 FP64 problem in full (200 steps)."""
+    w = W.plain64()
+    g = w.random_control(1, 0.02)
+    check(run_both(w, g), TOL64, TOL64, "plain64 D2Q5 fp64")
+
+
+@pytest.mark.parametrize("Q", [5, 9])
+def test_plain_ragged_fp64(Q):
+    """Several tiles with a ragged tail in x and y; checkpoint interval not dividing N."""
+    w = W.plain64(150, 37, 23, sigma=3.0, Q=Q)
+    w.ckpt_every = 6
+    g = w.random_control(2, 0.02)
+    check(run_both(w, g), TOL64, TOL64, f"plain ragged Q{Q}")
+
+
+def test_aniso_fp64_checkpointed():
+    """Rotated anisotropic tensors, shear convection, chemotaxis; k = 7."""
+    w = W.aniso(72, 56, 31, seed=1, precision=64, ckpt_every=7)
+    g = w.random_control(3, 0.02)
+    check(run_both(w, g), TOL64, TOL64, "aniso fp64")
+
+
+def test_geometry_fp64():
+    """Solid discs with bounce-back, solid frame, masked control window."""
+    w = W.geometry(96, 80, 25, seed=2, precision=64, ckpt_every=8, win=40, rmin=3, rmax=9)
+    g = w.random_control(4, 0.02)
+    check(run_both(w, g), TOL64, TOL64, "geometry fp64")
+
+
+def test_field_tensors_and_velocity_fp64():
+    """Per-node tensor fields and per-node convection (FIELD modes)."""
+    w = W.aniso(48, 40, 16, seed=5, precision=64, ckpt_every=5)
+    Du, Dv = w.D_fields()
+    rng = np.random.default_rng(0)
+    w.aniso, w.D_u_field, w.D_v_field = "field", Du, Dv * 1.3
+    w.adv = "field"
+    w.a_field = rng.uniform(-0.03, 0.03, (w.ny, w.nx, 2))
+    g = w.random_control(5, 0.02)
+    check(run_both(w, g), TOL64, TOL64, "field modes fp64")
+
+
+@pytest.mark.parametrize("source_order", [1, 2])
+def test_explicit_seeds_fp64(source_order):
+    """Adjoint seeded with arbitrary (seed_u, seed_v): the VJP used by autograd."""
+    w = W.aniso(40, 32, 12, seed=6, precision=64, ckpt_every=4)
+    w.source_order = source_order
+    rng = np.random.default_rng(1)
+    seeds = (rng.standard_normal((w.ny, w.nx)), rng.standard_normal((w.ny, w.nx)))
+    g = w.random_control(6, 0.02)
+    check(run_both(w, g, seeds=seeds), TOL64, TOL64, f"seeded order {source_order}")
+
+
+def test_launch_shape_independent_bitwise():
+    """FP64 results are bitwise identical across block shapes (no halo race)."""
+    w = W.geometry(80, 64, 12, seed=3, precision=64, ckpt_every=5, win=30, rmin=3, rmax=8)
+    g = w.random_control(7, 0.02)
+    from paper_1908_03876_gb300.problem import Problem
+
+    outs = []
+    for shape in [(32, 1), (64, 4), (128, 2), (32, 32)]:
+        p = Problem(w)
+        p.set_launch(*shape)
+        p.forward(g)
+        E = p.adjoint(g)
+        u, v = p.fields()
+        outs.append((u.cpu().numpy(), v.cpu().numpy(), E.cpu().numpy()))
+    for o in outs[1:]:
+        for a, b in zip(outs[0], o):
+            assert np.array_equal(a, b)
+
+
+def test_repeated_adjoint_and_state():
+    """A second adjoint after one forward repeats the first (tape bookkeeping);
+    adjoint before any forward is refused."""
+    from paper_1908_03876_gb300 import _lib
+    from paper_1908_03876_gb300.problem import Problem
+
+    w = W.aniso(40, 40, 20, seed=8, precision=64, ckpt_every=6)
+    g = w.random_control(8, 0.02)
+    p = Problem(w)
+    with pytest.raises(_lib.CxError) as ei:
+        p.adjoint(g)
+    assert ei.value.code == 4
+    p.forward(g)
+    E1 = p.adjoint(g).clone()
+    E2 = p.adjoint(g)
+    assert torch.equal(E1, E2)
+
+
+def test_step_matches_oracle_fp64():
+    """One Armijo steepest-descent iteration (cx_step) against the oracle's."""
+    from paper_1908_03876_gb300.problem import Problem
+
+    w = W.plain64(32, 32, 30, sigma=2.0, Q=9)
+    p = Problem(w)
+    g = p.zeros_control()
+    info = p.step(g)
+    go, io = oracle.gd_step(oracle.from_workload(w), np.zeros(w.ctrl_shape))
+    print("step", info, io)
+    assert abs(info["J0"] - io["J0"]) <= 1e-12 * abs(io["J0"])
+    assert abs(info["J"] - io["J"]) <= 1e-12 * abs(io["J"])
+    assert abs(info["lam"] - io["lam"]) <= 1e-12 * io["lam"] and info["trials"] == io["trials"]
+    assert rel(g, go) < 1e-12
+    info2 = p.step(g)
+    go2, io2 = oracle.gd_step(oracle.from_workload(w), go, lam_prev=io["lam"])
+    assert abs(info2["J"] - io2["J"]) <= 1e-12 * abs(io2["J"])
+    assert rel(g, go2) < 1e-12
+
+
+# ---------------------------------------------------------------- FP32 parity
+
+def test_aniso_fp32_against_fp64_oracle():
+    w = W.aniso(96, 80, 60, seed=1, precision=32, ckpt_every=16)
+    g = w.random_control(9, 0.02)
+    check(run_both(w, g), TOL32_FIELD, TOL32_GRAD, "aniso fp32")
+
+
+def test_geometry_fp32_against_fp64_oracle():
+    w = W.geometry(96, 96, 40, seed=2, precision=32, ckpt_every=10, win=48, rmin=3, rmax=10)
+    g = w.random_control(10, 0.02)
+    check(run_both(w, g), TOL32_FIELD, TOL32_GRAD, "geometry fp32")
+
+
+# ------------------------------------------------- full-size workload (sampled)
+
+def test_aniso1024_fp32_full_size_sampled():
+    """1024x1024 D2Q9 FP32 in the benchmark's launch configuration: the first
+    steps against the oracle (every node), and u-mass conservation over the
+    full 2000 steps (sum_i S_i = 0, no source in the u equation)."""
+    from paper_1908_03876_gb300.problem import Problem
+
+    wf = W.aniso()  # 1024^2, N = 2000, k = 100
+    short = W.aniso(N=3, ckpt_every=2)
+    g = short.random_control(11, 0.02)
+    check(run_both(short, g), TOL32_FIELD, TOL32_GRAD, "aniso1024 fp32, 3 steps")
+    p = Problem(wf)
+    J = p.forward(None)
+    u, v = p.fields()
+    mass0 = float(np.sum(wf.u0))
+    massN = float(u.double().sum().item())
+    print(f"aniso1024 2000 steps: J={J.item():.6e}, u-mass drift {abs(massN / mass0 - 1):.2e}")
+    assert np.isfinite(J.item())
+    assert abs(massN / mass0 - 1) < 1e-5
