@@ -146,7 +146,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="small profiling case: the same 1024x1024 lattice, 20 time steps, k = 10, "
+                         "one warm-up and one timed gradient evaluation, no CPU baseline or e2e leg")
     args = ap.parse_args()
+    if args.profile:
+        WORKLOAD.update(N=20, k=10)
+        args.steps, args.warmup, args.no_cpu_baseline = 1, 1, True
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -237,7 +243,7 @@ def main():
 
     # ---- end to end: host control in, host gradient and cost out, every step
     e2e = None
-    if rank == 0:
+    if rank == 0 and not args.profile:
         try:
             g_host = torch.empty(g.shape, dtype=g.dtype, pin_memory=True)
             g_host.copy_(g.cpu())

@@ -172,7 +172,7 @@ cx_status cx_get_psi0(cx_problem* p, void* out);
 cx_status cx_get_norms(cx_problem* p, double* J, double* grad_sq, double* grad_inf);
 
 /* Launch shape of the lattice kernels (threads per block in x and y; bx a
- * multiple of 32, bx * by <= 1024).  Errors: CX_ERR_INVALID_ARG. */
+ * multiple of 32, bx * by <= 256).  Errors: CX_ERR_INVALID_ARG. */
 cx_status cx_set_launch(cx_problem* p, int bx, int by);
 
 /* Per-phase timing with CUDA events on the problem's stream: enable != 0

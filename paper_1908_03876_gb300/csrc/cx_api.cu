@@ -376,7 +376,8 @@ cx_status cx_workspace_size(const cx_problem_desc* desc, size_t* bytes) {
 }
 
 cx_status cx_set_launch(cx_problem* p, int bx, int by) {
-    if (!p || bx < 32 || bx % 32 != 0 || by < 1 || bx * by > 1024 || bx * by < 32) return CX_ERR_INVALID_ARG;
+    // the lattice kernels are compiled for at most 256 threads per block
+    if (!p || bx < 32 || bx % 32 != 0 || by < 1 || bx * by > 256) return CX_ERR_INVALID_ARG;
     p->L.block = dim3(bx, by);
     p->L.grid = dim3((p->d.nx + bx - 1) / bx, (p->d.ny + by - 1) / by);
     p->nblocks = (int)(p->L.grid.x * p->L.grid.y);

@@ -30,6 +30,8 @@ class Problem:
         self.lib = _lib.load()
         self.w = w
         self.device = torch.device(device)
+        if self.device.type == "cuda" and self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
         self.precision = precision or w.precision
         self.dtype = torch.float64 if self.precision == 64 else torch.float32
         self.stream = stream or torch.cuda.current_stream(self.device)
@@ -136,7 +138,8 @@ class Problem:
 
     def step(self, g, E=None):
         """One Armijo steepest-descent iteration, g updated in place."""
-        if g.dtype != self.dtype or not g.is_contiguous() or g.device != self.device:
+        if g.dtype != self.dtype or not g.is_contiguous() or g.device != self.device or \
+                tuple(g.shape) != tuple(self.ctrl_shape):
             raise ValueError("g must be a contiguous device tensor of the problem's dtype")
         E = E if E is not None else torch.empty_like(g)
         info = _lib.StepInfo()

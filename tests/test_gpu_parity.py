@@ -130,7 +130,7 @@ def test_launch_shape_independent_bitwise():
     from paper_1908_03876_gb300.problem import Problem
 
     outs = []
-    for shape in [(32, 1), (64, 4), (128, 2), (32, 32)]:
+    for shape in [(32, 1), (64, 4), (128, 2), (32, 8), (256, 1)]:
         p = Problem(w)
         p.set_launch(*shape)
         p.forward(g)
