@@ -171,9 +171,11 @@ cx_status cx_get_psi0(cx_problem* p, void* out);
  * error (CX_ERR_UNSTABLE for a non-finite value). */
 cx_status cx_get_norms(cx_problem* p, double* J, double* grad_sq, double* grad_inf);
 
-/* Launch shape of the lattice kernels (threads per block in x and y; bx a
- * multiple of 32, bx * by <= 256).  Errors: CX_ERR_INVALID_ARG. */
-cx_status cx_set_launch(cx_problem* p, int bx, int by);
+/* Launch shape of the persistent lattice kernels: `threads` per block (64,
+ * 128 or 256) and `blocks` resident blocks (0: every SM at full occupancy).
+ * Results do not depend on the shape.
+ * Errors: CX_ERR_INVALID_ARG (also when blocks * threads / 32 > 32768). */
+cx_status cx_set_launch(cx_problem* p, int threads, int blocks);
 
 /* Per-phase timing with CUDA events on the problem's stream: enable != 0
  * starts accumulating.  cx_get_timing (synchronising) returns milliseconds

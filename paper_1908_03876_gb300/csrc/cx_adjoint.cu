@@ -15,187 +15,231 @@
 //               lambda_Phi^n = c_n sigma^n + c'_{n+1} sigma^{n+1} + (G path),
 //               sigma^n = sum_i rho_v,i w~_i.
 // The tape (u^n, G^n) comes from the forward recompute of the segment.
+//
+// Execution: the persistent, two-stage cp.async pipeline of the forward
+// kernel (see cx_forward.cu), staging the pulled adjoint populations, the tape,
+// sigma^{n+1}, g^n and the angle of the next node while the current one runs.
 #include "cx_device.cuh"
 
 namespace cx {
 
-template <typename T, int Q>
-__global__ void __launch_bounds__(256) k_adjoint(const CxConst C, const AdjArgs<T> A) {
+template <int Q> constexpr int adj_stage_values() { return 2 * Q + 6; } // pops, u, Gx, Gy, sigma, g, theta
+
+template <typename T, int Q, int NT>
+__device__ __forceinline__ void adj_stage(const CxConst& C, const AdjArgs<T>& A, const NodeIdx& nd, T* s) {
     using L = Lat<Q>;
-    __shared__ double red[32];
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    double e2 = 0.0, emax = 0.0;
-    const bool inside = (x < C.nx) && (y < C.ny);
-    const int k = y * C.nx + x;
-    const bool fluid = inside && !(C.has_solid && C.solid[k]);
-    if (fluid) {
-        const size_t pl = (size_t)C.plane;
-        T ru[Q], rv[Q];
-        const int xm = x == 0 ? C.nx - 1 : x - 1, xp = x == C.nx - 1 ? 0 : x + 1;
-        const int ym = y == 0 ? C.ny - 1 : y - 1, yp = y == C.ny - 1 ? 0 : y + 1;
+    if (!nd.fluid) return;
+    const int x = nd.x, y = nd.y, k = nd.k;
+    const size_t pl = (size_t)C.plane;
+    const int xm = x == 0 ? C.nx - 1 : x - 1, xp = x == C.nx - 1 ? 0 : x + 1;
+    const int rm = (y == 0 ? C.ny - 1 : y - 1) * C.nx, r0 = y * C.nx, rp = (y == C.ny - 1 ? 0 : y + 1) * C.nx;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int xd = L::ex(i) > 0 ? xp : (L::ex(i) < 0 ? xm : x);
+        const int kd = (L::ey(i) > 0 ? rp : (L::ey(i) < 0 ? rm : r0)) + xd;
+        const bool bounce = C.has_solid && i != 0 && C.solid[kd];
         if (A.terminal) {
-            const T wu0 = ldg(A.wu + k);
-            const T wv0 = A.wv ? ldg(A.wv + k) : T(0);
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const int xd = L::ex(i) > 0 ? xp : (L::ex(i) < 0 ? xm : x);
-                const int yd = L::ey(i) > 0 ? yp : (L::ey(i) < 0 ? ym : y);
-                const int kd = yd * C.nx + xd;
-                if (i != 0 && C.has_solid && C.solid[kd]) {
-                    ru[i] = wu0;
-                    rv[i] = wv0;
-                } else {
-                    ru[i] = ldg(A.wu + kd);
-                    rv[i] = A.wv ? ldg(A.wv + kd) : T(0);
-                }
-            }
+            // psi^N_i(x) is the seed w(x) in every direction
+            cp_async(s + i * NT, A.wu + (bounce ? k : kd));
+            if (A.wv) cp_async(s + (Q + i) * NT, A.wv + (bounce ? k : kd));
+        } else if (bounce) {
+            cp_async(s + i * NT, A.rin[L::opp(i)] + k);
+            cp_async(s + (Q + i) * NT, A.rin[Q + L::opp(i)] + k);
         } else {
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const int xd = L::ex(i) > 0 ? xp : (L::ex(i) < 0 ? xm : x);
-                const int yd = L::ey(i) > 0 ? yp : (L::ey(i) < 0 ? ym : y);
-                const int kd = yd * C.nx + xd;
-                if (i != 0 && C.has_solid && C.solid[kd]) {
-                    ru[i] = ldg(A.Rin + L::opp(i) * pl + k);
-                    rv[i] = ldg(A.Rin + (Q + L::opp(i)) * pl + k);
-                } else {
-                    ru[i] = ldg(A.Rin + i * pl + kd);
-                    rv[i] = ldg(A.Rin + (Q + i) * pl + kd);
-                }
-            }
+            cp_async(s + i * NT, A.rin[i] + kd);
+            cp_async(s + (Q + i) * NT, A.rin[Q + i] + kd);
         }
-        NodeCoef<T> nc;
-        node_coef<T>(C, x, y, k, nc);
-        const T Tu = ldg(A.tape + k);
-        const T Gx = ldg(A.tape + pl + k);
-        const T Gy = ldg(A.tape + 2 * pl + k);
-        const T tau = T(C.tau);
-
-        // --- transposed collisions: mt = M^T Pi^T (N^-1 M rho), Tcal = sum_k z_k mh_k
-        T mh[Q], lam[Q], z[Q];
-        T psu[Q], psv[Q];
-        {
-            meq_unit<T, Q>(nc.ax, nc.ay, T(C.d_u), mh);
-#pragma unroll
-            for (int kk = 0; kk < Q; ++kk) {
-                T s = T(0);
-#pragma unroll
-                for (int i = 0; i < Q; ++i)
-                    if (L::M(kk, i) != 0) s += T(L::M(kk, i)) * ru[i];
-                lam[kk] = s * T(L::inv_n(kk));
-            }
-            relax_T<T, Q>(C, nc.Ku0, nc.Ku1, nc.Ku2, lam, z);
-            T Tc = T(0);
-#pragma unroll
-            for (int kk = 0; kk < Q; ++kk) Tc += z[kk] * mh[kk];
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                T s = T(0);
-#pragma unroll
-                for (int kk = 0; kk < Q; ++kk)
-                    if (L::M(kk, i) != 0) s += T(L::M(kk, i)) * z[kk];
-                psu[i] = ru[i] - s + Tc;
-            }
-        }
-        {
-            meq_unit<T, Q>(nc.ax, nc.ay, T(C.d_v), mh);
-#pragma unroll
-            for (int kk = 0; kk < Q; ++kk) {
-                T s = T(0);
-#pragma unroll
-                for (int i = 0; i < Q; ++i)
-                    if (L::M(kk, i) != 0) s += T(L::M(kk, i)) * rv[i];
-                lam[kk] = s * T(L::inv_n(kk));
-            }
-            relax_T<T, Q>(C, nc.Kv0, nc.Kv1, nc.Kv2, lam, z);
-            T Tc = T(0);
-#pragma unroll
-            for (int kk = 0; kk < Q; ++kk) Tc += z[kk] * mh[kk];
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                T s = T(0);
-#pragma unroll
-                for (int kk = 0; kk < Q; ++kk)
-                    if (L::M(kk, i) != 0) s += T(L::M(kk, i)) * z[kk];
-                psv[i] = rv[i] - s + Tc;
-            }
-        }
-
-        // --- coupling through tau S_u,i = 3 w_i chi u e_i . (K_u G)
-        T Yx = T(0), Yy = T(0);
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            Yx += T(3.0 * L::w(i) * L::ex(i)) * ru[i];
-            Yy += T(3.0 * L::w(i) * L::ey(i)) * ru[i];
-        }
-        const T chi = T(C.chi);
-        T adj_Tu = chi * (Yx * (nc.Ku0 * Gx + nc.Ku1 * Gy) + Yy * (nc.Ku1 * Gx + nc.Ku2 * Gy));
-        const T aGx = chi * Tu * (nc.Ku0 * Yx + nc.Ku1 * Yy);
-        const T aGy = chi * Tu * (nc.Ku1 * Yx + nc.Ku2 * Yy);
-        // G = -(K_v (j_v - a v)/tau + K_v a Phi/2) / (d_v Cs^2)
-        const T KGx = nc.Kv0 * aGx + nc.Kv1 * aGy, KGy = nc.Kv1 * aGx + nc.Kv2 * aGy;
-        const T sc = T(3.0) / T(C.d_v);
-        const T ajx = -KGx * sc / tau, ajy = -KGy * sc / tau;
-        const T aKG = nc.ax * KGx + nc.ay * KGy;
-        T adj_Tv = aKG * sc / tau;
-        T adj_Phi = T(-0.5) * aKG * sc;
-
-        // --- reaction/control source: sigma^n and the use of Phi^n at step n+1
-        const T Kax = nc.Kv0 * nc.ax + nc.Kv1 * nc.ay, Kay = nc.Kv1 * nc.ax + nc.Kv2 * nc.ay;
-        const T Vx = nc.ax - T(0.5) * Kax, Vy = nc.ay - T(0.5) * Kay;
-        T sigma = T(0);
-#pragma unroll
-        for (int i = 0; i < Q; ++i)
-            sigma += T(L::w(i)) * (T(1) + T(3) * (Vx * T(L::ex(i)) + Vy * T(L::ey(i)))) * rv[i];
-        const T cn = (C.source_order == 1 || A.n == 0) ? tau : T(1.5) * tau;
-        adj_Phi += cn * sigma;
-        if (!A.terminal && C.source_order != 1) adj_Phi += T(-0.5) * tau * A.sigma[k];
-        A.sigma[k] = sigma;
-        adj_Tu += T(C.r_vu) * adj_Phi;
-        adj_Tv += T(C.r_vv) * adj_Phi;
-
-        const int c = ctrl_window(C, x, y);
-        if (ctrl_active(C, c)) {
-            const T gv = A.g ? ldg(A.g + c) : T(0);
-            const T E = adj_Phi + T(2.0 * C.alpha) * gv;
-            A.dJdg[c] = E;
-            e2 = (double)E * (double)E;
-            emax = fabs((double)E);
-        } else if (c >= 0) {
-            A.dJdg[c] = T(0);
-        }
-        T* Ou = A.Rout;
-        T* Ov = A.Rout + (size_t)Q * pl;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            Ou[i * pl + k] = psu[i] + adj_Tu;
-            Ov[i * pl + k] = psv[i] + adj_Tv + T(L::ex(i)) * ajx + T(L::ey(i)) * ajy;
-        }
-    } else if (inside) {
-        // solid window nodes are not controlled: zero gradient
-        const int c = ctrl_window(C, x, y);
-        if (c >= 0) A.dJdg[c] = T(0);
     }
-    const double b2 = block_sum(e2, red);
-    const double bm = block_max(emax, red);
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
-        const int b = blockIdx.x + gridDim.x * blockIdx.y;
-        A.e2_part[b] += b2;
-        A.emax_part[b] = fmax(A.emax_part[b], bm);
+    cp_async(s + (2 * Q) * NT, A.tape + k);
+    cp_async(s + (2 * Q + 1) * NT, A.tape + pl + k);
+    cp_async(s + (2 * Q + 2) * NT, A.tape + 2 * pl + k);
+    if (!A.terminal) cp_async(s + (2 * Q + 3) * NT, A.sigma + k);
+    if (nd.ctrl && A.g) cp_async(s + (2 * Q + 4) * NT, A.g + nd.c);
+    if (C.aniso == CX_ANISO_ROTATED) cp_async(s + (2 * Q + 5) * NT, reinterpret_cast<const T*>(C.theta) + k);
+}
+
+template <typename T, int Q, int NT>
+__device__ __forceinline__ void adj_compute(const CxConst& C, const KConst<T>& KC, const AdjArgs<T>& A,
+                                            const NodeIdx& nd, const T* s, typename SqAccT<T>::type& acc) {
+    using L = Lat<Q>;
+    if (!nd.fluid) {
+        if (nd.c >= 0) A.dJdg[nd.c] = T(0); // solid window nodes are not controlled
+        return;
+    }
+    const int y = nd.y, k = nd.k;
+    T ru[Q], rv[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        ru[i] = s[i * NT];
+        rv[i] = (A.terminal && !A.wv) ? T(0) : s[(Q + i) * NT];
+    }
+    const T Tu = s[(2 * Q) * NT];
+    const T Gx = s[(2 * Q + 1) * NT];
+    const T Gy = s[(2 * Q + 2) * NT];
+    const T sig_next = A.terminal ? T(0) : s[(2 * Q + 3) * NT];
+    const T gv = (nd.ctrl && A.g) ? s[(2 * Q + 4) * NT] : T(0);
+    NodeCoef<T> nc;
+    node_coef_th<T>(C, KC, (C.aniso == CX_ANISO_ROTATED) ? s[(2 * Q + 5) * NT] : T(0), y, k, nc);
+
+    // --- transposed collisions: mt = M^T Pi^T (N^-1 M rho), Tcal = sum_k z_k mh_k
+    T mh[Q], mom[Q], z[Q], mt[Q];
+    T psu[Q], psv[Q];
+    meq_unit<T, Q>(nc.ax, nc.ay, KC.d_u, mh);
+    Transform<T, Q>::moments(ru, mom);
+    relax_n<T, Q>(KC, nc.Ku0, nc.Ku1, nc.Ku2, mom, z);
+    T Tc = T(0);
+#pragma unroll
+    for (int kk = 0; kk < Q; ++kk) Tc += z[kk] * mh[kk];
+    Transform<T, Q>::transpose(z, mt);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) psu[i] = ru[i] - mt[i] + Tc;
+
+    meq_unit<T, Q>(nc.ax, nc.ay, KC.d_v, mh);
+    Transform<T, Q>::moments(rv, mom);
+    relax_n<T, Q>(KC, nc.Kv0, nc.Kv1, nc.Kv2, mom, z);
+    Tc = T(0);
+#pragma unroll
+    for (int kk = 0; kk < Q; ++kk) Tc += z[kk] * mh[kk];
+    Transform<T, Q>::transpose(z, mt);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) psv[i] = rv[i] - mt[i] + Tc;
+
+    // --- coupling through tau S_u,i = 3 w_i chi u e_i . (K_u G)
+    T Yx = T(0), Yy = T(0);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        Yx += T(3.0 * L::w(i) * L::ex(i)) * ru[i];
+        Yy += T(3.0 * L::w(i) * L::ey(i)) * ru[i];
+    }
+    const T chi = KC.chi;
+    T adj_Tu = chi * (Yx * (nc.Ku0 * Gx + nc.Ku1 * Gy) + Yy * (nc.Ku1 * Gx + nc.Ku2 * Gy));
+    const T aGx = chi * Tu * (nc.Ku0 * Yx + nc.Ku1 * Yy);
+    const T aGy = chi * Tu * (nc.Ku1 * Yx + nc.Ku2 * Yy);
+    // G = -(K_v (j_v - a v)/tau + K_v a Phi/2) / (d_v Cs^2)
+    const T KGx = nc.Kv0 * aGx + nc.Kv1 * aGy, KGy = nc.Kv1 * aGx + nc.Kv2 * aGy;
+    const T sc = KC.asc; // 1 / (d_v Cs^2)
+    const T ajx = -KGx * sc * KC.inv_tau, ajy = -KGy * sc * KC.inv_tau;
+    const T aKG = nc.ax * KGx + nc.ay * KGy;
+    T adj_Tv = aKG * sc * KC.inv_tau;
+    T adj_Phi = T(-0.5) * aKG * sc;
+
+    // --- reaction/control source: sigma^n and the use of Phi^n at step n+1
+    const T Kax = nc.Kv0 * nc.ax + nc.Kv1 * nc.ay, Kay = nc.Kv1 * nc.ax + nc.Kv2 * nc.ay;
+    const T Vx = nc.ax - T(0.5) * Kax, Vy = nc.ay - T(0.5) * Kay;
+    T sigma = T(0);
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+        sigma += T(L::w(i)) * (T(1) + T(3) * (Vx * T(L::ex(i)) + Vy * T(L::ey(i)))) * rv[i];
+    adj_Phi += ((A.n == 0) ? KC.c_first : KC.c_now) * sigma;
+    if (!A.terminal) adj_Phi += KC.c_prev * sig_next; // Phi^n feeds step n+1 with c'_{n+1}
+    A.sigma[k] = sigma;
+    adj_Tu += KC.r_vu * adj_Phi;
+    adj_Tv += KC.r_vv * adj_Phi;
+
+    if (nd.ctrl) {
+        const T E = adj_Phi + KC.two_alpha * gv;
+        A.dJdg[nd.c] = E;
+        acc.add(E);
+    } else if (nd.c >= 0) {
+        A.dJdg[nd.c] = T(0);
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        A.rout[i][k] = psu[i] + adj_Tu;
+        A.rout[Q + i][k] = psv[i] + adj_Tv + T(L::ex(i)) * ajx + T(L::ey(i)) * ajy;
+    }
+}
+
+template <typename T, int Q, int NT>
+__global__ void __launch_bounds__(NT) k_adjoint(const CxConst C, const KConst<T> KC, const AdjArgs<T> A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int NV = adj_stage_values<Q>();
+    T* const s0 = reinterpret_cast<T*>(smem_raw) + threadIdx.x;
+    T* const s1 = s0 + NV * NT;
+    typename SqAccT<T>::type acc;
+    ChunkIter<NT> it(C);
+    NodeIdx cur = it.valid() ? it.node(C) : no_node();
+    allow_next_grid();
+    wait_prior_grid(); // the previous step's populations and node state are complete
+    if (it.valid()) adj_stage<T, Q, NT>(C, A, cur, s0);
+    cp_async_commit();
+    bool odd = false;
+    while (it.valid()) {
+        it.next();
+        const NodeIdx nxt = it.valid() ? it.node(C) : no_node();
+        if (it.valid()) adj_stage<T, Q, NT>(C, A, nxt, odd ? s0 : s1);
+        cp_async_commit();
+        cp_async_wait<1>();
+        adj_compute<T, Q, NT>(C, KC, A, cur, odd ? s1 : s0, acc);
+        cur = nxt;
+        odd = !odd;
+    }
+    cp_async_wait<0>();
+    const int w = blockIdx.x * (NT >> 5) + (threadIdx.x >> 5);
+    acc.flush(A.e2_part + w, A.emax_part + w);
+}
+
+template <typename T, int Q, int NT>
+static cudaError_t launch_qn(const CxConst& C, const KConst<T>& K, const AdjArgs<T>& A, const Launch& L,
+                             cudaStream_t s) {
+    const size_t smem = (size_t)2 * adj_stage_values<Q>() * NT * sizeof(T);
+    static bool attr_set = false; // the attribute belongs to the function, once per process
+    if (!attr_set) {
+        cudaError_t e =
+            cudaFuncSetAttribute(k_adjoint<T, Q, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 112 * 1024);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = L.grid;
+    cfg.blockDim = L.block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_adjoint<T, Q, NT>, C, K, A);
+}
+
+template <typename T, int Q>
+static cudaError_t launch_q(const CxConst& C, const KConst<T>& K, const AdjArgs<T>& A, const Launch& L,
+                            cudaStream_t s) {
+    switch (L.block.x) {
+    case 64: return launch_qn<T, Q, 64>(C, K, A, L, s);
+    case 128: return launch_qn<T, Q, 128>(C, K, A, L, s);
+    case 256: return launch_qn<T, Q, 256>(C, K, A, L, s);
+    default: return cudaErrorInvalidConfiguration;
     }
 }
 
 template <typename T>
-cudaError_t launch_adjoint(const CxConst& C, const AdjArgs<T>& A, const Launch& L, cudaStream_t s) {
-    if (C.Q == 9)
-        k_adjoint<T, 9><<<L.grid, L.block, 0, s>>>(C, A);
-    else
-        k_adjoint<T, 5><<<L.grid, L.block, 0, s>>>(C, A);
-    return cudaGetLastError();
+cudaError_t launch_adjoint(const CxConst& C, const KConst<T>& K, const AdjArgs<T>& A, const Launch& L,
+                           cudaStream_t s) {
+    return C.Q == 9 ? launch_q<T, 9>(C, K, A, L, s) : launch_q<T, 5>(C, K, A, L, s);
 }
 
-template cudaError_t launch_adjoint<float>(const CxConst&, const AdjArgs<float>&, const Launch&, cudaStream_t);
-template cudaError_t launch_adjoint<double>(const CxConst&, const AdjArgs<double>&, const Launch&, cudaStream_t);
+template cudaError_t launch_adjoint<float>(const CxConst&, const KConst<float>&, const AdjArgs<float>&,
+                                           const Launch&, cudaStream_t);
+template cudaError_t launch_adjoint<double>(const CxConst&, const KConst<double>&, const AdjArgs<double>&,
+                                            const Launch&, cudaStream_t);
+
+template <typename T, int Q, int NT> static int occ_qn() {
+    cudaFuncSetAttribute(k_adjoint<T, Q, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 112 * 1024);
+    int nb = 0;
+    const size_t smem = (size_t)2 * adj_stage_values<Q>() * NT * sizeof(T);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adjoint<T, Q, NT>, NT, smem) != cudaSuccess) return 1;
+    return nb > 0 ? nb : 1;
+}
+template <typename T, int Q> static int occ_q(int threads) {
+    return threads == 64 ? occ_qn<T, Q, 64>() : (threads == 128 ? occ_qn<T, Q, 128>() : occ_qn<T, Q, 256>());
+}
+
+template <typename T> int adjoint_occupancy(int Q, int threads) {
+    return Q == 9 ? occ_q<T, 9>(threads) : occ_q<T, 5>(threads);
+}
+template int adjoint_occupancy<float>(int, int);
+template int adjoint_occupancy<double>(int, int);
 
 } // namespace cx

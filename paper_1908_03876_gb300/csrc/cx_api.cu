@@ -27,6 +27,7 @@ using namespace cx;
 namespace {
 
 constexpr size_t ALIGN = 256;
+constexpr int MAX_WARPS = 32768; // warps of a persistent launch (partial-sum slots)
 inline size_t up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 enum { PH_FWD = 0, PH_REC = 1, PH_ADJ = 2, PH_OTHER = 3 };
@@ -54,8 +55,14 @@ struct cx_problem {
     Layout lay;
     cudaStream_t stream;
     char* ws;
-    Launch L;
-    int nblocks;
+    KConst<float> Kf;
+    KConst<double> Kd;
+    const KConst<float>& kc(float*) const { return Kf; }
+    const KConst<double>& kc(double*) const { return Kd; }
+    Launch L;      // 2D launch of the set-up, initial and final kernels
+    Launch Lf, La; // persistent launches of the forward and adjoint kernels
+    int nblocks;   // blocks of L
+    int nsm = 1;
     bool has_init = false, fwd_valid = false, adj_valid = false;
     bool tape_last_valid = false; // tape holds the last segment (written by the forward)
     bool have_lam = false;
@@ -113,8 +120,9 @@ static Layout make_layout(const cx_problem_desc* d) {
     L.plane = up((size_t)d->nx * d->ny, 64);
     const int cnx = d->ctrl_nx > 0 ? d->ctrl_nx : d->nx, cny = d->ctrl_nx > 0 ? d->ctrl_ny : d->ny;
     L.nctrl = (size_t)cnx * cny;
-    // partial buffers sized for the smallest admissible block (32 x 1)
-    L.nparts = ((d->nx + 31) / 32) * d->ny;
+    // partial buffers: per-block sums of the 2D kernels (blocks of 256 threads,
+    // at most (nx/32 + 1) * ny of them) or per-warp sums of the persistent ones
+    L.nparts = std::max(((d->nx + 31) / 32) * d->ny, MAX_WARPS);
     const size_t pop = (size_t)2 * L.Q * L.plane * L.esz, fld = L.plane * L.esz;
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -196,13 +204,19 @@ static void range_end(cx_problem* p, TimedRange* r, long long launches) {
 
 // ----------------------------------------------------------- templated core
 
+// plane j of a [2][Q][plane] population buffer
+template <typename T, typename P> static void set_planes(const cx_problem* p, P (&dst)[18], T* buf) {
+    for (int j = 0; j < 18; ++j) dst[j] = j < 2 * p->lay.Q ? buf + (size_t)j * p->lay.plane : nullptr;
+}
+
 template <typename T> static cx_status run_forward(cx_problem* p, const T* g, const T* E, double lam, double* J_dev,
                                                   bool flag_unstable) {
     const Layout& Ly = p->lay;
     const CxConst& C = p->C;
     double* part = p->at<double>(Ly.off_part);
     double* gsq = part + Ly.nparts;
-    CX_CUDA(cudaMemsetAsync(gsq, 0, sizeof(double) * p->nblocks, p->stream));
+    const int fw = (int)(p->Lf.grid.x * (p->Lf.block.x / 32));
+    CX_CUDA(cudaMemsetAsync(gsq, 0, sizeof(double) * fw, p->stream));
     TimedRange* r;
     range_begin(p, PH_FWD, &r);
     const T* in = reinterpret_cast<const T*>(p->ckpt_slot(0));
@@ -210,29 +224,31 @@ template <typename T> static cx_status run_forward(cx_problem* p, const T* g, co
     for (int n = 0; n < Ly.N; ++n) {
         const int seg = n / Ly.k;
         FwdArgs<T> A{};
-        A.Pin = in;
+        T* out;
         if (n + 1 < Ly.N && (n + 1) % Ly.k == 0) {
-            A.Pout = reinterpret_cast<T*>(p->ckpt_slot((n + 1) / Ly.k));
+            out = reinterpret_cast<T*>(p->ckpt_slot((n + 1) / Ly.k));
             A.phi_ckpt = reinterpret_cast<T*>(p->ckpt_phi_slot((n + 1) / Ly.k));
         } else {
-            A.Pout = p->at<T>((n % 2) ? Ly.off_popB : Ly.off_popA);
+            out = p->at<T>((n % 2) ? Ly.off_popB : Ly.off_popA);
             A.phi_ckpt = nullptr;
         }
+        set_planes(p, A.pin, in);
+        set_planes(p, A.pout, out);
         A.phi = phi;
         A.g = g ? g + (size_t)n * Ly.nctrl : nullptr;
         A.E = E ? E + (size_t)n * Ly.nctrl : nullptr;
-        A.lam = lam;
+        A.lam = T(lam);
         A.tape = (seg == Ly.S - 1) ? reinterpret_cast<T*>(p->tape_slot(n - seg * Ly.k)) : nullptr;
         A.gsq_part = gsq;
         A.n = n;
-        CX_CUDA(launch_forward<T>(C, A, p->L, p->stream));
-        in = A.Pout;
+        CX_CUDA(launch_forward<T>(C, p->kc((T*)nullptr), A, p->Lf, p->stream));
+        in = out;
     }
     double* cost = part;
     CX_CUDA(launch_final<T>(C, in, p->at<T>(Ly.off_ut), p->at<T>(Ly.off_uN), p->at<T>(Ly.off_vN), p->at<T>(Ly.off_wu),
                             cost, p->L, p->stream));
     double* scal = p->at<double>(Ly.off_scal);
-    CX_CUDA(launch_finalize(cost, gsq, p->nblocks, C.alpha, scal, p->at<int>(Ly.off_status),
+    CX_CUDA(launch_finalize(cost, p->nblocks, gsq, fw, C.alpha, scal, p->at<int>(Ly.off_status),
                             flag_unstable ? ST_UNSTABLE : 0, 0, p->stream));
     range_end(p, r, Ly.N);
     if (J_dev) CX_CUDA(cudaMemcpyAsync(J_dev, scal, sizeof(double), cudaMemcpyDeviceToDevice, p->stream));
@@ -250,6 +266,7 @@ static cx_status run_adjoint(cx_problem* p, const T* g, const T* seed_u, const T
     double* e2 = part + 2 * (size_t)Ly.nparts;
     double* emax = part + 3 * (size_t)Ly.nparts;
     CX_CUDA(cudaMemsetAsync(e2, 0, sizeof(double) * 2 * Ly.nparts, p->stream));
+    const int aw = (int)(p->La.grid.x * (p->La.block.x / 32));
     T* sigma = p->at<T>(Ly.off_sigma);
     CX_CUDA(cudaMemsetAsync(sigma, 0, Ly.plane * sizeof(T), p->stream));
     T* phi = p->at<T>(Ly.off_phi);
@@ -265,16 +282,17 @@ static cx_status run_adjoint(cx_problem* p, const T* g, const T* seed_u, const T
             const T* in = reinterpret_cast<const T*>(p->ckpt_slot(s));
             for (int n = n0; n < n1; ++n) {
                 FwdArgs<T> A{};
-                A.Pin = in;
-                A.Pout = p->at<T>((n % 2) ? Ly.off_popB : Ly.off_popA);
+                T* out = p->at<T>((n % 2) ? Ly.off_popB : Ly.off_popA);
+                set_planes(p, A.pin, in);
+                set_planes(p, A.pout, out);
                 A.phi = phi;
                 A.phi_ckpt = nullptr;
                 A.g = g ? g + (size_t)n * Ly.nctrl : nullptr;
                 A.tape = reinterpret_cast<T*>(p->tape_slot(n - n0));
                 A.gsq_part = nullptr;
                 A.n = n;
-                CX_CUDA(launch_forward<T>(C, A, p->L, p->stream));
-                in = A.Pout;
+                CX_CUDA(launch_forward<T>(C, p->kc((T*)nullptr), A, p->Lf, p->stream));
+                in = out;
             }
             range_end(p, r, n1 - n0);
         }
@@ -283,10 +301,11 @@ static cx_status run_adjoint(cx_problem* p, const T* g, const T* seed_u, const T
         for (int n = n1 - 1; n >= n0; --n) {
             AdjArgs<T> A{};
             A.terminal = (n == Ly.N - 1);
-            A.Rin = psi_in;
+            T* out = p->at<T>((n % 2) ? Ly.off_adjB : Ly.off_adjA);
+            if (psi_in) set_planes(p, A.rin, psi_in);
+            set_planes(p, A.rout, out);
             A.wu = seed_u ? seed_u : p->at<T>(Ly.off_wu);
             A.wv = seed_v;
-            A.Rout = p->at<T>((n % 2) ? Ly.off_adjB : Ly.off_adjA);
             A.tape = reinterpret_cast<const T*>(p->tape_slot(n - n0));
             A.sigma = sigma;
             A.g = g ? g + (size_t)n * Ly.nctrl : nullptr;
@@ -294,13 +313,13 @@ static cx_status run_adjoint(cx_problem* p, const T* g, const T* seed_u, const T
             A.e2_part = e2;
             A.emax_part = emax;
             A.n = n;
-            CX_CUDA(launch_adjoint<T>(C, A, p->L, p->stream));
-            psi_in = A.Rout;
+            CX_CUDA(launch_adjoint<T>(C, p->kc((T*)nullptr), A, p->La, p->stream));
+            psi_in = out;
         }
         range_end(p, r, n1 - n0);
     }
     double* scal = p->at<double>(Ly.off_scal);
-    CX_CUDA(launch_finalize(e2, emax, p->nblocks, 0.0, scal + 2, p->at<int>(Ly.off_status), ST_UNSTABLE, 1,
+    CX_CUDA(launch_finalize(e2, aw, emax, aw, 0.0, scal + 2, p->at<int>(Ly.off_status), ST_UNSTABLE, 1,
                             p->stream));
     p->psi0 = const_cast<T*>(psi_in);
     p->adj_valid = true;
@@ -342,7 +361,7 @@ template <typename T> static cx_status run_step(cx_problem* p, T* g, T* E, cx_st
         if (rc) return rc;
         const double Jt = j4[0];
         if (std::isfinite(Jt) && Jt <= J0 - 1e-4 * lam * e2) {
-            CX_CUDA(launch_axpy<T>(g, E, lam, (size_t)p->lay.N * p->lay.nctrl, p->stream));
+            CX_CUDA(launch_axpy<T>(g, E, T(lam), (size_t)p->lay.N * p->lay.nctrl, p->stream));
             p->fwd_valid = true; // the accepted trial's forward state is the new control's
             p->adj_valid = false;
             p->lam_prev = lam;
@@ -375,12 +394,39 @@ cx_status cx_workspace_size(const cx_problem_desc* desc, size_t* bytes) {
     return CX_OK;
 }
 
-cx_status cx_set_launch(cx_problem* p, int bx, int by) {
-    // the lattice kernels are compiled for at most 256 threads per block
-    if (!p || bx < 32 || bx % 32 != 0 || by < 1 || bx * by > 256) return CX_ERR_INVALID_ARG;
-    p->L.block = dim3(bx, by);
-    p->L.grid = dim3((p->d.nx + bx - 1) / bx, (p->d.ny + by - 1) / by);
+static void set_2d(cx_problem* p) {
+    const int bx = p->d.nx >= 128 ? 128 : (p->d.nx >= 64 ? 64 : 32);
+    p->L.block = dim3(bx, 256 / bx);
+    p->L.grid = dim3((p->d.nx + bx - 1) / bx, (p->d.ny + 256 / bx - 1) / (256 / bx));
     p->nblocks = (int)(p->L.grid.x * p->L.grid.y);
+}
+
+// Persistent grid: `blocks` blocks of `threads` threads (0 blocks: all SMs at
+// full residency), never more blocks than row segments of work.
+static cx_status set_persistent(cx_problem* p, Launch& L, int threads, int blocks, int per_sm) {
+    const int nseg = (p->d.nx + threads - 1) / threads;
+    const long long work = (long long)nseg * p->d.ny;
+    long long nb = blocks > 0 ? blocks : (long long)p->nsm * per_sm;
+    nb = std::min(nb, work);
+    if (nb < 1) nb = 1;
+    if (nb * (threads / 32) > MAX_WARPS) return CX_ERR_INVALID_ARG;
+    L.block = dim3(threads);
+    L.grid = dim3((unsigned)nb);
+    return CX_OK;
+}
+
+cx_status cx_set_launch(cx_problem* p, int threads, int blocks) {
+    if (!p || (threads != 64 && threads != 128 && threads != 256) || blocks < 0) return CX_ERR_INVALID_ARG;
+    const bool dbl = p->lay.esz == 8;
+    const int of = dbl ? forward_occupancy<double>(p->lay.Q, threads) : forward_occupancy<float>(p->lay.Q, threads);
+    const int oa = dbl ? adjoint_occupancy<double>(p->lay.Q, threads) : adjoint_occupancy<float>(p->lay.Q, threads);
+    Launch f, a;
+    cx_status rc = set_persistent(p, f, threads, blocks, of);
+    if (rc) return rc;
+    rc = set_persistent(p, a, threads, blocks, oa);
+    if (rc) return rc;
+    p->Lf = f;
+    p->La = a;
     return CX_OK;
 }
 
@@ -402,6 +448,9 @@ cx_status cx_create(const cx_problem_desc* desc, void* workspace, size_t bytes, 
     C.aniso = desc->aniso;
     C.adv = desc->adv;
     C.has_solid = desc->solid ? 1 : 0;
+    C.ctrl_full = (desc->ctrl_nx == 0 || (desc->ctrl_x0 == 0 && desc->ctrl_y0 == 0 && desc->ctrl_nx == desc->nx &&
+                                          desc->ctrl_ny == desc->ny)) &&
+                  !desc->ctrl_mask && !desc->solid;
     if (desc->ctrl_nx > 0) {
         C.cx0 = desc->ctrl_x0;
         C.cy0 = desc->ctrl_y0;
@@ -448,8 +497,21 @@ cx_status cx_create(const cx_problem_desc* desc, void* workspace, size_t bytes, 
     C.solid = desc->solid ? reinterpret_cast<uint8_t*>(ws + Ly.off_solid) : nullptr;
     C.cmask = (desc->solid || desc->ctrl_mask) ? reinterpret_cast<uint8_t*>(ws + Ly.off_cmask) : nullptr;
     p->C = C;
-    const int bx = desc->nx >= 128 ? 128 : (desc->nx >= 64 ? 64 : 32);
-    cx_set_launch(p, bx, 256 / bx);
+    p->Kf = make_kconst<float>(C, C.Q);
+    p->Kd = make_kconst<double>(C, C.Q);
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            delete p;
+            return CX_ERR_CUDA;
+        }
+    }
+    set_2d(p);
+    if (cx_set_launch(p, 256, 0) != CX_OK) {
+        delete p;
+        return CX_ERR_INTERNAL;
+    }
     cudaError_t e;
     if (desc->precision == 64)
         e = launch_setup_fields<double>(C, *desc, (double*)C.theta, (double*)C.Kfield, (double*)C.a,

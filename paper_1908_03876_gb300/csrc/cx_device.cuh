@@ -69,6 +69,67 @@ template <> struct Lat<5> {
     static constexpr int JX = 1, JY = 2;
 };
 
+// Moment transforms.  m = M f and its transpose out = M^T r, written for D2Q9
+// with the pair sums/differences of opposite directions (f1 +- f3, f2 +- f4,
+// f5 +- f7, f6 +- f8), which M0's rows are built from; the generic table loop
+// serves D2Q5.
+template <typename T, int Q> struct Transform {
+    __host__ __device__ static inline void moments(const T (&f)[Q], T (&m)[Q]) {
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            T s = T(0);
+#pragma unroll
+            for (int i = 0; i < Q; ++i)
+                if (Lat<Q>::M(k, i) != 0) s += T(Lat<Q>::M(k, i)) * f[i];
+            m[k] = s;
+        }
+    }
+    __host__ __device__ static inline void transpose(const T (&r)[Q], T (&o)[Q]) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            T s = T(0);
+#pragma unroll
+            for (int k = 0; k < Q; ++k)
+                if (Lat<Q>::M(k, i) != 0) s += T(Lat<Q>::M(k, i)) * r[k];
+            o[i] = s;
+        }
+    }
+};
+template <typename T> struct Transform<T, 9> {
+    __host__ __device__ static inline void moments(const T (&f)[9], T (&m)[9]) {
+        const T a = f[1] + f[3], b = f[2] + f[4], c = f[5] + f[7], d = f[6] + f[8];
+        const T ax = f[1] - f[3], by = f[2] - f[4], cd = f[5] - f[7], dd = f[6] - f[8];
+        const T ab = a + b, cs = c + d;
+        m[0] = f[0] + ab + cs;
+        m[1] = T(-4) * f[0] - ab + T(2) * cs;
+        m[2] = T(4) * f[0] - T(2) * ab + cs;
+        const T p = cd - dd, q = cd + dd;
+        m[3] = ax + p;
+        m[4] = T(-2) * ax + p;
+        m[5] = by + q;
+        m[6] = T(-2) * by + q;
+        m[7] = a - b;
+        m[8] = c - d;
+    }
+    __host__ __device__ static inline void transpose(const T (&r)[9], T (&o)[9]) {
+        const T base1 = r[0] - r[1] - T(2) * r[2];
+        const T base2 = r[0] + T(2) * r[1] + r[2];
+        const T A = base1 + r[7], C = base1 - r[7];
+        const T B = r[3] - T(2) * r[4], D = r[5] - T(2) * r[6];
+        const T E = base2 + r[8], G = base2 - r[8];
+        const T F = r[3] + r[4] + r[5] + r[6], H = r[5] + r[6] - r[3] - r[4];
+        o[0] = r[0] - T(4) * r[1] + T(4) * r[2];
+        o[1] = A + B;
+        o[3] = A - B;
+        o[2] = C + D;
+        o[4] = C - D;
+        o[5] = E + F;
+        o[7] = E - F;
+        o[6] = G + H;
+        o[8] = G - H;
+    }
+};
+
 // relaxation rate of non-flux moment k (Pi = diag(s0,s1,s2) + K-block + diag(s4,s5,s6);
 // the q_x rate is s3).  D2Q5: (rho, -, -, e, p_xx) -> (s0, s1, s5).
 template <int Q> __host__ __device__ inline int rate_index(int k);
@@ -87,20 +148,30 @@ template <typename T> struct NodeCoef {
 
 template <typename T> __device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
 
+// sin and cos of 2t: libm in FP64; in FP32 a reduction to [-pi, pi] then the
+// hardware approximations (absolute error about 1e-6, far below the FP32
+// tolerance of the fields).
+__device__ __forceinline__ void sincos2(double t, double* s, double* c) { sincos(2.0 * t, s, c); }
+__device__ __forceinline__ void sincos2(float t, float* s, float* c) {
+    float x = 2.0f * t;
+    x = fmaf(-6.28318530717958647692f, rintf(x * 0.15915494309189533577f), x);
+    __sincosf(x, s, c);
+}
+
+// Node coefficients given the node's angle th (used only for ROTATED tensors).
 template <typename T>
-__device__ __forceinline__ void node_coef(const CxConst& C, int x, int y, int k, NodeCoef<T>& c) {
+__device__ __forceinline__ void node_coef_th(const CxConst& C, const KConst<T>& KC, T th, int y, int k,
+                                             NodeCoef<T>& c) {
     if (C.aniso == CX_ANISO_ROTATED) {
         // K = R diag(k1, k2) R^T = kbar I + kd [[cos 2t, sin 2t], [sin 2t, -cos 2t]]
-        T th = ldg(reinterpret_cast<const T*>(C.theta) + k);
         T s2, c2;
-        if constexpr (sizeof(T) == 4) sincosf(2.0f * th, &s2, &c2);
-        else sincos(2.0 * th, &s2, &c2);
-        c.Ku0 = T(C.ku_bar) + T(C.ku_d) * c2;
-        c.Ku1 = T(C.ku_d) * s2;
-        c.Ku2 = T(C.ku_bar) - T(C.ku_d) * c2;
-        c.Kv0 = T(C.kv_bar) + T(C.kv_d) * c2;
-        c.Kv1 = T(C.kv_d) * s2;
-        c.Kv2 = T(C.kv_bar) - T(C.kv_d) * c2;
+        sincos2(th, &s2, &c2);
+        c.Ku0 = KC.ku_bar + KC.ku_d * c2;
+        c.Ku1 = KC.ku_d * s2;
+        c.Ku2 = KC.ku_bar - KC.ku_d * c2;
+        c.Kv0 = KC.kv_bar + KC.kv_d * c2;
+        c.Kv1 = KC.kv_d * s2;
+        c.Kv2 = KC.kv_bar - KC.kv_d * c2;
     } else if (C.aniso == CX_ANISO_FIELD) {
         const T* K = reinterpret_cast<const T*>(C.Kfield);
         const size_t pl = C.plane;
@@ -111,12 +182,12 @@ __device__ __forceinline__ void node_coef(const CxConst& C, int x, int y, int k,
         c.Kv1 = ldg(K + 4 * pl + k);
         c.Kv2 = ldg(K + 5 * pl + k);
     } else {
-        c.Ku0 = T(C.Ku[0]);
-        c.Ku1 = T(C.Ku[1]);
-        c.Ku2 = T(C.Ku[2]);
-        c.Kv0 = T(C.Kv[0]);
-        c.Kv1 = T(C.Kv[1]);
-        c.Kv2 = T(C.Kv[2]);
+        c.Ku0 = KC.Ku[0];
+        c.Ku1 = KC.Ku[1];
+        c.Ku2 = KC.Ku[2];
+        c.Kv0 = KC.Kv[0];
+        c.Kv1 = KC.Kv[1];
+        c.Kv2 = KC.Kv[2];
     }
     if (C.adv == CX_ADV_ROW) {
         const T* a = reinterpret_cast<const T*>(C.a);
@@ -131,6 +202,13 @@ __device__ __forceinline__ void node_coef(const CxConst& C, int x, int y, int k,
         c.ay = T(0);
     }
 }
+
+template <typename T>
+__device__ __forceinline__ void node_coef(const CxConst& C, const KConst<T>& KC, int x, int y, int k, NodeCoef<T>& c) {
+    const T th = (C.aniso == CX_ANISO_ROTATED) ? ldg(reinterpret_cast<const T*>(C.theta) + k) : T(0);
+    node_coef_th<T>(C, KC, th, y, k, c);
+}
+
 
 // Moments at unit density of the equilibrium phi^eq = w_i aleph_i Theta
 // (eq. phieq with T = a Theta, C = (a a) Theta):
@@ -174,24 +252,39 @@ __device__ __forceinline__ void meq_unit(T ax, T ay, T d, T (&mh)[Q]) {
 // Pi (m - m^eq) for one species: diagonal rates on non-flux moments, the
 // 2x2 block K on (j_x, j_y).
 template <typename T, int Q>
-__device__ __forceinline__ void relax(const CxConst& C, T K0, T K1, T K2, const T (&dm)[Q], T (&out)[Q]) {
+__device__ __forceinline__ void relax(const KConst<T>& KC, T K0, T K1, T K2, const T (&dm)[Q], T (&out)[Q]) {
     using L = Lat<Q>;
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
         const int r = rate_index<Q>(k);
-        if (r >= 0) out[k] = T(C.s[r]) * dm[k];
+        if (r >= 0) out[k] = KC.s[r] * dm[k];
     }
     out[L::JX] = K0 * dm[L::JX] + K1 * dm[L::JY];
     out[L::JY] = K1 * dm[L::JX] + K2 * dm[L::JY];
 }
 
+// N^-1 Pi (m - m^eq) with the 1/|row|^2 factors folded into the rates
+// (sn[k] = s_k / |row_k|^2).  Pi^T N^-1 has the same entries because K is
+// symmetric and both flux rows have the same norm, so the adjoint uses it too.
+template <typename T, int Q>
+__device__ __forceinline__ void relax_n(const KConst<T>& KC, T K0, T K1, T K2, const T (&dm)[Q], T (&out)[Q]) {
+    using L = Lat<Q>;
+#pragma unroll
+    for (int k = 0; k < Q; ++k)
+        if (k != L::JX && k != L::JY) out[k] = KC.sn[k] * dm[k];
+    out[L::JX] = (K0 * dm[L::JX] + K1 * dm[L::JY]) * KC.invn_jx;
+    out[L::JY] = (K1 * dm[L::JX] + K2 * dm[L::JY]) * KC.invn_jy;
+}
+
 // Pi^T lambda (K symmetric, so the block is unchanged; diagonal rates too).
 template <typename T, int Q>
-__device__ __forceinline__ void relax_T(const CxConst& C, T K0, T K1, T K2, const T (&lam)[Q], T (&out)[Q]) {
-    relax<T, Q>(C, K0, K1, K2, lam, out);
+__device__ __forceinline__ void relax_T(const KConst<T>& KC, T K0, T K1, T K2, const T (&lam)[Q], T (&out)[Q]) {
+    relax<T, Q>(KC, K0, K1, K2, lam, out);
 }
 
 // ---------------------------------------------------- deterministic reductions
+// (FP64 variants for the FP64 kernels; the FP32 kernels use the compensated
+// FP32 helpers below.)
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -202,6 +295,57 @@ __device__ __forceinline__ double warp_max(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
+}
+
+// Compensated FP32 arithmetic (an unevaluated pair hi + lo): error-free
+// two-sum (Knuth) and fma two-product give sums of squares with FP64-level
+// accuracy while the FP32 kernels issue no FP64 instruction per node.
+struct CF {
+    float hi, lo;
+};
+__device__ __forceinline__ CF cf_add(CF a, CF b) {
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    const float e = (a.hi - (s - bb)) + (b.hi - bb) + a.lo + b.lo;
+    const float h = s + e;
+    return CF{h, e - (h - s)};
+}
+__device__ __forceinline__ CF cf_sq(float x) {
+    const float p = x * x;
+    return CF{p, fmaf(x, x, -p)};
+}
+
+// Sum of x^2 over the block in a fixed order, as a double in thread 0.
+__device__ __forceinline__ double block_sumsq(float x, double* sh) {
+    CF v = cf_sq(x);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        CF w{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+        v = cf_add(v, w);
+    }
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    const int nthr = blockDim.x * blockDim.y;
+    if ((tid & 31) == 0) sh[tid >> 5] = (double)v.hi + (double)v.lo;
+    __syncthreads();
+    double r = 0.0;
+    if (tid == 0)
+        for (int w = 0; w < (nthr + 31) / 32; ++w) r += sh[w];
+    __syncthreads();
+    return r;
+}
+__device__ __forceinline__ double block_sumsq(double x, double* sh);
+__device__ __forceinline__ float block_maxf(float x, float* sh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = fmaxf(x, __shfl_xor_sync(0xffffffffu, x, o));
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    const int nthr = blockDim.x * blockDim.y;
+    if ((tid & 31) == 0) sh[tid >> 5] = x;
+    __syncthreads();
+    float r = 0.0f;
+    if (tid == 0)
+        for (int w = 0; w < (nthr + 31) / 32; ++w) r = fmaxf(r, sh[w]);
+    __syncthreads();
+    return r;
 }
 
 // Block sum in a fixed order; result valid in thread 0.
@@ -238,5 +382,178 @@ __device__ __forceinline__ int ctrl_window(const CxConst& C, int x, int y) {
 }
 // window entry c is a controlled node (mask set, fluid)
 __device__ __forceinline__ bool ctrl_active(const CxConst& C, int c) { return c >= 0 && (!C.cmask || C.cmask[c]); }
+
+__device__ __forceinline__ double block_sumsq(double x, double* sh) { return block_sum(x * x, sh); }
+
+// Sum of x^2 and max |x| over the block in one pass (thread 0 holds both).
+__device__ __forceinline__ void block_sumsq_max(float x, double* sh, double* sum, double* mx) {
+    CF v = cf_sq(x);
+    float m = fabsf(x);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        CF w{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+        v = cf_add(v, w);
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    }
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    const int nthr = blockDim.x * blockDim.y;
+    if ((tid & 31) == 0) {
+        sh[tid >> 5] = (double)v.hi + (double)v.lo;
+        sh[16 + (tid >> 5)] = (double)m;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double r = 0.0, q = 0.0;
+        for (int w = 0; w < (nthr + 31) / 32; ++w) {
+            r += sh[w];
+            q = fmax(q, sh[16 + w]);
+        }
+        *sum = r;
+        *mx = q;
+    }
+}
+__device__ __forceinline__ void block_sumsq_max(double x, double* sh, double* sum, double* mx) {
+    double v = warp_sum(x * x), m = warp_max(fabs(x));
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    const int nthr = blockDim.x * blockDim.y;
+    if ((tid & 31) == 0) {
+        sh[tid >> 5] = v;
+        sh[16 + (tid >> 5)] = m;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double r = 0.0, q = 0.0;
+        for (int w = 0; w < (nthr + 31) / 32; ++w) {
+            r += sh[w];
+            q = fmax(q, sh[16 + w]);
+        }
+        *sum = r;
+        *mx = q;
+    }
+}
+__device__ __forceinline__ double block_maxd(double x, double* sh) { return block_max(fabs(x), sh); }
+__device__ __forceinline__ double block_maxd(float x, double* sh) {
+    return (double)block_maxf(fabsf(x), reinterpret_cast<float*>(sh));
+}
+
+// ------------------------------------------- programmatic dependent launch
+// The lattice kernels are launched with programmatic stream serialisation: a
+// step's grid may be scheduled while the previous step is finishing; it runs
+// its index set-up, then waits here until the previous grid has completed and
+// its writes are visible.  Launched without the attribute, the wait is a no-op.
+__device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void allow_next_grid() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
+// ------------------------------------------------ asynchronous staging copies
+// 4- or 8-byte cp.async from global to the issuing thread's own shared slots;
+// every thread reads back only what it staged itself, so a wait_group is the
+// only synchronisation the pipelined kernels need.
+template <typename T> __device__ __forceinline__ void cp_async(T* smem, const T* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    if constexpr (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Compensated accumulation of x^2 across the nodes a thread owns, then one
+// warp reduction; lane 0 adds the warp's share to its FP64 slot.
+struct SqAcc {
+    CF s{0.0f, 0.0f};
+    float m = 0.0f;
+    __device__ __forceinline__ void add(float x) {
+        s = cf_add(s, cf_sq(x));
+        m = fmaxf(m, fabsf(x));
+    }
+    __device__ __forceinline__ void flush(double* sum_slot, double* max_slot) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            CF w{__shfl_xor_sync(0xffffffffu, s.hi, o), __shfl_xor_sync(0xffffffffu, s.lo, o)};
+            s = cf_add(s, w);
+            m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            if (sum_slot) *sum_slot += (double)s.hi + (double)s.lo;
+            if (max_slot) *max_slot = fmax(*max_slot, (double)m);
+        }
+    }
+};
+struct SqAccD {
+    double s = 0.0, m = 0.0;
+    __device__ __forceinline__ void add(double x) {
+        s += x * x;
+        m = fmax(m, fabs(x));
+    }
+    __device__ __forceinline__ void flush(double* sum_slot, double* max_slot) {
+        s = warp_sum(s);
+        m = warp_max(m);
+        if ((threadIdx.x & 31) == 0) {
+            if (sum_slot) *sum_slot += s;
+            if (max_slot) *max_slot = fmax(*max_slot, m);
+        }
+    }
+};
+template <typename T> struct SqAccT;
+template <> struct SqAccT<float> { using type = SqAcc; };
+template <> struct SqAccT<double> { using type = SqAccD; };
+
+// Work decomposition of the persistent lattice kernels: a chunk is one row
+// segment of NT consecutive nodes; block b takes chunks b, b + G, b + 2G, ...
+// The (row, segment) pair advances incrementally, so no per-node division.
+struct NodeIdx {
+    int x, y, k, c; // column, row, node index, control index (-1: none)
+    bool fluid;     // inside the grid and not solid
+    bool ctrl;      // controlled node (window & mask & fluid)
+};
+
+template <int NT> struct ChunkIter {
+    int nseg, nch, ch, y, seg, dy, dseg;
+    __device__ __forceinline__ ChunkIter(const CxConst& C) {
+        nseg = (C.nx + NT - 1) / NT;
+        nch = nseg * C.ny;
+        ch = blockIdx.x;
+        y = ch / nseg;
+        seg = ch - y * nseg;
+        dy = gridDim.x / nseg;
+        dseg = gridDim.x - dy * nseg;
+    }
+    __device__ __forceinline__ bool valid() const { return ch < nch; }
+    __device__ __forceinline__ void next() {
+        ch += gridDim.x;
+        seg += dseg;
+        y += dy;
+        if (seg >= nseg) {
+            seg -= nseg;
+            ++y;
+        }
+    }
+    __device__ __forceinline__ NodeIdx node(const CxConst& C) const {
+        NodeIdx r;
+        r.x = seg * NT + (int)threadIdx.x;
+        r.y = y;
+        r.k = r.y * C.nx + r.x;
+        r.fluid = r.x < C.nx && !(C.has_solid && C.solid[r.k]);
+        if (C.ctrl_full) {
+            r.c = r.k;
+        } else {
+            const int cx = r.x - C.cx0, cy = r.y - C.cy0;
+            r.c = (r.x < C.nx && cx >= 0 && cy >= 0 && cx < C.cnx && cy < C.cny) ? cy * C.cnx + cx : -1;
+        }
+        r.ctrl = r.fluid && r.c >= 0 && (!C.cmask || C.cmask[r.c]);
+        if (r.x >= C.nx) r.c = -1;
+        return r;
+    }
+};
+__device__ __forceinline__ NodeIdx no_node() {
+    NodeIdx r;
+    r.x = r.y = r.k = 0;
+    r.c = -1;
+    r.fluid = r.ctrl = false;
+    return r;
+}
 
 } // namespace cx

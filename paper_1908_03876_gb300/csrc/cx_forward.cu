@@ -15,168 +15,219 @@
 //              V = (I - K_v/2) a, kappa_x = 0; c_n = 3 tau/2, c'_n = -tau/2;
 //              c_0 = tau, c'_0 = 0 because Phi^{-1} := Phi^0)
 // The node also writes Phi^n (node-local state for the next step), optionally
-// the adjoint tape (u, G_x, G_y), and adds sum (g^n)^2 to its block's FP64
-// partial of the control penalty.
+// the adjoint tape (u, G_x, G_y), and accumulates (g^n)^2 for the penalty.
+//
+// Execution: a persistent grid; each block walks row segments of blockDim.x
+// nodes.  While a thread computes its current node it has already issued the
+// cp.async copies of its next node's populations and per-node scalars into its
+// own shared-memory slots (two stages), so DRAM latency overlaps the
+// arithmetic without holding registers for loads in flight.
 #include "cx_device.cuh"
 
 namespace cx {
 
-template <typename T, int Q>
-__global__ void __launch_bounds__(256) k_forward(const CxConst C, const FwdArgs<T> A) {
+template <int Q> constexpr int fwd_stage_values() { return 2 * Q + 4; } // pops, theta, g, E, Phi^{n-1}
+
+template <typename T, int Q, int NT>
+__device__ __forceinline__ void fwd_stage(const CxConst& C, const FwdArgs<T>& A, const NodeIdx& nd, T* s) {
     using L = Lat<Q>;
-    __shared__ double red[32];
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    double gsq = 0.0;
-    const bool inside = (x < C.nx) && (y < C.ny);
-    const int k = y * C.nx + x;
-    const bool fluid = inside && !(C.has_solid && C.solid[k]);
-    if (fluid) {
-        const size_t pl = (size_t)C.plane;
-        T fu[Q], fv[Q];
-        if (A.n == 0) {
+    if (!nd.fluid) return;
+    const int x = nd.x, y = nd.y, k = nd.k;
+    if (A.n == 0) {
 #pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                fu[i] = ldg(A.Pin + i * pl + k);
-                fv[i] = ldg(A.Pin + (Q + i) * pl + k);
-            }
-        } else {
-            const int xm = x == 0 ? C.nx - 1 : x - 1, xp = x == C.nx - 1 ? 0 : x + 1;
-            const int ym = y == 0 ? C.ny - 1 : y - 1, yp = y == C.ny - 1 ? 0 : y + 1;
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const int xs = L::ex(i) > 0 ? xm : (L::ex(i) < 0 ? xp : x);
-                const int ys = L::ey(i) > 0 ? ym : (L::ey(i) < 0 ? yp : y);
-                const int ks = ys * C.nx + xs;
-                if (C.has_solid && i != 0 && C.solid[ks]) {
-                    fu[i] = ldg(A.Pin + L::opp(i) * pl + k);
-                    fv[i] = ldg(A.Pin + (Q + L::opp(i)) * pl + k);
-                } else {
-                    fu[i] = ldg(A.Pin + i * pl + ks);
-                    fv[i] = ldg(A.Pin + (Q + i) * pl + ks);
-                }
-            }
-        }
-        NodeCoef<T> nc;
-        node_coef<T>(C, x, y, k, nc);
-
-        // moments m = M f of both species
-        T mu[Q], mv[Q];
-#pragma unroll
-        for (int kk = 0; kk < Q; ++kk) {
-            T su = T(0), sv = T(0);
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                if (L::M(kk, i) == 1) {
-                    su += fu[i];
-                    sv += fv[i];
-                } else if (L::M(kk, i) == -1) {
-                    su -= fu[i];
-                    sv -= fv[i];
-                } else if (L::M(kk, i) != 0) {
-                    su += T(L::M(kk, i)) * fu[i];
-                    sv += T(L::M(kk, i)) * fv[i];
-                }
-            }
-            mu[kk] = su;
-            mv[kk] = sv;
-        }
-        const T Tu = mu[0], Tv = mv[0];
-        const T jvx = mv[L::JX], jvy = mv[L::JY];
-
-        // control and reaction source
-        T g = T(0);
-        const int c = ctrl_window(C, x, y);
-        if (ctrl_active(C, c)) {
-            if (A.g) g = ldg(A.g + c);
-            if (A.E) g = fma(-T(A.lam), ldg(A.E + c), g); // same rounding as the accepted update
-            gsq = (double)g * (double)g;
-        }
-        const T Phi = T(C.r_vu) * Tu + T(C.r_vv) * Tv + g;
-        const T Phi_prev = (A.n == 0) ? Phi : A.phi[k];
-
-        // grad v (reading of C146)
-        const T tau = T(C.tau);
-        const T rx = (jvx - nc.ax * Tv) / tau, ry = (jvy - nc.ay * Tv) / tau;
-        const T Kax = nc.Kv0 * nc.ax + nc.Kv1 * nc.ay, Kay = nc.Kv1 * nc.ax + nc.Kv2 * nc.ay;
-        const T sc = T(-3.0) / T(C.d_v); // -1 / (d_v Cs^2)
-        const T Gx = sc * (nc.Kv0 * rx + nc.Kv1 * ry + T(0.5) * Kax * Phi);
-        const T Gy = sc * (nc.Kv1 * rx + nc.Kv2 * ry + T(0.5) * Kay * Phi);
-
-        // --- species u: MRT collision + chemotactic cross-diffusion source
-        T mh[Q], dm[Q], rl[Q];
-        meq_unit<T, Q>(nc.ax, nc.ay, T(C.d_u), mh);
-#pragma unroll
-        for (int kk = 0; kk < Q; ++kk) dm[kk] = mu[kk] - Tu * mh[kk];
-        relax<T, Q>(C, nc.Ku0, nc.Ku1, nc.Ku2, dm, rl);
-#pragma unroll
-        for (int kk = 0; kk < Q; ++kk) rl[kk] *= T(L::inv_n(kk));
-        // (w_i/Cs^2) chi u e_i.(K_u G) = 3 w_i e_i . F
-        const T Fx = T(C.chi) * Tu * (nc.Ku0 * Gx + nc.Ku1 * Gy);
-        const T Fy = T(C.chi) * Tu * (nc.Ku1 * Gx + nc.Ku2 * Gy);
-        T* Pu = A.Pout;
+        for (int i = 0; i < 2 * Q; ++i) cp_async(s + i * NT, A.pin[i] + k);
+    } else {
+        const int xm = x == 0 ? C.nx - 1 : x - 1, xp = x == C.nx - 1 ? 0 : x + 1;
+        const int rm = (y == 0 ? C.ny - 1 : y - 1) * C.nx, r0 = y * C.nx, rp = (y == C.ny - 1 ? 0 : y + 1) * C.nx;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            T s = T(0);
-#pragma unroll
-            for (int kk = 0; kk < Q; ++kk)
-                if (L::M(kk, i) != 0) s += T(L::M(kk, i)) * rl[kk];
-            const T src = T(3.0 * L::w(i)) * (T(L::ex(i)) * Fx + T(L::ey(i)) * Fy);
-            Pu[i * pl + k] = fu[i] - s + src;
+            const int xs = L::ex(i) > 0 ? xm : (L::ex(i) < 0 ? xp : x);
+            const int ks = (L::ey(i) > 0 ? rm : (L::ey(i) < 0 ? rp : r0)) + xs;
+            if (C.has_solid && i != 0 && C.solid[ks]) {
+                cp_async(s + i * NT, A.pin[L::opp(i)] + k);
+                cp_async(s + (Q + i) * NT, A.pin[Q + L::opp(i)] + k);
+            } else {
+                cp_async(s + i * NT, A.pin[i] + ks);
+                cp_async(s + (Q + i) * NT, A.pin[Q + i] + ks);
+            }
         }
-
-        // --- species v: MRT collision + reaction/control source with the
-        //     tau/2 time-derivative term
-        meq_unit<T, Q>(nc.ax, nc.ay, T(C.d_v), mh);
-#pragma unroll
-        for (int kk = 0; kk < Q; ++kk) dm[kk] = mv[kk] - Tv * mh[kk];
-        relax<T, Q>(C, nc.Kv0, nc.Kv1, nc.Kv2, dm, rl);
-#pragma unroll
-        for (int kk = 0; kk < Q; ++kk) rl[kk] *= T(L::inv_n(kk));
-        const T Vx = nc.ax - T(0.5) * Kax, Vy = nc.ay - T(0.5) * Kay; // V = (I - K_v/2) a
-        T cn, cp;
-        if (C.source_order == 1 || A.n == 0) {
-            cn = tau;
-            cp = T(0);
-        } else {
-            cn = T(1.5) * tau;
-            cp = T(-0.5) * tau;
-        }
-        const T srcv = cn * Phi + cp * Phi_prev;
-        T* Pv = A.Pout + (size_t)Q * pl;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            T s = T(0);
-#pragma unroll
-            for (int kk = 0; kk < Q; ++kk)
-                if (L::M(kk, i) != 0) s += T(L::M(kk, i)) * rl[kk];
-            const T wt = T(L::w(i)) * (T(1) + T(3) * (Vx * T(L::ex(i)) + Vy * T(L::ey(i))));
-            Pv[i * pl + k] = fv[i] - s + wt * srcv;
-        }
-        A.phi[k] = Phi;
-        if (A.phi_ckpt) A.phi_ckpt[k] = Phi;
-        if (A.tape) {
-            A.tape[k] = Tu;
-            A.tape[pl + k] = Gx;
-            A.tape[2 * pl + k] = Gy;
-        }
+        cp_async(s + (2 * Q + 3) * NT, A.phi + k);
     }
-    if (A.gsq_part) {
-        const double b = block_sum(gsq, red);
-        if (threadIdx.x == 0 && threadIdx.y == 0) A.gsq_part[blockIdx.x + gridDim.x * blockIdx.y] += b;
+    if (C.aniso == CX_ANISO_ROTATED) cp_async(s + 2 * Q * NT, reinterpret_cast<const T*>(C.theta) + k);
+    if (nd.ctrl) {
+        if (A.g) cp_async(s + (2 * Q + 1) * NT, A.g + nd.c);
+        if (A.E) cp_async(s + (2 * Q + 2) * NT, A.E + nd.c);
+    }
+}
+
+template <typename T, int Q, int NT>
+__device__ __forceinline__ void fwd_compute(const CxConst& C, const KConst<T>& KC, const FwdArgs<T>& A,
+                                            const NodeIdx& nd, const T* s, typename SqAccT<T>::type& acc) {
+    using L = Lat<Q>;
+    if (!nd.fluid) return;
+    const int y = nd.y, k = nd.k;
+    T fu[Q], fv[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        fu[i] = s[i * NT];
+        fv[i] = s[(Q + i) * NT];
+    }
+    T g = T(0);
+    if (nd.ctrl) {
+        if (A.g) g = s[(2 * Q + 1) * NT];
+        if (A.E) g = fma(-A.lam, s[(2 * Q + 2) * NT], g); // same rounding as the accepted update
+        acc.add(g);
+    }
+    NodeCoef<T> nc;
+    node_coef_th<T>(C, KC, (C.aniso == CX_ANISO_ROTATED) ? s[2 * Q * NT] : T(0), y, k, nc);
+
+    // moments m = M f of both species
+    T mu[Q], mv[Q];
+    Transform<T, Q>::moments(fu, mu);
+    Transform<T, Q>::moments(fv, mv);
+    const T Tu = mu[0], Tv = mv[0];
+    const T jvx = mv[L::JX], jvy = mv[L::JY];
+
+    // reaction and control source
+    const T Phi = KC.r_vu * Tu + KC.r_vv * Tv + g;
+    const T Phi_prev = (A.n == 0) ? Phi : s[(2 * Q + 3) * NT];
+
+    // grad v (reading of C146)
+    const T rx = (jvx - nc.ax * Tv) * KC.inv_tau, ry = (jvy - nc.ay * Tv) * KC.inv_tau;
+    const T Kax = nc.Kv0 * nc.ax + nc.Kv1 * nc.ay, Kay = nc.Kv1 * nc.ax + nc.Kv2 * nc.ay;
+    const T Gx = KC.gsc * (nc.Kv0 * rx + nc.Kv1 * ry + T(0.5) * Kax * Phi);
+    const T Gy = KC.gsc * (nc.Kv1 * rx + nc.Kv2 * ry + T(0.5) * Kay * Phi);
+
+    // --- species u: MRT collision + chemotactic cross-diffusion source
+    T mh[Q], dm[Q], rl[Q], bt[Q];
+    meq_unit<T, Q>(nc.ax, nc.ay, KC.d_u, mh);
+#pragma unroll
+    for (int kk = 0; kk < Q; ++kk) dm[kk] = mu[kk] - Tu * mh[kk];
+    relax_n<T, Q>(KC, nc.Ku0, nc.Ku1, nc.Ku2, dm, rl);
+    // (w_i/Cs^2) chi u e_i.(K_u G) = 3 w_i e_i . F
+    const T Fx = KC.chi * Tu * (nc.Ku0 * Gx + nc.Ku1 * Gy);
+    const T Fy = KC.chi * Tu * (nc.Ku1 * Gx + nc.Ku2 * Gy);
+    Transform<T, Q>::transpose(rl, bt); // M^-1 Pi (m - m^eq) = M^T N^-1 Pi (m - m^eq)
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const T src = T(3.0 * L::w(i)) * (T(L::ex(i)) * Fx + T(L::ey(i)) * Fy);
+        A.pout[i][k] = fu[i] - bt[i] + src;
+    }
+
+    // --- species v: MRT collision + reaction/control source with the tau/2
+    //     time-derivative term
+    meq_unit<T, Q>(nc.ax, nc.ay, KC.d_v, mh);
+#pragma unroll
+    for (int kk = 0; kk < Q; ++kk) dm[kk] = mv[kk] - Tv * mh[kk];
+    relax_n<T, Q>(KC, nc.Kv0, nc.Kv1, nc.Kv2, dm, rl);
+    const T Vx = nc.ax - T(0.5) * Kax, Vy = nc.ay - T(0.5) * Kay; // V = (I - K_v/2) a
+    const T srcv = (A.n == 0) ? KC.c_first * Phi : KC.c_now * Phi + KC.c_prev * Phi_prev;
+    Transform<T, Q>::transpose(rl, bt);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const T wt = T(L::w(i)) * (T(1) + T(3) * (Vx * T(L::ex(i)) + Vy * T(L::ey(i))));
+        A.pout[Q + i][k] = fv[i] - bt[i] + wt * srcv;
+    }
+    A.phi[k] = Phi;
+    if (A.phi_ckpt) A.phi_ckpt[k] = Phi;
+    if (A.tape) {
+        const size_t pl = (size_t)C.plane;
+        A.tape[k] = Tu;
+        A.tape[pl + k] = Gx;
+        A.tape[2 * pl + k] = Gy;
+    }
+}
+
+template <typename T, int Q, int NT>
+__global__ void __launch_bounds__(NT) k_forward(const CxConst C, const KConst<T> KC, const FwdArgs<T> A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int NV = fwd_stage_values<Q>();
+    T* const s0 = reinterpret_cast<T*>(smem_raw) + threadIdx.x;
+    T* const s1 = s0 + NV * NT;
+    typename SqAccT<T>::type acc;
+    ChunkIter<NT> it(C);
+    NodeIdx cur = it.valid() ? it.node(C) : no_node();
+    allow_next_grid();
+    wait_prior_grid(); // the previous step's populations and node state are complete
+    if (it.valid()) fwd_stage<T, Q, NT>(C, A, cur, s0);
+    cp_async_commit();
+    bool odd = false;
+    while (it.valid()) {
+        it.next();
+        const NodeIdx nxt = it.valid() ? it.node(C) : no_node();
+        if (it.valid()) fwd_stage<T, Q, NT>(C, A, nxt, odd ? s0 : s1);
+        cp_async_commit();
+        cp_async_wait<1>(); // this thread's copies for the current node have landed
+        fwd_compute<T, Q, NT>(C, KC, A, cur, odd ? s1 : s0, acc);
+        cur = nxt;
+        odd = !odd;
+    }
+    cp_async_wait<0>();
+    if (A.gsq_part) acc.flush(A.gsq_part + blockIdx.x * (NT >> 5) + (threadIdx.x >> 5), nullptr);
+}
+
+template <typename T, int Q, int NT>
+static cudaError_t launch_qn(const CxConst& C, const KConst<T>& K, const FwdArgs<T>& A, const Launch& L,
+                             cudaStream_t s) {
+    const size_t smem = (size_t)2 * fwd_stage_values<Q>() * NT * sizeof(T);
+    static bool attr_set = false; // the attribute belongs to the function, once per process
+    if (!attr_set) {
+        cudaError_t e =
+            cudaFuncSetAttribute(k_forward<T, Q, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = L.grid;
+    cfg.blockDim = L.block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_forward<T, Q, NT>, C, K, A);
+}
+
+template <typename T, int Q>
+static cudaError_t launch_q(const CxConst& C, const KConst<T>& K, const FwdArgs<T>& A, const Launch& L,
+                            cudaStream_t s) {
+    switch (L.block.x) {
+    case 64: return launch_qn<T, Q, 64>(C, K, A, L, s);
+    case 128: return launch_qn<T, Q, 128>(C, K, A, L, s);
+    case 256: return launch_qn<T, Q, 256>(C, K, A, L, s);
+    default: return cudaErrorInvalidConfiguration;
     }
 }
 
 template <typename T>
-cudaError_t launch_forward(const CxConst& C, const FwdArgs<T>& A, const Launch& L, cudaStream_t s) {
-    if (C.Q == 9)
-        k_forward<T, 9><<<L.grid, L.block, 0, s>>>(C, A);
-    else
-        k_forward<T, 5><<<L.grid, L.block, 0, s>>>(C, A);
-    return cudaGetLastError();
+cudaError_t launch_forward(const CxConst& C, const KConst<T>& K, const FwdArgs<T>& A, const Launch& L,
+                           cudaStream_t s) {
+    return C.Q == 9 ? launch_q<T, 9>(C, K, A, L, s) : launch_q<T, 5>(C, K, A, L, s);
 }
 
-template cudaError_t launch_forward<float>(const CxConst&, const FwdArgs<float>&, const Launch&, cudaStream_t);
-template cudaError_t launch_forward<double>(const CxConst&, const FwdArgs<double>&, const Launch&, cudaStream_t);
+template cudaError_t launch_forward<float>(const CxConst&, const KConst<float>&, const FwdArgs<float>&, const Launch&,
+                                           cudaStream_t);
+template cudaError_t launch_forward<double>(const CxConst&, const KConst<double>&, const FwdArgs<double>&,
+                                            const Launch&, cudaStream_t);
+
+template <typename T, int Q, int NT> static int occ_qn() {
+    cudaFuncSetAttribute(k_forward<T, Q, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    int nb = 0;
+    const size_t smem = (size_t)2 * fwd_stage_values<Q>() * NT * sizeof(T);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_forward<T, Q, NT>, NT, smem) != cudaSuccess) return 1;
+    return nb > 0 ? nb : 1;
+}
+template <typename T, int Q> static int occ_q(int threads) {
+    return threads == 64 ? occ_qn<T, Q, 64>() : (threads == 128 ? occ_qn<T, Q, 128>() : occ_qn<T, Q, 256>());
+}
+
+// resident blocks per SM of the persistent kernel for a block size
+template <typename T> int forward_occupancy(int Q, int threads) {
+    return Q == 9 ? occ_q<T, 9>(threads) : occ_q<T, 5>(threads);
+}
+template int forward_occupancy<float>(int, int);
+template int forward_occupancy<double>(int, int);
 
 } // namespace cx

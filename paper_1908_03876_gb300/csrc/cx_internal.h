@@ -15,6 +15,7 @@ struct CxConst {
     long long plane;      // elements per node plane (nx*ny rounded up to 64)
     int Q, n_steps;
     int aniso, adv, has_solid;
+    int ctrl_full;                    // control window = whole grid, no mask
     int cx0, cy0, cnx, cny;
     int source_order;
     double tau, d_u, d_v, chi, r_vu, r_vv, alpha;
@@ -28,30 +29,46 @@ struct CxConst {
     const uint8_t* cmask;             // [cny*cnx] window & mask & fluid, or null
 };
 
+// The same constants in the kernels' own precision, precomputed on the host
+// so that no FP64 arithmetic or conversion runs per node in FP32 mode.
+template <typename T> struct KConst {
+    T s[7];
+    T sn[9];                 // rate of moment k times 1/|M row k|^2 (0 for the flux moments)
+    T invn_jx, invn_jy;      // 1/|M row| of the two flux moments
+    T chi, r_vu, r_vv, tau, inv_tau;
+    T gsc;                   // -1 / (d_v Cs^2) = -3 / d_v
+    T asc;                   //  1 / (d_v Cs^2) =  3 / d_v
+    T d_u, d_v;
+    T Ku[3], Kv[3];
+    T ku_bar, ku_d, kv_bar, kv_d;
+    T two_alpha;
+    T c_first, c_now, c_prev; // source coefficients: step 0, steps >= 1 (Phi^n, Phi^{n-1})
+};
+
 template <typename T> struct FwdArgs {
-    const T* Pin;        // [2][Q][plane] populations read (pull) or, at n = 0, f^0 read locally
-    T* Pout;             // [2][Q][plane] post-collision populations of step n
+    const T* pin[18];    // plane j of [2][Q][plane] populations read (pull), or f^0 read locally at n = 0
+    T* pout[18];         // plane j of the post-collision populations of step n
     T* phi;              // [plane] Phi^{n-1} in, Phi^n out (node-local, in place)
     T* phi_ckpt;         // [plane] copy of Phi^n when Pout is a checkpoint slot, else null
     const T* g;          // [cny*cnx] control g^n, or null (zero control)
     const T* E;          // [cny*cnx] gradient for trial controls g - lam E, or null
-    double lam;
+    T lam;
     T* tape;             // [3][plane] (u^n, G_x^n, G_y^n) or null
-    double* gsq_part;    // per-block partial of sum (g^n)^2 (accumulated), or null
+    double* gsq_part;    // per-warp partial of sum (g^n)^2 (accumulated over steps), or null
     int n;               // time step index
 };
 
 template <typename T> struct AdjArgs {
-    const T* Rin;        // [2][Q][plane] psi^{n+1}, or null at the terminal step
+    const T* rin[18];    // plane j of psi^{n+1} ([2][Q][plane]); unused at the terminal step
     const T* wu;         // terminal seeds psi^N_u,i = wu(x), psi^N_v,i = wv(x) (terminal step only)
     const T* wv;
-    T* Rout;             // [2][Q][plane] psi^n
+    T* rout[18];         // plane j of psi^n
     const T* tape;       // [3][plane] (u^n, G_x^n, G_y^n)
     T* sigma;            // [plane] sigma^{n+1} in, sigma^n out
     const T* g;          // [cny*cnx] g^n or null
     T* dJdg;             // [cny*cnx] output dJ/dg^n
-    double* e2_part;     // per-block partial of sum E^2 (accumulated)
-    double* emax_part;   // per-block partial of max |E| (accumulated)
+    double* e2_part;     // per-warp partial of sum E^2 (accumulated over steps)
+    double* emax_part;   // per-warp partial of max |E| (accumulated over steps)
     int n;
     int terminal;        // n == N-1: psi^{n+1} is the broadcast seed
 };
@@ -61,18 +78,23 @@ struct Launch {
 };
 
 // kernel launchers (cx_forward.cu / cx_adjoint.cu / cx_misc.cu), one per precision
-template <typename T> cudaError_t launch_forward(const CxConst& C, const FwdArgs<T>& A, const Launch& L, cudaStream_t s);
-template <typename T> cudaError_t launch_adjoint(const CxConst& C, const AdjArgs<T>& A, const Launch& L, cudaStream_t s);
+template <typename T> KConst<T> make_kconst(const CxConst& C, int Q);
+template <typename T>
+cudaError_t launch_forward(const CxConst& C, const KConst<T>& K, const FwdArgs<T>& A, const Launch& L, cudaStream_t s);
+template <typename T>
+cudaError_t launch_adjoint(const CxConst& C, const KConst<T>& K, const AdjArgs<T>& A, const Launch& L, cudaStream_t s);
 template <typename T>
 cudaError_t launch_init(const CxConst& C, const double* u0d, const double* v0d, const T* u0, const T* v0, T* P,
                         const Launch& L, cudaStream_t s);
 template <typename T>
 cudaError_t launch_final(const CxConst& C, const T* Pin, const T* u_tgt, T* uN, T* vN, T* wu, double* cost_part,
                          const Launch& L, cudaStream_t s);
-cudaError_t launch_finalize(const double* part_a, const double* part_b, int nparts, double scale_b, double* out,
+cudaError_t launch_finalize(const double* part_a, int na, const double* part_b, int nb, double scale_b, double* out,
                             int* status, int status_bit, int mode, cudaStream_t s);
+template <typename T> int forward_occupancy(int Q, int threads);
+template <typename T> int adjoint_occupancy(int Q, int threads);
 template <typename T>
-cudaError_t launch_axpy(T* g, const T* E, double lam, size_t n, cudaStream_t s);
+cudaError_t launch_axpy(T* g, const T* E, T lam, size_t n, cudaStream_t s);
 template <typename T>
 cudaError_t launch_convert(const double* in, T* out, size_t n, cudaStream_t s);
 template <typename T>

@@ -6,10 +6,13 @@
 
 namespace cx {
 
+template <typename T> KConst<T> make_kconst(const CxConst& C, int Q);
+
 // f^0 = phi^eq(Theta_0) for both species (eq. phieq; the initial condition of
 // the forward solve).  Reads FP64 (u0d) or T (u0) initial fields.
 template <typename T, int Q>
-__global__ void k_init(const CxConst C, const double* u0d, const double* v0d, const T* u0, const T* v0, T* P) {
+__global__ void k_init(const CxConst C, const KConst<T> KC, const double* u0d, const double* v0d, const T* u0,
+                       const T* v0, T* P) {
     using L = Lat<Q>;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -18,7 +21,7 @@ __global__ void k_init(const CxConst C, const double* u0d, const double* v0d, co
     const size_t pl = (size_t)C.plane;
     const bool solid = C.has_solid && C.solid[k];
     NodeCoef<T> nc;
-    node_coef<T>(C, x, y, k, nc);
+    node_coef<T>(C, KC, x, y, k, nc);
     const T Tu = solid ? T(0) : (u0d ? T(u0d[k]) : u0[k]);
     const T Tv = solid ? T(0) : (v0d ? T(v0d[k]) : v0[k]);
     const T a2 = nc.ax * nc.ax + nc.ay * nc.ay;
@@ -37,10 +40,11 @@ __global__ void k_init(const CxConst C, const double* u0d, const double* v0d, co
 template <typename T>
 cudaError_t launch_init(const CxConst& C, const double* u0d, const double* v0d, const T* u0, const T* v0, T* P,
                         const Launch& L, cudaStream_t s) {
+    const KConst<T> K = make_kconst<T>(C, C.Q);
     if (C.Q == 9)
-        k_init<T, 9><<<L.grid, L.block, 0, s>>>(C, u0d, v0d, u0, v0, P);
+        k_init<T, 9><<<L.grid, L.block, 0, s>>>(C, K, u0d, v0d, u0, v0, P);
     else
-        k_init<T, 5><<<L.grid, L.block, 0, s>>>(C, u0d, v0d, u0, v0, P);
+        k_init<T, 5><<<L.grid, L.block, 0, s>>>(C, K, u0d, v0d, u0, v0, P);
     return cudaGetLastError();
 }
 
@@ -100,15 +104,14 @@ cudaError_t launch_final(const CxConst& C, const T* Pin, const T* u_tgt, T* uN, 
 // mode 0: out = sum(a) + scale_b * sum(b)          (cost J)
 // mode 1: out[0] = sum(a), out[1] = max(b)         (gradient norms)
 // A non-finite result sets status_bit in *status.
-__global__ void __launch_bounds__(256) k_finalize(const double* a, const double* b, int n, double scale_b,
+__global__ void __launch_bounds__(256) k_finalize(const double* a, int na, const double* b, int nb, double scale_b,
                                                    double* out, int* status, int status_bit, int mode) {
     __shared__ double sa[256], sb[256];
     const int t = threadIdx.x;
     double ra = 0.0, rb = 0.0;
-    for (int i = t; i < n; i += 256) {
-        ra += a[i];
-        if (b) rb = (mode == 1) ? fmax(rb, b[i]) : rb + b[i];
-    }
+    for (int i = t; i < na; i += 256) ra += a[i];
+    if (b)
+        for (int i = t; i < nb; i += 256) rb = (mode == 1) ? fmax(rb, b[i]) : rb + b[i];
     sa[t] = ra;
     sb[t] = rb;
     __syncthreads();
@@ -132,19 +135,19 @@ __global__ void __launch_bounds__(256) k_finalize(const double* a, const double*
     }
 }
 
-cudaError_t launch_finalize(const double* a, const double* b, int n, double scale_b, double* out, int* status,
-                            int status_bit, int mode, cudaStream_t s) {
-    k_finalize<<<1, 256, 0, s>>>(a, b, n, scale_b, out, status, status_bit, mode);
+cudaError_t launch_finalize(const double* a, int na, const double* b, int nb, double scale_b, double* out,
+                            int* status, int status_bit, int mode, cudaStream_t s) {
+    k_finalize<<<1, 256, 0, s>>>(a, na, b, nb, scale_b, out, status, status_bit, mode);
     return cudaGetLastError();
 }
 
 // g <- g - lam E (accepted Armijo step)
-template <typename T> __global__ void k_axpy(T* g, const T* E, double lam, size_t n) {
+template <typename T> __global__ void k_axpy(T* g, const T* E, T lam, size_t n) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        g[i] = fma(-T(lam), E[i], g[i]); // bit-identical to the trial control of the forward
+        g[i] = fma(-lam, E[i], g[i]); // bit-identical to the trial control of the forward
 }
 
-template <typename T> cudaError_t launch_axpy(T* g, const T* E, double lam, size_t n, cudaStream_t s) {
+template <typename T> cudaError_t launch_axpy(T* g, const T* E, T lam, size_t n, cudaStream_t s) {
     int blocks = (int)((n + 255) / 256);
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) blocks = 1;
@@ -221,12 +224,58 @@ cudaError_t launch_setup_fields(const CxConst& C, const cx_problem_desc& d, T* t
     return cudaGetLastError();
 }
 
+template <int Q> static void fold_rates(const CxConst& C, double* sn, double* jx, double* jy) {
+    for (int k = 0; k < Q; ++k) {
+        const int r = rate_index<Q>(k);
+        sn[k] = r >= 0 ? C.s[r] * Lat<Q>::inv_n(k) : 0.0;
+    }
+    *jx = Lat<Q>::inv_n(Lat<Q>::JX);
+    *jy = Lat<Q>::inv_n(Lat<Q>::JY);
+}
+
+template <typename T> KConst<T> make_kconst(const CxConst& C, int Q) {
+    KConst<T> K{};
+    for (int i = 0; i < 7; ++i) K.s[i] = T(C.s[i]);
+    double sn[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, jx = 0.0, jy = 0.0;
+    if (Q == 9)
+        fold_rates<9>(C, sn, &jx, &jy);
+    else
+        fold_rates<5>(C, sn, &jx, &jy);
+    for (int k = 0; k < 9; ++k) K.sn[k] = T(sn[k]);
+    K.invn_jx = T(jx);
+    K.invn_jy = T(jy);
+    K.chi = T(C.chi);
+    K.r_vu = T(C.r_vu);
+    K.r_vv = T(C.r_vv);
+    K.tau = T(C.tau);
+    K.inv_tau = T(1.0 / C.tau);
+    K.gsc = T(-3.0 / C.d_v);
+    K.asc = T(3.0 / C.d_v);
+    K.d_u = T(C.d_u);
+    K.d_v = T(C.d_v);
+    for (int i = 0; i < 3; ++i) {
+        K.Ku[i] = T(C.Ku[i]);
+        K.Kv[i] = T(C.Kv[i]);
+    }
+    K.ku_bar = T(C.ku_bar);
+    K.ku_d = T(C.ku_d);
+    K.kv_bar = T(C.kv_bar);
+    K.kv_d = T(C.kv_d);
+    K.two_alpha = T(2.0 * C.alpha);
+    // tau Phi^n + (tau/2)(Phi^n - Phi^{n-1}); Phi^{-1} := Phi^0 at step 0
+    K.c_first = T(C.tau);
+    K.c_now = C.source_order == 1 ? T(C.tau) : T(1.5 * C.tau);
+    K.c_prev = C.source_order == 1 ? T(0) : T(-0.5 * C.tau);
+    return K;
+}
+
 #define CX_INST(T)                                                                                                   \
+    template KConst<T> make_kconst<T>(const CxConst&, int);                                                               \
     template cudaError_t launch_init<T>(const CxConst&, const double*, const double*, const T*, const T*, T*,        \
                                         const Launch&, cudaStream_t);                                                 \
     template cudaError_t launch_final<T>(const CxConst&, const T*, const T*, T*, T*, T*, double*, const Launch&,      \
                                          cudaStream_t);                                                               \
-    template cudaError_t launch_axpy<T>(T*, const T*, double, size_t, cudaStream_t);                                 \
+    template cudaError_t launch_axpy<T>(T*, const T*, T, size_t, cudaStream_t);                                 \
     template cudaError_t launch_convert<T>(const double*, T*, size_t, cudaStream_t);                                 \
     template cudaError_t launch_setup_fields<T>(const CxConst&, const cx_problem_desc&, T*, T*, T*, T*, uint8_t*,    \
                                                 uint8_t*, cudaStream_t);
