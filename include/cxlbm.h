@@ -184,6 +184,43 @@ cx_status cx_set_launch(cx_problem* p, int threads, int blocks);
 cx_status cx_set_timing(cx_problem* p, int enable);
 cx_status cx_get_timing(cx_problem* p, double* ms, long long* launches);
 
+/* ------------------------------------------------------------------------
+ * Forward solve without any device allocation.  (No counterpart in the paper:
+ * this is a deployment variant of cx_forward.)
+ *
+ * For callers that cannot call cudaMalloc or hand the library a workspace --
+ * code running inside a host callback or a plug-in of another runtime, a
+ * process whose device memory is reserved up front by a pool it does not
+ * control, or code that must not touch the allocator while another library
+ * holds it.  The call computes what cx_create + cx_set_initial + cx_forward +
+ * cx_get_fields compute for the same descriptor (same kernels and launch
+ * shapes), with every scratch buffer placed in one file-scope __device__
+ * array of CX_STATIC_SCRATCH_BYTES that each GPU loading the library holds
+ * until the process exits.  It calls no cudaMalloc, cudaFree or allocating
+ * library routine.
+ *
+ *   desc     as for cx_create; its device arrays, like u0, v0 and g, are read
+ *            by work queued on `stream` and must stay valid until it completes
+ *   u0, v0   device T [ny][nx] initial fields
+ *   g        device T [N][ctrl_ny][ctrl_nx] control, or NULL (zero control)
+ *   J_dev    device double: the cost J (may be NULL)
+ *   uN, vN   device T [ny][nx]: u^N, v^N (either may be NULL)
+ *   stream   the stream every operation is ordered on; asynchronous
+ *
+ * Limits and sharing: problems whose scratch (three population lattices,
+ * six node fields and the reduction slots; about 2 * (6 Q + 8) * sizeof(T)
+ * bytes per node) exceeds CX_STATIC_SCRATCH_BYTES are rejected with
+ * CX_ERR_WORKSPACE.  Every call uses the same array and leaves its contents
+ * there; the call clears what it accumulates into, but two calls that overlap
+ * on the GPU (different streams or host threads) race on the array.  The
+ * first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.
+ * Errors: CX_ERR_INVALID_ARG, CX_ERR_WORKSPACE (too large), CX_ERR_CUDA. */
+#define CX_STATIC_SCRATCH_BYTES (32u << 20)
+cx_status cx_forward_static(const cx_problem_desc* desc, const void* u0, const void* v0, const void* g,
+                            double* J_dev, void* uN, void* vN, cudaStream_t stream);
+
 /* Release the host object (the workspace stays the caller's). */
 cx_status cx_destroy(cx_problem* p);
 

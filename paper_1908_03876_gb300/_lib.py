@@ -22,8 +22,9 @@ STATUS = {
 EXPORTS = [
     "cx_workspace_size", "cx_create", "cx_set_initial", "cx_forward", "cx_adjoint", "cx_gradient", "cx_step",
     "cx_get_fields", "cx_get_psi0", "cx_get_norms", "cx_set_launch", "cx_set_timing", "cx_get_timing",
-    "cx_destroy", "cx_status_string",
+    "cx_destroy", "cx_status_string", "cx_forward_static",
 ]
+STATIC_SCRATCH_BYTES = 32 << 20  # CX_STATIC_SCRATCH_BYTES of include/cxlbm.h
 
 
 class CxError(RuntimeError):
@@ -87,6 +88,7 @@ def load():
         "cx_set_timing": [vp, cint],
         "cx_get_timing": [vp, dp, ctypes.POINTER(ctypes.c_longlong)],
         "cx_destroy": [vp],
+        "cx_forward_static": [D, vp, vp, vp, vp, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)

@@ -79,6 +79,7 @@ class Problem:
         d.s = (ctypes.c_double * 7)(*w.s)
         d.source_order = w.source_order
         self.desc = d
+        self._desc_arrays = keep  # the descriptor's device arrays stay valid with the Problem
         nbytes = ctypes.c_size_t(0)
         _lib.check(self.lib.cx_workspace_size(ctypes.byref(d), ctypes.byref(nbytes)), "cx_workspace_size")
         self.workspace_bytes = nbytes.value
