@@ -92,6 +92,21 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def _traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    from the kernel sources as they are now; else None."""
+    try:
+        from paper_1908_03876_gb300.kernel_hash import kernel_source_hash
+
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            tr = json.load(fh)
+        if tr.get("kernel_source_hash") != kernel_source_hash() or kernel not in tr:
+            return None
+        return tr[kernel]["dram_bytes_per_launch"]
+    except Exception:
+        return None
+
+
 def cpu_baseline(nsteps=8):
     """The FP64 CPU oracle, as it stands, on a bounded sample of the workload:
     the full 1024x1024 lattice for `nsteps` time steps, forward + adjoint."""
@@ -238,8 +253,8 @@ def main():
     dom = max(roof, key=lambda k: roof[k]["ms_total"]) if roof else "forward"
     kern = {"forward": "k_forward", "recompute": "k_forward (tape)", "adjoint": "k_adjoint"}[dom]
     roofline = {"bound": "hbm", "achieved": roof[dom]["achieved"], "peak": hbm, "unit": "GB/s",
-                "frac": roof[dom]["frac"], "traffic": None, "kernel": kern, "peak_source": peak_kind,
-                "bytes_per_launch": BYTES[dom] * nodes}
+                "frac": roof[dom]["frac"], "traffic": _traffic(kern.split()[0]), "kernel": kern,
+                "peak_source": peak_kind, "bytes_per_launch": BYTES[dom] * nodes}
 
     # ---- end to end: host control in, host gradient and cost out, every step
     e2e = None

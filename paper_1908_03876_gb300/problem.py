@@ -89,6 +89,7 @@ class Problem:
         _lib.check(self.lib.cx_create(ctypes.byref(d), _ptr(self.ws), nbytes.value,
                                       ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)), "cx_create")
         self.h = h
+        self.generation = 0  # counts forward solves (the checkpoints belong to the latest one)
         self._J = torch.zeros(1, dtype=torch.float64, device=dev)
         self.set_initial(w.u0, w.v0)
 
@@ -120,6 +121,7 @@ class Problem:
         g = self._t(g, self.ctrl_shape)
         _lib.check(self.lib.cx_forward(self.h, _ptr(g), _ptr(self._J)), "cx_forward")
         self._g_fwd = g
+        self.generation += 1
         return self._J
 
     def adjoint(self, g=None, seed_u=None, seed_v=None, out=None):
@@ -129,12 +131,14 @@ class Problem:
         sv = self._t(seed_v, (self.w.ny, self.w.nx))
         out = out if out is not None else torch.empty(self.ctrl_shape, dtype=self.dtype, device=self.device)
         _lib.check(self.lib.cx_adjoint(self.h, _ptr(g), _ptr(su), _ptr(sv), _ptr(out)), "cx_adjoint")
+        self._keep_adj = (g, su, sv)  # inputs stay alive until the queued work has read them
         return out
 
     def gradient(self, g=None, out=None):
         g = self._t(g, self.ctrl_shape)
         out = out if out is not None else torch.empty(self.ctrl_shape, dtype=self.dtype, device=self.device)
         _lib.check(self.lib.cx_gradient(self.h, _ptr(g), _ptr(out), _ptr(self._J)), "cx_gradient")
+        self.generation += 1
         return self._J, out
 
     def step(self, g, E=None):
@@ -145,6 +149,7 @@ class Problem:
         E = E if E is not None else torch.empty_like(g)
         info = _lib.StepInfo()
         _lib.check(self.lib.cx_step(self.h, _ptr(g), _ptr(E), ctypes.byref(info)), "cx_step")
+        self.generation += 1
         return dict(J0=info.J0, J=info.J, lam=info.lam, grad_sq=info.grad_sq, grad_inf=info.grad_inf,
                     trials=info.trials)
 
