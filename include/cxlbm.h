@@ -185,6 +185,45 @@ cx_status cx_set_timing(cx_problem* p, int enable);
 cx_status cx_get_timing(cx_problem* p, double* ms, long long* launches);
 
 /* ------------------------------------------------------------------------
+ * Batched problems: `count` independent problems (uneven sizes, tensors,
+ * chemotaxis, masks, controls) that share n_steps, ckpt_every, lattice and
+ * precision.  Every time step of every problem runs in one persistent launch
+ * (tiles of all problems in one work list); the launch sequence of a forward
+ * or gradient evaluation is captured once as a CUDA graph and replayed until
+ * the bindings or tile shapes change.  Per node the arithmetic is that of
+ * cx_forward / cx_adjoint (same formulas; results agree to rounding), and
+ * replays of the captured graph are bitwise reproducible.
+ *   descs            host array of `count` descriptors (as for cx_create)
+ *   workspace        device, cx_batch_workspace_size bytes, 256-byte aligned
+ *   stream           must not be the legacy default stream (graph capture)
+ * Errors: CX_ERR_INVALID_ARG (mismatched n_steps/ckpt_every/lattice/precision,
+ * count outside 1..4096), CX_ERR_WORKSPACE, CX_ERR_CUDA. */
+typedef struct cx_batch cx_batch;
+cx_status cx_batch_workspace_size(const cx_problem_desc* descs, int count, size_t* bytes);
+cx_status cx_batch_create(const cx_problem_desc* descs, int count, void* workspace, size_t bytes,
+                          cudaStream_t stream, cx_batch** out);
+/* u0[i], v0[i]: device T [ny_i][nx_i] (host arrays of device pointers). */
+cx_status cx_batch_set_initial(cx_batch* b, const void* const* u0, const void* const* v0);
+/* Controls g[i] (device T [N][ctrl], NULL entries: zero control) and gradient
+ * outputs dJdg[i] (device T, may be NULL for forward-only use); host arrays.
+ * Synchronous (uploads the problem table). */
+cx_status cx_batch_bind(cx_batch* b, const void* const* g, void* const* dJdg);
+/* Tile shapes: `threads` per block (128 or 256), `blocks` persistent blocks
+ * (0: every SM at full residency), tile_x[i] = tile width of problem i (a
+ * divisor of threads, >= 32, threads / tile_x[i] <= 8; NULL: threads).  The
+ * tile height is threads / tile_x[i].  Synchronous. */
+cx_status cx_batch_set_tiles(cx_batch* b, int threads, int blocks, const int* tile_x);
+/* Forward of every problem; J_dev (device double [count], may be NULL). */
+cx_status cx_batch_forward(cx_batch* b, double* J_dev);
+/* Forward + recompute + AMRT adjoint of every problem into the bound dJdg;
+ * out_dev (device double [3 count], may be NULL): J, ||dJ/dg||^2, max |dJ/dg|. */
+cx_status cx_batch_gradient(cx_batch* b, double* out_dev);
+cx_status cx_batch_get_fields(cx_batch* b, int i, void* u_out, void* v_out);
+/* Synchronising: CX_ERR_UNSTABLE if any problem's J or gradient was non-finite. */
+cx_status cx_batch_get_status(cx_batch* b);
+cx_status cx_batch_destroy(cx_batch* b);
+
+/* ------------------------------------------------------------------------
  * Forward solve without any device allocation.  (No counterpart in the paper:
  * this is a deployment variant of cx_forward.)
  *

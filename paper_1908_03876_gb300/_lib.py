@@ -23,6 +23,8 @@ EXPORTS = [
     "cx_workspace_size", "cx_create", "cx_set_initial", "cx_forward", "cx_adjoint", "cx_gradient", "cx_step",
     "cx_get_fields", "cx_get_psi0", "cx_get_norms", "cx_set_launch", "cx_set_timing", "cx_get_timing",
     "cx_destroy", "cx_status_string", "cx_forward_static",
+    "cx_batch_workspace_size", "cx_batch_create", "cx_batch_set_initial", "cx_batch_bind", "cx_batch_set_tiles",
+    "cx_batch_forward", "cx_batch_gradient", "cx_batch_get_fields", "cx_batch_get_status", "cx_batch_destroy",
 ]
 STATIC_SCRATCH_BYTES = 32 << 20  # CX_STATIC_SCRATCH_BYTES of include/cxlbm.h
 
@@ -89,6 +91,16 @@ def load():
         "cx_get_timing": [vp, dp, ctypes.POINTER(ctypes.c_longlong)],
         "cx_destroy": [vp],
         "cx_forward_static": [D, vp, vp, vp, vp, vp, vp, vp],
+        "cx_batch_workspace_size": [D, cint, ctypes.POINTER(ctypes.c_size_t)],
+        "cx_batch_create": [D, cint, vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)],
+        "cx_batch_set_initial": [vp, vp, vp],
+        "cx_batch_bind": [vp, vp, vp],
+        "cx_batch_set_tiles": [vp, cint, cint, vp],
+        "cx_batch_forward": [vp, vp],
+        "cx_batch_gradient": [vp, vp],
+        "cx_batch_get_fields": [vp, cint, vp, vp],
+        "cx_batch_get_status": [vp],
+        "cx_batch_destroy": [vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)

@@ -1,0 +1,122 @@
+"""Many independent control problems advanced together on one GPU.
+
+Thin binding over the cx_batch_* calls of include/cxlbm.h: one persistent
+launch per time step covers every problem's tiles, and the launch sequence of
+a forward or gradient evaluation is a captured CUDA graph replayed on each
+call.  PyTorch provides the memory and a (non-default) stream.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from .problem import _ptr, make_desc
+
+
+def _vp_array(ts):
+    arr = (ctypes.c_void_p * len(ts))()
+    for i, t in enumerate(ts):
+        arr[i] = None if t is None else t.data_ptr()
+    return arr
+
+
+class Batch:
+    def __init__(self, workloads, device="cuda", stream: torch.cuda.Stream | None = None):
+        self.lib = _lib.load()
+        self.ws_list = list(workloads)
+        w0 = self.ws_list[0]
+        self.count = len(self.ws_list)
+        self.device = torch.device(device)
+        if self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        self.precision = w0.precision
+        self.dtype = torch.float64 if self.precision == 64 else torch.float32
+        # graph capture needs a stream other than the legacy default stream
+        self.stream = stream or torch.cuda.Stream(self.device)
+        descs = (_lib.Desc * self.count)()
+        self._keep = []
+        for i, w in enumerate(self.ws_list):
+            d, keep = make_desc(w, self.device, self.precision)
+            descs[i] = d
+            self._keep.append(keep)
+        self.descs = descs
+        nbytes = ctypes.c_size_t(0)
+        _lib.check(self.lib.cx_batch_workspace_size(descs, self.count, ctypes.byref(nbytes)), "cx_batch_workspace_size")
+        self.workspace_bytes = nbytes.value
+        self.ws = torch.empty(nbytes.value, dtype=torch.uint8, device=self.device)
+        h = ctypes.c_void_p()
+        _lib.check(self.lib.cx_batch_create(descs, self.count, _ptr(self.ws), nbytes.value,
+                                            ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)),
+                   "cx_batch_create")
+        self.h = h
+        self._keep = None  # cx_batch_create synchronised: the descriptor arrays were read
+        u0 = [torch.as_tensor(w.u0, dtype=self.dtype, device=self.device).contiguous() for w in self.ws_list]
+        v0 = [torch.as_tensor(w.v0, dtype=self.dtype, device=self.device).contiguous() for w in self.ws_list]
+        _lib.check(self.lib.cx_batch_set_initial(self.h, _vp_array(u0), _vp_array(v0)), "cx_batch_set_initial")
+        self.stream.synchronize()
+        self.out = torch.zeros(3 * self.count, dtype=torch.float64, device=self.device)
+        self.g = None
+        self.E = None
+
+    def zeros_controls(self):
+        return [torch.zeros(w.ctrl_shape, dtype=self.dtype, device=self.device) for w in self.ws_list]
+
+    def bind(self, g, E=None):
+        """Controls g[i] and gradient outputs E[i] (lists of device tensors)."""
+        self.g = [None if x is None else x.contiguous() for x in g]
+        self.E = E if E is not None else [torch.empty(w.ctrl_shape, dtype=self.dtype, device=self.device)
+                                         for w in self.ws_list]
+        torch.cuda.synchronize(self.device)
+        _lib.check(self.lib.cx_batch_bind(self.h, _vp_array(self.g), _vp_array(self.E)), "cx_batch_bind")
+
+    def set_tiles(self, threads=256, blocks=0, tile_x=None):
+        arr = None if tile_x is None else (ctypes.c_int * self.count)(*tile_x)
+        _lib.check(self.lib.cx_batch_set_tiles(self.h, threads, blocks, arr), "cx_batch_set_tiles")
+
+    def _enter(self):
+        # inputs written on the caller's stream are visible to the batch's stream
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+
+    def _leave(self):
+        # results are visible to work the caller queues next on its stream
+        torch.cuda.current_stream(self.device).wait_stream(self.stream)
+
+    def forward(self):
+        """J of every problem (device FP64 [count])."""
+        self._enter()
+        _lib.check(self.lib.cx_batch_forward(self.h, _ptr(self.out)), "cx_batch_forward")
+        self._leave()
+        return self.out[: self.count]
+
+    def gradient(self):
+        """(J, ||dJ/dg||^2, max |dJ/dg|) per problem; gradients land in self.E."""
+        self._enter()
+        _lib.check(self.lib.cx_batch_gradient(self.h, _ptr(self.out)), "cx_batch_gradient")
+        self._leave()
+        return self.out[: self.count], self.out[self.count: 2 * self.count], self.out[2 * self.count:]
+
+    def fields(self, i):
+        w = self.ws_list[i]
+        u = torch.empty((w.ny, w.nx), dtype=self.dtype, device=self.device)
+        v = torch.empty_like(u)
+        self._enter()
+        _lib.check(self.lib.cx_batch_get_fields(self.h, i, _ptr(u), _ptr(v)), "cx_batch_get_fields")
+        self._leave()
+        return u, v
+
+    def status(self):
+        _lib.check(self.lib.cx_batch_get_status(self.h), "cx_batch_get_status")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.cx_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

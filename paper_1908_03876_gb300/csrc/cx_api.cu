@@ -20,66 +20,9 @@
 #include <new>
 #include <vector>
 
-#include "cx_internal.h"
+#include "cx_state.h"
 
 using namespace cx;
-
-namespace {
-
-constexpr size_t ALIGN = 256;
-constexpr int MAX_WARPS = 32768; // warps of a persistent launch (partial-sum slots)
-inline size_t up(size_t v, size_t a) { return (v + a - 1) / a * a; }
-
-enum { PH_FWD = 0, PH_REC = 1, PH_ADJ = 2, PH_OTHER = 3 };
-enum { ST_UNSTABLE = 1 };
-
-struct Layout {
-    size_t plane, nctrl, esz;
-    int Q, N, k, S, nparts;
-    size_t off_popA, off_popB, off_adjA, off_adjB, off_ckpt, off_ckpt_phi, off_phi, off_sigma, off_tape;
-    size_t off_uN, off_vN, off_wu, off_theta, off_K, off_a, off_ut, off_solid, off_cmask, off_part, off_scal,
-        off_status, total;
-};
-
-struct TimedRange {
-    int phase;
-    long long launches;
-    cudaEvent_t a, b;
-};
-
-} // namespace
-
-struct cx_problem {
-    cx_problem_desc d;
-    CxConst C;
-    Layout lay;
-    cudaStream_t stream;
-    char* ws;
-    KConst<float> Kf;
-    KConst<double> Kd;
-    const KConst<float>& kc(float*) const { return Kf; }
-    const KConst<double>& kc(double*) const { return Kd; }
-    Launch L;      // 2D launch of the set-up, initial and final kernels
-    Launch Lf, La; // persistent launches of the forward and adjoint kernels
-    int nblocks;   // blocks of L
-    int nsm = 1;
-    bool has_init = false, fwd_valid = false, adj_valid = false;
-    bool tape_last_valid = false; // tape holds the last segment (written by the forward)
-    bool have_lam = false;
-    double lam_prev = 0.0;
-    void* psi0 = nullptr;
-    bool timing = false;
-    std::vector<TimedRange> ranges;
-    size_t n_ranges = 0;
-    double ms[4] = {0, 0, 0, 0};
-    long long launches[4] = {0, 0, 0, 0};
-
-    template <typename P> P* at(size_t off) const { return reinterpret_cast<P*>(ws + off); }
-    size_t pop_bytes() const { return (size_t)2 * lay.Q * lay.plane * lay.esz; }
-    char* ckpt_slot(int s) const { return ws + lay.off_ckpt + (size_t)s * pop_bytes(); }
-    char* ckpt_phi_slot(int s) const { return ws + lay.off_ckpt_phi + (size_t)s * lay.plane * lay.esz; }
-    char* tape_slot(int j) const { return ws + lay.off_tape + (size_t)j * 3 * lay.plane * lay.esz; }
-};
 
 // ------------------------------------------------------------ validation
 
@@ -110,7 +53,7 @@ static cx_status validate(const cx_problem_desc* d) {
     return CX_OK;
 }
 
-static Layout make_layout(const cx_problem_desc* d) {
+Layout cx::make_layout(const cx_problem_desc* d) {
     Layout L{};
     L.esz = d->precision == 64 ? 8 : 4;
     L.Q = d->lattice;

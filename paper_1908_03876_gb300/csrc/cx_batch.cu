@@ -1,0 +1,740 @@
+// cx_batch.cu -- many independent problems advanced together: one persistent
+// launch per time step covers every problem's tiles, and the whole sequence
+// of a gradient evaluation (forward, recompute, AMRT adjoint, reductions) is
+// captured once as a CUDA graph and replayed.
+//
+// Problems share N, the checkpoint interval k, the lattice and the precision;
+// sizes, tensors, chemotaxis, masks and controls differ.  Each problem keeps
+// its own cx_problem workspace inside the batch workspace (same layout and
+// set-up as a single problem); the batch adds a device table of per-problem
+// records, the tile prefix array and per-tile FP64 reduction slots.
+//
+// Work decomposition: problem p is cut into tiles of TX_p x (NT / TX_p) nodes
+// (TX_p per problem, chosen by the autotuner); tiles of all problems form one
+// list; block b of the persistent grid takes tiles b, b + G, ...; the tile's
+// problem is found by binary search in the prefix array held in shared
+// memory.  Per node the arithmetic is the single-problem kernels' (the same
+// stage/compute bodies); reductions go to one slot per (tile, warp), summed
+// per problem in a fixed order, so replays are bitwise reproducible.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "cx_adj_body.cuh"
+#include "cx_fwd_body.cuh"
+#include "cx_state.h"
+
+namespace cx {
+
+enum { ROLE_POPA = 0, ROLE_POPB = 1, ROLE_CKPT = 2, ROLE_ADJA = 3, ROLE_ADJB = 4 };
+
+template <typename T> struct BRec {
+    CxConst C;
+    KConst<T> K;
+    T* pop[5];       // base of popA, popB, checkpoint 0, adjA, adjB ([2][Q][plane] each)
+    T* ckpt_phi;     // [S][plane]
+    T* phi;
+    T* sigma;
+    T* tape;         // [k][3][plane]
+    T* wu;
+    const T* g;      // [N][nctrl] or null
+    T* dJdg;         // [N][nctrl] or null
+    long long plane, nctrl, pop_elems;
+    int tile0;       // first global tile of this problem
+    int tx, ty;      // tile shape (tx * ty = NT)
+    int tiles_x;
+    int slot0;       // first reduction slot
+};
+
+struct BStep {
+    int n;
+    int in_role, in_slot;
+    int out_role, out_slot;
+    int phi_ckpt_slot; // -1: none
+    int tape_slot;     // -1: none
+    int want_sum;      // accumulate the sum of squares (g for the forward, E for the adjoint)
+    int terminal;
+};
+
+template <typename T> __device__ __forceinline__ T* role_ptr(const BRec<T>& R, int role, int slot) {
+    return role == ROLE_CKPT ? R.pop[2] + (size_t)slot * R.pop_elems : R.pop[role];
+}
+
+template <typename T> struct BFwdArgs {
+    const T* inb;
+    T* outb;
+    long long pl;
+    T* phi;
+    T* phi_ckpt;
+    const T* g;
+    const T* E;
+    T lam;
+    T* tape;
+    int n;
+    __device__ __forceinline__ const T* in(int j) const { return inb + (size_t)j * pl; }
+    __device__ __forceinline__ T* out(int j) const { return outb + (size_t)j * pl; }
+};
+
+template <typename T> struct BAdjArgs {
+    const T* rinb;
+    T* routb;
+    long long pl;
+    const T* wu;
+    const T* wv;
+    const T* tape;
+    T* sigma;
+    const T* g;
+    T* dJdg;
+    int n;
+    int terminal;
+    __device__ __forceinline__ const T* in(int j) const { return rinb + (size_t)j * pl; }
+    __device__ __forceinline__ T* out(int j) const { return routb + (size_t)j * pl; }
+};
+
+template <typename T> __device__ __forceinline__ BFwdArgs<T> fwd_args(const BRec<T>& R, const BStep& st) {
+    BFwdArgs<T> A;
+    A.inb = role_ptr(R, st.in_role, st.in_slot);
+    A.outb = role_ptr(R, st.out_role, st.out_slot);
+    A.pl = R.plane;
+    A.phi = R.phi;
+    A.phi_ckpt = st.phi_ckpt_slot >= 0 ? R.ckpt_phi + (size_t)st.phi_ckpt_slot * R.plane : nullptr;
+    A.g = R.g ? R.g + (size_t)st.n * R.nctrl : nullptr;
+    A.E = nullptr;
+    A.lam = T(0);
+    A.tape = st.tape_slot >= 0 ? R.tape + (size_t)st.tape_slot * 3 * R.plane : nullptr;
+    A.n = st.n;
+    return A;
+}
+
+template <typename T> __device__ __forceinline__ BAdjArgs<T> adj_args(const BRec<T>& R, const BStep& st) {
+    BAdjArgs<T> A;
+    A.rinb = role_ptr(R, st.in_role, st.in_slot);
+    A.routb = role_ptr(R, st.out_role, st.out_slot);
+    A.pl = R.plane;
+    A.wu = R.wu;
+    A.wv = nullptr;
+    A.tape = R.tape + (size_t)st.tape_slot * 3 * R.plane;
+    A.sigma = R.sigma;
+    A.g = R.g ? R.g + (size_t)st.n * R.nctrl : nullptr;
+    A.dJdg = R.dJdg + (size_t)st.n * R.nctrl;
+    A.n = st.n;
+    A.terminal = st.terminal;
+    return A;
+}
+
+// problem owning global tile t (tile0 ascending, sh[count] = total)
+__device__ __forceinline__ int find_problem(const int* sh, int count, int t) {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (sh[mid] <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename T> __device__ __forceinline__ NodeIdx tile_node(const BRec<T>& R, int local) {
+    const CxConst& C = R.C;
+    const int tyi = local / R.tiles_x, txi = local - tyi * R.tiles_x;
+    NodeIdx r;
+    r.x = txi * R.tx + (int)threadIdx.x % R.tx;
+    r.y = tyi * R.ty + (int)threadIdx.x / R.tx;
+    const bool in = r.x < C.nx && r.y < C.ny;
+    r.k = in ? r.y * C.nx + r.x : 0;
+    r.fluid = in && !(C.has_solid && C.solid[r.k]);
+    if (!in) {
+        r.c = -1;
+    } else if (C.ctrl_full) {
+        r.c = r.k;
+    } else {
+        const int cx = r.x - C.cx0, cy = r.y - C.cy0;
+        r.c = (cx >= 0 && cy >= 0 && cx < C.cnx && cy < C.cny) ? cy * C.cnx + cx : -1;
+    }
+    r.ctrl = r.fluid && r.c >= 0 && (!C.cmask || C.cmask[r.c]);
+    return r;
+}
+
+template <typename T, int Q, int NT, bool ADJ>
+__global__ void __launch_bounds__(NT) k_batch(const BRec<T>* __restrict__ recs, const int* __restrict__ tile0, int count,
+                                              int total, BStep st, double* sum_slots, double* max_slots) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int NV = ADJ ? 2 * Q + 6 : 2 * Q + 4;
+    int* sh_tile0 = reinterpret_cast<int*>(smem_raw + (size_t)2 * NV * NT * sizeof(T));
+    for (int i = threadIdx.x; i <= count; i += NT) sh_tile0[i] = tile0[i];
+    __syncthreads();
+    T* const s0 = reinterpret_cast<T*>(smem_raw) + threadIdx.x;
+    T* const s1 = s0 + NV * NT;
+    allow_next_grid();
+    wait_prior_grid();
+
+    int t = blockIdx.x;
+    int p = t < total ? find_problem(sh_tile0, count, t) : 0;
+    NodeIdx cur = t < total ? tile_node(recs[p], t - sh_tile0[p]) : no_node();
+    if (t < total) {
+        if constexpr (ADJ)
+            adj_stage<T, Q, NT>(recs[p].C, adj_args(recs[p], st), cur, s0);
+        else
+            fwd_stage<T, Q, NT>(recs[p].C, fwd_args(recs[p], st), cur, s0);
+    }
+    cp_async_commit();
+    bool odd = false;
+    while (t < total) {
+        const int tn = t + gridDim.x;
+        int pn = 0;
+        NodeIdx nxt = no_node();
+        if (tn < total) {
+            pn = find_problem(sh_tile0, count, tn);
+            nxt = tile_node(recs[pn], tn - sh_tile0[pn]);
+            if constexpr (ADJ)
+                adj_stage<T, Q, NT>(recs[pn].C, adj_args(recs[pn], st), nxt, odd ? s0 : s1);
+            else
+                fwd_stage<T, Q, NT>(recs[pn].C, fwd_args(recs[pn], st), nxt, odd ? s0 : s1);
+        }
+        cp_async_commit();
+        cp_async_wait<1>();
+        const BRec<T>& R = recs[p];
+        typename SqAccT<T>::type acc;
+        if constexpr (ADJ)
+            adj_compute<T, Q, NT>(R.C, R.K, adj_args(R, st), cur, odd ? s1 : s0, acc);
+        else
+            fwd_compute<T, Q, NT>(R.C, R.K, fwd_args(R, st), cur, odd ? s1 : s0, acc);
+        if (st.want_sum) {
+            const int slot = R.slot0 + (t - sh_tile0[p]) * (NT >> 5) + ((int)threadIdx.x >> 5);
+            acc.flush(sum_slots + slot, max_slots ? max_slots + slot : nullptr);
+        }
+        t = tn;
+        p = pn;
+        cur = nxt;
+        odd = !odd;
+    }
+    cp_async_wait<0>();
+}
+
+// Per-problem fixed-order sums: J_p = cost_p + alpha_p * sum(gsq slots) (mode 0)
+// or (sum E^2, max |E|) (mode 1).  One block per problem.
+struct BFin {
+    const double* cost; // per-problem cost partial array (block partials of k_final)
+    int ncost;
+    int slot0, nslots;
+    double alpha;
+};
+__global__ void __launch_bounds__(256) k_bfinalize(const BFin* fin, const double* sums, const double* maxs, int mode,
+                                                    double* out_a, double* out_b, int* status) {
+    __shared__ double sa[256], sb[256];
+    const BFin F = fin[blockIdx.x];
+    const int t = threadIdx.x;
+    double ra = 0.0, rb = 0.0;
+    if (mode == 0)
+        for (int i = t; i < F.ncost; i += 256) ra += F.cost[i];
+    for (int i = t; i < F.nslots; i += 256) {
+        if (mode == 0) rb += sums[F.slot0 + i];
+        else {
+            ra += sums[F.slot0 + i];
+            rb = fmax(rb, maxs[F.slot0 + i]);
+        }
+    }
+    sa[t] = ra;
+    sb[t] = rb;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (t < h) {
+            sa[t] += sa[t + h];
+            sb[t] = (mode == 1) ? fmax(sb[t], sb[t + h]) : sb[t] + sb[t + h];
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        if (mode == 0) {
+            const double J = sa[0] + F.alpha * sb[0];
+            out_a[blockIdx.x] = J;
+            if (!isfinite(J)) atomicOr(status, ST_UNSTABLE);
+        } else {
+            out_a[blockIdx.x] = sa[0];
+            if (out_b) out_b[blockIdx.x] = sb[0];
+            if (!isfinite(sa[0])) atomicOr(status, ST_UNSTABLE);
+        }
+    }
+}
+
+// Node-plane operations over all problems: zero sigma (op 0), restore Phi
+// from checkpoint slot `slot` (op 1).
+template <typename T>
+__global__ void k_bplanes(const BRec<T>* __restrict__ recs, int count, int op, int slot) {
+    const int p = blockIdx.y;
+    if (p >= count) return;
+    const BRec<T>& R = recs[p];
+    const size_t n = (size_t)R.C.nx * R.C.ny;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        if (op == 0) R.sigma[i] = T(0);
+        else R.phi[i] = R.ckpt_phi[(size_t)slot * R.plane + i];
+    }
+}
+
+} // namespace cx
+
+using namespace cx;
+
+namespace {
+
+struct BatchHost {
+    int count = 0, threads = 256, blocks = 0, total_tiles = 0, nslots = 0;
+    size_t slot_cap = 0;
+    int Q = 9, N = 1, k = 1, S = 1;
+    size_t esz = 4;
+    std::vector<cx_problem*> probs;
+    std::vector<int> tx; // tile width per problem
+    char* ws = nullptr;
+    size_t off_rec = 0, off_tile0 = 0, off_fin = 0, off_sums = 0, off_maxs = 0, off_out = 0, off_status = 0;
+    size_t rec_bytes = 0;
+    std::vector<const void*> g;
+    std::vector<void*> dJdg;
+    cudaStream_t stream = nullptr;
+    cudaGraphExec_t graph_grad = nullptr, graph_fwd = nullptr;
+    bool has_init = false, bound = false;
+};
+
+} // namespace
+
+struct cx_batch {
+    BatchHost h;
+};
+
+namespace {
+
+constexpr int MAX_BATCH = 4096;
+
+size_t rec_size(size_t esz) { return esz == 8 ? sizeof(BRec<double>) : sizeof(BRec<float>); }
+
+// Reduction slots any admissible tiling of a problem can need: (threads/32)
+// slots per tile, tiles = ceil(nx/tx) ceil(ny/ty) <= nx ny/128 + nx/32 + ny + 1
+// for 128 <= threads = tx ty <= 256, tx >= 32, ty >= 1.
+size_t slot_capacity(const cx_problem_desc& d) {
+    const size_t nx = d.nx, ny = d.ny;
+    return 8 * (nx * ny / 128 + nx / 32 + ny + 2);
+}
+
+// tiles and reduction slots for the current tile shapes
+void plan_tiles(BatchHost& h, std::vector<int>& tile0, std::vector<int>& slot0) {
+    tile0.assign(h.count + 1, 0);
+    slot0.assign(h.count + 1, 0);
+    for (int i = 0; i < h.count; ++i) {
+        const int tx = h.tx[i], ty = h.threads / tx;
+        const int nt = ((h.probs[i]->d.nx + tx - 1) / tx) * ((h.probs[i]->d.ny + ty - 1) / ty);
+        tile0[i + 1] = tile0[i] + nt;
+        slot0[i + 1] = slot0[i] + nt * (h.threads / 32);
+    }
+    h.total_tiles = tile0[h.count];
+    h.nslots = slot0[h.count];
+}
+
+template <typename T> cx_status upload_table(BatchHost& h) {
+    std::vector<int> tile0, slot0;
+    plan_tiles(h, tile0, slot0);
+    if ((size_t)h.nslots > h.slot_cap) return CX_ERR_INTERNAL; // cannot happen for admissible tilings
+    std::vector<BRec<T>> recs(h.count);
+    std::vector<BFin> fin(h.count);
+    for (int i = 0; i < h.count; ++i) {
+        cx_problem* p = h.probs[i];
+        BRec<T>& R = recs[i];
+        std::memset(&R, 0, sizeof(R));
+        R.C = p->C;
+        R.K = p->kc((T*)nullptr);
+        R.pop[ROLE_POPA] = p->at<T>(p->lay.off_popA);
+        R.pop[ROLE_POPB] = p->at<T>(p->lay.off_popB);
+        R.pop[ROLE_CKPT] = reinterpret_cast<T*>(p->ckpt_slot(0));
+        R.pop[ROLE_ADJA] = p->at<T>(p->lay.off_adjA);
+        R.pop[ROLE_ADJB] = p->at<T>(p->lay.off_adjB);
+        R.ckpt_phi = reinterpret_cast<T*>(p->ckpt_phi_slot(0));
+        R.phi = p->at<T>(p->lay.off_phi);
+        R.sigma = p->at<T>(p->lay.off_sigma);
+        R.tape = reinterpret_cast<T*>(p->tape_slot(0));
+        R.wu = p->at<T>(p->lay.off_wu);
+        R.g = h.g.empty() ? nullptr : static_cast<const T*>(h.g[i]);
+        R.dJdg = h.dJdg.empty() ? nullptr : static_cast<T*>(h.dJdg[i]);
+        R.plane = (long long)p->lay.plane;
+        R.nctrl = (long long)p->lay.nctrl;
+        R.pop_elems = (long long)(2 * p->lay.Q * p->lay.plane);
+        R.tile0 = tile0[i];
+        R.tx = h.tx[i];
+        R.ty = h.threads / h.tx[i];
+        R.tiles_x = (p->d.nx + R.tx - 1) / R.tx;
+        R.slot0 = slot0[i];
+        fin[i].cost = p->at<double>(p->lay.off_part);
+        fin[i].ncost = p->nblocks;
+        fin[i].slot0 = slot0[i];
+        fin[i].nslots = slot0[i + 1] - slot0[i];
+        fin[i].alpha = p->C.alpha;
+    }
+    if (cudaMemcpy(h.ws + h.off_rec, recs.data(), sizeof(BRec<T>) * h.count, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(h.ws + h.off_tile0, tile0.data(), sizeof(int) * (h.count + 1), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(h.ws + h.off_fin, fin.data(), sizeof(BFin) * h.count, cudaMemcpyHostToDevice) != cudaSuccess)
+        return CX_ERR_CUDA;
+    return CX_OK;
+}
+
+void drop_graphs(BatchHost& h) {
+    if (h.graph_grad) cudaGraphExecDestroy(h.graph_grad);
+    if (h.graph_fwd) cudaGraphExecDestroy(h.graph_fwd);
+    h.graph_grad = h.graph_fwd = nullptr;
+}
+
+template <typename T, int Q, int NT, bool ADJ>
+cudaError_t launch_bq(const BatchHost& h, const BStep& st, int blocks) {
+    constexpr int NV = ADJ ? 2 * Q + 6 : 2 * Q + 4;
+    const size_t smem = (size_t)2 * NV * NT * sizeof(T) + sizeof(int) * (h.count + 1);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_batch<T, Q, NT, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             128 * 1024);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = h.stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    double* sums = reinterpret_cast<double*>(h.ws + h.off_sums);
+    double* maxs = ADJ ? reinterpret_cast<double*>(h.ws + h.off_maxs) : nullptr;
+    return cudaLaunchKernelEx(&cfg, k_batch<T, Q, NT, ADJ>, reinterpret_cast<const BRec<T>*>(h.ws + h.off_rec),
+                              reinterpret_cast<const int*>(h.ws + h.off_tile0), h.count, h.total_tiles, st, sums,
+                              maxs);
+}
+
+template <typename T, bool ADJ> cudaError_t launch_b(const BatchHost& h, const BStep& st) {
+    const int blocks = std::max(1, std::min(h.blocks, h.total_tiles));
+    if (h.Q == 9) {
+        if (h.threads == 128) return launch_bq<T, 9, 128, ADJ>(h, st, blocks);
+        return launch_bq<T, 9, 256, ADJ>(h, st, blocks);
+    }
+    if (h.threads == 128) return launch_bq<T, 5, 128, ADJ>(h, st, blocks);
+    return launch_bq<T, 5, 256, ADJ>(h, st, blocks);
+}
+
+template <typename T> cudaError_t launch_planes(const BatchHost& h, int op, int slot) {
+    dim3 grid(64, h.count), block(256);
+    k_bplanes<T><<<grid, block, 0, h.stream>>>(reinterpret_cast<const BRec<T>*>(h.ws + h.off_rec), h.count, op,
+                                                 slot);
+    return cudaGetLastError();
+}
+
+#define B_CUDA(x)                                                                                                    \
+    do {                                                                                                             \
+        if ((x) != cudaSuccess) return CX_ERR_CUDA;                                                                  \
+    } while (0)
+
+// Forward of every problem; J_p into out[0..count).
+template <typename T> cx_status enqueue_forward(BatchHost& h) {
+    double* sums = reinterpret_cast<double*>(h.ws + h.off_sums);
+    B_CUDA(cudaMemsetAsync(sums, 0, sizeof(double) * h.nslots, h.stream));
+    const int N = h.N, k = h.k, S = h.S;
+    int in_role = ROLE_CKPT, in_slot = 0;
+    for (int n = 0; n < N; ++n) {
+        const int seg = n / k;
+        BStep st{};
+        st.n = n;
+        st.in_role = in_role;
+        st.in_slot = in_slot;
+        if (n + 1 < N && (n + 1) % k == 0) {
+            st.out_role = ROLE_CKPT;
+            st.out_slot = (n + 1) / k;
+            st.phi_ckpt_slot = (n + 1) / k;
+        } else {
+            st.out_role = (n % 2) ? ROLE_POPB : ROLE_POPA;
+            st.out_slot = 0;
+            st.phi_ckpt_slot = -1;
+        }
+        st.tape_slot = (seg == S - 1) ? n - seg * k : -1;
+        st.want_sum = 1;
+        B_CUDA((launch_b<T, false>(h, st)));
+        in_role = st.out_role;
+        in_slot = st.out_slot;
+    }
+    for (int i = 0; i < h.count; ++i) {
+        cx_problem* p = h.probs[i];
+        const T* in = in_role == ROLE_CKPT ? reinterpret_cast<const T*>(p->ckpt_slot(in_slot))
+                                           : p->at<T>(in_role == ROLE_POPA ? p->lay.off_popA : p->lay.off_popB);
+        B_CUDA(launch_final<T>(p->C, in, p->at<T>(p->lay.off_ut), p->at<T>(p->lay.off_uN), p->at<T>(p->lay.off_vN),
+                               p->at<T>(p->lay.off_wu), p->at<double>(p->lay.off_part), p->L, h.stream));
+    }
+    k_bfinalize<<<h.count, 256, 0, h.stream>>>(reinterpret_cast<const BFin*>(h.ws + h.off_fin), sums, nullptr, 0,
+                                                reinterpret_cast<double*>(h.ws + h.off_out), nullptr,
+                                                reinterpret_cast<int*>(h.ws + h.off_status));
+    B_CUDA(cudaGetLastError());
+    return CX_OK;
+}
+
+// Recompute + AMRT adjoint of every problem; ||E_p||^2, max|E_p| into out[count..3 count).
+template <typename T> cx_status enqueue_adjoint(BatchHost& h) {
+    double* sums = reinterpret_cast<double*>(h.ws + h.off_sums);
+    double* maxs = reinterpret_cast<double*>(h.ws + h.off_maxs);
+    B_CUDA(cudaMemsetAsync(sums, 0, sizeof(double) * h.nslots, h.stream));
+    B_CUDA(cudaMemsetAsync(maxs, 0, sizeof(double) * h.nslots, h.stream));
+    B_CUDA(launch_planes<T>(h, 0, 0));
+    const int N = h.N, k = h.k, S = h.S;
+    int in_role = -1, in_slot = 0;
+    for (int s = S - 1; s >= 0; --s) {
+        const int n0 = s * k, n1 = std::min(N, n0 + k);
+        if (s < S - 1) { // the last segment's tape comes from the forward
+            if (s >= 1) B_CUDA(launch_planes<T>(h, 1, s));
+            int ri = ROLE_CKPT, rs = s;
+            for (int n = n0; n < n1; ++n) {
+                BStep st{};
+                st.n = n;
+                st.in_role = ri;
+                st.in_slot = rs;
+                st.out_role = (n % 2) ? ROLE_POPB : ROLE_POPA;
+                st.out_slot = 0;
+                st.phi_ckpt_slot = -1;
+                st.tape_slot = n - n0;
+                st.want_sum = 0;
+                B_CUDA((launch_b<T, false>(h, st)));
+                ri = st.out_role;
+                rs = 0;
+            }
+        }
+        for (int n = n1 - 1; n >= n0; --n) {
+            BStep st{};
+            st.n = n;
+            st.terminal = (n == N - 1);
+            st.in_role = st.terminal ? ROLE_ADJA : in_role;
+            st.in_slot = in_slot;
+            st.out_role = (n % 2) ? ROLE_ADJB : ROLE_ADJA;
+            st.out_slot = 0;
+            st.phi_ckpt_slot = -1;
+            st.tape_slot = n - n0;
+            st.want_sum = 1;
+            B_CUDA((launch_b<T, true>(h, st)));
+            in_role = st.out_role;
+            in_slot = 0;
+        }
+    }
+    double* out = reinterpret_cast<double*>(h.ws + h.off_out);
+    k_bfinalize<<<h.count, 256, 0, h.stream>>>(reinterpret_cast<const BFin*>(h.ws + h.off_fin), sums, maxs, 1,
+                                                out + h.count, out + 2 * h.count,
+                                                reinterpret_cast<int*>(h.ws + h.off_status));
+    B_CUDA(cudaGetLastError());
+    return CX_OK;
+}
+
+template <typename T> cx_status capture(BatchHost& h, bool with_adjoint, cudaGraphExec_t* exec) {
+    cudaGraph_t graph = nullptr;
+    B_CUDA(cudaStreamBeginCapture(h.stream, cudaStreamCaptureModeThreadLocal));
+    cx_status rc = enqueue_forward<T>(h);
+    if (rc == CX_OK && with_adjoint) rc = enqueue_adjoint<T>(h);
+    const cudaError_t e = cudaStreamEndCapture(h.stream, &graph);
+    if (rc != CX_OK || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc != CX_OK ? rc : CX_ERR_CUDA;
+    }
+    const cudaError_t ei = cudaGraphInstantiate(exec, graph, 0);
+    cudaGraphDestroy(graph);
+    return ei == cudaSuccess ? CX_OK : CX_ERR_CUDA;
+}
+
+template <typename T> cx_status run(BatchHost& h, bool with_adjoint, double* out_dev) {
+    cudaGraphExec_t* ex = with_adjoint ? &h.graph_grad : &h.graph_fwd;
+    if (!*ex) {
+        cx_status rc = capture<T>(h, with_adjoint, ex);
+        if (rc) return rc;
+    }
+    B_CUDA(cudaGraphLaunch(*ex, h.stream));
+    for (cx_problem* p : h.probs) {
+        p->fwd_valid = true;
+        p->adj_valid = false;
+        p->tape_last_valid = !with_adjoint || h.S == 1;
+    }
+    if (out_dev)
+        B_CUDA(cudaMemcpyAsync(out_dev, h.ws + h.off_out, sizeof(double) * (with_adjoint ? 3 : 1) * h.count,
+                               cudaMemcpyDeviceToDevice, h.stream));
+    return CX_OK;
+}
+
+cx_status batch_layout(const cx_problem_desc* d, int count, std::vector<size_t>* offs, size_t* table_off,
+                       size_t* total) {
+    if (!d || count < 1 || count > MAX_BATCH) return CX_ERR_INVALID_ARG;
+    size_t o = 0;
+    for (int i = 0; i < count; ++i) {
+        if (d[i].n_steps != d[0].n_steps || d[i].lattice != d[0].lattice || d[i].precision != d[0].precision ||
+            (d[i].ckpt_every ? d[i].ckpt_every : d[i].n_steps) != (d[0].ckpt_every ? d[0].ckpt_every : d[0].n_steps))
+            return CX_ERR_INVALID_ARG;
+        size_t b = 0;
+        cx_status rc = cx_workspace_size(&d[i], &b);
+        if (rc) return rc;
+        if (offs) offs->push_back(o);
+        o = up(o + b, ALIGN);
+    }
+    *table_off = o;
+    // records, tile prefix, finalize records, slots (sized for the densest tiling), outputs, status
+    size_t slots = 0;
+    for (int i = 0; i < count; ++i) slots += slot_capacity(d[i]);
+    const size_t esz = d[0].precision == 64 ? 8 : 4;
+    o = up(o + rec_size(esz) * count, ALIGN);
+    o = up(o + sizeof(int) * (count + 1), ALIGN);
+    o = up(o + sizeof(BFin) * count, ALIGN);
+    o = up(o + sizeof(double) * slots, ALIGN);
+    o = up(o + sizeof(double) * slots, ALIGN);
+    o = up(o + sizeof(double) * 3 * count, ALIGN);
+    o = up(o + sizeof(int) * 4, ALIGN);
+    *total = o;
+    return CX_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+cx_status cx_batch_workspace_size(const cx_problem_desc* descs, int count, size_t* bytes) {
+    if (!bytes) return CX_ERR_INVALID_ARG;
+    size_t toff = 0;
+    return batch_layout(descs, count, nullptr, &toff, bytes);
+}
+
+cx_status cx_batch_set_tiles(cx_batch* b, int threads, int blocks, const int* tile_x) {
+    if (!b || (threads != 128 && threads != 256) || blocks < 0) return CX_ERR_INVALID_ARG;
+    BatchHost& h = b->h;
+    std::vector<int> tx(h.count);
+    for (int i = 0; i < h.count; ++i) {
+        const int t = tile_x ? tile_x[i] : std::min(threads, 256);
+        if (t < 32 || t > threads || threads % t != 0 || threads / t > 8) return CX_ERR_INVALID_ARG;
+        tx[i] = t;
+    }
+    h.threads = threads;
+    h.tx = tx;
+    const int occ = h.esz == 8 ? forward_occupancy<double>(h.Q, threads) : forward_occupancy<float>(h.Q, threads);
+    h.blocks = blocks > 0 ? blocks : h.probs[0]->nsm * occ;
+    drop_graphs(h);
+    return h.esz == 8 ? upload_table<double>(h) : upload_table<float>(h);
+}
+
+cx_status cx_batch_create(const cx_problem_desc* descs, int count, void* workspace, size_t bytes, cudaStream_t stream,
+                          cx_batch** out) {
+    if (!out) return CX_ERR_INVALID_ARG;
+    *out = nullptr;
+    std::vector<size_t> offs;
+    size_t toff = 0, total = 0;
+    cx_status rc = batch_layout(descs, count, &offs, &toff, &total);
+    if (rc) return rc;
+    if (!workspace || bytes < total || reinterpret_cast<uintptr_t>(workspace) % ALIGN) return CX_ERR_WORKSPACE;
+    cx_batch* b = new (std::nothrow) cx_batch();
+    if (!b) return CX_ERR_INTERNAL;
+    BatchHost& h = b->h;
+    h.count = count;
+    h.ws = static_cast<char*>(workspace);
+    h.stream = stream;
+    h.Q = descs[0].lattice;
+    h.N = descs[0].n_steps;
+    h.k = descs[0].ckpt_every > 0 ? std::min(descs[0].ckpt_every, h.N) : h.N;
+    h.S = (h.N + h.k - 1) / h.k;
+    h.esz = descs[0].precision == 64 ? 8 : 4;
+    for (int i = 0; i < count; ++i) {
+        cx_problem* p = nullptr;
+        size_t pb = 0;
+        rc = cx_workspace_size(&descs[i], &pb);
+        if (rc == CX_OK) rc = cx_create(&descs[i], h.ws + offs[i], pb, stream, &p);
+        if (rc) {
+            for (cx_problem* q : h.probs) cx_destroy(q);
+            delete b;
+            return rc;
+        }
+        h.probs.push_back(p);
+    }
+    size_t o = toff;
+    h.off_rec = o;
+    o = up(o + rec_size(h.esz) * count, ALIGN);
+    h.off_tile0 = o;
+    o = up(o + sizeof(int) * (count + 1), ALIGN);
+    h.off_fin = o;
+    o = up(o + sizeof(BFin) * count, ALIGN);
+    size_t slots = 0;
+    for (int i = 0; i < count; ++i) slots += slot_capacity(descs[i]);
+    h.slot_cap = slots;
+    h.off_sums = o;
+    o = up(o + sizeof(double) * slots, ALIGN);
+    h.off_maxs = o;
+    o = up(o + sizeof(double) * slots, ALIGN);
+    h.off_out = o;
+    o = up(o + sizeof(double) * 3 * count, ALIGN);
+    h.off_status = o;
+    if (cudaMemset(h.ws + h.off_status, 0, sizeof(int) * 4) != cudaSuccess) {
+        cx_batch_destroy(b);
+        return CX_ERR_CUDA;
+    }
+    rc = cx_batch_set_tiles(b, 256, 0, nullptr);
+    if (rc) {
+        cx_batch_destroy(b);
+        return rc;
+    }
+    *out = b;
+    return CX_OK;
+}
+
+cx_status cx_batch_set_initial(cx_batch* b, const void* const* u0, const void* const* v0) {
+    if (!b || !u0 || !v0) return CX_ERR_INVALID_ARG;
+    for (int i = 0; i < b->h.count; ++i) {
+        cx_status rc = cx_set_initial(b->h.probs[i], u0[i], v0[i]);
+        if (rc) return rc;
+    }
+    b->h.has_init = true;
+    return CX_OK;
+}
+
+cx_status cx_batch_bind(cx_batch* b, const void* const* g, void* const* dJdg) {
+    if (!b) return CX_ERR_INVALID_ARG;
+    BatchHost& h = b->h;
+    h.g.assign(h.count, nullptr);
+    h.dJdg.assign(h.count, nullptr);
+    for (int i = 0; i < h.count; ++i) {
+        if (g) h.g[i] = g[i];
+        if (dJdg) h.dJdg[i] = dJdg[i];
+    }
+    h.bound = true;
+    drop_graphs(h);
+    return h.esz == 8 ? upload_table<double>(h) : upload_table<float>(h);
+}
+
+cx_status cx_batch_forward(cx_batch* b, double* J_dev) {
+    if (!b) return CX_ERR_INVALID_ARG;
+    if (!b->h.has_init || !b->h.bound) return CX_ERR_STATE;
+    return b->h.esz == 8 ? run<double>(b->h, false, J_dev) : run<float>(b->h, false, J_dev);
+}
+
+cx_status cx_batch_gradient(cx_batch* b, double* out_dev) {
+    if (!b) return CX_ERR_INVALID_ARG;
+    if (!b->h.has_init || !b->h.bound) return CX_ERR_STATE;
+    for (void* p : b->h.dJdg)
+        if (!p) return CX_ERR_INVALID_ARG;
+    return b->h.esz == 8 ? run<double>(b->h, true, out_dev) : run<float>(b->h, true, out_dev);
+}
+
+cx_status cx_batch_get_fields(cx_batch* b, int i, void* u_out, void* v_out) {
+    if (!b || i < 0 || i >= b->h.count) return CX_ERR_INVALID_ARG;
+    return cx_get_fields(b->h.probs[i], u_out, v_out);
+}
+
+cx_status cx_batch_get_status(cx_batch* b) {
+    if (!b) return CX_ERR_INVALID_ARG;
+    int st = 0;
+    if (cudaMemcpyAsync(&st, b->h.ws + b->h.off_status, sizeof(int), cudaMemcpyDeviceToHost, b->h.stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(b->h.stream) != cudaSuccess)
+        return CX_ERR_CUDA;
+    return (st & ST_UNSTABLE) ? CX_ERR_UNSTABLE : CX_OK;
+}
+
+cx_status cx_batch_destroy(cx_batch* b) {
+    if (!b) return CX_ERR_INVALID_ARG;
+    drop_graphs(b->h);
+    for (cx_problem* p : b->h.probs) cx_destroy(p);
+    delete b;
+    return CX_OK;
+}
+
+} // extern "C"

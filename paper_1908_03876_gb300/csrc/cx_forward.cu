@@ -22,121 +22,9 @@
 // cp.async copies of its next node's populations and per-node scalars into its
 // own shared-memory slots (two stages), so DRAM latency overlaps the
 // arithmetic without holding registers for loads in flight.
-#include "cx_device.cuh"
+#include "cx_fwd_body.cuh"
 
 namespace cx {
-
-template <int Q> constexpr int fwd_stage_values() { return 2 * Q + 4; } // pops, theta, g, E, Phi^{n-1}
-
-template <typename T, int Q, int NT>
-__device__ __forceinline__ void fwd_stage(const CxConst& C, const FwdArgs<T>& A, const NodeIdx& nd, T* s) {
-    using L = Lat<Q>;
-    if (!nd.fluid) return;
-    const int x = nd.x, y = nd.y, k = nd.k;
-    if (A.n == 0) {
-#pragma unroll
-        for (int i = 0; i < 2 * Q; ++i) cp_async(s + i * NT, A.pin[i] + k);
-    } else {
-        const int xm = x == 0 ? C.nx - 1 : x - 1, xp = x == C.nx - 1 ? 0 : x + 1;
-        const int rm = (y == 0 ? C.ny - 1 : y - 1) * C.nx, r0 = y * C.nx, rp = (y == C.ny - 1 ? 0 : y + 1) * C.nx;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const int xs = L::ex(i) > 0 ? xm : (L::ex(i) < 0 ? xp : x);
-            const int ks = (L::ey(i) > 0 ? rm : (L::ey(i) < 0 ? rp : r0)) + xs;
-            if (C.has_solid && i != 0 && C.solid[ks]) {
-                cp_async(s + i * NT, A.pin[L::opp(i)] + k);
-                cp_async(s + (Q + i) * NT, A.pin[Q + L::opp(i)] + k);
-            } else {
-                cp_async(s + i * NT, A.pin[i] + ks);
-                cp_async(s + (Q + i) * NT, A.pin[Q + i] + ks);
-            }
-        }
-        cp_async(s + (2 * Q + 3) * NT, A.phi + k);
-    }
-    if (C.aniso == CX_ANISO_ROTATED) cp_async(s + 2 * Q * NT, reinterpret_cast<const T*>(C.theta) + k);
-    if (nd.ctrl) {
-        if (A.g) cp_async(s + (2 * Q + 1) * NT, A.g + nd.c);
-        if (A.E) cp_async(s + (2 * Q + 2) * NT, A.E + nd.c);
-    }
-}
-
-template <typename T, int Q, int NT>
-__device__ __forceinline__ void fwd_compute(const CxConst& C, const KConst<T>& KC, const FwdArgs<T>& A,
-                                            const NodeIdx& nd, const T* s, typename SqAccT<T>::type& acc) {
-    using L = Lat<Q>;
-    if (!nd.fluid) return;
-    const int y = nd.y, k = nd.k;
-    T fu[Q], fv[Q];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        fu[i] = s[i * NT];
-        fv[i] = s[(Q + i) * NT];
-    }
-    T g = T(0);
-    if (nd.ctrl) {
-        if (A.g) g = s[(2 * Q + 1) * NT];
-        if (A.E) g = fma(-A.lam, s[(2 * Q + 2) * NT], g); // same rounding as the accepted update
-        acc.add(g);
-    }
-    NodeCoef<T> nc;
-    node_coef_th<T>(C, KC, (C.aniso == CX_ANISO_ROTATED) ? s[2 * Q * NT] : T(0), y, k, nc);
-
-    // moments m = M f of both species
-    T mu[Q], mv[Q];
-    Transform<T, Q>::moments(fu, mu);
-    Transform<T, Q>::moments(fv, mv);
-    const T Tu = mu[0], Tv = mv[0];
-    const T jvx = mv[L::JX], jvy = mv[L::JY];
-
-    // reaction and control source
-    const T Phi = KC.r_vu * Tu + KC.r_vv * Tv + g;
-    const T Phi_prev = (A.n == 0) ? Phi : s[(2 * Q + 3) * NT];
-
-    // grad v (reading of C146)
-    const T rx = (jvx - nc.ax * Tv) * KC.inv_tau, ry = (jvy - nc.ay * Tv) * KC.inv_tau;
-    const T Kax = nc.Kv0 * nc.ax + nc.Kv1 * nc.ay, Kay = nc.Kv1 * nc.ax + nc.Kv2 * nc.ay;
-    const T Gx = KC.gsc * (nc.Kv0 * rx + nc.Kv1 * ry + T(0.5) * Kax * Phi);
-    const T Gy = KC.gsc * (nc.Kv1 * rx + nc.Kv2 * ry + T(0.5) * Kay * Phi);
-
-    // --- species u: MRT collision + chemotactic cross-diffusion source
-    T mh[Q], dm[Q], rl[Q], bt[Q];
-    meq_unit<T, Q>(nc.ax, nc.ay, KC.d_u, mh);
-#pragma unroll
-    for (int kk = 0; kk < Q; ++kk) dm[kk] = mu[kk] - Tu * mh[kk];
-    relax_n<T, Q>(KC, nc.Ku0, nc.Ku1, nc.Ku2, dm, rl);
-    // (w_i/Cs^2) chi u e_i.(K_u G) = 3 w_i e_i . F
-    const T Fx = KC.chi * Tu * (nc.Ku0 * Gx + nc.Ku1 * Gy);
-    const T Fy = KC.chi * Tu * (nc.Ku1 * Gx + nc.Ku2 * Gy);
-    Transform<T, Q>::transpose(rl, bt); // M^-1 Pi (m - m^eq) = M^T N^-1 Pi (m - m^eq)
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const T src = T(3.0 * L::w(i)) * (T(L::ex(i)) * Fx + T(L::ey(i)) * Fy);
-        A.pout[i][k] = fu[i] - bt[i] + src;
-    }
-
-    // --- species v: MRT collision + reaction/control source with the tau/2
-    //     time-derivative term
-    meq_unit<T, Q>(nc.ax, nc.ay, KC.d_v, mh);
-#pragma unroll
-    for (int kk = 0; kk < Q; ++kk) dm[kk] = mv[kk] - Tv * mh[kk];
-    relax_n<T, Q>(KC, nc.Kv0, nc.Kv1, nc.Kv2, dm, rl);
-    const T Vx = nc.ax - T(0.5) * Kax, Vy = nc.ay - T(0.5) * Kay; // V = (I - K_v/2) a
-    const T srcv = (A.n == 0) ? KC.c_first * Phi : KC.c_now * Phi + KC.c_prev * Phi_prev;
-    Transform<T, Q>::transpose(rl, bt);
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const T wt = T(L::w(i)) * (T(1) + T(3) * (Vx * T(L::ex(i)) + Vy * T(L::ey(i))));
-        A.pout[Q + i][k] = fv[i] - bt[i] + wt * srcv;
-    }
-    A.phi[k] = Phi;
-    if (A.phi_ckpt) A.phi_ckpt[k] = Phi;
-    if (A.tape) {
-        const size_t pl = (size_t)C.plane;
-        A.tape[k] = Tu;
-        A.tape[pl + k] = Gx;
-        A.tape[2 * pl + k] = Gy;
-    }
-}
 
 template <typename T, int Q, int NT>
 __global__ void __launch_bounds__(NT) k_forward(const CxConst C, const KConst<T> KC, const FwdArgs<T> A) {
@@ -149,16 +37,16 @@ __global__ void __launch_bounds__(NT) k_forward(const CxConst C, const KConst<T>
     NodeIdx cur = it.valid() ? it.node(C) : no_node();
     allow_next_grid();
     wait_prior_grid(); // the previous step's populations and node state are complete
-    if (it.valid()) fwd_stage<T, Q, NT>(C, A, cur, s0);
+    if (it.valid()) fwd_stage<T, Q, NT, FwdArgs<T>>(C, A, cur, s0);
     cp_async_commit();
     bool odd = false;
     while (it.valid()) {
         it.next();
         const NodeIdx nxt = it.valid() ? it.node(C) : no_node();
-        if (it.valid()) fwd_stage<T, Q, NT>(C, A, nxt, odd ? s0 : s1);
+        if (it.valid()) fwd_stage<T, Q, NT, FwdArgs<T>>(C, A, nxt, odd ? s0 : s1);
         cp_async_commit();
         cp_async_wait<1>(); // this thread's copies for the current node have landed
-        fwd_compute<T, Q, NT>(C, KC, A, cur, odd ? s1 : s0, acc);
+        fwd_compute<T, Q, NT, FwdArgs<T>>(C, KC, A, cur, odd ? s1 : s0, acc);
         cur = nxt;
         odd = !odd;
     }

@@ -56,6 +56,8 @@ template <typename T> struct FwdArgs {
     T* tape;             // [3][plane] (u^n, G_x^n, G_y^n) or null
     double* gsq_part;    // per-warp partial of sum (g^n)^2 (accumulated over steps), or null
     int n;               // time step index
+    __device__ __forceinline__ const T* in(int j) const { return pin[j]; }
+    __device__ __forceinline__ T* out(int j) const { return pout[j]; }
 };
 
 template <typename T> struct AdjArgs {
@@ -71,6 +73,8 @@ template <typename T> struct AdjArgs {
     double* emax_part;   // per-warp partial of max |E| (accumulated over steps)
     int n;
     int terminal;        // n == N-1: psi^{n+1} is the broadcast seed
+    __device__ __forceinline__ const T* in(int j) const { return rin[j]; }
+    __device__ __forceinline__ T* out(int j) const { return rout[j]; }
 };
 
 struct Launch {

@@ -38,46 +38,7 @@ class Problem:
         self.N = w.N
         self.ctrl_shape = w.ctrl_shape
         dev = self.device
-        f64 = lambda a: None if a is None else torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
-        u8 = lambda a: None if a is None else torch.as_tensor(np.ascontiguousarray(a, dtype=np.uint8), device=dev)
-        keep = {}
-        d = _lib.Desc()
-        d.nx, d.ny, d.n_steps, d.lattice = w.nx, w.ny, w.N, w.Q
-        d.precision = self.precision
-        d.ckpt_every = w.ckpt_every or w.N
-        d.tau = 1.0
-        d.aniso = {"const": _lib.CX_ANISO_CONST, "rotated": _lib.CX_ANISO_ROTATED, "field": _lib.CX_ANISO_FIELD}[w.aniso]
-        d.D_u = (ctypes.c_double * 3)(*w.D_u_const)
-        d.D_v = (ctypes.c_double * 3)(*w.D_v_const)
-        d.lam_u = (ctypes.c_double * 2)(*w.lam_u)
-        d.lam_v = (ctypes.c_double * 2)(*w.lam_v)
-        if w.aniso == "rotated":
-            keep["theta"] = f64(w.theta)
-            d.theta = _ptr(keep["theta"])
-        if w.aniso == "field":
-            keep["Du"], keep["Dv"] = f64(w.D_u_field), f64(w.D_v_field)
-            d.D_u_field, d.D_v_field = _ptr(keep["Du"]), _ptr(keep["Dv"])
-        d.d_u, d.d_v = w.d_u, w.d_v
-        d.chi, d.r_vu, d.r_vv = w.chi, w.r_vu, w.r_vv
-        d.adv = {"none": _lib.CX_ADV_NONE, "row": _lib.CX_ADV_ROW, "field": _lib.CX_ADV_FIELD}[w.adv]
-        if w.adv == "row":
-            keep["a"] = f64(w.a_row)
-        elif w.adv == "field":
-            keep["a"] = f64(w.a_field)
-        d.a = _ptr(keep.get("a"))
-        if w.solid is not None:
-            keep["solid"] = u8(w.solid)
-            d.solid = _ptr(keep["solid"])
-        if w.window is not None:
-            d.ctrl_x0, d.ctrl_y0, d.ctrl_nx, d.ctrl_ny = w.window
-        if w.cmask is not None:
-            keep["cmask"] = u8(w.cmask)
-            d.ctrl_mask = _ptr(keep["cmask"])
-        keep["ut"] = f64(w.u_tgt)
-        d.u_target = _ptr(keep["ut"])
-        d.alpha = w.alpha
-        d.s = (ctypes.c_double * 7)(*w.s)
-        d.source_order = w.source_order
+        d, keep = make_desc(w, dev, self.precision)
         self.desc = d
         self._desc_arrays = keep  # the descriptor's device arrays stay valid with the Problem
         nbytes = ctypes.c_size_t(0)
@@ -193,3 +154,52 @@ class Problem:
             self.close()
         except Exception:
             pass
+
+
+def make_desc(w: Workload, dev, precision=None):
+    """cx_problem_desc for a workload; returns (desc, device arrays it points to).
+
+    The arrays must stay alive while the library may read them (until cx_create
+    or the static forward's queued work has run)."""
+    precision = precision or w.precision
+    f64 = lambda a: None if a is None else torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    u8 = lambda a: None if a is None else torch.as_tensor(np.ascontiguousarray(a, dtype=np.uint8), device=dev)
+    keep = {}
+    d = _lib.Desc()
+    d.nx, d.ny, d.n_steps, d.lattice = w.nx, w.ny, w.N, w.Q
+    d.precision = precision
+    d.ckpt_every = w.ckpt_every or w.N
+    d.tau = 1.0
+    d.aniso = {"const": _lib.CX_ANISO_CONST, "rotated": _lib.CX_ANISO_ROTATED, "field": _lib.CX_ANISO_FIELD}[w.aniso]
+    d.D_u = (ctypes.c_double * 3)(*w.D_u_const)
+    d.D_v = (ctypes.c_double * 3)(*w.D_v_const)
+    d.lam_u = (ctypes.c_double * 2)(*w.lam_u)
+    d.lam_v = (ctypes.c_double * 2)(*w.lam_v)
+    if w.aniso == "rotated":
+        keep["theta"] = f64(w.theta)
+        d.theta = _ptr(keep["theta"])
+    if w.aniso == "field":
+        keep["Du"], keep["Dv"] = f64(w.D_u_field), f64(w.D_v_field)
+        d.D_u_field, d.D_v_field = _ptr(keep["Du"]), _ptr(keep["Dv"])
+    d.d_u, d.d_v = w.d_u, w.d_v
+    d.chi, d.r_vu, d.r_vv = w.chi, w.r_vu, w.r_vv
+    d.adv = {"none": _lib.CX_ADV_NONE, "row": _lib.CX_ADV_ROW, "field": _lib.CX_ADV_FIELD}[w.adv]
+    if w.adv == "row":
+        keep["a"] = f64(w.a_row)
+    elif w.adv == "field":
+        keep["a"] = f64(w.a_field)
+    d.a = _ptr(keep.get("a"))
+    if w.solid is not None:
+        keep["solid"] = u8(w.solid)
+        d.solid = _ptr(keep["solid"])
+    if w.window is not None:
+        d.ctrl_x0, d.ctrl_y0, d.ctrl_nx, d.ctrl_ny = w.window
+    if w.cmask is not None:
+        keep["cmask"] = u8(w.cmask)
+        d.ctrl_mask = _ptr(keep["cmask"])
+    keep["ut"] = f64(w.u_tgt)
+    d.u_target = _ptr(keep["ut"])
+    d.alpha = w.alpha
+    d.s = (ctypes.c_double * 7)(*w.s)
+    d.source_order = w.source_order
+    return d, keep

@@ -214,7 +214,7 @@ def geometry(nx=4096, ny=4096, N=5000, seed=2, precision=32, ckpt_every=100, win
     return replace(w, name="geom", solid=solid, window=window, cmask=cmask)
 
 
-def batch_workloads(n_problems=256, N=1000, seed=3, sizes=(64, 128, 256, 512)):
+def batch_workloads(n_problems=256, N=1000, seed=3, sizes=(64, 128, 256, 512), ckpt_every=100, precision=32):
     """Independent problems for the batched launch."""
     out = []
     for i in range(n_problems):
@@ -227,8 +227,8 @@ def batch_workloads(n_problems=256, N=1000, seed=3, sizes=(64, 128, 256, 512)):
         u0 = bumps(nx, ny, seed + i, sig)
         u_tgt = 1.0 + 0.2 * _periodic_gauss(nx, ny, nx / 2, ny / 2, 2 * sig)
         lam = (0.08, 0.08 / ratio)
-        out.append(Workload(name=f"batch{i}", nx=nx, ny=ny, N=N, Q=9, precision=32, aniso="rotated",
+        out.append(Workload(name=f"batch{i}", nx=nx, ny=ny, N=N, Q=9, precision=precision, aniso="rotated",
                             lam_u=lam, lam_v=lam, theta=np.full((ny, nx), ang), chi=chi,
-                            u0=u0, v0=np.zeros((ny, nx)), u_tgt=u_tgt, alpha=1e-3,
+                            u0=u0, v0=np.zeros((ny, nx)), u_tgt=u_tgt, alpha=1e-3, ckpt_every=ckpt_every,
                             extra=dict(ratio=ratio, angle=ang)))
     return out

@@ -97,3 +97,17 @@ def test_create_rejects_bad_workspace_without_gpu(lib):
     assert so.cx_create(ctypes.byref(_desc(mod)), ctypes.c_void_p(0x1001), 1 << 30, None, ctypes.byref(h)) == 2
     assert so.cx_create(ctypes.byref(_desc(mod)), ctypes.c_void_p(0x1000), 16, None, ctypes.byref(h)) == 2
     assert so.cx_status_string(6) == b"line search failed"
+
+
+def test_batch_descriptors_must_share_schedule(lib):
+    so, mod = lib
+    d = (mod.Desc * 2)(_desc(mod), _desc(mod, nx=40, ny=24))
+    n = ctypes.c_size_t(0)
+    assert so.cx_batch_workspace_size(d, 2, ctypes.byref(n)) == 0
+    single = ctypes.c_size_t(0)
+    assert so.cx_workspace_size(ctypes.byref(d[0]), ctypes.byref(single)) == 0
+    assert n.value > single.value
+    for kw in (dict(n_steps=21), dict(precision=64), dict(lattice=5), dict(ckpt_every=7)):
+        bad = (mod.Desc * 2)(_desc(mod), _desc(mod, **kw))
+        assert so.cx_batch_workspace_size(bad, 2, ctypes.byref(n)) == 1, kw
+    assert so.cx_batch_workspace_size(d, 0, ctypes.byref(n)) == 1

@@ -1,0 +1,129 @@
+"""Batched problems: one persistent launch per step over all problems' tiles,
+replayed as a CUDA graph.  Checked against the oracle per problem, against the
+single-problem path and across tile shapes (same per-node formulas, compiled
+in other kernels: equal to 1e-13), and across graph replays (bitwise)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+from paper_1908_03876_gb300 import workloads as W  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1908_03876_gb300.build import build
+
+    build()
+    oracle.build()
+
+
+def _mixed(precision=64, N=14, k=5):
+    """Uneven sizes, tensors, chemotaxis; one complex-geometry problem."""
+    ws = []
+    for i, (nx, ny) in enumerate([(40, 24), (64, 16), (33, 47), (48, 48), (20, 28)]):
+        w = W.aniso(nx, ny, N, seed=10 + i, precision=precision, ckpt_every=k, chi=-0.02 * (i + 1))
+        w.lam_u = w.lam_v = (0.08, 0.08 / (1 + i))
+        ws.append(w)
+    g = W.geometry(56, 44, N, seed=2, precision=precision, ckpt_every=k, win=24, rmin=3, rmax=7)
+    ws.append(g)
+    return ws
+
+
+def _run_batch(ws, tile_x=None, threads=256):
+    from paper_1908_03876_gb300.batch import Batch
+
+    b = Batch(ws)
+    gs = [torch.as_tensor(w.random_control(50 + i, 0.02), dtype=b.dtype, device=b.device) for i, w in enumerate(ws)]
+    b.bind(gs)
+    if tile_x is not None:
+        b.set_tiles(threads, 0, tile_x)
+    J, e2, emax = b.gradient()
+    b.stream.synchronize()
+    b.status()
+    fields = [b.fields(i) for i in range(len(ws))]
+    torch.cuda.synchronize()
+    return b, gs, J.cpu().numpy().copy(), [E.cpu().numpy().copy() for E in b.E], \
+        [(u.cpu().numpy(), v.cpu().numpy()) for u, v in fields], e2.cpu().numpy().copy()
+
+
+def test_batch_fp64_matches_oracle_per_problem():
+    ws = _mixed()
+    b, gs, J, Es, fields, e2 = _run_batch(ws)
+    for i, w in enumerate(ws):
+        Jo, Eo, _ = oracle.adjoint(oracle.from_workload(w), gs[i].cpu().numpy())
+        eJ = abs(J[i] - Jo) / abs(Jo)
+        eE = np.linalg.norm(Es[i] - Eo) / np.linalg.norm(Eo)
+        print(f"problem {i} ({w.nx}x{w.ny}): J rel {eJ:.1e}, dJ/dg rel L2 {eE:.1e}")
+        assert eJ < 1e-12 and eE < 1e-12
+        assert abs(e2[i] - np.sum(Eo * Eo)) <= 1e-12 * np.sum(Eo * Eo)
+
+
+def _close(a, b, tol=1e-13):
+    a, b = np.asarray(a), np.asarray(b)
+    return np.linalg.norm(a - b) <= tol * np.linalg.norm(b)
+
+
+def test_batch_equals_single_problem():
+    from paper_1908_03876_gb300.problem import Problem
+
+    ws = _mixed(N=9, k=4)
+    b, gs, J, Es, fields, _ = _run_batch(ws)
+    for i, w in enumerate(ws):
+        p = Problem(w)
+        Jp, Ep = p.gradient(gs[i])
+        u, v = p.fields()
+        assert _close(Es[i], Ep.cpu().numpy())
+        assert _close(fields[i][0], u.cpu().numpy()) and _close(fields[i][1], v.cpu().numpy())
+        assert abs(Jp.item() - J[i]) <= 1e-14 * abs(J[i])
+
+
+def test_batch_tile_shapes_and_replay():
+    ws = _mixed(N=9, k=4)
+    _, _, J1, E1, F1, _ = _run_batch(ws, tile_x=[32] * len(ws), threads=256)
+    _, _, J2, E2, F2, _ = _run_batch(ws, tile_x=[64, 128, 32, 64, 32, 128], threads=128)
+    b, gs, J3, E3, F3, _ = _run_batch(ws)
+    J4, _, _ = b.gradient()  # graph replay
+    b.stream.synchronize()
+    for a, c in zip(E1, E2):
+        assert _close(a, c)
+    for a, c in zip(E1, E3):
+        assert _close(a, c)
+    for (u1, v1), (u2, v2) in zip(F1, F2):
+        assert _close(u1, u2) and _close(v1, v2)
+    assert np.allclose(J1, J2, rtol=1e-13, atol=0)
+    assert np.array_equal(J3, J4.cpu().numpy())  # replaying the captured graph is deterministic
+
+
+def test_batch_fp32_against_fp64_oracle():
+    ws = _mixed(precision=32, N=30, k=8)
+    b, gs, J, Es, fields, _ = _run_batch(ws)
+    for i, w in enumerate(ws):
+        Jo, Eo, _ = oracle.adjoint(oracle.from_workload(w), gs[i].double().cpu().numpy())
+        eJ = abs(J[i] - Jo) / abs(Jo)
+        eE = np.linalg.norm(Es[i] - Eo) / np.linalg.norm(Eo)
+        print(f"fp32 problem {i}: J rel {eJ:.1e}, dJ/dg rel L2 {eE:.1e}")
+        assert eJ < 1e-4 and eE < 1e-3
+
+
+def test_autotuner_picks_admissible_config(tmp_path):
+    from paper_1908_03876_gb300 import autotune
+    from paper_1908_03876_gb300.batch import Batch
+
+    ws = [W.aniso(nx, ny, 8, seed=3, precision=32, ckpt_every=8) for nx, ny in [(64, 64), (128, 64), (64, 128)]]
+    cfg = autotune.autotune(ws, probe_steps=6, cache_path=str(tmp_path / "tune.json"))
+    assert cfg["threads"] in (128, 256)
+    for nx, tx in cfg["tile_x"].items():
+        assert cfg["threads"] % tx == 0 and cfg["threads"] // tx <= 8
+    again = autotune.autotune(ws, probe_steps=6, cache_path=str(tmp_path / "tune.json"))
+    assert again["tile_x"] == cfg["tile_x"]
+    b = Batch(ws)
+    b.bind(b.zeros_controls())
+    J0 = b.forward().cpu().numpy().copy()
+    autotune.apply(b, cfg)
+    J1 = b.forward().cpu().numpy()
+    assert np.allclose(J0, J1, rtol=1e-6)
