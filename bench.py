@@ -154,6 +154,112 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args, rank, world, local):
+    """Aggregate MLUPS of many independent problems in one persistent launch per
+    step, replayed as a CUDA graph; problems are sharded over ranks (no
+    collective on the data path)."""
+    import numpy as np
+    import torch
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1908_03876_gb300.build import build
+
+    if rank == 0:
+        build()
+    if dist:
+        dist.barrier()
+    from paper_1908_03876_gb300 import autotune
+    from paper_1908_03876_gb300 import workloads as W
+    from paper_1908_03876_gb300.batch import Batch
+
+    from paper_1908_03876_gb300 import sharding
+
+    allw = W.batch_workloads(args.problems, N=1000, seed=3)
+    mine = sharding.my_problems(allw, rank, world)
+    t0 = time.perf_counter()
+    cfg = autotune.autotune(mine, probe_steps=12, device=dev)
+    t_tune = time.perf_counter() - t0
+    b = Batch(mine, device=dev)
+    gs = [torch.as_tensor(w.random_control(500 + i, 0.01), dtype=torch.float32, device=dev) for i, w in enumerate(mine)]
+    b.bind(gs)
+    autotune.apply(b, cfg)
+    nodes = sum(w.nx * w.ny for w in mine)
+    N = mine[0].N
+    for _ in range(args.warmup):
+        b.gradient()
+    torch.cuda.synchronize()
+    clocks = Clocks()
+    if rank == 0:
+        clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(b.stream)
+    for _ in range(args.steps):
+        b.gradient()
+    e1.record(b.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    clk = clocks.stop(local) if rank == 0 else None
+    b.status()
+    ms, all_nodes = sharding.aggregate(ms, float(nodes))
+    mlups = all_nodes * N / (ms * 1e-3) / 1e6
+    hbm, peak_kind = _peaks()
+    k = mine[0].ckpt_every
+    byts = all_nodes * (N * BYTES["forward"] + (N - k) * BYTES["recompute"] + N * BYTES["adjoint"])
+    ach = byts / (ms * 1e-3) / world / 1e9
+    b.close()
+    del gs
+    torch.cuda.empty_cache()
+    # per-problem gradient error against the FP64 oracle on a sample
+    err = []
+    if rank == 0:
+        import oracle
+
+        oracle.build()
+        sample = [W.batch_workloads(args.problems, N=6, seed=3, ckpt_every=3)[i] for i in (0, 1, 2, 3, 5, 8)]
+        sb = Batch(sample, device=dev)
+        sg = [torch.as_tensor(w.random_control(700 + i, 0.01), dtype=torch.float32, device=dev)
+              for i, w in enumerate(sample)]
+        sb.bind(sg)
+        autotune.apply(sb, {"threads": cfg["threads"], "tile_x": {w.nx: cfg["tile_x"].get(w.nx, 64) for w in sample}})
+        sb.gradient()
+        torch.cuda.synchronize()
+        for i, w in enumerate(sample):
+            _, Eo, _ = oracle.adjoint(oracle.from_workload(w), sg[i].double().cpu().numpy())
+            E = sb.E[i].double().cpu().numpy()
+            err.append(float(np.linalg.norm(E - Eo) / np.linalg.norm(Eo)))
+    if rank == 0:
+        line = {
+            "metric": "fwd+adjoint MLUPS (batched)", "value": mlups, "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 reductions)", "data": "synthetic (seeded)",
+            "config": {"workload": f"batch: {args.problems} problems, nx, ny in {{64,128,256,512}}, 1000 steps, "
+                                   "checkpoint every 100, one persistent launch per step, CUDA graph",
+                       "nodes": all_nodes, "tiles": cfg, "autotune_s": t_tune,
+                       "l2": "inputs larger than L2"},
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                         "traffic": None, "kernel": "k_batch (all lattice launches of the step)",
+                         "peak_source": peak_kind},
+            "per_problem_grad_rel_err_fp32_vs_oracle": {"sample": "6 problems, 6 steps", "max": max(err),
+                                                        "values": err},
+            "clocks": clk, "e2e": None,
+            # per gradient: N forward + one final per problem + finalize, zero sigma, S-2 Phi restores,
+            # N-k recompute, N adjoint, finalize
+            "gpu_launches": args.steps * (N + len(mine) + 1 + 1 + max(0, N // k - 2) + (N - k) + N + 1),
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -161,6 +267,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="aniso1024", choices=["aniso1024", "batch"],
+                    help="aniso1024 (default bench line) or batch: 256 independent problems, sizes {64..512}^2, "
+                         "1000 steps, one persistent launch per step replayed as a CUDA graph")
+    ap.add_argument("--problems", type=int, default=256)
     ap.add_argument("--profile", action="store_true",
                     help="small profiling case: the same 1024x1024 lattice, 20 time steps, k = 10, "
                          "one warm-up and one timed gradient evaluation, no CPU baseline or e2e leg")
@@ -174,6 +284,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "batch":
+        run_batch(args, rank, world, local)
         return
 
     import numpy as np
