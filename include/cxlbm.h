@@ -92,6 +92,9 @@ typedef struct {
     double alpha;             /* control penalty weight, >= 0                        */
     double s[7];              /* free relaxation rates s0..s6 of Pi, in (0, 2)       */
     int source_order;         /* 2: keep (tau/2)(Phi^n - Phi^{n-1}); 1: drop it      */
+    int ctrl_windows;         /* W: g piecewise constant in time over W equal windows
+                                 (g^n = G_{n/(N/W)}, W divides N); 0: one value per
+                                 step (W = N).  Controls and gradients are [W][ctrl]. */
 } cx_problem_desc;
 
 typedef struct cx_problem cx_problem; /* opaque, library-owned host object */
@@ -123,8 +126,8 @@ cx_status cx_create(const cx_problem_desc* desc, void* workspace, size_t bytes, 
  * the initial condition of the forward solve.  Errors: CX_ERR_INVALID_ARG. */
 cx_status cx_set_initial(cx_problem* p, const void* u0, const void* v0);
 
-/* Forward MRT solve over N steps with control g (device T [N][ctrl_ny][ctrl_nx])
- * (step 2 of the discrete-adjoint algorithm, Sec. 3.2.1).  Stores every k-th
+/* Forward MRT solve over N steps with control g (device T [W][ctrl_ny][ctrl_nx],
+ * W = ctrl_windows or N, or NULL for zero control) (step 2 of the discrete-adjoint algorithm, Sec. 3.2.1).  Stores every k-th
  * state as a checkpoint and the last segment's adjoint tape, then writes the
  * FP64 cost J to J_dev (device double, may be NULL).  Needs cx_set_initial.
  * Errors: CX_ERR_STATE (no initial state), CX_ERR_INVALID_ARG, CX_ERR_CUDA. */
@@ -136,9 +139,11 @@ cx_status cx_forward(cx_problem* p, const void* g, double* J_dev);
  * g must be the control of the preceding cx_forward.  seed_u / seed_v
  * (device T [ny][nx]) are the adjoint of u^N / v^N; seed_u == NULL uses
  * u^N - u_target (the cost's own terminal term), seed_v == NULL uses 0.
- * Writes dJdg (device T [N][ctrl_ny][ctrl_nx]): the gradient of
+ * Writes dJdg (device T [W][ctrl_ny][ctrl_nx]): the gradient of
  * sum(seed_u u^N + seed_v v^N) + alpha ||g||^2 -- of J itself when both seeds
- * are NULL -- with zeros at uncontrolled nodes.
+ * are NULL -- with zeros at uncontrolled nodes.  With time windows, the
+ * gradient of window w is the sum of the per-step gradients over its steps
+ * (the penalty alpha sum_n ||g^n||^2 counts each window N/W times).
  * Errors: CX_ERR_STATE (no forward since the last cx_create / cx_set_initial). */
 cx_status cx_adjoint(cx_problem* p, const void* g, const void* seed_u, const void* seed_v, void* dJdg);
 
@@ -149,7 +154,7 @@ cx_status cx_gradient(cx_problem* p, const void* g, void* dJdg, double* J_dev);
 /* One steepest-descent iteration with Armijo backtracking (step 5 of the
  * algorithm; first trial min(1, 1/||E||_inf), the heuristic of the remark
  * after the continuous gradient algorithm, then twice the previous step).
- * g_inout (device T [N][ctrl_ny][ctrl_nx]) is updated in place to g - lam E
+ * g_inout (device T [W][ctrl_ny][ctrl_nx]) is updated in place to g - lam E
  * when J(g - lam E) <= J(g) - 1e-4 lam ||E||^2 (FP64 test); lam halves up to
  * 30 times.  E_work (device T, same shape, caller-owned) receives the
  * gradient E = dJ/dg at the incoming g.  Runs a forward first unless the
@@ -204,7 +209,7 @@ cx_status cx_batch_create(const cx_problem_desc* descs, int count, void* workspa
                           cudaStream_t stream, cx_batch** out);
 /* u0[i], v0[i]: device T [ny_i][nx_i] (host arrays of device pointers). */
 cx_status cx_batch_set_initial(cx_batch* b, const void* const* u0, const void* const* v0);
-/* Controls g[i] (device T [N][ctrl], NULL entries: zero control) and gradient
+/* Controls g[i] (device T [W][ctrl], NULL entries: zero control) and gradient
  * outputs dJdg[i] (device T, may be NULL for forward-only use); host arrays.
  * Synchronous (uploads the problem table). */
 cx_status cx_batch_bind(cx_batch* b, const void* const* g, void* const* dJdg);
@@ -221,7 +226,61 @@ cx_status cx_batch_gradient(cx_batch* b, double* out_dev);
 cx_status cx_batch_get_fields(cx_batch* b, int i, void* u_out, void* v_out);
 /* Synchronising: CX_ERR_UNSTABLE if any problem's J or gradient was non-finite. */
 cx_status cx_batch_get_status(cx_batch* b);
+/* Switch problems on (enabled[i] != 0) or off for every later forward,
+ * gradient and step (NULL: all on).  Switched-off problems cost no lattice
+ * work; their outputs, fields and gradients are undefined until they are
+ * switched on and evaluated again.  Synchronous. */
+cx_status cx_batch_set_enabled(cx_batch* b, const int* enabled);
+/* One steepest-descent iteration with Armijo backtracking for every enabled
+ * problem, each with the rule of cx_step (its own step length and history):
+ * the bound g[i] are updated in place, the bound dJdg[i] receive the
+ * gradients at the incoming controls.  Each line-search trial is one batched
+ * forward over the problems still searching.  The AMRT gradient reuses the
+ * accepted trials' forward state when the previous step accepted every
+ * problem.  info (host, count entries, may be NULL) as for cx_step (trials = 0
+ * for switched-off or stationary problems); status (host int [count], may be
+ * NULL): CX_OK, CX_ERR_LINESEARCH (no accepted trial: g[i] unchanged) or
+ * CX_ERR_UNSTABLE per problem.  Every bound g[i] and dJdg[i] must be non-NULL.
+ * Synchronous.  Errors: CX_ERR_STATE (no initial state or binding),
+ * CX_ERR_INVALID_ARG, CX_ERR_CUDA. */
+cx_status cx_batch_step(cx_batch* b, cx_step_info* info, int* status);
 cx_status cx_batch_destroy(cx_batch* b);
+
+/* ------------------------------------------------------------------------
+ * Warm-start surrogate kernels.  (No counterpart in the paper: a small
+ * convolutional network proposes the initial control that the paper's
+ * gradient algorithm then refines.)  Tensors are NCHW; uint16_t* arguments are
+ * BF16 device arrays, float* FP32 device arrays; every call is asynchronous
+ * on `stream`.  Convolutions are 3x3 with zero padding 1 or 1x1 (ks), as
+ * implicit GEMMs on the tensor cores with FP32 accumulation.
+ * Errors: CX_ERR_INVALID_ARG for inconsistent shapes or NULL arguments,
+ * CX_ERR_CUDA on a launch failure. */
+/* y[B][Cout][H][W] = act(bias + conv(x[B][Cin][H][W], w[Cout][Cin][ks][ks])); act = ReLU if relu. bias may be NULL. */
+cx_status cx_nn_conv_forward(const uint16_t* x, const uint16_t* w, const float* bias, uint16_t* y, int B, int Cin,
+                             int Cout, int H, int W, int ks, int relu, cudaStream_t stream);
+/* dx = gradient w.r.t. x of sum(dy * conv(x, w)); w_flip: scratch of Cout*Cin*ks*ks BF16. */
+cx_status cx_nn_conv_backward_data(const uint16_t* dy, const uint16_t* w, uint16_t* dx, uint16_t* w_flip, int B,
+                                   int Cin, int Cout, int H, int W, int ks, cudaStream_t stream);
+/* FP32 scratch bytes for cx_nn_conv_backward_weight with `splits` pixel ranges. */
+size_t cx_nn_conv_backward_weight_scratch(int B, int Cin, int Cout, int H, int W, int ks, int splits);
+/* dw[Cout][Cin][ks][ks] (FP32) and db[Cout] (FP32, may be NULL): gradients of sum(dy * conv). */
+cx_status cx_nn_conv_backward_weight(const uint16_t* x, const uint16_t* dy, float* dw, float* db, float* scratch,
+                                     int splits, int B, int Cin, int Cout, int H, int W, int ks,
+                                     cudaStream_t stream);
+/* dz = dy where y > 0, else 0 (y = ReLU output). */
+cx_status cx_nn_relu_backward(const uint16_t* y, const uint16_t* dy, uint16_t* dz, size_t n, cudaStream_t stream);
+cx_status cx_nn_add(const uint16_t* a, const uint16_t* b, uint16_t* out, size_t n, cudaStream_t stream);
+/* 2x2 average pooling of [BC][H][W] (H, W even); backward: in = dY [BC][H/2][W/2], out = dX [BC][H][W]. */
+cx_status cx_nn_pool2(const uint16_t* in, uint16_t* out, int BC, int H, int W, int backward, cudaStream_t stream);
+/* nearest 2x upsampling of [BC][H][W]; backward: in = dY [BC][2H][2W], out = dX [BC][H][W]. */
+cx_status cx_nn_up2(const uint16_t* in, uint16_t* out, int BC, int H, int W, int backward, cudaStream_t stream);
+/* loss (device double, may be NULL) = mean((out - target)^2); dout (may be NULL) = its gradient. */
+cx_status cx_nn_mse(const uint16_t* out, const float* target, uint16_t* dout, double* loss, size_t n,
+                    cudaStream_t stream);
+/* Adam step t >= 1 on FP32 master weights p (moments m, v), writing the BF16 copy p_bf16. */
+cx_status cx_nn_adam(float* p, float* m, float* v, const float* g, uint16_t* p_bf16, size_t n, float lr, float b1,
+                     float b2, float eps, int t, cudaStream_t stream);
+cx_status cx_nn_cast_bf16(const float* in, uint16_t* out, size_t n, cudaStream_t stream);
 
 /* ------------------------------------------------------------------------
  * Forward solve without any device allocation.  (No counterpart in the paper:
@@ -241,7 +300,7 @@ cx_status cx_batch_destroy(cx_batch* b);
  *   desc     as for cx_create; its device arrays, like u0, v0 and g, are read
  *            by work queued on `stream` and must stay valid until it completes
  *   u0, v0   device T [ny][nx] initial fields
- *   g        device T [N][ctrl_ny][ctrl_nx] control, or NULL (zero control)
+ *   g        device T [W][ctrl_ny][ctrl_nx], W = ctrl_windows or N control, or NULL (zero control)
  *   J_dev    device double: the cost J (may be NULL)
  *   uN, vN   device T [ny][nx]: u^N, v^N (either may be NULL)
  *   stream   the stream every operation is ordered on; asynchronous

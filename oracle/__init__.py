@@ -119,12 +119,30 @@ class Problem:
     s: tuple = (1.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0)
     source_order: int = 2
     tau: float = 1.0
+    windows: int = 0
     _keep: list = field(default_factory=list, repr=False)
 
     @property
     def ctrl_shape(self):
         w = self.window or (0, 0, self.nx, self.ny)
-        return (self.N, w[3], w[2])
+        return (self.windows or self.N, w[3], w[2])
+
+    # Time-windowed controls (windows = W > 0): the control is restricted to
+    # the subspace g^n = G_{n // (N/W)} of the paper's space-time controls.
+    # Every solve runs on the expanded per-step control P G; the gradient on
+    # the subspace is the adjoint of P applied to the per-step gradient, i.e.
+    # the sum of dJ/dg^n over the steps of each window.
+    def expand(self, g):
+        if g is None or not self.windows:
+            return g
+        g = np.asarray(g, dtype=np.float64)
+        return np.repeat(g, self.N // self.windows, axis=0)
+
+    def restrict_gradient(self, dJdg_steps):
+        if not self.windows:
+            return dJdg_steps
+        L = self.N // self.windows
+        return dJdg_steps.reshape((self.windows, L) + dJdg_steps.shape[1:]).sum(axis=1)
 
     def _struct(self):
         arrs = dict(
@@ -159,7 +177,7 @@ def forward(p: Problem, g=None):
     """Forward MRT solve.  Returns (J, u^N, v^N)."""
     lib = _load()
     st = p._struct()
-    g = _f64(g)
+    g = _f64(p.expand(g))
     J = ctypes.c_double(0.0)
     uN = np.zeros((p.ny, p.nx))
     vN = np.zeros((p.ny, p.nx))
@@ -172,7 +190,7 @@ def forward_trace(p: Problem, g=None):
     lib = _load()
     st = p._struct()
     mu, mv, sp = np.zeros(p.N), np.zeros(p.N), np.zeros(p.N)
-    _check(lib.or_forward_trace(ctypes.byref(st), _ptr(_f64(g)), _ptr(mu), _ptr(mv), _ptr(sp)), "trace")
+    _check(lib.or_forward_trace(ctypes.byref(st), _ptr(_f64(p.expand(g))), _ptr(mu), _ptr(mv), _ptr(sp)), "trace")
     return mu, mv, sp
 
 
@@ -180,7 +198,7 @@ def tlm(p: Problem, g, dg, df0=None):
     """Tangent-linear model.  Returns (dJ, du^N, dv^N)."""
     lib = _load()
     st = p._struct()
-    g, dg, df0 = _f64(g), _f64(dg), _f64(df0)
+    g, dg, df0 = _f64(p.expand(g)), _f64(p.expand(dg)), _f64(df0)
     dJ = ctypes.c_double(0.0)
     du = np.zeros((p.ny, p.nx))
     dv = np.zeros((p.ny, p.nx))
@@ -189,16 +207,17 @@ def tlm(p: Problem, g, dg, df0=None):
 
 
 def adjoint(p: Problem, g=None, seed_u=None, seed_v=None, want_psi0=False):
-    """AMRT adjoint sweep.  Returns (J, dJ/dg [N, cny, cnx], psi0 [ny, nx, 2, Q] or None)."""
+    """AMRT adjoint sweep.  Returns (J, dJ/dg [W or N, cny, cnx], psi0 [ny, nx, 2, Q] or None)."""
     lib = _load()
     st = p._struct()
-    g, su, sv = _f64(g), _f64(seed_u), _f64(seed_v)
-    dJdg = np.zeros(p.ctrl_shape)
+    g, su, sv = _f64(p.expand(g)), _f64(seed_u), _f64(seed_v)
+    w = p.window or (0, 0, p.nx, p.ny)
+    dJdg = np.zeros((p.N, w[3], w[2]))
     psi0 = np.zeros((p.ny, p.nx, 2, p.Q)) if want_psi0 else None
     J = ctypes.c_double(0.0)
     _check(lib.or_adjoint(ctypes.byref(st), _ptr(g), _ptr(su), _ptr(sv), _ptr(dJdg), _ptr(psi0),
                           ctypes.byref(J)), "adjoint")
-    return J.value, dJdg, psi0
+    return J.value, p.restrict_gradient(dJdg), psi0
 
 
 def lattice(Q: int):
@@ -258,4 +277,4 @@ def from_workload(w, N=None) -> Problem:
     return Problem(nx=w.nx, ny=w.ny, N=w.N if N is None else N, Q=w.Q, Du=Du, Dv=Dv, u0=w.u0, v0=w.v0,
                    u_tgt=w.u_tgt, d_u=w.d_u, d_v=w.d_v, chi=w.chi, r_vu=w.r_vu, r_vv=w.r_vv,
                    a=w.a_fields(), solid=w.solid, window=w.window, cmask=w.cmask, alpha=w.alpha,
-                   s=tuple(w.s), source_order=w.source_order)
+                   s=tuple(w.s), source_order=w.source_order, windows=w.windows)

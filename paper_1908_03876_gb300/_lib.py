@@ -25,6 +25,10 @@ EXPORTS = [
     "cx_destroy", "cx_status_string", "cx_forward_static",
     "cx_batch_workspace_size", "cx_batch_create", "cx_batch_set_initial", "cx_batch_bind", "cx_batch_set_tiles",
     "cx_batch_forward", "cx_batch_gradient", "cx_batch_get_fields", "cx_batch_get_status", "cx_batch_destroy",
+    "cx_batch_set_enabled", "cx_batch_step",
+    "cx_nn_conv_forward", "cx_nn_conv_backward_data", "cx_nn_conv_backward_weight_scratch",
+    "cx_nn_conv_backward_weight", "cx_nn_relu_backward", "cx_nn_add", "cx_nn_pool2", "cx_nn_up2", "cx_nn_mse",
+    "cx_nn_adam", "cx_nn_cast_bf16",
 ]
 STATIC_SCRATCH_BYTES = 32 << 20  # CX_STATIC_SCRATCH_BYTES of include/cxlbm.h
 
@@ -52,6 +56,7 @@ class Desc(ctypes.Structure):
         ("u_target", ctypes.c_void_p), ("alpha", ctypes.c_double),
         ("s", ctypes.c_double * 7),
         ("source_order", ctypes.c_int),
+        ("ctrl_windows", ctypes.c_int),
     ]
 
 
@@ -101,11 +106,26 @@ def load():
         "cx_batch_get_fields": [vp, cint, vp, vp],
         "cx_batch_get_status": [vp],
         "cx_batch_destroy": [vp],
+        "cx_batch_set_enabled": [vp, vp],
+        "cx_batch_step": [vp, ctypes.POINTER(StepInfo), vp],
+        "cx_nn_conv_forward": [vp, vp, vp, vp, cint, cint, cint, cint, cint, cint, cint, vp],
+        "cx_nn_conv_backward_data": [vp, vp, vp, vp, cint, cint, cint, cint, cint, cint, vp],
+        "cx_nn_conv_backward_weight": [vp, vp, vp, vp, vp, cint, cint, cint, cint, cint, cint, cint, vp],
+        "cx_nn_relu_backward": [vp, vp, vp, ctypes.c_size_t, vp],
+        "cx_nn_add": [vp, vp, vp, ctypes.c_size_t, vp],
+        "cx_nn_pool2": [vp, vp, cint, cint, cint, cint, vp],
+        "cx_nn_up2": [vp, vp, cint, cint, cint, cint, vp],
+        "cx_nn_mse": [vp, vp, vp, vp, ctypes.c_size_t, vp],
+        "cx_nn_adam": [vp, vp, vp, vp, vp, ctypes.c_size_t, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                       ctypes.c_float, cint, vp],
+        "cx_nn_cast_bf16": [vp, vp, ctypes.c_size_t, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
         f.argtypes = args
         f.restype = cint
+    lib.cx_nn_conv_backward_weight_scratch.argtypes = [cint] * 7
+    lib.cx_nn_conv_backward_weight_scratch.restype = ctypes.c_size_t
     lib.cx_status_string.argtypes = [cint]
     lib.cx_status_string.restype = ctypes.c_char_p
     _lib = lib

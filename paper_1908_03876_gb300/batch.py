@@ -98,6 +98,26 @@ class Batch:
         self._leave()
         return self.out[: self.count], self.out[self.count: 2 * self.count], self.out[2 * self.count:]
 
+    def step(self):
+        """One Armijo gradient-descent iteration of every enabled problem: the
+        bound controls are updated in place, self.E holds the gradients at the
+        incoming controls.  Returns (info, status): per-problem dicts (J0, J,
+        lam, grad_sq, grad_inf, trials) and cx_status codes."""
+        info = (_lib.StepInfo * self.count)()
+        st = (ctypes.c_int * self.count)()
+        self._enter()
+        _lib.check(self.lib.cx_batch_step(self.h, info, st), "cx_batch_step")
+        self._leave()
+        out = [dict(J0=x.J0, J=x.J, lam=x.lam, grad_sq=x.grad_sq, grad_inf=x.grad_inf, trials=x.trials)
+               for x in info]
+        return out, list(st)
+
+    def set_enabled(self, mask=None):
+        """Switch problems on/off (sequence of bools, None: all on)."""
+        arr = None if mask is None else (ctypes.c_int * self.count)(*[1 if m else 0 for m in mask])
+        self._enter()
+        _lib.check(self.lib.cx_batch_set_enabled(self.h, arr), "cx_batch_set_enabled")
+
     def fields(self, i):
         w = self.ws_list[i]
         u = torch.empty((w.ny, w.nx), dtype=self.dtype, device=self.device)

@@ -139,9 +139,10 @@ __device__ __forceinline__ void adj_compute(const CxConst& C, const KConst<T>& K
     adj_Tv += KC.r_vv * adj_Phi;
 
     if (nd.ctrl) {
-        const T E = adj_Phi + KC.two_alpha * gv;
+        T E = adj_Phi + KC.two_alpha * gv;
+        if (A.accum) E += A.dJdg[nd.c]; // chain rule of g^n = G_w: sum over the window's steps
         A.dJdg[nd.c] = E;
-        acc.add(E);
+        if (A.norm) acc.add(E);
     } else if (nd.c >= 0) {
         A.dJdg[nd.c] = T(0);
     }

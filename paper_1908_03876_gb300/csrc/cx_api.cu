@@ -38,6 +38,9 @@ static cx_status validate(const cx_problem_desc* d) {
     for (int i = 0; i < 7; ++i)
         if (!(d->s[i] > 0.0 && d->s[i] < 2.0)) return CX_ERR_INVALID_ARG;
     if (d->source_order != 1 && d->source_order != 2) return CX_ERR_INVALID_ARG;
+    if (d->ctrl_windows < 0 || d->ctrl_windows > d->n_steps ||
+        (d->ctrl_windows > 0 && d->n_steps % d->ctrl_windows != 0))
+        return CX_ERR_INVALID_ARG;
     if (d->aniso == CX_ANISO_ROTATED && !d->theta) return CX_ERR_INVALID_ARG;
     if (d->aniso == CX_ANISO_FIELD && (!d->D_u_field || !d->D_v_field)) return CX_ERR_INVALID_ARG;
     if (d->aniso < 0 || d->aniso > 2 || d->adv < 0 || d->adv > 2) return CX_ERR_INVALID_ARG;
@@ -60,6 +63,8 @@ Layout cx::make_layout(const cx_problem_desc* d) {
     L.N = d->n_steps;
     L.k = d->ckpt_every > 0 ? std::min(d->ckpt_every, d->n_steps) : d->n_steps;
     L.S = (L.N + L.k - 1) / L.k;
+    L.nwin = d->ctrl_windows > 0 ? d->ctrl_windows : d->n_steps;
+    L.win_len = L.N / L.nwin;
     L.plane = up((size_t)d->nx * d->ny, 64);
     const int cnx = d->ctrl_nx > 0 ? d->ctrl_nx : d->nx, cny = d->ctrl_nx > 0 ? d->ctrl_ny : d->ny;
     L.nctrl = (size_t)cnx * cny;
@@ -178,8 +183,8 @@ template <typename T> static cx_status run_forward(cx_problem* p, const T* g, co
         set_planes(p, A.pin, in);
         set_planes(p, A.pout, out);
         A.phi = phi;
-        A.g = g ? g + (size_t)n * Ly.nctrl : nullptr;
-        A.E = E ? E + (size_t)n * Ly.nctrl : nullptr;
+        A.g = g ? g + (size_t)(n / Ly.win_len) * Ly.nctrl : nullptr;
+        A.E = E ? E + (size_t)(n / Ly.win_len) * Ly.nctrl : nullptr;
         A.lam = T(lam);
         A.tape = (seg == Ly.S - 1) ? reinterpret_cast<T*>(p->tape_slot(n - seg * Ly.k)) : nullptr;
         A.gsq_part = gsq;
@@ -230,7 +235,7 @@ static cx_status run_adjoint(cx_problem* p, const T* g, const T* seed_u, const T
                 set_planes(p, A.pout, out);
                 A.phi = phi;
                 A.phi_ckpt = nullptr;
-                A.g = g ? g + (size_t)n * Ly.nctrl : nullptr;
+                A.g = g ? g + (size_t)(n / Ly.win_len) * Ly.nctrl : nullptr;
                 A.tape = reinterpret_cast<T*>(p->tape_slot(n - n0));
                 A.gsq_part = nullptr;
                 A.n = n;
@@ -251,8 +256,10 @@ static cx_status run_adjoint(cx_problem* p, const T* g, const T* seed_u, const T
             A.wv = seed_v;
             A.tape = reinterpret_cast<const T*>(p->tape_slot(n - n0));
             A.sigma = sigma;
-            A.g = g ? g + (size_t)n * Ly.nctrl : nullptr;
-            A.dJdg = dJdg + (size_t)n * Ly.nctrl;
+            A.g = g ? g + (size_t)(n / Ly.win_len) * Ly.nctrl : nullptr;
+            A.dJdg = dJdg + (size_t)(n / Ly.win_len) * Ly.nctrl;
+            A.accum = (n % Ly.win_len) != Ly.win_len - 1; // the reverse sweep meets a window's last step first
+            A.norm = (n % Ly.win_len) == 0;
             A.e2_part = e2;
             A.emax_part = emax;
             A.n = n;
@@ -304,7 +311,7 @@ template <typename T> static cx_status run_step(cx_problem* p, T* g, T* E, cx_st
         if (rc) return rc;
         const double Jt = j4[0];
         if (std::isfinite(Jt) && Jt <= J0 - 1e-4 * lam * e2) {
-            CX_CUDA(launch_axpy<T>(g, E, T(lam), (size_t)p->lay.N * p->lay.nctrl, p->stream));
+            CX_CUDA(launch_axpy<T>(g, E, T(lam), (size_t)p->lay.nwin * p->lay.nctrl, p->stream));
             p->fwd_valid = true; // the accepted trial's forward state is the new control's
             p->adj_valid = false;
             p->lam_prev = lam;

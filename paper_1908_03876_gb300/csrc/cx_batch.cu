@@ -42,6 +42,8 @@ template <typename T> struct BRec {
     const T* g;      // [N][nctrl] or null
     T* dJdg;         // [N][nctrl] or null
     long long plane, nctrl, pop_elems;
+    int win_len;     // steps per control window (1: one control per step)
+    int nwin;        // control windows
     int tile0;       // first global tile of this problem
     int tx, ty;      // tile shape (tx * ty = NT)
     int tiles_x;
@@ -56,6 +58,7 @@ struct BStep {
     int tape_slot;     // -1: none
     int want_sum;      // accumulate the sum of squares (g for the forward, E for the adjoint)
     int terminal;
+    int trial;         // forward at the line-search trial g - lam_p dJ/dg (per-problem lam_p)
 };
 
 template <typename T> __device__ __forceinline__ T* role_ptr(const BRec<T>& R, int role, int slot) {
@@ -89,20 +92,24 @@ template <typename T> struct BAdjArgs {
     T* dJdg;
     int n;
     int terminal;
+    int accum;
+    int norm;
     __device__ __forceinline__ const T* in(int j) const { return rinb + (size_t)j * pl; }
     __device__ __forceinline__ T* out(int j) const { return routb + (size_t)j * pl; }
 };
 
-template <typename T> __device__ __forceinline__ BFwdArgs<T> fwd_args(const BRec<T>& R, const BStep& st) {
+template <typename T>
+__device__ __forceinline__ BFwdArgs<T> fwd_args(const BRec<T>& R, const BStep& st, const T* lam, int p) {
     BFwdArgs<T> A;
     A.inb = role_ptr(R, st.in_role, st.in_slot);
     A.outb = role_ptr(R, st.out_role, st.out_slot);
     A.pl = R.plane;
     A.phi = R.phi;
     A.phi_ckpt = st.phi_ckpt_slot >= 0 ? R.ckpt_phi + (size_t)st.phi_ckpt_slot * R.plane : nullptr;
-    A.g = R.g ? R.g + (size_t)st.n * R.nctrl : nullptr;
-    A.E = nullptr;
-    A.lam = T(0);
+    const size_t w = (size_t)(st.n / R.win_len) * R.nctrl;
+    A.g = R.g ? R.g + w : nullptr;
+    A.E = st.trial ? R.dJdg + w : nullptr;
+    A.lam = st.trial ? lam[p] : T(0);
     A.tape = st.tape_slot >= 0 ? R.tape + (size_t)st.tape_slot * 3 * R.plane : nullptr;
     A.n = st.n;
     return A;
@@ -117,10 +124,13 @@ template <typename T> __device__ __forceinline__ BAdjArgs<T> adj_args(const BRec
     A.wv = nullptr;
     A.tape = R.tape + (size_t)st.tape_slot * 3 * R.plane;
     A.sigma = R.sigma;
-    A.g = R.g ? R.g + (size_t)st.n * R.nctrl : nullptr;
-    A.dJdg = R.dJdg + (size_t)st.n * R.nctrl;
+    const size_t w = (size_t)(st.n / R.win_len) * R.nctrl;
+    A.g = R.g ? R.g + w : nullptr;
+    A.dJdg = R.dJdg + w;
     A.n = st.n;
     A.terminal = st.terminal;
+    A.accum = (st.n % R.win_len) != R.win_len - 1;
+    A.norm = (st.n % R.win_len) == 0;
     return A;
 }
 
@@ -158,7 +168,8 @@ template <typename T> __device__ __forceinline__ NodeIdx tile_node(const BRec<T>
 
 template <typename T, int Q, int NT, bool ADJ>
 __global__ void __launch_bounds__(NT) k_batch(const BRec<T>* __restrict__ recs, const int* __restrict__ tile0, int count,
-                                              int total, BStep st, double* sum_slots, double* max_slots) {
+                                              int total, BStep st, double* sum_slots, double* max_slots,
+                                              const int* __restrict__ active, const T* __restrict__ lam) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int NV = ADJ ? 2 * Q + 6 : 2 * Q + 4;
     int* sh_tile0 = reinterpret_cast<int*>(smem_raw + (size_t)2 * NV * NT * sizeof(T));
@@ -169,28 +180,38 @@ __global__ void __launch_bounds__(NT) k_batch(const BRec<T>* __restrict__ recs, 
     allow_next_grid();
     wait_prior_grid();
 
-    int t = blockIdx.x;
-    int p = t < total ? find_problem(sh_tile0, count, t) : 0;
+    // this block's tiles are blockIdx.x, blockIdx.x + G, ...; tiles of
+    // problems switched off in `active` are skipped (a whole problem at once)
+    const int G = gridDim.x;
+    auto next_live = [&](int tt, int& q) -> int {
+        while (tt < total) {
+            q = find_problem(sh_tile0, count, tt);
+            if (__ldg(active + q)) return tt;
+            tt += ((sh_tile0[q + 1] - tt + G - 1) / G) * G;
+        }
+        return total;
+    };
+    int p = 0;
+    int t = next_live(blockIdx.x, p);
     NodeIdx cur = t < total ? tile_node(recs[p], t - sh_tile0[p]) : no_node();
     if (t < total) {
         if constexpr (ADJ)
             adj_stage<T, Q, NT>(recs[p].C, adj_args(recs[p], st), cur, s0);
         else
-            fwd_stage<T, Q, NT>(recs[p].C, fwd_args(recs[p], st), cur, s0);
+            fwd_stage<T, Q, NT>(recs[p].C, fwd_args(recs[p], st, lam, p), cur, s0);
     }
     cp_async_commit();
     bool odd = false;
     while (t < total) {
-        const int tn = t + gridDim.x;
         int pn = 0;
+        const int tn = next_live(t + G, pn);
         NodeIdx nxt = no_node();
         if (tn < total) {
-            pn = find_problem(sh_tile0, count, tn);
             nxt = tile_node(recs[pn], tn - sh_tile0[pn]);
             if constexpr (ADJ)
                 adj_stage<T, Q, NT>(recs[pn].C, adj_args(recs[pn], st), nxt, odd ? s0 : s1);
             else
-                fwd_stage<T, Q, NT>(recs[pn].C, fwd_args(recs[pn], st), nxt, odd ? s0 : s1);
+                fwd_stage<T, Q, NT>(recs[pn].C, fwd_args(recs[pn], st, lam, pn), nxt, odd ? s0 : s1);
         }
         cp_async_commit();
         cp_async_wait<1>();
@@ -199,7 +220,7 @@ __global__ void __launch_bounds__(NT) k_batch(const BRec<T>* __restrict__ recs, 
         if constexpr (ADJ)
             adj_compute<T, Q, NT>(R.C, R.K, adj_args(R, st), cur, odd ? s1 : s0, acc);
         else
-            fwd_compute<T, Q, NT>(R.C, R.K, fwd_args(R, st), cur, odd ? s1 : s0, acc);
+            fwd_compute<T, Q, NT>(R.C, R.K, fwd_args(R, st, lam, p), cur, odd ? s1 : s0, acc);
         if (st.want_sum) {
             const int slot = R.slot0 + (t - sh_tile0[p]) * (NT >> 5) + ((int)threadIdx.x >> 5);
             acc.flush(sum_slots + slot, max_slots ? max_slots + slot : nullptr);
@@ -221,8 +242,9 @@ struct BFin {
     double alpha;
 };
 __global__ void __launch_bounds__(256) k_bfinalize(const BFin* fin, const double* sums, const double* maxs, int mode,
-                                                    double* out_a, double* out_b, int* status) {
+                                                    double* out_a, double* out_b, int* status, const int* active) {
     __shared__ double sa[256], sb[256];
+    if (!active[blockIdx.x]) return; // switched off: outputs left as they were
     const BFin F = fin[blockIdx.x];
     const int t = threadIdx.x;
     double ra = 0.0, rb = 0.0;
@@ -258,6 +280,20 @@ __global__ void __launch_bounds__(256) k_bfinalize(const BFin* fin, const double
     }
 }
 
+// Accepted line-search steps: g_p <- g_p - lam_p dJ/dg_p for every problem
+// with lam_p != 0, rounded as the trial control of the forward.
+template <typename T> __global__ void k_baxpy(const BRec<T>* __restrict__ recs, int count, const T* __restrict__ lam) {
+    const int p = blockIdx.y;
+    if (p >= count || lam[p] == T(0)) return;
+    const BRec<T>& R = recs[p];
+    T* g = const_cast<T*>(R.g);
+    const T* E = R.dJdg;
+    const T l = lam[p];
+    const size_t n = (size_t)R.nwin * R.nctrl;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        g[i] = fma(-l, E[i], g[i]);
+}
+
 // Node-plane operations over all problems: zero sigma (op 0), restore Phi
 // from checkpoint slot `slot` (op 1).
 template <typename T>
@@ -287,13 +323,23 @@ struct BatchHost {
     std::vector<int> tx; // tile width per problem
     char* ws = nullptr;
     size_t off_rec = 0, off_tile0 = 0, off_fin = 0, off_sums = 0, off_maxs = 0, off_out = 0, off_status = 0;
+    size_t off_active = 0, off_lam = 0;
     size_t rec_bytes = 0;
     std::vector<const void*> g;
     std::vector<void*> dJdg;
     cudaStream_t stream = nullptr;
-    cudaGraphExec_t graph_grad = nullptr, graph_fwd = nullptr;
+    // captured launch sequences: forward, forward + adjoint, line-search trial forward, adjoint only
+    cudaGraphExec_t graphs[4] = {nullptr, nullptr, nullptr, nullptr};
     bool has_init = false, bound = false;
+    std::vector<int> enabled;      // problems the caller keeps switched on
+    std::vector<double> lam_prev;  // last accepted step length per problem (0: none yet)
+    std::vector<double> J_at_g;    // cost at the current control, valid while fwd_at_g
+    bool J_on_device = false;      // ... or in out[0..count) (after cx_batch_forward / _gradient)
+    bool fwd_at_g = false;         // every enabled problem's forward state (checkpoints, last
+                                   // tape, final populations) belongs to its current control
 };
+
+enum { G_FWD = 0, G_GRAD = 1, G_TRIAL = 2, G_ADJ = 3 };
 
 } // namespace
 
@@ -355,6 +401,8 @@ template <typename T> cx_status upload_table(BatchHost& h) {
         R.dJdg = h.dJdg.empty() ? nullptr : static_cast<T*>(h.dJdg[i]);
         R.plane = (long long)p->lay.plane;
         R.nctrl = (long long)p->lay.nctrl;
+        R.win_len = p->lay.win_len;
+        R.nwin = p->lay.nwin;
         R.pop_elems = (long long)(2 * p->lay.Q * p->lay.plane);
         R.tile0 = tile0[i];
         R.tx = h.tx[i];
@@ -375,9 +423,10 @@ template <typename T> cx_status upload_table(BatchHost& h) {
 }
 
 void drop_graphs(BatchHost& h) {
-    if (h.graph_grad) cudaGraphExecDestroy(h.graph_grad);
-    if (h.graph_fwd) cudaGraphExecDestroy(h.graph_fwd);
-    h.graph_grad = h.graph_fwd = nullptr;
+    for (cudaGraphExec_t& g : h.graphs) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
+    }
 }
 
 template <typename T, int Q, int NT, bool ADJ>
@@ -405,7 +454,8 @@ cudaError_t launch_bq(const BatchHost& h, const BStep& st, int blocks) {
     double* maxs = ADJ ? reinterpret_cast<double*>(h.ws + h.off_maxs) : nullptr;
     return cudaLaunchKernelEx(&cfg, k_batch<T, Q, NT, ADJ>, reinterpret_cast<const BRec<T>*>(h.ws + h.off_rec),
                               reinterpret_cast<const int*>(h.ws + h.off_tile0), h.count, h.total_tiles, st, sums,
-                              maxs);
+                              maxs, reinterpret_cast<const int*>(h.ws + h.off_active),
+                              reinterpret_cast<const T*>(h.ws + h.off_lam));
 }
 
 template <typename T, bool ADJ> cudaError_t launch_b(const BatchHost& h, const BStep& st) {
@@ -430,8 +480,8 @@ template <typename T> cudaError_t launch_planes(const BatchHost& h, int op, int 
         if ((x) != cudaSuccess) return CX_ERR_CUDA;                                                                  \
     } while (0)
 
-// Forward of every problem; J_p into out[0..count).
-template <typename T> cx_status enqueue_forward(BatchHost& h) {
+// Forward of every problem (at g_p, or at the trial g_p - lam_p dJ/dg_p); J_p into out[0..count).
+template <typename T> cx_status enqueue_forward(BatchHost& h, bool trial) {
     double* sums = reinterpret_cast<double*>(h.ws + h.off_sums);
     B_CUDA(cudaMemsetAsync(sums, 0, sizeof(double) * h.nslots, h.stream));
     const int N = h.N, k = h.k, S = h.S;
@@ -453,6 +503,7 @@ template <typename T> cx_status enqueue_forward(BatchHost& h) {
         }
         st.tape_slot = (seg == S - 1) ? n - seg * k : -1;
         st.want_sum = 1;
+        st.trial = trial ? 1 : 0;
         B_CUDA((launch_b<T, false>(h, st)));
         in_role = st.out_role;
         in_slot = st.out_slot;
@@ -466,7 +517,8 @@ template <typename T> cx_status enqueue_forward(BatchHost& h) {
     }
     k_bfinalize<<<h.count, 256, 0, h.stream>>>(reinterpret_cast<const BFin*>(h.ws + h.off_fin), sums, nullptr, 0,
                                                 reinterpret_cast<double*>(h.ws + h.off_out), nullptr,
-                                                reinterpret_cast<int*>(h.ws + h.off_status));
+                                                reinterpret_cast<int*>(h.ws + h.off_status),
+                                                reinterpret_cast<const int*>(h.ws + h.off_active));
     B_CUDA(cudaGetLastError());
     return CX_OK;
 }
@@ -519,16 +571,18 @@ template <typename T> cx_status enqueue_adjoint(BatchHost& h) {
     double* out = reinterpret_cast<double*>(h.ws + h.off_out);
     k_bfinalize<<<h.count, 256, 0, h.stream>>>(reinterpret_cast<const BFin*>(h.ws + h.off_fin), sums, maxs, 1,
                                                 out + h.count, out + 2 * h.count,
-                                                reinterpret_cast<int*>(h.ws + h.off_status));
+                                                reinterpret_cast<int*>(h.ws + h.off_status),
+                                                reinterpret_cast<const int*>(h.ws + h.off_active));
     B_CUDA(cudaGetLastError());
     return CX_OK;
 }
 
-template <typename T> cx_status capture(BatchHost& h, bool with_adjoint, cudaGraphExec_t* exec) {
+template <typename T> cx_status capture(BatchHost& h, int mode, cudaGraphExec_t* exec) {
     cudaGraph_t graph = nullptr;
     B_CUDA(cudaStreamBeginCapture(h.stream, cudaStreamCaptureModeThreadLocal));
-    cx_status rc = enqueue_forward<T>(h);
-    if (rc == CX_OK && with_adjoint) rc = enqueue_adjoint<T>(h);
+    cx_status rc = CX_OK;
+    if (mode != G_ADJ) rc = enqueue_forward<T>(h, mode == G_TRIAL);
+    if (rc == CX_OK && (mode == G_GRAD || mode == G_ADJ)) rc = enqueue_adjoint<T>(h);
     const cudaError_t e = cudaStreamEndCapture(h.stream, &graph);
     if (rc != CX_OK || e != cudaSuccess) {
         if (graph) cudaGraphDestroy(graph);
@@ -539,21 +593,156 @@ template <typename T> cx_status capture(BatchHost& h, bool with_adjoint, cudaGra
     return ei == cudaSuccess ? CX_OK : CX_ERR_CUDA;
 }
 
-template <typename T> cx_status run(BatchHost& h, bool with_adjoint, double* out_dev) {
-    cudaGraphExec_t* ex = with_adjoint ? &h.graph_grad : &h.graph_fwd;
+template <typename T> cx_status run_graph(BatchHost& h, int mode) {
+    cudaGraphExec_t* ex = &h.graphs[mode];
     if (!*ex) {
-        cx_status rc = capture<T>(h, with_adjoint, ex);
+        cx_status rc = capture<T>(h, mode, ex);
         if (rc) return rc;
     }
     B_CUDA(cudaGraphLaunch(*ex, h.stream));
+    const bool adj = mode == G_GRAD || mode == G_ADJ;
     for (cx_problem* p : h.probs) {
         p->fwd_valid = true;
         p->adj_valid = false;
-        p->tape_last_valid = !with_adjoint || h.S == 1;
+        p->tape_last_valid = !adj || h.S == 1;
     }
+    return CX_OK;
+}
+
+template <typename T> cx_status run(BatchHost& h, bool with_adjoint, double* out_dev) {
+    cx_status rc = run_graph<T>(h, with_adjoint ? G_GRAD : G_FWD);
+    if (rc) return rc;
+    h.fwd_at_g = !with_adjoint || h.S == 1;
+    h.J_on_device = true;
     if (out_dev)
         B_CUDA(cudaMemcpyAsync(out_dev, h.ws + h.off_out, sizeof(double) * (with_adjoint ? 3 : 1) * h.count,
                                cudaMemcpyDeviceToDevice, h.stream));
+    return CX_OK;
+}
+
+cx_status upload_ints(BatchHost& h, size_t off, const std::vector<int>& v) {
+    B_CUDA(cudaMemcpyAsync(h.ws + off, v.data(), sizeof(int) * v.size(), cudaMemcpyHostToDevice, h.stream));
+    return CX_OK;
+}
+
+// per-problem step lengths in the precision T of the controls
+cx_status upload_lam(BatchHost& h, const std::vector<double>& lam) {
+    if (h.esz == 8) {
+        B_CUDA(cudaMemcpyAsync(h.ws + h.off_lam, lam.data(), sizeof(double) * lam.size(), cudaMemcpyHostToDevice,
+                               h.stream));
+    } else {
+        std::vector<float> f(lam.begin(), lam.end());
+        B_CUDA(cudaMemcpyAsync(h.ws + h.off_lam, f.data(), sizeof(float) * f.size(), cudaMemcpyHostToDevice,
+                               h.stream));
+        B_CUDA(cudaStreamSynchronize(h.stream)); // f is a local
+    }
+    return CX_OK;
+}
+
+cx_status read_out(BatchHost& h, std::vector<double>& out, int& status) {
+    out.resize(3 * (size_t)h.count);
+    B_CUDA(cudaMemcpyAsync(out.data(), h.ws + h.off_out, sizeof(double) * out.size(), cudaMemcpyDeviceToHost,
+                           h.stream));
+    B_CUDA(cudaMemcpyAsync(&status, h.ws + h.off_status, sizeof(int), cudaMemcpyDeviceToHost, h.stream));
+    B_CUDA(cudaStreamSynchronize(h.stream));
+    return CX_OK;
+}
+
+// One Armijo gradient step of every enabled problem (the single-problem rule
+// of cx_step: c1 = 1e-4, first trial 2 lam_prev or min(1, 1/max|E|), halving,
+// at most 30 trials).  Trials run as one batched forward over the problems
+// still searching; the others are switched off in the device mask.
+template <typename T> cx_status batch_step(BatchHost& h, cx_step_info* info, int* pstatus) {
+    const int n = h.count;
+    std::vector<int> act(h.enabled);
+    cx_status rc = upload_ints(h, h.off_active, act);
+    if (rc) return rc;
+    std::vector<double> out;
+    int dstat = 0;
+    std::vector<double> J0(n), e2(n), einf(n);
+    if (!h.fwd_at_g) {
+        rc = run_graph<T>(h, G_GRAD);
+        if (rc) return rc;
+        rc = read_out(h, out, dstat);
+        if (rc) return rc;
+        for (int i = 0; i < n; ++i) J0[i] = out[i];
+    } else {
+        rc = run_graph<T>(h, G_ADJ);
+        if (rc) return rc;
+        rc = read_out(h, out, dstat);
+        if (rc) return rc;
+        if (h.J_on_device)
+            for (int i = 0; i < n; ++i) J0[i] = out[i];
+        else
+            J0 = h.J_at_g;
+    }
+    std::vector<int> st(n, CX_OK), trials(n, 0);
+    std::vector<double> lam(n, 0.0), Jt(n, 0.0), acc_lam(n, 0.0);
+    std::vector<int> search(n, 0);
+    int nsearch = 0;
+    for (int i = 0; i < n; ++i) {
+        e2[i] = out[n + i];
+        einf[i] = out[2 * n + i];
+        Jt[i] = J0[i];
+        if (!h.enabled[i]) continue;
+        if (!std::isfinite(J0[i]) || !std::isfinite(e2[i])) {
+            st[i] = CX_ERR_UNSTABLE;
+            continue;
+        }
+        if (e2[i] == 0.0) continue; // stationary: nothing to do
+        lam[i] = h.lam_prev[i] > 0.0 ? 2.0 * h.lam_prev[i] : std::min(1.0, einf[i] > 0.0 ? 1.0 / einf[i] : 1.0);
+        search[i] = 1;
+        ++nsearch;
+    }
+    for (int t = 0; t < 30 && nsearch > 0; ++t) {
+        if ((rc = upload_ints(h, h.off_active, search)) || (rc = upload_lam(h, lam))) return rc;
+        rc = run_graph<T>(h, G_TRIAL);
+        if (rc) return rc;
+        rc = read_out(h, out, dstat);
+        if (rc) return rc;
+        for (int i = 0; i < n; ++i) {
+            if (!search[i]) continue;
+            ++trials[i];
+            if (std::isfinite(out[i]) && out[i] <= J0[i] - 1e-4 * lam[i] * e2[i]) {
+                Jt[i] = out[i];
+                acc_lam[i] = lam[i];
+                h.lam_prev[i] = lam[i];
+                search[i] = 0;
+                --nsearch;
+            } else {
+                lam[i] *= 0.5;
+            }
+        }
+    }
+    bool all_ok = true;
+    for (int i = 0; i < n; ++i)
+        if (search[i]) {
+            st[i] = CX_ERR_LINESEARCH;
+            all_ok = false;
+        } else if (st[i] != CX_OK) {
+            all_ok = false;
+        }
+    if ((rc = upload_lam(h, acc_lam))) return rc;
+    k_baxpy<T><<<dim3(64, n), 256, 0, h.stream>>>(reinterpret_cast<const BRec<T>*>(h.ws + h.off_rec), n,
+                                                   reinterpret_cast<const T*>(h.ws + h.off_lam));
+    B_CUDA(cudaGetLastError());
+    if ((rc = upload_ints(h, h.off_active, h.enabled))) return rc;
+    // accepted trials left each problem's forward state at its new control
+    h.J_at_g = Jt;
+    h.J_on_device = false;
+    h.fwd_at_g = all_ok;
+    for (int i = 0; i < n; ++i) {
+        if (pstatus) pstatus[i] = st[i];
+        if (info) {
+            info[i].J0 = J0[i];
+            info[i].J = Jt[i];
+            info[i].lam = acc_lam[i];
+            info[i].grad_sq = e2[i];
+            info[i].grad_inf = einf[i];
+            info[i].trials = trials[i];
+        }
+    }
+    B_CUDA(cudaStreamSynchronize(h.stream));
     return CX_OK;
 }
 
@@ -583,6 +772,8 @@ cx_status batch_layout(const cx_problem_desc* d, int count, std::vector<size_t>*
     o = up(o + sizeof(double) * slots, ALIGN);
     o = up(o + sizeof(double) * 3 * count, ALIGN);
     o = up(o + sizeof(int) * 4, ALIGN);
+    o = up(o + sizeof(int) * count, ALIGN);    // enabled / searching mask
+    o = up(o + sizeof(double) * count, ALIGN); // step lengths
     *total = o;
     return CX_OK;
 }
@@ -663,7 +854,17 @@ cx_status cx_batch_create(const cx_problem_desc* descs, int count, void* workspa
     h.off_out = o;
     o = up(o + sizeof(double) * 3 * count, ALIGN);
     h.off_status = o;
-    if (cudaMemset(h.ws + h.off_status, 0, sizeof(int) * 4) != cudaSuccess) {
+    o = up(o + sizeof(int) * 4, ALIGN);
+    h.off_active = o;
+    o = up(o + sizeof(int) * count, ALIGN);
+    h.off_lam = o;
+    h.enabled.assign(count, 1);
+    h.lam_prev.assign(count, 0.0);
+    h.J_at_g.assign(count, 0.0);
+    if (cudaMemset(h.ws + h.off_status, 0, sizeof(int) * 4) != cudaSuccess ||
+        cudaMemset(h.ws + h.off_lam, 0, sizeof(double) * count) != cudaSuccess ||
+        cudaMemcpy(h.ws + h.off_active, h.enabled.data(), sizeof(int) * count, cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
         cx_batch_destroy(b);
         return CX_ERR_CUDA;
     }
@@ -683,6 +884,8 @@ cx_status cx_batch_set_initial(cx_batch* b, const void* const* u0, const void* c
         if (rc) return rc;
     }
     b->h.has_init = true;
+    b->h.fwd_at_g = false;
+    b->h.lam_prev.assign(b->h.count, 0.0);
     return CX_OK;
 }
 
@@ -696,6 +899,8 @@ cx_status cx_batch_bind(cx_batch* b, const void* const* g, void* const* dJdg) {
         if (dJdg) h.dJdg[i] = dJdg[i];
     }
     h.bound = true;
+    h.fwd_at_g = false;
+    h.lam_prev.assign(h.count, 0.0);
     drop_graphs(h);
     return h.esz == 8 ? upload_table<double>(h) : upload_table<float>(h);
 }
@@ -712,6 +917,31 @@ cx_status cx_batch_gradient(cx_batch* b, double* out_dev) {
     for (void* p : b->h.dJdg)
         if (!p) return CX_ERR_INVALID_ARG;
     return b->h.esz == 8 ? run<double>(b->h, true, out_dev) : run<float>(b->h, true, out_dev);
+}
+
+cx_status cx_batch_set_enabled(cx_batch* b, const int* enabled) {
+    if (!b) return CX_ERR_INVALID_ARG;
+    BatchHost& h = b->h;
+    std::vector<int> e(h.count, 1);
+    if (enabled)
+        for (int i = 0; i < h.count; ++i) {
+            if (!h.enabled[i] && enabled[i]) h.fwd_at_g = false; // its state may be stale
+            e[i] = enabled[i] ? 1 : 0;
+        }
+    h.enabled = e;
+    cx_status rc = upload_ints(h, h.off_active, h.enabled);
+    if (rc) return rc;
+    B_CUDA(cudaStreamSynchronize(h.stream));
+    return CX_OK;
+}
+
+cx_status cx_batch_step(cx_batch* b, cx_step_info* info, int* status) {
+    if (!b) return CX_ERR_INVALID_ARG;
+    BatchHost& h = b->h;
+    if (!h.has_init || !h.bound) return CX_ERR_STATE;
+    for (int i = 0; i < h.count; ++i)
+        if (!h.g[i] || !h.dJdg[i]) return CX_ERR_INVALID_ARG;
+    return h.esz == 8 ? batch_step<double>(h, info, status) : batch_step<float>(h, info, status);
 }
 
 cx_status cx_batch_get_fields(cx_batch* b, int i, void* u_out, void* v_out) {

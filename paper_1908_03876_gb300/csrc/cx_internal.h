@@ -73,6 +73,8 @@ template <typename T> struct AdjArgs {
     double* emax_part;   // per-warp partial of max |E| (accumulated over steps)
     int n;
     int terminal;        // n == N-1: psi^{n+1} is the broadcast seed
+    int accum;           // time-windowed control: add to the window's gradient (not its last step)
+    int norm;            // add this step's gradient values to the norm partials (window complete)
     __device__ __forceinline__ const T* in(int j) const { return rin[j]; }
     __device__ __forceinline__ T* out(int j) const { return rout[j]; }
 };

@@ -123,6 +123,7 @@ cx_status run_static(const cx_problem_desc* d, const CxConst& C, const StaticLay
         return CX_ERR_CUDA;
     if (launch_init<T>(C, nullptr, nullptr, u0, v0, P0, L2, s) != cudaSuccess) return CX_ERR_CUDA;
     const T* in = P0;
+    const int win_len = d->ctrl_windows > 0 ? d->n_steps / d->ctrl_windows : 1;
     for (int n = 0; n < d->n_steps; ++n) {
         FwdArgs<T> A{};
         T* out = reinterpret_cast<T*>(ws + ((n % 2) ? Ly.off_PB : Ly.off_PA));
@@ -132,7 +133,7 @@ cx_status run_static(const cx_problem_desc* d, const CxConst& C, const StaticLay
         }
         A.phi = reinterpret_cast<T*>(ws + Ly.off_phi);
         A.phi_ckpt = nullptr;
-        A.g = g ? g + (size_t)n * Ly.nctrl : nullptr;
+        A.g = g ? g + (size_t)(n / win_len) * Ly.nctrl : nullptr;
         A.E = nullptr;
         A.lam = T(0);
         A.tape = nullptr;

@@ -202,4 +202,5 @@ def make_desc(w: Workload, dev, precision=None):
     d.alpha = w.alpha
     d.s = (ctypes.c_double * 7)(*w.s)
     d.source_order = w.source_order
+    d.ctrl_windows = w.windows
     return d, keep

@@ -70,6 +70,7 @@ class Workload:
     s: tuple = (1.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0)
     source_order: int = 2
     ckpt_every: int = 0
+    windows: int = 0          # W > 0: control piecewise constant over W equal time windows
     extra: dict = field(default_factory=dict)
 
     # ---- views of the same inputs in per-node form (input shaping only)
@@ -80,7 +81,7 @@ class Workload:
     @property
     def ctrl_shape(self):
         w = self.win
-        return (self.N, w[3], w[2])
+        return (self.windows or self.N, w[3], w[2])
 
     def D_fields(self):
         """Per-node (Dxx, Dxy, Dyy) for both species, [ny, nx, 3] each."""

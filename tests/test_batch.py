@@ -127,3 +127,58 @@ def test_autotuner_picks_admissible_config(tmp_path):
     autotune.apply(b, cfg)
     J1 = b.forward().cpu().numpy()
     assert np.allclose(J0, J1, rtol=1e-6)
+
+
+def test_batch_step_matches_oracle_gd():
+    """Batched Armijo iterations (one trial forward over the problems still
+    searching) against the oracle's per-problem iterations: J, step length,
+    trials and the updated control after each of three steps."""
+    from paper_1908_03876_gb300.batch import Batch
+
+    ws = _mixed(N=12, k=5)
+    b = Batch(ws)
+    gs = b.zeros_controls()
+    b.bind(gs)
+    go = [np.zeros(w.ctrl_shape) for w in ws]
+    lam_prev = [None] * len(ws)
+    for it in range(3):
+        info, st = b.step()
+        assert all(s == 0 for s in st), st
+        for i, w in enumerate(ws):
+            go[i], io = oracle.gd_step(oracle.from_workload(w), go[i], lam_prev=lam_prev[i])
+            lam_prev[i] = io["lam"]
+            assert abs(info[i]["J0"] - io["J0"]) <= 1e-12 * abs(io["J0"]), (it, i)
+            assert abs(info[i]["J"] - io["J"]) <= 1e-12 * abs(io["J"]), (it, i)
+            assert info[i]["trials"] == io["trials"] and abs(info[i]["lam"] - io["lam"]) <= 1e-14 * io["lam"]
+            err = np.linalg.norm(gs[i].cpu().numpy() - go[i]) / np.linalg.norm(go[i])
+            assert err < 1e-12, (it, i, err)
+
+
+def test_batch_windowed_and_switched_off():
+    """Windowed controls in the batch (gradients against the oracle), and a
+    switched-off problem: its control and gradient buffers are left alone and
+    the others step as in a batch without it."""
+    from paper_1908_03876_gb300.batch import Batch
+
+    ws = _mixed(N=12, k=5)[:4]
+    for w in ws:
+        w.windows = 3
+    b = Batch(ws)
+    gs = [torch.as_tensor(w.random_control(70 + i, 0.02), dtype=b.dtype, device=b.device) for i, w in enumerate(ws)]
+    b.bind(gs)
+    J, _, _ = b.gradient()
+    J = J.cpu().numpy()
+    for i, w in enumerate(ws):
+        Jo, Eo, _ = oracle.adjoint(oracle.from_workload(w), gs[i].cpu().numpy())
+        assert abs(J[i] - Jo) <= 1e-12 * abs(Jo)
+        assert np.linalg.norm(b.E[i].cpu().numpy() - Eo) <= 1e-12 * np.linalg.norm(Eo)
+    before = [g.cpu().numpy().copy() for g in gs]
+    E_off = b.E[2].clone()
+    b.set_enabled([True, True, False, True])
+    info, st = b.step()
+    assert st == [0, 0, 0, 0] and info[2]["trials"] == 0
+    assert np.array_equal(gs[2].cpu().numpy(), before[2]) and torch.equal(b.E[2], E_off)
+    for i in (0, 1, 3):
+        go, io = oracle.gd_step(oracle.from_workload(ws[i]), before[i])
+        assert abs(info[i]["J"] - io["J"]) <= 1e-12 * abs(io["J"]) and info[i]["trials"] == io["trials"]
+        assert np.linalg.norm(gs[i].cpu().numpy() - go) <= 1e-12 * np.linalg.norm(go)

@@ -181,6 +181,34 @@ def test_step_matches_oracle_fp64():
     assert rel(g, go2) < 1e-12
 
 
+@pytest.mark.parametrize("k", [5, 30])
+def test_windowed_control_fp64(k):
+    """Control piecewise constant over W = 5 time windows (30 steps): J, fields
+    and the window gradients (sums of the per-step gradients) against the
+    oracle; checkpoint intervals that cut windows (k = 5 with 6-step windows)
+    and a single segment."""
+    w = W.aniso(40, 36, 30, seed=4, precision=64, ckpt_every=k)
+    w.windows = 5
+    g = w.random_control(7, 0.05)
+    assert g.shape == (5, 36, 40)
+    check(run_both(w, g), TOL64, TOL64, f"windowed fp64 k{k}")
+
+
+def test_windowed_step_matches_oracle_fp64():
+    """cx_step on a windowed control against the oracle's Armijo iteration."""
+    from paper_1908_03876_gb300.problem import Problem
+
+    w = W.plain64(24, 24, 20, sigma=2.0, Q=9)
+    w.windows = 4
+    p = Problem(w)
+    g = p.zeros_control()
+    assert tuple(g.shape) == (4, 24, 24)
+    info = p.step(g)
+    go, io = oracle.gd_step(oracle.from_workload(w), np.zeros(w.ctrl_shape))
+    assert abs(info["J"] - io["J"]) <= 1e-12 * abs(io["J"]) and info["trials"] == io["trials"]
+    assert rel(g, go) < 1e-12
+
+
 # ---------------------------------------------------------------- FP32 parity
 
 def test_aniso_fp32_against_fp64_oracle():

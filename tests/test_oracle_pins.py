@@ -384,3 +384,35 @@ def test_gd_step_decreases_cost():
     assert info["J"] < info["J0"]
     g2, info2 = oracle.gd_step(p, g1, lam_prev=info["lam"])
     assert info2["J"] < info["J"]
+
+
+def test_windowed_gradient_fd():
+    """Control piecewise constant over W time windows (the subspace g^n = G_w):
+    every component of the window gradient against central finite differences
+    of J(G), and W = N reproduces the per-step control exactly."""
+    w = W.plain64(10, 10, 12, sigma=2.0, Q=9)
+    w.chi = -0.05
+    w.alpha = 1e-2
+    w.windows = 3
+    p = oracle.from_workload(w)
+    assert w.ctrl_shape == (3, 10, 10)
+    G = w.random_control(5, 0.05)
+    J0, E, _ = oracle.adjoint(p, G)
+    assert E.shape == G.shape
+    h = 1e-6
+    fd = np.zeros_like(G)
+    for idx in np.ndindex(G.shape):
+        gp = G.copy()
+        gp[idx] += h
+        gm = G.copy()
+        gm[idx] -= h
+        fd[idx] = (oracle.forward(p, gp)[0] - oracle.forward(p, gm)[0]) / (2 * h)
+    assert np.abs(fd - E).max() <= 1e-6 * np.abs(E).max()
+    # the same control written per step (windows = N) gives the same J and the
+    # per-step gradient whose window sums are E
+    w.windows = 0
+    q = oracle.from_workload(w)
+    g_steps = np.repeat(G, 4, axis=0)
+    Jq, Eq, _ = oracle.adjoint(q, g_steps)
+    assert Jq == J0
+    assert np.abs(Eq.reshape(3, 4, 10, 10).sum(1) - E).max() <= 1e-14 * np.abs(E).max()
