@@ -180,10 +180,16 @@ def run_batch(args, rank, world, local):
 
     from paper_1908_03876_gb300 import sharding
 
-    allw = W.batch_workloads(args.problems, N=1000, seed=3)
+    if args.profile:  # small profiling case: 20 steps, k = 10, default tiles
+        allw = W.batch_workloads(args.problems, N=20, seed=3, ckpt_every=10)
+    else:
+        allw = W.batch_workloads(args.problems, N=1000, seed=3)
     mine = sharding.my_problems(allw, rank, world)
     t0 = time.perf_counter()
-    cfg = autotune.autotune(mine, probe_steps=12, device=dev)
+    if args.profile:
+        cfg = {"threads": 256, "tile_x": {s: 256 for s in (64, 128, 256, 512)}}
+    else:
+        cfg = autotune.autotune(mine, probe_steps=12, device=dev)
     t_tune = time.perf_counter() - t0
     b = Batch(mine, device=dev)
     gs = [torch.as_tensor(w.random_control(500 + i, 0.01), dtype=torch.float32, device=dev) for i, w in enumerate(mine)]
@@ -219,8 +225,9 @@ def run_batch(args, rank, world, local):
     del gs
     torch.cuda.empty_cache()
     # per-problem gradient error against the FP64 oracle on a sample
-    err = []
-    if rank == 0:
+    err = [float("nan")]
+    if rank == 0 and not args.profile:
+        err = []
         import oracle
 
         oracle.build()
@@ -260,6 +267,86 @@ def run_batch(args, rank, world, local):
         dist.destroy_process_group()
 
 
+def run_warmstart(args, rank, world, local):
+    """Learned warm start against the plain method on held-out problems.
+
+    Data: args.ws_train seeded problems solved by the plain batched Armijo
+    descent from g = 0 (stop at ||E||/||E0|| < 1e-4 or 200 iterations); the
+    U-Net is trained on (inputs, g*) with the library's BF16 kernels.  On
+    args.ws_test held-out problems the plain run from g = 0 defines J*; then
+    the warm start (U-Net proposal + descent) and the cold start (descent from
+    g = 0) are timed until each problem's cost is <= J* (1 + 1e-6).
+    """
+    import numpy as np
+    import torch
+
+    if rank != 0:  # independent replicas only; rank 0 reports
+        return
+    torch.cuda.set_device(local)
+    from paper_1908_03876_gb300.build import build
+
+    build()
+    from paper_1908_03876_gb300 import warmstart as WS
+
+    def log(m):
+        print(m, file=sys.stderr, flush=True)
+
+    size, N, win = args.ws_size, args.ws_steps, 8
+    k = max(8, N // 4)
+    t0 = time.perf_counter()
+    train = WS.problems(args.ws_train, 10_000, size=size, N=N, windows=win, ckpt_every=k)
+    test = WS.problems(args.ws_test, 900_000, size=size, N=N, windows=win, ckpt_every=k)
+    ref_tr = WS.descend(train, max_iter=200, log=log)
+    t_data = time.perf_counter() - t0
+    log(f"data: {t_data:.1f} s, iterations mean {ref_tr['iters'].mean():.1f}")
+    X = WS.features(train)
+    G = np.stack(ref_tr["g"])
+    model = WS.Surrogate(windows=win)
+    bs = 16
+    steps_per_epoch = len(X) // bs
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t1 = time.perf_counter()
+    e0.record()
+    losses = model.fit(X, G, epochs=args.ws_epochs, batch_size=bs, lr=2e-3, log=log)
+    e1.record()
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t1
+    train_ms = e0.elapsed_time(e1)
+    flops = model.net.flops(bs, size, size) * steps_per_epoch * args.ws_epochs
+    tf = flops / (train_ms * 1e-3) / 1e12
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            pk = json.load(fh)
+        peak, pk_kind = float(pk["bf16_tflops_sustained"]), "measured (sustained bf16)"
+    except Exception:
+        peak, pk_kind = 1700.0, "fallback"
+    ref_te = WS.descend(test, max_iter=200, log=log)
+    clocks = Clocks()
+    clocks.start()
+    ev = WS.evaluate(model, test, ref_te, log=log)
+    clk = clocks.stop(local)
+    line = {
+        "metric": "wall time to the plain optimum cost (1e-6 rel), learned warm start",
+        "value": ev["warm_seconds"], "unit": "s", "n_gpus": 1, "steps": 1, "warmup": 0,
+        "ms_per_step": ev["warm_seconds"] * 1e3, "higher_is_better": False, "scaling": "replicas only",
+        "vs_baseline": None, "dtype": "f32 lattice (FP64 reductions), bf16 U-Net (FP32 accumulation)",
+        "data": "synthetic (seeded)",
+        "config": {"workload": f"warm start: {args.ws_train} training + {args.ws_test} held-out problems, "
+                               f"{size}x{size} D2Q9 FP32, {N} steps, control constant over {win} windows, "
+                               "random chi, eigenvalue ratio and angle",
+                   "unet": "4 levels, 32-256 channels, additive skips", "epochs": args.ws_epochs,
+                   "batch": bs, "l2": "batched lattices larger than L2"},
+        "cold_seconds": ev["cold_seconds"], "speedup_vs_plain": ev["cold_seconds"] / ev["warm_seconds"],
+        "eval": ev, "datagen_seconds": t_data, "train_seconds": t_train, "train_loss": losses[-1],
+        "roofline": {"bound": "tensor", "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
+                     "traffic": None, "kernel": "U-Net training (all convolution launches)",
+                     "peak_source": pk_kind},
+        "clocks": clk, "e2e": None,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -267,13 +354,18 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="aniso1024", choices=["aniso1024", "batch"],
+    ap.add_argument("--workload", default="aniso1024", choices=["aniso1024", "batch", "warmstart"],
                     help="aniso1024 (default bench line) or batch: 256 independent problems, sizes {64..512}^2, "
                          "1000 steps, one persistent launch per step replayed as a CUDA graph")
     ap.add_argument("--problems", type=int, default=256)
+    ap.add_argument("--ws-train", type=int, default=2000)
+    ap.add_argument("--ws-test", type=int, default=200)
+    ap.add_argument("--ws-size", type=int, default=128)
+    ap.add_argument("--ws-steps", type=int, default=128)
+    ap.add_argument("--ws-epochs", type=int, default=40)
     ap.add_argument("--profile", action="store_true",
-                    help="small profiling case: the same 1024x1024 lattice, 20 time steps, k = 10, "
-                         "one warm-up and one timed gradient evaluation, no CPU baseline or e2e leg")
+                    help="small profiling case: the same lattices (batch: --problems of them), 20 time steps, "
+                         "k = 10, one warm-up and one timed gradient evaluation, no CPU baseline or e2e leg")
     args = ap.parse_args()
     if args.profile:
         WORKLOAD.update(N=20, k=10)
@@ -287,6 +379,9 @@ def main():
         return
     if args.workload == "batch":
         run_batch(args, rank, world, local)
+        return
+    if args.workload == "warmstart":
+        run_warmstart(args, rank, world, local)
         return
 
     import numpy as np

@@ -206,5 +206,30 @@ class UNet:
         self.adam_step(lr)
         return loss
 
+    def flops(self, B, H, W, training=True):
+        """Convolution FLOPs (2 per multiply-add) of one forward, or of one
+        training step (forward, data gradients except the input layer's, and
+        weight gradients), for a batch of B H x W inputs."""
+        total = 0
+        h, w = H, W
+        sizes = []
+        for l in range(self.L):
+            if l > 0:
+                h, w = h // 2, w // 2
+            sizes.append((h, w))
+        for l, (c1, c2) in enumerate(self.enc):
+            hh, ww = sizes[l]
+            for c, first in ((c1, l == 0), (c2, False)):
+                f = 2 * B * hh * ww * c.cout * c.cin * c.ks * c.ks
+                total += f * (1 + (0 if first else 1) + 1) if training else f
+        for l, (c1, c2) in self.dec.items():
+            hh, ww = sizes[l]
+            for c in (c1, c2):
+                f = 2 * B * hh * ww * c.cout * c.cin * c.ks * c.ks
+                total += 3 * f if training else f
+        f = 2 * B * H * W * self.head.cout * self.head.cin
+        total += 3 * f if training else f
+        return total
+
     def state(self):
         return {"w": [c.w.cpu() for c in self.layers], "b": [c.b.cpu() for c in self.layers]}
