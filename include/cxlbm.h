@@ -215,14 +215,28 @@ cx_status cx_batch_set_initial(cx_batch* b, const void* const* u0, const void* c
 cx_status cx_batch_bind(cx_batch* b, const void* const* g, void* const* dJdg);
 /* Tile shapes: `threads` per block (128 or 256), `blocks` persistent blocks
  * (0: every SM at full residency), tile_x[i] = tile width of problem i (a
- * divisor of threads, >= 32, threads / tile_x[i] <= 8; NULL: threads).  The
- * tile height is threads / tile_x[i].  Synchronous. */
-cx_status cx_batch_set_tiles(cx_batch* b, int threads, int blocks, const int* tile_x);
+ * power of two dividing threads, >= 32, threads / tile_x[i] <= 8; NULL:
+ * threads), rows[i] = nodes each thread updates per tile, 1..16 (NULL: 2).
+ * The tile height is (threads / tile_x[i]) rows[i].  Synchronous. */
+cx_status cx_batch_set_tiles(cx_batch* b, int threads, int blocks, const int* tile_x, const int* rows);
 /* Forward of every problem; J_dev (device double [count], may be NULL). */
 cx_status cx_batch_forward(cx_batch* b, double* J_dev);
 /* Forward + recompute + AMRT adjoint of every problem into the bound dJdg;
  * out_dev (device double [3 count], may be NULL): J, ||dJ/dg||^2, max |dJ/dg|. */
 cx_status cx_batch_gradient(cx_batch* b, double* out_dev);
+/* AMRT adjoint of every enabled problem seeded with seed_u[i] (device T
+ * [ny_i][nx_i], the adjoint of u^N; NULL array or entry: u^N - u_target),
+ * into the bound dJdg: the gradient of sum(seed_u u^N) + alpha ||g||^2 at the
+ * bound controls.  add_to_cost_seed != 0: the seed is (u^N - u_target) +
+ * seed_u[i] instead (the gradient of J + sum(seed_u u^N)).  Needs the preceding cx_batch_forward (or accepted
+ * cx_batch_step) at those controls; out_dev (device double [3 count], may be
+ * NULL) receives ||dJ/dg||^2 and max |dJ/dg| in its last 2 count entries.
+ * Errors: CX_ERR_STATE (no forward state at the bound controls). */
+cx_status cx_batch_adjoint(cx_batch* b, const void* const* seed_u, int add_to_cost_seed, double* out_dev);
+/* g[i] <- g[i] - lam[i] dJdg[i] for every enabled problem (lam: host double
+ * [count], 0 leaves a problem alone), rounded as a line-search trial;
+ * forgets the step-length history.  Asynchronous. */
+cx_status cx_batch_axpy(cx_batch* b, const double* lam);
 cx_status cx_batch_get_fields(cx_batch* b, int i, void* u_out, void* v_out);
 /* Synchronising: CX_ERR_UNSTABLE if any problem's J or gradient was non-finite. */
 cx_status cx_batch_get_status(cx_batch* b);
@@ -258,6 +272,14 @@ cx_status cx_batch_destroy(cx_batch* b);
 /* y[B][Cout][H][W] = act(bias + conv(x[B][Cin][H][W], w[Cout][Cin][ks][ks])); act = ReLU if relu. bias may be NULL. */
 cx_status cx_nn_conv_forward(const uint16_t* x, const uint16_t* w, const float* bias, uint16_t* y, int B, int Cin,
                              int Cout, int H, int W, int ks, int relu, cudaStream_t stream);
+/* As cx_nn_conv_forward without activation, writing FP32 y (the network's output layer). */
+cx_status cx_nn_conv_forward_f32(const uint16_t* x, const uint16_t* w, const float* bias, float* y, int B, int Cin,
+                                 int Cout, int H, int W, int ks, cudaStream_t stream);
+/* Separable periodic low-pass of BC planes [H][W] (FP32): out = taps (*) along
+ * x then y, taps[0..2 radius] a device FP32 array (radius <= 64); tmp is
+ * scratch of the same size as in. */
+cx_status cx_nn_smooth(const float* in, float* tmp, float* out, int BC, int H, int W, const float* taps, int radius,
+                       cudaStream_t stream);
 /* dx = gradient w.r.t. x of sum(dy * conv(x, w)); w_flip: scratch of Cout*Cin*ks*ks BF16. */
 cx_status cx_nn_conv_backward_data(const uint16_t* dy, const uint16_t* w, uint16_t* dx, uint16_t* w_flip, int B,
                                    int Cin, int Cout, int H, int W, int ks, cudaStream_t stream);

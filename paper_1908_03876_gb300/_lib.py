@@ -25,10 +25,10 @@ EXPORTS = [
     "cx_destroy", "cx_status_string", "cx_forward_static",
     "cx_batch_workspace_size", "cx_batch_create", "cx_batch_set_initial", "cx_batch_bind", "cx_batch_set_tiles",
     "cx_batch_forward", "cx_batch_gradient", "cx_batch_get_fields", "cx_batch_get_status", "cx_batch_destroy",
-    "cx_batch_set_enabled", "cx_batch_step",
+    "cx_batch_set_enabled", "cx_batch_step", "cx_batch_adjoint", "cx_batch_axpy",
     "cx_nn_conv_forward", "cx_nn_conv_backward_data", "cx_nn_conv_backward_weight_scratch",
     "cx_nn_conv_backward_weight", "cx_nn_relu_backward", "cx_nn_add", "cx_nn_pool2", "cx_nn_up2", "cx_nn_mse",
-    "cx_nn_adam", "cx_nn_cast_bf16",
+    "cx_nn_adam", "cx_nn_cast_bf16", "cx_nn_conv_forward_f32", "cx_nn_smooth",
 ]
 STATIC_SCRATCH_BYTES = 32 << 20  # CX_STATIC_SCRATCH_BYTES of include/cxlbm.h
 
@@ -100,7 +100,7 @@ def load():
         "cx_batch_create": [D, cint, vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)],
         "cx_batch_set_initial": [vp, vp, vp],
         "cx_batch_bind": [vp, vp, vp],
-        "cx_batch_set_tiles": [vp, cint, cint, vp],
+        "cx_batch_set_tiles": [vp, cint, cint, vp, vp],
         "cx_batch_forward": [vp, vp],
         "cx_batch_gradient": [vp, vp],
         "cx_batch_get_fields": [vp, cint, vp, vp],
@@ -108,7 +108,11 @@ def load():
         "cx_batch_destroy": [vp],
         "cx_batch_set_enabled": [vp, vp],
         "cx_batch_step": [vp, ctypes.POINTER(StepInfo), vp],
+        "cx_batch_adjoint": [vp, vp, cint, vp],
+        "cx_batch_axpy": [vp, vp],
         "cx_nn_conv_forward": [vp, vp, vp, vp, cint, cint, cint, cint, cint, cint, cint, vp],
+        "cx_nn_conv_forward_f32": [vp, vp, vp, vp, cint, cint, cint, cint, cint, cint, vp],
+        "cx_nn_smooth": [vp, vp, vp, cint, cint, cint, vp, cint, vp],
         "cx_nn_conv_backward_data": [vp, vp, vp, vp, cint, cint, cint, cint, cint, cint, vp],
         "cx_nn_conv_backward_weight": [vp, vp, vp, vp, vp, cint, cint, cint, cint, cint, cint, cint, vp],
         "cx_nn_relu_backward": [vp, vp, vp, ctypes.c_size_t, vp],

@@ -1,11 +1,12 @@
 """Tile-shape and schedule autotuner for the batched launch.
 
 Tunables: threads per block (128, 256) and, per size class (problems with the
-same nx), the tile width tx (tile = tx x threads/tx nodes).  The tuner times a
-short probe batch (the same problems with a few time steps) by coordinate
-descent: start from tx = min(threads, nx) for every class, then for each class
-try the other admissible widths while the rest stay fixed, keeping the
-fastest.  Results are cached in a JSON file keyed by the device, lattice,
+same nx), the tile width tx and the rows r each thread updates per tile (tile
+= tx x r threads/tx nodes).  The tuner times a short probe batch (the same
+problems with a few time steps) by coordinate descent: start from
+tx = min(threads, nx), r = 2 for every class, then for each class try the
+other admissible widths, then the other row counts, while the rest stay
+fixed, keeping the fastest.  Results are cached in a JSON file keyed by the device, lattice,
 precision and the size-class histogram.
 """
 from __future__ import annotations
@@ -19,6 +20,7 @@ import torch
 from .batch import Batch
 
 WIDTHS = (32, 64, 128, 256)
+ROWS = (1, 2, 4, 8)
 
 
 def _signature(workloads, device):
@@ -47,7 +49,7 @@ def _time_forward(b: Batch, reps=3):
 
 
 def autotune(workloads, probe_steps=12, threads_options=(128, 256), cache_path=None, device="cuda"):
-    """Returns {"threads": T, "blocks": 0, "tile_x": {nx: tx}, "ms": best probe time}."""
+    """Returns {"threads": T, "blocks": 0, "tile_x": {nx: tx}, "rows": {nx: r}, "ms": best probe time}."""
     sig = _signature(workloads, device)
     if cache_path and os.path.exists(cache_path):
         with open(cache_path) as fh:
@@ -55,6 +57,7 @@ def autotune(workloads, probe_steps=12, threads_options=(128, 256), cache_path=N
         if sig in cache:
             got = cache[sig]
             got["tile_x"] = {int(k): v for k, v in got["tile_x"].items()}
+            got["rows"] = {int(k): v for k, v in got.get("rows", {}).items()}
             return got
     probe = [replace(w, N=probe_steps, ckpt_every=probe_steps) for w in workloads]
     b = Batch(probe, device=device)
@@ -63,34 +66,46 @@ def autotune(workloads, probe_steps=12, threads_options=(128, 256), cache_path=N
     best = None
     for threads in threads_options:
         choice = {nx: min(threads, max(t for t in _admissible(threads, nx))) for nx in classes}
+        rows = {nx: 2 for nx in classes}
 
-        def run(ch):
-            b.set_tiles(threads, 0, [ch[w.nx] for w in probe])
+        def run(ch, rw):
+            b.set_tiles(threads, 0, [ch[w.nx] for w in probe], [rw[w.nx] for w in probe])
             return _time_forward(b)
 
-        t_best = run(choice)
+        t_best = run(choice, rows)
         for nx in classes:
             for tx in _admissible(threads, nx):
                 if tx == choice[nx]:
                     continue
                 trial = dict(choice)
                 trial[nx] = tx
-                t = run(trial)
+                t = run(trial, rows)
                 if t < t_best:
                     t_best, choice = t, trial
+            for r in ROWS:
+                if r == rows[nx]:
+                    continue
+                trial = dict(rows)
+                trial[nx] = r
+                t = run(choice, trial)
+                if t < t_best:
+                    t_best, rows = t, trial
         if best is None or t_best < best["ms"]:
-            best = {"threads": threads, "blocks": 0, "tile_x": dict(choice), "ms": t_best}
+            best = {"threads": threads, "blocks": 0, "tile_x": dict(choice), "rows": dict(rows), "ms": t_best}
     b.close()
     if cache_path:
         cache = {}
         if os.path.exists(cache_path):
             with open(cache_path) as fh:
                 cache = json.load(fh)
-        cache[sig] = {**best, "tile_x": {str(k): v for k, v in best["tile_x"].items()}}
+        cache[sig] = {**best, "tile_x": {str(k): v for k, v in best["tile_x"].items()},
+                      "rows": {str(k): v for k, v in best["rows"].items()}}
         with open(cache_path, "w") as fh:
             json.dump(cache, fh, indent=1)
     return best
 
 
 def apply(batch: Batch, cfg):
-    batch.set_tiles(cfg["threads"], cfg.get("blocks", 0), [cfg["tile_x"][w.nx] for w in batch.ws_list])
+    rows = cfg.get("rows", {})
+    batch.set_tiles(cfg["threads"], cfg.get("blocks", 0), [cfg["tile_x"][w.nx] for w in batch.ws_list],
+                    [rows.get(w.nx, 2) for w in batch.ws_list])

@@ -72,9 +72,11 @@ class Batch:
         torch.cuda.synchronize(self.device)
         _lib.check(self.lib.cx_batch_bind(self.h, _vp_array(self.g), _vp_array(self.E)), "cx_batch_bind")
 
-    def set_tiles(self, threads=256, blocks=0, tile_x=None):
+    def set_tiles(self, threads=256, blocks=0, tile_x=None, rows=None):
+        """Tile width and rows per thread of every problem (None: defaults)."""
         arr = None if tile_x is None else (ctypes.c_int * self.count)(*tile_x)
-        _lib.check(self.lib.cx_batch_set_tiles(self.h, threads, blocks, arr), "cx_batch_set_tiles")
+        rws = None if rows is None else (ctypes.c_int * self.count)(*rows)
+        _lib.check(self.lib.cx_batch_set_tiles(self.h, threads, blocks, arr, rws), "cx_batch_set_tiles")
 
     def _enter(self):
         # inputs written on the caller's stream are visible to the batch's stream
@@ -97,6 +99,26 @@ class Batch:
         _lib.check(self.lib.cx_batch_gradient(self.h, _ptr(self.out)), "cx_batch_gradient")
         self._leave()
         return self.out[: self.count], self.out[self.count: 2 * self.count], self.out[2 * self.count:]
+
+    def adjoint(self, seeds=None, add_to_cost_seed=False):
+        """Seeded AMRT sweep (seeds: list of [ny, nx] device tensors, the
+        adjoint of u^N, or additions to u^N - u_target) after forward();
+        gradients land in self.E.  Returns (||dJ/dg||^2, max |dJ/dg|) per
+        problem."""
+        self._seeds = None if seeds is None else [s.contiguous() for s in seeds]
+        arr = None if seeds is None else _vp_array(self._seeds)
+        self._enter()
+        _lib.check(self.lib.cx_batch_adjoint(self.h, arr, 1 if add_to_cost_seed else 0, _ptr(self.out)),
+                   "cx_batch_adjoint")
+        self._leave()
+        return self.out[self.count: 2 * self.count], self.out[2 * self.count:]
+
+    def axpy(self, lam):
+        """g[i] <- g[i] - lam[i] E[i] (lam: per-problem floats)."""
+        arr = (ctypes.c_double * self.count)(*[float(x) for x in lam])
+        self._enter()
+        _lib.check(self.lib.cx_batch_axpy(self.h, arr), "cx_batch_axpy")
+        self._leave()
 
     def step(self):
         """One Armijo gradient-descent iteration of every enabled problem: the

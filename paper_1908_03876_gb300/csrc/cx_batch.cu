@@ -45,7 +45,9 @@ template <typename T> struct BRec {
     int win_len;     // steps per control window (1: one control per step)
     int nwin;        // control windows
     int tile0;       // first global tile of this problem
-    int tx, ty;      // tile shape (tx * ty = NT)
+    int tx, ty;      // threads of a block as tx x ty (tx * ty = NT)
+    int tx_shift;    // log2 tx
+    int rr;          // rows per thread: a tile is tx x (ty rr) nodes
     int tiles_x;
     int slot0;       // first reduction slot
 };
@@ -145,12 +147,18 @@ __device__ __forceinline__ int find_problem(const int* sh, int count, int t) {
     return lo;
 }
 
-template <typename T> __device__ __forceinline__ NodeIdx tile_node(const BRec<T>& R, int local) {
-    const CxConst& C = R.C;
+// this thread's first node (row step 0) of tile `local` of problem R
+template <typename T> __device__ __forceinline__ void tile_origin(const BRec<T>& R, int local, int& x, int& y) {
     const int tyi = local / R.tiles_x, txi = local - tyi * R.tiles_x;
+    x = txi * R.tx + ((int)threadIdx.x & (R.tx - 1));
+    y = tyi * R.ty * R.rr + ((int)threadIdx.x >> R.tx_shift);
+}
+
+template <typename T> __device__ __forceinline__ NodeIdx node_at(const BRec<T>& R, int x, int y) {
+    const CxConst& C = R.C;
     NodeIdx r;
-    r.x = txi * R.tx + (int)threadIdx.x % R.tx;
-    r.y = tyi * R.ty + (int)threadIdx.x / R.tx;
+    r.x = x;
+    r.y = y;
     const bool in = r.x < C.nx && r.y < C.ny;
     r.k = in ? r.y * C.nx + r.x : 0;
     r.fluid = in && !(C.has_solid && C.solid[r.k]);
@@ -191,23 +199,39 @@ __global__ void __launch_bounds__(NT) k_batch(const BRec<T>* __restrict__ recs, 
         }
         return total;
     };
+    // Work items are (tile, row step j < rr): the thread updates node
+    // (x, y + j ty) of the tile; the next item is staged while the current
+    // one is computed.  Cost / gradient partials accumulate over a run of
+    // consecutive items of one problem and are flushed into the slot of the
+    // run's first tile (the runs are the same at every launch, so the sums
+    // are reproducible).
     int p = 0;
     int t = next_live(blockIdx.x, p);
-    NodeIdx cur = t < total ? tile_node(recs[p], t - sh_tile0[p]) : no_node();
+    int j = 0, x = 0, y = 0;
+    NodeIdx cur = no_node();
     if (t < total) {
+        tile_origin(recs[p], t - sh_tile0[p], x, y);
+        cur = node_at(recs[p], x, y);
         if constexpr (ADJ)
             adj_stage<T, Q, NT>(recs[p].C, adj_args(recs[p], st), cur, s0);
         else
             fwd_stage<T, Q, NT>(recs[p].C, fwd_args(recs[p], st, lam, p), cur, s0);
     }
     cp_async_commit();
+    int run_tile = t;
+    typename SqAccT<T>::type acc;
     bool odd = false;
     while (t < total) {
-        int pn = 0;
-        const int tn = next_live(t + G, pn);
+        const BRec<T>& R = recs[p];
+        int tn = t, pn = p, jn = j + 1, xn = x, yn = y + R.ty;
+        if (jn == R.rr) {
+            jn = 0;
+            tn = next_live(t + G, pn);
+            if (tn < total) tile_origin(recs[pn], tn - sh_tile0[pn], xn, yn);
+        }
         NodeIdx nxt = no_node();
         if (tn < total) {
-            nxt = tile_node(recs[pn], tn - sh_tile0[pn]);
+            nxt = node_at(recs[pn], xn, yn);
             if constexpr (ADJ)
                 adj_stage<T, Q, NT>(recs[pn].C, adj_args(recs[pn], st), nxt, odd ? s0 : s1);
             else
@@ -215,18 +239,23 @@ __global__ void __launch_bounds__(NT) k_batch(const BRec<T>* __restrict__ recs, 
         }
         cp_async_commit();
         cp_async_wait<1>();
-        const BRec<T>& R = recs[p];
-        typename SqAccT<T>::type acc;
         if constexpr (ADJ)
             adj_compute<T, Q, NT>(R.C, R.K, adj_args(R, st), cur, odd ? s1 : s0, acc);
         else
             fwd_compute<T, Q, NT>(R.C, R.K, fwd_args(R, st, lam, p), cur, odd ? s1 : s0, acc);
-        if (st.want_sum) {
-            const int slot = R.slot0 + (t - sh_tile0[p]) * (NT >> 5) + ((int)threadIdx.x >> 5);
-            acc.flush(sum_slots + slot, max_slots ? max_slots + slot : nullptr);
+        if (pn != p || tn >= total) {
+            if (st.want_sum) {
+                const int slot = R.slot0 + (run_tile - sh_tile0[p]) * (NT >> 5) + ((int)threadIdx.x >> 5);
+                acc.flush(sum_slots + slot, max_slots ? max_slots + slot : nullptr);
+            }
+            acc = typename SqAccT<T>::type{};
+            run_tile = tn;
         }
         t = tn;
         p = pn;
+        j = jn;
+        x = xn;
+        y = yn;
         cur = nxt;
         odd = !odd;
     }
@@ -294,6 +323,12 @@ template <typename T> __global__ void k_baxpy(const BRec<T>* __restrict__ recs, 
         g[i] = fma(-l, E[i], g[i]);
 }
 
+// terminal adjoint seed plus a caller's addition: wu += add (n nodes)
+template <typename T> __global__ void k_add_seed(T* wu, const T* add, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        wu[i] += add[i];
+}
+
 // Node-plane operations over all problems: zero sigma (op 0), restore Phi
 // from checkpoint slot `slot` (op 1).
 template <typename T>
@@ -321,6 +356,7 @@ struct BatchHost {
     size_t esz = 4;
     std::vector<cx_problem*> probs;
     std::vector<int> tx; // tile width per problem
+    std::vector<int> rr; // rows per thread per tile, per problem
     char* ws = nullptr;
     size_t off_rec = 0, off_tile0 = 0, off_fin = 0, off_sums = 0, off_maxs = 0, off_out = 0, off_status = 0;
     size_t off_active = 0, off_lam = 0;
@@ -366,8 +402,8 @@ void plan_tiles(BatchHost& h, std::vector<int>& tile0, std::vector<int>& slot0) 
     tile0.assign(h.count + 1, 0);
     slot0.assign(h.count + 1, 0);
     for (int i = 0; i < h.count; ++i) {
-        const int tx = h.tx[i], ty = h.threads / tx;
-        const int nt = ((h.probs[i]->d.nx + tx - 1) / tx) * ((h.probs[i]->d.ny + ty - 1) / ty);
+        const int tx = h.tx[i], th = (h.threads / tx) * h.rr[i];
+        const int nt = ((h.probs[i]->d.nx + tx - 1) / tx) * ((h.probs[i]->d.ny + th - 1) / th);
         tile0[i + 1] = tile0[i] + nt;
         slot0[i + 1] = slot0[i] + nt * (h.threads / 32);
     }
@@ -407,6 +443,9 @@ template <typename T> cx_status upload_table(BatchHost& h) {
         R.tile0 = tile0[i];
         R.tx = h.tx[i];
         R.ty = h.threads / h.tx[i];
+        R.tx_shift = 0;
+        while ((1 << R.tx_shift) < R.tx) ++R.tx_shift;
+        R.rr = h.rr[i];
         R.tiles_x = (p->d.nx + R.tx - 1) / R.tx;
         R.slot0 = slot0[i];
         fin[i].cost = p->at<double>(p->lay.off_part);
@@ -788,17 +827,21 @@ cx_status cx_batch_workspace_size(const cx_problem_desc* descs, int count, size_
     return batch_layout(descs, count, nullptr, &toff, bytes);
 }
 
-cx_status cx_batch_set_tiles(cx_batch* b, int threads, int blocks, const int* tile_x) {
+cx_status cx_batch_set_tiles(cx_batch* b, int threads, int blocks, const int* tile_x, const int* rows) {
     if (!b || (threads != 128 && threads != 256) || blocks < 0) return CX_ERR_INVALID_ARG;
     BatchHost& h = b->h;
-    std::vector<int> tx(h.count);
+    std::vector<int> tx(h.count), rr(h.count);
     for (int i = 0; i < h.count; ++i) {
         const int t = tile_x ? tile_x[i] : std::min(threads, 256);
-        if (t < 32 || t > threads || threads % t != 0 || threads / t > 8) return CX_ERR_INVALID_ARG;
+        if (t < 32 || t > threads || threads % t != 0 || threads / t > 8 || (t & (t - 1))) return CX_ERR_INVALID_ARG;
+        const int r = rows ? rows[i] : 2;
+        if (r < 1 || r > 16) return CX_ERR_INVALID_ARG;
         tx[i] = t;
+        rr[i] = r;
     }
     h.threads = threads;
     h.tx = tx;
+    h.rr = rr;
     const int occ = h.esz == 8 ? forward_occupancy<double>(h.Q, threads) : forward_occupancy<float>(h.Q, threads);
     h.blocks = blocks > 0 ? blocks : h.probs[0]->nsm * occ;
     drop_graphs(h);
@@ -868,7 +911,7 @@ cx_status cx_batch_create(const cx_problem_desc* descs, int count, void* workspa
         cx_batch_destroy(b);
         return CX_ERR_CUDA;
     }
-    rc = cx_batch_set_tiles(b, 256, 0, nullptr);
+    rc = cx_batch_set_tiles(b, 256, 0, nullptr, nullptr);
     if (rc) {
         cx_batch_destroy(b);
         return rc;
@@ -932,6 +975,70 @@ cx_status cx_batch_set_enabled(cx_batch* b, const int* enabled) {
     cx_status rc = upload_ints(h, h.off_active, h.enabled);
     if (rc) return rc;
     B_CUDA(cudaStreamSynchronize(h.stream));
+    return CX_OK;
+}
+
+cx_status cx_batch_adjoint(cx_batch* b, const void* const* seed_u, int add_to_cost_seed, double* out_dev) {
+    if (!b) return CX_ERR_INVALID_ARG;
+    BatchHost& h = b->h;
+    if (!h.has_init || !h.bound) return CX_ERR_STATE;
+    if (!h.fwd_at_g) return CX_ERR_STATE; // needs the forward state of the bound controls
+    for (void* p : h.dJdg)
+        if (!p) return CX_ERR_INVALID_ARG;
+    if (seed_u)
+        for (int i = 0; i < h.count; ++i) {
+            if (!seed_u[i] || !h.enabled[i]) continue;
+            cx_problem* p = h.probs[i];
+            const size_t n = (size_t)p->d.nx * p->d.ny;
+            if (!add_to_cost_seed) {
+                B_CUDA(cudaMemcpyAsync(p->ws + p->lay.off_wu, seed_u[i], n * h.esz, cudaMemcpyDeviceToDevice,
+                                       h.stream));
+            } else {
+                const int blocks = (int)std::min<size_t>((n + 255) / 256, 1024);
+                if (h.esz == 8)
+                    k_add_seed<double><<<blocks, 256, 0, h.stream>>>(p->at<double>(p->lay.off_wu),
+                                                                     static_cast<const double*>(seed_u[i]), n);
+                else
+                    k_add_seed<float><<<blocks, 256, 0, h.stream>>>(p->at<float>(p->lay.off_wu),
+                                                                    static_cast<const float*>(seed_u[i]), n);
+                B_CUDA(cudaGetLastError());
+            }
+        }
+    cx_status rc = h.esz == 8 ? run_graph<double>(h, G_ADJ) : run_graph<float>(h, G_ADJ);
+    if (rc) return rc;
+    // the terminal seeds now hold seed_u and the recompute overwrote the tape:
+    // the next step or gradient starts with a full forward
+    h.fwd_at_g = false;
+    if (out_dev)
+        B_CUDA(cudaMemcpyAsync(out_dev + h.count, h.ws + h.off_out + sizeof(double) * h.count,
+                               sizeof(double) * 2 * h.count, cudaMemcpyDeviceToDevice, h.stream));
+    return CX_OK;
+}
+
+cx_status cx_batch_axpy(cx_batch* b, const double* lam) {
+    if (!b || !lam) return CX_ERR_INVALID_ARG;
+    BatchHost& h = b->h;
+    if (!h.bound) return CX_ERR_STATE;
+    std::vector<double> l(h.count, 0.0);
+    for (int i = 0; i < h.count; ++i) {
+        if (!std::isfinite(lam[i])) return CX_ERR_INVALID_ARG;
+        if (!h.enabled[i] || lam[i] == 0.0) continue;
+        if (!h.g[i] || !h.dJdg[i]) return CX_ERR_INVALID_ARG;
+        l[i] = lam[i];
+    }
+    cx_status rc = upload_lam(h, l);
+    if (rc) return rc;
+    if (h.esz == 8)
+        k_baxpy<double><<<dim3(64, h.count), 256, 0, h.stream>>>(
+            reinterpret_cast<const BRec<double>*>(h.ws + h.off_rec), h.count,
+            reinterpret_cast<const double*>(h.ws + h.off_lam));
+    else
+        k_baxpy<float><<<dim3(64, h.count), 256, 0, h.stream>>>(
+            reinterpret_cast<const BRec<float>*>(h.ws + h.off_rec), h.count,
+            reinterpret_cast<const float*>(h.ws + h.off_lam));
+    B_CUDA(cudaGetLastError());
+    h.fwd_at_g = false;
+    h.lam_prev.assign(h.count, 0.0);
     return CX_OK;
 }
 

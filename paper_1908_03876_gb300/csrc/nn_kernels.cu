@@ -49,8 +49,9 @@ __device__ __forceinline__ float im2col(const bf16* X, const ConvShape& s, int k
     return __bfloat162float(X[((size_t)b * s.Cin + ci) * hw + (size_t)yy * s.W + xx]);
 }
 
-// mode 0: forward (A = W [Cout][K], B = im2col(X));  mode 1: weight gradient
-// (A = dY as [Cout][pixels], B[k=pixel][n=(ci,t)] = im2col(X)[n][k]).
+// mode 0: forward (A = W [Cout][K], B = im2col(X)), BF16 output; mode 2: the
+// same with FP32 output; mode 1: weight gradient (A = dY as [Cout][pixels],
+// B[k=pixel][n=(ci,t)] = im2col(X)[n][k]).
 template <int MODE>
 __global__ void __launch_bounds__(NTHR) k_conv_gemm(const bf16* __restrict__ A_src, const bf16* __restrict__ X,
                                                     const float* __restrict__ bias, bf16* __restrict__ Y,
@@ -60,11 +61,12 @@ __global__ void __launch_bounds__(NTHR) k_conv_gemm(const bf16* __restrict__ A_s
     const int kk = s.ks * s.ks;
     const int hw = s.H * s.W;
     const int M = s.Cout;
-    const int N = MODE == 0 ? s.B * hw : s.Cin * kk;
-    const int Ktot = MODE == 0 ? s.Cin * kk : s.B * hw;
+    constexpr bool FWD = MODE != 1;
+    const int N = FWD ? s.B * hw : s.Cin * kk;
+    const int Ktot = FWD ? s.Cin * kk : s.B * hw;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-    const int kbeg = MODE == 0 ? 0 : blockIdx.z * k_chunk;
-    const int kend = MODE == 0 ? Ktot : min(Ktot, kbeg + k_chunk);
+    const int kbeg = FWD ? 0 : blockIdx.z * k_chunk;
+    const int kend = FWD ? Ktot : min(Ktot, kbeg + k_chunk);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int wm = warp >> 1, wn = warp & 1;
     const int g = lane >> 2, tg = lane & 3;
@@ -83,7 +85,7 @@ __global__ void __launch_bounds__(NTHR) k_conv_gemm(const bf16* __restrict__ A_s
             const int m = m0 + r, k = k0 + c;
             float v = 0.0f;
             if (m < M && k < kend) {
-                if (MODE == 0) v = __bfloat162float(A_src[(size_t)m * Ktot + k]);
+                if (FWD) v = __bfloat162float(A_src[(size_t)m * Ktot + k]);
                 else {
                     const int b = k / hw, p = k - b * hw;
                     v = __bfloat162float(A_src[((size_t)b * s.Cout + m) * hw + p]);
@@ -95,7 +97,7 @@ __global__ void __launch_bounds__(NTHR) k_conv_gemm(const bf16* __restrict__ A_s
             const int r = e / BK, c = e - r * BK;
             const int n = n0 + r, k = k0 + c;
             float v = 0.0f;
-            if (n < N && k < kend) v = MODE == 0 ? im2col(X, s, k, n) : im2col(X, s, n, k);
+            if (n < N && k < kend) v = FWD ? im2col(X, s, k, n) : im2col(X, s, n, k);
             Bs[r][c] = __float2bfloat16(v);
         }
         __syncthreads();
@@ -134,11 +136,12 @@ __global__ void __launch_bounds__(NTHR) k_conv_gemm(const bf16* __restrict__ A_s
                 const int n = n0 + wn * 32 + nt * 8 + 2 * tg + (r & 1);
                 if (m >= M || n >= N) continue;
                 float v = acc[mt][nt][r];
-                if (MODE == 0) {
+                if (FWD) {
                     if (bias) v += bias[m];
                     if (relu) v = fmaxf(v, 0.0f);
                     const int b = n / hw, p = n - b * hw;
-                    Y[((size_t)b * s.Cout + m) * hw + p] = __float2bfloat16(v);
+                    if (MODE == 0) Y[((size_t)b * s.Cout + m) * hw + p] = __float2bfloat16(v);
+                    else reinterpret_cast<float*>(Y)[((size_t)b * s.Cout + m) * hw + p] = v;
                 } else {
                     partial[((size_t)blockIdx.z * M + m) * N + n] = v;
                 }
@@ -256,6 +259,24 @@ __global__ void k_adam(float* p, float* m, float* v, const float* g, bf16* pb, s
         pb[i] = __float2bfloat16(pi);
     }
 }
+// separable periodic Gaussian low-pass of [BC][H][W] FP32 planes, one axis
+// per launch (axis 0: along x, 1: along y); taps w[-r..r] in `taps`
+__global__ void k_smooth(const float* in, float* out, int BC, int H, int W, int axis, const float* taps, int r) {
+    const size_t n = (size_t)BC * H * W;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t bc = i / ((size_t)H * W);
+        const int rem = (int)(i - bc * H * W), y = rem / W, x = rem - y * W;
+        const float* plane = in + bc * H * W;
+        float acc = 0.0f;
+        for (int d = -r; d <= r; ++d) {
+            const int xx = axis == 0 ? ((x + d) % W + W) % W : x;
+            const int yy = axis == 1 ? ((y + d) % H + H) % H : y;
+            acc = fmaf(taps[d + r], plane[(size_t)yy * W + xx], acc);
+        }
+        out[i] = acc;
+    }
+}
+
 __global__ void k_cast(const float* in, bf16* out, size_t n) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         out[i] = __float2bfloat16(in[i]);
@@ -290,6 +311,29 @@ cx_status cx_nn_conv_forward(const uint16_t* x, const uint16_t* w, const float* 
     dim3 grid((B * H * W + BN - 1) / BN, (Cout + BM - 1) / BM);
     k_conv_gemm<0><<<grid, NTHR, 0, stream>>>(reinterpret_cast<const bf16*>(w), reinterpret_cast<const bf16*>(x),
                                               bias, reinterpret_cast<bf16*>(y), nullptr, s, relu, 0);
+    NN_CHECK();
+    return CX_OK;
+}
+
+cx_status cx_nn_conv_forward_f32(const uint16_t* x, const uint16_t* w, const float* bias, float* y, int B, int Cin,
+                                 int Cout, int H, int W, int ks, cudaStream_t stream) {
+    if (!x || !w || !y || !shape_ok(B, Cin, Cout, H, W, ks)) return CX_ERR_INVALID_ARG;
+    ConvShape s{B, Cin, Cout, H, W, ks};
+    dim3 grid((B * H * W + BN - 1) / BN, (Cout + BM - 1) / BM);
+    k_conv_gemm<2><<<grid, NTHR, 0, stream>>>(reinterpret_cast<const bf16*>(w), reinterpret_cast<const bf16*>(x),
+                                              bias, reinterpret_cast<bf16*>(y), nullptr, s, 0, 0);
+    NN_CHECK();
+    return CX_OK;
+}
+
+cx_status cx_nn_smooth(const float* in, float* tmp, float* out, int BC, int H, int W, const float* taps, int radius,
+                       cudaStream_t stream) {
+    if (!in || !tmp || !out || !taps || BC < 1 || H < 1 || W < 1 || radius < 0 || radius > 64)
+        return CX_ERR_INVALID_ARG;
+    const size_t n = (size_t)BC * H * W;
+    k_smooth<<<grid_for(n), 256, 0, stream>>>(in, tmp, BC, H, W, 0, taps, radius);
+    NN_CHECK();
+    k_smooth<<<grid_for(n), 256, 0, stream>>>(tmp, out, BC, H, W, 1, taps, radius);
     NN_CHECK();
     return CX_OK;
 }

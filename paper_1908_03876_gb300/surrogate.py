@@ -78,8 +78,13 @@ class UNet:
     def _new(self, B, C, H, W):
         return torch.empty((B, C, H, W), dtype=torch.bfloat16, device=self.device)
 
-    def _conv(self, c: Conv, x, relu):
+    def _conv(self, c: Conv, x, relu, out_f32=False):
         B, _, H, W = x.shape
+        if out_f32:
+            y = torch.empty((B, c.cout, H, W), dtype=torch.float32, device=self.device)
+            _lib.check(self.lib.cx_nn_conv_forward_f32(_p(x), _p(c.wb), _p(c.b), _p(y), B, c.cin, c.cout, H, W, c.ks,
+                                                       self._s()), "cx_nn_conv_forward_f32")
+            return y
         y = self._new(B, c.cout, H, W)
         _lib.check(self.lib.cx_nn_conv_forward(_p(x), _p(c.wb), _p(c.b), _p(y), B, c.cin, c.cout, H, W, c.ks,
                                                1 if relu else 0, self._s()), "cx_nn_conv_forward")
@@ -133,8 +138,9 @@ class UNet:
         return y
 
     # -------------------------------------------------------------- network
-    def forward(self, x):
-        """x: BF16 [B, cin, H, W] (H, W divisible by 2^(levels-1)); returns BF16 [B, cout, H, W]."""
+    def forward(self, x, out_f32=False):
+        """x: BF16 [B, cin, H, W] (H, W divisible by 2^(levels-1)); returns
+        [B, cout, H, W] in BF16 (training) or FP32 (out_f32: inference)."""
         x = x.to(torch.bfloat16).contiguous()
         cache = {"enc": [], "dec": {}}
         h = x
@@ -153,7 +159,7 @@ class UNet:
             d2 = self._conv(c2, s, True)
             cache["dec"][l] = (u, d1, s, d2)
             h = d2
-        out = self._conv(self.head, h, False)
+        out = self._conv(self.head, h, False, out_f32=out_f32)
         cache["head_in"] = h
         self.cache = cache
         return out
@@ -205,6 +211,22 @@ class UNet:
         self.backward(dout)
         self.adam_step(lr)
         return loss
+
+    def smooth(self, y, sigma):
+        """Periodic Gaussian low-pass (standard deviation sigma cells) of every
+        [H][W] plane of the FP32 tensor y."""
+        if sigma <= 0:
+            return y
+        r = int(np.ceil(3 * sigma))
+        d = np.arange(-r, r + 1)
+        taps = np.exp(-0.5 * (d / sigma) ** 2)
+        taps = torch.as_tensor(taps / taps.sum(), dtype=torch.float32, device=self.device)
+        B, C, H, W = y.shape
+        tmp = torch.empty_like(y)
+        out = torch.empty_like(y)
+        _lib.check(self.lib.cx_nn_smooth(_p(y), _p(tmp), _p(out), B * C, H, W, _p(taps), r, self._s()),
+                   "cx_nn_smooth")
+        return out
 
     def flops(self, B, H, W, training=True):
         """Convolution FLOPs (2 per multiply-add) of one forward, or of one

@@ -34,14 +34,14 @@ def _mixed(precision=64, N=14, k=5):
     return ws
 
 
-def _run_batch(ws, tile_x=None, threads=256):
+def _run_batch(ws, tile_x=None, threads=256, rows=None):
     from paper_1908_03876_gb300.batch import Batch
 
     b = Batch(ws)
     gs = [torch.as_tensor(w.random_control(50 + i, 0.02), dtype=b.dtype, device=b.device) for i, w in enumerate(ws)]
     b.bind(gs)
-    if tile_x is not None:
-        b.set_tiles(threads, 0, tile_x)
+    if tile_x is not None or rows is not None:
+        b.set_tiles(threads, 0, tile_x, rows)
     J, e2, emax = b.gradient()
     b.stream.synchronize()
     b.status()
@@ -85,7 +85,7 @@ def test_batch_equals_single_problem():
 def test_batch_tile_shapes_and_replay():
     ws = _mixed(N=9, k=4)
     _, _, J1, E1, F1, _ = _run_batch(ws, tile_x=[32] * len(ws), threads=256)
-    _, _, J2, E2, F2, _ = _run_batch(ws, tile_x=[64, 128, 32, 64, 32, 128], threads=128)
+    _, _, J2, E2, F2, _ = _run_batch(ws, tile_x=[64, 128, 32, 64, 32, 128], threads=128, rows=[1, 3, 16, 2, 5, 1])
     b, gs, J3, E3, F3, _ = _run_batch(ws)
     J4, _, _ = b.gradient()  # graph replay
     b.stream.synchronize()
@@ -119,8 +119,9 @@ def test_autotuner_picks_admissible_config(tmp_path):
     assert cfg["threads"] in (128, 256)
     for nx, tx in cfg["tile_x"].items():
         assert cfg["threads"] % tx == 0 and cfg["threads"] // tx <= 8
+        assert cfg["rows"][nx] in autotune.ROWS
     again = autotune.autotune(ws, probe_steps=6, cache_path=str(tmp_path / "tune.json"))
-    assert again["tile_x"] == cfg["tile_x"]
+    assert again["tile_x"] == cfg["tile_x"] and again["rows"] == cfg["rows"]
     b = Batch(ws)
     b.bind(b.zeros_controls())
     J0 = b.forward().cpu().numpy().copy()
@@ -182,3 +183,43 @@ def test_batch_windowed_and_switched_off():
         go, io = oracle.gd_step(oracle.from_workload(ws[i]), before[i])
         assert abs(info[i]["J"] - io["J"]) <= 1e-12 * abs(io["J"]) and info[i]["trials"] == io["trials"]
         assert np.linalg.norm(gs[i].cpu().numpy() - go) <= 1e-12 * np.linalg.norm(go)
+
+
+def test_batch_seeded_adjoint_and_axpy():
+    """Seeded AMRT sweep of every problem (the adjoint of u^N given per
+    problem) against the oracle's seeded adjoint, then a per-problem axpy of
+    the controls, and a step from there (which must restart with a forward)."""
+    from paper_1908_03876_gb300.batch import Batch
+
+    ws = _mixed(N=12, k=5)[:3]
+    b = Batch(ws)
+    gs = [torch.as_tensor(w.random_control(90 + i, 0.02), dtype=b.dtype, device=b.device) for i, w in enumerate(ws)]
+    b.bind(gs)
+    b.forward()
+    rng = np.random.default_rng(5)
+    seeds = [torch.as_tensor(rng.standard_normal((w.ny, w.nx)), dtype=b.dtype, device=b.device) for w in ws]
+    e2, _ = b.adjoint(seeds)
+    e2 = e2.cpu().numpy()
+    for i, w in enumerate(ws):
+        _, Eo, _ = oracle.adjoint(oracle.from_workload(w), gs[i].cpu().numpy(), seed_u=seeds[i].cpu().numpy())
+        assert np.linalg.norm(b.E[i].cpu().numpy() - Eo) <= 1e-12 * np.linalg.norm(Eo), i
+        assert abs(e2[i] - np.sum(Eo * Eo)) <= 1e-11 * np.sum(Eo * Eo)
+    b.forward()
+    b.adjoint(seeds, add_to_cost_seed=True)  # seed = (u^N - u_target) + seeds
+    for i, w in enumerate(ws):
+        p = oracle.from_workload(w)
+        _, uN, _ = oracle.forward(p, gs[i].cpu().numpy())
+        _, Eo, _ = oracle.adjoint(p, gs[i].cpu().numpy(), seed_u=uN - w.u_tgt + seeds[i].cpu().numpy())
+        assert np.linalg.norm(b.E[i].cpu().numpy() - Eo) <= 1e-12 * np.linalg.norm(Eo), i
+    before = [g.cpu().numpy().copy() for g in gs]
+    E = [e.cpu().numpy().copy() for e in b.E]
+    lam = [0.5, 0.0, 2.0]
+    b.axpy(lam)
+    torch.cuda.synchronize()
+    for i in range(3):
+        assert np.abs(gs[i].cpu().numpy() - (before[i] - lam[i] * E[i])).max() <= 1e-14 * (1 + np.abs(before[i]).max())
+    info, st = b.step()
+    assert st == [0, 0, 0]
+    for i, w in enumerate(ws):
+        J0o = oracle.forward(oracle.from_workload(w), before[i] - lam[i] * E[i])[0]
+        assert abs(info[i]["J0"] - J0o) <= 1e-12 * abs(J0o)

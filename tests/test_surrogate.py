@@ -226,3 +226,31 @@ def test_unet_training_lowers_loss():
         last = float(net.train_step(xd, td, lr=2e-3))
     print(f"[unet train] loss {first:.3e} -> {last:.3e}")
     assert last < 0.1 * first
+
+
+def test_conv_forward_f32_and_smooth():
+    """FP32-output head convolution, and the periodic Gaussian low-pass
+    against an explicit periodic sum."""
+    lib, check = _lib()
+    B, Cin, Cout, H, W = 2, 32, 8, 12, 16
+    x = bf16_data((B, Cin, H, W), 20)
+    w = bf16_data((Cout, Cin, 1, 1), 21, scale=0.2)
+    b = torch.linspace(-0.1, 0.1, Cout, dtype=torch.float32)
+    xd, wd, bd = x.cuda(), w.cuda(), b.cuda()
+    y = torch.empty((B, Cout, H, W), dtype=torch.float32, device="cuda")
+    check(lib.cx_nn_conv_forward_f32(_p(xd), _p(wd), _p(bd), _p(y), B, Cin, Cout, H, W, 1, _s()), "conv f32")
+    ref = R.conv(x.double(), w.double(), b.double())
+    assert rel_l2(y, ref) < 1e-6
+    sigma, r = 1.5, 5
+    d = np.arange(-r, r + 1)
+    taps = np.exp(-0.5 * (d / sigma) ** 2)
+    taps /= taps.sum()
+    f = torch.randn((3, H, W), generator=torch.Generator().manual_seed(22), dtype=torch.float64)
+    fd = f.float().cuda()
+    tmp, out = torch.empty_like(fd), torch.empty_like(fd)
+    td = torch.as_tensor(taps, dtype=torch.float32, device="cuda")
+    check(lib.cx_nn_smooth(_p(fd), _p(tmp), _p(out), 3, H, W, _p(td), r, _s()), "smooth")
+    g = f.numpy()
+    ex = sum(taps[i] * np.roll(g, -int(d[i]), axis=2) for i in range(len(d)))
+    ex = sum(taps[i] * np.roll(ex, -int(d[i]), axis=1) for i in range(len(d)))
+    assert np.abs(out.cpu().numpy() - ex).max() < 1e-5
