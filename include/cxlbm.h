@@ -265,24 +265,33 @@ cx_status cx_batch_destroy(cx_batch* b);
  * convolutional network proposes the initial control that the paper's
  * gradient algorithm then refines.)  Tensors are NCHW; uint16_t* arguments are
  * BF16 device arrays, float* FP32 device arrays; every call is asynchronous
- * on `stream`.  Convolutions are 3x3 with zero padding 1 or 1x1 (ks), as
- * implicit GEMMs on the tensor cores with FP32 accumulation.
+ * on `stream`.  Convolutions are 3x3 with zero padding 1 or 1x1 (ks), direct
+ * convolutions on the tensor cores (BF16 products, FP32 accumulation) that
+ * read weights in the packed layouts of cx_nn_pack_weights.
  * Errors: CX_ERR_INVALID_ARG for inconsistent shapes or NULL arguments,
  * CX_ERR_CUDA on a launch failure. */
-/* y[B][Cout][H][W] = act(bias + conv(x[B][Cin][H][W], w[Cout][Cin][ks][ks])); act = ReLU if relu. bias may be NULL. */
-cx_status cx_nn_conv_forward(const uint16_t* x, const uint16_t* w, const float* bias, uint16_t* y, int B, int Cin,
-                             int Cout, int H, int W, int ks, int relu, cudaStream_t stream);
+/* Elements of the packed BF16 weights of a [Cout][Cin][ks][ks] layer:
+ * which = 0 the forward pack, 1 the data-gradient pack. */
+size_t cx_nn_packed_weights(int Cout, int Cin, int ks, int which);
+/* Both packs of BF16 weights w[Cout][Cin][ks][ks]: w_fwd [ceil(Cin/16)][ks*ks][Cout][16]
+ * and w_bwd [ceil(Cout/16)][ks*ks][Cin][16] (flipped taps, in/out swapped), zero-padded. */
+cx_status cx_nn_pack_weights(const uint16_t* w, int Cout, int Cin, int ks, uint16_t* w_fwd, uint16_t* w_bwd,
+                             cudaStream_t stream);
+/* y[B][Cout][H][W] = act(bias + conv(x[B][Cin][H][W], w)); w_fwd the forward
+ * pack of w; act = ReLU if relu.  bias may be NULL. */
+cx_status cx_nn_conv_forward(const uint16_t* x, const uint16_t* w_fwd, const float* bias, uint16_t* y, int B,
+                             int Cin, int Cout, int H, int W, int ks, int relu, cudaStream_t stream);
 /* As cx_nn_conv_forward without activation, writing FP32 y (the network's output layer). */
-cx_status cx_nn_conv_forward_f32(const uint16_t* x, const uint16_t* w, const float* bias, float* y, int B, int Cin,
-                                 int Cout, int H, int W, int ks, cudaStream_t stream);
+cx_status cx_nn_conv_forward_f32(const uint16_t* x, const uint16_t* w_fwd, const float* bias, float* y, int B,
+                                 int Cin, int Cout, int H, int W, int ks, cudaStream_t stream);
 /* Separable periodic low-pass of BC planes [H][W] (FP32): out = taps (*) along
  * x then y, taps[0..2 radius] a device FP32 array (radius <= 64); tmp is
  * scratch of the same size as in. */
 cx_status cx_nn_smooth(const float* in, float* tmp, float* out, int BC, int H, int W, const float* taps, int radius,
                        cudaStream_t stream);
-/* dx = gradient w.r.t. x of sum(dy * conv(x, w)); w_flip: scratch of Cout*Cin*ks*ks BF16. */
-cx_status cx_nn_conv_backward_data(const uint16_t* dy, const uint16_t* w, uint16_t* dx, uint16_t* w_flip, int B,
-                                   int Cin, int Cout, int H, int W, int ks, cudaStream_t stream);
+/* dx[B][Cin][H][W] = gradient w.r.t. x of sum(dy * conv(x, w)); w_bwd the data-gradient pack of w. */
+cx_status cx_nn_conv_backward_data(const uint16_t* dy, const uint16_t* w_bwd, uint16_t* dx, int B, int Cin, int Cout,
+                                   int H, int W, int ks, cudaStream_t stream);
 /* FP32 scratch bytes for cx_nn_conv_backward_weight with `splits` pixel ranges. */
 size_t cx_nn_conv_backward_weight_scratch(int B, int Cin, int Cout, int H, int W, int ks, int splits);
 /* dw[Cout][Cin][ks][ks] (FP32) and db[Cout] (FP32, may be NULL): gradients of sum(dy * conv). */

@@ -1,17 +1,19 @@
 // nn_kernels.cu -- kernels of the warm-start surrogate (a small convolutional
-// U-Net that maps a problem's initial state and parameters to a proposed
-// control).  BF16 weights and activations, FP32 accumulation.
+// U-Net that proposes the initial control).  BF16 weights and activations,
+// FP32 accumulation, on the tensor cores through mma.sync m16n8k16.
 //
-// Convolutions (3x3, padding 1, or 1x1) are implicit GEMMs on the tensor
-// cores with mma.sync m16n8k16 (BF16 inputs, FP32 accumulators):
-//   forward        Y[b,co,p] = bias[co] + sum_{ci,t} W[co,ci,t] X[b,ci,p+t]
-//                  (M = Cout, N = B*H*W pixels, K = Cin*ks*ks)
-//   data gradient  the forward kernel applied to dY with W' [ci,co,flip(t)]
-//   weight grad.   dW[co,ci,t] = sum_{b,p} dY[b,co,p] X[b,ci,p+t]
-//                  (M = Cout, N = Cin*ks*ks, K = B*H*W, split over blocks into
-//                  FP32 partials reduced in a fixed order)
-// Tiles: 64 x 64 x 32 per block of 4 warps, each warp a 32 x 32 sub-tile of
-// 2 x 4 mma tiles; operands staged in padded shared memory.
+// Convolutions (3x3 with zero padding 1, or 1x1) are direct: a block owns 64
+// output channels x one 8x8 pixel tile of one image and loops over the input
+// channels in chunks of 16.  Per chunk it stages the input patch (8+2)^2 x 16
+// channel-last in shared memory once and reuses it for all 9 taps, with the
+// chunk's weights pre-packed as [chunk][tap][out][16]:
+//   forward        Y[b,o,p] = bias[o] + sum_{c,t} W[o,c,t] X[b,c,p+t]
+//   data gradient  the same kernel on dY with the flipped, transposed pack
+//   weight grad.   dW[o,c,t] = sum_{b,p} dY[b,o,p] X[b,c,p+t]: a block owns
+//                  64 outputs x 16 inputs x 9 taps and loops over pixel tiles
+//                  (split over blocks into FP32 partials reduced in a fixed
+//                  order); the patch is staged twice (aligned and shifted by
+//                  one column) so every fragment load is a 32-bit pair.
 #include <cstdint>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -22,7 +24,10 @@ namespace nn {
 
 typedef __nv_bfloat16 bf16;
 
-constexpr int BM = 64, BN = 64, BK = 32, PADK = BK + 8, NTHR = 128;
+constexpr int NTHR = 128;
+constexpr int CT = 64;  // output channels per block
+constexpr int KC = 16;  // input channels per chunk
+constexpr int KCP = 24; // padded channel stride of a staged pixel (halfs): conflict-free fragment loads
 
 __device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
     asm volatile(
@@ -32,44 +37,50 @@ __device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-struct ConvShape {
-    int B, Cin, Cout, H, W, ks;
-};
+__device__ __forceinline__ uint32_t ld32(const bf16* p) { return *reinterpret_cast<const uint32_t*>(p); }
 
-// element (k, n) of the implicit im2col matrix of X: k = ci*ks*ks + t, n = b*H*W + y*W + x
-__device__ __forceinline__ float im2col(const bf16* X, const ConvShape& s, int k, int n) {
-    const int kk = s.ks * s.ks;
-    const int ci = k / kk, t = k - ci * kk;
-    const int hw = s.H * s.W;
-    const int b = n / hw, r = n - b * hw;
-    const int y = r / s.W, x = r - y * s.W;
-    const int pad = s.ks / 2;
-    const int yy = y + t / s.ks - pad, xx = x + t % s.ks - pad;
-    if (yy < 0 || yy >= s.H || xx < 0 || xx >= s.W) return 0.0f;
-    return __bfloat162float(X[((size_t)b * s.Cin + ci) * hw + (size_t)yy * s.W + xx]);
+// Weight packs: forward Wf[c][t][o][j] = W[o][16c+j][t] (out = Cout, in = Cin);
+// data gradient Wb[c][t][o][j] = W[16c+j][o][taps-1-t] (out = Cin, in = Cout).
+__global__ void k_pack(const bf16* __restrict__ W, bf16* __restrict__ Wf, bf16* __restrict__ Wb, int Cout, int Cin,
+                       int taps) {
+    const size_t nf = (size_t)((Cin + KC - 1) / KC) * taps * Cout * KC;
+    const size_t nb = (size_t)((Cout + KC - 1) / KC) * taps * Cin * KC;
+    const bf16 zero = __float2bfloat16(0.0f);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nf + nb; i += (size_t)gridDim.x * blockDim.x) {
+        const bool fwd = i < nf;
+        const size_t e = fwd ? i : i - nf;
+        const int OC = fwd ? Cout : Cin, IC = fwd ? Cin : Cout;
+        const int j = (int)(e % KC);
+        const size_t r = e / KC;
+        const int o = (int)(r % OC);
+        const size_t r2 = r / OC;
+        const int t = (int)(r2 % taps), c = (int)(r2 / taps);
+        const int in = c * KC + j;
+        bf16 v = zero;
+        if (in < IC) v = fwd ? W[((size_t)o * Cin + in) * taps + t] : W[((size_t)in * Cin + o) * taps + (taps - 1 - t)];
+        (fwd ? Wf : Wb)[e] = v;
+    }
 }
 
-// mode 0: forward (A = W [Cout][K], B = im2col(X)), BF16 output; mode 2: the
-// same with FP32 output; mode 1: weight gradient (A = dY as [Cout][pixels],
-// B[k=pixel][n=(ci,t)] = im2col(X)[n][k]).
-template <int MODE>
-__global__ void __launch_bounds__(NTHR) k_conv_gemm(const bf16* __restrict__ A_src, const bf16* __restrict__ X,
-                                                    const float* __restrict__ bias, bf16* __restrict__ Y,
-                                                    float* __restrict__ partial, ConvShape s, int relu, int k_chunk) {
-    __shared__ __align__(16) bf16 As[BM][PADK];
-    __shared__ __align__(16) bf16 Bs[BN][PADK];
-    const int kk = s.ks * s.ks;
-    const int hw = s.H * s.W;
-    const int M = s.Cout;
-    constexpr bool FWD = MODE != 1;
-    const int N = FWD ? s.B * hw : s.Cin * kk;
-    const int Ktot = FWD ? s.Cin * kk : s.B * hw;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-    const int kbeg = FWD ? 0 : blockIdx.z * k_chunk;
-    const int kend = FWD ? Ktot : min(Ktot, kbeg + k_chunk);
+// Direct convolution, one 8x8 pixel tile x 64 outputs per block (4 warps:
+// 2 output halves x 2 pixel-row halves, each 2 x 4 mma tiles).
+// OUT 0: BF16 output with bias and optional ReLU; 1: FP32 output with bias.
+template <int KS, int OUT>
+__global__ void __launch_bounds__(NTHR) k_conv(const bf16* __restrict__ X, const bf16* __restrict__ Wp,
+                                               const float* __restrict__ bias, void* __restrict__ Yv, int B, int IC,
+                                               int OC, int H, int W, int relu) {
+    constexpr int PW = 8 + KS - 1, PP = PW * PW, TAPS = KS * KS, OFF = KS / 2;
+    __shared__ __align__(16) bf16 Ps[PP][KCP];
+    __shared__ __align__(16) bf16 Ws[TAPS][CT][KCP];
+    const int tiles_x = (W + 7) >> 3, tiles_y = (H + 7) >> 3;
+    int bt = blockIdx.x;
+    const int b = bt / (tiles_x * tiles_y);
+    bt -= b * tiles_x * tiles_y;
+    const int y0 = (bt / tiles_x) * 8, x0 = (bt % tiles_x) * 8;
+    const int oc0 = blockIdx.y * CT;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm = warp >> 1, wn = warp & 1;
-    const int g = lane >> 2, tg = lane & 3;
+    const int wm = warp >> 1, wn = warp & 1, g = lane >> 2, tg = lane & 3;
+    const size_t hw = (size_t)H * W;
     float acc[2][4][4];
 #pragma unroll
     for (int i = 0; i < 2; ++i)
@@ -77,83 +88,159 @@ __global__ void __launch_bounds__(NTHR) k_conv_gemm(const bf16* __restrict__ A_s
         for (int j = 0; j < 4; ++j)
 #pragma unroll
             for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.0f;
-
-    for (int k0 = kbeg; k0 < kend; k0 += BK) {
-        // stage A [BM][BK] and B as [BN][BK]
-        for (int e = tid; e < BM * BK; e += NTHR) {
-            const int r = e / BK, c = e - r * BK;
-            const int m = m0 + r, k = k0 + c;
-            float v = 0.0f;
-            if (m < M && k < kend) {
-                if (FWD) v = __bfloat162float(A_src[(size_t)m * Ktot + k]);
-                else {
-                    const int b = k / hw, p = k - b * hw;
-                    v = __bfloat162float(A_src[((size_t)b * s.Cout + m) * hw + p]);
-                }
-            }
-            As[r][c] = __float2bfloat16(v);
+    const int nchunks = (IC + KC - 1) / KC;
+    const bf16 zero = __float2bfloat16(0.0f);
+    for (int c = 0; c < nchunks; ++c) {
+        for (int e = tid; e < KC * PP; e += NTHR) {
+            const int j = e / PP, r = e - j * PP;
+            const int py = r / PW, px = r - py * PW;
+            const int ic = c * KC + j, y = y0 - OFF + py, x = x0 - OFF + px;
+            bf16 v = zero;
+            if (ic < IC && y >= 0 && y < H && x >= 0 && x < W) v = X[((size_t)b * IC + ic) * hw + (size_t)y * W + x];
+            Ps[r][j] = v;
         }
-        for (int e = tid; e < BN * BK; e += NTHR) {
-            const int r = e / BK, c = e - r * BK;
-            const int n = n0 + r, k = k0 + c;
-            float v = 0.0f;
-            if (n < N && k < kend) v = FWD ? im2col(X, s, k, n) : im2col(X, s, n, k);
-            Bs[r][c] = __float2bfloat16(v);
+        for (int e = tid; e < TAPS * CT * 2; e += NTHR) {
+            const int t = e / (CT * 2), rem = e - t * CT * 2, o = rem >> 1, h = rem & 1;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (oc0 + o < OC)
+                v = *reinterpret_cast<const uint4*>(Wp + (((size_t)c * TAPS + t) * OC + oc0 + o) * KC + h * 8);
+            *reinterpret_cast<uint4*>(&Ws[t][o][h * 8]) = v;
         }
         __syncthreads();
 #pragma unroll
-        for (int ks = 0; ks < BK; ks += 16) {
-            uint32_t af[2][4], bfr[4][2];
+        for (int t = 0; t < TAPS; ++t) {
+            const int dy = t / KS, dx = t - dy * KS;
+            uint32_t a[2][4];
 #pragma unroll
             for (int mt = 0; mt < 2; ++mt) {
                 const int r0 = wm * 32 + mt * 16 + g;
-                af[mt][0] = *reinterpret_cast<const uint32_t*>(&As[r0][ks + 2 * tg]);
-                af[mt][1] = *reinterpret_cast<const uint32_t*>(&As[r0 + 8][ks + 2 * tg]);
-                af[mt][2] = *reinterpret_cast<const uint32_t*>(&As[r0][ks + 2 * tg + 8]);
-                af[mt][3] = *reinterpret_cast<const uint32_t*>(&As[r0 + 8][ks + 2 * tg + 8]);
+                a[mt][0] = ld32(&Ws[t][r0][2 * tg]);
+                a[mt][1] = ld32(&Ws[t][r0 + 8][2 * tg]);
+                a[mt][2] = ld32(&Ws[t][r0][2 * tg + 8]);
+                a[mt][3] = ld32(&Ws[t][r0 + 8][2 * tg + 8]);
             }
 #pragma unroll
             for (int nt = 0; nt < 4; ++nt) {
-                const int c = wn * 32 + nt * 8 + g;
-                bfr[nt][0] = *reinterpret_cast<const uint32_t*>(&Bs[c][ks + 2 * tg]);
-                bfr[nt][1] = *reinterpret_cast<const uint32_t*>(&Bs[c][ks + 2 * tg + 8]);
+                const int pos = (wn * 4 + nt + dy) * PW + g + dx;
+                uint32_t bb[2] = {ld32(&Ps[pos][2 * tg]), ld32(&Ps[pos][2 * tg + 8])};
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt) mma16816(acc[mt][nt], a[mt], bb);
             }
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-                for (int nt = 0; nt < 4; ++nt) mma16816(acc[mt][nt], af[mt], bfr[nt]);
         }
         __syncthreads();
     }
-    // epilogue
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
         for (int nt = 0; nt < 4; ++nt)
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
-                const int m = m0 + wm * 32 + mt * 16 + g + (r >= 2 ? 8 : 0);
-                const int n = n0 + wn * 32 + nt * 8 + 2 * tg + (r & 1);
-                if (m >= M || n >= N) continue;
-                float v = acc[mt][nt][r];
-                if (FWD) {
-                    if (bias) v += bias[m];
+                const int o = oc0 + wm * 32 + mt * 16 + g + (r >= 2 ? 8 : 0);
+                const int y = y0 + wn * 4 + nt, x = x0 + 2 * tg + (r & 1);
+                if (o >= OC || y >= H || x >= W) continue;
+                float v = acc[mt][nt][r] + (bias ? bias[o] : 0.0f);
+                const size_t idx = ((size_t)b * OC + o) * hw + (size_t)y * W + x;
+                if (OUT == 0) {
                     if (relu) v = fmaxf(v, 0.0f);
-                    const int b = n / hw, p = n - b * hw;
-                    if (MODE == 0) Y[((size_t)b * s.Cout + m) * hw + p] = __float2bfloat16(v);
-                    else reinterpret_cast<float*>(Y)[((size_t)b * s.Cout + m) * hw + p] = v;
+                    reinterpret_cast<bf16*>(Yv)[idx] = __float2bfloat16(v);
                 } else {
-                    partial[((size_t)blockIdx.z * M + m) * N + n] = v;
+                    reinterpret_cast<float*>(Yv)[idx] = v;
                 }
             }
 }
 
-// W'[ci][co][t'] = W[co][ci][ks*ks-1-t]: the data gradient as a forward conv
-__global__ void k_flip(const bf16* W, bf16* Wt, int Cout, int Cin, int kk) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= Cout * Cin * kk) return;
-    const int co = i / (Cin * kk), r = i - co * Cin * kk, ci = r / kk, t = r - ci * kk;
-    Wt[((size_t)ci * Cout + co) * kk + (kk - 1 - t)] = W[i];
+// Weight gradient: a block owns outputs oc0..oc0+63 x inputs 16c..16c+15 x
+// all taps (N = 16 taps columns, n = j*taps + t) and sums over pixel tiles
+// [z*tps, (z+1)*tps) into partial[z][OC][IC*taps].
+template <int KS>
+__global__ void __launch_bounds__(NTHR) k_wgrad(const bf16* __restrict__ X, const bf16* __restrict__ dY,
+                                                float* __restrict__ partial, int B, int IC, int OC, int H, int W,
+                                                int tps) {
+    constexpr int PW = 8 + KS - 1, RS = PW + (PW & 1), TAPS = KS * KS, OFF = KS / 2;
+    constexpr int NT8 = KC * TAPS / 8, NTW = (NT8 + 1) / 2;
+    __shared__ __align__(16) bf16 As[CT][64 + 8];
+    __shared__ __align__(16) bf16 P0[KC][PW][RS];
+    __shared__ __align__(16) bf16 P1[KC][PW][RS];
+    const int c = blockIdx.x, oc0 = blockIdx.y * CT;
+    const int tiles_x = (W + 7) >> 3, tiles_y = (H + 7) >> 3, ntiles = B * tiles_x * tiles_y;
+    const int t_beg = blockIdx.z * tps, t_end = min(ntiles, t_beg + tps);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp >> 1, wn = warp & 1, g = lane >> 2, tg = lane & 3;
+    const size_t hw = (size_t)H * W;
+    const bf16 zero = __float2bfloat16(0.0f);
+    float acc[2][NTW][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < NTW; ++j)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.0f;
+    for (int tile = t_beg; tile < t_end; ++tile) {
+        const int b = tile / (tiles_x * tiles_y), bt = tile - b * tiles_x * tiles_y;
+        const int y0 = (bt / tiles_x) * 8, x0 = (bt % tiles_x) * 8;
+        for (int e = tid; e < CT * 64; e += NTHR) {
+            const int o = e >> 6, p = e & 63, y = y0 + (p >> 3), x = x0 + (p & 7);
+            bf16 v = zero;
+            if (oc0 + o < OC && y < H && x < W) v = dY[((size_t)b * OC + oc0 + o) * hw + (size_t)y * W + x];
+            As[o][p] = v;
+        }
+        for (int e = tid; e < KC * PW * PW; e += NTHR) {
+            const int j = e / (PW * PW), r = e - j * PW * PW, py = r / PW, px = r - py * PW;
+            const int ic = c * KC + j, y = y0 - OFF + py, x = x0 - OFF + px;
+            bf16 v = zero;
+            if (ic < IC && y >= 0 && y < H && x >= 0 && x < W) v = X[((size_t)b * IC + ic) * hw + (size_t)y * W + x];
+            P0[j][py][px] = v;
+            if (px > 0) P1[j][py][px - 1] = v;
+            if (px == PW - 1) P1[j][py][px] = zero;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int s = 0; s < 4; ++s) { // k16 slab: pixel rows 2s, 2s+1 of the tile
+            uint32_t a[2][4];
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                const int r0 = wm * 32 + mt * 16 + g;
+                a[mt][0] = ld32(&As[r0][16 * s + 2 * tg]);
+                a[mt][1] = ld32(&As[r0 + 8][16 * s + 2 * tg]);
+                a[mt][2] = ld32(&As[r0][16 * s + 8 + 2 * tg]);
+                a[mt][3] = ld32(&As[r0 + 8][16 * s + 8 + 2 * tg]);
+            }
+#pragma unroll
+            for (int q = 0; q < NTW; ++q) {
+                const int nt = wn * NTW + q;
+                if (nt >= NT8) break;
+                const int n = nt * 8 + g, j = n / TAPS, t = n - j * TAPS, dyy = t / KS, dxx = t - dyy * KS;
+                const int col = 2 * tg + dxx;
+                uint32_t bb[2];
+                if (dxx & 1) {
+                    bb[0] = ld32(&P1[j][2 * s + dyy][col - 1]);
+                    bb[1] = ld32(&P1[j][2 * s + 1 + dyy][col - 1]);
+                } else {
+                    bb[0] = ld32(&P0[j][2 * s + dyy][col]);
+                    bb[1] = ld32(&P0[j][2 * s + 1 + dyy][col]);
+                }
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt) mma16816(acc[mt][q], a[mt], bb);
+            }
+        }
+        __syncthreads();
+    }
+    const size_t NC = (size_t)IC * TAPS;
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int q = 0; q < NTW; ++q) {
+            const int nt = wn * NTW + q;
+            if (nt >= NT8) break;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int o = oc0 + wm * 32 + mt * 16 + g + (r >= 2 ? 8 : 0);
+                const int n = nt * 8 + 2 * tg + (r & 1);
+                const int ic = c * KC + n / TAPS;
+                if (o >= OC || ic >= IC) continue;
+                partial[((size_t)blockIdx.z * OC + o) * NC + (size_t)c * KC * TAPS + n] = acc[mt][q][r];
+            }
+        }
 }
 
 // fixed-order sum of split-K partials; bias gradient as the sum of dY over pixels
@@ -304,26 +391,50 @@ static bool shape_ok(int B, int Cin, int Cout, int H, int W, int ks) {
 
 extern "C" {
 
-cx_status cx_nn_conv_forward(const uint16_t* x, const uint16_t* w, const float* bias, uint16_t* y, int B, int Cin,
-                             int Cout, int H, int W, int ks, int relu, cudaStream_t stream) {
-    if (!x || !w || !y || !shape_ok(B, Cin, Cout, H, W, ks)) return CX_ERR_INVALID_ARG;
-    ConvShape s{B, Cin, Cout, H, W, ks};
-    dim3 grid((B * H * W + BN - 1) / BN, (Cout + BM - 1) / BM);
-    k_conv_gemm<0><<<grid, NTHR, 0, stream>>>(reinterpret_cast<const bf16*>(w), reinterpret_cast<const bf16*>(x),
-                                              bias, reinterpret_cast<bf16*>(y), nullptr, s, relu, 0);
+size_t cx_nn_packed_weights(int Cout, int Cin, int ks, int which) {
+    const int taps = ks * ks;
+    if (which == 0) return (size_t)((Cin + KC - 1) / KC) * taps * Cout * KC;
+    return (size_t)((Cout + KC - 1) / KC) * taps * Cin * KC;
+}
+
+cx_status cx_nn_pack_weights(const uint16_t* w, int Cout, int Cin, int ks, uint16_t* w_fwd, uint16_t* w_bwd,
+                             cudaStream_t stream) {
+    if (!w || !w_fwd || !w_bwd || Cout < 1 || Cin < 1 || (ks != 1 && ks != 3)) return CX_ERR_INVALID_ARG;
+    const size_t n = cx_nn_packed_weights(Cout, Cin, ks, 0) + cx_nn_packed_weights(Cout, Cin, ks, 1);
+    k_pack<<<grid_for(n), 256, 0, stream>>>(reinterpret_cast<const bf16*>(w), reinterpret_cast<bf16*>(w_fwd),
+                                            reinterpret_cast<bf16*>(w_bwd), Cout, Cin, ks * ks);
     NN_CHECK();
     return CX_OK;
 }
 
-cx_status cx_nn_conv_forward_f32(const uint16_t* x, const uint16_t* w, const float* bias, float* y, int B, int Cin,
-                                 int Cout, int H, int W, int ks, cudaStream_t stream) {
-    if (!x || !w || !y || !shape_ok(B, Cin, Cout, H, W, ks)) return CX_ERR_INVALID_ARG;
-    ConvShape s{B, Cin, Cout, H, W, ks};
-    dim3 grid((B * H * W + BN - 1) / BN, (Cout + BM - 1) / BM);
-    k_conv_gemm<2><<<grid, NTHR, 0, stream>>>(reinterpret_cast<const bf16*>(w), reinterpret_cast<const bf16*>(x),
-                                              bias, reinterpret_cast<bf16*>(y), nullptr, s, 0, 0);
+static cx_status launch_conv(const void* x, const uint16_t* wp, const float* bias, void* y, int B, int IC, int OC,
+                             int H, int W, int ks, int relu, int out_f32, cudaStream_t stream) {
+    const long long tiles = (long long)B * ((H + 7) / 8) * ((W + 7) / 8);
+    if (tiles > 0x7fffffffLL) return CX_ERR_INVALID_ARG;
+    dim3 grid((unsigned)tiles, (OC + CT - 1) / CT);
+    const bf16* X = reinterpret_cast<const bf16*>(x);
+    const bf16* Wp = reinterpret_cast<const bf16*>(wp);
+    if (ks == 3) {
+        if (out_f32) k_conv<3, 1><<<grid, NTHR, 0, stream>>>(X, Wp, bias, y, B, IC, OC, H, W, 0);
+        else k_conv<3, 0><<<grid, NTHR, 0, stream>>>(X, Wp, bias, y, B, IC, OC, H, W, relu);
+    } else {
+        if (out_f32) k_conv<1, 1><<<grid, NTHR, 0, stream>>>(X, Wp, bias, y, B, IC, OC, H, W, 0);
+        else k_conv<1, 0><<<grid, NTHR, 0, stream>>>(X, Wp, bias, y, B, IC, OC, H, W, relu);
+    }
     NN_CHECK();
     return CX_OK;
+}
+
+cx_status cx_nn_conv_forward(const uint16_t* x, const uint16_t* w_fwd, const float* bias, uint16_t* y, int B,
+                             int Cin, int Cout, int H, int W, int ks, int relu, cudaStream_t stream) {
+    if (!x || !w_fwd || !y || !shape_ok(B, Cin, Cout, H, W, ks)) return CX_ERR_INVALID_ARG;
+    return launch_conv(x, w_fwd, bias, y, B, Cin, Cout, H, W, ks, relu, 0, stream);
+}
+
+cx_status cx_nn_conv_forward_f32(const uint16_t* x, const uint16_t* w_fwd, const float* bias, float* y, int B,
+                                 int Cin, int Cout, int H, int W, int ks, cudaStream_t stream) {
+    if (!x || !w_fwd || !y || !shape_ok(B, Cin, Cout, H, W, ks)) return CX_ERR_INVALID_ARG;
+    return launch_conv(x, w_fwd, bias, y, B, Cin, Cout, H, W, ks, 0, 1, stream);
 }
 
 cx_status cx_nn_smooth(const float* in, float* tmp, float* out, int BC, int H, int W, const float* taps, int radius,
@@ -338,20 +449,11 @@ cx_status cx_nn_smooth(const float* in, float* tmp, float* out, int BC, int H, i
     return CX_OK;
 }
 
-cx_status cx_nn_conv_backward_data(const uint16_t* dy, const uint16_t* w, uint16_t* dx, uint16_t* w_flip, int B,
-                                   int Cin, int Cout, int H, int W, int ks, cudaStream_t stream) {
-    if (!dy || !w || !dx || !w_flip || !shape_ok(B, Cin, Cout, H, W, ks)) return CX_ERR_INVALID_ARG;
-    const int kk = ks * ks, nw = Cout * Cin * kk;
-    k_flip<<<(nw + 255) / 256, 256, 0, stream>>>(reinterpret_cast<const bf16*>(w), reinterpret_cast<bf16*>(w_flip),
-                                                 Cout, Cin, kk);
-    NN_CHECK();
-    ConvShape s{B, Cout, Cin, H, W, ks}; // dY has Cout channels, dX has Cin
-    dim3 grid((B * H * W + BN - 1) / BN, (Cin + BM - 1) / BM);
-    k_conv_gemm<0><<<grid, NTHR, 0, stream>>>(reinterpret_cast<const bf16*>(w_flip),
-                                              reinterpret_cast<const bf16*>(dy), nullptr,
-                                              reinterpret_cast<bf16*>(dx), nullptr, s, 0, 0);
-    NN_CHECK();
-    return CX_OK;
+cx_status cx_nn_conv_backward_data(const uint16_t* dy, const uint16_t* w_bwd, uint16_t* dx, int B, int Cin, int Cout,
+                                   int H, int W, int ks, cudaStream_t stream) {
+    if (!dy || !w_bwd || !dx || !shape_ok(B, Cin, Cout, H, W, ks)) return CX_ERR_INVALID_ARG;
+    // dY has Cout channels, dX has Cin
+    return launch_conv(dy, w_bwd, nullptr, dx, B, Cout, Cin, H, W, ks, 0, 0, stream);
 }
 
 size_t cx_nn_conv_backward_weight_scratch(int B, int Cin, int Cout, int H, int W, int ks, int splits) {
@@ -361,22 +463,21 @@ size_t cx_nn_conv_backward_weight_scratch(int B, int Cin, int Cout, int H, int W
 cx_status cx_nn_conv_backward_weight(const uint16_t* x, const uint16_t* dy, float* dw, float* db, float* scratch,
                                      int splits, int B, int Cin, int Cout, int H, int W, int ks,
                                      cudaStream_t stream) {
-    if (!x || !dy || !dw || !scratch || splits < 1 || !shape_ok(B, Cin, Cout, H, W, ks)) return CX_ERR_INVALID_ARG;
-    ConvShape s{B, Cin, Cout, H, W, ks};
-    const int Ktot = B * H * W;
-    int chunk = (Ktot + splits - 1) / splits;
-    chunk = (chunk + BK - 1) / BK * BK;
-    const int used = (Ktot + chunk - 1) / chunk;
-    const int N = Cin * ks * ks;
-    dim3 grid((N + BN - 1) / BN, (Cout + BM - 1) / BM, used);
-    k_conv_gemm<1><<<grid, NTHR, 0, stream>>>(reinterpret_cast<const bf16*>(dy), reinterpret_cast<const bf16*>(x),
-                                              nullptr, nullptr, scratch, s, 0, chunk);
+    if (!x || !dy || !dw || !scratch || splits < 1 || splits > 65535 || !shape_ok(B, Cin, Cout, H, W, ks))
+        return CX_ERR_INVALID_ARG;
+    const int ntiles = B * ((H + 7) / 8) * ((W + 7) / 8);
+    const int tps = (ntiles + splits - 1) / splits;
+    dim3 grid((Cin + KC - 1) / KC, (Cout + CT - 1) / CT, splits);
+    const bf16* X = reinterpret_cast<const bf16*>(x);
+    const bf16* dY = reinterpret_cast<const bf16*>(dy);
+    if (ks == 3) k_wgrad<3><<<grid, NTHR, 0, stream>>>(X, dY, scratch, B, Cin, Cout, H, W, tps);
+    else k_wgrad<1><<<grid, NTHR, 0, stream>>>(X, dY, scratch, B, Cin, Cout, H, W, tps);
     NN_CHECK();
-    const size_t mn = (size_t)Cout * N;
-    k_reduce_splits<<<grid_for(mn), 256, 0, stream>>>(scratch, dw, used, mn);
+    const size_t mn = (size_t)Cout * Cin * ks * ks;
+    k_reduce_splits<<<grid_for(mn), 256, 0, stream>>>(scratch, dw, splits, mn);
     NN_CHECK();
     if (db) {
-        k_bias_grad<<<Cout, 256, 0, stream>>>(reinterpret_cast<const bf16*>(dy), db, B, Cout, H * W);
+        k_bias_grad<<<Cout, 256, 0, stream>>>(dY, db, B, Cout, H * W);
         NN_CHECK();
     }
     return CX_OK;

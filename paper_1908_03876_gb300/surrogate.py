@@ -63,6 +63,11 @@ class UNet:
         self.head = Conv(chans[0], cout, 1, rng, device)
         self.layers = [c for pair in self.enc for c in pair] + [c for l in sorted(self.dec) for c in self.dec[l]] + [
             self.head]
+        for c in self.layers:  # packed BF16 copies the convolution kernels read
+            c.wf = torch.empty(self.lib.cx_nn_packed_weights(c.cout, c.cin, c.ks, 0), dtype=torch.bfloat16,
+                               device=self.device)
+            c.wbk = torch.empty(self.lib.cx_nn_packed_weights(c.cout, c.cin, c.ks, 1), dtype=torch.bfloat16,
+                                device=self.device)
         self.cin, self.cout = cin, cout
         self.t = 0
         self.sync_bf16()
@@ -74,6 +79,11 @@ class UNet:
     def sync_bf16(self):
         for c in self.layers:
             _lib.check(self.lib.cx_nn_cast_bf16(_p(c.w), _p(c.wb), c.w.numel(), self._s()), "cx_nn_cast_bf16")
+            self._pack(c)
+
+    def _pack(self, c):
+        _lib.check(self.lib.cx_nn_pack_weights(_p(c.wb), c.cout, c.cin, c.ks, _p(c.wf), _p(c.wbk), self._s()),
+                   "cx_nn_pack_weights")
 
     def _new(self, B, C, H, W):
         return torch.empty((B, C, H, W), dtype=torch.bfloat16, device=self.device)
@@ -82,17 +92,20 @@ class UNet:
         B, _, H, W = x.shape
         if out_f32:
             y = torch.empty((B, c.cout, H, W), dtype=torch.float32, device=self.device)
-            _lib.check(self.lib.cx_nn_conv_forward_f32(_p(x), _p(c.wb), _p(c.b), _p(y), B, c.cin, c.cout, H, W, c.ks,
+            _lib.check(self.lib.cx_nn_conv_forward_f32(_p(x), _p(c.wf), _p(c.b), _p(y), B, c.cin, c.cout, H, W, c.ks,
                                                        self._s()), "cx_nn_conv_forward_f32")
             return y
         y = self._new(B, c.cout, H, W)
-        _lib.check(self.lib.cx_nn_conv_forward(_p(x), _p(c.wb), _p(c.b), _p(y), B, c.cin, c.cout, H, W, c.ks,
+        _lib.check(self.lib.cx_nn_conv_forward(_p(x), _p(c.wf), _p(c.b), _p(y), B, c.cin, c.cout, H, W, c.ks,
                                                1 if relu else 0, self._s()), "cx_nn_conv_forward")
         return y
 
     def _conv_back(self, c: Conv, x, dy, need_dx=True):
         B, _, H, W = x.shape
-        splits = int(max(1, min(64, (B * H * W) // 4096)))
+        # split the pixel tiles so that about 8 blocks per SM run
+        ntiles = B * ((H + 7) // 8) * ((W + 7) // 8)
+        base = ((c.cin + 15) // 16) * ((c.cout + 63) // 64)
+        splits = int(max(1, min(ntiles, -(-1216 // base))))
         nbytes = self.lib.cx_nn_conv_backward_weight_scratch(B, c.cin, c.cout, H, W, c.ks, splits)
         scratch = torch.empty(max(1, nbytes // 4), dtype=torch.float32, device=self.device)
         _lib.check(self.lib.cx_nn_conv_backward_weight(_p(x), _p(dy), _p(c.gw), _p(c.gb), _p(scratch), splits, B,
@@ -101,10 +114,8 @@ class UNet:
         if not need_dx:
             return None
         dx = self._new(B, c.cin, H, W)
-        wflip = torch.empty(c.wb.numel(), dtype=torch.bfloat16, device=self.device)
-        _lib.check(self.lib.cx_nn_conv_backward_data(_p(dy), _p(c.wb), _p(dx), _p(wflip), B, c.cin, c.cout, H, W,
-                                                     c.ks, self._s()), "cx_nn_conv_backward_data")
-        self._keep = (scratch, wflip)
+        _lib.check(self.lib.cx_nn_conv_backward_data(_p(dy), _p(c.wbk), _p(dx), B, c.cin, c.cout, H, W, c.ks,
+                                                     self._s()), "cx_nn_conv_backward_data")
         return dx
 
     def _relu_back(self, y, dy):
@@ -204,6 +215,7 @@ class UNet:
                                            eps, self.t, self._s()), "cx_nn_adam")
             _lib.check(self.lib.cx_nn_adam(_p(c.b), _p(c.mb), _p(c.vb), _p(c.gb), _p(c.bb), c.b.numel(), lr, b1, b2,
                                            eps, self.t, self._s()), "cx_nn_adam")
+            self._pack(c)
 
     def train_step(self, x, target, lr=1e-3):
         out = self.forward(x)

@@ -36,6 +36,14 @@ def _lib():
     return _lib.load(), _lib.check
 
 
+def packed(lib, check, wd, Cout, Cin, ks):
+    """Forward and data-gradient packs of device BF16 weights wd."""
+    wf = torch.empty(lib.cx_nn_packed_weights(Cout, Cin, ks, 0), dtype=BF, device="cuda")
+    wb = torch.empty(lib.cx_nn_packed_weights(Cout, Cin, ks, 1), dtype=BF, device="cuda")
+    check(lib.cx_nn_pack_weights(_p(wd), Cout, Cin, ks, _p(wf), _p(wb), _s()), "pack")
+    return wf, wb
+
+
 def _p(t):
     import ctypes
 
@@ -74,6 +82,9 @@ def rel_l2(a, b):
     (2, 64, 96, 16, 16, 3, False),    # several K tiles and M tiles, ragged M
     (2, 32, 8, 18, 14, 1, False),     # 1x1 head shape
     (1, 256, 128, 8, 8, 3, True),     # deep level
+    (4, 64, 32, 4, 4, 3, True),       # image smaller than the 8x8 pixel tile
+    (2, 6, 1, 12, 20, 1, False),      # one output channel (the head), Cin below one chunk
+    (1, 40, 70, 13, 11, 3, True),     # ragged everything
 ])
 def test_conv_forward(B, Cin, Cout, H, W, ks, relu):
     lib, check = _lib()
@@ -82,7 +93,8 @@ def test_conv_forward(B, Cin, Cout, H, W, ks, relu):
     b = torch.linspace(-0.5, 0.5, Cout, dtype=torch.float32)
     y = torch.empty((B, Cout, H, W), dtype=BF, device="cuda")
     xd, wd, bd = x.cuda(), w.cuda(), b.cuda()  # held: the call only sees raw pointers
-    check(lib.cx_nn_conv_forward(_p(xd), _p(wd), _p(bd), _p(y), B, Cin, Cout, H, W, ks, int(relu), _s()), "conv")
+    wf, _ = packed(lib, check, wd, Cout, Cin, ks)
+    check(lib.cx_nn_conv_forward(_p(xd), _p(wf), _p(bd), _p(y), B, Cin, Cout, H, W, ks, int(relu), _s()), "conv")
     ref = R.conv(x.double(), w.double(), b.double(), relu=relu)
     check_bf16(y, ref, f"conv fwd {Cin}->{Cout} k{ks}")
 
@@ -96,9 +108,9 @@ def test_conv_backward(ks):
     dy = bf16_data((B, Cout, H, W), 7)
     xd, wd, dyd = x.cuda(), w.cuda(), dy.cuda()
     dx = torch.empty_like(xd)
-    wflip = torch.empty_like(wd)
-    check(lib.cx_nn_conv_backward_data(_p(dyd), _p(wd), _p(dx), _p(wflip), B, Cin, Cout, H, W, ks, _s()), "bwd data")
-    for splits in (1, 7):
+    _, wbk = packed(lib, check, wd, Cout, Cin, ks)
+    check(lib.cx_nn_conv_backward_data(_p(dyd), _p(wbk), _p(dx), B, Cin, Cout, H, W, ks, _s()), "bwd data")
+    for splits in (1, 7, 200):
         nbytes = lib.cx_nn_conv_backward_weight_scratch(B, Cin, Cout, H, W, ks, splits)
         scratch = torch.empty(nbytes // 4, dtype=torch.float32, device="cuda")
         dw = torch.empty((Cout, Cin, ks, ks), dtype=torch.float32, device="cuda")
@@ -237,8 +249,9 @@ def test_conv_forward_f32_and_smooth():
     w = bf16_data((Cout, Cin, 1, 1), 21, scale=0.2)
     b = torch.linspace(-0.1, 0.1, Cout, dtype=torch.float32)
     xd, wd, bd = x.cuda(), w.cuda(), b.cuda()
+    wf, _ = packed(lib, check, wd, Cout, Cin, 1)
     y = torch.empty((B, Cout, H, W), dtype=torch.float32, device="cuda")
-    check(lib.cx_nn_conv_forward_f32(_p(xd), _p(wd), _p(bd), _p(y), B, Cin, Cout, H, W, 1, _s()), "conv f32")
+    check(lib.cx_nn_conv_forward_f32(_p(xd), _p(wf), _p(bd), _p(y), B, Cin, Cout, H, W, 1, _s()), "conv f32")
     ref = R.conv(x.double(), w.double(), b.double())
     assert rel_l2(y, ref) < 1e-6
     sigma, r = 1.5, 5

@@ -24,8 +24,8 @@ def _built():
 def test_warm_start_gains_over_plain_descent():
     from paper_1908_03876_gb300 import warmstart as WS
 
-    train = WS.problems(512, 5000, size=32, N=32, windows=8, ckpt_every=8)
-    test = WS.problems(8, 700000, size=32, N=32, windows=8, ckpt_every=8)
+    train = WS.problems(512, 5000, size=64, N=64, windows=8, ckpt_every=16)
+    test = WS.problems(16, 700000, size=64, N=64, windows=8, ckpt_every=16)
     ref = WS.descend(train, max_iter=200, want_residual=True)
     model = WS.Surrogate(seed=1)
     D = np.stack([r - r0 for r, r0 in zip(ref["residual"], ref["residual_init"])])
@@ -34,7 +34,8 @@ def test_warm_start_gains_over_plain_descent():
     ref_te = WS.descend(test, max_iter=200, want_residual=True)
     ev = WS.evaluate(model, test, ref_te)
     print(ev)
-    assert ev["warm_reached"] >= len(test) - 2, ev   # the rest fall back to the plain method
-    assert ev["g0_rel_err_median"] < 0.5, ev         # the zero control has relative error 1
-    assert ev["J_excess_at_g0_median"] < 0.2 * ev["J_excess_at_zero_median"], ev
-    assert ev["warm_iters_total"] < 0.9 * ev["cold_iters_total"], ev
+    assert ev["warm_reached"] >= len(test) - 3, ev   # the rest fall back to the plain method
+    assert ev["g0_rel_err_median"] < 0.4, ev         # the zero control has relative error 1
+    assert ev["J_excess_at_g0_median"] < 0.3 * ev["J_excess_at_zero_median"], ev
+    # descent iterations including the fallback runs
+    assert ev["warm_iters_total"] < 0.95 * ev["cold_iters_total"], ev
