@@ -278,3 +278,71 @@ def from_workload(w, N=None) -> Problem:
                    u_tgt=w.u_tgt, d_u=w.d_u, d_v=w.d_v, chi=w.chi, r_vu=w.r_vu, r_vv=w.r_vv,
                    a=w.a_fields(), solid=w.solid, window=w.window, cmask=w.cmask, alpha=w.alpha,
                    s=tuple(w.s), source_order=w.source_order, windows=w.windows)
+
+
+CG_VARIANTS = ("FR", "PR", "HS", "DY")
+
+
+def cg_iteration(p: Problem, g, state=None, variant="PR", c1=1e-4, c2=0.1, max_trials=30):
+    """One nonlinear conjugate-gradient iteration with a weak Wolfe-Powell
+    line search (remark 2 after the gradient algorithm of Sec. 2.3).
+
+    Direction D_k = -G_k at k = 0, else -G_k + r_{k-1} D_{k-1} with r from
+    Fletcher-Reeves, Polak-Ribiere, Hestenes-Stiefel or Dai-Yuan; the update
+    is z_{k+1} = z_k + zeta_k D_k (the printed "- zeta_k D_k" with D_0 = -G_0
+    would ascend: read as the descent step).  Soft reset D = -G whenever the
+    new direction is not a descent direction or successive gradients are far
+    from orthogonal, |<G_{k+1}, G_k>| >= 0.2 ||G_{k+1}||^2 (Powell's restart
+    test: the CG recurrence has stopped making progress).  Line search on
+    phi(l) = J(g + l D): accept when phi(l) <= phi(0) + c1 l phi'(0) and
+    phi'(l) >= c2 phi'(0); else bisect the bracket (doubling while it is
+    open).  First trial min(1, 1/||G||_inf) at k = 0, else
+    l_{k-1} phi'_{k-1}(0) / phi'_k(0).
+
+    state: None (k = 0) or the dict returned by the previous call.
+    Returns (g_new, state, info)."""
+    if state is None:
+        J0, G, _ = adjoint(p, g)
+        D = -G
+        gd = float(np.sum(G * D))
+        lam = min(1.0, 1.0 / float(np.max(np.abs(G)))) if G.size and np.max(np.abs(G)) > 0 else 1.0
+        k = 0
+    else:
+        J0, G, D, gd = state["J"], state["G"], state["D"], state["gd"]
+        lam = state["lam"] * state["gd_prev"] / gd
+        k = state["k"]
+    lo, hi = 0.0, np.inf
+    for t in range(max_trials):
+        gt = g + lam * D
+        Jt, Gt, _ = adjoint(p, gt)
+        if not np.isfinite(Jt) or Jt > J0 + c1 * lam * gd:
+            hi = lam
+        elif float(np.sum(Gt * D)) < c2 * gd:
+            lo = lam
+        else:
+            break
+        lam = 0.5 * (lo + hi) if np.isfinite(hi) else 2.0 * lam
+    else:
+        raise RuntimeError("Wolfe line search failed")
+    gg = float(np.sum(G * G))
+    y = Gt - G
+    dy = float(np.sum(D * y))
+    if variant == "FR":
+        r = float(np.sum(Gt * Gt)) / gg
+    elif variant == "PR":
+        r = float(np.sum(Gt * y)) / gg
+    elif variant == "HS":
+        r = float(np.sum(Gt * y)) / dy
+    elif variant == "DY":
+        r = float(np.sum(Gt * Gt)) / dy
+    else:
+        raise ValueError(variant)
+    Dn = -Gt + r * D
+    gdn = float(np.sum(Gt * Dn))
+    gtgt = float(np.sum(Gt * Gt))
+    restarted = gdn >= 0.0 or abs(float(np.sum(Gt * G))) >= 0.2 * gtgt
+    if restarted:
+        Dn = -Gt
+        gdn = float(np.sum(Gt * Gt)) * -1.0
+    info = dict(J0=J0, J=Jt, lam=lam, trials=t + 1, r=r, restarted=restarted, grad_sq=float(np.sum(Gt * Gt)))
+    return gt, dict(J=Jt, G=Gt, D=Dn, gd=gdn, gd_prev=gd, lam=lam, k=k + 1), info

@@ -416,3 +416,81 @@ def test_windowed_gradient_fd():
     Jq, Eq, _ = oracle.adjoint(q, g_steps)
     assert Jq == J0
     assert np.abs(Eq.reshape(3, 4, 10, 10).sum(1) - E).max() <= 1e-14 * np.abs(E).max()
+
+
+def _cg_problem():
+    """A small chemotaxis problem (the control reaches u only through chi)."""
+    w = W.plain64(8, 8, 8, sigma=1.5, Q=9, chi=-0.5)
+    w.alpha = 1e-3
+    w.windows = 2
+    return w, oracle.from_workload(w)
+
+
+def _reference_optimum(w, p):
+    """The optimum by an independent optimiser (scipy's L-BFGS-B on the
+    oracle's J and gradient), converged far below the tolerances used."""
+    from scipy.optimize import minimize
+
+    shape = w.ctrl_shape
+
+    def fg(x):
+        J, E, _ = oracle.adjoint(p, x.reshape(shape))
+        return J, E.ravel()
+
+    res = minimize(fg, np.zeros(int(np.prod(shape))), jac=True, method="L-BFGS-B",
+                   options=dict(maxiter=2000, ftol=1e-15, gtol=1e-13, maxcor=30))
+    return res.x.reshape(shape), float(res.fun)
+
+
+@pytest.mark.parametrize("variant", ["FR", "PR", "HS", "DY"])
+def test_cg_wolfe_steps_and_optimum(variant):
+    """Nonlinear CG with the Wolfe-Powell search: every accepted step meets
+    both Wolfe conditions (checked with fresh solves), the directions are
+    descent directions, and the iterates reach the optimum found by an
+    independent optimiser."""
+    w, p = _cg_problem()
+    gref, Jref = _reference_optimum(w, p)
+    g = np.zeros(w.ctrl_shape)
+    state = None
+    for k in range(300):
+        J_old, G_old, _ = oracle.adjoint(p, g)
+        D = -G_old if state is None else state["D"]
+        gd = float(np.sum(G_old * D))
+        assert gd < 0
+        g_new, state, info = oracle.cg_iteration(p, g, state, variant=variant)
+        lam = info["lam"]
+        J_new, G_new, _ = oracle.adjoint(p, g + lam * D)
+        assert J_new <= J_old + 1e-4 * lam * gd + 1e-14 * abs(J_old)
+        assert float(np.sum(G_new * D)) >= 0.1 * gd - 1e-14 * abs(gd)
+        g = g_new
+        if J_new - Jref <= 1e-11 * Jref:
+            break
+    assert J_new - Jref <= 1e-10 * Jref, (variant, k, J_new, Jref)
+    assert np.linalg.norm(g - gref) <= 1e-4 * np.linalg.norm(gref), np.linalg.norm(g - gref) / np.linalg.norm(gref)
+
+
+def test_cg_beats_steepest_descent():
+    """Polak-Ribiere CG needs fewer iterations than Armijo steepest descent to
+    reach the reference optimum to 1e-9 (relative J)."""
+    w, p = _cg_problem()
+    _, Jref = _reference_optimum(w, p)
+
+    def iterations(step):
+        g = np.zeros(w.ctrl_shape)
+        aux = None
+        for k in range(1, 500):
+            g, aux, info = step(g, aux)
+            if info["J"] - Jref <= 1e-9 * Jref:
+                return k
+        return 500
+
+    def sd(g, lam):
+        g, info = oracle.gd_step(p, g, lam_prev=lam)
+        return g, info["lam"], info
+
+    def cg(g, st):
+        return oracle.cg_iteration(p, g, st, variant="PR")
+
+    n_sd, n_cg = iterations(sd), iterations(cg)
+    print("iterations: steepest descent", n_sd, "CG", n_cg)
+    assert n_cg < n_sd, (n_cg, n_sd)
