@@ -354,6 +354,62 @@ def run_warmstart(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+def run_cg(args, rank, world, local):
+    """Nonlinear CG (Polak-Ribiere, Wolfe-Powell search) against Armijo
+    steepest descent on one problem: wall time and iterations until
+    J <= J* (1 + 1e-6), J* = the lowest cost either method reaches in its
+    iteration budget (a converged CG run)."""
+    import numpy as np
+    import torch
+
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    from paper_1908_03876_gb300.build import build
+
+    build()
+    from paper_1908_03876_gb300 import workloads as W
+    from paper_1908_03876_gb300.problem import Problem
+
+    w = W.aniso(256, 256, 200, seed=1, precision=32, ckpt_every=50)
+    w.windows = 8
+
+    def run(method, n_iter, target=None):
+        p = Problem(w)
+        g = p.zeros_control()
+        Js, t_hit, it_hit = [], None, None
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(n_iter):
+            info = p.cg_step(g, "PR") if method == "cg" else p.step(g)
+            Js.append(info["J"])
+            if target is not None and info["J"] <= target:
+                t_hit, it_hit = time.perf_counter() - t0, k + 1
+                break
+        torch.cuda.synchronize()
+        p.close()
+        return Js, t_hit, it_hit
+
+    Jcg, _, _ = run("cg", 150)
+    Jsd, _, _ = run("sd", 600)
+    Jstar = min(min(Jcg), min(Jsd))
+    target = Jstar * (1 + 1e-6)
+    _, t_cg, it_cg = run("cg", 150, target)
+    _, t_sd, it_sd = run("sd", 600, target)
+    line = {
+        "metric": "wall time to J* (1e-6 rel): nonlinear CG (Polak-Ribiere, Wolfe-Powell) vs Armijo steepest descent",
+        "value": t_cg, "unit": "s", "n_gpus": 1, "steps": 1, "warmup": 0,
+        "ms_per_step": None if t_cg is None else t_cg * 1e3, "higher_is_better": False, "scaling": "replicas only",
+        "vs_baseline": None, "dtype": "f32 (FP64 reductions)", "data": "synthetic (seeded)",
+        "config": {"workload": "aniso 256x256 D2Q9 FP32, 200 steps, k = 50, control constant over 8 windows",
+                   "J_star": Jstar, "iteration budgets": {"cg": 150, "steepest_descent": 600}},
+        "steepest_descent_seconds": t_sd, "cg_iterations": it_cg, "steepest_descent_iterations": it_sd,
+        "speedup_vs_steepest_descent": None if (t_cg is None or t_sd is None) else t_sd / t_cg,
+        "J_final": {"cg": Jcg[-1], "steepest_descent": Jsd[-1]},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -361,7 +417,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="aniso1024", choices=["aniso1024", "batch", "warmstart"],
+    ap.add_argument("--workload", default="aniso1024", choices=["aniso1024", "batch", "warmstart", "cg"],
                     help="aniso1024 (default bench line) or batch: 256 independent problems, sizes {64..512}^2, "
                          "1000 steps, one persistent launch per step replayed as a CUDA graph")
     ap.add_argument("--problems", type=int, default=256)
@@ -389,6 +445,9 @@ def main():
         return
     if args.workload == "warmstart":
         run_warmstart(args, rank, world, local)
+        return
+    if args.workload == "cg":
+        run_cg(args, rank, world, local)
         return
 
     import numpy as np

@@ -164,6 +164,35 @@ cx_status cx_gradient(cx_problem* p, const void* g, void* dJdg, double* J_dev);
  * NULL.  Errors: CX_ERR_LINESEARCH (g_inout unchanged), CX_ERR_UNSTABLE. */
 cx_status cx_step(cx_problem* p, void* g_inout, void* E_work, cx_step_info* info);
 
+/* Nonlinear conjugate gradients (remark 2 after the gradient algorithm,
+ * Sec. 2.3): direction D_k = -G_k (k = 0), else -G_k + r_{k-1} D_{k-1} with r
+ * from Fletcher-Reeves, Polak-Ribiere, Hestenes-Stiefel or Dai-Yuan, reset to
+ * -G_k when D_k is not a descent direction or |<G_k, G_{k-1}>| >= 0.2
+ * ||G_k||^2; step g <- g + lam D_k with lam from a weak Wolfe-Powell line
+ * search (J(g + lam D) <= J(g) + 1e-4 lam <G, D>, <G(g + lam D), D> >=
+ * 0.1 <G, D>; bisection of the bracket, doubling while it is open, at most
+ * 30 trials; first trial min(1, 1/||G||_inf), then lam_{k-1} <G,D>_{k-1} /
+ * <G,D>_k).  Each trial costs a forward solve, and an AMRT sweep when the
+ * decrease condition holds; the accepted trial's gradient is the next
+ * iteration's.  work: device T [4][W][ctrl_ny][ctrl_nx], caller-owned and
+ * kept between calls (gradients, direction, trial control).  The iteration
+ * state refers to g_inout as the previous call left it: call cx_cg_reset
+ * after changing g or the initial state (cx_set_initial resets it).
+ * Synchronous.  Errors: CX_ERR_LINESEARCH (no step met the conditions; the
+ * state is reset), CX_ERR_UNSTABLE, CX_ERR_STATE, CX_ERR_INVALID_ARG. */
+enum { CX_CG_FR = 0, CX_CG_PR = 1, CX_CG_HS = 2, CX_CG_DY = 3 };
+typedef struct {
+    double J0;      /* cost at the incoming control       */
+    double J;       /* cost at the accepted control       */
+    double lam;     /* accepted step length along D       */
+    double grad_sq; /* ||G||^2 at the accepted control     */
+    double beta;    /* r_k of the chosen formula           */
+    int trials;     /* line-search trials (forward solves) */
+    int restarted;  /* 1 if the new direction is -G       */
+} cx_cg_info;
+cx_status cx_cg_step(cx_problem* p, void* g_inout, void* work, int variant, cx_cg_info* info);
+cx_status cx_cg_reset(cx_problem* p);
+
 /* u^N and v^N of the last forward (device T [ny][nx] each, either may be NULL). */
 cx_status cx_get_fields(cx_problem* p, void* u_out, void* v_out);
 
@@ -237,6 +266,10 @@ cx_status cx_batch_adjoint(cx_batch* b, const void* const* seed_u, int add_to_co
  * [count], 0 leaves a problem alone), rounded as a line-search trial;
  * forgets the step-length history.  Asynchronous. */
 cx_status cx_batch_axpy(cx_batch* b, const double* lam);
+/* Capture every launch sequence (forward, gradient, line-search trial,
+ * adjoint) as CUDA graphs now rather than on first use, without running
+ * them.  Needs the bindings; synchronous. */
+cx_status cx_batch_prepare(cx_batch* b);
 cx_status cx_batch_get_fields(cx_batch* b, int i, void* u_out, void* v_out);
 /* Synchronising: CX_ERR_UNSTABLE if any problem's J or gradient was non-finite. */
 cx_status cx_batch_get_status(cx_batch* b);

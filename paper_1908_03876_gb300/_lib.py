@@ -22,10 +22,10 @@ STATUS = {
 EXPORTS = [
     "cx_workspace_size", "cx_create", "cx_set_initial", "cx_forward", "cx_adjoint", "cx_gradient", "cx_step",
     "cx_get_fields", "cx_get_psi0", "cx_get_norms", "cx_set_launch", "cx_set_timing", "cx_get_timing",
-    "cx_destroy", "cx_status_string", "cx_forward_static",
+    "cx_destroy", "cx_status_string", "cx_forward_static", "cx_cg_step", "cx_cg_reset",
     "cx_batch_workspace_size", "cx_batch_create", "cx_batch_set_initial", "cx_batch_bind", "cx_batch_set_tiles",
     "cx_batch_forward", "cx_batch_gradient", "cx_batch_get_fields", "cx_batch_get_status", "cx_batch_destroy",
-    "cx_batch_set_enabled", "cx_batch_step", "cx_batch_adjoint", "cx_batch_axpy",
+    "cx_batch_set_enabled", "cx_batch_step", "cx_batch_adjoint", "cx_batch_axpy", "cx_batch_prepare",
     "cx_nn_conv_forward", "cx_nn_conv_backward_data", "cx_nn_conv_backward_weight_scratch",
     "cx_nn_conv_backward_weight", "cx_nn_relu_backward", "cx_nn_add", "cx_nn_pool2", "cx_nn_up2", "cx_nn_mse",
     "cx_nn_adam", "cx_nn_cast_bf16", "cx_nn_conv_forward_f32", "cx_nn_smooth", "cx_nn_packed_weights",
@@ -59,6 +59,15 @@ class Desc(ctypes.Structure):
         ("source_order", ctypes.c_int),
         ("ctrl_windows", ctypes.c_int),
     ]
+
+
+class CGInfo(ctypes.Structure):
+    _fields_ = [("J0", ctypes.c_double), ("J", ctypes.c_double), ("lam", ctypes.c_double),
+                ("grad_sq", ctypes.c_double), ("beta", ctypes.c_double), ("trials", ctypes.c_int),
+                ("restarted", ctypes.c_int)]
+
+
+CG_VARIANTS = {"FR": 0, "PR": 1, "HS": 2, "DY": 3}
 
 
 class StepInfo(ctypes.Structure):
@@ -97,6 +106,8 @@ def load():
         "cx_get_timing": [vp, dp, ctypes.POINTER(ctypes.c_longlong)],
         "cx_destroy": [vp],
         "cx_forward_static": [D, vp, vp, vp, vp, vp, vp, vp],
+        "cx_cg_step": [vp, vp, vp, cint, ctypes.POINTER(CGInfo)],
+        "cx_cg_reset": [vp],
         "cx_batch_workspace_size": [D, cint, ctypes.POINTER(ctypes.c_size_t)],
         "cx_batch_create": [D, cint, vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)],
         "cx_batch_set_initial": [vp, vp, vp],
@@ -111,6 +122,7 @@ def load():
         "cx_batch_step": [vp, ctypes.POINTER(StepInfo), vp],
         "cx_batch_adjoint": [vp, vp, cint, vp],
         "cx_batch_axpy": [vp, vp],
+        "cx_batch_prepare": [vp],
         "cx_nn_conv_forward": [vp, vp, vp, vp, cint, cint, cint, cint, cint, cint, cint, vp],
         "cx_nn_conv_forward_f32": [vp, vp, vp, vp, cint, cint, cint, cint, cint, cint, vp],
         "cx_nn_smooth": [vp, vp, vp, cint, cint, cint, vp, cint, vp],

@@ -113,6 +113,12 @@ class Batch:
         self._leave()
         return self.out[self.count: 2 * self.count], self.out[2 * self.count:]
 
+    def prepare(self):
+        """Capture every launch sequence as a CUDA graph now (not on first use)."""
+        self._enter()
+        _lib.check(self.lib.cx_batch_prepare(self.h), "cx_batch_prepare")
+        self._leave()
+
     def axpy(self, lam):
         """g[i] <- g[i] - lam[i] E[i] (lam: per-problem floats)."""
         arr = (ctypes.c_double * self.count)(*[float(x) for x in lam])

@@ -332,6 +332,125 @@ template <typename T> static cx_status run_step(cx_problem* p, T* g, T* E, cx_st
     return CX_ERR_LINESEARCH;
 }
 
+// Nonlinear conjugate gradients with a weak Wolfe-Powell line search (remark
+// 2 after the gradient algorithm, Sec. 2.3).  The search direction is held
+// negated, P = -D, so that trial controls are g - lam P as in the Armijo
+// search.  work: [4][W][ctrl] = two gradient slots (current / trial), P, and
+// the trial control.
+template <typename T> static cx_status run_cg_step(cx_problem* p, T* g, T* work, int variant, cx_cg_info* info) {
+    const size_t n = (size_t)p->lay.nwin * p->lay.nctrl;
+    T* slot[2] = {work, work + n};
+    T* P = work + 2 * n;
+    T* gt = work + 3 * n;
+    double* part = p->at<double>(p->lay.off_part);
+    double* dots = p->at<double>(p->lay.off_scal) + 8;
+    auto read_dots = [&](const T* x0, const T* y0, const T* x1, const T* y1, const T* x2, const T* y2, const T* x3,
+                         const T* y3, double* out) -> cx_status {
+        const T* const xs[4] = {x0, x1, x2, x3};
+        const T* const ys[4] = {y0, y1, y2, y3};
+        CX_CUDA(launch_dots<T>(xs, ys, n, part, dots, p->stream));
+        CX_CUDA(cudaMemcpyAsync(out, dots, 4 * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+        CX_CUDA(cudaStreamSynchronize(p->stream));
+        return CX_OK;
+    };
+    cx_status rc;
+    double J0, gd, lam;
+    if (p->cg_k < 0) {
+        T* G = slot[0];
+        rc = run_forward<T>(p, g, nullptr, 0.0, nullptr, true);
+        if (rc) return rc;
+        rc = run_adjoint<T>(p, g, nullptr, nullptr, G);
+        if (rc) return rc;
+        double s4[4];
+        int st = 0;
+        if ((rc = read_scalars(p, s4, &st))) return rc;
+        if (st & ST_UNSTABLE) return CX_ERR_UNSTABLE;
+        CX_CUDA(cudaMemcpyAsync(P, G, n * sizeof(T), cudaMemcpyDeviceToDevice, p->stream));
+        J0 = s4[0];
+        p->cg_gg = s4[2];
+        gd = -s4[2];
+        lam = std::min(1.0, s4[3] > 0.0 ? 1.0 / s4[3] : 1.0);
+        p->cg_slot = 0;
+        p->cg_k = 0;
+    } else {
+        J0 = p->cg_J;
+        gd = p->cg_gd;
+        lam = p->cg_lam * p->cg_gd_prev / gd;
+    }
+    T* G = slot[p->cg_slot];
+    T* Gt = slot[1 - p->cg_slot];
+    const double c1 = 1e-4, c2 = 0.1;
+    double lo = 0.0, hi = INFINITY, Jt = 0.0;
+    int t = 0;
+    bool ok = false;
+    for (; t < 30; ++t) {
+        CX_CUDA(launch_lincomb<T>(gt, g, T(-lam), P, n, p->stream));
+        if ((rc = run_forward<T>(p, gt, nullptr, 0.0, nullptr, false))) return rc;
+        double s4[4];
+        if ((rc = read_scalars(p, s4, nullptr))) return rc;
+        Jt = s4[0];
+        if (!std::isfinite(Jt) || Jt > J0 + c1 * lam * gd) {
+            hi = lam;
+        } else {
+            if ((rc = run_adjoint<T>(p, gt, nullptr, nullptr, Gt))) return rc;
+            double d4[4];
+            if ((rc = read_dots(Gt, P, Gt, P, Gt, P, Gt, P, d4))) return rc;
+            const double dphi = -d4[0]; // <G(lam), D>
+            if (dphi < c2 * gd) {
+                lo = lam;
+            } else {
+                ok = true;
+                break;
+            }
+        }
+        lam = std::isfinite(hi) ? 0.5 * (lo + hi) : 2.0 * lam;
+    }
+    if (!ok) {
+        p->cg_k = -1;
+        p->fwd_valid = false;
+        return CX_ERR_LINESEARCH;
+    }
+    // a = <Gt,Gt>, b = <Gt,G>, c = <P,Gt>, d = <P,G>
+    double q[4];
+    if ((rc = read_dots(Gt, Gt, Gt, G, P, Gt, P, G, q))) return rc;
+    const double a = q[0], b = q[1], c = q[2], d = q[3];
+    const double dy = -(c - d); // <D, Gt - G>
+    double r;
+    switch (variant) {
+    case CX_CG_FR: r = a / p->cg_gg; break;
+    case CX_CG_PR: r = (a - b) / p->cg_gg; break;
+    case CX_CG_HS: r = (a - b) / dy; break;
+    default: r = a / dy; break;
+    }
+    double gd_new = -(a + r * c);
+    const bool restart = !(gd_new < 0.0) || std::fabs(b) >= 0.2 * a;
+    if (restart) {
+        CX_CUDA(cudaMemcpyAsync(P, Gt, n * sizeof(T), cudaMemcpyDeviceToDevice, p->stream));
+        gd_new = -a;
+    } else {
+        CX_CUDA(launch_lincomb<T>(P, Gt, T(r), P, n, p->stream)); // P <- Gt + r P
+    }
+    CX_CUDA(cudaMemcpyAsync(g, gt, n * sizeof(T), cudaMemcpyDeviceToDevice, p->stream));
+    if (info) {
+        info->J0 = J0;
+        info->J = Jt;
+        info->lam = lam;
+        info->grad_sq = a;
+        info->beta = r;
+        info->trials = t + 1;
+        info->restarted = restart ? 1 : 0;
+    }
+    p->cg_J = Jt;
+    p->cg_gg = a;
+    p->cg_gd_prev = gd;
+    p->cg_gd = gd_new;
+    p->cg_lam = lam;
+    p->cg_slot = 1 - p->cg_slot;
+    p->cg_k += 1;
+    CX_CUDA(cudaStreamSynchronize(p->stream));
+    return CX_OK;
+}
+
 // ------------------------------------------------------------------- C ABI
 
 extern "C" {
@@ -495,6 +614,7 @@ cx_status cx_set_initial(cx_problem* p, const void* u0, const void* v0) {
                                reinterpret_cast<float*>(p->ckpt_slot(0)), p->L, p->stream);
     if (e != cudaSuccess) return CX_ERR_CUDA;
     p->has_init = true;
+    p->cg_k = -1;
     p->fwd_valid = p->adj_valid = false;
     p->have_lam = false;
     return CX_OK;
@@ -519,6 +639,19 @@ cx_status cx_gradient(cx_problem* p, const void* g, void* dJdg, double* J_dev) {
     cx_status rc = cx_forward(p, g, J_dev);
     if (rc) return rc;
     return cx_adjoint(p, g, nullptr, nullptr, dJdg);
+}
+
+cx_status cx_cg_step(cx_problem* p, void* g_inout, void* work, int variant, cx_cg_info* info) {
+    if (!p || !g_inout || !work || variant < CX_CG_FR || variant > CX_CG_DY) return CX_ERR_INVALID_ARG;
+    if (!p->has_init) return CX_ERR_STATE;
+    if (p->lay.esz == 8) return run_cg_step<double>(p, (double*)g_inout, (double*)work, variant, info);
+    return run_cg_step<float>(p, (float*)g_inout, (float*)work, variant, info);
+}
+
+cx_status cx_cg_reset(cx_problem* p) {
+    if (!p) return CX_ERR_INVALID_ARG;
+    p->cg_k = -1;
+    return CX_OK;
 }
 
 cx_status cx_step(cx_problem* p, void* g_inout, void* E_work, cx_step_info* info) {

@@ -1015,6 +1015,21 @@ cx_status cx_batch_adjoint(cx_batch* b, const void* const* seed_u, int add_to_co
     return CX_OK;
 }
 
+cx_status cx_batch_prepare(cx_batch* b) {
+    if (!b) return CX_ERR_INVALID_ARG;
+    BatchHost& h = b->h;
+    if (!h.bound) return CX_ERR_STATE;
+    for (int mode = 0; mode < 4; ++mode) {
+        if (h.graphs[mode]) continue;
+        bool have_E = !h.dJdg.empty();
+        for (void* e : h.dJdg) have_E = have_E && e;
+        if (mode != G_FWD && !have_E) continue; // gradient, trial and adjoint graphs read dJdg
+        cx_status rc = h.esz == 8 ? capture<double>(h, mode, &h.graphs[mode]) : capture<float>(h, mode, &h.graphs[mode]);
+        if (rc) return rc;
+    }
+    return CX_OK;
+}
+
 cx_status cx_batch_axpy(cx_batch* b, const double* lam) {
     if (!b || !lam) return CX_ERR_INVALID_ARG;
     BatchHost& h = b->h;

@@ -102,6 +102,11 @@ template <typename T> int adjoint_occupancy(int Q, int threads);
 template <typename T>
 cudaError_t launch_axpy(T* g, const T* E, T lam, size_t n, cudaStream_t s);
 template <typename T>
+cudaError_t launch_lincomb(T* out, const T* a, T alpha, const T* b, size_t n, cudaStream_t s);
+template <typename T>
+cudaError_t launch_dots(const T* const (&x)[4], const T* const (&y)[4], size_t n, double* part, double* out,
+                        cudaStream_t s);
+template <typename T>
 cudaError_t launch_convert(const double* in, T* out, size_t n, cudaStream_t s);
 template <typename T>
 cudaError_t launch_setup_fields(const CxConst& C, const cx_problem_desc& d, T* theta, T* Kfield, T* a, T* u_tgt,

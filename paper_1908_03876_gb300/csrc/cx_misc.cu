@@ -1,5 +1,6 @@
 // cx_misc.cu -- initial equilibrium, final moments and cost, fixed-order
 // FP64 reductions, control update and field set-up kernels.
+#include <algorithm>
 #include <cmath>
 
 #include "cx_device.cuh"
@@ -141,6 +142,66 @@ cudaError_t launch_finalize(const double* a, int na, const double* b, int nb, do
     return cudaGetLastError();
 }
 
+// out <- a + alpha b (fused; the CG trial control g - lam P and the direction
+// update P <- G + r P)
+template <typename T> __global__ void k_lincomb(T* out, const T* a, T alpha, const T* b, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = fma(alpha, b[i], a[i]);
+}
+
+template <typename T> cudaError_t launch_lincomb(T* out, const T* a, T alpha, const T* b, size_t n, cudaStream_t s) {
+    int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 16);
+    k_lincomb<T><<<std::max(blocks, 1), 256, 0, s>>>(out, a, alpha, b, n);
+    return cudaGetLastError();
+}
+
+// Four dot products <x_j, y_j> (j < 4, FP64 products and sums): block
+// partials part[j][block], then one block sums each j in a fixed order.
+constexpr int DOT_BLOCKS = 512;
+template <typename T>
+__global__ void __launch_bounds__(256) k_dots(const T* x0, const T* y0, const T* x1, const T* y1, const T* x2,
+                                               const T* y2, const T* x3, const T* y3, size_t n, double* part) {
+    __shared__ double sh[4][256];
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        s[0] = fma((double)x0[i], (double)y0[i], s[0]);
+        s[1] = fma((double)x1[i], (double)y1[i], s[1]);
+        s[2] = fma((double)x2[i], (double)y2[i], s[2]);
+        s[3] = fma((double)x3[i], (double)y3[i], s[3]);
+    }
+    for (int j = 0; j < 4; ++j) sh[j][threadIdx.x] = s[j];
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h)
+            for (int j = 0; j < 4; ++j) sh[j][threadIdx.x] += sh[j][threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int j = 0; j < 4; ++j) part[j * DOT_BLOCKS + blockIdx.x] = sh[j][0];
+}
+
+__global__ void __launch_bounds__(256) k_dots_final(const double* part, double* out) {
+    __shared__ double sh[256];
+    const int j = blockIdx.x;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < DOT_BLOCKS; i += 256) s += part[j * DOT_BLOCKS + i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) sh[threadIdx.x] += sh[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[j] = sh[0];
+}
+
+template <typename T>
+cudaError_t launch_dots(const T* const (&x)[4], const T* const (&y)[4], size_t n, double* part, double* out,
+                        cudaStream_t s) {
+    k_dots<T><<<DOT_BLOCKS, 256, 0, s>>>(x[0], y[0], x[1], y[1], x[2], y[2], x[3], y[3], n, part);
+    k_dots_final<<<4, 256, 0, s>>>(part, out);
+    return cudaGetLastError();
+}
+
 // g <- g - lam E (accepted Armijo step)
 template <typename T> __global__ void k_axpy(T* g, const T* E, T lam, size_t n) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
@@ -276,6 +337,9 @@ template <typename T> KConst<T> make_kconst(const CxConst& C, int Q) {
     template cudaError_t launch_final<T>(const CxConst&, const T*, const T*, T*, T*, T*, double*, const Launch&,      \
                                          cudaStream_t);                                                               \
     template cudaError_t launch_axpy<T>(T*, const T*, T, size_t, cudaStream_t);                                 \
+    template cudaError_t launch_lincomb<T>(T*, const T*, T, const T*, size_t, cudaStream_t);                         \
+    template cudaError_t launch_dots<T>(const T* const (&)[4], const T* const (&)[4], size_t, double*, double*,      \
+                                        cudaStream_t);                                                               \
     template cudaError_t launch_convert<T>(const double*, T*, size_t, cudaStream_t);                                 \
     template cudaError_t launch_setup_fields<T>(const CxConst&, const cx_problem_desc&, T*, T*, T*, T*, uint8_t*,    \
                                                 uint8_t*, cudaStream_t);

@@ -114,6 +114,25 @@ class Problem:
         return dict(J0=info.J0, J=info.J, lam=info.lam, grad_sq=info.grad_sq, grad_inf=info.grad_inf,
                     trials=info.trials)
 
+    def cg_step(self, g, variant="PR"):
+        """One nonlinear conjugate-gradient iteration (Wolfe-Powell search), g
+        updated in place; the iteration state (gradients, direction) stays in
+        a work buffer of this object until cg_reset()."""
+        if g.dtype != self.dtype or not g.is_contiguous() or g.device != self.device or \
+                tuple(g.shape) != tuple(self.ctrl_shape):
+            raise ValueError("g must be a contiguous device tensor of the problem's dtype")
+        if getattr(self, "_cg_work", None) is None:
+            self._cg_work = torch.empty((4,) + tuple(self.ctrl_shape), dtype=self.dtype, device=self.device)
+        info = _lib.CGInfo()
+        _lib.check(self.lib.cx_cg_step(self.h, _ptr(g), _ptr(self._cg_work), _lib.CG_VARIANTS[variant],
+                                       ctypes.byref(info)), "cx_cg_step")
+        self.generation += 1
+        return dict(J0=info.J0, J=info.J, lam=info.lam, grad_sq=info.grad_sq, r=info.beta, trials=info.trials,
+                    restarted=bool(info.restarted))
+
+    def cg_reset(self):
+        _lib.check(self.lib.cx_cg_reset(self.h), "cx_cg_reset")
+
     def fields(self):
         u = torch.empty((self.w.ny, self.w.nx), dtype=self.dtype, device=self.device)
         v = torch.empty_like(u)

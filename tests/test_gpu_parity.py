@@ -209,6 +209,30 @@ def test_windowed_step_matches_oracle_fp64():
     assert rel(g, go) < 1e-12
 
 
+@pytest.mark.parametrize("variant", ["FR", "PR", "HS", "DY"])
+def test_cg_matches_oracle_fp64(variant):
+    """Nonlinear CG (Wolfe-Powell line search) on the GPU against the
+    oracle's iterations: J, step, trials, r and restarts per iteration, and
+    the control after four iterations."""
+    from paper_1908_03876_gb300.problem import Problem
+
+    w = W.aniso(40, 36, 20, seed=4, precision=64, ckpt_every=7)
+    w.windows = 4
+    w.chi = -0.3
+    p = Problem(w)
+    g = p.zeros_control()
+    po = oracle.from_workload(w)
+    go, st = np.zeros(w.ctrl_shape), None
+    for it in range(4):
+        info = p.cg_step(g, variant)
+        go, st, io = oracle.cg_iteration(po, go, st, variant=variant)
+        print(variant, it, info, {k: io[k] for k in ("J", "lam", "trials", "r", "restarted")})
+        assert abs(info["J"] - io["J"]) <= 1e-12 * abs(io["J"])
+        assert abs(info["lam"] - io["lam"]) <= 1e-10 * io["lam"] and info["trials"] == io["trials"]
+        assert abs(info["r"] - io["r"]) <= 1e-8 * max(1e-3, abs(io["r"])) and info["restarted"] == io["restarted"]
+    assert rel(g, go) < 1e-11
+
+
 # ---------------------------------------------------------------- FP32 parity
 
 def test_aniso_fp32_against_fp64_oracle():
