@@ -346,3 +346,26 @@ def cg_iteration(p: Problem, g, state=None, variant="PR", c1=1e-4, c2=0.1, max_t
         gdn = float(np.sum(Gt * Gt)) * -1.0
     info = dict(J0=J0, J=Jt, lam=lam, trials=t + 1, r=r, restarted=restarted, grad_sq=float(np.sum(Gt * Gt)))
     return gt, dict(J=Jt, G=Gt, D=Dn, gd=gdn, gd_prev=gd, lam=lam, k=k + 1), info
+
+
+def lma_step(p: Problem, g, c1=1e-4, max_trials=30):
+    """One steepest-descent iteration with the step length of the quadratic
+    model built from the sensitivity problem (eqs. LM / LMA, Sec. 2.3):
+    u^N(g - lam E) ~ u^N(g) - lam du^N with du^N the tangent-linear response to
+    E, so J(g - lam E) ~ J - lam ||E||^2 + lam^2 (||du^N||^2 + 2 alpha L ||E||^2)/2
+    (L steps per control window), minimised by
+    lam* = ||E||^2 / (||du^N||^2 + 2 alpha L ||E||^2).  Accepted under the
+    Armijo test J(g - lam E) <= J - c1 lam ||E||^2, halving lam otherwise.
+    Returns (g_new, info)."""
+    J0, E, _ = adjoint(p, g)
+    _, du, _ = tlm(p, g, E)
+    e2 = float(np.sum(E * E))
+    L = p.N // p.windows if p.windows else 1
+    lam = e2 / (float(np.sum(du * du)) + 2.0 * p.alpha * L * e2)
+    for t in range(max_trials):
+        gt = g - lam * E
+        Jt, _, _ = forward(p, gt)
+        if Jt <= J0 - c1 * lam * e2:
+            return gt, dict(J0=J0, J=Jt, lam=lam, trials=t + 1, E2=e2)
+        lam *= 0.5
+    raise RuntimeError("line search failed")

@@ -494,3 +494,30 @@ def test_cg_beats_steepest_descent():
     n_sd, n_cg = iterations(sd), iterations(cg)
     print("iterations: steepest descent", n_sd, "CG", n_cg)
     assert n_cg < n_sd, (n_cg, n_sd)
+
+
+def test_lma_step_minimises_the_quadratic_model():
+    """The sensitivity-based step length (eq. LMA) is the minimiser of the
+    quadratic model of J along -E: J at lam* matches the model to second
+    order and the directional derivative there nearly vanishes (checked with
+    fresh forward solves and central differences, not the adjoint)."""
+    w, p = _cg_problem()
+    g = w.random_control(3, 0.01)
+    J0, E, _ = oracle.adjoint(p, g)
+    g1, info = oracle.lma_step(p, g)
+    lam = info["lam"]
+    assert info["trials"] == 1 and info["J"] < J0
+    e2 = float(np.sum(E * E))
+
+    def phi(l):
+        return oracle.forward(p, g - l * E)[0]
+
+    h = 1e-4 * lam
+    slope0 = (phi(h) - phi(-h)) / (2 * h)
+    slope = (phi(lam + h) - phi(lam - h)) / (2 * h)
+    assert abs(slope0 + e2) <= 1e-5 * e2          # phi'(0) = -||E||^2
+    assert abs(slope) <= 0.02 * e2, (slope, e2)   # phi'(lam*) ~ 0 (the model is quadratic up to chemotaxis)
+    # the exact 1-D minimiser lies within a few percent of lam*
+    ls = lam * np.linspace(0.9, 1.1, 21)
+    best = ls[int(np.argmin([phi(l) for l in ls]))]
+    assert abs(best - lam) <= 0.05 * lam
