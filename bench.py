@@ -355,10 +355,10 @@ def run_warmstart(args, rank, world, local):
 
 
 def run_cg(args, rank, world, local):
-    """Nonlinear CG (Polak-Ribiere, Wolfe-Powell search) against Armijo
-    steepest descent on one problem: wall time and iterations until
-    J <= J* (1 + 1e-6), J* = the lowest cost either method reaches in its
-    iteration budget (a converged CG run)."""
+    """Nonlinear CG (Polak-Ribiere, Wolfe-Powell search) and steepest descent
+    with the linearised (sensitivity) line search against Armijo steepest
+    descent on one problem: wall time and iterations until J <= J* (1 + 1e-6),
+    J* = the lowest cost any method reaches in its iteration budget."""
     import numpy as np
     import torch
 
@@ -381,7 +381,7 @@ def run_cg(args, rank, world, local):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for k in range(n_iter):
-            info = p.cg_step(g, "PR") if method == "cg" else p.step(g)
+            info = p.cg_step(g, "PR") if method == "cg" else (p.lma_step(g) if method == "lma" else p.step(g))
             Js.append(info["J"])
             if target is not None and info["J"] <= target:
                 t_hit, it_hit = time.perf_counter() - t0, k + 1
@@ -392,10 +392,12 @@ def run_cg(args, rank, world, local):
 
     Jcg, _, _ = run("cg", 150)
     Jsd, _, _ = run("sd", 600)
-    Jstar = min(min(Jcg), min(Jsd))
+    Jlm, _, _ = run("lma", 600)
+    Jstar = min(min(Jcg), min(Jsd), min(Jlm))
     target = Jstar * (1 + 1e-6)
     _, t_cg, it_cg = run("cg", 150, target)
     _, t_sd, it_sd = run("sd", 600, target)
+    _, t_lm, it_lm = run("lma", 600, target)
     line = {
         "metric": "wall time to J* (1e-6 rel): nonlinear CG (Polak-Ribiere, Wolfe-Powell) vs Armijo steepest descent",
         "value": t_cg, "unit": "s", "n_gpus": 1, "steps": 1, "warmup": 0,
@@ -404,8 +406,9 @@ def run_cg(args, rank, world, local):
         "config": {"workload": "aniso 256x256 D2Q9 FP32, 200 steps, k = 50, control constant over 8 windows",
                    "J_star": Jstar, "iteration budgets": {"cg": 150, "steepest_descent": 600}},
         "steepest_descent_seconds": t_sd, "cg_iterations": it_cg, "steepest_descent_iterations": it_sd,
+        "lma_seconds": t_lm, "lma_iterations": it_lm,
         "speedup_vs_steepest_descent": None if (t_cg is None or t_sd is None) else t_sd / t_cg,
-        "J_final": {"cg": Jcg[-1], "steepest_descent": Jsd[-1]},
+        "J_final": {"cg": Jcg[-1], "steepest_descent": Jsd[-1], "lma": Jlm[-1]},
     }
     print(json.dumps(line), flush=True)
 

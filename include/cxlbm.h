@@ -164,6 +164,25 @@ cx_status cx_gradient(cx_problem* p, const void* g, void* dJdg, double* J_dev);
  * NULL.  Errors: CX_ERR_LINESEARCH (g_inout unchanged), CX_ERR_UNSTABLE. */
 cx_status cx_step(cx_problem* p, void* g_inout, void* E_work, cx_step_info* info);
 
+/* Sensitivity (tangent-linear) problem along the control direction dg
+ * (device T [W][ctrl], like g) about the trajectory of control g, which must
+ * be the control of the preceding cx_forward (its checkpoints are reused;
+ * the state stays valid for a following cx_adjoint or step).  The forward
+ * step of cx_forward linearised about that trajectory, solved by the same
+ * MRT scheme (the sensitivity system of the remark after the gradient
+ * algorithm, Sec. 2.3), from du^0 = dv^0 = 0.  Writes du^N, dv^N (device T
+ * [ny][nx], either may be NULL) and ||du^N||^2 (host double, may be NULL;
+ * synchronising when given).  Errors: CX_ERR_STATE (no forward). */
+cx_status cx_tlm(cx_problem* p, const void* g, const void* dg, void* du_out, void* dv_out, double* du_sq);
+
+/* One steepest-descent iteration whose step length minimises the quadratic
+ * model of J along -E from the sensitivity problem (eqs. LM / LMA, Sec. 2.3):
+ * lam* = ||E||^2 / (||du^N(E)||^2 + 2 alpha L ||E||^2), L = N/W steps per
+ * control window; accepted under the Armijo test of cx_step (halved up to 30
+ * times if it fails).  Costs one adjoint, one sensitivity pass and usually
+ * one trial forward.  Arguments and errors as cx_step. */
+cx_status cx_lma_step(cx_problem* p, void* g_inout, void* E_work, cx_step_info* info);
+
 /* Nonlinear conjugate gradients (remark 2 after the gradient algorithm,
  * Sec. 2.3): direction D_k = -G_k (k = 0), else -G_k + r_{k-1} D_{k-1} with r
  * from Fletcher-Reeves, Polak-Ribiere, Hestenes-Stiefel or Dai-Yuan, reset to

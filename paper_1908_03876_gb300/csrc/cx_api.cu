@@ -99,6 +99,7 @@ Layout cx::make_layout(const cx_problem_desc* d) {
     L.off_part = take(sizeof(double) * 4 * (size_t)L.nparts);
     L.off_scal = take(sizeof(double) * 16);
     L.off_status = take(sizeof(int) * 4);
+    L.off_tlm = take(4 * fld);
     L.total = o;
     return L;
 }
@@ -319,6 +320,119 @@ template <typename T> static cx_status run_step(cx_problem* p, T* g, T* E, cx_st
             if (info) {
                 info->J0 = J0;
                 info->J = Jt;
+                info->lam = lam;
+                info->grad_sq = e2;
+                info->grad_inf = einf;
+                info->trials = t + 1;
+            }
+            return CX_OK;
+        }
+        lam *= 0.5;
+    }
+    p->fwd_valid = false;
+    return CX_ERR_LINESEARCH;
+}
+
+// Tangent-linear (sensitivity) pass along the control direction dg about the
+// base trajectory of control g (the state of the preceding forward): each
+// checkpointed segment is recomputed with its tape, then the tangent steps of
+// the segment run on the adjoint's ping-pong lattices (free here).  The
+// tangent starts from df^0 = 0.  du_out / dv_out (may be null) receive du^N,
+// dv^N; *du_sq (host, may be null) receives ||du^N||^2.
+template <typename T>
+static cx_status run_tlm(cx_problem* p, const T* g, const T* dg, T* du_out, T* dv_out, double* du_sq) {
+    const Layout& Ly = p->lay;
+    const CxConst& C = p->C;
+    T* zero = p->at<T>(Ly.off_tlm);
+    T* du = du_out ? du_out : zero + Ly.plane;
+    T* dv = dv_out ? dv_out : zero + 2 * Ly.plane;
+    T* scratch = zero + 3 * Ly.plane;
+    T* dphi = p->at<T>(Ly.off_sigma);
+    T* phi = p->at<T>(Ly.off_phi);
+    T* dA = p->at<T>(Ly.off_adjA);
+    T* dB = p->at<T>(Ly.off_adjB);
+    CX_CUDA(cudaMemsetAsync(zero, 0, Ly.plane * sizeof(T), p->stream));
+    CX_CUDA(cudaMemsetAsync(dA, 0, (size_t)2 * Ly.Q * Ly.plane * sizeof(T), p->stream)); // df^0 = 0
+    const T* din = dA;
+    for (int s = 0; s < Ly.S; ++s) {
+        const int n0 = s * Ly.k, n1 = std::min(Ly.N, n0 + Ly.k);
+        if (s >= 1)
+            CX_CUDA(cudaMemcpyAsync(phi, p->ckpt_phi_slot(s), Ly.plane * sizeof(T), cudaMemcpyDeviceToDevice,
+                                    p->stream));
+        const T* in = reinterpret_cast<const T*>(p->ckpt_slot(s));
+        for (int n = n0; n < n1; ++n) { // base recompute with tape
+            FwdArgs<T> A{};
+            T* out = p->at<T>((n % 2) ? Ly.off_popB : Ly.off_popA);
+            set_planes(p, A.pin, in);
+            set_planes(p, A.pout, out);
+            A.phi = phi;
+            A.g = g ? g + (size_t)(n / Ly.win_len) * Ly.nctrl : nullptr;
+            A.tape = reinterpret_cast<T*>(p->tape_slot(n - n0));
+            A.n = n;
+            CX_CUDA(launch_forward<T>(C, p->kc((T*)nullptr), A, p->Lf, p->stream));
+            in = out;
+        }
+        for (int n = n0; n < n1; ++n) { // tangent steps of the segment
+            TlmArgs<T> A{};
+            T* out = (din == dA) ? dB : dA;
+            set_planes(p, A.pin, din);
+            set_planes(p, A.pout, out);
+            A.dphi = dphi;
+            A.tape = reinterpret_cast<const T*>(p->tape_slot(n - n0));
+            A.dg = dg ? dg + (size_t)(n / Ly.win_len) * Ly.nctrl : nullptr;
+            A.n = n;
+            CX_CUDA(launch_tlm<T>(C, p->kc((T*)nullptr), A, p->Lf, p->stream));
+            din = out;
+        }
+    }
+    double* part = p->at<double>(Ly.off_part);
+    CX_CUDA(launch_final<T>(C, din, zero, du, dv, scratch, part, p->L, p->stream));
+    double* out = p->at<double>(Ly.off_scal) + 12;
+    CX_CUDA(launch_finalize(part, p->nblocks, nullptr, 0, 0.0, out, p->at<int>(Ly.off_status), ST_UNSTABLE, 0,
+                            p->stream));
+    p->tape_last_valid = true; // the last segment was recomputed last
+    p->adj_valid = false;
+    if (du_sq) {
+        double h = 0.0;
+        CX_CUDA(cudaMemcpyAsync(&h, out, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+        CX_CUDA(cudaStreamSynchronize(p->stream));
+        *du_sq = 2.0 * h;
+    }
+    return CX_OK;
+}
+
+// One steepest-descent iteration with the step length of the quadratic model
+// of J along -E built from the sensitivity problem (eqs. LM / LMA, Sec. 2.3):
+// J(g - lam E) ~ J - lam ||E||^2 + lam^2 (||S E||^2 + 2 alpha L ||E||^2) / 2,
+// minimised by lam* = ||E||^2 / (||S E||^2 + 2 alpha L ||E||^2), S E = du^N the
+// tangent response to E and L the steps per control window.  The step is
+// accepted under the Armijo test of cx_step (halved if it fails).
+template <typename T> static cx_status run_lma_step(cx_problem* p, T* g, T* E, cx_step_info* info) {
+    cx_status rc;
+    if (!p->fwd_valid) {
+        if ((rc = run_forward<T>(p, g, nullptr, 0.0, nullptr, true))) return rc;
+    }
+    if ((rc = run_adjoint<T>(p, g, nullptr, nullptr, E))) return rc;
+    double s4[4];
+    int st = 0;
+    if ((rc = read_scalars(p, s4, &st))) return rc;
+    if (st & ST_UNSTABLE) return CX_ERR_UNSTABLE;
+    const double J0 = s4[0], e2 = s4[2], einf = s4[3];
+    double sesq = 0.0;
+    if ((rc = run_tlm<T>(p, g, E, nullptr, nullptr, &sesq))) return rc;
+    const double curv = sesq + 2.0 * p->C.alpha * p->lay.win_len * e2;
+    double lam = curv > 0.0 ? e2 / curv : std::min(1.0, einf > 0.0 ? 1.0 / einf : 1.0);
+    for (int t = 0; t < 30; ++t) {
+        if ((rc = run_forward<T>(p, g, E, lam, nullptr, false))) return rc;
+        double j4[4];
+        if ((rc = read_scalars(p, j4, nullptr))) return rc;
+        if (std::isfinite(j4[0]) && j4[0] <= J0 - 1e-4 * lam * e2) {
+            CX_CUDA(launch_axpy<T>(g, E, T(lam), (size_t)p->lay.nwin * p->lay.nctrl, p->stream));
+            p->fwd_valid = true;
+            p->adj_valid = false;
+            if (info) {
+                info->J0 = J0;
+                info->J = j4[0];
                 info->lam = lam;
                 info->grad_sq = e2;
                 info->grad_inf = einf;
@@ -646,6 +760,21 @@ cx_status cx_cg_step(cx_problem* p, void* g_inout, void* work, int variant, cx_c
     if (!p->has_init) return CX_ERR_STATE;
     if (p->lay.esz == 8) return run_cg_step<double>(p, (double*)g_inout, (double*)work, variant, info);
     return run_cg_step<float>(p, (float*)g_inout, (float*)work, variant, info);
+}
+
+cx_status cx_tlm(cx_problem* p, const void* g, const void* dg, void* du_out, void* dv_out, double* du_sq) {
+    if (!p || !dg) return CX_ERR_INVALID_ARG;
+    if (!p->fwd_valid) return CX_ERR_STATE;
+    if (p->lay.esz == 8)
+        return run_tlm<double>(p, (const double*)g, (const double*)dg, (double*)du_out, (double*)dv_out, du_sq);
+    return run_tlm<float>(p, (const float*)g, (const float*)dg, (float*)du_out, (float*)dv_out, du_sq);
+}
+
+cx_status cx_lma_step(cx_problem* p, void* g_inout, void* E_work, cx_step_info* info) {
+    if (!p || !g_inout || !E_work) return CX_ERR_INVALID_ARG;
+    if (!p->has_init) return CX_ERR_STATE;
+    if (p->lay.esz == 8) return run_lma_step<double>(p, (double*)g_inout, (double*)E_work, info);
+    return run_lma_step<float>(p, (float*)g_inout, (float*)E_work, info);
 }
 
 cx_status cx_cg_reset(cx_problem* p) {

@@ -60,6 +60,17 @@ template <typename T> struct FwdArgs {
     __device__ __forceinline__ T* out(int j) const { return pout[j]; }
 };
 
+template <typename T> struct TlmArgs {
+    const T* pin[18];    // plane j of the tangent populations dP^{n-1} (pulled), or df^0 read locally at n = 0
+    T* pout[18];         // plane j of dP^n
+    T* dphi;             // [plane] dPhi^{n-1} in, dPhi^n out
+    const T* tape;       // [3][plane] base (u^n, G_x^n, G_y^n)
+    const T* dg;         // [cny*cnx] direction dg^n, or null
+    int n;
+    __device__ __forceinline__ const T* in(int j) const { return pin[j]; }
+    __device__ __forceinline__ T* out(int j) const { return pout[j]; }
+};
+
 template <typename T> struct AdjArgs {
     const T* rin[18];    // plane j of psi^{n+1} ([2][Q][plane]); unused at the terminal step
     const T* wu;         // terminal seeds psi^N_u,i = wu(x), psi^N_v,i = wv(x) (terminal step only)
@@ -98,6 +109,8 @@ cudaError_t launch_final(const CxConst& C, const T* Pin, const T* u_tgt, T* uN, 
 cudaError_t launch_finalize(const double* part_a, int na, const double* part_b, int nb, double scale_b, double* out,
                             int* status, int status_bit, int mode, cudaStream_t s);
 template <typename T> int forward_occupancy(int Q, int threads);
+template <typename T>
+cudaError_t launch_tlm(const CxConst& C, const KConst<T>& K, const TlmArgs<T>& A, const Launch& L, cudaStream_t s);
 template <typename T> int adjoint_occupancy(int Q, int threads);
 template <typename T>
 cudaError_t launch_axpy(T* g, const T* E, T lam, size_t n, cudaStream_t s);

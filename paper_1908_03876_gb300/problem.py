@@ -130,6 +130,30 @@ class Problem:
         return dict(J0=info.J0, J=info.J, lam=info.lam, grad_sq=info.grad_sq, r=info.beta, trials=info.trials,
                     restarted=bool(info.restarted))
 
+    def tlm(self, g, dg):
+        """Sensitivity (du^N, dv^N, ||du^N||^2) of the last forward's trajectory
+        (control g) along the direction dg."""
+        g = None if g is None else self._t(g, self.ctrl_shape)
+        dg = self._t(dg, self.ctrl_shape)
+        du = torch.empty((self.w.ny, self.w.nx), dtype=self.dtype, device=self.device)
+        dv = torch.empty_like(du)
+        sq = ctypes.c_double()
+        _lib.check(self.lib.cx_tlm(self.h, _ptr(g), _ptr(dg), _ptr(du), _ptr(dv), ctypes.byref(sq)), "cx_tlm")
+        return du, dv, sq.value
+
+    def lma_step(self, g, E=None):
+        """One steepest-descent iteration with the linearised (sensitivity)
+        line search, g updated in place."""
+        if g.dtype != self.dtype or not g.is_contiguous() or g.device != self.device or \
+                tuple(g.shape) != tuple(self.ctrl_shape):
+            raise ValueError("g must be a contiguous device tensor of the problem's dtype")
+        E = E if E is not None else torch.empty_like(g)
+        info = _lib.StepInfo()
+        _lib.check(self.lib.cx_lma_step(self.h, _ptr(g), _ptr(E), ctypes.byref(info)), "cx_lma_step")
+        self.generation += 1
+        return dict(J0=info.J0, J=info.J, lam=info.lam, grad_sq=info.grad_sq, grad_inf=info.grad_inf,
+                    trials=info.trials)
+
     def cg_reset(self):
         _lib.check(self.lib.cx_cg_reset(self.h), "cx_cg_reset")
 

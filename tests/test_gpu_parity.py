@@ -233,6 +233,51 @@ def test_cg_matches_oracle_fp64(variant):
     assert rel(g, go) < 1e-11
 
 
+@pytest.mark.parametrize("k", [6, 20])
+def test_tlm_matches_oracle_fp64(k):
+    """Sensitivity problem (tangent-linear MRT pass) along a random direction:
+    du^N, dv^N against the oracle's tangent-linear model, with checkpoint
+    segments (k = 6) and without (k = N)."""
+    from paper_1908_03876_gb300.problem import Problem
+
+    w = W.aniso(40, 36, 20, seed=6, precision=64, ckpt_every=k)
+    w.windows = 4
+    w.chi = -0.3
+    g = w.random_control(11, 0.05)
+    dg = w.random_control(12, 1.0)
+    p = Problem(w)
+    p.forward(g)
+    du, dv, sq = p.tlm(g, dg)
+    _, duo, dvo = oracle.tlm(oracle.from_workload(w), g, dg)
+    print(f"tlm k={k}: du {rel(du, duo):.2e} dv {rel(dv, dvo):.2e}")
+    assert rel(du, duo) < 1e-12 and rel(dv, dvo) < 1e-12
+    assert abs(sq - np.sum(duo * duo)) <= 1e-12 * np.sum(duo * duo)
+    # the forward state survives: an adjoint after the sensitivity pass is the plain one
+    E = p.adjoint(g)
+    _, Eo, _ = oracle.adjoint(oracle.from_workload(w), g)
+    assert rel(E, Eo) < 1e-12
+
+
+def test_lma_step_matches_oracle_fp64():
+    """Steepest descent with the linearised line search: three iterations
+    against the oracle's."""
+    from paper_1908_03876_gb300.problem import Problem
+
+    w = W.aniso(40, 36, 20, seed=4, precision=64, ckpt_every=7)
+    w.windows = 4
+    w.chi = -0.3
+    p = Problem(w)
+    g = p.zeros_control()
+    po = oracle.from_workload(w)
+    go = np.zeros(w.ctrl_shape)
+    for it in range(3):
+        info = p.lma_step(g)
+        go, io = oracle.lma_step(po, go)
+        assert abs(info["J"] - io["J"]) <= 1e-12 * abs(io["J"])
+        assert abs(info["lam"] - io["lam"]) <= 1e-10 * io["lam"] and info["trials"] == io["trials"]
+    assert rel(g, go) < 1e-11
+
+
 # ---------------------------------------------------------------- FP32 parity
 
 def test_aniso_fp32_against_fp64_oracle():
