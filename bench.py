@@ -369,6 +369,7 @@ def run_cg(args, rank, world, local):
 
     build()
     from paper_1908_03876_gb300 import workloads as W
+    from paper_1908_03876_gb300._lib import CxError
     from paper_1908_03876_gb300.problem import Problem
 
     w = W.aniso(256, 256, 200, seed=1, precision=32, ckpt_every=50)
@@ -381,7 +382,12 @@ def run_cg(args, rank, world, local):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for k in range(n_iter):
-            info = p.cg_step(g, "PR") if method == "cg" else (p.lma_step(g) if method == "lma" else p.step(g))
+            try:
+                info = p.cg_step(g, "PR") if method == "cg" else (p.lma_step(g) if method == "lma" else p.step(g))
+            except CxError as e:  # no acceptable step: converged to the FP32 resolution of J
+                if e.code != 6:
+                    raise
+                break
             Js.append(info["J"])
             if target is not None and info["J"] <= target:
                 t_hit, it_hit = time.perf_counter() - t0, k + 1
