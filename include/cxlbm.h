@@ -193,12 +193,17 @@ cx_status cx_lma_step(cx_problem* p, void* g_inout, void* E_work, cx_step_info* 
  * 30 trials; first trial min(1, 1/||G||_inf), then lam_{k-1} <G,D>_{k-1} /
  * <G,D>_k).  Each trial costs a forward solve, and an AMRT sweep when the
  * decrease condition holds; the accepted trial's gradient is the next
- * iteration's.  work: device T [4][W][ctrl_ny][ctrl_nx], caller-owned and
+ * iteration's.  If no trial meets both conditions (no progress along the CG
+ * direction, e.g. at the rounding floor of FP32 lattices) the iteration
+ * falls back to a steepest-descent step with Armijo backtracking from
+ * min(1, 1/||G||_inf) (soft reset; trials then counts 30 + its trials).
+ * work: device T [4][W][ctrl_ny][ctrl_nx], caller-owned and
  * kept between calls (gradients, direction, trial control).  The iteration
  * state refers to g_inout as the previous call left it: call cx_cg_reset
  * after changing g or the initial state (cx_set_initial resets it).
- * Synchronous.  Errors: CX_ERR_LINESEARCH (no step met the conditions; the
- * state is reset), CX_ERR_UNSTABLE, CX_ERR_STATE, CX_ERR_INVALID_ARG. */
+ * Synchronous.  Errors: CX_ERR_LINESEARCH (not even the fallback step
+ * decreased J; the state is reset), CX_ERR_UNSTABLE, CX_ERR_STATE,
+ * CX_ERR_INVALID_ARG. */
 enum { CX_CG_FR = 0, CX_CG_PR = 1, CX_CG_HS = 2, CX_CG_DY = 3 };
 typedef struct {
     double J0;      /* cost at the incoming control       */

@@ -297,7 +297,10 @@ def cg_iteration(p: Problem, g, state=None, variant="PR", c1=1e-4, c2=0.1, max_t
     phi(l) = J(g + l D): accept when phi(l) <= phi(0) + c1 l phi'(0) and
     phi'(l) >= c2 phi'(0); else bisect the bracket (doubling while it is
     open).  First trial min(1, 1/||G||_inf) at k = 0, else
-    l_{k-1} phi'_{k-1}(0) / phi'_k(0).
+    l_{k-1} phi'_{k-1}(0) / phi'_k(0).  If no trial meets both conditions
+    (the CG direction makes no progress, e.g. at the rounding floor of an FP32
+    lattice), the iteration falls back to a steepest-descent step with Armijo
+    backtracking from min(1, 1/||G||_inf) (soft reset).
 
     state: None (k = 0) or the dict returned by the previous call.
     Returns (g_new, state, info)."""
@@ -323,7 +326,20 @@ def cg_iteration(p: Problem, g, state=None, variant="PR", c1=1e-4, c2=0.1, max_t
             break
         lam = 0.5 * (lo + hi) if np.isfinite(hi) else 2.0 * lam
     else:
-        raise RuntimeError("Wolfe line search failed")
+        # soft reset: steepest descent with Armijo backtracking
+        gg = float(np.sum(G * G))
+        lam = min(1.0, 1.0 / float(np.max(np.abs(G)))) if np.max(np.abs(G)) > 0 else 1.0
+        for t2 in range(max_trials):
+            gt = g - lam * G
+            Jt, Gt, _ = adjoint(p, gt)
+            if np.isfinite(Jt) and Jt <= J0 - c1 * lam * gg:
+                break
+            lam *= 0.5
+        else:
+            raise RuntimeError("line search failed")
+        gtgt = float(np.sum(Gt * Gt))
+        info = dict(J0=J0, J=Jt, lam=lam, trials=max_trials + t2 + 1, r=0.0, restarted=True, grad_sq=gtgt)
+        return gt, dict(J=Jt, G=Gt, D=-Gt, gd=-gtgt, gd_prev=-gg, lam=lam, k=k + 1), info
     gg = float(np.sum(G * G))
     y = Gt - G
     dy = float(np.sum(D * y))

@@ -484,6 +484,7 @@ template <typename T> static cx_status run_cg_step(cx_problem* p, T* g, T* work,
         p->cg_gg = s4[2];
         gd = -s4[2];
         lam = std::min(1.0, s4[3] > 0.0 ? 1.0 / s4[3] : 1.0);
+        p->cg_ginf = s4[3];
         p->cg_slot = 0;
         p->cg_k = 0;
     } else {
@@ -520,9 +521,59 @@ template <typename T> static cx_status run_cg_step(cx_problem* p, T* g, T* work,
         lam = std::isfinite(hi) ? 0.5 * (lo + hi) : 2.0 * lam;
     }
     if (!ok) {
-        p->cg_k = -1;
-        p->fwd_valid = false;
-        return CX_ERR_LINESEARCH;
+        // soft reset: steepest descent with Armijo backtracking
+        double gnorm[4];
+        if ((rc = read_dots(G, G, G, G, G, G, G, G, gnorm))) return rc;
+        const double gg0 = gnorm[0];
+        double lam2 = p->cg_ginf > 0.0 ? std::min(1.0, 1.0 / p->cg_ginf) : 1.0;
+        int t2 = 0;
+        bool ok2 = false;
+        for (; t2 < 30; ++t2) {
+            CX_CUDA(launch_lincomb<T>(gt, g, T(-lam2), G, n, p->stream));
+            if ((rc = run_forward<T>(p, gt, nullptr, 0.0, nullptr, false))) return rc;
+            double s4[4];
+            if ((rc = read_scalars(p, s4, nullptr))) return rc;
+            if (std::isfinite(s4[0]) && s4[0] <= J0 - c1 * lam2 * gg0) {
+                Jt = s4[0];
+                ok2 = true;
+                break;
+            }
+            lam2 *= 0.5;
+        }
+        if (!ok2) {
+            p->cg_k = -1;
+            p->fwd_valid = false;
+            return CX_ERR_LINESEARCH;
+        }
+        if ((rc = run_adjoint<T>(p, gt, nullptr, nullptr, Gt))) return rc;
+        double s4[4];
+        if ((rc = read_scalars(p, s4, nullptr))) return rc;
+        CX_CUDA(cudaMemcpyAsync(P, Gt, n * sizeof(T), cudaMemcpyDeviceToDevice, p->stream));
+        CX_CUDA(cudaMemcpyAsync(g, gt, n * sizeof(T), cudaMemcpyDeviceToDevice, p->stream));
+        if (info) {
+            info->J0 = J0;
+            info->J = Jt;
+            info->lam = lam2;
+            info->grad_sq = s4[2];
+            info->beta = 0.0;
+            info->trials = 30 + t2 + 1;
+            info->restarted = 1;
+        }
+        p->cg_J = Jt;
+        p->cg_gg = s4[2];
+        p->cg_ginf = s4[3];
+        p->cg_gd_prev = -gg0;
+        p->cg_gd = -s4[2];
+        p->cg_lam = lam2;
+        p->cg_slot = 1 - p->cg_slot;
+        p->cg_k += 1;
+        CX_CUDA(cudaStreamSynchronize(p->stream));
+        return CX_OK;
+    }
+    {
+        double s4[4];
+        if ((rc = read_scalars(p, s4, nullptr))) return rc; // max |Gt| of the accepted trial's sweep
+        p->cg_ginf = s4[3];
     }
     // a = <Gt,Gt>, b = <Gt,G>, c = <P,Gt>, d = <P,G>
     double q[4];

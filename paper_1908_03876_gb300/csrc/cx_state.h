@@ -57,7 +57,7 @@ struct cx_problem {
     // nonlinear CG state (cx_cg_step): iteration, cost, <G,G>, <G,D>, the
     // previous <G,D> and step, and which work slot holds the current gradient
     int cg_k = -1;
-    double cg_J = 0.0, cg_gg = 0.0, cg_gd = 0.0, cg_gd_prev = 0.0, cg_lam = 0.0;
+    double cg_J = 0.0, cg_gg = 0.0, cg_gd = 0.0, cg_gd_prev = 0.0, cg_lam = 0.0, cg_ginf = 0.0;
     int cg_slot = 0;
     void* psi0 = nullptr;
     bool timing = false;
