@@ -69,6 +69,7 @@ def _load():
         lib.or_forward_trace.argtypes = [P, vp, vp, vp, vp]
         lib.or_tlm.argtypes = [P, vp, vp, vp, vp, vp, dp]
         lib.or_adjoint.argtypes = [P, vp, vp, vp, vp, vp, dp]
+        lib.or_cadjoint.argtypes = [P, vp, vp, dp]
         lib.or_lattice.argtypes = [ctypes.c_int, vp, vp, vp, vp]
         lib.or_feq.argtypes = [ctypes.c_int, ctypes.c_double, vp, ctypes.c_double, vp]
         lib.or_collide_node.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp,
@@ -218,6 +219,19 @@ def adjoint(p: Problem, g=None, seed_u=None, seed_v=None, want_psi0=False):
     _check(lib.or_adjoint(ctypes.byref(st), _ptr(g), _ptr(su), _ptr(sv), _ptr(dJdg), _ptr(psi0),
                           ctypes.byref(J)), "adjoint")
     return J.value, p.restrict_gradient(dJdg), psi0
+
+
+def cadjoint(p: Problem, g=None):
+    """Continuous-adjoint gradient (adjoint PDE solved by the MRT scheme with
+    time reversed, see mrt_oracle.h).  Returns (J, dJ/dg [W or N, cny, cnx])."""
+    lib = _load()
+    st = p._struct()
+    g = _f64(p.expand(g))
+    w = p.window or (0, 0, p.nx, p.ny)
+    dJdg = np.zeros((p.N, w[3], w[2]))
+    J = ctypes.c_double(0.0)
+    _check(lib.or_cadjoint(ctypes.byref(st), _ptr(g), _ptr(dJdg), ctypes.byref(J)), "cadjoint")
+    return J.value, p.restrict_gradient(dJdg)
 
 
 def lattice(Q: int):

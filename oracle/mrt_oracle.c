@@ -809,3 +809,122 @@ int or_feq(int Q, double Theta, const double a[2], double d, double* out) {
     feq_lat(&L, Theta, aa, d, out);
     return 0;
 }
+
+/* ------------------------------------------------- continuous adjoint */
+
+/* The continuous adjoint system (see mrt_oracle.h), time-reversed, solved by
+ * the forward MRT scheme of Sec. 3.1 with:
+ *   - convection velocity -a for both adjoint species (a.grad X = div(a X)
+ *     for the solenoidal fields used here);
+ *   - the terms chi grad v . grad u~ + r_vu v~ (for u~) and r_vv v~ (for v~)
+ *     as first-order sources tau w~_i Phi (no (tau/2) time-derivative term);
+ *   - -div(chi u grad u~) in the v~ equation as the chemotaxis-type source
+ *     (w_i / Cs^2) chi u e_i . (K_v grad u~), the construction the forward
+ *     uses for -div(chi u grad v);
+ *   - grad u~ from u~'s first non-equilibrium moment,
+ *     -K_u (j~_u + a u~) / (tau d_u Cs^2) (relation C146 without the source
+ *     correction, since that source depends on grad u~ itself);
+ *   - u, grad v at forward step n (the collision of step n) paired with the
+ *     adjoint step from t_{n+1} back to t_n.
+ * At s = 0 the adjoint populations are phi^eq(u~(0), -a) and 0. */
+int or_cadjoint(const or_problem* p, const double* g, double* dJdg, double* J) {
+    lattice_t L;
+    if (lattice_init(&L, p->Q)) return -1;
+    int Q = p->Q, nx = p->nx, ny = p->ny, N = p->N;
+    size_t nn = (size_t)nx * ny, npop = nn * 2 * Q;
+    double* fN = calloc(npop, sizeof(double));
+    double* traj = calloc((size_t)N * npop, sizeof(double));
+    double* fa = calloc(npop, sizeof(double));
+    double* Pa = calloc(npop, sizeof(double));
+    node_t* nodes = malloc(sizeof(node_t) * nn);
+    double* wtu = malloc(sizeof(double) * nn * 9);
+    double* wtv = malloc(sizeof(double) * nn * 9);
+    if (!fN || !traj || !fa || !Pa || !nodes || !wtu || !wtv) return -2;
+    int rc = run_forward(p, g, fN, traj, NULL, NULL, NULL, NULL);
+    if (rc) return rc;
+    double* u = malloc(sizeof(double) * nn);
+    macro_fields(p, fN, u, NULL);
+    if (J) *J = terminal_cost(p, u) + control_penalty(p, g);
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            size_t k = (size_t)y * nx + x;
+            node_params(&L, p, x, y, &nodes[k]);
+            /* w~_i = w_i (1 + V.e_i / Cs^2), V = (I - K/2)(-a), per adjoint species */
+            for (int sp = 0; sp < 2; ++sp) {
+                double (*K)[2] = sp == 0 ? nodes[k].Ku : nodes[k].Kv;
+                double am[2] = {-nodes[k].a[0], -nodes[k].a[1]};
+                double V[2] = {am[0] - 0.5 * (K[0][0] * am[0] + K[0][1] * am[1]),
+                               am[1] - 0.5 * (K[1][0] * am[0] + K[1][1] * am[1])};
+                double* wt = (sp == 0 ? wtu : wtv) + k * 9;
+                for (int i = 0; i < Q; ++i) wt[i] = L.w[i] * (1.0 + (V[0] * L.e[i][0] + V[1] * L.e[i][1]) / CS2);
+            }
+        }
+    /* initial adjoint populations */
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            if (is_solid(p, x, y)) continue;
+            size_t k = (size_t)y * nx + x;
+            double am[2] = {-nodes[k].a[0], -nodes[k].a[1]};
+            feq_lat(&L, u[k] - p->u_tgt[k], am, p->d_u, fa + (k * 2) * Q);
+        }
+    size_t nctrl = (size_t)p->cnx * p->cny;
+    memset(dJdg, 0, sizeof(double) * (size_t)N * nctrl);
+    double Pi[9][9], feq[9];
+    for (int n = N - 1; n >= 0; --n) {
+        const double* f = traj + (size_t)n * npop; /* forward pre-collision state of step n */
+        memset(Pa, 0, sizeof(double) * npop);
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                if (is_solid(p, x, y)) continue;
+                size_t k = (size_t)y * nx + x;
+                const node_t* nd = &nodes[k];
+                /* forward quantities of step n: u^n and grad v^n */
+                state_t st;
+                double Ptmp[18];
+                collide_local(&L, p, nd, n, f + (k * 2) * Q, f + (k * 2 + 1) * Q, g_at(p, g, n, x, y), 0.0,
+                              Ptmp, Ptmp + 9, &st);
+                const double* au = fa + (k * 2) * Q;
+                const double* av = fa + (k * 2 + 1) * Q;
+                double ut = 0.0, vt = 0.0, ju[2] = {0.0, 0.0};
+                for (int i = 0; i < Q; ++i) {
+                    ut += au[i];
+                    vt += av[i];
+                    ju[0] += L.e[i][0] * au[i];
+                    ju[1] += L.e[i][1] * au[i];
+                }
+                double am[2] = {-nd->a[0], -nd->a[1]};
+                double r[2] = {(ju[0] - am[0] * ut) / p->tau, (ju[1] - am[1] * ut) / p->tau};
+                double gu[2];
+                for (int c = 0; c < 2; ++c) gu[c] = -(nd->Ku[c][0] * r[0] + nd->Ku[c][1] * r[1]) / (p->d_u * CS2);
+                int c = ctrl_index(p, x, y);
+                if (c >= 0) dJdg[(size_t)n * nctrl + c] = 2.0 * p->alpha * g_at(p, g, n, x, y) + vt;
+                double Phu = p->chi * (st.G[0] * gu[0] + st.G[1] * gu[1]) + p->r_vu * vt;
+                double Phv = p->r_vv * vt;
+                double* Pu = Pa + (k * 2) * Q;
+                double* Pv = Pa + (k * 2 + 1) * Q;
+                Pi_matrix(&L, p, nd->Ku, Pi);
+                feq_lat(&L, ut, am, p->d_u, feq);
+                mrt_collide(&L, Pi, au, feq, Pu);
+                for (int i = 0; i < Q; ++i) Pu[i] += p->tau * wtu[k * 9 + i] * Phu;
+                Pi_matrix(&L, p, nd->Kv, Pi);
+                feq_lat(&L, vt, am, p->d_v, feq);
+                mrt_collide(&L, Pi, av, feq, Pv);
+                double F[2];
+                for (int cc = 0; cc < 2; ++cc)
+                    F[cc] = p->chi * st.Theta_u * (nd->Kv[cc][0] * gu[0] + nd->Kv[cc][1] * gu[1]);
+                for (int i = 0; i < Q; ++i)
+                    Pv[i] += p->tau * wtv[k * 9 + i] * Phv + L.w[i] / CS2 * (L.e[i][0] * F[0] + L.e[i][1] * F[1]);
+            }
+        stream_pull(&L, p, Pa, fa);
+    }
+    /* controlled nodes that are solid carry no gradient */
+    free(fN);
+    free(traj);
+    free(fa);
+    free(Pa);
+    free(nodes);
+    free(wtu);
+    free(wtv);
+    free(u);
+    return 0;
+}

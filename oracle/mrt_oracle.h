@@ -88,6 +88,17 @@ int or_tlm(const or_problem* p, const double* g, const double* dg, const double*
 int or_adjoint(const or_problem* p, const double* g, const double* seed_u,
                const double* seed_v, double* dJdg, double* psi0, double* J);
 
+/* Continuous-adjoint gradient (the algorithm of Sec. 3.2.1 that solves the
+ * adjoint PDE system (FVM-PF-Adj) by the same MRT scheme with time reversed).
+ * For Phi_u = 0, Phi_v = r_vu u + r_vv v + g, J = 1/2 |u(T) - u_tgt|^2 +
+ * alpha int g^2, and s = T - t, the system reads
+ *   du~/ds = div(D_u grad u~) + a.grad u~ + chi grad v . grad u~ + r_vu v~
+ *   dv~/ds = div(D_v grad v~) + a.grad v~ + r_vv v~ - div(chi u grad u~)
+ *   u~(s=0) = u^N - u_tgt,  v~(s=0) = 0,   dJ/dg = 2 alpha g + v~.
+ * Output dJdg [N][cny][cnx] with dJ/dg^n = 2 alpha g^n + v~(t_{n+1}); J (may be
+ * NULL). */
+int or_cadjoint(const or_problem* p, const double* g, double* dJdg, double* J);
+
 #ifdef __cplusplus
 }
 #endif
