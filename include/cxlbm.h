@@ -175,6 +175,21 @@ cx_status cx_step(cx_problem* p, void* g_inout, void* E_work, cx_step_info* info
  * synchronising when given).  Errors: CX_ERR_STATE (no forward). */
 cx_status cx_tlm(cx_problem* p, const void* g, const void* dg, void* du_out, void* dv_out, double* du_sq);
 
+/* Continuous-adjoint gradient (the algorithm of Sec. 3.2.1 that solves the
+ * adjoint PDE system (FVM-PF-Adj) by the MRT scheme with time reversed; an
+ * O(tau, h) approximation of the exact discrete gradient of cx_adjoint).
+ * For Phi_u = 0, Phi_v = r_vu u + r_vv v + g and the terminal cost, with
+ * s = T - t:
+ *   du~/ds = div(D_u grad u~) + a.grad u~ + chi grad v . grad u~ + r_vu v~
+ *   dv~/ds = div(D_v grad v~) + a.grad v~ + r_vv v~ - div(chi u grad u~)
+ *   u~(0) = u^N - u_target, v~(0) = 0;  dJ/dg^n = 2 alpha g^n + v~(t_{n+1})
+ * (summed over a window's steps for windowed controls), solved with
+ * convection -a, first-order sources, the chemotaxis-type source for the
+ * cross term and u, grad v of the forward steps from the tape.  g must be
+ * the control of the preceding cx_forward.  dJdg: device T [W][ctrl].
+ * Errors: CX_ERR_STATE (no forward). */
+cx_status cx_cadjoint(cx_problem* p, const void* g, void* dJdg);
+
 /* One steepest-descent iteration whose step length minimises the quadratic
  * model of J along -E from the sensitivity problem (eqs. LM / LMA, Sec. 2.3):
  * lam* = ||E||^2 / (||du^N(E)||^2 + 2 alpha L ||E||^2), L = N/W steps per

@@ -333,6 +333,68 @@ template <typename T> static cx_status run_step(cx_problem* p, T* g, T* E, cx_st
     return CX_ERR_LINESEARCH;
 }
 
+// Continuous-adjoint gradient (the adjoint PDE solved by the MRT scheme with
+// time reversed): segment by segment in reverse, recompute the forward
+// segment with its tape, then run the continuous-adjoint steps n = n1-1 ... n0
+// on the adjoint's ping-pong lattices.  Needs the forward state of g (wu holds
+// u^N - u_target).
+template <typename T> static cx_status run_cadj(cx_problem* p, const T* g, T* dJdg) {
+    const Layout& Ly = p->lay;
+    const CxConst& C = p->C;
+    double* part = p->at<double>(Ly.off_part);
+    double* e2 = part + 2 * (size_t)Ly.nparts;
+    double* emax = part + 3 * (size_t)Ly.nparts;
+    CX_CUDA(cudaMemsetAsync(e2, 0, sizeof(double) * 2 * Ly.nparts, p->stream));
+    const int aw = (int)(p->La.grid.x * (p->La.block.x / 32));
+    T* phi = p->at<T>(Ly.off_phi);
+    const T* in = nullptr;
+    for (int s = Ly.S - 1; s >= 0; --s) {
+        const int n0 = s * Ly.k, n1 = std::min(Ly.N, n0 + Ly.k);
+        if (s < Ly.S - 1 || !p->tape_last_valid) {
+            if (s >= 1)
+                CX_CUDA(cudaMemcpyAsync(phi, p->ckpt_phi_slot(s), Ly.plane * sizeof(T), cudaMemcpyDeviceToDevice,
+                                        p->stream));
+            const T* fin = reinterpret_cast<const T*>(p->ckpt_slot(s));
+            for (int n = n0; n < n1; ++n) {
+                FwdArgs<T> A{};
+                T* out = p->at<T>((n % 2) ? Ly.off_popB : Ly.off_popA);
+                set_planes(p, A.pin, fin);
+                set_planes(p, A.pout, out);
+                A.phi = phi;
+                A.g = g ? g + (size_t)(n / Ly.win_len) * Ly.nctrl : nullptr;
+                A.tape = reinterpret_cast<T*>(p->tape_slot(n - n0));
+                A.n = n;
+                CX_CUDA(launch_forward<T>(C, p->kc((T*)nullptr), A, p->Lf, p->stream));
+                fin = out;
+            }
+        }
+        for (int n = n1 - 1; n >= n0; --n) {
+            CadjArgs<T> A{};
+            A.first = (n == Ly.N - 1);
+            T* out = p->at<T>((n % 2) ? Ly.off_adjB : Ly.off_adjA);
+            if (in) set_planes(p, A.pin, in);
+            set_planes(p, A.pout, out);
+            A.w0 = p->at<T>(Ly.off_wu);
+            A.tape = reinterpret_cast<const T*>(p->tape_slot(n - n0));
+            A.g = g ? g + (size_t)(n / Ly.win_len) * Ly.nctrl : nullptr;
+            A.dJdg = dJdg + (size_t)(n / Ly.win_len) * Ly.nctrl;
+            A.accum = (n % Ly.win_len) != Ly.win_len - 1;
+            A.norm = (n % Ly.win_len) == 0;
+            A.e2_part = e2;
+            A.emax_part = emax;
+            A.n = n;
+            CX_CUDA(launch_cadj<T>(C, p->kc((T*)nullptr), A, p->La, p->stream));
+            in = out;
+        }
+    }
+    double* scal = p->at<double>(Ly.off_scal);
+    CX_CUDA(launch_finalize(e2, aw, emax, aw, 0.0, scal + 2, p->at<int>(Ly.off_status), ST_UNSTABLE, 1,
+                            p->stream));
+    p->adj_valid = false; // psi^0 of the discrete adjoint is not available
+    if (Ly.S > 1) p->tape_last_valid = false;
+    return CX_OK;
+}
+
 // Tangent-linear (sensitivity) pass along the control direction dg about the
 // base trajectory of control g (the state of the preceding forward): each
 // checkpointed segment is recomputed with its tape, then the tangent steps of
@@ -819,6 +881,13 @@ cx_status cx_tlm(cx_problem* p, const void* g, const void* dg, void* du_out, voi
     if (p->lay.esz == 8)
         return run_tlm<double>(p, (const double*)g, (const double*)dg, (double*)du_out, (double*)dv_out, du_sq);
     return run_tlm<float>(p, (const float*)g, (const float*)dg, (float*)du_out, (float*)dv_out, du_sq);
+}
+
+cx_status cx_cadjoint(cx_problem* p, const void* g, void* dJdg) {
+    if (!p || !dJdg) return CX_ERR_INVALID_ARG;
+    if (!p->fwd_valid) return CX_ERR_STATE;
+    if (p->lay.esz == 8) return run_cadj<double>(p, (const double*)g, (double*)dJdg);
+    return run_cadj<float>(p, (const float*)g, (float*)dJdg);
 }
 
 cx_status cx_lma_step(cx_problem* p, void* g_inout, void* E_work, cx_step_info* info) {

@@ -71,6 +71,22 @@ template <typename T> struct TlmArgs {
     __device__ __forceinline__ T* out(int j) const { return pout[j]; }
 };
 
+template <typename T> struct CadjArgs {
+    const T* pin[18];    // plane j of the continuous-adjoint populations (pulled); unused at the first step
+    T* pout[18];
+    const T* w0;         // [plane] u~ at s = 0 (u^N - u_target), first step only
+    const T* tape;       // [3][plane] forward (u^n, G_x^n, G_y^n)
+    const T* g;          // [cny*cnx] g^n or null
+    T* dJdg;             // [cny*cnx] gradient of control step n (window slot)
+    double* e2_part;
+    double* emax_part;
+    int n;
+    int first;           // n == N-1: populations phi^eq(w0, -a), 0
+    int accum, norm;     // time windows, as the discrete adjoint
+    __device__ __forceinline__ const T* in(int j) const { return pin[j]; }
+    __device__ __forceinline__ T* out(int j) const { return pout[j]; }
+};
+
 template <typename T> struct AdjArgs {
     const T* rin[18];    // plane j of psi^{n+1} ([2][Q][plane]); unused at the terminal step
     const T* wu;         // terminal seeds psi^N_u,i = wu(x), psi^N_v,i = wv(x) (terminal step only)
@@ -109,6 +125,8 @@ cudaError_t launch_final(const CxConst& C, const T* Pin, const T* u_tgt, T* uN, 
 cudaError_t launch_finalize(const double* part_a, int na, const double* part_b, int nb, double scale_b, double* out,
                             int* status, int status_bit, int mode, cudaStream_t s);
 template <typename T> int forward_occupancy(int Q, int threads);
+template <typename T>
+cudaError_t launch_cadj(const CxConst& C, const KConst<T>& K, const CadjArgs<T>& A, const Launch& L, cudaStream_t s);
 template <typename T>
 cudaError_t launch_tlm(const CxConst& C, const KConst<T>& K, const TlmArgs<T>& A, const Launch& L, cudaStream_t s);
 template <typename T> int adjoint_occupancy(int Q, int threads);

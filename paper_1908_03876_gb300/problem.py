@@ -141,6 +141,14 @@ class Problem:
         _lib.check(self.lib.cx_tlm(self.h, _ptr(g), _ptr(dg), _ptr(du), _ptr(dv), ctypes.byref(sq)), "cx_tlm")
         return du, dv, sq.value
 
+    def cadjoint(self, g, out=None):
+        """Continuous-adjoint gradient (time-reversed MRT solve of the adjoint
+        PDE) at the control of the last forward."""
+        g = None if g is None else self._t(g, self.ctrl_shape)
+        out = out if out is not None else torch.empty(self.ctrl_shape, dtype=self.dtype, device=self.device)
+        _lib.check(self.lib.cx_cadjoint(self.h, _ptr(g), _ptr(out)), "cx_cadjoint")
+        return out
+
     def lma_step(self, g, E=None):
         """One steepest-descent iteration with the linearised (sensitivity)
         line search, g updated in place."""

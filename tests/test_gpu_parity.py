@@ -258,6 +258,28 @@ def test_tlm_matches_oracle_fp64(k):
     assert rel(E, Eo) < 1e-12
 
 
+@pytest.mark.parametrize("case", ["aniso", "geometry"])
+def test_continuous_adjoint_matches_oracle_fp64(case):
+    """Continuous-adjoint gradient (time-reversed MRT solve of the adjoint
+    PDE) against the oracle's: rotated tensors with shear convection and time
+    windows, or solid discs with a masked control window; checkpointed."""
+    from paper_1908_03876_gb300.problem import Problem
+
+    if case == "aniso":
+        w = W.aniso(40, 36, 20, seed=7, precision=64, ckpt_every=6)
+        w.windows = 4
+        w.chi = -0.3
+    else:
+        w = W.geometry(48, 40, 16, seed=2, precision=64, ckpt_every=5, win=24, rmin=3, rmax=6)
+    g = w.random_control(13, 0.05)
+    p = Problem(w)
+    p.forward(g)
+    Ec = p.cadjoint(g)
+    _, Eo = oracle.cadjoint(oracle.from_workload(w), g)
+    print(f"continuous adjoint {case}: rel {rel(Ec, Eo):.2e}")
+    assert rel(Ec, Eo) < 1e-12
+
+
 def test_lma_step_matches_oracle_fp64():
     """Steepest descent with the linearised line search: three iterations
     against the oracle's."""
