@@ -294,6 +294,15 @@ def run_warmstart(args, rank, world, local):
 
     size, N, win = args.ws_size, args.ws_steps, 8
     k = max(8, N // 4)
+    if args.profile:  # three U-Net training steps on random 128x128 inputs (profiling case)
+        model = WS.Surrogate()
+        x = torch.randn((16, 6, size, size), device="cuda").to(torch.bfloat16)
+        t = torch.randn((16, 1, size, size), device="cuda")
+        for _ in range(3):
+            model.net.train_step(x, t)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": f"U-Net training steps, batch 16, {size}x{size}"}))
+        return
     t0 = time.perf_counter()
     train = WS.problems(args.ws_train, 10_000, size=size, N=N, windows=win, ckpt_every=k)
     test = WS.problems(args.ws_test, 900_000, size=size, N=N, windows=win, ckpt_every=k)
@@ -374,6 +383,16 @@ def run_cg(args, rank, world, local):
 
     w = W.aniso(256, 256, 200, seed=1, precision=32, ckpt_every=50)
     w.windows = 8
+    if args.profile:  # one forward, sensitivity pass and continuous adjoint (profiling case)
+        p = Problem(w)
+        g = p.zeros_control()
+        p.forward(g)
+        p.tlm(g, torch.ones_like(g))
+        p.forward(g)
+        p.cadjoint(g)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": "aniso 256x256, 200 steps: forward, sensitivity, continuous adjoint"}))
+        return
 
     def run(method, n_iter, target=None):
         p = Problem(w)
