@@ -94,15 +94,31 @@ class Clocks:
 
 def _traffic(kernel):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    from the kernel sources as they are now; else None."""
+    from the kernel's sources as they are now; else None."""
     try:
         from paper_1908_03876_gb300.kernel_hash import kernel_source_hash
 
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
             tr = json.load(fh)
-        if tr.get("kernel_source_hash") != kernel_source_hash() or kernel not in tr:
+        ent = tr.get(kernel)
+        if not ent or ent.get("sources_hash") != kernel_source_hash(kernel):
             return None
-        return tr[kernel]["dram_bytes_per_launch"]
+        return ent["dram_bytes_per_launch"]
+    except Exception:
+        return None
+
+
+def _batch_traffic(nodes):
+    """DRAM bytes of one batched forward launch over `nodes` nodes, from the
+    per-node figure of the committed k_batch capture (its sources unchanged)."""
+    try:
+        from paper_1908_03876_gb300.kernel_hash import kernel_source_hash
+
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            ent = json.load(fh).get("k_batch")
+        if not ent or ent.get("sources_hash") != kernel_source_hash("k_batch"):
+            return None
+        return ent["forward_dram_bytes_per_node"] * nodes
     except Exception:
         return None
 
@@ -254,7 +270,8 @@ def run_batch(args, rank, world, local):
                        "nodes": all_nodes, "tiles": cfg, "autotune_s": t_tune,
                        "l2": "inputs larger than L2"},
             "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                         "traffic": None, "kernel": "k_batch (all lattice launches of the step)",
+                         "traffic": _batch_traffic(all_nodes / world),
+                         "kernel": "k_batch (all lattice launches of the step)",
                          "peak_source": peak_kind},
             "per_problem_grad_rel_err_fp32_vs_oracle": {"sample": "6 problems, 6 steps", "max": max(err),
                                                         "values": err},
