@@ -366,7 +366,9 @@ cx_status cx_nn_conv_backward_data(const uint16_t* dy, const uint16_t* w_bwd, ui
                                    int H, int W, int ks, cudaStream_t stream);
 /* FP32 scratch bytes for cx_nn_conv_backward_weight with `splits` pixel ranges. */
 size_t cx_nn_conv_backward_weight_scratch(int B, int Cin, int Cout, int H, int W, int ks, int splits);
-/* dw[Cout][Cin][ks][ks] (FP32) and db[Cout] (FP32, may be NULL): gradients of sum(dy * conv). */
+/* dw[Cout][Cin][ks][ks] (FP32) and db[Cout] (FP32, may be NULL): gradients of sum(dy * conv);
+ * the pixel tiles are split over `splits` block ranges whose FP32 partials
+ * (in scratch) are summed in a fixed order. */
 cx_status cx_nn_conv_backward_weight(const uint16_t* x, const uint16_t* dy, float* dw, float* db, float* scratch,
                                      int splits, int B, int Cin, int Cout, int H, int W, int ks,
                                      cudaStream_t stream);

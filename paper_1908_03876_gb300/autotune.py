@@ -5,9 +5,11 @@ same nx), the tile width tx and the rows r each thread updates per tile (tile
 = tx x r threads/tx nodes).  The tuner times a short probe batch (the same
 problems with a few time steps) by coordinate descent: start from
 tx = min(threads, nx), r = 2 for every class, then for each class try the
-other admissible widths, then the other row counts, while the rest stay
-fixed, keeping the fastest.  Results are cached in a JSON file keyed by the device, lattice,
-precision and the size-class histogram.
+other row counts, then the other admissible widths, while the rest stay
+fixed, keeping the fastest.  The probe is a gradient evaluation (forward,
+segment recompute and adjoint: the kernels differ in their best tiles), not
+a forward alone.  Results are cached in a JSON file keyed by the device,
+lattice, precision and the size-class histogram.
 """
 from __future__ import annotations
 
@@ -36,13 +38,13 @@ def _admissible(threads, nx):
     return [t for t in WIDTHS if t <= threads and threads % t == 0 and threads // t <= 8 and t <= max(32, 2 * nx)]
 
 
-def _time_forward(b: Batch, reps=3):
-    b.forward()
+def _time_gradient(b: Batch, reps=2):
+    b.gradient()
     b.stream.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(b.stream)
     for _ in range(reps):
-        b.forward()
+        b.gradient()
     e1.record(b.stream)
     e1.synchronize()
     return e0.elapsed_time(e1) / reps
@@ -59,7 +61,7 @@ def autotune(workloads, probe_steps=12, threads_options=(128, 256), cache_path=N
             got["tile_x"] = {int(k): v for k, v in got["tile_x"].items()}
             got["rows"] = {int(k): v for k, v in got.get("rows", {}).items()}
             return got
-    probe = [replace(w, N=probe_steps, ckpt_every=probe_steps) for w in workloads]
+    probe = [replace(w, N=probe_steps, ckpt_every=max(1, probe_steps // 2)) for w in workloads]
     b = Batch(probe, device=device)
     b.bind([None] * len(probe), None)
     classes = sorted(set(w.nx for w in probe))
@@ -70,18 +72,10 @@ def autotune(workloads, probe_steps=12, threads_options=(128, 256), cache_path=N
 
         def run(ch, rw):
             b.set_tiles(threads, 0, [ch[w.nx] for w in probe], [rw[w.nx] for w in probe])
-            return _time_forward(b)
+            return _time_gradient(b)
 
         t_best = run(choice, rows)
         for nx in classes:
-            for tx in _admissible(threads, nx):
-                if tx == choice[nx]:
-                    continue
-                trial = dict(choice)
-                trial[nx] = tx
-                t = run(trial, rows)
-                if t < t_best:
-                    t_best, choice = t, trial
             for r in ROWS:
                 if r == rows[nx]:
                     continue
@@ -90,6 +84,14 @@ def autotune(workloads, probe_steps=12, threads_options=(128, 256), cache_path=N
                 t = run(choice, trial)
                 if t < t_best:
                     t_best, rows = t, trial
+            for tx in _admissible(threads, nx):
+                if tx == choice[nx]:
+                    continue
+                trial = dict(choice)
+                trial[nx] = tx
+                t = run(trial, rows)
+                if t < t_best:
+                    t_best, choice = t, trial
         if best is None or t_best < best["ms"]:
             best = {"threads": threads, "blocks": 0, "tile_x": dict(choice), "rows": dict(rows), "ms": t_best}
     b.close()

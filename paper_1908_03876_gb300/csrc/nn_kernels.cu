@@ -151,11 +151,13 @@ __global__ void __launch_bounds__(NTHR) k_conv(const bf16* __restrict__ X, const
 
 // Weight gradient: a block owns outputs oc0..oc0+63 x inputs 16c..16c+15 x
 // all taps (N = 16 taps columns, n = j*taps + t) and sums over pixel tiles
-// [z*tps, (z+1)*tps) into partial[z][OC][IC*taps].
+// [z*tps, (z+1)*tps) into partial[z][OC][IC*taps]; the blocks of the first
+// input chunk also sum dY per output channel (the bias gradient) into
+// bpart[z][OC].
 template <int KS>
 __global__ void __launch_bounds__(NTHR) k_wgrad(const bf16* __restrict__ X, const bf16* __restrict__ dY,
-                                                float* __restrict__ partial, int B, int IC, int OC, int H, int W,
-                                                int tps) {
+                                                float* __restrict__ partial, float* __restrict__ bpart, int B,
+                                                int IC, int OC, int H, int W, int tps) {
     constexpr int PW = 8 + KS - 1, RS = PW + (PW & 1), TAPS = KS * KS, OFF = KS / 2;
     constexpr int NT8 = KC * TAPS / 8, NTW = (NT8 + 1) / 2;
     __shared__ __align__(16) bf16 As[CT][64 + 8];
@@ -175,6 +177,7 @@ __global__ void __launch_bounds__(NTHR) k_wgrad(const bf16* __restrict__ X, cons
         for (int j = 0; j < NTW; ++j)
 #pragma unroll
             for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.0f;
+    float bsum = 0.0f; // thread o < 64 of the first input chunk: sum of dY over this block's pixels
     for (int tile = t_beg; tile < t_end; ++tile) {
         const int b = tile / (tiles_x * tiles_y), bt = tile - b * tiles_x * tiles_y;
         const int y0 = (bt / tiles_x) * 8, x0 = (bt % tiles_x) * 8;
@@ -194,6 +197,8 @@ __global__ void __launch_bounds__(NTHR) k_wgrad(const bf16* __restrict__ X, cons
             if (px == PW - 1) P1[j][py][px] = zero;
         }
         __syncthreads();
+        if (c == 0 && tid < CT)
+            for (int p = 0; p < 64; ++p) bsum += __bfloat162float(As[tid][(p + tid) & 63]);
 #pragma unroll
         for (int s = 0; s < 4; ++s) { // k16 slab: pixel rows 2s, 2s+1 of the tile
             uint32_t a[2][4];
@@ -226,6 +231,7 @@ __global__ void __launch_bounds__(NTHR) k_wgrad(const bf16* __restrict__ X, cons
         __syncthreads();
     }
     const size_t NC = (size_t)IC * TAPS;
+    if (c == 0 && tid < CT && oc0 + tid < OC) bpart[(size_t)blockIdx.z * OC + oc0 + tid] = bsum;
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
@@ -251,23 +257,6 @@ __global__ void k_reduce_splits(const float* partial, float* dW, int splits, siz
         dW[i] = s;
     }
 }
-__global__ void k_bias_grad(const bf16* dY, float* db, int B, int C, int hw) {
-    __shared__ float sh[256];
-    const int c = blockIdx.x;
-    float s = 0.0f;
-    for (int i = threadIdx.x; i < B * hw; i += 256) {
-        const int b = i / hw, p = i - b * hw;
-        s += __bfloat162float(dY[((size_t)b * C + c) * hw + p]);
-    }
-    sh[threadIdx.x] = s;
-    __syncthreads();
-    for (int h = 128; h > 0; h >>= 1) {
-        if (threadIdx.x < h) sh[threadIdx.x] += sh[threadIdx.x + h];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) db[c] = sh[0];
-}
-
 __global__ void k_relu_bwd(const bf16* y, const bf16* dy, bf16* dz, size_t n) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         dz[i] = __bfloat162float(y[i]) > 0.0f ? dy[i] : __float2bfloat16(0.0f);
@@ -457,7 +446,7 @@ cx_status cx_nn_conv_backward_data(const uint16_t* dy, const uint16_t* w_bwd, ui
 }
 
 size_t cx_nn_conv_backward_weight_scratch(int B, int Cin, int Cout, int H, int W, int ks, int splits) {
-    return (size_t)splits * Cout * Cin * ks * ks * sizeof(float);
+    return (size_t)splits * Cout * ((size_t)Cin * ks * ks + 1) * sizeof(float);
 }
 
 cx_status cx_nn_conv_backward_weight(const uint16_t* x, const uint16_t* dy, float* dw, float* db, float* scratch,
@@ -470,14 +459,15 @@ cx_status cx_nn_conv_backward_weight(const uint16_t* x, const uint16_t* dy, floa
     dim3 grid((Cin + KC - 1) / KC, (Cout + CT - 1) / CT, splits);
     const bf16* X = reinterpret_cast<const bf16*>(x);
     const bf16* dY = reinterpret_cast<const bf16*>(dy);
-    if (ks == 3) k_wgrad<3><<<grid, NTHR, 0, stream>>>(X, dY, scratch, B, Cin, Cout, H, W, tps);
-    else k_wgrad<1><<<grid, NTHR, 0, stream>>>(X, dY, scratch, B, Cin, Cout, H, W, tps);
-    NN_CHECK();
     const size_t mn = (size_t)Cout * Cin * ks * ks;
+    float* bpart = scratch + (size_t)splits * mn;
+    if (ks == 3) k_wgrad<3><<<grid, NTHR, 0, stream>>>(X, dY, scratch, bpart, B, Cin, Cout, H, W, tps);
+    else k_wgrad<1><<<grid, NTHR, 0, stream>>>(X, dY, scratch, bpart, B, Cin, Cout, H, W, tps);
+    NN_CHECK();
     k_reduce_splits<<<grid_for(mn), 256, 0, stream>>>(scratch, dw, splits, mn);
     NN_CHECK();
     if (db) {
-        k_bias_grad<<<Cout, 256, 0, stream>>>(dY, db, B, Cout, H * W);
+        k_reduce_splits<<<grid_for(Cout), 256, 0, stream>>>(bpart, db, splits, Cout);
         NN_CHECK();
     }
     return CX_OK;

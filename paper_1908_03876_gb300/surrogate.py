@@ -102,10 +102,10 @@ class UNet:
 
     def _conv_back(self, c: Conv, x, dy, need_dx=True):
         B, _, H, W = x.shape
-        # split the pixel tiles so that about 8 blocks per SM run
+        # split the pixel tiles so that about 2 blocks per SM run (fewer partials to reduce)
         ntiles = B * ((H + 7) // 8) * ((W + 7) // 8)
         base = ((c.cin + 15) // 16) * ((c.cout + 63) // 64)
-        splits = int(max(1, min(ntiles, -(-1216 // base))))
+        splits = int(max(1, min(ntiles, -(-304 // base))))
         nbytes = self.lib.cx_nn_conv_backward_weight_scratch(B, c.cin, c.cout, H, W, c.ks, splits)
         scratch = torch.empty(max(1, nbytes // 4), dtype=torch.float32, device=self.device)
         _lib.check(self.lib.cx_nn_conv_backward_weight(_p(x), _p(dy), _p(c.gw), _p(c.gb), _p(scratch), splits, B,
