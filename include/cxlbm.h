@@ -284,7 +284,7 @@ cx_status cx_batch_bind(cx_batch* b, const void* const* g, void* const* dJdg);
 /* Tile shapes: `threads` per block (128 or 256), `blocks` persistent blocks
  * (0: every SM at full residency), tile_x[i] = tile width of problem i (a
  * power of two dividing threads, >= 32, threads / tile_x[i] <= 8; NULL:
- * threads), rows[i] = nodes each thread updates per tile, 1..16 (NULL: 2).
+ * threads), rows[i] = nodes each thread updates per tile, 1..32 (NULL: 2).
  * The tile height is (threads / tile_x[i]) rows[i].  Synchronous. */
 cx_status cx_batch_set_tiles(cx_batch* b, int threads, int blocks, const int* tile_x, const int* rows);
 /* Forward of every problem; J_dev (device double [count], may be NULL). */

@@ -3,10 +3,10 @@
 Tunables: threads per block (128, 256) and, per size class (problems with the
 same nx), the tile width tx and the rows r each thread updates per tile (tile
 = tx x r threads/tx nodes).  The tuner times a short probe batch (the same
-problems with a few time steps) by coordinate descent: start from
-tx = min(threads, nx), r = 2 for every class, then for each class try the
-other row counts, then the other admissible widths, while the rest stay
-fixed, keeping the fastest.  The probe is a gradient evaluation (forward,
+problems with a few time steps): first the best of a few uniform shapes (the
+same width and rows for every class), then coordinate descent from it: for
+each class try the other row counts, then the other admissible widths, while
+the rest stay fixed, keeping the fastest.  The probe is a gradient evaluation (forward,
 segment recompute and adjoint: the kernels differ in their best tiles), not
 a forward alone.  Results are cached in a JSON file keyed by the device,
 lattice, precision and the size-class histogram.
@@ -22,7 +22,8 @@ import torch
 from .batch import Batch
 
 WIDTHS = (32, 64, 128, 256)
-ROWS = (1, 2, 4, 8)
+ROWS = (4, 8, 16, 32)
+UNIFORM = ((32, 8), (64, 8), (64, 16), (128, 16), (32, 16))
 
 
 def _signature(workloads, device):
@@ -50,7 +51,7 @@ def _time_gradient(b: Batch, reps=2):
     return e0.elapsed_time(e1) / reps
 
 
-def autotune(workloads, probe_steps=12, threads_options=(128, 256), cache_path=None, device="cuda"):
+def autotune(workloads, probe_steps=24, threads_options=(128, 256), cache_path=None, device="cuda"):
     """Returns {"threads": T, "blocks": 0, "tile_x": {nx: tx}, "rows": {nx: r}, "ms": best probe time}."""
     sig = _signature(workloads, device)
     if cache_path and os.path.exists(cache_path):
@@ -67,14 +68,19 @@ def autotune(workloads, probe_steps=12, threads_options=(128, 256), cache_path=N
     classes = sorted(set(w.nx for w in probe))
     best = None
     for threads in threads_options:
-        choice = {nx: min(threads, max(t for t in _admissible(threads, nx))) for nx in classes}
-        rows = {nx: 2 for nx in classes}
-
         def run(ch, rw):
             b.set_tiles(threads, 0, [ch[w.nx] for w in probe], [rw[w.nx] for w in probe])
             return _time_gradient(b)
 
-        t_best = run(choice, rows)
+        t_best, choice, rows = None, None, None
+        for tx, r in UNIFORM:
+            ch = {nx: min(tx, max(_admissible(threads, nx))) for nx in classes}
+            if any(c not in _admissible(threads, nx) for nx, c in ch.items()):
+                continue
+            rw = {nx: r for nx in classes}
+            t = run(ch, rw)
+            if t_best is None or t < t_best:
+                t_best, choice, rows = t, ch, rw
         for nx in classes:
             for r in ROWS:
                 if r == rows[nx]:

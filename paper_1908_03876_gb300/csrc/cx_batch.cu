@@ -835,7 +835,7 @@ cx_status cx_batch_set_tiles(cx_batch* b, int threads, int blocks, const int* ti
         const int t = tile_x ? tile_x[i] : std::min(threads, 256);
         if (t < 32 || t > threads || threads % t != 0 || threads / t > 8 || (t & (t - 1))) return CX_ERR_INVALID_ARG;
         const int r = rows ? rows[i] : 2;
-        if (r < 1 || r > 16) return CX_ERR_INVALID_ARG;
+        if (r < 1 || r > 32) return CX_ERR_INVALID_ARG;
         tx[i] = t;
         rr[i] = r;
     }
