@@ -356,6 +356,16 @@ cx_status cx_nn_conv_forward(const uint16_t* x, const uint16_t* w_fwd, const flo
 /* As cx_nn_conv_forward without activation, writing FP32 y (the network's output layer). */
 cx_status cx_nn_conv_forward_f32(const uint16_t* x, const uint16_t* w_fwd, const float* bias, float* y, int B,
                                  int Cin, int Cout, int H, int W, int ks, cudaStream_t stream);
+/* Tile of output channels of cx_nn_conv_forward_tc for Cout (the largest of
+ * 256, 128, 64, 32 dividing it), 0 when Cout is not a multiple of 32. */
+int cx_nn_conv_tc_tile(int Cout);
+/* cx_nn_conv_forward on the 5th-generation tensor cores (tcgen05 MMA with the
+ * accumulator in tensor memory; BF16 products, FP32 accumulation), for Cout a
+ * multiple of 32.  status (device int, may be NULL): bit 0 set if a bounded
+ * wait for the tensor cores timed out (the outputs of that tile are then not
+ * written).  Errors: CX_ERR_INVALID_ARG (shape or Cout), CX_ERR_CUDA. */
+cx_status cx_nn_conv_forward_tc(const uint16_t* x, const uint16_t* w_fwd, const float* bias, uint16_t* y, int B,
+                                int Cin, int Cout, int H, int W, int ks, int relu, int* status, cudaStream_t stream);
 /* Separable periodic low-pass of BC planes [H][W] (FP32): out = taps (*) along
  * x then y, taps[0..2 radius] a device FP32 array (radius <= 64); tmp is
  * scratch of the same size as in. */

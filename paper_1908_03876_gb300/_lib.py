@@ -30,7 +30,7 @@ EXPORTS = [
     "cx_nn_conv_forward", "cx_nn_conv_backward_data", "cx_nn_conv_backward_weight_scratch",
     "cx_nn_conv_backward_weight", "cx_nn_relu_backward", "cx_nn_add", "cx_nn_pool2", "cx_nn_up2", "cx_nn_mse",
     "cx_nn_adam", "cx_nn_cast_bf16", "cx_nn_conv_forward_f32", "cx_nn_smooth", "cx_nn_packed_weights",
-    "cx_nn_pack_weights",
+    "cx_nn_pack_weights", "cx_nn_conv_tc_tile", "cx_nn_conv_forward_tc",
 ]
 STATIC_SCRATCH_BYTES = 32 << 20  # CX_STATIC_SCRATCH_BYTES of include/cxlbm.h
 
@@ -132,6 +132,7 @@ def load():
         "cx_nn_smooth": [vp, vp, vp, cint, cint, cint, vp, cint, vp],
         "cx_nn_conv_backward_data": [vp, vp, vp, cint, cint, cint, cint, cint, cint, vp],
         "cx_nn_pack_weights": [vp, cint, cint, cint, vp, vp, vp],
+        "cx_nn_conv_forward_tc": [vp, vp, vp, vp, cint, cint, cint, cint, cint, cint, cint, vp, vp],
         "cx_nn_conv_backward_weight": [vp, vp, vp, vp, vp, cint, cint, cint, cint, cint, cint, cint, vp],
         "cx_nn_relu_backward": [vp, vp, vp, ctypes.c_size_t, vp],
         "cx_nn_add": [vp, vp, vp, ctypes.c_size_t, vp],
@@ -149,6 +150,8 @@ def load():
     lib.cx_nn_conv_backward_weight_scratch.argtypes = [cint] * 7
     lib.cx_nn_conv_backward_weight_scratch.restype = ctypes.c_size_t
     lib.cx_nn_packed_weights.argtypes = [cint] * 4
+    lib.cx_nn_conv_tc_tile.argtypes = [cint]
+    lib.cx_nn_conv_tc_tile.restype = cint
     lib.cx_nn_packed_weights.restype = ctypes.c_size_t
     lib.cx_status_string.argtypes = [cint]
     lib.cx_status_string.restype = ctypes.c_char_p

@@ -1,0 +1,272 @@
+// nn_tc.cu -- 3x3 / 1x1 convolution forward on the 5th-generation tensor cores
+// (tcgen05.mma, FP32 accumulators in tensor memory), for the warm-start
+// surrogate's layers with 32..256 output channels.
+//
+// A CTA owns a 16 x 8 pixel tile of one image (M = 128 rows of the MMA) and N
+// output channels (N = 32, 64, 128 or 256), and loops over the input channels
+// in chunks of 16 (K = 16 per MMA).  Per chunk all threads stage
+//   A: the (16+2) x (8+2) input patch, channel-interleaved as
+//      [ci/8][patch position][8 ci] -- every 8 consecutive pixels of a patch
+//      row form one 8 x 16-byte core matrix, so the operand of tap (dy, dx) is
+//      the same buffer at byte offset (dy * 10 + dx) * 16 with core-matrix
+//      strides 16 * 10 (next image row, M direction) and 16 * 180 (next 8
+//      channels, K direction);
+//   B: the chunk's weights of every tap as [tap][ci/8][oc][8 ci], core-matrix
+//      strides 128 (next 8 channels out, N direction) and 16 * N (K direction);
+// then one thread issues the 9 (or 1) MMAs of the chunk and commits them to
+// the chunk buffer's mbarrier.  Two buffers: staging chunk c+1 overlaps the
+// MMAs of chunk c.  The epilogue reads the accumulator lanes of each warp
+// (pixels 32 w .. 32 w + 31) with tcgen05.ld and applies bias and ReLU.
+// Every mbarrier wait is bounded; on timeout the kernel sets *status, skips
+// its stores, waits (bounded) for its own MMAs and frees its tensor memory.
+#include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "../../include/cxlbm.h"
+
+namespace nntc {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr int NTHR = 128;
+constexpr int TM = 128;        // MMA M: pixels per tile
+constexpr int TH = 16, TW = 8; // tile rows x columns
+constexpr unsigned WAIT_LIMIT = 1u << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared memory matrix descriptor, no swizzle, K-major core matrices of 8 rows x 16 bytes
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// instruction descriptor: kind::f16, BF16 x BF16 -> FP32, both operands K-major, M = 128
+__host__ __device__ constexpr uint32_t idesc_bf16(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait for the phase of the given parity; false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+    for (unsigned it = 0; it < WAIT_LIMIT; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void proxy_fence() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(dst)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+// 32 consecutive accumulator columns of this warp's 32 lanes
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+template <int KS> struct TcGeom {
+    static constexpr int PH = TH + KS - 1, PW = TW + KS - 1, PP = PH * PW, TAPS = KS * KS;
+    static constexpr int A_BYTES = 2 * PP * 16;
+    __host__ __device__ static constexpr int b_bytes(int n) { return TAPS * 2 * n * 16; }
+    __host__ __device__ static constexpr int buf_bytes(int n) { return ((A_BYTES + b_bytes(n)) + 127) / 128 * 128; }
+    __host__ __device__ static constexpr int smem_bytes(int n) { return 2 * buf_bytes(n) + 128; }
+};
+
+// Wp: the forward pack [ceil(IC/16)][taps][OC][16] (cx_nn_pack_weights)
+template <int KS>
+__global__ void __launch_bounds__(NTHR) k_conv_tc(const bf16* __restrict__ X, const bf16* __restrict__ Wp,
+                                                  const float* __restrict__ bias, bf16* __restrict__ Y, int B,
+                                                  int IC, int OC, int H, int W, int N, int relu, int* status) {
+    using Gm = TcGeom<KS>;
+    constexpr int PW = Gm::PW, PP = Gm::PP, TAPS = Gm::TAPS, OFF = KS / 2;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int bufb = Gm::buf_bytes(N);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 2 * bufb);
+    uint32_t* taddr_sh = reinterpret_cast<uint32_t*>(mbar + 2);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tiles_x = (W + TW - 1) / TW, tiles_y = (H + TH - 1) / TH;
+    int bt = blockIdx.x;
+    const int b = bt / (tiles_x * tiles_y);
+    bt -= b * tiles_x * tiles_y;
+    const int y0 = (bt / tiles_x) * TH, x0 = (bt % tiles_x) * TW;
+    const int oc0 = blockIdx.y * N;
+    const size_t hw = (size_t)H * W;
+    const bf16 zero = __float2bfloat16(0.0f);
+
+    if (warp == 0) tmem_alloc(taddr_sh, (uint32_t)N);
+    if (tid == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); // visible to the async proxy
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t taddr = *taddr_sh;
+    const uint32_t idesc = idesc_bf16(N);
+    const int nchunks = (IC + 15) / 16;
+    bool ok = true;
+    for (int c = 0; c < nchunks && ok; ++c) {
+        const int buf = c & 1;
+        unsigned char* A = smem + buf * bufb;
+        unsigned char* Bm = A + Gm::A_BYTES;
+        if (c >= 2) {
+            ok = mbar_wait(&mbar[buf], (unsigned)(((c - 2) >> 1) & 1)); // MMAs of chunk c-2 done
+            ok = __syncthreads_and(ok) != 0; // the same decision in every thread
+            if (!ok) break;
+        }
+        // A: [ci/8][pos][8]
+        for (int e = tid; e < 16 * PP; e += NTHR) {
+            const int j = e / PP, r = e - j * PP;
+            const int py = r / PW, px = r - py * PW;
+            const int ic = c * 16 + j, y = y0 - OFF + py, x = x0 - OFF + px;
+            bf16 v = zero;
+            if (ic < IC && y >= 0 && y < H && x >= 0 && x < W) v = X[((size_t)b * IC + ic) * hw + (size_t)y * W + x];
+            reinterpret_cast<bf16*>(A)[((j >> 3) * PP + r) * 8 + (j & 7)] = v;
+        }
+        // B: [tap][ci/8][oc][8]
+        for (int e = tid; e < TAPS * N * 2; e += NTHR) {
+            const int t = e / (N * 2), rem = e - t * N * 2, o = rem >> 1, h = rem & 1;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (oc0 + o < OC)
+                v = *reinterpret_cast<const uint4*>(Wp + (((size_t)c * TAPS + t) * OC + oc0 + o) * 16 + h * 8);
+            *reinterpret_cast<uint4*>(Bm + ((size_t)(t * 2 + h) * N + o) * 16) = v;
+        }
+        proxy_fence(); // generic-proxy writes visible to the tensor cores
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t a0 = smem_u32(A), b0 = smem_u32(Bm);
+#pragma unroll
+            for (int t = 0; t < TAPS; ++t) {
+                const int dy = t / KS, dx = t - dy * KS;
+                const uint64_t ad = sdesc(a0 + (uint32_t)((dy * PW + dx) * 16), PP * 16, PW * 16);
+                const uint64_t bd = sdesc(b0 + (uint32_t)(t * 2 * N * 16), N * 16, 128);
+                mma_bf16(taddr, ad, bd, idesc, (c > 0 || t > 0) ? 1u : 0u);
+            }
+            mma_commit(&mbar[buf]);
+        }
+    }
+    // the last commit covers every MMA issued before it
+    const int last = nchunks - 1;
+    if (ok) ok = mbar_wait(&mbar[last & 1], (unsigned)((last >> 1) & 1));
+    ok = __syncthreads_and(ok) != 0;
+    tc_fence_after();
+    if (!ok) {
+        if (tid == 0 && status) atomicOr(status, 1);
+        // bounded wait for any MMAs still in flight before the memory is freed
+        if (last >= 1) mbar_wait(&mbar[(last - 1) & 1], (unsigned)(((last - 1) >> 1) & 1));
+        mbar_wait(&mbar[last & 1], (unsigned)((last >> 1) & 1));
+    } else {
+        const int m = warp * 32 + lane;
+        const int y = y0 + m / TW, x = x0 + m % TW;
+        const bool in = y < H && x < W;
+        for (int col = 0; col < N; col += 32) {
+            float v[32];
+            tmem_ld32(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)col, v);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int o = oc0 + col + j;
+                if (!in || o >= OC) continue;
+                float r = v[j] + (bias ? bias[o] : 0.0f);
+                if (relu) r = fmaxf(r, 0.0f);
+                Y[((size_t)b * OC + o) * hw + (size_t)y * W + x] = __float2bfloat16(r);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(taddr, (uint32_t)N);
+}
+
+} // namespace nntc
+
+using namespace nntc;
+
+// Dynamic shared memory is sized so that every operand read the descriptors
+// can address stays inside the allocation.
+static int smem_floor(int bytes) { return bytes < 72 * 1024 ? 72 * 1024 : bytes; }
+
+extern "C" {
+
+int cx_nn_conv_tc_tile(int Cout) {
+    for (int n = 256; n >= 32; n >>= 1)
+        if (Cout % n == 0) return n;
+    return 0;
+}
+
+cx_status cx_nn_conv_forward_tc(const uint16_t* x, const uint16_t* w_fwd, const float* bias, uint16_t* y, int B,
+                                int Cin, int Cout, int H, int W, int ks, int relu, int* status, cudaStream_t stream) {
+    if (!x || !w_fwd || !y || B < 1 || Cin < 1 || H < 1 || W < 1 || (ks != 1 && ks != 3)) return CX_ERR_INVALID_ARG;
+    const int N = cx_nn_conv_tc_tile(Cout);
+    if (N == 0) return CX_ERR_INVALID_ARG;
+    const long long tiles = (long long)B * ((H + TH - 1) / TH) * ((W + TW - 1) / TW);
+    if (tiles > 0x7fffffffLL) return CX_ERR_INVALID_ARG;
+    dim3 grid((unsigned)tiles, Cout / N);
+    const bf16* X = reinterpret_cast<const bf16*>(x);
+    const bf16* Wp = reinterpret_cast<const bf16*>(w_fwd);
+    bf16* Y = reinterpret_cast<bf16*>(y);
+    if (ks == 3) {
+        const int smem = smem_floor(TcGeom<3>::smem_bytes(N));
+        if (cudaFuncSetAttribute(k_conv_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess)
+            return CX_ERR_CUDA;
+        k_conv_tc<3><<<grid, NTHR, smem, stream>>>(X, Wp, bias, Y, B, Cin, Cout, H, W, N, relu, status);
+    } else {
+        const int smem = smem_floor(TcGeom<1>::smem_bytes(N));
+        if (cudaFuncSetAttribute(k_conv_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess)
+            return CX_ERR_CUDA;
+        k_conv_tc<1><<<grid, NTHR, smem, stream>>>(X, Wp, bias, Y, B, Cin, Cout, H, W, N, relu, status);
+    }
+    return cudaGetLastError() == cudaSuccess ? CX_OK : CX_ERR_CUDA;
+}
+
+} // extern "C"

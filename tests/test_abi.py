@@ -24,7 +24,7 @@ def lib():
 def _header_symbols():
     with open(os.path.join(ROOT, "include", "cxlbm.h")) as fh:
         text = fh.read()
-    return sorted(set(re.findall(r"^(?:cx_status|const char\*|size_t)\s+(cx_\w+)\s*\(", text, flags=re.M)))
+    return sorted(set(re.findall(r"^(?:cx_status|const char\*|size_t|int)\s+(cx_\w+)\s*\(", text, flags=re.M)))
 
 
 def test_exports_every_declared_symbol(lib):

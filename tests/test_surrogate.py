@@ -267,3 +267,31 @@ def test_conv_forward_f32_and_smooth():
     ex = sum(taps[i] * np.roll(g, -int(d[i]), axis=2) for i in range(len(d)))
     ex = sum(taps[i] * np.roll(ex, -int(d[i]), axis=1) for i in range(len(d)))
     assert np.abs(out.cpu().numpy() - ex).max() < 1e-5
+
+
+@pytest.mark.parametrize("B,Cin,Cout,H,W,ks,relu", [
+    (2, 40, 64, 20, 13, 3, True),     # ragged input chunk and pixel tiles
+    (3, 32, 32, 16, 16, 1, False),    # 1x1
+    (1, 5, 32, 33, 9, 3, True),       # fewer inputs than one chunk
+])
+def test_conv_forward_tcgen05(B, Cin, Cout, H, W, ks, relu):
+    """Convolution on the tcgen05 tensor cores (accumulator in tensor memory)
+    against the FP64 reference and the mma.sync kernel."""
+    lib, check = _lib()
+    x = bf16_data((B, Cin, H, W), 31)
+    w = bf16_data((Cout, Cin, ks, ks), 32, scale=1.0 / np.sqrt(Cin * ks * ks))
+    b = torch.linspace(-0.3, 0.3, Cout, dtype=torch.float32)
+    xd, wd, bd = x.cuda(), w.cuda(), b.cuda()
+    wf, _ = packed(lib, check, wd, Cout, Cin, ks)
+    y = torch.empty((B, Cout, H, W), dtype=BF, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    check(lib.cx_nn_conv_forward_tc(_p(xd), _p(wf), _p(bd), _p(y), B, Cin, Cout, H, W, ks, int(relu), _p(st), _s()),
+          "conv tc")
+    y2 = torch.empty_like(y)
+    check(lib.cx_nn_conv_forward(_p(xd), _p(wf), _p(bd), _p(y2), B, Cin, Cout, H, W, ks, int(relu), _s()), "conv")
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    check_bf16(y, R.conv(x.double(), w.double(), b.double(), relu=relu), f"conv tcgen05 {Cin}->{Cout} k{ks}")
+    d = (y.double() - y2.double()).abs().max().item()
+    print(f"tcgen05 vs mma.sync max |diff| {d:.3e}")
+    assert d <= 2.0 ** -7 * y2.double().abs().max().item()
