@@ -232,10 +232,6 @@ __global__ void __launch_bounds__(NTHR) k_conv_tc(const bf16* __restrict__ X, co
 
 using namespace nntc;
 
-// Dynamic shared memory is sized so that every operand read the descriptors
-// can address stays inside the allocation.
-static int smem_floor(int bytes) { return bytes < 72 * 1024 ? 72 * 1024 : bytes; }
-
 extern "C" {
 
 int cx_nn_conv_tc_tile(int Cout) {
@@ -256,12 +252,12 @@ cx_status cx_nn_conv_forward_tc(const uint16_t* x, const uint16_t* w_fwd, const 
     const bf16* Wp = reinterpret_cast<const bf16*>(w_fwd);
     bf16* Y = reinterpret_cast<bf16*>(y);
     if (ks == 3) {
-        const int smem = smem_floor(TcGeom<3>::smem_bytes(N));
+        const int smem = TcGeom<3>::smem_bytes(N);
         if (cudaFuncSetAttribute(k_conv_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess)
             return CX_ERR_CUDA;
         k_conv_tc<3><<<grid, NTHR, smem, stream>>>(X, Wp, bias, Y, B, Cin, Cout, H, W, N, relu, status);
     } else {
-        const int smem = smem_floor(TcGeom<1>::smem_bytes(N));
+        const int smem = TcGeom<1>::smem_bytes(N);
         if (cudaFuncSetAttribute(k_conv_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess)
             return CX_ERR_CUDA;
         k_conv_tc<1><<<grid, NTHR, smem, stream>>>(X, Wp, bias, Y, B, Cin, Cout, H, W, N, relu, status);

@@ -273,6 +273,10 @@ def test_conv_forward_f32_and_smooth():
     (2, 40, 64, 20, 13, 3, True),     # ragged input chunk and pixel tiles
     (3, 32, 32, 16, 16, 1, False),    # 1x1
     (1, 5, 32, 33, 9, 3, True),       # fewer inputs than one chunk
+    (2, 64, 128, 16, 24, 3, True),    # 128-channel tile
+    (1, 128, 256, 8, 8, 3, False),    # 256-channel tile, image smaller than the pixel tile
+    (2, 48, 96, 12, 12, 3, True),     # 96 channels: three 32-channel tiles
+    (2, 256, 128, 16, 16, 1, False),  # 1x1 with 16 input chunks
 ])
 def test_conv_forward_tcgen05(B, Cin, Cout, H, W, ks, relu):
     """Convolution on the tcgen05 tensor cores (accumulator in tensor memory)
@@ -287,8 +291,12 @@ def test_conv_forward_tcgen05(B, Cin, Cout, H, W, ks, relu):
     st = torch.zeros(1, dtype=torch.int32, device="cuda")
     check(lib.cx_nn_conv_forward_tc(_p(xd), _p(wf), _p(bd), _p(y), B, Cin, Cout, H, W, ks, int(relu), _p(st), _s()),
           "conv tc")
-    y2 = torch.empty_like(y)
-    check(lib.cx_nn_conv_forward(_p(xd), _p(wf), _p(bd), _p(y2), B, Cin, Cout, H, W, ks, int(relu), _s()), "conv")
+    # the mma.sync kernel (through the FP32-output entry, no tensor-core dispatch)
+    y2 = torch.empty((B, Cout, H, W), dtype=torch.float32, device="cuda")
+    check(lib.cx_nn_conv_forward_f32(_p(xd), _p(wf), _p(bd), _p(y2), B, Cin, Cout, H, W, ks, _s()), "conv f32")
+    if relu:
+        y2 = torch.relu(y2)
+    y2 = y2.to(BF)
     torch.cuda.synchronize()
     assert int(st.item()) == 0
     check_bf16(y, R.conv(x.double(), w.double(), b.double(), relu=relu), f"conv tcgen05 {Cin}->{Cout} k{ks}")
