@@ -39,8 +39,11 @@ __device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], 
 
 __device__ __forceinline__ uint32_t ld32(const bf16* p) { return *reinterpret_cast<const uint32_t*>(p); }
 
-// Weight packs: forward Wf[c][t][o][j] = W[o][16c+j][t] (out = Cout, in = Cin);
-// data gradient Wb[c][t][o][j] = W[16c+j][o][taps-1-t] (out = Cin, in = Cout).
+// Weight packs, [c][t][h][o][8] with input channel 16c + 8h + jj:
+// forward Wf = W[o][in][t] (out = Cout, in = Cin); data gradient
+// Wb = W[in][o][taps-1-t] (out = Cin, in = Cout).  One chunk c is a
+// contiguous [taps][2][out][8] block: the tensor-core kernel copies it to
+// shared memory in one bulk copy.
 __global__ void k_pack(const bf16* __restrict__ W, bf16* __restrict__ Wf, bf16* __restrict__ Wb, int Cout, int Cin,
                        int taps) {
     const size_t nf = (size_t)((Cin + KC - 1) / KC) * taps * Cout * KC;
@@ -50,12 +53,14 @@ __global__ void k_pack(const bf16* __restrict__ W, bf16* __restrict__ Wf, bf16* 
         const bool fwd = i < nf;
         const size_t e = fwd ? i : i - nf;
         const int OC = fwd ? Cout : Cin, IC = fwd ? Cin : Cout;
-        const int j = (int)(e % KC);
-        const size_t r = e / KC;
+        const int jj = (int)(e % 8);
+        const size_t r = e / 8;
         const int o = (int)(r % OC);
         const size_t r2 = r / OC;
-        const int t = (int)(r2 % taps), c = (int)(r2 / taps);
-        const int in = c * KC + j;
+        const int h = (int)(r2 % 2);
+        const size_t r3 = r2 / 2;
+        const int t = (int)(r3 % taps), c = (int)(r3 / taps);
+        const int in = c * KC + h * 8 + jj;
         bf16 v = zero;
         if (in < IC) v = fwd ? W[((size_t)o * Cin + in) * taps + t] : W[((size_t)in * Cin + o) * taps + (taps - 1 - t)];
         (fwd ? Wf : Wb)[e] = v;
@@ -103,7 +108,7 @@ __global__ void __launch_bounds__(NTHR) k_conv(const bf16* __restrict__ X, const
             const int t = e / (CT * 2), rem = e - t * CT * 2, o = rem >> 1, h = rem & 1;
             uint4 v = make_uint4(0, 0, 0, 0);
             if (oc0 + o < OC)
-                v = *reinterpret_cast<const uint4*>(Wp + (((size_t)c * TAPS + t) * OC + oc0 + o) * KC + h * 8);
+                v = *reinterpret_cast<const uint4*>(Wp + ((((size_t)c * TAPS + t) * 2 + h) * OC + oc0 + o) * 8);
             *reinterpret_cast<uint4*>(&Ws[t][o][h * 8]) = v;
         }
         __syncthreads();

@@ -12,9 +12,12 @@
 //      strides 16 * 10 (next image row, M direction) and 16 * 180 (next 8
 //      channels, K direction);
 //   B: the chunk's weights of every tap as [tap][ci/8][oc][8 ci], core-matrix
-//      strides 128 (next 8 channels out, N direction) and 16 * N (K direction);
+//      strides 128 (next 8 channels out, N direction) and 16 * N (K direction)
+//      -- the layout of the weight pack, so when the tile covers every output
+//      channel the chunk arrives in one bulk asynchronous copy completed on
+//      the buffer's load mbarrier;
 // then one thread issues the 9 (or 1) MMAs of the chunk and commits them to
-// the chunk buffer's mbarrier.  Two buffers: staging chunk c+1 overlaps the
+// the chunk buffer's MMA mbarrier.  Two buffers: staging chunk c+1 overlaps the
 // MMAs of chunk c.  The epilogue reads the accumulator lanes of each warp
 // (pixels 32 w .. 32 w + 31) with tcgen05.ld and applies bias and ReLU.
 // Every mbarrier wait is bounded; on timeout the kernel sets *status, skips
@@ -91,6 +94,20 @@ __device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_
         : "memory");
 }
 
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// one bulk global -> shared copy (16-byte aligned, size a multiple of 16), completion on bar
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
                      smem_u32(bar))
@@ -118,7 +135,7 @@ template <int KS> struct TcGeom {
     static constexpr int A_BYTES = 2 * PP * 16;
     __host__ __device__ static constexpr int b_bytes(int n) { return TAPS * 2 * n * 16; }
     __host__ __device__ static constexpr int buf_bytes(int n) { return ((A_BYTES + b_bytes(n)) + 127) / 128 * 128; }
-    __host__ __device__ static constexpr int smem_bytes(int n) { return 2 * buf_bytes(n) + 128; }
+    __host__ __device__ static constexpr int smem_bytes(int n) { return 2 * buf_bytes(n) + 128; } // + 4 barriers
 };
 
 // Wp: the forward pack [ceil(IC/16)][taps][OC][16] (cx_nn_pack_weights)
@@ -130,8 +147,12 @@ __global__ void __launch_bounds__(NTHR) k_conv_tc(const bf16* __restrict__ X, co
     constexpr int PW = Gm::PW, PP = Gm::PP, TAPS = Gm::TAPS, OFF = KS / 2;
     extern __shared__ __align__(1024) unsigned char smem[];
     const int bufb = Gm::buf_bytes(N);
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 2 * bufb);
-    uint32_t* taddr_sh = reinterpret_cast<uint32_t*>(mbar + 2);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 2 * bufb); // MMAs of a buffer done
+    uint64_t* lbar = mbar + 2;                                        // bulk weight copy of a buffer landed
+    uint32_t* taddr_sh = reinterpret_cast<uint32_t*>(mbar + 4);
+    int* abort_sh = reinterpret_cast<int*>(mbar + 5);
+    const bool bulk = (N == OC); // the chunk's weight block is contiguous in the pack
+    const uint32_t b_bytes = (uint32_t)Gm::b_bytes(N);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tiles_x = (W + TW - 1) / TW, tiles_y = (H + TH - 1) / TH;
     int bt = blockIdx.x;
@@ -146,6 +167,9 @@ __global__ void __launch_bounds__(NTHR) k_conv_tc(const bf16* __restrict__ X, co
     if (tid == 0) {
         mbar_init(&mbar[0], 1);
         mbar_init(&mbar[1], 1);
+        mbar_init(&lbar[0], 1);
+        mbar_init(&lbar[1], 1);
+        *abort_sh = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); // visible to the async proxy
     }
     tc_fence_before();
@@ -155,14 +179,20 @@ __global__ void __launch_bounds__(NTHR) k_conv_tc(const bf16* __restrict__ X, co
     const uint32_t idesc = idesc_bf16(N);
     const int nchunks = (IC + 15) / 16;
     bool ok = true;
+    int n_copy[2] = {0, 0}, n_commit[2] = {0, 0}; // thread 0: operations issued per buffer
     for (int c = 0; c < nchunks && ok; ++c) {
         const int buf = c & 1;
         unsigned char* A = smem + buf * bufb;
         unsigned char* Bm = A + Gm::A_BYTES;
         if (c >= 2) {
             ok = mbar_wait(&mbar[buf], (unsigned)(((c - 2) >> 1) & 1)); // MMAs of chunk c-2 done
-            ok = __syncthreads_and(ok) != 0; // the same decision in every thread
+            ok = __syncthreads_and(ok && !*abort_sh) != 0;                 // the same decision in every thread
             if (!ok) break;
+        }
+        if (bulk && tid == 0) {
+            mbar_expect_tx(&lbar[buf], b_bytes);
+            bulk_copy(Bm, Wp + (size_t)c * TAPS * 2 * OC * 8, b_bytes, &lbar[buf]);
+            ++n_copy[buf];
         }
         // A: [ci/8][pos][8]
         for (int e = tid; e < 16 * PP; e += NTHR) {
@@ -173,17 +203,19 @@ __global__ void __launch_bounds__(NTHR) k_conv_tc(const bf16* __restrict__ X, co
             if (ic < IC && y >= 0 && y < H && x >= 0 && x < W) v = X[((size_t)b * IC + ic) * hw + (size_t)y * W + x];
             reinterpret_cast<bf16*>(A)[((j >> 3) * PP + r) * 8 + (j & 7)] = v;
         }
-        // B: [tap][ci/8][oc][8]
-        for (int e = tid; e < TAPS * N * 2; e += NTHR) {
-            const int t = e / (N * 2), rem = e - t * N * 2, o = rem >> 1, h = rem & 1;
-            uint4 v = make_uint4(0, 0, 0, 0);
-            if (oc0 + o < OC)
-                v = *reinterpret_cast<const uint4*>(Wp + (((size_t)c * TAPS + t) * OC + oc0 + o) * 16 + h * 8);
-            *reinterpret_cast<uint4*>(Bm + ((size_t)(t * 2 + h) * N + o) * 16) = v;
-        }
+        // B: [tap][ci/8][oc][8] (thread copies when the tile is a part of the output channels)
+        if (!bulk)
+            for (int e = tid; e < TAPS * N * 2; e += NTHR) {
+                const int th = e / N, o = e - th * N; // th = tap * 2 + h
+                uint4 v = make_uint4(0, 0, 0, 0);
+                if (oc0 + o < OC)
+                    v = *reinterpret_cast<const uint4*>(Wp + (((size_t)c * TAPS * 2 + th) * OC + oc0 + o) * 8);
+                *reinterpret_cast<uint4*>(Bm + ((size_t)th * N + o) * 16) = v;
+            }
         proxy_fence(); // generic-proxy writes visible to the tensor cores
         __syncthreads();
-        if (tid == 0) {
+        if (tid == 0 && bulk && !mbar_wait(&lbar[buf], (unsigned)((c >> 1) & 1))) *abort_sh = 1;
+        if (tid == 0 && !*abort_sh) {
             tc_fence_after();
             const uint32_t a0 = smem_u32(A), b0 = smem_u32(Bm);
 #pragma unroll
@@ -194,18 +226,25 @@ __global__ void __launch_bounds__(NTHR) k_conv_tc(const bf16* __restrict__ X, co
                 mma_bf16(taddr, ad, bd, idesc, (c > 0 || t > 0) ? 1u : 0u);
             }
             mma_commit(&mbar[buf]);
+            ++n_commit[buf];
         }
     }
     // the last commit covers every MMA issued before it
     const int last = nchunks - 1;
-    if (ok) ok = mbar_wait(&mbar[last & 1], (unsigned)((last >> 1) & 1));
-    ok = __syncthreads_and(ok) != 0;
+    __syncthreads();
+    if (ok && !*abort_sh) ok = mbar_wait(&mbar[last & 1], (unsigned)((last >> 1) & 1));
+    ok = __syncthreads_and(ok && !*abort_sh) != 0;
     tc_fence_after();
     if (!ok) {
-        if (tid == 0 && status) atomicOr(status, 1);
-        // bounded wait for any MMAs still in flight before the memory is freed
-        if (last >= 1) mbar_wait(&mbar[(last - 1) & 1], (unsigned)(((last - 1) >> 1) & 1));
-        mbar_wait(&mbar[last & 1], (unsigned)((last >> 1) & 1));
+        if (tid == 0) {
+            if (status) atomicOr(status, 1);
+            // bounded waits for copies and MMAs still in flight before the memory is freed
+            for (int q = 0; q < 2; ++q) {
+                if (n_copy[q] > 0) mbar_wait(&lbar[q], (unsigned)((n_copy[q] - 1) & 1));
+                if (n_commit[q] > 0) mbar_wait(&mbar[q], (unsigned)((n_commit[q] - 1) & 1));
+            }
+        }
+        __syncthreads();
     } else {
         const int m = warp * 32 + lane;
         const int y = y0 + m / TW, x = x0 + m % TW;
