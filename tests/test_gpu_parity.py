@@ -233,6 +233,34 @@ def test_cg_matches_oracle_fp64(variant):
     assert rel(g, go) < 1e-11
 
 
+def test_cg_fp32_runs_to_the_rounding_floor():
+    """FP32 lattices: nonlinear CG keeps decreasing J until the Wolfe search
+    can no longer make progress, where it falls back to Armijo steps (soft
+    reset) instead of failing; J never increases and ends well below J(0)."""
+    from paper_1908_03876_gb300._lib import CxError
+    from paper_1908_03876_gb300.problem import Problem
+
+    w = W.aniso(64, 64, 40, seed=3, precision=32, ckpt_every=10)
+    w.windows = 4
+    w.chi = -0.3
+    p = Problem(w)
+    g = p.zeros_control()
+    Js, fallbacks = [], 0
+    for it in range(80):
+        try:
+            info = p.cg_step(g, "PR")
+        except CxError as e:
+            assert e.code == 6  # not even a steepest-descent step decreased J: converged
+            break
+        fallbacks += info["trials"] > 30
+        if Js:
+            assert info["J0"] <= Js[-1] * (1 + 1e-12)
+        assert info["J"] <= info["J0"]
+        Js.append(info["J"])
+    print(f"CG FP32: {len(Js)} iterations, J {Js[0]:.6e} -> {Js[-1]:.6e}, {fallbacks} fallback steps")
+    assert len(Js) >= 10 and Js[-1] < Js[0]
+
+
 @pytest.mark.parametrize("k", [6, 20])
 def test_tlm_matches_oracle_fp64(k):
     """Sensitivity problem (tangent-linear MRT pass) along a random direction:
