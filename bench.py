@@ -455,6 +455,62 @@ def run_cg(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+def run_unet_layers(args, rank, world, local):
+    """Forward time of each 3x3 layer shape of the 4-level U-Net at 128x128,
+    batch 16, on the tcgen05 kernel and on the mma.sync kernel (same packed
+    weights; CUDA events, 20 launches after 3 warm-up launches)."""
+    import ctypes
+
+    import torch
+
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    from paper_1908_03876_gb300.build import build
+
+    build()
+    from paper_1908_03876_gb300 import _lib
+
+    lib = _lib.load()
+    BF = torch.bfloat16
+
+    def p(t):
+        return ctypes.c_void_p(t.data_ptr())
+
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    shapes = [(6, 32, 128), (32, 32, 128), (32, 64, 64), (64, 64, 64), (64, 128, 32), (128, 128, 32),
+              (128, 256, 16), (256, 256, 16), (256, 128, 32), (128, 64, 64), (64, 32, 128)]
+    B = 16
+    out = []
+    for cin, cout, hw in shapes:
+        x = torch.randn(B, cin, hw, hw, device="cuda").to(BF)
+        w = (0.05 * torch.randn(cout, cin, 3, 3, device="cuda")).to(BF)
+        wf = torch.empty(lib.cx_nn_packed_weights(cout, cin, 3, 0), dtype=BF, device="cuda")
+        wb = torch.empty(lib.cx_nn_packed_weights(cout, cin, 3, 1), dtype=BF, device="cuda")
+        _lib.check(lib.cx_nn_pack_weights(p(w), cout, cin, 3, p(wf), p(wb), s), "pack")
+        bias = torch.zeros(cout, device="cuda")
+        y = torch.empty(B, cout, hw, hw, dtype=BF, device="cuda")
+        yf = torch.empty(B, cout, hw, hw, dtype=torch.float32, device="cuda")
+        res = {}
+        for name, fn in (("tcgen05", lambda: lib.cx_nn_conv_forward_tc(p(x), p(wf), p(bias), p(y), B, cin, cout, hw,
+                                                                         hw, 3, 1, None, s)),
+                         ("mma_sync", lambda: lib.cx_nn_conv_forward_f32(p(x), p(wf), p(bias), p(yf), B, cin, cout,
+                                                                          hw, hw, 3, s))):
+            for _ in range(3):
+                fn()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(20):
+                fn()
+            e1.record()
+            torch.cuda.synchronize()
+            res[name] = e0.elapsed_time(e1) / 20 * 1e3
+        fl = 2 * B * hw * hw * cout * cin * 9
+        out.append({"layer": f"{cin}->{cout}@{hw}", **{k + "_us": round(v, 1) for k, v in res.items()},
+                    **{k + "_tflops": round(fl / v / 1e6, 1) for k, v in res.items()}})
+    print(json.dumps({"unet_layers": out}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -462,7 +518,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="aniso1024", choices=["aniso1024", "batch", "warmstart", "cg"],
+    ap.add_argument("--workload", default="aniso1024",
+                    choices=["aniso1024", "batch", "warmstart", "cg", "unetlayers"],
                     help="aniso1024 (default bench line) or batch: 256 independent problems, sizes {64..512}^2, "
                          "1000 steps, one persistent launch per step replayed as a CUDA graph")
     ap.add_argument("--problems", type=int, default=256)
@@ -493,6 +550,9 @@ def main():
         return
     if args.workload == "cg":
         run_cg(args, rank, world, local)
+        return
+    if args.workload == "unetlayers":
+        run_unet_layers(args, rank, world, local)
         return
 
     import numpy as np
