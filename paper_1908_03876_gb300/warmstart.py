@@ -273,27 +273,33 @@ def proposal_init(ws, d_of):
     return init
 
 
-def evaluate(model: Surrogate, ws, ref, max_iter=200, device="cuda", log=None, stall_tol=1e-9):
+def evaluate(model: Surrogate, ws, ref, max_iter=200, device="cuda", log=None, stall_tol=1e-9, repeats=3):
     """Warm vs cold on held-out problems.  ref: descend(...) result from g = 0
     (defines J*).  Both timed runs stop each problem at J <= J* (1 + 1e-6);
     the warm run's time includes the network, the forward at g = 0 and the
     seeded sweep that make its proposal.  A warm-started problem that stops
     improving (relative J decrease < stall_tol over 5 steps) above the target
-    falls back to the plain method from g = 0, and that time is added."""
+    falls back to the plain method from g = 0, and that time is added.  The
+    timed runs are repeated (deterministic: same iterations) and the median
+    wall times reported."""
     Jstar = ref["J"]
     target = Jstar * (1.0 + 1e-6)
     model.predict(features(ws[:1]), np.zeros((1, ws[0].ny, ws[0].nx)))  # module loading stays out of the timing
-    warm = descend(ws, init=model.initializer(ws), max_iter=max_iter, J_target=target, device=device, log=log,
-                   stall_tol=stall_tol)
-    # fallback: problems whose warm-started descent converged above the
-    # target are solved again by the plain method from g = 0
-    failed = [i for i in range(len(ws)) if not warm["reached"][i]]
-    fb_seconds, fb_iters = 0.0, 0
-    if failed:
-        fb = descend([ws[i] for i in failed], g0=None, max_iter=max_iter, J_target=target[failed], device=device,
-                     stall_tol=stall_tol)
-        fb_seconds, fb_iters = fb["seconds"], int(fb["iters"].sum())
-    cold = descend(ws, g0=None, max_iter=max_iter, J_target=target, device=device, log=log, stall_tol=stall_tol)
+    warm_s, cold_s = [], []
+    for rep in range(repeats):
+        warm = descend(ws, init=model.initializer(ws), max_iter=max_iter, J_target=target, device=device, log=log,
+                       stall_tol=stall_tol)
+        # fallback: problems whose warm-started descent converged above the
+        # target are solved again by the plain method from g = 0
+        failed = [i for i in range(len(ws)) if not warm["reached"][i]]
+        fb_seconds, fb_iters = 0.0, 0
+        if failed:
+            fb = descend([ws[i] for i in failed], g0=None, max_iter=max_iter, J_target=target[failed],
+                         device=device, stall_tol=stall_tol)
+            fb_seconds, fb_iters = fb["seconds"], int(fb["iters"].sum())
+        warm_s.append(warm["seconds"] + fb_seconds)
+        cold = descend(ws, g0=None, max_iter=max_iter, J_target=target, device=device, log=log, stall_tol=stall_tol)
+        cold_s.append(cold["seconds"])
     # the proposal itself, against g*; and the proposal from the exact d*
     n = len(ws)
     gstar = np.stack(ref["g"])
@@ -312,8 +318,8 @@ def evaluate(model: Surrogate, ws, ref, max_iter=200, device="cuda", log=None, s
                             np.linalg.norm(Ds.reshape(n, -1), axis=1)))
     return dict(
         problems=n,
-        warm_seconds=warm["seconds"] + fb_seconds, warm_seconds_without_fallback=warm["seconds"],
-        cold_seconds=cold["seconds"], fallback_problems=len(failed),
+        warm_seconds=float(np.median(warm_s)), cold_seconds=float(np.median(cold_s)),
+        warm_seconds_all=warm_s, cold_seconds_all=cold_s, fallback_problems=len(failed),
         fallback_final_excess=[float(warm["J"][i] / Jstar[i] - 1.0) for i in failed],
         warm_iters_total=int(warm["iters"].sum()) + fb_iters, cold_iters_total=int(cold["iters"].sum()),
         warm_iters_mean=float(warm["iters"].mean()), cold_iters_mean=float(cold["iters"].mean()),
