@@ -7,7 +7,7 @@ it; the product path never does.  It shares no code with the CUDA library.
 
 The arithmetic lives in ``mrt_oracle.c`` (plain C, FP64, one node at a time);
 this module only builds it with gcc and marshals arrays through ctypes.  The
-Armijo gradient-descent driver below follows the paper's discrete-adjoint
+Armijo gradient-descent iteration below follows the paper's discrete-adjoint
 algorithm (Sec. 3.2.1, the optimisation process after eq. JD-H-B) with the
 heuristic first step min(1, 1/||E||_inf) (remark after the continuous gradient
 algorithm, Sec. 2.3).

@@ -1,12 +1,13 @@
 """Warm-start surrogate: a 4-level convolutional U-Net (32-256 channels, BF16
-weights and activations, FP32 accumulation) that maps a problem's initial
-state and parameters to a proposed control.  The paper's gradient algorithm
-(Sec. 3.2.1) then refines the proposal; started from g = 0 it is the fallback
-and the judge of the surrogate's error.
+weights and activations, FP32 accumulation) whose prediction becomes the
+proposed initial control of a problem (warmstart.py).  The paper's gradient
+algorithm (Sec. 3.2.1) then refines the proposal; started from g = 0 it is
+the fallback and the reference the surrogate's error is measured against.
 
 Every layer runs in the library's hand-written kernels (cx_nn_* in
-include/cxlbm.h): implicit-GEMM convolutions on the tensor cores for the
-forward, data-gradient and weight-gradient passes, and elementwise kernels for
+include/cxlbm.h): direct convolutions on the tensor cores (tcgen05 for 32-128
+output channels, mma.sync otherwise) for the forward, data-gradient and
+weight-gradient passes, and elementwise kernels for
 ReLU, pooling, upsampling, skips, the loss and Adam.  PyTorch only holds the
 memory and the stream.
 

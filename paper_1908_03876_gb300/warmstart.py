@@ -4,9 +4,9 @@ The paper's method (Sec. 3.2.1: forward MRT solve, AMRT adjoint, gradient,
 Armijo step) solves each control problem from g = 0.  Here a U-Net
 (surrogate.UNet) trained on optimal solutions that the method itself computed
 proposes g0 for a new problem, and the same gradient descent refines it.
-Plain descent from g = 0 stays the fallback and the judge: the warm-started
-run counts as done when its cost reaches the plain optimum J* to within a
-relative 1e-6.
+Plain descent from g = 0 stays the fallback and the reference: the
+warm-started run counts as done when its cost reaches the plain optimum J*
+to within a relative 1e-6.
 
 What the network predicts.  At the optimum the gradient vanishes:
 S(g*)^T r* + 2 alpha L G* = 0, with r* = u^N(g*) - u_target the terminal
