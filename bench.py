@@ -201,16 +201,16 @@ def run_batch(args, rank, world, local):
     else:
         allw = W.batch_workloads(args.problems, N=1000, seed=3)
     mine = sharding.my_problems(allw, rank, world)
-    t0 = time.perf_counter()
-    if args.profile:
-        cfg = {"threads": 256, "tile_x": {s: 256 for s in (64, 128, 256, 512)}, "rows": {}}
-    else:
-        cfg = autotune.autotune(mine, probe_steps=12, device=dev)
-    t_tune = time.perf_counter() - t0
     b = Batch(mine, device=dev)
     gs = [torch.as_tensor(w.random_control(500 + i, 0.01), dtype=torch.float32, device=dev) for i, w in enumerate(mine)]
     b.bind(gs)
-    autotune.apply(b, cfg)
+    t0 = time.perf_counter()
+    if args.profile:
+        cfg = {"threads": 256, "tile_x": {s: 256 for s in (64, 128, 256, 512)}, "rows": {}}
+        autotune.apply(b, cfg)
+    else:
+        cfg = autotune.autotune(b, probe_steps=12)
+    t_tune = time.perf_counter() - t0
     nodes = sum(w.nx * w.ny for w in mine)
     N = mine[0].N
     for _ in range(args.warmup):

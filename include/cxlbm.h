@@ -287,6 +287,29 @@ cx_status cx_batch_bind(cx_batch* b, const void* const* g, void* const* dJdg);
  * threads), rows[i] = nodes each thread updates per tile, 1..32 (NULL: 2).
  * The tile height is (threads / tile_x[i]) rows[i].  Synchronous. */
 cx_status cx_batch_set_tiles(cx_batch* b, int threads, int blocks, const int* tile_x, const int* rows);
+/* Tile autotuner (the scheduling choice behind the one-launch-per-step batch;
+ * no equation of the method changes with it).  Size class = problems with the
+ * same nx.  Times a probe of min(probe_steps, N) forward steps, their segment
+ * recompute and the AMRT adjoint sweep on the batch's own problems (the
+ * kernels differ in their best tiles), with CUDA events on the batch stream:
+ * for threads 128 and 256 the best of five uniform (tile_x, rows) shapes,
+ * then coordinate descent per size class over rows {4, 8, 16, 32} and the
+ * admissible widths {32, 64, 128, 256}, the others fixed.  The winner is
+ * applied as by cx_batch_set_tiles (blocks = 0).
+ * cache_path (may be NULL): a text file of one line per tuned batch,
+ * "signature<TAB>threads<TAB>nx:tile_x:rows,...<TAB>ms", the signature
+ * naming the device, lattice, precision and size-class histogram; a matching
+ * line is applied without probing, a new result is added (the file is
+ * rewritten through a temporary and renamed).
+ * Needs cx_batch_set_initial and a binding with every dJdg set; the probe
+ * overwrites checkpoints 1.. and the tapes, so the next evaluation starts
+ * from the initial state.  Outputs (host, each may be NULL): threads_out,
+ * tile_x_out[count] and rows_out[count] per problem, probe_ms_out (the
+ * probe time of the winner, from the cache when it came from there).
+ * Synchronous.  CX_ERR_INVALID_ARG for probe_steps < 1, CX_ERR_STATE
+ * without the state above, CX_ERR_INTERNAL if the cache cannot be written. */
+cx_status cx_batch_autotune(cx_batch* b, int probe_steps, const char* cache_path, int* threads_out,
+                            int* tile_x_out, int* rows_out, double* probe_ms_out);
 /* Forward of every problem; J_dev (device double [count], may be NULL). */
 cx_status cx_batch_forward(cx_batch* b, double* J_dev);
 /* Forward + recompute + AMRT adjoint of every problem into the bound dJdg;

@@ -18,8 +18,12 @@
 // per problem in a fixed order, so replays are bitwise reproducible.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
+#include <fstream>
+#include <map>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "cx_adj_body.cuh"
@@ -817,6 +821,253 @@ cx_status batch_layout(const cx_problem_desc* d, int count, std::vector<size_t>*
     return CX_OK;
 }
 
+// ---- autotuner: probe timing, search, cache ----
+
+constexpr int TUNE_WIDTHS[4] = {32, 64, 128, 256};
+constexpr int TUNE_ROWS[4] = {4, 8, 16, 32};
+constexpr int TUNE_UNIFORM[5][2] = {{32, 8}, {64, 8}, {64, 16}, {128, 16}, {32, 16}};
+
+bool tune_admissible(int threads, int nx, int t) {
+    return t <= threads && threads % t == 0 && threads / t <= 8 && t <= std::max(32, 2 * nx);
+}
+
+int tune_widest(int threads, int nx) {
+    int w = 0;
+    for (int t : TUNE_WIDTHS)
+        if (tune_admissible(threads, nx, t)) w = t;
+    return w;
+}
+
+// The probe shortens the schedule to N' = min(N, probe) steps with interval
+// k' = min(k, N') (S = 1) or min(k, ceil(N'/2)) (S >= 2), so that it has
+// S' <= S segments (k' = k gives ceil(N'/k) <= S, otherwise S' <= 2 <= S) and
+// a recompute: every checkpoint slot, tape plane and step index it touches
+// exists for the full schedule too.  The guard puts N, k, S back on every
+// return path.
+struct ScheduleGuard {
+    BatchHost& h;
+    int N, k, S;
+    ScheduleGuard(BatchHost& hh, int probe) : h(hh), N(hh.N), k(hh.k), S(hh.S) {
+        const int n1 = std::min(N, probe);
+        int k1 = std::min(k, n1);
+        if (S >= 2 && n1 > 1) k1 = std::min(k, (n1 + 1) / 2);
+        h.N = n1;
+        h.k = k1;
+        h.S = (n1 + k1 - 1) / k1;
+    }
+    ~ScheduleGuard() {
+        h.N = N;
+        h.k = k;
+        h.S = S;
+    }
+};
+
+// Mean time of one probe (forward, recompute, adjoint; direct launches) with
+// the given tiles, after one untimed probe.
+template <typename T>
+cx_status time_probe(BatchHost& h, int threads, const std::vector<int>& tx, const std::vector<int>& rr,
+                     cudaEvent_t e0, cudaEvent_t e1, double* ms) {
+    B_CUDA(cudaStreamSynchronize(h.stream)); // nothing in flight reads the table while it is replaced
+    h.threads = threads;
+    h.tx = tx;
+    h.rr = rr;
+    const int occ = forward_occupancy<T>(h.Q, threads);
+    h.blocks = h.probs[0]->nsm * occ;
+    cx_status rc = upload_table<T>(h);
+    if (rc) return rc;
+    constexpr int REPS = 2;
+    for (int r = 0; r <= REPS; ++r) {
+        if (r == 1) B_CUDA(cudaEventRecord(e0, h.stream));
+        rc = enqueue_forward<T>(h, false);
+        if (rc == CX_OK) rc = enqueue_adjoint<T>(h);
+        if (rc) return rc;
+    }
+    B_CUDA(cudaEventRecord(e1, h.stream));
+    B_CUDA(cudaEventSynchronize(e1));
+    float t = 0.f;
+    B_CUDA(cudaEventElapsedTime(&t, e0, e1));
+    *ms = (double)t / REPS;
+    return CX_OK;
+}
+
+struct TuneChoice {
+    int threads = 0;
+    std::map<int, int> tx, rr; // per size class (nx)
+    double ms = 0.0;
+};
+
+template <typename T> cx_status tune_search(BatchHost& h, TuneChoice* best) {
+    std::vector<int> classes;
+    for (cx_problem* p : h.probs) classes.push_back(p->d.nx);
+    std::sort(classes.begin(), classes.end());
+    classes.erase(std::unique(classes.begin(), classes.end()), classes.end());
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return CX_ERR_CUDA;
+    }
+    cx_status rc = CX_OK;
+    best->threads = 0;
+    for (int threads : {128, 256}) {
+        auto timed = [&](const std::map<int, int>& tx, const std::map<int, int>& rr, double* ms) {
+            std::vector<int> vt(h.count), vr(h.count);
+            for (int i = 0; i < h.count; ++i) {
+                vt[i] = tx.at(h.probs[i]->d.nx);
+                vr[i] = rr.at(h.probs[i]->d.nx);
+            }
+            return time_probe<T>(h, threads, vt, vr, e0, e1, ms);
+        };
+        TuneChoice cur;
+        cur.threads = threads;
+        bool have = false;
+        for (const auto& u : TUNE_UNIFORM) {
+            std::map<int, int> tx, rr;
+            bool ok = true;
+            for (int nx : classes) {
+                const int t = std::min(u[0], tune_widest(threads, nx));
+                ok = ok && t > 0 && tune_admissible(threads, nx, t);
+                tx[nx] = t;
+                rr[nx] = u[1];
+            }
+            if (!ok) continue;
+            double ms = 0.0;
+            if ((rc = timed(tx, rr, &ms))) break;
+            if (!have || ms < cur.ms) {
+                cur.tx = tx;
+                cur.rr = rr;
+                cur.ms = ms;
+                have = true;
+            }
+        }
+        if (rc) break;
+        if (!have) continue;
+        for (int nx : classes) {
+            for (int r : TUNE_ROWS) {
+                if (r == cur.rr[nx]) continue;
+                std::map<int, int> rr = cur.rr;
+                rr[nx] = r;
+                double ms = 0.0;
+                if ((rc = timed(cur.tx, rr, &ms))) break;
+                if (ms < cur.ms) {
+                    cur.rr = rr;
+                    cur.ms = ms;
+                }
+            }
+            if (rc) break;
+            for (int t : TUNE_WIDTHS) {
+                if (!tune_admissible(threads, nx, t) || t == cur.tx[nx]) continue;
+                std::map<int, int> tx = cur.tx;
+                tx[nx] = t;
+                double ms = 0.0;
+                if ((rc = timed(tx, cur.rr, &ms))) break;
+                if (ms < cur.ms) {
+                    cur.tx = tx;
+                    cur.ms = ms;
+                }
+            }
+            if (rc) break;
+        }
+        if (rc) break;
+        if (best->threads == 0 || cur.ms < best->ms) *best = cur;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc == CX_OK && best->threads == 0) rc = CX_ERR_INTERNAL;
+    return rc;
+}
+
+std::string tune_signature(const BatchHost& h) {
+    int dev = 0;
+    cudaDeviceProp prop;
+    std::string name = "device";
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&prop, dev) == cudaSuccess) name = prop.name;
+    for (char& c : name)
+        if (c == '\t' || c == '\n') c = ' ';
+    std::map<int, int> hist;
+    for (cx_problem* p : h.probs) ++hist[p->d.nx];
+    std::string s = name + "|Q" + std::to_string(h.Q) + "|fp" + std::to_string(h.esz * 8) + "|";
+    for (const auto& kv : hist) s += std::to_string(kv.first) + ":" + std::to_string(kv.second) + ",";
+    return s;
+}
+
+std::vector<std::string> split_tabs(const std::string& line) {
+    std::vector<std::string> f;
+    size_t a = 0;
+    for (;;) {
+        const size_t b = line.find('\t', a);
+        f.push_back(line.substr(a, b == std::string::npos ? std::string::npos : b - a));
+        if (b == std::string::npos) break;
+        a = b + 1;
+    }
+    return f;
+}
+
+// The cached choice for this signature, if the file has one that is
+// admissible for every size class of the batch.
+bool cache_lookup(const char* path, const std::string& sig, const BatchHost& h, TuneChoice* c) {
+    std::ifstream in(path);
+    std::string line;
+    while (in && std::getline(in, line)) {
+        const std::vector<std::string> f = split_tabs(line);
+        if (f.size() != 4 || f[0] != sig) continue;
+        TuneChoice t;
+        t.threads = std::atoi(f[1].c_str());
+        t.ms = std::atof(f[3].c_str());
+        size_t a = 0;
+        while (a < f[2].size()) {
+            size_t b = f[2].find(',', a);
+            if (b == std::string::npos) b = f[2].size();
+            int nx = 0, tx = 0, r = 0;
+            if (std::sscanf(f[2].substr(a, b - a).c_str(), "%d:%d:%d", &nx, &tx, &r) == 3) {
+                t.tx[nx] = tx;
+                t.rr[nx] = r;
+            }
+            a = b + 1;
+        }
+        if (t.threads != 128 && t.threads != 256) continue;
+        bool ok = true;
+        for (cx_problem* p : h.probs) {
+            const int nx = p->d.nx;
+            ok = ok && t.tx.count(nx) && t.rr.count(nx) && tune_admissible(t.threads, nx, t.tx[nx]) &&
+                 (t.tx[nx] & (t.tx[nx] - 1)) == 0 && t.tx[nx] >= 32 && t.rr[nx] >= 1 && t.rr[nx] <= 32;
+        }
+        if (!ok) continue;
+        *c = t;
+        return true;
+    }
+    return false;
+}
+
+bool cache_store(const char* path, const std::string& sig, const TuneChoice& c) {
+    std::vector<std::string> keep;
+    {
+        std::ifstream in(path);
+        std::string line;
+        while (in && std::getline(in, line))
+            if (!line.empty() && split_tabs(line)[0] != sig) keep.push_back(line);
+    }
+    std::string entry = sig + "\t" + std::to_string(c.threads) + "\t";
+    bool first = true;
+    for (const auto& kv : c.tx) {
+        if (!first) entry += ",";
+        first = false;
+        entry += std::to_string(kv.first) + ":" + std::to_string(kv.second) + ":" + std::to_string(c.rr.at(kv.first));
+    }
+    char ms[64];
+    std::snprintf(ms, sizeof ms, "%.6f", c.ms);
+    entry += "\t";
+    entry += ms;
+    keep.push_back(entry);
+    const std::string tmp = std::string(path) + ".tmp";
+    {
+        std::ofstream out(tmp, std::ios::trunc);
+        for (const std::string& l : keep) out << l << "\n";
+        out.flush();
+        if (!out) return false;
+    }
+    return std::rename(tmp.c_str(), path) == 0;
+}
+
 } // namespace
 
 extern "C" {
@@ -1079,6 +1330,49 @@ cx_status cx_batch_get_status(cx_batch* b) {
         cudaStreamSynchronize(b->h.stream) != cudaSuccess)
         return CX_ERR_CUDA;
     return (st & ST_UNSTABLE) ? CX_ERR_UNSTABLE : CX_OK;
+}
+
+cx_status cx_batch_autotune(cx_batch* b, int probe_steps, const char* cache_path, int* threads_out,
+                            int* tile_x_out, int* rows_out, double* probe_ms_out) {
+    if (!b || probe_steps < 1) return CX_ERR_INVALID_ARG;
+    BatchHost& h = b->h;
+    if (!h.has_init || !h.bound) return CX_ERR_STATE;
+    for (void* p : h.dJdg)
+        if (!p) return CX_ERR_STATE;
+    const std::string sig = tune_signature(h);
+    TuneChoice c;
+    const bool cached = cache_path && cache_lookup(cache_path, sig, h, &c);
+    cx_status rc = CX_OK;
+    if (!cached) {
+        drop_graphs(h);
+        {
+            ScheduleGuard guard(h, probe_steps);
+            rc = h.esz == 8 ? tune_search<double>(h, &c) : tune_search<float>(h, &c);
+        }
+        // the probe overwrote checkpoints past the first, the tapes and the populations
+        h.fwd_at_g = false;
+        h.J_on_device = false;
+        for (cx_problem* p : h.probs) {
+            p->fwd_valid = false;
+            p->adj_valid = false;
+            p->tape_last_valid = false;
+        }
+        if (rc) return rc;
+    }
+    B_CUDA(cudaStreamSynchronize(h.stream));
+    std::vector<int> tx(h.count), rr(h.count);
+    for (int i = 0; i < h.count; ++i) {
+        tx[i] = c.tx.at(h.probs[i]->d.nx);
+        rr[i] = c.rr.at(h.probs[i]->d.nx);
+    }
+    rc = cx_batch_set_tiles(b, c.threads, 0, tx.data(), rr.data());
+    if (rc) return rc;
+    if (threads_out) *threads_out = c.threads;
+    if (tile_x_out) std::copy(tx.begin(), tx.end(), tile_x_out);
+    if (rows_out) std::copy(rr.begin(), rr.end(), rows_out);
+    if (probe_ms_out) *probe_ms_out = c.ms;
+    if (!cached && cache_path && !cache_store(cache_path, sig, c)) return CX_ERR_INTERNAL;
+    return CX_OK;
 }
 
 cx_status cx_batch_destroy(cx_batch* b) {

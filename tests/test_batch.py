@@ -111,23 +111,36 @@ def test_batch_fp32_against_fp64_oracle():
 
 
 def test_autotuner_picks_admissible_config(tmp_path):
+    """cx_batch_autotune: an admissible choice, applied to the batch, results
+    unchanged by it (the probe's overwritten state is recomputed), and the
+    cached line reused by a second batch of the same size classes."""
     from paper_1908_03876_gb300 import autotune
     from paper_1908_03876_gb300.batch import Batch
 
-    ws = [W.aniso(nx, ny, 8, seed=3, precision=32, ckpt_every=8) for nx, ny in [(64, 64), (128, 64), (64, 128)]]
-    cfg = autotune.autotune(ws, probe_steps=6, cache_path=str(tmp_path / "tune.json"))
-    assert cfg["threads"] in (128, 256)
-    for nx, tx in cfg["tile_x"].items():
-        assert cfg["threads"] % tx == 0 and cfg["threads"] // tx <= 8
-        assert cfg["rows"][nx] in autotune.ROWS or cfg["rows"][nx] in [r for _, r in autotune.UNIFORM]
-    again = autotune.autotune(ws, probe_steps=6, cache_path=str(tmp_path / "tune.json"))
-    assert again["tile_x"] == cfg["tile_x"] and again["rows"] == cfg["rows"]
+    ws = [W.aniso(nx, ny, 8, seed=3, precision=32, ckpt_every=4) for nx, ny in [(64, 64), (128, 64), (64, 128)]]
     b = Batch(ws)
     b.bind(b.zeros_controls())
     J0 = b.forward().cpu().numpy().copy()
-    autotune.apply(b, cfg)
+    cache = tmp_path / "tune.txt"
+    cfg = autotune.autotune(b, probe_steps=6, cache_path=cache)
+    assert cfg["threads"] in (128, 256) and cfg["ms"] > 0
+    for nx, tx in cfg["tile_x"].items():
+        assert cfg["threads"] % tx == 0 and cfg["threads"] // tx <= 8 and tx >= 32
+        assert cfg["rows"][nx] in (4, 8, 16, 32)
+    lines = cache.read_text().splitlines()
+    assert len(lines) == 1 and len(lines[0].split("\t")) == 4
     J1 = b.forward().cpu().numpy()
     assert np.allclose(J0, J1, rtol=1e-6)
+    J2, gsq, _ = (x.cpu().numpy().copy() for x in b.gradient())
+    b2 = Batch(ws)
+    b2.bind(b2.zeros_controls())
+    again = autotune.autotune(b2, probe_steps=6, cache_path=cache)
+    assert again["tile_x"] == cfg["tile_x"] and again["rows"] == cfg["rows"] and again["threads"] == cfg["threads"]
+    assert len(cache.read_text().splitlines()) == 1
+    J3, gsq3, _ = (x.cpu().numpy() for x in b2.gradient())
+    assert np.allclose(J2, J3, rtol=1e-6) and np.allclose(gsq, gsq3, rtol=1e-5)
+    b.close()
+    b2.close()
 
 
 def test_batch_step_matches_oracle_gd():
