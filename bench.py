@@ -522,12 +522,14 @@ def main():
                     choices=["aniso1024", "batch", "warmstart", "cg", "unetlayers"],
                     help="aniso1024 (default bench line) or batch: 256 independent problems, sizes {64..512}^2, "
                          "1000 steps, one persistent launch per step replayed as a CUDA graph")
+    ap.add_argument("--staging", default="rows", choices=["rows", "thread"],
+                    help="aniso1024: bulk row-window staging (default) or per-thread copies")
     ap.add_argument("--problems", type=int, default=256)
     ap.add_argument("--ws-train", type=int, default=2000)
     ap.add_argument("--ws-test", type=int, default=200)
-    ap.add_argument("--ws-size", type=int, default=128)
-    ap.add_argument("--ws-steps", type=int, default=128)
-    ap.add_argument("--ws-epochs", type=int, default=60)
+    ap.add_argument("--ws-size", type=int, default=256)
+    ap.add_argument("--ws-steps", type=int, default=256)
+    ap.add_argument("--ws-epochs", type=int, default=40)
     ap.add_argument("--profile", action="store_true",
                     help="small profiling case: the same lattices (batch: --problems of them), 20 time steps, "
                          "k = 10, one warm-up and one timed gradient evaluation, no CPU baseline or e2e leg")
@@ -578,6 +580,7 @@ def main():
     wl = WORKLOAD
     w = W.aniso(wl["nx"], wl["ny"], wl["N"], seed=1 + rank, precision=32, ckpt_every=wl["k"])
     prob = Problem(w, device=dev)
+    prob.set_staging(args.staging == "rows")
     g = torch.as_tensor(w.random_control(100 + rank, 0.01), dtype=torch.float32, device=dev).contiguous()
     E = torch.empty_like(g)
     nodes = w.nx * w.ny
@@ -630,7 +633,10 @@ def main():
         roof[ph] = {"achieved": ach, "frac": ach / hbm, "ms_total": ms, "launches": launches,
                     "us_per_launch": per_launch_s * 1e6, "bytes_per_node": BYTES[ph]}
     dom = max(roof, key=lambda k: roof[k]["ms_total"]) if roof else "forward"
-    kern = {"forward": "k_forward", "recompute": "k_forward (tape)", "adjoint": "k_adjoint"}[dom]
+    if args.staging == "rows":
+        kern = {"forward": "k_forward_rows", "recompute": "k_forward_rows (tape)", "adjoint": "k_adjoint_rows"}[dom]
+    else:
+        kern = {"forward": "k_forward", "recompute": "k_forward (tape)", "adjoint": "k_adjoint"}[dom]
     roofline = {"bound": "hbm", "achieved": roof[dom]["achieved"], "peak": hbm, "unit": "GB/s",
                 "frac": roof[dom]["frac"], "traffic": _traffic(kern.split()[0]), "kernel": kern,
                 "peak_source": peak_kind, "bytes_per_launch": BYTES[dom] * nodes}

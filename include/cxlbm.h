@@ -35,8 +35,8 @@
  *     stated otherwise; cx_step, cx_get_norms and cx_get_timing synchronise.
  *   - Every call returns a cx_status; CX_OK is 0.  A CUDA error (launch or a
  *     failed runtime call) returns CX_ERR_CUDA.  Errors a kernel detects (a
- *     non-finite cost or gradient) are recorded in a device status word and
- *     reported by the next synchronising call.
+ *     non-finite cost or gradient, a bounded wait that ran out) are recorded
+ *     in a device status word and reported by the next synchronising call.
  */
 #ifndef CXLBM_H
 #define CXLBM_H
@@ -249,6 +249,17 @@ cx_status cx_get_norms(cx_problem* p, double* J, double* grad_sq, double* grad_i
  * Results do not depend on the shape.
  * Errors: CX_ERR_INVALID_ARG (also when blocks * threads / 32 > 32768). */
 cx_status cx_set_launch(cx_problem* p, int threads, int blocks);
+/* Staging of the lattice kernels' inputs.  row_windows = 1 (default): the
+ * forward steps n >= 1 and the interior adjoint steps of grids without solid
+ * nodes, whose rows are a whole number of 16-byte units and whose launch has
+ * 128 or 256 threads, stage each row segment of the pulled populations and
+ * the node-local planes in shared memory with bulk asynchronous copies
+ * completed on an mbarrier (a wait that never completes ends the launch and
+ * later calls return CX_ERR_TIMEOUT); other steps use per-thread
+ * asynchronous copies.  row_windows = 0: per-thread copies everywhere.
+ * Results are bitwise identical either way (same arithmetic per node).
+ * CX_ERR_INVALID_ARG for other values. */
+cx_status cx_set_staging(cx_problem* p, int row_windows);
 
 /* Per-phase timing with CUDA events on the problem's stream: enable != 0
  * starts accumulating.  cx_get_timing (synchronising) returns milliseconds

@@ -23,7 +23,7 @@ EXPORTS = [
     "cx_workspace_size", "cx_create", "cx_set_initial", "cx_forward", "cx_adjoint", "cx_gradient", "cx_step",
     "cx_get_fields", "cx_get_psi0", "cx_get_norms", "cx_set_launch", "cx_set_timing", "cx_get_timing",
     "cx_destroy", "cx_status_string", "cx_forward_static", "cx_cg_step", "cx_cg_reset",
-    "cx_tlm", "cx_lma_step", "cx_cadjoint",
+    "cx_tlm", "cx_lma_step", "cx_cadjoint", "cx_set_staging",
     "cx_batch_workspace_size", "cx_batch_create", "cx_batch_set_initial", "cx_batch_bind", "cx_batch_set_tiles",
     "cx_batch_forward", "cx_batch_gradient", "cx_batch_get_fields", "cx_batch_get_status", "cx_batch_destroy",
     "cx_batch_set_enabled", "cx_batch_step", "cx_batch_adjoint", "cx_batch_axpy", "cx_batch_prepare",
@@ -113,6 +113,7 @@ def load():
         "cx_tlm": [vp, vp, vp, vp, vp, dp],
         "cx_lma_step": [vp, vp, vp, ctypes.POINTER(StepInfo)],
         "cx_cadjoint": [vp, vp, vp],
+        "cx_set_staging": [vp, cint],
         "cx_batch_workspace_size": [D, cint, ctypes.POINTER(ctypes.c_size_t)],
         "cx_batch_create": [D, cint, vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)],
         "cx_batch_set_initial": [vp, vp, vp],

@@ -60,9 +60,9 @@ __device__ __forceinline__ void adj_stage(const CxConst& C, const Args& A, const
     if (C.aniso == CX_ANISO_ROTATED) cp_async(s + (2 * Q + 5) * NT, reinterpret_cast<const T*>(C.theta) + k);
 }
 
-template <typename T, int Q, int NT, typename Args>
+template <typename T, int Q, int NT, typename Args, typename Stage>
 __device__ __forceinline__ void adj_compute(const CxConst& C, const KConst<T>& KC, const Args& A, const NodeIdx& nd,
-                                            const T* s, typename SqAccT<T>::type& acc) {
+                                            const Stage& S, typename SqAccT<T>::type& acc) {
     using L = Lat<Q>;
     if (!nd.fluid) {
         if (nd.c >= 0) A.dJdg[nd.c] = T(0); // solid window nodes are not controlled
@@ -72,16 +72,16 @@ __device__ __forceinline__ void adj_compute(const CxConst& C, const KConst<T>& K
     T ru[Q], rv[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        ru[i] = s[i * NT];
-        rv[i] = (A.terminal && !A.wv) ? T(0) : s[(Q + i) * NT];
+        ru[i] = S.pop(i, L::ex(i));
+        rv[i] = (A.terminal && !A.wv) ? T(0) : S.pop(Q + i, L::ex(i));
     }
-    const T Tu = s[(2 * Q) * NT];
-    const T Gx = s[(2 * Q + 1) * NT];
-    const T Gy = s[(2 * Q + 2) * NT];
-    const T sig_next = A.terminal ? T(0) : s[(2 * Q + 3) * NT];
-    const T gv = (nd.ctrl && A.g) ? s[(2 * Q + 4) * NT] : T(0);
+    const T Tu = S.val(2 * Q);
+    const T Gx = S.val(2 * Q + 1);
+    const T Gy = S.val(2 * Q + 2);
+    const T sig_next = A.terminal ? T(0) : S.val(2 * Q + 3);
+    const T gv = (nd.ctrl && A.g) ? S.val(2 * Q + 4) : T(0);
     NodeCoef<T> nc;
-    node_coef_th<T>(C, KC, (C.aniso == CX_ANISO_ROTATED) ? s[(2 * Q + 5) * NT] : T(0), y, k, nc);
+    node_coef_th<T>(C, KC, (C.aniso == CX_ANISO_ROTATED) ? S.val(2 * Q + 5) : T(0), y, k, nc);
 
     // --- transposed collisions: mt = M^T Pi^T (N^-1 M rho), Tcal = sum_k z_k mh_k
     T mh[Q], mom[Q], z[Q], mt[Q];

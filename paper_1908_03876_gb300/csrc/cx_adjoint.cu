@@ -19,6 +19,13 @@
 // Execution: the persistent, two-stage cp.async pipeline of the forward
 // kernel (see cx_forward.cu), staging the pulled adjoint populations, the tape,
 // sigma^{n+1}, g^n and the angle of the next node while the current one runs.
+// Interior steps (not the terminal one) of grids without solid nodes use the
+// row-window kernel k_adjoint_rows instead: bulk copies of the pulled
+// population windows (rows y + e_y,i, widened by 16 bytes per side) and of the
+// node-local planes per row segment, completed on an mbarrier per stage, as in
+// k_forward_rows.
+#include <algorithm>
+
 #include "cx_adj_body.cuh"
 
 namespace cx {
@@ -43,7 +50,7 @@ __global__ void __launch_bounds__(NT) k_adjoint(const CxConst C, const KConst<T>
         if (it.valid()) adj_stage<T, Q, NT, AdjArgs<T>>(C, A, nxt, odd ? s0 : s1);
         cp_async_commit();
         cp_async_wait<1>();
-        adj_compute<T, Q, NT, AdjArgs<T>>(C, KC, A, cur, odd ? s1 : s0, acc);
+        adj_compute<T, Q, NT, AdjArgs<T>>(C, KC, A, cur, ThreadSlots<T, NT>{odd ? s1 : s0}, acc);
         cur = nxt;
         odd = !odd;
     }
@@ -87,9 +94,157 @@ static cudaError_t launch_q(const CxConst& C, const KConst<T>& K, const AdjArgs<
     }
 }
 
+// Bulk copies of one row segment's stage (issued by one thread): the 2Q
+// windows of psi^{n+1}, the tape (u, G_x, G_y), sigma^{n+1}, g (whole-grid
+// control) and the angle (rotated tensors).
+template <typename T, int Q, int NT>
+__device__ __forceinline__ void adj_issue_rows(const CxConst& C, const AdjArgs<T>& A, int y, int x0, T* st,
+                                               uint64_t* bar) {
+    using L = Lat<Q>;
+    using RW = RowWindow<T, Q, NT>;
+    const int nx = C.nx, nv = min(NT, nx - x0);
+    const int rm = y == 0 ? C.ny - 1 : y - 1, rp = y == C.ny - 1 ? 0 : y + 1;
+    const bool rot = C.aniso == CX_ANISO_ROTATED, gb = A.g && C.ctrl_full;
+    const uint32_t nb = (uint32_t)nv * sizeof(T);
+    mbar_expect_tx(bar, (uint32_t)(2 * Q * (nv + 2 * RW::H)) * sizeof(T) + nb * (4u + gb + rot));
+#pragma unroll
+    for (int j = 0; j < 2 * Q; ++j) {
+        const int i = j < Q ? j : j - Q;
+        const int ys = L::ey(i) > 0 ? rp : (L::ey(i) < 0 ? rm : y); // pull from x + e_i
+        bulk_row_window<T, NT>(st + j * RW::W, A.in(j) + (size_t)ys * nx, x0, nv, nx, bar);
+    }
+    T* const loc = st + 2 * Q * RW::W;
+    const size_t k0 = (size_t)y * nx + x0, pl = (size_t)C.plane;
+    bulk_g2s(loc, A.tape + k0, nb, bar);
+    bulk_g2s(loc + NT, A.tape + pl + k0, nb, bar);
+    bulk_g2s(loc + 2 * NT, A.tape + 2 * pl + k0, nb, bar);
+    bulk_g2s(loc + 3 * NT, A.sigma + k0, nb, bar);
+    if (gb) bulk_g2s(loc + 4 * NT, A.g + k0, nb, bar);
+    if (rot) bulk_g2s(loc + 5 * NT, reinterpret_cast<const T*>(C.theta) + k0, nb, bar);
+}
+
+// g of a controlled node when the control window is not the whole grid
+template <typename T, int Q, int NT>
+__device__ __forceinline__ void adj_stage_ctrl(const CxConst& C, const AdjArgs<T>& A, const NodeIdx& nd, T* st) {
+    using RW = RowWindow<T, Q, NT>;
+    if (C.ctrl_full || !nd.ctrl || !A.g) return;
+    cp_async(st + 2 * Q * RW::W + 4 * NT + threadIdx.x, A.g + nd.c);
+}
+
+template <typename T, int Q, int NT> constexpr int adj_rows_stage_values() {
+    return 2 * Q * RowWindow<T, Q, NT>::W + 6 * NT;
+}
+template <typename T, int Q, int NT> constexpr size_t adj_rows_smem() {
+    return (size_t)2 * adj_rows_stage_values<T, Q, NT>() * sizeof(T) + 2 * sizeof(uint64_t);
+}
+
+template <typename T, int Q, int NT>
+__global__ void __launch_bounds__(NT) k_adjoint_rows(const CxConst C, const KConst<T> KC, const AdjArgs<T> A) {
+    using RW = RowWindow<T, Q, NT>;
+    constexpr int SV = adj_rows_stage_values<T, Q, NT>();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* const st0 = reinterpret_cast<T*>(smem_raw);
+    T* const st1 = st0 + SV;
+    uint64_t* const bar = reinterpret_cast<uint64_t*>(st1 + SV);
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    typename SqAccT<T>::type acc;
+    ChunkIter<NT> it(C);
+    NodeIdx cur = it.valid() ? it.node(C) : no_node();
+    allow_next_grid();
+    wait_prior_grid(); // the previous step's populations and node state are complete
+    if (it.valid()) {
+        if (threadIdx.x == 0) adj_issue_rows<T, Q, NT>(C, A, it.y, it.seg * NT, st0, &bar[0]);
+        adj_stage_ctrl<T, Q, NT>(C, A, cur, st0);
+    }
+    cp_async_commit();
+    unsigned phase = 0; // bit b: parity of stage b's next completion
+    int b = 0;          // stage of the current segment
+    bool ok = true;
+    while (it.valid()) {
+        it.next();
+        const NodeIdx nxt = it.valid() ? it.node(C) : no_node();
+        T* const sn = b ? st0 : st1;
+        if (it.valid()) { // stage b^1 is free: every thread passed the barrier that ended its last use
+            if (threadIdx.x == 0) adj_issue_rows<T, Q, NT>(C, A, it.y, it.seg * NT, sn, &bar[b ^ 1]);
+            adj_stage_ctrl<T, Q, NT>(C, A, nxt, sn);
+        }
+        cp_async_commit();
+        cp_async_wait<1>();
+        ok = mbar_wait(&bar[b], (phase >> b) & 1u);
+        phase ^= 1u << b;
+        if (ok) adj_compute<T, Q, NT, AdjArgs<T>>(C, KC, A, cur, RW{(b ? st1 : st0) + threadIdx.x}, acc);
+        if (__syncthreads_or(!ok)) { // all threads leave together when a stage never completed
+            ok = false;
+            break;
+        }
+        cur = nxt;
+        b ^= 1;
+    }
+    if (!ok) {
+        // bounded waits for the copies still in flight, then report
+        if (it.valid()) mbar_wait(&bar[b ^ 1], (phase >> (b ^ 1)) & 1u);
+        mbar_wait(&bar[b], ((phase >> b) & 1u) ^ 1u);
+        if (threadIdx.x == 0 && A.status) atomicOr(A.status, ST_TIMEOUT);
+    }
+    cp_async_wait<0>();
+    const int w = blockIdx.x * (NT >> 5) + (threadIdx.x >> 5);
+    acc.flush(A.e2_part + w, A.emax_part + w);
+}
+
+// an interior step the row-window kernel can take (see k_forward_rows)
+template <typename T> static bool rows_eligible(const CxConst& C, const AdjArgs<T>& A, const Launch& L) {
+    constexpr int H = 16 / (int)sizeof(T);
+    auto al = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; };
+    if (!L.row_windows || A.terminal || C.has_solid || C.nx % H != 0) return false;
+    if (L.block.x != 128 && L.block.x != 256) return false;
+    for (int j = 0; j < 2 * C.Q; ++j)
+        if (!al(A.rin[j])) return false;
+    if (!al(A.tape) || !al(A.sigma) || (C.plane * (long long)sizeof(T)) % 16 != 0) return false;
+    if (C.aniso == CX_ANISO_ROTATED && !al(C.theta)) return false;
+    if (C.ctrl_full && A.g && !al(A.g)) return false;
+    return true;
+}
+
+template <typename T, int Q, int NT>
+static cudaError_t launch_rows_qn(const CxConst& C, const KConst<T>& K, const AdjArgs<T>& A, const Launch& L,
+                                  cudaStream_t s) {
+    constexpr size_t smem = adj_rows_smem<T, Q, NT>();
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e =
+            cudaFuncSetAttribute(k_adjoint_rows<T, Q, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(L.rows_grid ? std::min(L.rows_grid, L.grid.x) : L.grid.x);
+    cfg.blockDim = L.block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_adjoint_rows<T, Q, NT>, C, K, A);
+}
+
+template <typename T, int Q>
+static cudaError_t launch_rows_q(const CxConst& C, const KConst<T>& K, const AdjArgs<T>& A, const Launch& L,
+                                 cudaStream_t s) {
+    return L.block.x == 128 ? launch_rows_qn<T, Q, 128>(C, K, A, L, s) : launch_rows_qn<T, Q, 256>(C, K, A, L, s);
+}
+
 template <typename T>
 cudaError_t launch_adjoint(const CxConst& C, const KConst<T>& K, const AdjArgs<T>& A, const Launch& L,
                            cudaStream_t s) {
+    if (rows_eligible<T>(C, A, L))
+        return C.Q == 9 ? launch_rows_q<T, 9>(C, K, A, L, s) : launch_rows_q<T, 5>(C, K, A, L, s);
     return C.Q == 9 ? launch_q<T, 9>(C, K, A, L, s) : launch_q<T, 5>(C, K, A, L, s);
 }
 
@@ -114,5 +269,22 @@ template <typename T> int adjoint_occupancy(int Q, int threads) {
 }
 template int adjoint_occupancy<float>(int, int);
 template int adjoint_occupancy<double>(int, int);
+
+template <typename T, int Q, int NT> static int rows_occ_qn() {
+    constexpr size_t smem = adj_rows_smem<T, Q, NT>();
+    cudaFuncSetAttribute(k_adjoint_rows<T, Q, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adjoint_rows<T, Q, NT>, NT, smem) != cudaSuccess) return 1;
+    return nb > 0 ? nb : 1;
+}
+template <typename T, int Q> static int rows_occ_q(int threads) {
+    return threads == 128 ? rows_occ_qn<T, Q, 128>() : rows_occ_qn<T, Q, 256>();
+}
+// resident blocks per SM of the row-window kernel (128 or 256 threads)
+template <typename T> int adjoint_rows_occupancy(int Q, int threads) {
+    return Q == 9 ? rows_occ_q<T, 9>(threads) : rows_occ_q<T, 5>(threads);
+}
+template int adjoint_rows_occupancy<float>(int, int);
+template int adjoint_rows_occupancy<double>(int, int);
 
 } // namespace cx

@@ -173,6 +173,7 @@ template <typename T> static cx_status run_forward(cx_problem* p, const T* g, co
     for (int n = 0; n < Ly.N; ++n) {
         const int seg = n / Ly.k;
         FwdArgs<T> A{};
+        A.status = p->at<int>(p->lay.off_status);
         T* out;
         if (n + 1 < Ly.N && (n + 1) % Ly.k == 0) {
             out = reinterpret_cast<T*>(p->ckpt_slot((n + 1) / Ly.k));
@@ -231,6 +232,7 @@ static cx_status run_adjoint(cx_problem* p, const T* g, const T* seed_u, const T
             const T* in = reinterpret_cast<const T*>(p->ckpt_slot(s));
             for (int n = n0; n < n1; ++n) {
                 FwdArgs<T> A{};
+                A.status = p->at<int>(p->lay.off_status);
                 T* out = p->at<T>((n % 2) ? Ly.off_popB : Ly.off_popA);
                 set_planes(p, A.pin, in);
                 set_planes(p, A.pout, out);
@@ -249,6 +251,7 @@ static cx_status run_adjoint(cx_problem* p, const T* g, const T* seed_u, const T
         range_begin(p, PH_ADJ, &r);
         for (int n = n1 - 1; n >= n0; --n) {
             AdjArgs<T> A{};
+            A.status = p->at<int>(p->lay.off_status);
             A.terminal = (n == Ly.N - 1);
             T* out = p->at<T>((n % 2) ? Ly.off_adjB : Ly.off_adjA);
             if (psi_in) set_planes(p, A.rin, psi_in);
@@ -301,6 +304,7 @@ template <typename T> static cx_status run_step(cx_problem* p, T* g, T* E, cx_st
     int st = 0;
     rc = read_scalars(p, s4, &st);
     if (rc) return rc;
+    if (st & ST_TIMEOUT) return CX_ERR_TIMEOUT;
     if (st & ST_UNSTABLE) return CX_ERR_UNSTABLE;
     const double J0 = s4[0], e2 = s4[2], einf = s4[3];
     double lam = p->have_lam ? 2.0 * p->lam_prev : std::min(1.0, einf > 0.0 ? 1.0 / einf : 1.0);
@@ -357,6 +361,7 @@ template <typename T> static cx_status run_cadj(cx_problem* p, const T* g, T* dJ
             const T* fin = reinterpret_cast<const T*>(p->ckpt_slot(s));
             for (int n = n0; n < n1; ++n) {
                 FwdArgs<T> A{};
+                A.status = p->at<int>(p->lay.off_status);
                 T* out = p->at<T>((n % 2) ? Ly.off_popB : Ly.off_popA);
                 set_planes(p, A.pin, fin);
                 set_planes(p, A.pout, out);
@@ -424,6 +429,7 @@ static cx_status run_tlm(cx_problem* p, const T* g, const T* dg, T* du_out, T* d
         const T* in = reinterpret_cast<const T*>(p->ckpt_slot(s));
         for (int n = n0; n < n1; ++n) { // base recompute with tape
             FwdArgs<T> A{};
+            A.status = p->at<int>(p->lay.off_status);
             T* out = p->at<T>((n % 2) ? Ly.off_popB : Ly.off_popA);
             set_planes(p, A.pin, in);
             set_planes(p, A.pout, out);
@@ -478,6 +484,7 @@ template <typename T> static cx_status run_lma_step(cx_problem* p, T* g, T* E, c
     double s4[4];
     int st = 0;
     if ((rc = read_scalars(p, s4, &st))) return rc;
+    if (st & ST_TIMEOUT) return CX_ERR_TIMEOUT;
     if (st & ST_UNSTABLE) return CX_ERR_UNSTABLE;
     const double J0 = s4[0], e2 = s4[2], einf = s4[3];
     double sesq = 0.0;
@@ -540,6 +547,7 @@ template <typename T> static cx_status run_cg_step(cx_problem* p, T* g, T* work,
         double s4[4];
         int st = 0;
         if ((rc = read_scalars(p, s4, &st))) return rc;
+        if (st & ST_TIMEOUT) return CX_ERR_TIMEOUT;
         if (st & ST_UNSTABLE) return CX_ERR_UNSTABLE;
         CX_CUDA(cudaMemcpyAsync(P, G, n * sizeof(T), cudaMemcpyDeviceToDevice, p->stream));
         J0 = s4[0];
@@ -721,8 +729,23 @@ cx_status cx_set_launch(cx_problem* p, int threads, int blocks) {
     if (rc) return rc;
     rc = set_persistent(p, a, threads, blocks, oa);
     if (rc) return rc;
+    f.row_windows = a.row_windows = p->Lf.row_windows;
+    if (blocks == 0 && threads != 64) { // the row-window kernels at their own residency
+        const int rf = dbl ? forward_rows_occupancy<double>(p->lay.Q, threads)
+                           : forward_rows_occupancy<float>(p->lay.Q, threads);
+        const int ra = dbl ? adjoint_rows_occupancy<double>(p->lay.Q, threads)
+                           : adjoint_rows_occupancy<float>(p->lay.Q, threads);
+        f.rows_grid = std::min<unsigned>(f.grid.x, (unsigned)(p->nsm * rf));
+        a.rows_grid = std::min<unsigned>(a.grid.x, (unsigned)(p->nsm * ra));
+    }
     p->Lf = f;
     p->La = a;
+    return CX_OK;
+}
+
+cx_status cx_set_staging(cx_problem* p, int row_windows) {
+    if (!p || (row_windows != 0 && row_windows != 1)) return CX_ERR_INVALID_ARG;
+    p->Lf.row_windows = p->La.row_windows = row_windows;
     return CX_OK;
 }
 
@@ -940,6 +963,7 @@ cx_status cx_get_norms(cx_problem* p, double* J, double* grad_sq, double* grad_i
     if (J) *J = s4[0];
     if (grad_sq) *grad_sq = s4[2];
     if (grad_inf) *grad_inf = s4[3];
+    if (st & ST_TIMEOUT) return CX_ERR_TIMEOUT;
     if (st & ST_UNSTABLE) return CX_ERR_UNSTABLE;
     return CX_OK;
 }

@@ -244,9 +244,9 @@ __global__ void __launch_bounds__(NT) k_batch(const BRec<T>* __restrict__ recs, 
         cp_async_commit();
         cp_async_wait<1>();
         if constexpr (ADJ)
-            adj_compute<T, Q, NT>(R.C, R.K, adj_args(R, st), cur, odd ? s1 : s0, acc);
+            adj_compute<T, Q, NT>(R.C, R.K, adj_args(R, st), cur, ThreadSlots<T, NT>{odd ? s1 : s0}, acc);
         else
-            fwd_compute<T, Q, NT>(R.C, R.K, fwd_args(R, st, lam, p), cur, odd ? s1 : s0, acc);
+            fwd_compute<T, Q, NT>(R.C, R.K, fwd_args(R, st, lam, p), cur, ThreadSlots<T, NT>{odd ? s1 : s0}, acc);
         if (pn != p || tn >= total) {
             if (st.want_sum) {
                 const int slot = R.slot0 + (run_tile - sh_tile0[p]) * (NT >> 5) + ((int)threadIdx.x >> 5);

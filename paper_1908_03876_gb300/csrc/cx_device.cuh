@@ -460,6 +460,81 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// Where a node's staged values sit in shared memory.  The bodies read
+// population plane j (0..2Q-1) as pop(j, sx), sx = the x offset of the pulled
+// neighbour (-e_x,i forward, +e_x,i adjoint), and node-local value v >= 2Q as
+// val(v).
+//
+// ThreadSlots: per-thread staging; value v of the thread's own node at
+// s[v NT] (s already offset by threadIdx.x); the staging copy resolved sx.
+template <typename T, int NT> struct ThreadSlots {
+    const T* s;
+    __device__ __forceinline__ T pop(int j, int) const { return s[j * NT]; }
+    __device__ __forceinline__ T val(int v) const { return s[v * NT]; }
+};
+// RowWindow: per-block staging of a row segment [x0, x0 + NT): plane j as a
+// window of the source row starting at x0 - H (H = 16 bytes of values),
+// NT + 2H wide, so the thread of node x0 + t pulls from H + t + sx; then the
+// node-local planes, NT each.  s is offset by threadIdx.x.
+template <typename T, int Q, int NT> struct RowWindow {
+    static constexpr int H = 16 / (int)sizeof(T);
+    static constexpr int W = NT + 2 * H;
+    const T* s;
+    __device__ __forceinline__ T pop(int j, int sx) const { return s[j * W + H + sx]; }
+    __device__ __forceinline__ T val(int v) const { return s[2 * Q * W + (v - 2 * Q) * NT]; }
+};
+
+// --------------------------------- bulk copies completed on an mbarrier
+// Every wait is bounded: a wait that gives up returns false and the kernel
+// reports ST_TIMEOUT through the problem's status word.
+constexpr unsigned MBAR_WAIT_LIMIT = 1u << 22;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+// makes the initialised barriers visible to the asynchronous proxy
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+    for (unsigned it = 0; it < MBAR_WAIT_LIMIT; ++it) {
+        uint32_t ok;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(ok)
+                     : "r"(smem_addr(bar)), "r"(parity)
+                     : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+// global -> shared bulk copy: both addresses 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+// Row window of one plane for RowWindow staging: source row `row` (nx
+// values, nx a multiple of H), destination `dst` = the plane's window of
+// NT + 2H values for nodes [x0, x0 + nv); the periodic neighbours of the row
+// ends come from the other end of the row.  Always nv + 2H values in total.
+template <typename T, int NT>
+__device__ __forceinline__ void bulk_row_window(T* dst, const T* row, int x0, int nv, int nx, uint64_t* bar) {
+    constexpr int H = 16 / (int)sizeof(T);
+    const int xa = x0 - H < 0 ? 0 : x0 - H;
+    const int xb = x0 + nv + H > nx ? nx : x0 + nv + H;
+    bulk_g2s(dst + (xa - (x0 - H)), row + xa, (uint32_t)((xb - xa) * sizeof(T)), bar);
+    if (x0 == 0) bulk_g2s(dst, row + nx - H, H * sizeof(T), bar);
+    if (x0 + nv == nx) bulk_g2s(dst + H + nv, row, H * sizeof(T), bar);
+}
+
 // Compensated accumulation of x^2 across the nodes a thread owns, then one
 // warp reduction; lane 0 adds the warp's share to its FP64 slot.
 struct SqAcc {

@@ -22,6 +22,19 @@
 // cp.async copies of its next node's populations and per-node scalars into its
 // own shared-memory slots (two stages), so DRAM latency overlaps the
 // arithmetic without holding registers for loads in flight.
+//
+// Row-window variant (k_forward_rows; steps n >= 1 of grids without solid
+// nodes whose rows are a whole number of 16-byte units): the block stages a
+// row segment at a time.  One thread issues, per population plane, bulk
+// asynchronous copies of the source row window (the segment widened by 16
+// bytes on each side, periodic ends taken from the other end of the row) and
+// of the node-local planes, all completing on the stage's mbarrier; every
+// thread then pulls its populations from the shared windows.  Two stages:
+// the copies of segment s+1 run while segment s is computed.  This replaces
+// the per-node address arithmetic and 4-byte copies of the per-thread
+// pipeline with a few dozen instructions per segment.
+#include <algorithm>
+
 #include "cx_fwd_body.cuh"
 
 namespace cx {
@@ -46,7 +59,7 @@ __global__ void __launch_bounds__(NT) k_forward(const CxConst C, const KConst<T>
         if (it.valid()) fwd_stage<T, Q, NT, FwdArgs<T>>(C, A, nxt, odd ? s0 : s1);
         cp_async_commit();
         cp_async_wait<1>(); // this thread's copies for the current node have landed
-        fwd_compute<T, Q, NT, FwdArgs<T>>(C, KC, A, cur, odd ? s1 : s0, acc);
+        fwd_compute<T, Q, NT, FwdArgs<T>>(C, KC, A, cur, ThreadSlots<T, NT>{odd ? s1 : s0}, acc);
         cur = nxt;
         odd = !odd;
     }
@@ -89,9 +102,157 @@ static cudaError_t launch_q(const CxConst& C, const KConst<T>& K, const FwdArgs<
     }
 }
 
+// Bulk copies of one row segment's stage (issued by one thread): the 2Q
+// population windows, the angle (rotated tensors), g and E (whole-grid
+// control) and Phi^{n-1}.
+template <typename T, int Q, int NT>
+__device__ __forceinline__ void fwd_issue_rows(const CxConst& C, const FwdArgs<T>& A, int y, int x0, T* st,
+                                               uint64_t* bar) {
+    using L = Lat<Q>;
+    using RW = RowWindow<T, Q, NT>;
+    const int nx = C.nx, nv = min(NT, nx - x0);
+    const int rm = y == 0 ? C.ny - 1 : y - 1, rp = y == C.ny - 1 ? 0 : y + 1;
+    const bool rot = C.aniso == CX_ANISO_ROTATED, gb = A.g && C.ctrl_full, eb = A.E && C.ctrl_full;
+    const uint32_t nb = (uint32_t)nv * sizeof(T);
+    mbar_expect_tx(bar, (uint32_t)(2 * Q * (nv + 2 * RW::H)) * sizeof(T) + nb * (1u + rot + gb + eb));
+#pragma unroll
+    for (int j = 0; j < 2 * Q; ++j) {
+        const int i = j < Q ? j : j - Q;
+        const int ys = L::ey(i) > 0 ? rm : (L::ey(i) < 0 ? rp : y); // pull from x - e_i
+        bulk_row_window<T, NT>(st + j * RW::W, A.in(j) + (size_t)ys * nx, x0, nv, nx, bar);
+    }
+    T* const loc = st + 2 * Q * RW::W;
+    const size_t k0 = (size_t)y * nx + x0;
+    if (rot) bulk_g2s(loc, reinterpret_cast<const T*>(C.theta) + k0, nb, bar);
+    if (gb) bulk_g2s(loc + NT, A.g + k0, nb, bar);
+    if (eb) bulk_g2s(loc + 2 * NT, A.E + k0, nb, bar);
+    bulk_g2s(loc + 3 * NT, A.phi + k0, nb, bar);
+}
+
+// g and E of a controlled node when the control window is not the whole grid:
+// per-thread copies into the node's own slots.
+template <typename T, int Q, int NT>
+__device__ __forceinline__ void fwd_stage_ctrl(const CxConst& C, const FwdArgs<T>& A, const NodeIdx& nd, T* st) {
+    using RW = RowWindow<T, Q, NT>;
+    if (C.ctrl_full || !nd.ctrl) return;
+    T* const loc = st + 2 * Q * RW::W + threadIdx.x;
+    if (A.g) cp_async(loc + NT, A.g + nd.c);
+    if (A.E) cp_async(loc + 2 * NT, A.E + nd.c);
+}
+
+template <typename T, int Q, int NT> constexpr int fwd_rows_stage_values() {
+    return 2 * Q * RowWindow<T, Q, NT>::W + 4 * NT;
+}
+template <typename T, int Q, int NT> constexpr size_t fwd_rows_smem() {
+    return (size_t)2 * fwd_rows_stage_values<T, Q, NT>() * sizeof(T) + 2 * sizeof(uint64_t);
+}
+
+template <typename T, int Q, int NT>
+__global__ void __launch_bounds__(NT) k_forward_rows(const CxConst C, const KConst<T> KC, const FwdArgs<T> A) {
+    using RW = RowWindow<T, Q, NT>;
+    constexpr int SV = fwd_rows_stage_values<T, Q, NT>();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* const st0 = reinterpret_cast<T*>(smem_raw);
+    T* const st1 = st0 + SV;
+    uint64_t* const bar = reinterpret_cast<uint64_t*>(st1 + SV);
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    typename SqAccT<T>::type acc;
+    ChunkIter<NT> it(C);
+    NodeIdx cur = it.valid() ? it.node(C) : no_node();
+    allow_next_grid();
+    wait_prior_grid(); // the previous step's populations and node state are complete
+    if (it.valid()) {
+        if (threadIdx.x == 0) fwd_issue_rows<T, Q, NT>(C, A, it.y, it.seg * NT, st0, &bar[0]);
+        fwd_stage_ctrl<T, Q, NT>(C, A, cur, st0);
+    }
+    cp_async_commit();
+    unsigned phase = 0; // bit b: parity of stage b's next completion
+    int b = 0;          // stage of the current segment
+    bool ok = true;
+    while (it.valid()) {
+        it.next();
+        const NodeIdx nxt = it.valid() ? it.node(C) : no_node();
+        T* const sn = b ? st0 : st1;
+        if (it.valid()) { // stage b^1 is free: every thread passed the barrier that ended its last use
+            if (threadIdx.x == 0) fwd_issue_rows<T, Q, NT>(C, A, it.y, it.seg * NT, sn, &bar[b ^ 1]);
+            fwd_stage_ctrl<T, Q, NT>(C, A, nxt, sn);
+        }
+        cp_async_commit();
+        cp_async_wait<1>();
+        ok = mbar_wait(&bar[b], (phase >> b) & 1u);
+        phase ^= 1u << b;
+        if (ok) fwd_compute<T, Q, NT, FwdArgs<T>>(C, KC, A, cur, RW{(b ? st1 : st0) + threadIdx.x}, acc);
+        if (__syncthreads_or(!ok)) { // all threads leave together when a stage never completed
+            ok = false;
+            break;
+        }
+        cur = nxt;
+        b ^= 1;
+    }
+    if (!ok) {
+        // bounded waits for the copies still in flight, then report
+        if (it.valid()) mbar_wait(&bar[b ^ 1], (phase >> (b ^ 1)) & 1u);
+        mbar_wait(&bar[b], ((phase >> b) & 1u) ^ 1u);
+        if (threadIdx.x == 0 && A.status) atomicOr(A.status, ST_TIMEOUT);
+    }
+    cp_async_wait<0>();
+    if (A.gsq_part) acc.flush(A.gsq_part + blockIdx.x * (NT >> 5) + (threadIdx.x >> 5), nullptr);
+}
+
+// a step the row-window kernel can take: pulled populations (n >= 1), no
+// solid nodes, rows a whole number of 16-byte units, 16-byte aligned planes
+template <typename T> static bool rows_eligible(const CxConst& C, const FwdArgs<T>& A, const Launch& L) {
+    constexpr int H = 16 / (int)sizeof(T);
+    auto al = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; };
+    if (!L.row_windows || A.n == 0 || C.has_solid || C.nx % H != 0 || !al(A.phi)) return false;
+    if (L.block.x != 128 && L.block.x != 256) return false;
+    for (int j = 0; j < 2 * C.Q; ++j)
+        if (!al(A.pin[j])) return false;
+    if (C.aniso == CX_ANISO_ROTATED && !al(C.theta)) return false;
+    if (C.ctrl_full && ((A.g && !al(A.g)) || (A.E && !al(A.E)))) return false;
+    return true;
+}
+
+template <typename T, int Q, int NT>
+static cudaError_t launch_rows_qn(const CxConst& C, const KConst<T>& K, const FwdArgs<T>& A, const Launch& L,
+                                  cudaStream_t s) {
+    constexpr size_t smem = fwd_rows_smem<T, Q, NT>();
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e =
+            cudaFuncSetAttribute(k_forward_rows<T, Q, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(L.rows_grid ? std::min(L.rows_grid, L.grid.x) : L.grid.x);
+    cfg.blockDim = L.block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_forward_rows<T, Q, NT>, C, K, A);
+}
+
+template <typename T, int Q>
+static cudaError_t launch_rows_q(const CxConst& C, const KConst<T>& K, const FwdArgs<T>& A, const Launch& L,
+                                 cudaStream_t s) {
+    return L.block.x == 128 ? launch_rows_qn<T, Q, 128>(C, K, A, L, s) : launch_rows_qn<T, Q, 256>(C, K, A, L, s);
+}
+
 template <typename T>
 cudaError_t launch_forward(const CxConst& C, const KConst<T>& K, const FwdArgs<T>& A, const Launch& L,
                            cudaStream_t s) {
+    if (rows_eligible<T>(C, A, L))
+        return C.Q == 9 ? launch_rows_q<T, 9>(C, K, A, L, s) : launch_rows_q<T, 5>(C, K, A, L, s);
     return C.Q == 9 ? launch_q<T, 9>(C, K, A, L, s) : launch_q<T, 5>(C, K, A, L, s);
 }
 
@@ -117,5 +278,23 @@ template <typename T> int forward_occupancy(int Q, int threads) {
 }
 template int forward_occupancy<float>(int, int);
 template int forward_occupancy<double>(int, int);
+
+
+template <typename T, int Q, int NT> static int rows_occ_qn() {
+    constexpr size_t smem = fwd_rows_smem<T, Q, NT>();
+    cudaFuncSetAttribute(k_forward_rows<T, Q, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_forward_rows<T, Q, NT>, NT, smem) != cudaSuccess) return 1;
+    return nb > 0 ? nb : 1;
+}
+template <typename T, int Q> static int rows_occ_q(int threads) {
+    return threads == 128 ? rows_occ_qn<T, Q, 128>() : rows_occ_qn<T, Q, 256>();
+}
+// resident blocks per SM of the row-window kernel (128 or 256 threads)
+template <typename T> int forward_rows_occupancy(int Q, int threads) {
+    return Q == 9 ? rows_occ_q<T, 9>(threads) : rows_occ_q<T, 5>(threads);
+}
+template int forward_rows_occupancy<float>(int, int);
+template int forward_rows_occupancy<double>(int, int);
 
 } // namespace cx

@@ -62,26 +62,26 @@ __device__ __forceinline__ void fwd_stage(const CxConst& C, const Args& A, const
     }
 }
 
-template <typename T, int Q, int NT, typename Args>
+template <typename T, int Q, int NT, typename Args, typename Stage>
 __device__ __forceinline__ void fwd_compute(const CxConst& C, const KConst<T>& KC, const Args& A, const NodeIdx& nd,
-                                            const T* s, typename SqAccT<T>::type& acc) {
+                                            const Stage& S, typename SqAccT<T>::type& acc) {
     using L = Lat<Q>;
     if (!nd.fluid) return;
     const int y = nd.y, k = nd.k;
     T fu[Q], fv[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        fu[i] = s[i * NT];
-        fv[i] = s[(Q + i) * NT];
+        fu[i] = S.pop(i, -L::ex(i));
+        fv[i] = S.pop(Q + i, -L::ex(i));
     }
     T g = T(0);
     if (nd.ctrl) {
-        if (A.g) g = s[(2 * Q + 1) * NT];
-        if (A.E) g = fma(-A.lam, s[(2 * Q + 2) * NT], g); // same rounding as the accepted update
+        if (A.g) g = S.val(2 * Q + 1);
+        if (A.E) g = fma(-A.lam, S.val(2 * Q + 2), g); // same rounding as the accepted update
         acc.add(g);
     }
     NodeCoef<T> nc;
-    node_coef_th<T>(C, KC, (C.aniso == CX_ANISO_ROTATED) ? s[2 * Q * NT] : T(0), y, k, nc);
+    node_coef_th<T>(C, KC, (C.aniso == CX_ANISO_ROTATED) ? S.val(2 * Q) : T(0), y, k, nc);
 
     // moments m = M f of both species
     T mu[Q], mv[Q];
@@ -92,7 +92,7 @@ __device__ __forceinline__ void fwd_compute(const CxConst& C, const KConst<T>& K
 
     // reaction and control source
     const T Phi = KC.r_vu * Tu + KC.r_vv * Tv + g;
-    const T Phi_prev = (A.n == 0) ? Phi : s[(2 * Q + 3) * NT];
+    const T Phi_prev = (A.n == 0) ? Phi : S.val(2 * Q + 3);
 
     // grad v (reading of C146)
     const T rx = (jvx - nc.ax * Tv) * KC.inv_tau, ry = (jvy - nc.ay * Tv) * KC.inv_tau;

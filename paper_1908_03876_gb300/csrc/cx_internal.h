@@ -45,6 +45,9 @@ template <typename T> struct KConst {
     T c_first, c_now, c_prev; // source coefficients: step 0, steps >= 1 (Phi^n, Phi^{n-1})
 };
 
+// bits of a problem's device status word
+enum { ST_UNSTABLE = 1, ST_TIMEOUT = 2 };
+
 template <typename T> struct FwdArgs {
     const T* pin[18];    // plane j of [2][Q][plane] populations read (pull), or f^0 read locally at n = 0
     T* pout[18];         // plane j of the post-collision populations of step n
@@ -55,6 +58,7 @@ template <typename T> struct FwdArgs {
     T lam;
     T* tape;             // [3][plane] (u^n, G_x^n, G_y^n) or null
     double* gsq_part;    // per-warp partial of sum (g^n)^2 (accumulated over steps), or null
+    int* status;         // status word (ST_TIMEOUT from the bulk-staged kernel), or null
     int n;               // time step index
     __device__ __forceinline__ const T* in(int j) const { return pin[j]; }
     __device__ __forceinline__ T* out(int j) const { return pout[j]; }
@@ -98,6 +102,7 @@ template <typename T> struct AdjArgs {
     T* dJdg;             // [cny*cnx] output dJ/dg^n
     double* e2_part;     // per-warp partial of sum E^2 (accumulated over steps)
     double* emax_part;   // per-warp partial of max |E| (accumulated over steps)
+    int* status;         // status word (ST_TIMEOUT from the bulk-staged kernel), or null
     int n;
     int terminal;        // n == N-1: psi^{n+1} is the broadcast seed
     int accum;           // time-windowed control: add to the window's gradient (not its last step)
@@ -108,6 +113,8 @@ template <typename T> struct AdjArgs {
 
 struct Launch {
     dim3 grid, block;
+    int row_windows = 1;   // steps that qualify use the row-window (bulk copy) kernels
+    unsigned rows_grid = 0; // blocks of the row-window kernels (0: grid.x)
 };
 
 // kernel launchers (cx_forward.cu / cx_adjoint.cu / cx_misc.cu), one per precision
@@ -116,6 +123,9 @@ template <typename T>
 cudaError_t launch_forward(const CxConst& C, const KConst<T>& K, const FwdArgs<T>& A, const Launch& L, cudaStream_t s);
 template <typename T>
 cudaError_t launch_adjoint(const CxConst& C, const KConst<T>& K, const AdjArgs<T>& A, const Launch& L, cudaStream_t s);
+// resident blocks per SM of the row-window forward / adjoint kernels
+template <typename T> int forward_rows_occupancy(int Q, int threads);
+template <typename T> int adjoint_rows_occupancy(int Q, int threads);
 template <typename T>
 cudaError_t launch_init(const CxConst& C, const double* u0d, const double* v0d, const T* u0, const T* v0, T* P,
                         const Launch& L, cudaStream_t s);

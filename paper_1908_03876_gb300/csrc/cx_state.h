@@ -15,7 +15,6 @@ constexpr int MAX_WARPS = 32768; // warps of a persistent launch (partial-sum sl
 inline size_t up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 enum { PH_FWD = 0, PH_REC = 1, PH_ADJ = 2, PH_OTHER = 3 };
-enum { ST_UNSTABLE = 1 };
 
 struct Layout {
     size_t plane, nctrl, esz;

@@ -107,6 +107,7 @@ cx_status run_static(const cx_problem_desc* d, const CxConst& C, const StaticLay
     nb = std::max(1LL, std::min(nb, (long long)nseg * d->ny));
     Lf.block = dim3(256);
     Lf.grid = dim3((unsigned)nb);
+    Lf.rows_grid = (unsigned)std::min<long long>(nb, (long long)nsm * forward_rows_occupancy<T>(d->lattice, 256));
     const int fw = (int)(nb * 8);
     const KConst<T> K = make_kconst<T>(C, C.Q);
 
@@ -126,6 +127,7 @@ cx_status run_static(const cx_problem_desc* d, const CxConst& C, const StaticLay
     const int win_len = d->ctrl_windows > 0 ? d->n_steps / d->ctrl_windows : 1;
     for (int n = 0; n < d->n_steps; ++n) {
         FwdArgs<T> A{};
+        A.status = status;
         T* out = reinterpret_cast<T*>(ws + ((n % 2) ? Ly.off_PB : Ly.off_PA));
         for (int j = 0; j < 18; ++j) {
             A.pin[j] = j < 2 * C.Q ? in + (size_t)j * Ly.plane : nullptr;

@@ -185,6 +185,11 @@ class Problem:
     def set_launch(self, bx, by):
         _lib.check(self.lib.cx_set_launch(self.h, bx, by), "cx_set_launch")
 
+    def set_staging(self, row_windows=True):
+        """Bulk row-window staging of the lattice kernels (True, the default)
+        or per-thread copies everywhere (False); results are identical."""
+        _lib.check(self.lib.cx_set_staging(self.h, 1 if row_windows else 0), "cx_set_staging")
+
     def set_timing(self, on=True):
         _lib.check(self.lib.cx_set_timing(self.h, 1 if on else 0), "cx_set_timing")
 

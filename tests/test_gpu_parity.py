@@ -143,6 +143,52 @@ def test_launch_shape_independent_bitwise():
             assert np.array_equal(a, b)
 
 
+def _staging_case(case):
+    if case == "aniso32_ragged":   # 200 columns: a partial last row segment for 128 and 256 threads
+        w = W.aniso(200, 48, 14, seed=11, precision=32, ckpt_every=5)
+    elif case == "aniso64_window":  # control on a sub-window: g arrives by per-thread copies
+        w = W.aniso(96, 40, 12, seed=12, precision=64, ckpt_every=4)
+        w.window = (10, 6, 50, 20)
+    elif case == "plain64_q5_windows":
+        w = W.plain64(64, 64, 24, sigma=4.0, Q=5)
+        w.ckpt_every, w.windows = 6, 4
+    else:  # one 16-byte unit per row (nx = 4): every segment touches both periodic ends
+        w = W.aniso(4, 24, 10, seed=13, precision=32, ckpt_every=5)
+    return w
+
+
+@pytest.mark.parametrize("case", ["aniso32_ragged", "aniso64_window", "plain64_q5_windows", "aniso32_nx4"])
+@pytest.mark.parametrize("threads", [128, 256])
+def test_row_window_staging_bitwise(case, threads):
+    """Bulk row-window staging (cp.async.bulk + mbarrier per row segment) and
+    per-thread staging give bitwise identical J, fields and dJ/dg; the
+    row-window result also matches the oracle."""
+    from paper_1908_03876_gb300.problem import Problem
+
+    w = _staging_case(case)
+    g = w.random_control(21, 0.02)
+    outs = []
+    for rows in (True, False):
+        p = Problem(w)
+        p.set_launch(threads, 0)
+        p.set_staging(rows)
+        J = float(p.forward(g).item())
+        E = p.adjoint(g)
+        u, v = p.fields()
+        torch.cuda.synchronize()
+        outs.append((J, u.cpu().numpy(), v.cpu().numpy(), E.cpu().numpy()))
+    assert outs[0][0] == outs[1][0]
+    for a, b in zip(outs[0][1:], outs[1][1:]):
+        assert np.array_equal(a, b)
+    po = oracle.from_workload(w)
+    Jo, uo, _ = oracle.forward(po, g)
+    _, Eo, _ = oracle.adjoint(po, g)
+    tol_f, tol_g = (TOL64, TOL64) if w.precision == 64 else (TOL32_FIELD, TOL32_GRAD)
+    eJ, eu, eE = abs(outs[0][0] - Jo) / abs(Jo), rel(outs[0][1], uo), rel(outs[0][3], Eo)
+    print(f"[row windows {case} t{threads}] rel err: J {eJ:.2e} u {eu:.2e} dJ/dg {eE:.2e}")
+    assert eJ < tol_f and eu < tol_f and eE < tol_g
+
+
 def test_repeated_adjoint_and_state():
     """A second adjoint after one forward repeats the first (tape bookkeeping);
     adjoint before any forward is refused."""
