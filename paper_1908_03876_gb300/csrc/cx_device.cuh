@@ -485,9 +485,16 @@ template <typename T, int Q, int NT> struct RowWindow {
 };
 
 // --------------------------------- bulk copies completed on an mbarrier
-// Every wait is bounded: a wait that gives up returns false and the kernel
-// reports ST_TIMEOUT through the problem's status word.
-constexpr unsigned MBAR_WAIT_LIMIT = 1u << 22;
+// Every wait is bounded in time (MBAR_WAIT_NS of the global timer): a wait
+// that gives up returns false, the kernel reports ST_TIMEOUT through the
+// problem's status word, and later launches that see the bit return at once.
+constexpr unsigned long long MBAR_WAIT_NS = 200000000ull; // 0.2 s
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+    return t;
+}
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
@@ -501,17 +508,28 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
                  : "memory");
 }
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    uint32_t ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                 " selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok)
+                 : "r"(smem_addr(bar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
-    for (unsigned it = 0; it < MBAR_WAIT_LIMIT; ++it) {
-        uint32_t ok;
-        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-                     " selp.u32 %0, 1, 0, p;\n}\n"
-                     : "=r"(ok)
-                     : "r"(smem_addr(bar)), "r"(parity)
-                     : "memory");
-        if (ok) return true;
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (unsigned it = 1;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 63u) == 0 && global_ns() - t0 > MBAR_WAIT_NS) return false;
     }
-    return false;
+}
+// true in every thread of the block when an earlier launch recorded a
+// timeout (read by thread 0, broadcast by the barrier, which also publishes
+// the block's mbarrier initialisation)
+__device__ __forceinline__ bool block_sees_timeout(const int* status) {
+    return __syncthreads_or(threadIdx.x == 0 && status && (*(volatile const int*)status & ST_TIMEOUT)) != 0;
 }
 // global -> shared bulk copy: both addresses 16-byte aligned, bytes a multiple of 16
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {

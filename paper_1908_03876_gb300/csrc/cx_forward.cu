@@ -160,12 +160,12 @@ __global__ void __launch_bounds__(NT) k_forward_rows(const CxConst C, const KCon
         mbar_init(&bar[1], 1);
         mbar_init_fence();
     }
-    __syncthreads();
     typename SqAccT<T>::type acc;
     ChunkIter<NT> it(C);
     NodeIdx cur = it.valid() ? it.node(C) : no_node();
     allow_next_grid();
     wait_prior_grid(); // the previous step's populations and node state are complete
+    if (block_sees_timeout(A.status)) return;
     if (it.valid()) {
         if (threadIdx.x == 0) fwd_issue_rows<T, Q, NT>(C, A, it.y, it.seg * NT, st0, &bar[0]);
         fwd_stage_ctrl<T, Q, NT>(C, A, cur, st0);

@@ -408,3 +408,75 @@ def test_aniso1024_fp32_full_size_sampled():
     print(f"aniso1024 2000 steps: J={J.item():.6e}, u-mass drift {abs(massN / mass0 - 1):.2e}")
     assert np.isfinite(J.item())
     assert abs(massN / mass0 - 1) < 1e-5
+
+
+def _crop(w, x0, y0, nx, ny, N, k):
+    """The sub-problem on [x0, x0 + nx) x [y0, y0 + ny) of workload w (inside
+    its control window), periodic at its own edges: its nodes farther than
+    2N from the crop's edges see exactly the full problem's data for N steps
+    (one lattice link per step in the forward and again in the adjoint)."""
+    from dataclasses import replace
+
+    wx0, wy0, wcx, wcy = w.win
+    assert wx0 <= x0 and x0 + nx <= wx0 + wcx and wy0 <= y0 and y0 + ny <= wy0 + wcy
+    sl = (slice(y0, y0 + ny), slice(x0, x0 + nx))
+    cm = None if w.cmask is None else w.cmask[y0 - wy0:y0 - wy0 + ny, x0 - wx0:x0 - wx0 + nx].copy()
+    return replace(w, nx=nx, ny=ny, N=N, ckpt_every=k, theta=w.theta[sl].copy(),
+                   solid=None if w.solid is None else w.solid[sl].copy(), u0=w.u0[sl].copy(),
+                   v0=w.v0[sl].copy(), u_tgt=w.u_tgt[sl].copy(), window=(0, 0, nx, ny), cmask=cm)
+
+
+def test_geometry4096_fp32_full_size_sampled():
+    """4096x4096 D2Q9 FP32 complex geometry (random discs, 20% solid, control
+    on the 256x256 window) in the benchmark's launch configuration.
+    (1) Three steps on the full grid: u^N, v^N and dJ/dg on a 128x128 patch
+    inside the control window against the oracle run on that patch (nodes at
+    least 10 links from the patch edges, which the patch's own periodic edges
+    cannot reach in 2 x 3 steps).  (2) The full 5000 steps (checkpoint every
+    100): J and the gradient finite, the gradient zero on solid window nodes,
+    and u-mass conserved (bounce-back walls, and the chemotactic source has
+    zero mass)."""
+    from paper_1908_03876_gb300.problem import Problem
+
+    N, m = 3, 10
+    wf = W.geometry(N=N, ckpt_every=2)
+    wx0, wy0 = wf.win[0], wf.win[1]
+    g = wf.random_control(12, 0.02)
+    p = Problem(wf)
+    J = p.forward(g)
+    E = p.adjoint(g)
+    u, v = p.fields()
+    torch.cuda.synchronize()
+    x0, y0, n = 65, wy0 + 128, 128  # a patch whose interior is 30% solid
+    wc = _crop(wf, x0, y0, n, n, N, 2)
+    gc = g[:, y0 - wy0:y0 - wy0 + n, x0 - wx0:x0 - wx0 + n].copy()
+    assert wc.solid[m:-m, m:-m].mean() > 0.2, "the patch should contain solid nodes"
+    po = oracle.from_workload(wc)
+    _, uo, vo = oracle.forward(po, gc)
+    _, Eo, _ = oracle.adjoint(po, gc)
+    ins = (slice(m, n - m), slice(m, n - m))
+    ug = u[y0:y0 + n, x0:x0 + n].cpu().numpy()[ins]
+    vg = v[y0:y0 + n, x0:x0 + n].cpu().numpy()[ins]
+    Eg = E[:, y0 - wy0:y0 - wy0 + n, x0 - wx0:x0 - wx0 + n].cpu().numpy()[(slice(None),) + ins]
+    eu, ev, eE = rel(ug, uo[ins]), rel(vg, vo[ins]), rel(Eg, Eo[(slice(None),) + ins])
+    print(f"geometry4096 fp32, 3 steps, patch interior: u {eu:.2e} v {ev:.2e} dJ/dg {eE:.2e}; J={J.item():.6e}")
+    assert eu < TOL32_FIELD and ev < TOL32_FIELD and eE < TOL32_GRAD
+    del p, u, v, E
+    torch.cuda.empty_cache()
+
+    from dataclasses import replace
+
+    wl = replace(wf, N=5000, ckpt_every=100)  # the full workload: 5000 steps, checkpoint every 100
+    p = Problem(wl)
+    gl = torch.as_tensor(wl.random_control(13, 0.01), dtype=torch.float32, device="cuda")
+    E = p.gradient(gl)
+    J, _, ginf = p.norms()
+    u, _ = p.fields()
+    solid_win = torch.as_tensor(1 - wl.cmask, device="cuda").bool()
+    mass0 = float(np.sum(wl.u0 * (1 - wl.solid)))
+    massN = float(u.double().sum().item())
+    print(f"geometry4096 5000 steps: J={J:.6e}, max|dJ/dg|={ginf:.3e}, u-mass drift {abs(massN / mass0 - 1):.2e}")
+    assert np.isfinite(J) and np.isfinite(ginf) and ginf > 0
+    assert bool(torch.isfinite(E).all())
+    assert float(E[:, solid_win].abs().max()) == 0.0
+    assert abs(massN / mass0 - 1) < 1e-4
