@@ -108,15 +108,15 @@ def _traffic(kernel):
         return None
 
 
-def _batch_traffic(nodes):
+def _batch_traffic(nodes, kernel="k_batch_rows"):
     """DRAM bytes of one batched forward launch over `nodes` nodes, from the
-    per-node figure of the committed k_batch capture (its sources unchanged)."""
+    per-node figure of the committed capture of `kernel` (its sources unchanged)."""
     try:
         from paper_1908_03876_gb300.kernel_hash import kernel_source_hash
 
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
-            ent = json.load(fh).get("k_batch")
-        if not ent or ent.get("sources_hash") != kernel_source_hash("k_batch"):
+            ent = json.load(fh).get(kernel)
+        if not ent or ent.get("sources_hash") != kernel_source_hash(kernel):
             return None
         return ent["forward_dram_bytes_per_node"] * nodes
     except Exception:
@@ -202,6 +202,7 @@ def run_batch(args, rank, world, local):
         allw = W.batch_workloads(args.problems, N=1000, seed=3)
     mine = sharding.my_problems(allw, rank, world)
     b = Batch(mine, device=dev)
+    b.set_staging(args.staging == "rows")
     gs = [torch.as_tensor(w.random_control(500 + i, 0.01), dtype=torch.float32, device=dev) for i, w in enumerate(mine)]
     b.bind(gs)
     t0 = time.perf_counter()
@@ -267,11 +268,13 @@ def run_batch(args, rank, world, local):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 reductions)", "data": "synthetic (seeded)",
             "config": {"workload": f"batch: {args.problems} problems, nx, ny in {{64,128,256,512}}, 1000 steps, "
                                    "checkpoint every 100, one persistent launch per step, CUDA graph",
-                       "nodes": all_nodes, "tiles": cfg, "autotune_s": t_tune,
+                       "nodes": all_nodes, "tiles": cfg, "autotune_s": t_tune, "staging": args.staging,
                        "l2": "inputs larger than L2"},
             "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                         "traffic": _batch_traffic(all_nodes / world),
-                         "kernel": "k_batch (all lattice launches of the step)",
+                         "traffic": _batch_traffic(all_nodes / world,
+                                                   "k_batch_rows" if args.staging == "rows" else "k_batch"),
+                         "kernel": ("k_batch_rows" if args.staging == "rows" else "k_batch")
+                                   + " (all lattice launches of the step)",
                          "peak_source": peak_kind},
             "per_problem_grad_rel_err_fp32_vs_oracle": {"sample": "6 problems, 6 steps", "max": max(err),
                                                         "values": err},
@@ -523,7 +526,7 @@ def main():
                     help="aniso1024 (default bench line) or batch: 256 independent problems, sizes {64..512}^2, "
                          "1000 steps, one persistent launch per step replayed as a CUDA graph")
     ap.add_argument("--staging", default="rows", choices=["rows", "thread"],
-                    help="aniso1024: bulk row-window staging (default) or per-thread copies")
+                    help="aniso1024 and batch: bulk row-window staging (default) or per-thread copies")
     ap.add_argument("--problems", type=int, default=256)
     ap.add_argument("--ws-train", type=int, default=2000)
     ap.add_argument("--ws-test", type=int, default=200)

@@ -27,7 +27,7 @@ EXPORTS = [
     "cx_batch_workspace_size", "cx_batch_create", "cx_batch_set_initial", "cx_batch_bind", "cx_batch_set_tiles",
     "cx_batch_forward", "cx_batch_gradient", "cx_batch_get_fields", "cx_batch_get_status", "cx_batch_destroy",
     "cx_batch_set_enabled", "cx_batch_step", "cx_batch_adjoint", "cx_batch_axpy", "cx_batch_prepare",
-    "cx_batch_autotune",
+    "cx_batch_autotune", "cx_batch_set_staging",
     "cx_nn_conv_forward", "cx_nn_conv_backward_data", "cx_nn_conv_backward_weight_scratch",
     "cx_nn_conv_backward_weight", "cx_nn_relu_backward", "cx_nn_add", "cx_nn_pool2", "cx_nn_up2", "cx_nn_mse",
     "cx_nn_adam", "cx_nn_cast_bf16", "cx_nn_conv_forward_f32", "cx_nn_smooth", "cx_nn_packed_weights",
@@ -129,6 +129,7 @@ def load():
         "cx_batch_adjoint": [vp, vp, cint, vp],
         "cx_batch_axpy": [vp, vp],
         "cx_batch_prepare": [vp],
+        "cx_batch_set_staging": [vp, cint],
         "cx_batch_autotune": [vp, cint, ctypes.c_char_p, ctypes.POINTER(cint), vp, vp, dp],
         "cx_nn_conv_forward": [vp, vp, vp, vp, cint, cint, cint, cint, cint, cint, cint, vp],
         "cx_nn_conv_forward_f32": [vp, vp, vp, vp, cint, cint, cint, cint, cint, cint, vp],

@@ -78,6 +78,11 @@ class Batch:
         rws = None if rows is None else (ctypes.c_int * self.count)(*rows)
         _lib.check(self.lib.cx_batch_set_tiles(self.h, threads, blocks, arr, rws), "cx_batch_set_tiles")
 
+    def set_staging(self, row_windows=True):
+        """Bulk row-window staging (True, the default) or per-thread copies
+        everywhere (False); results are identical."""
+        _lib.check(self.lib.cx_batch_set_staging(self.h, 1 if row_windows else 0), "cx_batch_set_staging")
+
     def _enter(self):
         # inputs written on the caller's stream are visible to the batch's stream
         self.stream.wait_stream(torch.cuda.current_stream(self.device))

@@ -266,6 +266,226 @@ __global__ void __launch_bounds__(NT) k_batch(const BRec<T>* __restrict__ recs, 
     cp_async_wait<0>();
 }
 
+// ---- row-window form of the batched kernel (no solid nodes in any problem,
+// rows a whole number of 16-byte units; not the first forward step nor the
+// terminal adjoint step).  An item's ty rows x tx columns are staged per
+// population plane as ty row windows (the item's columns widened by 16 bytes
+// per side, periodic ends from the other end of the row) plus the node-local
+// planes, by bulk asynchronous copies that the lanes of warp 0 issue and an
+// mbarrier per stage completes; otherwise the item order, the pipeline depth
+// and the reduction runs are those of k_batch.
+
+// Staged values of one item: thread (tyi, txi) of a tx-wide tile reads plane j
+// at pop + j pw + H + sx (pop offset by tyi (tx + 2H) + txi, pw = ty (tx + 2H))
+// and node-local value v at loc + (v - 2Q) NT (loc offset by threadIdx.x).
+template <typename T, int Q> struct TileWindow {
+    static constexpr int H = 16 / (int)sizeof(T);
+    const T* pops;
+    const T* loc;
+    int pw, nt;
+    __device__ __forceinline__ T pop(int j, int sx) const { return pops[j * pw + H + sx]; }
+    __device__ __forceinline__ T val(int v) const { return loc[(v - 2 * Q) * nt]; }
+};
+
+// population part of a stage: 2Q planes of at most NT / 32 windows (tx >= 32)
+template <typename T, int Q, int NT> constexpr int bwin_pop_values() {
+    return 2 * Q * (NT + 2 * (16 / (int)sizeof(T)) * (NT / 32));
+}
+template <typename T, int Q, int NT, bool ADJ> constexpr int bwin_stage_values() {
+    return bwin_pop_values<T, Q, NT>() + (ADJ ? 6 : 4) * NT;
+}
+template <typename T, int Q, int NT, bool ADJ> constexpr size_t bwin_smem_fixed() {
+    return (size_t)2 * bwin_stage_values<T, Q, NT, ADJ>() * sizeof(T) + 2 * sizeof(uint64_t);
+}
+
+// Issue the copies of item (problem R, tile columns [xt, xt + tx), rows
+// [yb, yb + ty)) into stage st; called by every lane of warp 0.
+template <typename T, int Q, int NT, bool ADJ, typename Args>
+__device__ __forceinline__ void bwin_issue(const BRec<T>& R, const Args& A, int xt, int yb, T* st, uint64_t* bar) {
+    using L = Lat<Q>;
+    constexpr int H = 16 / (int)sizeof(T);
+    constexpr int NL = ADJ ? 6 : 4;
+    const int lane = (int)threadIdx.x & 31;
+    const int nx = R.C.nx, ny = R.C.ny, tx = R.tx, ty = R.ty;
+    const int nv = min(tx, nx - xt), nr = max(0, min(ty, ny - yb)); // nr = 0: rows past the grid, nothing to copy
+    const int wr = tx + 2 * H, pw = ty * wr;
+    const bool rot = R.C.aniso == CX_ANISO_ROTATED, full = R.C.ctrl_full != 0;
+    const T* locsrc[NL];
+    if constexpr (ADJ) {
+        locsrc[0] = A.tape;
+        locsrc[1] = A.tape + R.plane;
+        locsrc[2] = A.tape + 2 * R.plane;
+        locsrc[3] = A.sigma;
+        locsrc[4] = (A.g && full) ? A.g : nullptr;
+        locsrc[5] = rot ? reinterpret_cast<const T*>(R.C.theta) : nullptr;
+    } else {
+        locsrc[0] = rot ? reinterpret_cast<const T*>(R.C.theta) : nullptr;
+        locsrc[1] = (A.g && full) ? A.g : nullptr;
+        locsrc[2] = (A.E && full) ? A.E : nullptr;
+        locsrc[3] = A.phi;
+    }
+    if (lane == 0) {
+        int nl = 0;
+#pragma unroll
+        for (int v = 0; v < NL; ++v) nl += locsrc[v] != nullptr;
+        mbar_expect_tx(bar, (uint32_t)((2 * Q * nr * (nv + 2 * H) + nl * nr * nv) * (int)sizeof(T)));
+    }
+    __syncwarp();
+    for (int idx = lane; idx < 2 * Q * nr; idx += 32) {
+        const int j = idx / nr, r = idx - j * nr;
+        const int i = j < Q ? j : j - Q;
+        const int y = yb + r;
+        const int dy = ADJ ? L::ey(i) : -L::ey(i); // pull from x + e_i (adjoint) or x - e_i (forward)
+        const int ys = y + dy < 0 ? ny - 1 : (y + dy >= ny ? 0 : y + dy);
+        bulk_row_window<T, NT>(st + j * pw + r * wr, A.in(j) + (size_t)ys * nx, xt, nv, nx, bar);
+    }
+    T* const loc = st + bwin_pop_values<T, Q, NT>();
+#pragma unroll
+    for (int v = 0; v < NL; ++v)
+        if (locsrc[v] && lane < nr)
+            bulk_g2s(loc + v * NT + lane * tx, locsrc[v] + (size_t)(yb + lane) * nx + xt, nv * sizeof(T), bar);
+}
+
+// g (and E) of a controlled node when the control window is not the whole
+// grid: per-thread copies into the node's own local slots.
+template <typename T, int Q, int NT, bool ADJ, typename Args>
+__device__ __forceinline__ void bwin_stage_ctrl(const BRec<T>& R, const Args& A, const NodeIdx& nd, T* st) {
+    if (R.C.ctrl_full || !nd.ctrl) return;
+    T* const loc = st + bwin_pop_values<T, Q, NT>() + threadIdx.x;
+    if constexpr (ADJ) {
+        if (A.g) cp_async(loc + 4 * NT, A.g + nd.c);
+    } else {
+        if (A.g) cp_async(loc + NT, A.g + nd.c);
+        if (A.E) cp_async(loc + 2 * NT, A.E + nd.c);
+    }
+}
+
+template <typename T, int Q, int NT, bool ADJ>
+__global__ void __launch_bounds__(NT) k_batch_rows(const BRec<T>* __restrict__ recs, const int* __restrict__ tile0,
+                                                   int count, int total, BStep st, double* sum_slots,
+                                                   double* max_slots, const int* __restrict__ active,
+                                                   const T* __restrict__ lam, int* status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int SV = bwin_stage_values<T, Q, NT, ADJ>();
+    T* const st0 = reinterpret_cast<T*>(smem_raw);
+    T* const st1 = st0 + SV;
+    uint64_t* const bar = reinterpret_cast<uint64_t*>(st1 + SV);
+    int* sh_tile0 = reinterpret_cast<int*>(bar + 2);
+    for (int i = threadIdx.x; i <= count; i += NT) sh_tile0[i] = tile0[i];
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_init_fence();
+    }
+    allow_next_grid();
+    wait_prior_grid();
+    if (block_sees_timeout(status)) return; // the barrier also publishes sh_tile0 and the mbarriers
+
+    const int G = gridDim.x;
+    auto next_live = [&](int tt, int& q) -> int {
+        while (tt < total) {
+            q = find_problem(sh_tile0, count, tt);
+            if (__ldg(active + q)) return tt;
+            tt += ((sh_tile0[q + 1] - tt + G - 1) / G) * G;
+        }
+        return total;
+    };
+    // copies of item (tile tt of problem q, rows step jj) into stage stg, by warp 0
+    auto issue = [&](int q, int tt, int jj, T* stg, uint64_t* bb) {
+        if (threadIdx.x >= 32) return;
+        const BRec<T>& R = recs[q];
+        const int local = tt - sh_tile0[q];
+        const int tyi = local / R.tiles_x, txi = local - tyi * R.tiles_x;
+        const int xt = txi * R.tx, yb = tyi * R.ty * R.rr + jj * R.ty;
+        if constexpr (ADJ)
+            bwin_issue<T, Q, NT, true>(R, adj_args(R, st), xt, yb, stg, bb);
+        else
+            bwin_issue<T, Q, NT, false>(R, fwd_args(R, st, lam, q), xt, yb, stg, bb);
+    };
+    auto stage_ctrl = [&](int q, const NodeIdx& nd, T* stg) {
+        const BRec<T>& R = recs[q];
+        if constexpr (ADJ)
+            bwin_stage_ctrl<T, Q, NT, true>(R, adj_args(R, st), nd, stg);
+        else
+            bwin_stage_ctrl<T, Q, NT, false>(R, fwd_args(R, st, lam, q), nd, stg);
+    };
+
+    int p = 0;
+    int t = next_live(blockIdx.x, p);
+    int j = 0, x = 0, y = 0;
+    NodeIdx cur = no_node();
+    if (t < total) {
+        tile_origin(recs[p], t - sh_tile0[p], x, y);
+        cur = node_at(recs[p], x, y);
+        issue(p, t, 0, st0, &bar[0]);
+        stage_ctrl(p, cur, st0);
+    }
+    cp_async_commit();
+    int run_tile = t;
+    typename SqAccT<T>::type acc;
+    unsigned phase = 0; // bit b: parity of stage b's next completion
+    int b = 0;          // stage of the current item
+    bool ok = true, next_issued = false;
+    while (t < total) {
+        const BRec<T>& R = recs[p];
+        int tn = t, pn = p, jn = j + 1, xn = x, yn = y + R.ty;
+        if (jn == R.rr) {
+            jn = 0;
+            tn = next_live(t + G, pn);
+            if (tn < total) tile_origin(recs[pn], tn - sh_tile0[pn], xn, yn);
+        }
+        NodeIdx nxt = no_node();
+        T* const sn = b ? st0 : st1;
+        if (tn < total) { // stage b^1 is free: every thread passed the barrier that ended its last use
+            nxt = node_at(recs[pn], xn, yn);
+            issue(pn, tn, jn, sn, &bar[b ^ 1]);
+            stage_ctrl(pn, nxt, sn);
+        }
+        next_issued = tn < total;
+        cp_async_commit();
+        cp_async_wait<1>();
+        ok = mbar_wait(&bar[b], (phase >> b) & 1u);
+        phase ^= 1u << b;
+        if (ok) {
+            constexpr int H = 16 / (int)sizeof(T);
+            const T* sc = b ? st1 : st0;
+            const int tyi = (int)threadIdx.x >> R.tx_shift, txi = (int)threadIdx.x & (R.tx - 1);
+            const TileWindow<T, Q> S{sc + tyi * (R.tx + 2 * H) + txi, sc + bwin_pop_values<T, Q, NT>() + threadIdx.x,
+                                     R.ty * (R.tx + 2 * H), NT};
+            if constexpr (ADJ)
+                adj_compute<T, Q, NT>(R.C, R.K, adj_args(R, st), cur, S, acc);
+            else
+                fwd_compute<T, Q, NT>(R.C, R.K, fwd_args(R, st, lam, p), cur, S, acc);
+        }
+        if (__syncthreads_or(!ok)) { // all threads leave together when a stage never completed
+            ok = false;
+            break;
+        }
+        if (pn != p || tn >= total) {
+            if (st.want_sum) {
+                const int slot = R.slot0 + (run_tile - sh_tile0[p]) * (NT >> 5) + ((int)threadIdx.x >> 5);
+                acc.flush(sum_slots + slot, max_slots ? max_slots + slot : nullptr);
+            }
+            acc = typename SqAccT<T>::type{};
+            run_tile = tn;
+        }
+        t = tn;
+        p = pn;
+        j = jn;
+        x = xn;
+        y = yn;
+        cur = nxt;
+        b ^= 1;
+    }
+    if (!ok) {
+        // bounded waits for the copies still in flight, then report
+        if (next_issued) mbar_wait(&bar[b ^ 1], (phase >> (b ^ 1)) & 1u);
+        mbar_wait(&bar[b], ((phase >> b) & 1u) ^ 1u);
+        if (threadIdx.x == 0 && status) atomicOr(status, ST_TIMEOUT);
+    }
+    cp_async_wait<0>();
+}
+
 // Per-problem fixed-order sums: J_p = cost_p + alpha_p * sum(gsq slots) (mode 0)
 // or (sum E^2, max |E|) (mode 1).  One block per problem.
 struct BFin {
@@ -377,6 +597,9 @@ struct BatchHost {
     bool J_on_device = false;      // ... or in out[0..count) (after cx_batch_forward / _gradient)
     bool fwd_at_g = false;         // every enabled problem's forward state (checkpoints, last
                                    // tape, final populations) belongs to its current control
+    int row_windows = 1;           // steps that qualify use k_batch_rows
+    bool rows_ok = false;          // every problem qualifies (no solids, aligned rows and controls)
+    int rows_blocks[2] = {0, 0};   // persistent blocks of k_batch_rows (forward, adjoint)
 };
 
 enum { G_FWD = 0, G_GRAD = 1, G_TRIAL = 2, G_ADJ = 3 };
@@ -458,6 +681,17 @@ template <typename T> cx_status upload_table(BatchHost& h) {
         fin[i].nslots = slot0[i + 1] - slot0[i];
         fin[i].alpha = p->C.alpha;
     }
+    // row-window staging: no solid nodes, rows of whole 16-byte units, 16-byte aligned control arrays
+    h.rows_ok = true;
+    for (int i = 0; i < h.count; ++i) {
+        const cx_problem* p = h.probs[i];
+        auto al = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; };
+        const bool gi = h.g.empty() || !h.g[i] || al(h.g[i]);
+        const bool ei = h.dJdg.empty() || !h.dJdg[i] || al(h.dJdg[i]);
+        if (p->C.has_solid || p->d.nx % (int)(16 / sizeof(T)) != 0 || !gi || !ei ||
+            ((size_t)p->lay.plane * sizeof(T)) % 16 != 0)
+            h.rows_ok = false;
+    }
     if (cudaMemcpy(h.ws + h.off_rec, recs.data(), sizeof(BRec<T>) * h.count, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(h.ws + h.off_tile0, tile0.data(), sizeof(int) * (h.count + 1), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(h.ws + h.off_fin, fin.data(), sizeof(BFin) * h.count, cudaMemcpyHostToDevice) != cudaSuccess)
@@ -501,7 +735,74 @@ cudaError_t launch_bq(const BatchHost& h, const BStep& st, int blocks) {
                               reinterpret_cast<const T*>(h.ws + h.off_lam));
 }
 
+template <typename T, int Q, int NT, bool ADJ> size_t bwin_smem(int count) {
+    return bwin_smem_fixed<T, Q, NT, ADJ>() + sizeof(int) * (count + 1);
+}
+
+template <typename T, int Q, int NT, bool ADJ>
+cudaError_t launch_bq_rows(const BatchHost& h, const BStep& st, int blocks) {
+    const size_t smem = bwin_smem<T, Q, NT, ADJ>(h.count);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_batch_rows<T, Q, NT, ADJ>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = h.stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    double* sums = reinterpret_cast<double*>(h.ws + h.off_sums);
+    double* maxs = ADJ ? reinterpret_cast<double*>(h.ws + h.off_maxs) : nullptr;
+    return cudaLaunchKernelEx(&cfg, k_batch_rows<T, Q, NT, ADJ>, reinterpret_cast<const BRec<T>*>(h.ws + h.off_rec),
+                              reinterpret_cast<const int*>(h.ws + h.off_tile0), h.count, h.total_tiles, st, sums,
+                              maxs, reinterpret_cast<const int*>(h.ws + h.off_active),
+                              reinterpret_cast<const T*>(h.ws + h.off_lam),
+                              reinterpret_cast<int*>(h.ws + h.off_status));
+}
+
+// resident blocks per SM of k_batch_rows for this batch's table size
+template <typename T, int Q, int NT, bool ADJ> int bwin_occupancy(int count) {
+    const size_t smem = bwin_smem<T, Q, NT, ADJ>(count);
+    if (smem > 200 * 1024) return 0;
+    cudaFuncSetAttribute(k_batch_rows<T, Q, NT, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_rows<T, Q, NT, ADJ>, NT, smem) != cudaSuccess)
+        return 0;
+    return nb;
+}
+template <typename T, bool ADJ> int bwin_occ(int Q, int threads, int count) {
+    if (Q == 9)
+        return threads == 128 ? bwin_occupancy<T, 9, 128, ADJ>(count) : bwin_occupancy<T, 9, 256, ADJ>(count);
+    return threads == 128 ? bwin_occupancy<T, 5, 128, ADJ>(count) : bwin_occupancy<T, 5, 256, ADJ>(count);
+}
+
+// persistent blocks of the row-window kernels (0: they do not fit; blocks > 0: the caller's count)
+void set_rows_blocks(BatchHost& h, int threads, int blocks) {
+    for (int a = 0; a < 2; ++a) {
+        const int ro = h.esz == 8 ? (a ? bwin_occ<double, true>(h.Q, threads, h.count)
+                                       : bwin_occ<double, false>(h.Q, threads, h.count))
+                                  : (a ? bwin_occ<float, true>(h.Q, threads, h.count)
+                                       : bwin_occ<float, false>(h.Q, threads, h.count));
+        h.rows_blocks[a] = ro <= 0 ? 0 : (blocks > 0 ? blocks : h.probs[0]->nsm * ro);
+    }
+}
+
 template <typename T, bool ADJ> cudaError_t launch_b(const BatchHost& h, const BStep& st) {
+    const bool rows = h.row_windows && h.rows_ok && h.rows_blocks[ADJ ? 1 : 0] > 0 && (ADJ ? !st.terminal : st.n > 0);
+    if (rows) {
+        const int rb = std::max(1, std::min(h.rows_blocks[ADJ ? 1 : 0], h.total_tiles));
+        if (h.Q == 9)
+            return h.threads == 128 ? launch_bq_rows<T, 9, 128, ADJ>(h, st, rb) : launch_bq_rows<T, 9, 256, ADJ>(h, st, rb);
+        return h.threads == 128 ? launch_bq_rows<T, 5, 128, ADJ>(h, st, rb) : launch_bq_rows<T, 5, 256, ADJ>(h, st, rb);
+    }
     const int blocks = std::max(1, std::min(h.blocks, h.total_tiles));
     if (h.Q == 9) {
         if (h.threads == 128) return launch_bq<T, 9, 128, ADJ>(h, st, blocks);
@@ -688,7 +989,7 @@ cx_status read_out(BatchHost& h, std::vector<double>& out, int& status) {
                            h.stream));
     B_CUDA(cudaMemcpyAsync(&status, h.ws + h.off_status, sizeof(int), cudaMemcpyDeviceToHost, h.stream));
     B_CUDA(cudaStreamSynchronize(h.stream));
-    return CX_OK;
+    return (status & ST_TIMEOUT) ? CX_ERR_TIMEOUT : CX_OK;
 }
 
 // One Armijo gradient step of every enabled problem (the single-problem rule
@@ -873,6 +1174,7 @@ cx_status time_probe(BatchHost& h, int threads, const std::vector<int>& tx, cons
     h.rr = rr;
     const int occ = forward_occupancy<T>(h.Q, threads);
     h.blocks = h.probs[0]->nsm * occ;
+    set_rows_blocks(h, threads, 0);
     cx_status rc = upload_table<T>(h);
     if (rc) return rc;
     constexpr int REPS = 2;
@@ -1095,6 +1397,7 @@ cx_status cx_batch_set_tiles(cx_batch* b, int threads, int blocks, const int* ti
     h.rr = rr;
     const int occ = h.esz == 8 ? forward_occupancy<double>(h.Q, threads) : forward_occupancy<float>(h.Q, threads);
     h.blocks = blocks > 0 ? blocks : h.probs[0]->nsm * occ;
+    set_rows_blocks(h, threads, blocks);
     drop_graphs(h);
     return h.esz == 8 ? upload_table<double>(h) : upload_table<float>(h);
 }
@@ -1329,6 +1632,7 @@ cx_status cx_batch_get_status(cx_batch* b) {
             cudaSuccess ||
         cudaStreamSynchronize(b->h.stream) != cudaSuccess)
         return CX_ERR_CUDA;
+    if (st & ST_TIMEOUT) return CX_ERR_TIMEOUT;
     return (st & ST_UNSTABLE) ? CX_ERR_UNSTABLE : CX_OK;
 }
 
@@ -1372,6 +1676,13 @@ cx_status cx_batch_autotune(cx_batch* b, int probe_steps, const char* cache_path
     if (rows_out) std::copy(rr.begin(), rr.end(), rows_out);
     if (probe_ms_out) *probe_ms_out = c.ms;
     if (!cached && cache_path && !cache_store(cache_path, sig, c)) return CX_ERR_INTERNAL;
+    return CX_OK;
+}
+
+cx_status cx_batch_set_staging(cx_batch* b, int row_windows) {
+    if (!b || (row_windows != 0 && row_windows != 1)) return CX_ERR_INVALID_ARG;
+    if (b->h.row_windows != row_windows) drop_graphs(b->h);
+    b->h.row_windows = row_windows;
     return CX_OK;
 }
 

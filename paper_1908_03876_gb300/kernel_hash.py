@@ -13,6 +13,8 @@ KERNEL_SOURCES = {
     "k_adjoint_rows": ("cx_device.cuh", "cx_adj_body.cuh", "cx_internal.h", "cx_adjoint.cu"),
     "k_batch": ("cx_device.cuh", "cx_fwd_body.cuh", "cx_adj_body.cuh", "cx_internal.h", "cx_state.h",
                 "cx_batch.cu"),
+    "k_batch_rows": ("cx_device.cuh", "cx_fwd_body.cuh", "cx_adj_body.cuh", "cx_internal.h", "cx_state.h",
+                     "cx_batch.cu"),
     "k_tlm": ("cx_device.cuh", "cx_internal.h", "cx_tlm.cu"),
     "k_cadj": ("cx_device.cuh", "cx_internal.h", "cx_cadj.cu"),
     "nn": ("nn_kernels.cu",),

@@ -236,3 +236,90 @@ def test_batch_seeded_adjoint_and_axpy():
     for i, w in enumerate(ws):
         J0o = oracle.forward(oracle.from_workload(w), before[i] - lam[i] * E[i])[0]
         assert abs(info[i]["J0"] - J0o) <= 1e-12 * abs(J0o)
+
+
+def _aligned(precision=64, N=12, k=5, windows=0):
+    """Problems the row-window batched kernel takes (no solid nodes, nx a
+    whole number of 16-byte units): uneven sizes, heights that leave partial
+    tiles, one problem with its control on a sub-window (g and E staged per
+    thread)."""
+    ws = []
+    for i, (nx, ny) in enumerate([(40, 24), (64, 18), (96, 47), (20, 28), (128, 33)]):
+        w = W.aniso(nx, ny, N, seed=30 + i, precision=precision, ckpt_every=k, chi=-0.02 * (i + 1))
+        w.lam_u = w.lam_v = (0.08, 0.08 / (1 + i))
+        w.windows = windows
+        ws.append(w)
+    ws[2].window = (8, 5, 60, 30)
+    return ws
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("tiles", [None, (256, 32, 4), (128, 64, 3), (256, 128, 16)])
+def test_batch_row_windows_bitwise_and_oracle(precision, tiles):
+    """The row-window batched kernel (bulk copies of each item's row windows,
+    mbarrier per stage) against per-thread staging: J, ||dJ/dg||^2, gradients
+    and fields bitwise equal; FP64 gradients against the oracle."""
+    ws = _aligned(precision)
+    outs = []
+    for rows in (True, False):
+        from paper_1908_03876_gb300.batch import Batch
+
+        b = Batch(ws)
+        b.set_staging(rows)
+        gs = [torch.as_tensor(w.random_control(50 + i, 0.02), dtype=b.dtype, device=b.device)
+              for i, w in enumerate(ws)]
+        b.bind(gs)
+        if tiles is not None:
+            th, tx, r = tiles
+            b.set_tiles(th, 0, [min(tx, th) for _ in ws], [r] * len(ws))
+        J, e2, _ = b.gradient()
+        b.status()
+        fields = [tuple(f.cpu().numpy() for f in b.fields(i)) for i in range(len(ws))]
+        outs.append((J.cpu().numpy().copy(), e2.cpu().numpy().copy(), [E.cpu().numpy().copy() for E in b.E],
+                     fields, [g.cpu().numpy() for g in gs]))
+        b.close()
+    (Jr, e2r, Er, Fr, gr), (Jt, e2t, Et, Ft, _) = outs
+    assert np.array_equal(Jr, Jt) and np.array_equal(e2r, e2t)
+    for i in range(len(ws)):
+        assert np.array_equal(Er[i], Et[i]), i
+        assert np.array_equal(Fr[i][0], Ft[i][0]) and np.array_equal(Fr[i][1], Ft[i][1]), i
+    tol_J, tol_E = (1e-12, 1e-12) if precision == 64 else (1e-4, 1e-3)
+    for i, w in enumerate(ws):
+        Jo, Eo, _ = oracle.adjoint(oracle.from_workload(w), gr[i].astype(np.float64))
+        eJ, eE = abs(Jr[i] - Jo) / abs(Jo), np.linalg.norm(Er[i] - Eo) / np.linalg.norm(Eo)
+        print(f"row windows fp{precision} tiles {tiles} problem {i}: J {eJ:.1e} dJ/dg {eE:.1e}")
+        assert eJ < tol_J and eE < tol_E
+
+
+def test_batch_row_windows_steps_and_windows():
+    """Armijo steps (line-search trial forwards read g - lam E through the row
+    windows) and time-windowed controls with the row-window kernel: controls
+    after two steps bitwise equal to per-thread staging, and the windowed
+    gradient against the oracle."""
+    from paper_1908_03876_gb300.batch import Batch
+
+    ws = _aligned(64, windows=3)
+    res = []
+    for rows in (True, False):
+        b = Batch(ws)
+        b.set_staging(rows)
+        gs = [torch.as_tensor(w.random_control(80 + i, 0.02), dtype=b.dtype, device=b.device)
+              for i, w in enumerate(ws)]
+        b.bind(gs)
+        J, _, _ = b.gradient()
+        J = J.cpu().numpy().copy()
+        if rows:
+            for i, w in enumerate(ws):
+                Jo, Eo, _ = oracle.adjoint(oracle.from_workload(w), gs[i].cpu().numpy())
+                assert abs(J[i] - Jo) <= 1e-12 * abs(Jo)
+                assert np.linalg.norm(b.E[i].cpu().numpy() - Eo) <= 1e-12 * np.linalg.norm(Eo), i
+        infos = []
+        for _ in range(2):
+            info, st = b.step()
+            assert all(s == 0 for s in st), st
+            infos.append([(x["J0"], x["J"], x["lam"], x["trials"]) for x in info])
+        res.append((infos, [g.cpu().numpy().copy() for g in gs]))
+        b.close()
+    assert res[0][0] == res[1][0]
+    for a, c in zip(res[0][1], res[1][1]):
+        assert np.array_equal(a, c)
