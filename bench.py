@@ -202,6 +202,7 @@ def run_batch(args, rank, world, local):
         allw = W.batch_workloads(args.problems, N=1000, seed=3)
     mine = sharding.my_problems(allw, rank, world)
     b = Batch(mine, device=dev)
+    args.staging = args.staging or "thread"
     b.set_staging(args.staging == "rows")
     gs = [torch.as_tensor(w.random_control(500 + i, 0.01), dtype=torch.float32, device=dev) for i, w in enumerate(mine)]
     b.bind(gs)
@@ -525,8 +526,9 @@ def main():
                     choices=["aniso1024", "batch", "warmstart", "cg", "unetlayers"],
                     help="aniso1024 (default bench line) or batch: 256 independent problems, sizes {64..512}^2, "
                          "1000 steps, one persistent launch per step replayed as a CUDA graph")
-    ap.add_argument("--staging", default="rows", choices=["rows", "thread"],
-                    help="aniso1024 and batch: bulk row-window staging (default) or per-thread copies")
+    ap.add_argument("--staging", default=None, choices=["rows", "thread"],
+                    help="bulk row-window staging or per-thread copies (default: rows for aniso1024, "
+                         "thread for batch, the faster of each)")
     ap.add_argument("--problems", type=int, default=256)
     ap.add_argument("--ws-train", type=int, default=2000)
     ap.add_argument("--ws-test", type=int, default=200)
@@ -583,6 +585,7 @@ def main():
     wl = WORKLOAD
     w = W.aniso(wl["nx"], wl["ny"], wl["N"], seed=1 + rank, precision=32, ckpt_every=wl["k"])
     prob = Problem(w, device=dev)
+    args.staging = args.staging or "rows"
     prob.set_staging(args.staging == "rows")
     g = torch.as_tensor(w.random_control(100 + rank, 0.01), dtype=torch.float32, device=dev).contiguous()
     E = torch.empty_like(g)

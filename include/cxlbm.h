@@ -322,15 +322,19 @@ cx_status cx_batch_set_tiles(cx_batch* b, int threads, int blocks, const int* ti
 cx_status cx_batch_autotune(cx_batch* b, int probe_steps, const char* cache_path, int* threads_out,
                             int* tile_x_out, int* rows_out, double* probe_ms_out);
 /* Staging of the batched kernel's inputs, as cx_set_staging for one problem:
- * row_windows = 1 (default) stages each work item's rows of pulled
+ * row_windows = 1 stages each work item's rows of pulled
  * populations and node-local planes by bulk asynchronous copies completed on
  * an mbarrier, on every step but the first forward step and the terminal
  * adjoint step, when no problem has solid nodes, every nx is a whole number of
  * 16-byte units and the bound control and gradient arrays are 16-byte aligned
- * (otherwise, and with row_windows = 0, per-thread copies).  A wait that never
- * completes ends the launch; later calls that read the status return
- * CX_ERR_TIMEOUT.  Results are bitwise identical either way.  Drops the
- * captured graphs.  CX_ERR_INVALID_ARG for other values. */
+ * (otherwise, and with row_windows = 0, the default, per-thread copies).  A
+ * wait that never completes ends the launch; later calls that read the status
+ * return CX_ERR_TIMEOUT.  Results are bitwise identical either way.  The
+ * default is per-thread staging because the batched kernel holds about 128
+ * registers per thread (16 resident warps per SM), too few to hide the block
+ * barrier each row-window item needs (measured 6.8 against 8.5 GLUPS on the
+ * 256-problem workload).  Drops the captured graphs.  CX_ERR_INVALID_ARG for
+ * other values. */
 cx_status cx_batch_set_staging(cx_batch* b, int row_windows);
 /* Forward of every problem; J_dev (device double [count], may be NULL). */
 cx_status cx_batch_forward(cx_batch* b, double* J_dev);

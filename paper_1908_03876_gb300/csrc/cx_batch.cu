@@ -597,7 +597,7 @@ struct BatchHost {
     bool J_on_device = false;      // ... or in out[0..count) (after cx_batch_forward / _gradient)
     bool fwd_at_g = false;         // every enabled problem's forward state (checkpoints, last
                                    // tape, final populations) belongs to its current control
-    int row_windows = 1;           // steps that qualify use k_batch_rows
+    int row_windows = 0;           // 1: steps that qualify use k_batch_rows (slower here, see cx_batch_set_staging)
     bool rows_ok = false;          // every problem qualifies (no solids, aligned rows and controls)
     int rows_blocks[2] = {0, 0};   // persistent blocks of k_batch_rows (forward, adjoint)
 };

@@ -469,7 +469,7 @@ def test_geometry4096_fp32_full_size_sampled():
     wl = replace(wf, N=5000, ckpt_every=100)  # the full workload: 5000 steps, checkpoint every 100
     p = Problem(wl)
     gl = torch.as_tensor(wl.random_control(13, 0.01), dtype=torch.float32, device="cuda")
-    E = p.gradient(gl)
+    _, E = p.gradient(gl)
     J, _, ginf = p.norms()
     u, _ = p.fields()
     solid_win = torch.as_tensor(1 - wl.cmask, device="cuda").bool()
