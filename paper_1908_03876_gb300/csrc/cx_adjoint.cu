@@ -94,24 +94,33 @@ static cudaError_t launch_q(const CxConst& C, const KConst<T>& K, const AdjArgs<
     }
 }
 
-// Sources of the adjoint stage: psi^{n+1} pulled from x + e_i (row
-// y + e_y,i), then the tape (u, G_x, G_y), sigma^{n+1}, g (whole-grid
+// Bulk copies of one row segment's stage (issued by one thread): the 2Q
+// windows of psi^{n+1}, the tape (u, G_x, G_y), sigma^{n+1}, g (whole-grid
 // control) and the angle (rotated tensors).
-template <typename T, int Q>
-__device__ __forceinline__ void adj_row_sources(const CxConst& C, const AdjArgs<T>& A, RowSources<T, Q, 6>& S) {
+template <typename T, int Q, int NT>
+__device__ __forceinline__ void adj_issue_rows(const CxConst& C, const AdjArgs<T>& A, int y, int x0, T* st,
+                                               uint64_t* bar) {
     using L = Lat<Q>;
+    using RW = RowWindow<T, Q, NT>;
+    const int nx = C.nx, nv = min(NT, nx - x0);
+    const int rm = y == 0 ? C.ny - 1 : y - 1, rp = y == C.ny - 1 ? 0 : y + 1;
+    const bool rot = C.aniso == CX_ANISO_ROTATED, gb = A.g && C.ctrl_full;
+    const uint32_t nb = (uint32_t)nv * sizeof(T);
+    mbar_expect_tx(bar, (uint32_t)(2 * Q * (nv + 2 * RW::H)) * sizeof(T) + nb * (4u + gb + rot));
 #pragma unroll
     for (int j = 0; j < 2 * Q; ++j) {
-        S.src[j] = A.in(j);
-        S.dy[j] = L::ey(j < Q ? j : j - Q);
+        const int i = j < Q ? j : j - Q;
+        const int ys = L::ey(i) > 0 ? rp : (L::ey(i) < 0 ? rm : y); // pull from x + e_i
+        bulk_row_window<T, NT>(st + j * RW::W, A.in(j) + (size_t)ys * nx, x0, nv, nx, bar);
     }
-    S.src[2 * Q] = A.tape;
-    S.src[2 * Q + 1] = A.tape + C.plane;
-    S.src[2 * Q + 2] = A.tape + 2 * C.plane;
-    S.src[2 * Q + 3] = A.sigma;
-    S.src[2 * Q + 4] = C.ctrl_full ? A.g : nullptr;
-    S.src[2 * Q + 5] = C.aniso == CX_ANISO_ROTATED ? reinterpret_cast<const T*>(C.theta) : nullptr;
-    S.nloc = 4 + (S.src[2 * Q + 4] != nullptr) + (S.src[2 * Q + 5] != nullptr);
+    T* const loc = st + 2 * Q * RW::W;
+    const size_t k0 = (size_t)y * nx + x0, pl = (size_t)C.plane;
+    bulk_g2s(loc, A.tape + k0, nb, bar);
+    bulk_g2s(loc + NT, A.tape + pl + k0, nb, bar);
+    bulk_g2s(loc + 2 * NT, A.tape + 2 * pl + k0, nb, bar);
+    bulk_g2s(loc + 3 * NT, A.sigma + k0, nb, bar);
+    if (gb) bulk_g2s(loc + 4 * NT, A.g + k0, nb, bar);
+    if (rot) bulk_g2s(loc + 5 * NT, reinterpret_cast<const T*>(C.theta) + k0, nb, bar);
 }
 
 // g of a controlled node when the control window is not the whole grid
@@ -130,19 +139,17 @@ template <typename T, int Q, int NT> constexpr size_t adj_rows_smem() {
 }
 
 template <typename T, int Q, int NT>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 2) k_adjoint_rows(const CxConst C, const KConst<T> KC, const AdjArgs<T> A) {
+__global__ void __launch_bounds__(NT) k_adjoint_rows(const CxConst C, const KConst<T> KC, const AdjArgs<T> A) {
     using RW = RowWindow<T, Q, NT>;
     constexpr int SV = adj_rows_stage_values<T, Q, NT>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* const st0 = reinterpret_cast<T*>(smem_raw);
     T* const st1 = st0 + SV;
     uint64_t* const bar = reinterpret_cast<uint64_t*>(st1 + SV);
-    __shared__ RowSources<T, Q, 6> src;
     if (threadIdx.x == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         mbar_init_fence();
-        adj_row_sources<T, Q>(C, A, src);
     }
     typename SqAccT<T>::type acc;
     ChunkIter<NT> it(C);
@@ -151,7 +158,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 2) k_adjoint_rows(con
     wait_prior_grid(); // the previous step's populations and node state are complete
     if (block_sees_timeout(A.status)) return;
     if (it.valid()) {
-        if (threadIdx.x < 32) warp_issue_rows<T, Q, NT, 6>(src, C, it.y, it.seg * NT, st0, &bar[0]);
+        if (threadIdx.x == 0) adj_issue_rows<T, Q, NT>(C, A, it.y, it.seg * NT, st0, &bar[0]);
         adj_stage_ctrl<T, Q, NT>(C, A, cur, st0);
     }
     cp_async_commit();
@@ -163,7 +170,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 2) k_adjoint_rows(con
         const NodeIdx nxt = it.valid() ? it.node(C) : no_node();
         T* const sn = b ? st0 : st1;
         if (it.valid()) { // stage b^1 is free: every thread passed the barrier that ended its last use
-            if (threadIdx.x < 32) warp_issue_rows<T, Q, NT, 6>(src, C, it.y, it.seg * NT, sn, &bar[b ^ 1]);
+            if (threadIdx.x == 0) adj_issue_rows<T, Q, NT>(C, A, it.y, it.seg * NT, sn, &bar[b ^ 1]);
             adj_stage_ctrl<T, Q, NT>(C, A, nxt, sn);
         }
         cp_async_commit();

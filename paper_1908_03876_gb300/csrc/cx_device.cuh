@@ -553,36 +553,6 @@ __device__ __forceinline__ void bulk_row_window(T* dst, const T* row, int x0, in
     if (x0 + nv == nx) bulk_g2s(dst + H + nv, row, H * sizeof(T), bar);
 }
 
-// Sources of a row-window stage, set once per block in shared memory: the 2Q
-// population planes with the row offset each pulls from, then NL node-local
-// planes (null: not staged).
-template <typename T, int Q, int NL> struct RowSources {
-    const T* src[2 * Q + NL];
-    int dy[2 * Q];
-    int nloc; // node-local planes present
-};
-
-// The copies of the row segment [x0, x0 + NT) of row y into stage st, issued
-// by the lanes of warp 0 in parallel (lane j < 2Q: the row window of plane j;
-// lane 2Q + v: node-local plane v); all complete on bar.
-template <typename T, int Q, int NT, int NL>
-__device__ __forceinline__ void warp_issue_rows(const RowSources<T, Q, NL>& S, const CxConst& C, int y, int x0, T* st,
-                                                uint64_t* bar) {
-    using RW = RowWindow<T, Q, NT>;
-    const int lane = (int)threadIdx.x & 31;
-    const int nx = C.nx, nv = min(NT, nx - x0);
-    if (lane == 0) mbar_expect_tx(bar, (uint32_t)((2 * Q * (nv + 2 * RW::H) + S.nloc * nv) * (int)sizeof(T)));
-    __syncwarp();
-    if (lane < 2 * Q) {
-        int ys = y + S.dy[lane];
-        ys = ys < 0 ? C.ny - 1 : (ys >= C.ny ? 0 : ys);
-        bulk_row_window<T, NT>(st + lane * RW::W, S.src[lane] + (size_t)ys * nx, x0, nv, nx, bar);
-    } else if (lane < 2 * Q + NL) {
-        const T* q = S.src[lane];
-        if (q) bulk_g2s(st + 2 * Q * RW::W + (lane - 2 * Q) * NT, q + (size_t)y * nx + x0, nv * sizeof(T), bar);
-    }
-}
-
 // Compensated accumulation of x^2 across the nodes a thread owns, then one
 // warp reduction; lane 0 adds the warp's share to its FP64 slot.
 struct SqAcc {

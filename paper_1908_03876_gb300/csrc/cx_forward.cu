@@ -25,8 +25,7 @@
 //
 // Row-window variant (k_forward_rows; steps n >= 1 of grids without solid
 // nodes whose rows are a whole number of 16-byte units): the block stages a
-// row segment at a time.  The lanes of warp 0 issue, one population plane
-// each, bulk
+// row segment at a time.  One thread issues, per population plane, bulk
 // asynchronous copies of the source row window (the segment widened by 16
 // bytes on each side, periodic ends taken from the other end of the row) and
 // of the node-local planes, all completing on the stage's mbarrier; every
@@ -103,22 +102,31 @@ static cudaError_t launch_q(const CxConst& C, const KConst<T>& K, const FwdArgs<
     }
 }
 
-// Sources of the forward stage: populations pulled from x - e_i (row
-// y - e_y,i), then the angle (rotated tensors), g and E (whole-grid control)
-// and Phi^{n-1}.
-template <typename T, int Q>
-__device__ __forceinline__ void fwd_row_sources(const CxConst& C, const FwdArgs<T>& A, RowSources<T, Q, 4>& S) {
+// Bulk copies of one row segment's stage (issued by one thread): the 2Q
+// population windows, the angle (rotated tensors), g and E (whole-grid
+// control) and Phi^{n-1}.
+template <typename T, int Q, int NT>
+__device__ __forceinline__ void fwd_issue_rows(const CxConst& C, const FwdArgs<T>& A, int y, int x0, T* st,
+                                               uint64_t* bar) {
     using L = Lat<Q>;
+    using RW = RowWindow<T, Q, NT>;
+    const int nx = C.nx, nv = min(NT, nx - x0);
+    const int rm = y == 0 ? C.ny - 1 : y - 1, rp = y == C.ny - 1 ? 0 : y + 1;
+    const bool rot = C.aniso == CX_ANISO_ROTATED, gb = A.g && C.ctrl_full, eb = A.E && C.ctrl_full;
+    const uint32_t nb = (uint32_t)nv * sizeof(T);
+    mbar_expect_tx(bar, (uint32_t)(2 * Q * (nv + 2 * RW::H)) * sizeof(T) + nb * (1u + rot + gb + eb));
 #pragma unroll
     for (int j = 0; j < 2 * Q; ++j) {
-        S.src[j] = A.in(j);
-        S.dy[j] = -L::ey(j < Q ? j : j - Q);
+        const int i = j < Q ? j : j - Q;
+        const int ys = L::ey(i) > 0 ? rm : (L::ey(i) < 0 ? rp : y); // pull from x - e_i
+        bulk_row_window<T, NT>(st + j * RW::W, A.in(j) + (size_t)ys * nx, x0, nv, nx, bar);
     }
-    S.src[2 * Q] = C.aniso == CX_ANISO_ROTATED ? reinterpret_cast<const T*>(C.theta) : nullptr;
-    S.src[2 * Q + 1] = C.ctrl_full ? A.g : nullptr;
-    S.src[2 * Q + 2] = C.ctrl_full ? A.E : nullptr;
-    S.src[2 * Q + 3] = A.phi;
-    S.nloc = (S.src[2 * Q] != nullptr) + (S.src[2 * Q + 1] != nullptr) + (S.src[2 * Q + 2] != nullptr) + 1;
+    T* const loc = st + 2 * Q * RW::W;
+    const size_t k0 = (size_t)y * nx + x0;
+    if (rot) bulk_g2s(loc, reinterpret_cast<const T*>(C.theta) + k0, nb, bar);
+    if (gb) bulk_g2s(loc + NT, A.g + k0, nb, bar);
+    if (eb) bulk_g2s(loc + 2 * NT, A.E + k0, nb, bar);
+    bulk_g2s(loc + 3 * NT, A.phi + k0, nb, bar);
 }
 
 // g and E of a controlled node when the control window is not the whole grid:
@@ -140,19 +148,17 @@ template <typename T, int Q, int NT> constexpr size_t fwd_rows_smem() {
 }
 
 template <typename T, int Q, int NT>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 2) k_forward_rows(const CxConst C, const KConst<T> KC, const FwdArgs<T> A) {
+__global__ void __launch_bounds__(NT) k_forward_rows(const CxConst C, const KConst<T> KC, const FwdArgs<T> A) {
     using RW = RowWindow<T, Q, NT>;
     constexpr int SV = fwd_rows_stage_values<T, Q, NT>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* const st0 = reinterpret_cast<T*>(smem_raw);
     T* const st1 = st0 + SV;
     uint64_t* const bar = reinterpret_cast<uint64_t*>(st1 + SV);
-    __shared__ RowSources<T, Q, 4> src;
     if (threadIdx.x == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         mbar_init_fence();
-        fwd_row_sources<T, Q>(C, A, src);
     }
     typename SqAccT<T>::type acc;
     ChunkIter<NT> it(C);
@@ -161,7 +167,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 2) k_forward_rows(con
     wait_prior_grid(); // the previous step's populations and node state are complete
     if (block_sees_timeout(A.status)) return;
     if (it.valid()) {
-        if (threadIdx.x < 32) warp_issue_rows<T, Q, NT, 4>(src, C, it.y, it.seg * NT, st0, &bar[0]);
+        if (threadIdx.x == 0) fwd_issue_rows<T, Q, NT>(C, A, it.y, it.seg * NT, st0, &bar[0]);
         fwd_stage_ctrl<T, Q, NT>(C, A, cur, st0);
     }
     cp_async_commit();
@@ -173,7 +179,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 2) k_forward_rows(con
         const NodeIdx nxt = it.valid() ? it.node(C) : no_node();
         T* const sn = b ? st0 : st1;
         if (it.valid()) { // stage b^1 is free: every thread passed the barrier that ended its last use
-            if (threadIdx.x < 32) warp_issue_rows<T, Q, NT, 4>(src, C, it.y, it.seg * NT, sn, &bar[b ^ 1]);
+            if (threadIdx.x == 0) fwd_issue_rows<T, Q, NT>(C, A, it.y, it.seg * NT, sn, &bar[b ^ 1]);
             fwd_stage_ctrl<T, Q, NT>(C, A, nxt, sn);
         }
         cp_async_commit();
