@@ -529,6 +529,8 @@ def main():
     ap.add_argument("--staging", default=None, choices=["rows", "thread"],
                     help="bulk row-window staging or per-thread copies (default: rows for aniso1024, "
                          "thread for batch, the faster of each)")
+    ap.add_argument("--threads", type=int, default=256, choices=[128, 256],
+                    help="aniso1024: threads per block of the persistent lattice kernels")
     ap.add_argument("--problems", type=int, default=256)
     ap.add_argument("--ws-train", type=int, default=2000)
     ap.add_argument("--ws-test", type=int, default=200)
@@ -587,6 +589,8 @@ def main():
     prob = Problem(w, device=dev)
     args.staging = args.staging or "rows"
     prob.set_staging(args.staging == "rows")
+    if args.threads != 256:
+        prob.set_launch(args.threads, 0)
     g = torch.as_tensor(w.random_control(100 + rank, 0.01), dtype=torch.float32, device=dev).contiguous()
     E = torch.empty_like(g)
     nodes = w.nx * w.ny
@@ -684,6 +688,7 @@ def main():
                                    "rotated anisotropic D_u = D_v, shear convection, chemotaxis chi=-0.1",
                        "step": "one gradient evaluation (forward + recompute + AMRT adjoint + FP64 reductions)",
                        "l2": "inputs larger than L2 (8.4 GB control, 1.5 GB checkpoints per step)",
+                       "staging": args.staging, "threads_per_block": args.threads,
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline,
             "kernels": roof,
