@@ -258,7 +258,11 @@ cx_status cx_set_launch(cx_problem* p, int threads, int blocks);
  * later calls return CX_ERR_TIMEOUT); other steps use per-thread
  * asynchronous copies.  row_windows = 0: per-thread copies everywhere.
  * Results are bitwise identical either way (same arithmetic per node).
- * CX_ERR_INVALID_ARG for other values. */
+ * row_windows = 2 is a test mode of the timeout path: each stage expects 16
+ * bytes more than it copies, so every wait runs out (0.2 s), the launch ends
+ * early with the status bit set, later launches return at once, and the next
+ * synchronising call returns CX_ERR_TIMEOUT; the problem stays in that state
+ * (create a new one).  CX_ERR_INVALID_ARG for other values. */
 cx_status cx_set_staging(cx_problem* p, int row_windows);
 
 /* Per-phase timing with CUDA events on the problem's stream: enable != 0

@@ -744,7 +744,7 @@ cx_status cx_set_launch(cx_problem* p, int threads, int blocks) {
 }
 
 cx_status cx_set_staging(cx_problem* p, int row_windows) {
-    if (!p || (row_windows != 0 && row_windows != 1)) return CX_ERR_INVALID_ARG;
+    if (!p || row_windows < 0 || row_windows > 2) return CX_ERR_INVALID_ARG;
     p->Lf.row_windows = p->La.row_windows = row_windows;
     return CX_OK;
 }

@@ -59,6 +59,7 @@ template <typename T> struct FwdArgs {
     T* tape;             // [3][plane] (u^n, G_x^n, G_y^n) or null
     double* gsq_part;    // per-warp partial of sum (g^n)^2 (accumulated over steps), or null
     int* status;         // status word (ST_TIMEOUT from the bulk-staged kernel), or null
+    unsigned tx_pad;     // test mode of the bulk-staged kernel: bytes each stage expects beyond its copies
     int n;               // time step index
     __device__ __forceinline__ const T* in(int j) const { return pin[j]; }
     __device__ __forceinline__ T* out(int j) const { return pout[j]; }
@@ -103,6 +104,7 @@ template <typename T> struct AdjArgs {
     double* e2_part;     // per-warp partial of sum E^2 (accumulated over steps)
     double* emax_part;   // per-warp partial of max |E| (accumulated over steps)
     int* status;         // status word (ST_TIMEOUT from the bulk-staged kernel), or null
+    unsigned tx_pad;     // test mode of the bulk-staged kernel: bytes each stage expects beyond its copies
     int n;
     int terminal;        // n == N-1: psi^{n+1} is the broadcast seed
     int accum;           // time-windowed control: add to the window's gradient (not its last step)
@@ -113,7 +115,8 @@ template <typename T> struct AdjArgs {
 
 struct Launch {
     dim3 grid, block;
-    int row_windows = 1;   // steps that qualify use the row-window (bulk copy) kernels
+    int row_windows = 1;   // steps that qualify use the row-window (bulk copy) kernels; 2: their
+                           // test mode, every stage wait runs out (timeout path)
     unsigned rows_grid = 0; // blocks of the row-window kernels (0: grid.x)
 };
 

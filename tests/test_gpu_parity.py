@@ -189,6 +189,38 @@ def test_row_window_staging_bitwise(case, threads):
     assert eJ < tol_f and eu < tol_f and eE < tol_g
 
 
+def test_row_window_wait_timeout_is_reported():
+    """A stage wait that never completes ends its launch within the wait's
+    time bound instead of hanging: in the staging test mode every stage
+    expects 16 bytes more than it copies, the next synchronising call reports
+    CX_ERR_TIMEOUT (and keeps reporting it), and the context stays usable: a
+    new problem then matches the oracle."""
+    import time
+
+    from paper_1908_03876_gb300 import _lib
+    from paper_1908_03876_gb300.problem import Problem
+
+    w = W.aniso(64, 32, 6, seed=3, precision=32, ckpt_every=3)
+    g = w.random_control(5, 0.02)
+    p = Problem(w)
+    _lib.check(p.lib.cx_set_staging(p.h, 2), "cx_set_staging")
+    t0 = time.perf_counter()
+    p.forward(g)
+    with pytest.raises(_lib.CxError) as ei:
+        p.norms()
+    dt = time.perf_counter() - t0
+    print(f"timeout reported after {dt:.2f} s")
+    assert ei.value.code == 7 and dt < 30
+    p.forward(g)
+    with pytest.raises(_lib.CxError) as ei:
+        p.norms()
+    assert ei.value.code == 7
+    q = Problem(w)
+    J = float(q.forward(g).item())
+    Jo, _, _ = oracle.forward(oracle.from_workload(w), g)
+    assert abs(J - Jo) / abs(Jo) < TOL32_FIELD
+
+
 def test_repeated_adjoint_and_state():
     """A second adjoint after one forward repeats the first (tape bookkeeping);
     adjoint before any forward is refused."""
