@@ -24,6 +24,7 @@
 #include <map>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "cx_adj_body.cuh"
@@ -209,17 +210,28 @@ __global__ void __launch_bounds__(NT) k_batch(const BRec<T>* __restrict__ recs, 
     // consecutive items of one problem and are flushed into the slot of the
     // run's first tile (the runs are the same at every launch, so the sums
     // are reproducible).
+    // the argument block depends only on the problem (the step is the launch's):
+    // built once per change of problem and carried from staging to compute
+    using Args = std::conditional_t<ADJ, BAdjArgs<T>, BFwdArgs<T>>;
+    auto make_args = [&](int q) -> Args {
+        if constexpr (ADJ)
+            return adj_args(recs[q], st);
+        else
+            return fwd_args(recs[q], st, lam, q);
+    };
     int p = 0;
     int t = next_live(blockIdx.x, p);
     int j = 0, x = 0, y = 0;
     NodeIdx cur = no_node();
+    Args Ac{};
     if (t < total) {
         tile_origin(recs[p], t - sh_tile0[p], x, y);
         cur = node_at(recs[p], x, y);
+        Ac = make_args(p);
         if constexpr (ADJ)
-            adj_stage<T, Q, NT>(recs[p].C, adj_args(recs[p], st), cur, s0);
+            adj_stage<T, Q, NT>(recs[p].C, Ac, cur, s0);
         else
-            fwd_stage<T, Q, NT>(recs[p].C, fwd_args(recs[p], st, lam, p), cur, s0);
+            fwd_stage<T, Q, NT>(recs[p].C, Ac, cur, s0);
     }
     cp_async_commit();
     int run_tile = t;
@@ -234,19 +246,21 @@ __global__ void __launch_bounds__(NT) k_batch(const BRec<T>* __restrict__ recs, 
             if (tn < total) tile_origin(recs[pn], tn - sh_tile0[pn], xn, yn);
         }
         NodeIdx nxt = no_node();
+        Args An = Ac;
         if (tn < total) {
             nxt = node_at(recs[pn], xn, yn);
+            if (pn != p) An = make_args(pn);
             if constexpr (ADJ)
-                adj_stage<T, Q, NT>(recs[pn].C, adj_args(recs[pn], st), nxt, odd ? s0 : s1);
+                adj_stage<T, Q, NT>(recs[pn].C, An, nxt, odd ? s0 : s1);
             else
-                fwd_stage<T, Q, NT>(recs[pn].C, fwd_args(recs[pn], st, lam, pn), nxt, odd ? s0 : s1);
+                fwd_stage<T, Q, NT>(recs[pn].C, An, nxt, odd ? s0 : s1);
         }
         cp_async_commit();
         cp_async_wait<1>();
         if constexpr (ADJ)
-            adj_compute<T, Q, NT>(R.C, R.K, adj_args(R, st), cur, ThreadSlots<T, NT>{odd ? s1 : s0}, acc);
+            adj_compute<T, Q, NT>(R.C, R.K, Ac, cur, ThreadSlots<T, NT>{odd ? s1 : s0}, acc);
         else
-            fwd_compute<T, Q, NT>(R.C, R.K, fwd_args(R, st, lam, p), cur, ThreadSlots<T, NT>{odd ? s1 : s0}, acc);
+            fwd_compute<T, Q, NT>(R.C, R.K, Ac, cur, ThreadSlots<T, NT>{odd ? s1 : s0}, acc);
         if (pn != p || tn >= total) {
             if (st.want_sum) {
                 const int slot = R.slot0 + (run_tile - sh_tile0[p]) * (NT >> 5) + ((int)threadIdx.x >> 5);
@@ -261,6 +275,7 @@ __global__ void __launch_bounds__(NT) k_batch(const BRec<T>* __restrict__ recs, 
         x = xn;
         y = yn;
         cur = nxt;
+        Ac = An;
         odd = !odd;
     }
     cp_async_wait<0>();
