@@ -336,8 +336,8 @@ cx_status cx_batch_autotune(cx_batch* b, int probe_steps, const char* cache_path
  * return CX_ERR_TIMEOUT.  Results are bitwise identical either way.  The
  * default is per-thread staging because the batched kernel holds about 128
  * registers per thread (16 resident warps per SM), too few to hide the block
- * barrier each row-window item needs (measured 6.8 against 8.5 GLUPS on the
- * 256-problem workload).  Drops the captured graphs.  CX_ERR_INVALID_ARG for
+ * barrier each row-window item needs (measured 6.8 against 8.5 GLUPS for the
+ * per-thread form on the 256-problem workload).  Drops the captured graphs.  CX_ERR_INVALID_ARG for
  * other values. */
 cx_status cx_batch_set_staging(cx_batch* b, int row_windows);
 /* Forward of every problem; J_dev (device double [count], may be NULL). */
