@@ -459,6 +459,67 @@ def run_cg(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+def run_fp64(args, rank, world, local):
+    """FP64 lattices on the GPU (not a target: the FP64 pipe of a GB300 is far
+    narrower than its FP32 pipe): the 64x64 D2Q5 problem (L2-resident, time per
+    step) and the 1024x1024 D2Q9 anisotropic problem for 200 steps, k = 20
+    (fwd+adjoint MLUPS and the per-phase launch times, HBM fraction at FP64
+    bytes); J of the small problem against the FP64 oracle."""
+    import torch
+
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    from paper_1908_03876_gb300.build import build
+
+    build()
+    import oracle
+
+    oracle.build()
+    from paper_1908_03876_gb300 import workloads as W
+    from paper_1908_03876_gb300.problem import Problem
+
+    hbm, peak_kind = _peaks()
+    out = {}
+    for name, w, reps in [("plain64 (64x64 D2Q5, N=200)", W.plain64(), 20),
+                          ("aniso1024 (1024x1024 D2Q9, N=200, k=20)",
+                           W.aniso(1024, 1024, 200, seed=1, precision=64, ckpt_every=20), 3)]:
+        p = Problem(w)
+        g = torch.as_tensor(w.random_control(100, 0.01), dtype=torch.float64, device="cuda").contiguous()
+        E = torch.empty_like(g)
+        for _ in range(2):
+            p.gradient(g, out=E)
+        torch.cuda.synchronize()
+        p.set_timing(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(p.stream)
+        for _ in range(reps):
+            J, _ = p.gradient(g, out=E)
+        e1.record(p.stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        phases = p.timing()
+        p.set_timing(False)
+        nodes = w.nx * w.ny
+        ent = {"ms_per_gradient": ms, "us_per_step": ms * 1e3 / w.N, "mlups": nodes * w.N / (ms * 1e-3) / 1e6}
+        if w.Q == 9:
+            for ph in ("forward", "recompute", "adjoint"):
+                t, n = phases[ph]
+                if n > 0:
+                    us = t * 1e3 / n
+                    gbs = 2 * BYTES[ph] * nodes / (us * 1e-6) / 1e9
+                    ent[ph] = {"us_per_launch": us, "GB/s (FP64 bytes)": gbs, "hbm_frac": gbs / hbm}
+        if nodes <= 4096:  # the oracle's J for the small problem (the large one is checked by the tests)
+            Jo, _, _ = oracle.forward(oracle.from_workload(w), g.cpu().numpy())
+            ent["J_rel_err_vs_oracle"] = abs(float(J.item()) - Jo) / abs(Jo)
+        out[name] = ent
+        p.close()
+    line = {"metric": "FP64 lattices: fwd+adjoint MLUPS", "value": out["aniso1024 (1024x1024 D2Q9, N=200, k=20)"]["mlups"],
+            "unit": "MLUPS", "n_gpus": 1, "higher_is_better": True, "dtype": "f64", "data": "synthetic (seeded)",
+            "peak_hbm_gbs": hbm, "peak_source": peak_kind, "results": out}
+    print(json.dumps(line), flush=True)
+
+
 def run_unet_layers(args, rank, world, local):
     """Forward time of each 3x3 layer shape of the 4-level U-Net at 128x128,
     batch 16, on the tcgen05 kernel and on the mma.sync kernel (same packed
@@ -523,7 +584,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="aniso1024",
-                    choices=["aniso1024", "batch", "warmstart", "cg", "unetlayers"],
+                    choices=["aniso1024", "batch", "warmstart", "cg", "unetlayers", "fp64"],
                     help="aniso1024 (default bench line) or batch: 256 independent problems, sizes {64..512}^2, "
                          "1000 steps, one persistent launch per step replayed as a CUDA graph")
     ap.add_argument("--staging", default=None, choices=["rows", "thread"],
@@ -560,6 +621,8 @@ def main():
     if args.workload == "cg":
         run_cg(args, rank, world, local)
         return
+    if args.workload == "fp64":
+        return run_fp64(args, rank, world, local)
     if args.workload == "unetlayers":
         run_unet_layers(args, rank, world, local)
         return
