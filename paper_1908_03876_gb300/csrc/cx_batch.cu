@@ -219,12 +219,27 @@ __global__ void __launch_bounds__(NT) k_batch(const BRec<T>* __restrict__ recs, 
         else
             return fwd_args(recs[q], st, lam, q);
     };
+    // The current problem's constants in a per-warp shared-memory slot (two
+    // slots: the next problem's are loaded while the current one's are in use),
+    // read at shared-memory latency by the per-node arithmetic.
+    __shared__ KConst<T> kc_sh[NT / 32][2];
+    const int warp = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
+    auto load_kc = [&](int q, int slot) {
+        static_assert(sizeof(KConst<T>) % 4 == 0, "KConst is copied as 32-bit words");
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(&recs[q].K);
+        uint32_t* dst = reinterpret_cast<uint32_t*>(&kc_sh[warp][slot]);
+        __syncwarp();
+        for (int i = lane; i < (int)(sizeof(KConst<T>) / 4); i += 32) dst[i] = __ldg(src + i);
+        __syncwarp();
+    };
     int p = 0;
     int t = next_live(blockIdx.x, p);
     int j = 0, x = 0, y = 0;
     NodeIdx cur = no_node();
     Args Ac{};
+    int sc = 0; // slot of the current problem's constants
     if (t < total) {
+        load_kc(p, 0);
         tile_origin(recs[p], t - sh_tile0[p], x, y);
         cur = node_at(recs[p], x, y);
         Ac = make_args(p);
@@ -249,7 +264,10 @@ __global__ void __launch_bounds__(NT) k_batch(const BRec<T>* __restrict__ recs, 
         Args An = Ac;
         if (tn < total) {
             nxt = node_at(recs[pn], xn, yn);
-            if (pn != p) An = make_args(pn);
+            if (pn != p) {
+                An = make_args(pn);
+                load_kc(pn, sc ^ 1);
+            }
             if constexpr (ADJ)
                 adj_stage<T, Q, NT>(recs[pn].C, An, nxt, odd ? s0 : s1);
             else
@@ -258,9 +276,9 @@ __global__ void __launch_bounds__(NT) k_batch(const BRec<T>* __restrict__ recs, 
         cp_async_commit();
         cp_async_wait<1>();
         if constexpr (ADJ)
-            adj_compute<T, Q, NT>(R.C, R.K, Ac, cur, ThreadSlots<T, NT>{odd ? s1 : s0}, acc);
+            adj_compute<T, Q, NT>(R.C, kc_sh[warp][sc], Ac, cur, ThreadSlots<T, NT>{odd ? s1 : s0}, acc);
         else
-            fwd_compute<T, Q, NT>(R.C, R.K, Ac, cur, ThreadSlots<T, NT>{odd ? s1 : s0}, acc);
+            fwd_compute<T, Q, NT>(R.C, kc_sh[warp][sc], Ac, cur, ThreadSlots<T, NT>{odd ? s1 : s0}, acc);
         if (pn != p || tn >= total) {
             if (st.want_sum) {
                 const int slot = R.slot0 + (run_tile - sh_tile0[p]) * (NT >> 5) + ((int)threadIdx.x >> 5);
@@ -269,6 +287,7 @@ __global__ void __launch_bounds__(NT) k_batch(const BRec<T>* __restrict__ recs, 
             acc = typename SqAccT<T>::type{};
             run_tile = tn;
         }
+        if (pn != p) sc ^= 1;
         t = tn;
         p = pn;
         j = jn;
