@@ -159,8 +159,12 @@ template <typename T> __device__ __forceinline__ void tile_origin(const BRec<T>&
     y = tyi * R.ty * R.rr + ((int)threadIdx.x >> R.tx_shift);
 }
 
+template <typename T> __device__ __forceinline__ NodeIdx node_at(const BRec<T>& R, int x, int y);
+__device__ __forceinline__ NodeIdx node_at_c(const CxConst& C, int x, int y);
 template <typename T> __device__ __forceinline__ NodeIdx node_at(const BRec<T>& R, int x, int y) {
-    const CxConst& C = R.C;
+    return node_at_c(R.C, x, y);
+}
+__device__ __forceinline__ NodeIdx node_at_c(const CxConst& C, int x, int y) {
     NodeIdx r;
     r.x = x;
     r.y = y;
@@ -219,17 +223,25 @@ __global__ void __launch_bounds__(NT) k_batch(const BRec<T>* __restrict__ recs, 
         else
             return fwd_args(recs[q], st, lam, q);
     };
-    // The current problem's constants in a per-warp shared-memory slot (two
-    // slots: the next problem's are loaded while the current one's are in use),
-    // read at shared-memory latency by the per-node arithmetic.
-    __shared__ KConst<T> kc_sh[NT / 32][2];
+    // The current problem's descriptor and constants in a per-warp
+    // shared-memory slot (two slots: the next problem's are loaded while the
+    // current one's are in use), read at shared-memory latency by the node
+    // indexing, the staging and the per-node arithmetic.
+    struct ProbConst {
+        CxConst C;
+        KConst<T> K;
+    };
+    __shared__ ProbConst pc_sh[NT / 32][2];
     const int warp = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
     auto load_kc = [&](int q, int slot) {
-        static_assert(sizeof(KConst<T>) % 4 == 0, "KConst is copied as 32-bit words");
-        const uint32_t* src = reinterpret_cast<const uint32_t*>(&recs[q].K);
-        uint32_t* dst = reinterpret_cast<uint32_t*>(&kc_sh[warp][slot]);
+        static_assert(sizeof(CxConst) % 4 == 0 && sizeof(KConst<T>) % 4 == 0, "copied as 32-bit words");
+        const uint32_t* srcC = reinterpret_cast<const uint32_t*>(&recs[q].C);
+        const uint32_t* srcK = reinterpret_cast<const uint32_t*>(&recs[q].K);
+        uint32_t* dstC = reinterpret_cast<uint32_t*>(&pc_sh[warp][slot].C);
+        uint32_t* dstK = reinterpret_cast<uint32_t*>(&pc_sh[warp][slot].K);
         __syncwarp();
-        for (int i = lane; i < (int)(sizeof(KConst<T>) / 4); i += 32) dst[i] = __ldg(src + i);
+        for (int i = lane; i < (int)(sizeof(CxConst) / 4); i += 32) dstC[i] = __ldg(srcC + i);
+        for (int i = lane; i < (int)(sizeof(KConst<T>) / 4); i += 32) dstK[i] = __ldg(srcK + i);
         __syncwarp();
     };
     int p = 0;
@@ -241,12 +253,12 @@ __global__ void __launch_bounds__(NT) k_batch(const BRec<T>* __restrict__ recs, 
     if (t < total) {
         load_kc(p, 0);
         tile_origin(recs[p], t - sh_tile0[p], x, y);
-        cur = node_at(recs[p], x, y);
+        cur = node_at_c(pc_sh[warp][0].C, x, y);
         Ac = make_args(p);
         if constexpr (ADJ)
-            adj_stage<T, Q, NT>(recs[p].C, Ac, cur, s0);
+            adj_stage<T, Q, NT>(pc_sh[warp][0].C, Ac, cur, s0);
         else
-            fwd_stage<T, Q, NT>(recs[p].C, Ac, cur, s0);
+            fwd_stage<T, Q, NT>(pc_sh[warp][0].C, Ac, cur, s0);
     }
     cp_async_commit();
     int run_tile = t;
@@ -263,22 +275,26 @@ __global__ void __launch_bounds__(NT) k_batch(const BRec<T>* __restrict__ recs, 
         NodeIdx nxt = no_node();
         Args An = Ac;
         if (tn < total) {
-            nxt = node_at(recs[pn], xn, yn);
+            const int sn = pn != p ? sc ^ 1 : sc;
             if (pn != p) {
                 An = make_args(pn);
-                load_kc(pn, sc ^ 1);
+                load_kc(pn, sn);
             }
+            const CxConst& Cn = pc_sh[warp][sn].C;
+            nxt = node_at_c(Cn, xn, yn);
             if constexpr (ADJ)
-                adj_stage<T, Q, NT>(recs[pn].C, An, nxt, odd ? s0 : s1);
+                adj_stage<T, Q, NT>(Cn, An, nxt, odd ? s0 : s1);
             else
-                fwd_stage<T, Q, NT>(recs[pn].C, An, nxt, odd ? s0 : s1);
+                fwd_stage<T, Q, NT>(Cn, An, nxt, odd ? s0 : s1);
         }
         cp_async_commit();
         cp_async_wait<1>();
         if constexpr (ADJ)
-            adj_compute<T, Q, NT>(R.C, kc_sh[warp][sc], Ac, cur, ThreadSlots<T, NT>{odd ? s1 : s0}, acc);
+            adj_compute<T, Q, NT>(pc_sh[warp][sc].C, pc_sh[warp][sc].K, Ac, cur, ThreadSlots<T, NT>{odd ? s1 : s0},
+                                  acc);
         else
-            fwd_compute<T, Q, NT>(R.C, kc_sh[warp][sc], Ac, cur, ThreadSlots<T, NT>{odd ? s1 : s0}, acc);
+            fwd_compute<T, Q, NT>(pc_sh[warp][sc].C, pc_sh[warp][sc].K, Ac, cur, ThreadSlots<T, NT>{odd ? s1 : s0},
+                                  acc);
         if (pn != p || tn >= total) {
             if (st.want_sum) {
                 const int slot = R.slot0 + (run_tile - sh_tile0[p]) * (NT >> 5) + ((int)threadIdx.x >> 5);
