@@ -14,8 +14,11 @@
 // list; block b of the persistent grid takes tiles b, b + G, ...; the tile's
 // problem is found by binary search in the prefix array held in shared
 // memory.  Per node the arithmetic is the single-problem kernels' (the same
-// stage/compute bodies); reductions go to one slot per (tile, warp), summed
-// per problem in a fixed order, so replays are bitwise reproducible.
+// stage/compute bodies); the current problem's descriptor and constants sit
+// in a per-warp shared-memory slot, its argument block in registers, both
+// refreshed only when the problem changes.  Reductions go to one slot per
+// (tile, warp), summed per problem in a fixed order, so replays are bitwise
+// reproducible.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
