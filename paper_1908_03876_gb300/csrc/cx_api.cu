@@ -442,6 +442,7 @@ static cx_status run_tlm(cx_problem* p, const T* g, const T* dg, T* du_out, T* d
         }
         for (int n = n0; n < n1; ++n) { // tangent steps of the segment
             TlmArgs<T> A{};
+            A.status = p->at<int>(p->lay.off_status);
             T* out = (din == dA) ? dB : dA;
             set_planes(p, A.pin, din);
             set_planes(p, A.pout, out);

@@ -71,6 +71,8 @@ template <typename T> struct TlmArgs {
     T* dphi;             // [plane] dPhi^{n-1} in, dPhi^n out
     const T* tape;       // [3][plane] base (u^n, G_x^n, G_y^n)
     const T* dg;         // [cny*cnx] direction dg^n, or null
+    int* status;         // status word (ST_TIMEOUT from the bulk-staged kernel), or null
+    unsigned tx_pad;     // test mode of the bulk-staged kernel: bytes each stage expects beyond its copies
     int n;
     __device__ __forceinline__ const T* in(int j) const { return pin[j]; }
     __device__ __forceinline__ T* out(int j) const { return pout[j]; }

@@ -364,6 +364,33 @@ def test_tlm_matches_oracle_fp64(k):
     assert rel(E, Eo) < 1e-12
 
 
+@pytest.mark.parametrize("window", [None, (10, 6, 60, 20)])
+@pytest.mark.parametrize("threads", [128, 256])
+def test_tlm_row_windows_bitwise(window, threads):
+    """The sensitivity pass with row-window staging (k_tlm_rows) and with
+    per-thread staging gives bitwise identical du^N, dv^N (FP32, a partial
+    last row segment; with the control on a sub-window dg is staged per
+    thread)."""
+    from paper_1908_03876_gb300.problem import Problem
+
+    w = W.aniso(200, 40, 12, seed=7, precision=32, ckpt_every=5)
+    w.windows = 4
+    w.window = window
+    g = w.random_control(13, 0.05)
+    dg = w.random_control(14, 1.0)
+    outs = []
+    for rows in (True, False):
+        p = Problem(w)
+        p.set_launch(threads, 0)
+        p.set_staging(rows)
+        p.forward(g)
+        du, dv, sq = p.tlm(g, dg)
+        torch.cuda.synchronize()
+        outs.append((du.cpu().numpy(), dv.cpu().numpy(), sq))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    assert outs[0][2] == outs[1][2]
+
+
 @pytest.mark.parametrize("case", ["aniso", "geometry"])
 def test_continuous_adjoint_matches_oracle_fp64(case):
     """Continuous-adjoint gradient (time-reversed MRT solve of the adjoint
