@@ -375,6 +375,7 @@ template <typename T> static cx_status run_cadj(cx_problem* p, const T* g, T* dJ
         }
         for (int n = n1 - 1; n >= n0; --n) {
             CadjArgs<T> A{};
+            A.status = p->at<int>(p->lay.off_status);
             A.first = (n == Ly.N - 1);
             T* out = p->at<T>((n % 2) ? Ly.off_adjB : Ly.off_adjA);
             if (in) set_planes(p, A.pin, in);

@@ -90,6 +90,8 @@ template <typename T> struct CadjArgs {
     int n;
     int first;           // n == N-1: populations phi^eq(w0, -a), 0
     int accum, norm;     // time windows, as the discrete adjoint
+    int* status;         // status word (ST_TIMEOUT from the bulk-staged kernel), or null
+    unsigned tx_pad;     // test mode of the bulk-staged kernel: bytes each stage expects beyond its copies
     __device__ __forceinline__ const T* in(int j) const { return pin[j]; }
     __device__ __forceinline__ T* out(int j) const { return pout[j]; }
 };

@@ -17,6 +17,8 @@ KERNEL_SOURCES = {
                      "cx_batch.cu"),
     "k_tlm": ("cx_device.cuh", "cx_internal.h", "cx_tlm.cu"),
     "k_cadj": ("cx_device.cuh", "cx_internal.h", "cx_cadj.cu"),
+    "k_tlm_rows": ("cx_device.cuh", "cx_internal.h", "cx_tlm.cu"),
+    "k_cadj_rows": ("cx_device.cuh", "cx_internal.h", "cx_cadj.cu"),
     "nn": ("nn_kernels.cu",),
 }
 

@@ -391,6 +391,29 @@ def test_tlm_row_windows_bitwise(window, threads):
     assert outs[0][2] == outs[1][2]
 
 
+@pytest.mark.parametrize("window", [None, (10, 6, 60, 20)])
+def test_cadjoint_row_windows_bitwise(window):
+    """The continuous adjoint with row-window staging (k_cadj_rows) and with
+    per-thread staging gives bitwise identical gradients (FP32, a partial
+    last row segment; with the control on a sub-window g is staged per
+    thread)."""
+    from paper_1908_03876_gb300.problem import Problem
+
+    w = W.aniso(200, 40, 12, seed=8, precision=32, ckpt_every=5)
+    w.windows = 4
+    w.window = window
+    g = w.random_control(15, 0.05)
+    outs = []
+    for rows in (True, False):
+        p = Problem(w)
+        p.set_staging(rows)
+        p.forward(g)
+        E = p.cadjoint(g)
+        torch.cuda.synchronize()
+        outs.append(E.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
+
+
 @pytest.mark.parametrize("case", ["aniso", "geometry"])
 def test_continuous_adjoint_matches_oracle_fp64(case):
     """Continuous-adjoint gradient (time-reversed MRT solve of the adjoint
