@@ -251,14 +251,17 @@ cx_status cx_get_norms(cx_problem* p, double* J, double* grad_sq, double* grad_i
 cx_status cx_set_launch(cx_problem* p, int threads, int blocks);
 /* Staging of the lattice kernels' inputs.  row_windows = 1 (default): the
  * forward steps n >= 1 and the interior adjoint steps of grids without solid
- * nodes, whose rows are a whole number of 16-byte units and whose launch has
- * 128 or 256 threads, stage each row segment of the pulled populations and
+ * nodes, whose rows are a whole number of 16-byte units, whose launch has
+ * 128 or 256 threads and gives each block at least two row segments (the
+ * sensitivity and continuous-adjoint passes too), stage each row segment of
+ * the pulled populations and
  * the node-local planes in shared memory with bulk asynchronous copies
  * completed on an mbarrier (a wait that never completes ends the launch and
  * later calls return CX_ERR_TIMEOUT); other steps use per-thread
  * asynchronous copies.  row_windows = 0: per-thread copies everywhere.
  * Results are bitwise identical either way (same arithmetic per node).
- * row_windows = 2 is a test mode of the timeout path: each stage expects 16
+ * row_windows = 2 is a test mode of the timeout path (the segment-count
+ * condition is not applied): each stage expects 16
  * bytes more than it copies, so every wait runs out (0.2 s), the launch ends
  * early with the status bit set, later launches return at once, and the next
  * synchronising call returns CX_ERR_TIMEOUT; the problem stays in that state

@@ -201,6 +201,7 @@ template <typename T> static bool rows_eligible(const CxConst& C, const AdjArgs<
     constexpr int H = 16 / (int)sizeof(T);
     auto al = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; };
     if (!L.row_windows || A.terminal || C.has_solid || C.nx % H != 0) return false;
+    if (!rows_pipelined(C, L, L.rows_grid ? std::min(L.rows_grid, L.grid.x) : L.grid.x)) return false;
     if (L.block.x != 128 && L.block.x != 256) return false;
     for (int j = 0; j < 2 * C.Q; ++j)
         if (!al(A.rin[j])) return false;

@@ -309,6 +309,7 @@ template <typename T> static bool cadj_rows_eligible(const CxConst& C, const Cad
     constexpr int H = 16 / (int)sizeof(T);
     auto al = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; };
     if (!L.row_windows || A.first || C.has_solid || C.nx % H != 0) return false;
+    if (!rows_pipelined(C, L, L.grid.x)) return false;
     if (L.block.x != 128 && L.block.x != 256) return false;
     for (int j = 0; j < 2 * C.Q; ++j)
         if (!al(A.pin[j])) return false;

@@ -484,6 +484,17 @@ template <typename T, int Q, int NT> struct RowWindow {
     __device__ __forceinline__ T val(int v) const { return s[2 * Q * W + (v - 2 * Q) * NT]; }
 };
 
+// Row windows pay when each block of the persistent grid walks several row
+// segments, so that one segment's copies run while the previous one is
+// computed; with a segment or less per block (small, L2-resident grids) there
+// is nothing to overlap and the per-thread staging is faster.  The test mode
+// of the staging switch (2) takes the row-window kernels regardless.
+inline bool rows_pipelined(const CxConst& C, const Launch& L, unsigned blocks) {
+    if (L.row_windows == 2) return true;
+    const long long segs = (long long)((C.nx + (int)L.block.x - 1) / (int)L.block.x) * C.ny;
+    return segs >= 2LL * blocks;
+}
+
 // --------------------------------- bulk copies completed on an mbarrier
 // Every wait is bounded in time (MBAR_WAIT_NS of the global timer): a wait
 // that gives up returns false, the kernel reports ST_TIMEOUT through the

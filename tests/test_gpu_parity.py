@@ -170,7 +170,7 @@ def test_row_window_staging_bitwise(case, threads):
     outs = []
     for rows in (True, False):
         p = Problem(w)
-        p.set_launch(threads, 0)
+        p.set_launch(threads, 4)  # several row segments per block: the row-window kernels take the steps
         p.set_staging(rows)
         J = float(p.forward(g).item())
         E = p.adjoint(g)
@@ -381,7 +381,7 @@ def test_tlm_row_windows_bitwise(window, threads):
     outs = []
     for rows in (True, False):
         p = Problem(w)
-        p.set_launch(threads, 0)
+        p.set_launch(threads, 4)  # several row segments per block: the row-window kernels take the steps
         p.set_staging(rows)
         p.forward(g)
         du, dv, sq = p.tlm(g, dg)
@@ -407,6 +407,7 @@ def test_cadjoint_row_windows_against_per_thread(window):
     outs = []
     for rows in (True, False):
         p = Problem(w)
+        p.set_launch(256, 4)  # several row segments per block: the row-window kernels take the steps
         p.set_staging(rows)
         p.forward(g)
         E = p.cadjoint(g)
