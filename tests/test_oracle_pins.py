@@ -280,6 +280,211 @@ def test_chemotaxis_coupling_against_pde():
     assert np.linalg.norm(u_flip - us) / np.linalg.norm(us - us.mean()) > 20 * errs[0][0]
 
 
+# ------------------------------------------- convective source (V and grad v)
+#
+# The source weights w~_i = w_i (1 + V.e_i / Cs^2) with V = (I - K_v/2) a
+# (eq. PhiS and the choice of V after PC13, kappa_x = 0) and the term
+# (1/2) K_v a Phi_v of the local grad v (relation C146) only act where
+# convection meets a source.  A mistake in either (V = a, a sign, swapped
+# components, the term dropped) leaves an O(tau) error in the recovered PDE:
+# under diffusive refinement that is O(h^2), the same order as the scheme's
+# own truncation error, so a convergence-rate test against a closed form or an
+# independent PDE solver cannot see it (the last two tests below pass with any
+# of those mistakes planted).  The first two tests isolate each term with an
+# observable that the PDE fixes exactly and that such a mistake moves at first
+# order.
+
+def _const_aniso(n, lam, th):
+    return np.broadcast_to(rotated_tensor(lam, np.array(th)), (n, n, 3)).copy()
+
+
+def _plume_centre_velocity_error(r, a=(0.08, 0.05), n=96, N=120, sig=3.0):
+    """Relative error of the centre-of-mass velocity of a v plume that reacts
+    linearly (Phi_v = r v), against the convection velocity a.
+
+    For dv/dt = div(D grad v) - div(a v) + r v with constant D and a, the mass
+    grows as e^{rt} and the centre of mass moves at exactly a, for every r.
+    The plume stays far from the periodic edges, so sum x v / sum v is its
+    centre.  Measured between N/2 and N steps (after the start-up transient)."""
+    D = _const_aniso(n, (0.08, 0.02), 0.6)
+    x = np.arange(n)[None, :]
+    y = np.arange(n)[:, None]
+    v0 = np.exp(-((x - 32.0) ** 2 + (y - 32.0) ** 2) / (2 * sig * sig))
+    af = np.broadcast_to(np.array(a, float), (n, n, 2)).copy()
+    centres = []
+    for steps in (N // 2, N):
+        p = oracle.Problem(nx=n, ny=n, N=steps, Q=9, Du=D, Dv=D, u0=np.zeros((n, n)), v0=v0,
+                           u_tgt=np.zeros((n, n)), a=af, r_vv=r)
+        _, _, v = oracle.forward(p)
+        m = v.sum()
+        centres.append(np.array([(v * x).sum() / m, (v * y).sum() / m]))
+    w = (centres[1] - centres[0]) / (N - N // 2)
+    return w / np.array(a) - 1.0
+
+
+def test_reacting_plume_centre_moves_with_convection():
+    """Pins V of the source weights (eq. PhiS, V after PC13).  The source
+    deposits first moment V Phi per step; only V = (I - K_v/2) a makes the
+    centre of a reacting plume move at a up to O(r^2) in the reaction rate per
+    step r.  Planted V = a, V = (I + K_v/2) a or swapped components give a
+    first-order error (r/2 and more; halving r only halves it), which this
+    test rejects through the ratio of the errors at r and r/2 (measured 3.90
+    and 2.1e-3 at r = 0.05 here, against ratios 1.45-1.97 and errors up to
+    4.8e-2 with those mistakes)."""
+    e0 = _plume_centre_velocity_error(0.0)
+    e1 = _plume_centre_velocity_error(0.05)
+    e2 = _plume_centre_velocity_error(0.025)
+    print("centre-velocity errors", e0, e1, e2, e1 / e2)
+    assert np.abs(e0).max() < 1e-10          # no source: exact transport speed
+    assert np.abs(e1).max() < 4e-3
+    assert np.all((e1 / e2 > 3.5) & (e1 / e2 < 4.5))
+
+
+def _uniform_chemical_drift(N, chi=1.0, a=(0.06, -0.04), n=48, g0=0.01, sig=4.0):
+    """u^N with and without chemotaxis when v is uniform and produced
+    uniformly (Phi_v = g0 everywhere, r_vu = r_vv = 0): grad v = 0 exactly,
+    so the PDE's chemotactic flux chi u grad v vanishes and u must not feel
+    chi.  Returns ||u(chi) - u(0)|| / ||u(0) - 1||."""
+    Du = _const_aniso(n, (0.08, 0.02), 0.6)
+    Dv = _const_aniso(n, (0.2, 0.05), 1.0)
+    x = np.arange(n)[None, :]
+    y = np.arange(n)[:, None]
+    u0 = 1.0 + 0.5 * np.exp(-((x - n / 2) ** 2 + (y - n / 2) ** 2) / (2 * sig * sig))
+    af = np.broadcast_to(np.array(a, float), (n, n, 2)).copy()
+    g = np.full((N, n, n), g0)
+    us = []
+    for c in (chi, 0.0):
+        p = oracle.Problem(nx=n, ny=n, N=N, Q=9, Du=Du, Dv=Dv, u0=u0, v0=np.ones((n, n)),
+                           u_tgt=np.zeros((n, n)), a=af, chi=c)
+        _, u, v = oracle.forward(p, g)
+        assert np.ptp(v) == 0.0   # the chemical stays uniform
+        us.append(u)
+    return np.linalg.norm(us[0] - us[1]) / np.linalg.norm(us[1] - 1.0)
+
+
+def test_uniform_chemical_exerts_no_chemotactic_drift():
+    """Pins the (1/2) K_v a Phi_v term of grad v (reading of C146) and,
+    again, V.  With uniform v and uniform production Phi, the pre-collision
+    flux settles at j_v - a v = K_v^-1 (V - a) Phi, so the local estimate is
+    G = -[(V - a) + K_v a / 2] Phi / (d_v Cs^2): zero only with both terms as
+    read.  From the equilibrium start G decays like (I - K_v)^n, giving u one
+    bounded displacement; any mistake in either term leaves a constant G, a
+    chemotactic drift of u that grows linearly in time.  Measured: 1.8e-4 at
+    40 and 80 steps; 6e-3 to 4e-2, doubling from 40 to 80 steps, with the term
+    dropped, its sign flipped, its factor 1/2 replaced by 1, or V = a."""
+    d40, d80 = _uniform_chemical_drift(40), _uniform_chemical_drift(80)
+    print("uniform-chemical drift", d40, d80)
+    assert d80 < 1e-3
+    assert d80 < 1.2 * d40
+
+
+def test_advected_reacting_gaussian_closed_form():
+    """Constant convection, anisotropic diffusion and a linear reaction on v
+    (chi = 0): v(t) = e^{rt} G(x - a t; S0 + 2 D_v t) with G a Gaussian
+    (periodic images summed).  Second-order convergence under diffusive
+    refinement (h/2, tau/4, a/2, r/4).  Checks the reaction's time levels
+    (c_n Phi^n + c'_n Phi^{n-1}) against e^{rt} together with convection and
+    anisotropic diffusion; it does not see V (see above)."""
+    D = rotated_tensor((0.08, 0.02), np.array(0.6))
+    Dm = np.array([[D[0], D[1]], [D[1], D[2]]])
+    errs = []
+    for k in range(3):
+        n, s0, N = 32 * 2 ** k, 2.0 * 2 ** k, 25 * 4 ** k
+        a, r = np.array([0.08, -0.04]) / 2 ** k, 0.02 / 4 ** k
+        mu, mass = np.array([n / 2, n / 2]), 100.0 * (n / 32) ** 2
+        v0 = _gauss_field(n, mu, s0 ** 2 * np.eye(2), mass)
+        Df = np.broadcast_to(D, (n, n, 3)).copy()
+        p = oracle.Problem(nx=n, ny=n, N=N, Q=9, Du=Df, Dv=Df, u0=np.zeros((n, n)), v0=v0,
+                           u_tgt=np.zeros((n, n)), a=np.broadcast_to(a, (n, n, 2)).copy(), r_vv=r)
+        _, _, v = oracle.forward(p)
+        exact = np.exp(r * N) * _gauss_field(n, mu + a * N, s0 ** 2 * np.eye(2) + 2 * Dm * N, mass)
+        errs.append(np.linalg.norm(v - exact) / np.linalg.norm(exact))
+    print("advected reacting Gaussian errors", errs)
+    assert errs[0] < 4e-2
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 3.5 < r1 < 4.6 and 3.5 < r2 < 4.6, errs
+
+
+def _spectral_shear_ref(L, T, Du, Dv, chi, rvu, rvv, a0, gsrc, u0, v0, dt=0.02):
+    """Pseudo-spectral RK4 solution of
+    u_t = div(D_u grad u - chi u grad v - a u),
+    v_t = div(D_v grad v - a v) + r_vu u + r_vv v + g(x, t),
+    a = (a0 sin(2 pi y / L), 0), on a periodic square."""
+    n = u0.shape[0]
+    k = 2 * np.pi * np.fft.fftfreq(n, d=L / n)
+    KX, KY = np.meshgrid(k, k)
+    x = np.arange(n)[None, :] * L / n
+    y = np.arange(n)[:, None] * L / n
+    ax = a0 * np.sin(2 * np.pi * y / L) * np.ones_like(x)
+
+    def d(f, K):
+        return np.real(np.fft.ifft2(1j * K * np.fft.fft2(f)))
+
+    def rhs(u, v, t):
+        ux, uy, vx, vy = d(u, KX), d(u, KY), d(v, KX), d(v, KY)
+        fxu = Du[0] * ux + Du[1] * uy - chi * u * vx - ax * u
+        fyu = Du[1] * ux + Du[2] * uy - chi * u * vy
+        fxv = Dv[0] * vx + Dv[1] * vy - ax * v
+        fyv = Dv[1] * vx + Dv[2] * vy
+        return d(fxu, KX) + d(fyu, KY), d(fxv, KX) + d(fyv, KY) + rvu * u + rvv * v + gsrc(x, y, t)
+
+    u, v, t = u0.copy(), v0.copy(), 0.0
+    for _ in range(int(round(T / dt))):
+        k1 = rhs(u, v, t)
+        k2 = rhs(u + dt / 2 * k1[0], v + dt / 2 * k1[1], t + dt / 2)
+        k3 = rhs(u + dt / 2 * k2[0], v + dt / 2 * k2[1], t + dt / 2)
+        k4 = rhs(u + dt * k3[0], v + dt * k3[1], t + dt)
+        u = u + dt / 6 * (k1[0] + 2 * k2[0] + 2 * k3[0] + k4[0])
+        v = v + dt / 6 * (k1[1] + 2 * k2[1] + 2 * k3[1] + k4[1])
+        t += dt
+    return u, v
+
+
+@pytest.mark.slow
+def test_shear_convection_and_source_against_pde():
+    """Chemotaxis with the shear convection of the benchmark workload and a
+    smooth space-time control g: the scheme converges at second order to an
+    independent pseudo-spectral solution (g^n = g(t_n) tau in lattice
+    units).  A consistency check of the convective source path as a whole;
+    by itself it cannot pin V or the (1/2) K_v a Phi_v term (see above)."""
+    L, T = 32, 20
+    Du = rotated_tensor((0.08, 0.02), np.array(0.6))
+    Dv = rotated_tensor((0.2, 0.1), np.array(-0.3))
+    chi, rvu, rvv, a0, gam = -0.1, 0.02, -0.01, 0.1, 0.01
+    kk = 2 * np.pi / L
+
+    def gsrc(x, y, t):
+        return gam * (1 + np.sin(kk * x + 2 * np.pi * 0.3 * t / T) * np.cos(kk * y))
+
+    def init(n):
+        x = np.arange(n)[None, :] * L / n
+        y = np.arange(n)[:, None] * L / n
+        return 1 + 0.2 * np.cos(kk * x) * np.sin(kk * y) + 0.1 * np.sin(2 * kk * x), \
+            1 + 0.3 * np.sin(kk * (x + y)) * np.ones_like(x)
+
+    us, vs = _spectral_shear_ref(L, T, Du, Dv, chi, rvu, rvv, a0, gsrc, *init(L))
+    errs = []
+    for r in (1, 2, 4):
+        n, N = L * r, T * r * r
+        u0, v0 = init(n)
+        x = np.arange(n)[None, :] / r
+        y = np.arange(n)[:, None] / r
+        ax = (a0 / r) * np.sin(kk * y) * np.ones_like(x)
+        g = np.stack([gsrc(x, y, m / r ** 2) / r ** 2 for m in range(N)])
+        p = oracle.Problem(nx=n, ny=n, N=N, Q=9, Du=np.broadcast_to(Du, (n, n, 3)).copy(),
+                           Dv=np.broadcast_to(Dv, (n, n, 3)).copy(), u0=u0, v0=v0, u_tgt=np.zeros((n, n)),
+                           chi=chi, r_vu=rvu / r ** 2, r_vv=rvv / r ** 2,
+                           a=np.stack([ax, np.zeros_like(ax)], -1))
+        _, u, v = oracle.forward(p, g)
+        u, v = u[::r, ::r], v[::r, ::r]
+        errs.append((np.linalg.norm(u - us) / np.linalg.norm(us - us.mean()),
+                     np.linalg.norm(v - vs) / np.linalg.norm(vs - vs.mean())))
+    print("shear + source vs pseudo-spectral", errs)
+    for c in range(2):
+        r1, r2 = errs[0][c] / errs[1][c], errs[1][c] / errs[2][c]
+        assert 3.5 < r1 < 4.6 and 3.5 < r2 < 4.6, errs
+
+
 # --------------------------------------------------------- adjoint / gradient
 
 @pytest.mark.parametrize("case", [
