@@ -123,11 +123,10 @@ def _batch_traffic(nodes, kernel="k_batch_rows"):
         return None
 
 
-def cpu_baseline(nsteps=8):
+def cpu_baseline(nsteps=8, single_thread=True):
     """The FP64 CPU oracle, as it stands, on a bounded sample of the workload:
-    the full 1024x1024 lattice for `nsteps` time steps, forward + adjoint."""
-    import numpy as np  # noqa: F401
-
+    the full 1024x1024 lattice for `nsteps` time steps, forward + adjoint, on
+    all host cores (OpenMP over rows) and, if asked, on one core."""
     import oracle
     from paper_1908_03876_gb300 import workloads as W
 
@@ -135,13 +134,117 @@ def cpu_baseline(nsteps=8):
     w = W.aniso(WORKLOAD["nx"], WORKLOAD["ny"], nsteps, seed=1, precision=64, ckpt_every=nsteps)
     p = oracle.from_workload(w)
     g = w.random_control(0, 0.01)
-    t0 = time.perf_counter()
-    oracle.adjoint(p, g)  # runs the forward and the AMRT sweep
-    dt = time.perf_counter() - t0
-    mlups = w.nx * w.ny * nsteps / dt / 1e6
-    return {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": f"{w.nx}x{w.ny} D2Q9 FP64, {nsteps} of {WORKLOAD['N']} time steps, forward + AMRT adjoint, "
-                      f"{dt:.1f} s, single-threaded C"}
+    ncpu = os.cpu_count() or 1
+
+    def timed(threads):
+        used = oracle.set_threads(threads)
+        t0 = time.perf_counter()
+        oracle.adjoint(p, g)  # runs the forward and the AMRT sweep
+        dt = time.perf_counter() - t0
+        return w.nx * w.ny * nsteps / dt / 1e6, dt, used
+
+    mlups, dt, used = timed(ncpu)
+    out = {"value": mlups, "unit": "MLUPS", "cores": used, "kind": "oracle", "nproc": ncpu,
+           "sample": f"{w.nx}x{w.ny} D2Q9 FP64, {nsteps} of {WORKLOAD['N']} time steps, forward + AMRT adjoint, "
+                     f"{dt:.1f} s, C with OpenMP over rows on {used} threads"}
+    if single_thread:
+        m1, dt1, _ = timed(1)
+        out["single_thread"] = {"value": m1, "unit": "MLUPS", "cores": 1, "seconds": dt1}
+        oracle.set_threads(ncpu)
+    return out
+
+
+def geometry_block(dev, staging, steps=5, warmup=2, N=20, k=10):
+    """The complex-geometry workload (4096x4096 D2Q9 FP32, random solid discs,
+    20% solid, one-cell solid frame, control on a 256x256 masked window) on
+    its full grid: per-launch times of the forward, recompute and adjoint
+    kernels from CUDA events over `steps` gradient evaluations of N time steps
+    (checkpoint every k), and the HBM fraction at the algorithmic bytes per
+    fluid node (populations, angle, node-local scalars, one byte of mask) plus
+    the control and gradient bytes of the controlled nodes."""
+    import numpy as np
+    import torch
+
+    from paper_1908_03876_gb300 import workloads as W
+    from paper_1908_03876_gb300.problem import Problem
+
+    w = W.geometry(4096, 4096, N, seed=2, precision=32, ckpt_every=k)
+    fluid = int(np.count_nonzero(w.solid == 0))
+    ctrl = int(np.count_nonzero(w.cmask))
+    prob = Problem(w, device=dev)
+    prob.set_staging(staging == "rows")
+    g = torch.as_tensor(w.random_control(200, 0.01), dtype=torch.float32, device=dev).contiguous()
+    E = torch.empty_like(g)
+    for _ in range(warmup):
+        prob.gradient(g, out=E)
+    torch.cuda.synchronize()
+    prob.set_timing(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(prob.stream)
+    for _ in range(steps):
+        prob.gradient(g, out=E)
+    ev1.record(prob.stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / steps
+    phases = prob.timing()
+    prob.set_timing(False)
+    J, _, _ = prob.norms()
+    prob.close()
+    hbm, peak_kind = _peaks()
+    # algorithmic bytes per fluid node: 144 (populations) + 4 (angle) + 1 (mask) + node-local scalars
+    per_fluid = dict(forward=144 + 4 + 1 + 8, recompute=144 + 4 + 1 + 8 + 12, adjoint=144 + 4 + 1 + 12 + 8)
+    per_ctrl = dict(forward=4, recompute=4, adjoint=8)
+    out = {}
+    for ph in ("forward", "recompute", "adjoint"):
+        t, n = phases[ph]
+        if n <= 0:
+            continue
+        us = t * 1e3 / n
+        byts = per_fluid[ph] * fluid + per_ctrl[ph] * ctrl
+        ach = byts / (us * 1e-6) / 1e9
+        out[ph] = {"us_per_launch": us, "launches": n, "bytes_per_launch": byts, "achieved": ach,
+                   "frac": ach / hbm, "bytes_per_fluid_node": per_fluid[ph], "bytes_per_ctrl_node": per_ctrl[ph]}
+    return {"workload": f"geometry4096: 4096x4096 D2Q9 FP32, {100 * (1 - fluid / w.nx / w.ny):.1f}% solid discs + "
+                        f"frame, control on a 256x256 masked window, {N} steps, checkpoint every {k}",
+            "fluid_nodes": fluid, "controlled_nodes": ctrl, "staging": staging, "ms_per_gradient": ms,
+            "fluid_mlups": fluid * N / (ms * 1e-3) / 1e6, "kernels": out, "peak": hbm, "peak_source": peak_kind,
+            "J": J}
+
+
+def fp32_error_vs_oracle(dev, nx=128, N=None, k=None):
+    """Relative L2 errors of the FP32 GPU path against the FP64 oracle on the
+    benchmark's physics and schedule (N steps, checkpoint every k) at a grid
+    the oracle finishes in seconds: u^N, v^N, dJ/dg and J."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_1908_03876_gb300 import workloads as W
+    from paper_1908_03876_gb300.problem import Problem
+
+    N = N or WORKLOAD["N"]
+    k = k or WORKLOAD["k"]
+    oracle.build()
+    oracle.set_threads(os.cpu_count() or 1)
+    w = W.aniso(nx, nx, N, seed=1, precision=32, ckpt_every=k)
+    g = w.random_control(100, 0.01)
+    p = Problem(w, device=dev)
+    J = float(p.forward(g).item())
+    E = p.adjoint(g).double().cpu().numpy()
+    u, v = p.fields()
+    u, v = u.double().cpu().numpy(), v.double().cpu().numpy()
+    p.close()
+    po = oracle.from_workload(w)
+    Jo, uo, vo = oracle.forward(po, g)
+    _, Eo, _ = oracle.adjoint(po, g)
+
+    def rel(a, b):
+        return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+    return {"workload": f"aniso {nx}x{nx} D2Q9 FP32, {N} steps, checkpoint every {k} (the benchmark's physics "
+                        "and schedule at a size the oracle finishes in seconds)",
+            "u": rel(u, uo), "v": rel(v, vo), "dJdg": rel(E, Eo), "J": abs(J - Jo) / abs(Jo),
+            "tolerance": {"fields": 1e-4, "dJdg": 1e-3}}
 
 
 def run_reference(args, rank, world):
@@ -153,12 +256,13 @@ def run_reference(args, rank, world):
     times = []
     base = None
     for i in range(warm + steps):
-        b = cpu_baseline(nsteps)
+        b = cpu_baseline(nsteps, single_thread=False)
         if i >= warm:
             times.append(b)
         base = b
     val = statistics.mean(t["value"] for t in times)
     base["value"] = val
+    base.pop("single_thread", None)
     line = {"metric": "fwd+adjoint MLUPS", "value": val, "unit": "MLUPS", "n_gpus": args.gpus, "steps": steps,
             "warmup": warm, "ms_per_step": WORKLOAD["nx"] * WORKLOAD["ny"] * WORKLOAD["N"] / val / 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -773,6 +877,8 @@ def main():
     launches_per_step = 3 * w.N - wl["k"] + 3
     if rank == 0:
         cpu = None if args.no_cpu_baseline else cpu_baseline()
+        fp32_err = None if args.profile else fp32_error_vs_oracle(dev)
+        geom = None if args.profile else geometry_block(dev, args.staging)
         line = {
             "metric": "fwd+adjoint MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -786,6 +892,8 @@ def main():
             "roofline": roofline,
             "kernels": roof,
             "cpu_baseline": cpu,
+            "fp32_err_vs_oracle": fp32_err,
+            "geometry4096": geom,
             "clocks": clk,
             "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps,

@@ -147,6 +147,19 @@ cx_status cx_forward(cx_problem* p, const void* g, double* J_dev);
  * Errors: CX_ERR_STATE (no forward since the last cx_create / cx_set_initial). */
 cx_status cx_adjoint(cx_problem* p, const void* g, const void* seed_u, const void* seed_v, void* dJdg);
 
+/* Vector-Jacobian product of the solve (u^N, v^N) = F(g): the same seeded
+ * AMRT sweep as cx_adjoint (the adjoint system with the final condition
+ * given by the seeds, Sec. 3.2.1) without the control-penalty term, i.e.
+ *   vjp = (du^N/dg)^T seed_u + (dv^N/dg)^T seed_v,
+ * device T [W][ctrl_ny][ctrl_nx], zero at uncontrolled nodes; with time
+ * windows the per-step products summed over each window's steps (the chain
+ * rule of g^n = G_w).  seed_u / seed_v: device T [ny][nx], NULL meaning a
+ * zero seed.  g must be the control of the preceding cx_forward.  This is
+ * the backward of a differentiable solve (an autograd function); J and the
+ * penalty belong to cx_adjoint.  Errors: CX_ERR_INVALID_ARG (vjp NULL),
+ * CX_ERR_STATE (no forward). */
+cx_status cx_adjoint_vjp(cx_problem* p, const void* g, const void* seed_u, const void* seed_v, void* vjp);
+
 /* cx_forward followed by cx_adjoint with NULL seeds: J (device double, may be
  * NULL) and dJ/dg. */
 cx_status cx_gradient(cx_problem* p, const void* g, void* dJdg, double* J_dev);
@@ -474,21 +487,30 @@ cx_status cx_nn_cast_bf16(const float* in, uint16_t* out, size_t n, cudaStream_t
  *   g        device T [W][ctrl_ny][ctrl_nx], W = ctrl_windows or N control, or NULL (zero control)
  *   J_dev    device double: the cost J (may be NULL)
  *   uN, vN   device T [ny][nx]: u^N, v^N (either may be NULL)
+ *   status_dev device int (may be NULL): written when the queued work ends,
+ *            with CX_OK, CX_ERR_TIMEOUT (a bounded wait of a row-window
+ *            kernel ran out: the outputs are not valid) or CX_ERR_UNSTABLE
+ *            (J is not finite).  The call's return value covers only what
+ *            the host checks before queueing the work.
  *   stream   the stream every operation is ordered on; asynchronous
  *
- * Limits and sharing: problems whose scratch (three population lattices,
- * six node fields and the reduction slots; about 2 * (6 Q + 8) * sizeof(T)
- * bytes per node) exceeds CX_STATIC_SCRATCH_BYTES are rejected with
- * CX_ERR_WORKSPACE.  Every call uses the same array and leaves its contents
- * there; the call clears what it accumulates into, but two calls that overlap
- * on the GPU (different streams or host threads) race on the array.  The
- * first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.
+ * Limits and sharing: the scratch is three population lattices (2Q planes
+ * each), 5 to 13 node planes (Phi, u^N, v^N, the terminal seed and the
+ * target, plus the angle, tensor or velocity fields the descriptor asks for),
+ * one byte per node of solid mask and per control node of control mask, and
+ * 16 max(ceil(nx/32) ny, 32768) bytes of FP64 partial sums: about
+ * (6Q + 6) sizeof(T) bytes per node for the rotated-tensor workloads, so up
+ * to about 520 x 520 nodes in FP32 with D2Q9.  Problems that need more than
+ * CX_STATIC_SCRATCH_BYTES are rejected with CX_ERR_WORKSPACE.  Every call
+ * uses the same array and leaves its contents there; the call clears what it
+ * accumulates into, but two calls that overlap on the GPU (different streams
+ * or host threads) race on the array.  Each call looks up the array's device
+ * address (cudaGetSymbolAddress, with the caller's device current), which
+ * allocates nothing.
  * Errors: CX_ERR_INVALID_ARG, CX_ERR_WORKSPACE (too large), CX_ERR_CUDA. */
-#define CX_STATIC_SCRATCH_BYTES (32u << 20)
+#define CX_STATIC_SCRATCH_BYTES (64u << 20)
 cx_status cx_forward_static(const cx_problem_desc* desc, const void* u0, const void* v0, const void* g,
-                            double* J_dev, void* uN, void* vN, cudaStream_t stream);
+                            double* J_dev, void* uN, void* vN, int* status_dev, cudaStream_t stream);
 
 /* Release the host object (the workspace stays the caller's). */
 cx_status cx_destroy(cx_problem* p);

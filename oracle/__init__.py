@@ -29,14 +29,15 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (portable flags: x86_64 and aarch64)."""
+    """Compile the oracle with gcc (portable flags: x86_64 and aarch64; the
+    per-node loops run on OpenMP threads, bitwise independent of their count)."""
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < max(
         os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "mrt_oracle.h"))
     ):
         tmp = _SO + f".{os.getpid()}.tmp"
         subprocess.check_call(
-            ["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-ffp-contract=off", "-o", tmp, _SRC, "-lm"]
+            ["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-ffp-contract=off", "-fopenmp", "-o", tmp, _SRC, "-lm"]
         )
         os.replace(tmp, _SO)
     return _SO
@@ -70,12 +71,20 @@ def _load():
         lib.or_tlm.argtypes = [P, vp, vp, vp, vp, vp, dp]
         lib.or_adjoint.argtypes = [P, vp, vp, vp, vp, vp, dp]
         lib.or_cadjoint.argtypes = [P, vp, vp, dp]
+        lib.or_set_threads.argtypes = [ctypes.c_int]
+        lib.or_set_threads.restype = ctypes.c_int
         lib.or_lattice.argtypes = [ctypes.c_int, vp, vp, vp, vp]
         lib.or_feq.argtypes = [ctypes.c_int, ctypes.c_double, vp, ctypes.c_double, vp]
         lib.or_collide_node.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp,
                                         ctypes.c_double, ctypes.c_double, vp, vp, dp]
         _lib = lib
     return _lib
+
+
+def set_threads(n: int = 0) -> int:
+    """Threads of the oracle's per-node loops (n <= 0: leave as is); returns
+    the count in use.  Results are bitwise the same for every count."""
+    return int(_load().or_set_threads(int(n)))
 
 
 def _ptr(a):

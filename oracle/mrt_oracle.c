@@ -18,12 +18,20 @@
  *     is solid.
  *   - control g^n drives step n -> n+1 (n = 0..N-1); J = 1/2 sum (u^N - u_tgt)^2
  *     + alpha sum_{n<N} sum g^2; the gradient is the exact gradient of this J.
+ *
+ * The per-node loops (collision, streaming, set-up) run rows in parallel with
+ * OpenMP when it is compiled in; every node's arithmetic and every sum's order
+ * are those of the serial loops, so results are bitwise the same for any
+ * thread count (or_set_threads).
  */
 #include "mrt_oracle.h"
 
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define CS2 (1.0 / 3.0)
 
@@ -384,6 +392,7 @@ int or_collide_node(const or_problem* p, int x, int y, int n, const double* f_u,
 static void stream_pull(const lattice_t* L, const or_problem* p, const double* P, double* f) {
     int Q = L->Q, nx = p->nx, ny = p->ny;
     memset(f, 0, sizeof(double) * (size_t)nx * ny * 2 * Q);
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             if (is_solid(p, x, y)) continue;
@@ -405,6 +414,7 @@ static void stream_pull(const lattice_t* L, const or_problem* p, const double* P
 static void stream_pull_T(const lattice_t* L, const or_problem* p, const double* psi, double* rho) {
     int Q = L->Q, nx = p->nx, ny = p->ny;
     memset(rho, 0, sizeof(double) * (size_t)nx * ny * 2 * Q);
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             if (is_solid(p, x, y)) continue;
@@ -424,6 +434,7 @@ static void stream_pull_T(const lattice_t* L, const or_problem* p, const double*
 static void init_populations(const lattice_t* L, const or_problem* p, double* f) {
     int Q = L->Q, nx = p->nx, ny = p->ny;
     memset(f, 0, sizeof(double) * (size_t)nx * ny * 2 * Q);
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             if (is_solid(p, x, y)) continue;
@@ -452,14 +463,16 @@ static int run_forward(const or_problem* p, const double* g, double* fN, double*
     double* P = calloc(npop, sizeof(double));
     double* Phi = calloc(nn, sizeof(double));
     node_t* nodes = malloc(sizeof(node_t) * nn);
-    if (!f || !P || !Phi || !nodes) return -2;
+    double* Th = (mass_u || mass_v || sum_phi) ? calloc(2 * nn, sizeof(double)) : NULL;
+    if (!f || !P || !Phi || !nodes || ((mass_u || mass_v || sum_phi) && !Th)) return -2;
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) node_params(&L, p, x, y, &nodes[y * nx + x]);
     init_populations(&L, p, f);
     for (int n = 0; n < p->N; ++n) {
         if (traj) memcpy(traj + (size_t)n * npop, f, sizeof(double) * npop);
-        double mu = 0.0, mv = 0.0, sp = 0.0;
         memset(P, 0, sizeof(double) * npop);
+#pragma omp parallel for schedule(static)
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x) {
                 if (is_solid(p, x, y)) continue;
@@ -468,10 +481,21 @@ static int run_forward(const or_problem* p, const double* g, double* fN, double*
                 collide_local(&L, p, &nodes[k], n, f + (k * 2) * Q, f + (k * 2 + 1) * Q, g_at(p, g, n, x, y),
                               Phi[k], P + (k * 2) * Q, P + (k * 2 + 1) * Q, &st);
                 Phi[k] = st.Phi;
-                mu += st.Theta_u;
-                mv += st.Theta_v;
-                sp += st.Phi;
+                if (Th) {
+                    Th[2 * k] = st.Theta_u;
+                    Th[2 * k + 1] = st.Theta_v;
+                }
             }
+        double mu = 0.0, mv = 0.0, sp = 0.0;
+        if (Th)
+            for (int y = 0; y < ny; ++y)
+                for (int x = 0; x < nx; ++x) {
+                    if (is_solid(p, x, y)) continue;
+                    size_t k = (size_t)y * nx + x;
+                    mu += Th[2 * k];
+                    mv += Th[2 * k + 1];
+                    sp += Phi[k];
+                }
         if (Phi_traj) memcpy(Phi_traj + (size_t)n * nn, Phi, sizeof(double) * nn);
         if (mass_u) mass_u[n] = mu;
         if (mass_v) mass_v[n] = mv;
@@ -483,6 +507,7 @@ static int run_forward(const or_problem* p, const double* g, double* fN, double*
     free(P);
     free(Phi);
     free(nodes);
+    free(Th);
     return 0;
 }
 
@@ -565,6 +590,7 @@ int or_tlm(const or_problem* p, const double* g, const double* dg, const double*
     double *Phi = calloc(nn, sizeof(double)), *dPhi = calloc(nn, sizeof(double));
     node_t* nodes = malloc(sizeof(node_t) * nn);
     if (!f || !P || !df || !dP || !Phi || !dPhi || !nodes) return -2;
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) node_params(&L, p, x, y, &nodes[y * nx + x]);
     init_populations(&L, p, f);
@@ -576,13 +602,14 @@ int or_tlm(const or_problem* p, const double* g, const double* dg, const double*
                 for (int j = 0; j < 2 * Q; ++j) df[k * 2 * Q + j] = df0[k * 2 * Q + j];
             }
     }
-    double Pi[9][9], feq[9], dfeq[9];
     for (int n = 0; n < p->N; ++n) {
         memset(P, 0, sizeof(double) * npop);
         memset(dP, 0, sizeof(double) * npop);
+#pragma omp parallel for schedule(static)
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x) {
                 if (is_solid(p, x, y)) continue;
+                double Pi[9][9], dfeq[9];
                 size_t k = (size_t)y * nx + x;
                 const node_t* nd = &nodes[k];
                 const double *fu = f + (k * 2) * Q, *fv = f + (k * 2 + 1) * Q;
@@ -624,7 +651,6 @@ int or_tlm(const or_problem* p, const double* g, const double* dg, const double*
                 }
                 Phi[k] = st.Phi;
                 dPhi[k] = dPh;
-                (void)feq;
             }
         stream_pull(&L, p, P, f);
         stream_pull(&L, p, dP, df);
@@ -677,6 +703,7 @@ int or_adjoint(const or_problem* p, const double* g, const double* seed_u, const
     if (!traj || !Phi_traj || !fN || !psi || !rho || !sigma_next || !sigma_now || !u || !nodes) return -2;
     int rc = run_forward(p, g, fN, traj, Phi_traj, NULL, NULL, NULL);
     if (rc) return rc;
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) node_params(&L, p, x, y, &nodes[y * nx + x]);
     macro_fields(p, fN, u, NULL);
@@ -696,15 +723,16 @@ int or_adjoint(const or_problem* p, const double* g, const double* seed_u, const
         }
     if (dJdg) memset(dJdg, 0, sizeof(double) * nc * (size_t)N);
 
-    double Pi[9][9], mt[9], psi_u[9], psi_v[9];
     for (int n = N - 1; n >= 0; --n) {
         /* streaming along -e_i, backward in time */
         stream_pull_T(&L, p, psi, rho);
         memset(psi, 0, sizeof(double) * npop);
         const double* f = traj + (size_t)n * npop;
+#pragma omp parallel for schedule(static)
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x) {
                 if (is_solid(p, x, y)) continue;
+                double Pi[9][9], mt[9], psi_u[9], psi_v[9];
                 size_t k = (size_t)y * nx + x;
                 const node_t* nd = &nodes[k];
                 const double *fu = f + (k * 2) * Q, *fv = f + (k * 2 + 1) * Q;
@@ -785,6 +813,16 @@ int or_adjoint(const or_problem* p, const double* g, const double* seed_u, const
 
 /* ------------------------------------------------------ unit-test access */
 
+int or_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
 int or_lattice(int Q, int* e, double* w, double* M, double* Minv) {
     lattice_t L;
     if (lattice_init(&L, Q)) return -1;
@@ -845,6 +883,7 @@ int or_cadjoint(const or_problem* p, const double* g, double* dJdg, double* J) {
     double* u = malloc(sizeof(double) * nn);
     macro_fields(p, fN, u, NULL);
     if (J) *J = terminal_cost(p, u) + control_penalty(p, g);
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             size_t k = (size_t)y * nx + x;
@@ -869,13 +908,14 @@ int or_cadjoint(const or_problem* p, const double* g, double* dJdg, double* J) {
         }
     size_t nctrl = (size_t)p->cnx * p->cny;
     memset(dJdg, 0, sizeof(double) * (size_t)N * nctrl);
-    double Pi[9][9], feq[9];
     for (int n = N - 1; n >= 0; --n) {
         const double* f = traj + (size_t)n * npop; /* forward pre-collision state of step n */
         memset(Pa, 0, sizeof(double) * npop);
+#pragma omp parallel for schedule(static)
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x) {
                 if (is_solid(p, x, y)) continue;
+                double Pi[9][9], feq[9];
                 size_t k = (size_t)y * nx + x;
                 const node_t* nd = &nodes[k];
                 /* forward quantities of step n: u^n and grad v^n */

@@ -54,6 +54,11 @@ typedef struct {
     const double* v0;            /* [ny][nx] initial v */
 } or_problem;
 
+/* Threads of the per-node loops (OpenMP builds; n <= 0 leaves the count as it
+ * is).  Returns the count now in use (1 without OpenMP).  Results do not
+ * depend on it. */
+int or_set_threads(int n);
+
 /* Lattice tables for unit tests: e [Q][2], w [Q], M [Q][Q], Minv [Q][Q]. */
 int or_lattice(int Q, int* e, double* w, double* M, double* Minv);
 

@@ -20,7 +20,8 @@ STATUS = {
 
 # every exported symbol of include/cxlbm.h
 EXPORTS = [
-    "cx_workspace_size", "cx_create", "cx_set_initial", "cx_forward", "cx_adjoint", "cx_gradient", "cx_step",
+    "cx_workspace_size", "cx_create", "cx_set_initial", "cx_forward", "cx_adjoint", "cx_adjoint_vjp",
+    "cx_gradient", "cx_step",
     "cx_get_fields", "cx_get_psi0", "cx_get_norms", "cx_set_launch", "cx_set_timing", "cx_get_timing",
     "cx_destroy", "cx_status_string", "cx_forward_static", "cx_cg_step", "cx_cg_reset",
     "cx_tlm", "cx_lma_step", "cx_cadjoint", "cx_set_staging",
@@ -33,7 +34,7 @@ EXPORTS = [
     "cx_nn_adam", "cx_nn_cast_bf16", "cx_nn_conv_forward_f32", "cx_nn_smooth", "cx_nn_packed_weights",
     "cx_nn_pack_weights", "cx_nn_conv_tc_tile", "cx_nn_conv_forward_tc",
 ]
-STATIC_SCRATCH_BYTES = 32 << 20  # CX_STATIC_SCRATCH_BYTES of include/cxlbm.h
+STATIC_SCRATCH_BYTES = 64 << 20  # CX_STATIC_SCRATCH_BYTES of include/cxlbm.h
 
 
 class CxError(RuntimeError):
@@ -98,6 +99,7 @@ def load():
         "cx_set_initial": [vp, vp, vp],
         "cx_forward": [vp, vp, vp],
         "cx_adjoint": [vp, vp, vp, vp, vp],
+        "cx_adjoint_vjp": [vp, vp, vp, vp, vp],
         "cx_gradient": [vp, vp, vp, vp],
         "cx_step": [vp, vp, vp, ctypes.POINTER(StepInfo)],
         "cx_get_fields": [vp, vp, vp],
@@ -107,7 +109,7 @@ def load():
         "cx_set_timing": [vp, cint],
         "cx_get_timing": [vp, dp, ctypes.POINTER(ctypes.c_longlong)],
         "cx_destroy": [vp],
-        "cx_forward_static": [D, vp, vp, vp, vp, vp, vp, vp],
+        "cx_forward_static": [D, vp, vp, vp, vp, vp, vp, vp, vp],
         "cx_cg_step": [vp, vp, vp, cint, ctypes.POINTER(CGInfo)],
         "cx_cg_reset": [vp],
         "cx_tlm": [vp, vp, vp, vp, vp, dp],

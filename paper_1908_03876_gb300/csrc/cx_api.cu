@@ -208,10 +208,15 @@ template <typename T> static cx_status run_forward(cx_problem* p, const T* g, co
     return CX_OK;
 }
 
+// penalty = false: the control-penalty term 2 alpha g^n is left out of the
+// gradient, which is then the plain vector-Jacobian product of the solve.
 template <typename T>
-static cx_status run_adjoint(cx_problem* p, const T* g, const T* seed_u, const T* seed_v, T* dJdg) {
+static cx_status run_adjoint(cx_problem* p, const T* g, const T* seed_u, const T* seed_v, T* dJdg,
+                             bool penalty = true) {
     const Layout& Ly = p->lay;
     const CxConst& C = p->C;
+    KConst<T> KA = p->kc((T*)nullptr);
+    if (!penalty) KA.two_alpha = T(0);
     double* part = p->at<double>(Ly.off_part);
     double* e2 = part + 2 * (size_t)Ly.nparts;
     double* emax = part + 3 * (size_t)Ly.nparts;
@@ -267,7 +272,7 @@ static cx_status run_adjoint(cx_problem* p, const T* g, const T* seed_u, const T
             A.e2_part = e2;
             A.emax_part = emax;
             A.n = n;
-            CX_CUDA(launch_adjoint<T>(C, p->kc((T*)nullptr), A, p->La, p->stream));
+            CX_CUDA(launch_adjoint<T>(C, KA, A, p->La, p->stream));
             psi_in = out;
         }
         range_end(p, r, n1 - n0);
@@ -885,6 +890,19 @@ cx_status cx_adjoint(cx_problem* p, const void* g, const void* seed_u, const voi
     if (p->lay.esz == 8)
         return run_adjoint<double>(p, (const double*)g, (const double*)seed_u, (const double*)seed_v, (double*)dJdg);
     return run_adjoint<float>(p, (const float*)g, (const float*)seed_u, (const float*)seed_v, (float*)dJdg);
+}
+
+cx_status cx_adjoint_vjp(cx_problem* p, const void* g, const void* seed_u, const void* seed_v, void* vjp) {
+    if (!p || !vjp) return CX_ERR_INVALID_ARG;
+    if (!p->fwd_valid) return CX_ERR_STATE;
+    if (!seed_u) { // a zero seed for u^N: the first plane of the tangent-linear scratch, cleared here
+        seed_u = p->ws + p->lay.off_tlm;
+        CX_CUDA(cudaMemsetAsync(p->ws + p->lay.off_tlm, 0, p->lay.plane * p->lay.esz, p->stream));
+    }
+    if (p->lay.esz == 8)
+        return run_adjoint<double>(p, (const double*)g, (const double*)seed_u, (const double*)seed_v, (double*)vjp,
+                                   false);
+    return run_adjoint<float>(p, (const float*)g, (const float*)seed_u, (const float*)seed_v, (float*)vjp, false);
 }
 
 cx_status cx_gradient(cx_problem* p, const void* g, void* dJdg, double* J_dev) {

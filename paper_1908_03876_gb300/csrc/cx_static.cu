@@ -8,9 +8,10 @@
 // All scratch memory of the call lives in one file-scope __device__ array of
 // CX_STATIC_SCRATCH_BYTES (declared in include/cxlbm.h), which every GPU that
 // loads the library holds until the process exits.  Host code cannot use the
-// array's name as a device address, so the address is obtained once per
-// device with cudaGetSymbolAddress (on the first call on that device, with the
-// device current) and passed to the kernels.
+// array's name as a device address, so every call looks the address up with
+// cudaGetSymbolAddress (with the caller's device current; the lookup
+// allocates nothing) and passes it to the kernels.  Nothing is cached, so a
+// cudaDeviceReset between calls (which reloads the module) is harmless.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -22,9 +23,6 @@ using namespace cx;
 static __device__ __align__(256) unsigned char cx_static_scratch[CX_STATIC_SCRATCH_BYTES];
 
 namespace {
-
-constexpr int MAX_DEVICES = 64;
-void* g_scratch[MAX_DEVICES] = {};
 
 inline size_t up256(size_t v) { return (v + 255) / 256 * 256; }
 
@@ -88,9 +86,16 @@ bool k_of(double lam, double dd, double tau, double* k) {
     return lam >= 0.0 && *k > 0.0 && *k < 2.0;
 }
 
+// The call's outcome as a cx_status code, from the status word the kernels set:
+// a bounded wait of a row-window kernel that ran out, or a non-finite cost.
+__global__ void k_status_code(const int* bits, int* out) {
+    const int b = *bits;
+    *out = (b & ST_TIMEOUT) ? (int)CX_ERR_TIMEOUT : ((b & ST_UNSTABLE) ? (int)CX_ERR_UNSTABLE : (int)CX_OK);
+}
+
 template <typename T>
 cx_status run_static(const cx_problem_desc* d, const CxConst& C, const StaticLayout& Ly, char* ws, const T* u0,
-                     const T* v0, const T* g, double* J_dev, T* uN, T* vN, cudaStream_t s) {
+                     const T* v0, const T* g, double* J_dev, T* uN, T* vN, int* status_dev, cudaStream_t s) {
     int nsm = 1, dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
@@ -149,7 +154,12 @@ cx_status run_static(const cx_problem_desc* d, const CxConst& C, const StaticLay
     if (launch_final<T>(C, in, reinterpret_cast<T*>(ws + Ly.off_ut), uN_ws, vN_ws,
                         reinterpret_cast<T*>(ws + Ly.off_wu), cost, L2, s) != cudaSuccess)
         return CX_ERR_CUDA;
-    if (launch_finalize(cost, nb2, gsq, fw, C.alpha, scal, status, 1, 0, s) != cudaSuccess) return CX_ERR_CUDA;
+    if (launch_finalize(cost, nb2, gsq, fw, C.alpha, scal, status, ST_UNSTABLE, 0, s) != cudaSuccess)
+        return CX_ERR_CUDA;
+    if (status_dev) {
+        k_status_code<<<1, 1, 0, s>>>(status, status_dev);
+        if (cudaGetLastError() != cudaSuccess) return CX_ERR_CUDA;
+    }
     const size_t bytes = (size_t)d->nx * d->ny * sizeof(T);
     if (J_dev && cudaMemcpyAsync(J_dev, scal, sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         return CX_ERR_CUDA;
@@ -161,22 +171,17 @@ cx_status run_static(const cx_problem_desc* d, const CxConst& C, const StaticLay
 } // namespace
 
 extern "C" cx_status cx_forward_static(const cx_problem_desc* desc, const void* u0, const void* v0, const void* g,
-                                       double* J_dev, void* uN, void* vN, cudaStream_t stream) {
+                                       double* J_dev, void* uN, void* vN, int* status_dev, cudaStream_t stream) {
     size_t check = 0;
     cx_status rc = cx_workspace_size(desc, &check); // same descriptor validation as cx_create
     if (rc) return rc;
     if (!u0 || !v0) return CX_ERR_INVALID_ARG;
     const StaticLayout Ly = static_layout(desc);
     if (Ly.total > (size_t)CX_STATIC_SCRATCH_BYTES) return CX_ERR_WORKSPACE; // problem too large for the array
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return CX_ERR_CUDA;
-    if (!g_scratch[dev]) {
-        // once per device, with that device current: the array's device address
-        void* ptr = nullptr;
-        if (cudaGetSymbolAddress(&ptr, cx_static_scratch) != cudaSuccess || !ptr) return CX_ERR_CUDA;
-        g_scratch[dev] = ptr;
-    }
-    char* ws = static_cast<char*>(g_scratch[dev]);
+    // the array's device address on the current device (looked up on every call)
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, cx_static_scratch) != cudaSuccess || !ptr) return CX_ERR_CUDA;
+    char* ws = static_cast<char*>(ptr);
 
     CxConst C{};
     C.nx = desc->nx;
@@ -229,7 +234,7 @@ extern "C" cx_status cx_forward_static(const cx_problem_desc* desc, const void* 
     C.cmask = (desc->solid || desc->ctrl_mask) ? reinterpret_cast<uint8_t*>(ws + Ly.off_cmask) : nullptr;
     if (desc->precision == 64)
         return run_static<double>(desc, C, Ly, ws, (const double*)u0, (const double*)v0, (const double*)g, J_dev,
-                                  (double*)uN, (double*)vN, stream);
+                                  (double*)uN, (double*)vN, status_dev, stream);
     return run_static<float>(desc, C, Ly, ws, (const float*)u0, (const float*)v0, (const float*)g, J_dev,
-                             (float*)uN, (float*)vN, stream);
+                             (float*)uN, (float*)vN, status_dev, stream);
 }

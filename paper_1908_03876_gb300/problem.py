@@ -95,6 +95,17 @@ class Problem:
         self._keep_adj = (g, su, sv)  # inputs stay alive until the queued work has read them
         return out
 
+    def vjp(self, g=None, seed_u=None, seed_v=None, out=None):
+        """Vector-Jacobian product (du^N/dg)^T seed_u + (dv^N/dg)^T seed_v of
+        the last forward's solve (no penalty term; None seeds are zero)."""
+        g = self._t(g, self.ctrl_shape)
+        su = self._t(seed_u, (self.w.ny, self.w.nx))
+        sv = self._t(seed_v, (self.w.ny, self.w.nx))
+        out = out if out is not None else torch.empty(self.ctrl_shape, dtype=self.dtype, device=self.device)
+        _lib.check(self.lib.cx_adjoint_vjp(self.h, _ptr(g), _ptr(su), _ptr(sv), _ptr(out)), "cx_adjoint_vjp")
+        self._keep_adj = (g, su, sv)
+        return out
+
     def gradient(self, g=None, out=None):
         g = self._t(g, self.ctrl_shape)
         out = out if out is not None else torch.empty(self.ctrl_shape, dtype=self.dtype, device=self.device)

@@ -57,7 +57,7 @@ def test_autograd_matches_finite_differences():
 
 
 def test_autograd_matches_oracle_vjp():
-    """The backward equals the oracle's seeded adjoint minus the penalty term."""
+    """The backward equals the oracle's seeded adjoint with alpha = 0."""
     from paper_1908_03876_gb300.autograd import solve
     from paper_1908_03876_gb300.problem import Problem
 
@@ -81,6 +81,47 @@ def test_autograd_matches_oracle_vjp():
         err = np.linalg.norm(a.cpu().numpy() - b) / np.linalg.norm(b)
         print(f"VJP through {name}^N vs oracle: rel L2 {err:.2e}")
         assert err < 1e-12
+
+
+def test_autograd_windowed_control_with_penalty():
+    """Time-windowed control (W = 4 windows of 3 steps) with alpha > 0: the
+    backward is the library's penalty-free vector-Jacobian product, equal to
+    the oracle's seeded adjoint with alpha = 0 (summed over each window's
+    steps), and to central differences of a loss that adds its own penalty."""
+    from paper_1908_03876_gb300.autograd import solve
+    from paper_1908_03876_gb300.problem import Problem
+
+    w = W.aniso(40, 32, 12, seed=9, precision=64, ckpt_every=5)
+    w.windows = 4
+    w.alpha = 0.05
+    p = Problem(w)
+    rng = np.random.default_rng(7)
+    su, sv = rng.standard_normal((w.ny, w.nx)), rng.standard_normal((w.ny, w.nx))
+    tsu, tsv = torch.as_tensor(su, device=p.device), torch.as_tensor(sv, device=p.device)
+    g0 = w.random_control(8, 0.05)
+    assert g0.shape == (4, 32, 40)
+
+    def loss_of(g):
+        u, v = solve(g, p)
+        return (tsu * u).sum() + (tsv * v).sum() + 0.7 * (g * g).sum()
+
+    g = torch.as_tensor(g0, device=p.device).requires_grad_(True)
+    loss_of(g).backward()
+    po = oracle.from_workload(w)
+    po.alpha = 0.0
+    _, Eo, _ = oracle.adjoint(po, g0, su, sv)
+    vjp = g.grad.cpu().numpy() - 1.4 * g0
+    err = np.linalg.norm(vjp - Eo) / np.linalg.norm(Eo)
+    print(f"windowed VJP (alpha = {w.alpha}) vs oracle with alpha = 0: rel L2 {err:.2e}")
+    assert err < 1e-12
+    h = 1e-6
+    for seed in range(3):
+        d = torch.as_tensor(np.random.default_rng(20 + seed).standard_normal(g.shape), device=p.device)
+        with torch.no_grad():
+            fd = (loss_of(g + h * d) - loss_of(g - h * d)) / (2 * h)
+        ad = (g.grad * d).sum()
+        print(f"direction {seed}: autograd {ad.item():.12e} fd {fd.item():.12e}")
+        assert abs(ad.item() - fd.item()) <= 1e-7 * abs(fd.item()) + 1e-9
 
 
 def test_backward_after_other_forward_recomputes():

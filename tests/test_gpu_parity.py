@@ -418,6 +418,34 @@ def test_cadjoint_row_windows_against_per_thread(window):
     assert d < 1e-5
 
 
+@pytest.mark.parametrize("window", [None, (10, 6, 60, 20)])
+def test_cadjoint_row_windows_fp64_against_oracle(window):
+    """The continuous adjoint with row-window staging (k_cadj_rows takes every
+    step but the first: 200 columns, a partial last row segment, four blocks
+    of 256 threads so each walks many segments) against the oracle's at 1e-12
+    in FP64; the number of entries that differ from per-thread staging is
+    printed."""
+    from paper_1908_03876_gb300.problem import Problem
+
+    w = W.aniso(200, 40, 12, seed=8, precision=64, ckpt_every=5)
+    w.windows = 4
+    w.window = window
+    w.chi = -0.3
+    g = w.random_control(15, 0.05)
+    outs = []
+    for rows in (True, False):
+        p = Problem(w)
+        p.set_launch(256, 4)
+        p.set_staging(rows)
+        p.forward(g)
+        outs.append(p.cadjoint(g).cpu().numpy())
+    _, Eo = oracle.cadjoint(oracle.from_workload(w), g)
+    e = rel(outs[0], Eo)
+    nd = int(np.count_nonzero(outs[0] != outs[1]))
+    print(f"cadjoint row windows fp64 ({window}): rel {e:.2e} vs oracle, {nd} entries differ from per-thread")
+    assert e < 1e-12
+
+
 @pytest.mark.parametrize("case", ["aniso", "geometry"])
 def test_continuous_adjoint_matches_oracle_fp64(case):
     """Continuous-adjoint gradient (time-reversed MRT solve of the adjoint
@@ -472,6 +500,23 @@ def test_geometry_fp32_against_fp64_oracle():
     w = W.geometry(96, 96, 40, seed=2, precision=32, ckpt_every=10, win=48, rmin=3, rmax=10)
     g = w.random_control(10, 0.02)
     check(run_both(w, g), TOL32_FIELD, TOL32_GRAD, "geometry fp32")
+
+
+@pytest.mark.parametrize("case", ["aniso128_2000", "geometry80_5000"])
+def test_fp32_at_full_horizon_against_fp64_oracle(case):
+    """FP32 lattices over the benchmark workloads' full horizons, element-wise
+    against the FP64 oracle: the anisotropic problem (shear convection,
+    chemotaxis) at 128x128 for 2000 steps with a checkpoint every 100, and
+    the complex-geometry problem (discs, bounce-back, masked control window)
+    at 80x80 for 5000 steps with a checkpoint every 100.  u^N and v^N within
+    1e-4 relative L2, dJ/dg within 1e-3; the measured errors are printed."""
+    if case == "aniso128_2000":
+        w = W.aniso(128, 128, 2000, seed=1, precision=32, ckpt_every=100)
+    else:
+        w = W.geometry(80, 80, 5000, seed=2, precision=32, ckpt_every=100, win=40, rmin=3, rmax=8)
+    g = w.random_control(9, 0.01)
+    oracle.set_threads(0)
+    check(run_both(w, g), TOL32_FIELD, TOL32_GRAD, f"{case} fp32 vs fp64 oracle")
 
 
 # ------------------------------------------------- full-size workload (sampled)
