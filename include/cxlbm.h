@@ -497,7 +497,8 @@ cx_status cx_nn_cast_bf16(const float* in, uint16_t* out, size_t n, cudaStream_t
  * Limits and sharing: the scratch is three population lattices (2Q planes
  * each), 5 to 13 node planes (Phi, u^N, v^N, the terminal seed and the
  * target, plus the angle, tensor or velocity fields the descriptor asks for),
- * one byte per node of solid mask and per control node of control mask, and
+ * two bytes per node of solid mask and bounce-back flags, one per control
+ * node of control mask, and
  * 16 max(ceil(nx/32) ny, 32768) bytes of FP64 partial sums: about
  * (6Q + 6) sizeof(T) bytes per node for the rotated-tensor workloads, so up
  * to about 520 x 520 nodes in FP32 with D2Q9.  Problems that need more than

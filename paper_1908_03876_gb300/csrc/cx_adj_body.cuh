@@ -35,11 +35,13 @@ __device__ __forceinline__ void adj_stage(const CxConst& C, const Args& A, const
     const size_t pl = (size_t)C.plane;
     const int xm = x == 0 ? C.nx - 1 : x - 1, xp = x == C.nx - 1 ? 0 : x + 1;
     const int rm = (y == 0 ? C.ny - 1 : y - 1) * C.nx, r0 = y * C.nx, rp = (y == C.ny - 1 ? 0 : y + 1) * C.nx;
+    const unsigned bb = C.has_solid ? C.bounce[k] : 0u; // forward pulls that bounce back
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const int xd = L::ex(i) > 0 ? xp : (L::ex(i) < 0 ? xm : x);
         const int kd = (L::ey(i) > 0 ? rp : (L::ey(i) < 0 ? rm : r0)) + xd;
-        const bool bounce = C.has_solid && i != 0 && C.solid[kd];
+        // x + e_i is solid exactly when the forward pull of direction opp(i) bounces back
+        const bool bounce = i != 0 && ((bb >> (L::opp(i) - 1)) & 1u);
         if (A.terminal) {
             // psi^N_i(x) is the seed w(x) in every direction
             cp_async(s + i * NT, A.wu + (bounce ? k : kd));
@@ -72,8 +74,13 @@ __device__ __forceinline__ void adj_compute(const CxConst& C, const KConst<T>& K
     T ru[Q], rv[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        ru[i] = S.pop(i, L::ex(i));
-        rv[i] = (A.terminal && !A.wv) ? T(0) : S.pop(Q + i, L::ex(i));
+        if (S.adj_bounce(i)) { // bounce-back transposed: the node's own opposite adjoint population
+            ru[i] = ldg(A.in(L::opp(i)) + k);
+            rv[i] = ldg(A.in(Q + L::opp(i)) + k);
+        } else {
+            ru[i] = S.pop(i, L::ex(i));
+            rv[i] = (A.terminal && !A.wv) ? T(0) : S.pop(Q + i, L::ex(i));
+        }
     }
     const T Tu = S.val(2 * Q);
     const T Gx = S.val(2 * Q + 1);

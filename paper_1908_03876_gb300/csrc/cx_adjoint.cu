@@ -27,6 +27,7 @@
 #include <algorithm>
 
 #include "cx_adj_body.cuh"
+#include "cx_rows.cuh"
 
 namespace cx {
 
@@ -96,7 +97,8 @@ static cudaError_t launch_q(const CxConst& C, const KConst<T>& K, const AdjArgs<
 
 // Bulk copies of one row segment's stage (issued by one thread): the 2Q
 // windows of psi^{n+1}, the tape (u, G_x, G_y), sigma^{n+1}, g (whole-grid
-// control) and the angle (rotated tensors).
+// control), the angle (rotated tensors) and, on grids with solid nodes, the
+// bounce-back flags (one byte per node).
 template <typename T, int Q, int NT>
 __device__ __forceinline__ void adj_issue_rows(const CxConst& C, const AdjArgs<T>& A, int y, int x0, T* st,
                                                uint64_t* bar) {
@@ -106,7 +108,8 @@ __device__ __forceinline__ void adj_issue_rows(const CxConst& C, const AdjArgs<T
     const int rm = y == 0 ? C.ny - 1 : y - 1, rp = y == C.ny - 1 ? 0 : y + 1;
     const bool rot = C.aniso == CX_ANISO_ROTATED, gb = A.g && C.ctrl_full;
     const uint32_t nb = (uint32_t)nv * sizeof(T);
-    mbar_expect_tx(bar, (uint32_t)(2 * Q * (nv + 2 * RW::H)) * sizeof(T) + nb * (4u + gb + rot) + A.tx_pad);
+    mbar_expect_tx(bar, (uint32_t)(2 * Q * (nv + 2 * RW::H)) * sizeof(T) + nb * (4u + gb + rot) +
+                            (C.has_solid ? (uint32_t)nv : 0u) + A.tx_pad);
 #pragma unroll
     for (int j = 0; j < 2 * Q; ++j) {
         const int i = j < Q ? j : j - Q;
@@ -121,6 +124,7 @@ __device__ __forceinline__ void adj_issue_rows(const CxConst& C, const AdjArgs<T
     bulk_g2s(loc + 3 * NT, A.sigma + k0, nb, bar);
     if (gb) bulk_g2s(loc + 4 * NT, A.g + k0, nb, bar);
     if (rot) bulk_g2s(loc + 5 * NT, reinterpret_cast<const T*>(C.theta) + k0, nb, bar);
+    if (C.has_solid) bulk_g2s(loc + 6 * NT, C.bounce + k0, (uint32_t)nv, bar);
 }
 
 // g of a controlled node when the control window is not the whole grid
@@ -132,66 +136,41 @@ __device__ __forceinline__ void adj_stage_ctrl(const CxConst& C, const AdjArgs<T
 }
 
 template <typename T, int Q, int NT> constexpr int adj_rows_stage_values() {
-    return 2 * Q * RowWindow<T, Q, NT>::W + 6 * NT;
+    return 2 * Q * RowWindow<T, Q, NT>::W + 6 * NT + NT / (int)sizeof(T); // + one flag byte per node
 }
 template <typename T, int Q, int NT> constexpr size_t adj_rows_smem() {
-    return (size_t)2 * adj_rows_stage_values<T, Q, NT>() * sizeof(T) + 2 * sizeof(uint64_t);
+    return rows_pipe_smem<T>(adj_rows_stage_values<T, Q, NT>());
 }
 
-template <typename T, int Q, int NT>
-__global__ void __launch_bounds__(NT) k_adjoint_rows(const CxConst C, const KConst<T> KC, const AdjArgs<T> A) {
+// SB: the grid has solid nodes (bounce-back flags staged with each segment).
+// Block: NT compute threads and one producer warp (see cx_rows.cuh).
+template <typename T, int Q, int NT, bool SB>
+__global__ void __launch_bounds__(NT + 32, sizeof(T) == 4 ? (NT == 256 ? 3 : 5) : 1)
+    k_adjoint_rows(const CxConst C, const KConst<T> KC, const AdjArgs<T> A) {
     using RW = RowWindow<T, Q, NT>;
-    constexpr int SV = adj_rows_stage_values<T, Q, NT>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* const st0 = reinterpret_cast<T*>(smem_raw);
-    T* const st1 = st0 + SV;
-    uint64_t* const bar = reinterpret_cast<uint64_t*>(st1 + SV);
-    if (threadIdx.x == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        mbar_init_fence();
-    }
-    typename SqAccT<T>::type acc;
-    ChunkIter<NT> it(C);
-    NodeIdx cur = it.valid() ? it.node(C) : no_node();
+    RowsPipe<T, NT> pipe(smem_raw, adj_rows_stage_values<T, Q, NT>());
+    pipe.init();
     allow_next_grid();
     wait_prior_grid(); // the previous step's populations and node state are complete
     if (block_sees_timeout(A.status)) return;
-    if (it.valid()) {
-        if (threadIdx.x == 0) adj_issue_rows<T, Q, NT>(C, A, it.y, it.seg * NT, st0, &bar[0]);
-        adj_stage_ctrl<T, Q, NT>(C, A, cur, st0);
+    if (threadIdx.x >= NT) {
+        pipe.produce(C, A.status,
+                     [&](int y, int x0, T* st, uint64_t* bar) { adj_issue_rows<T, Q, NT>(C, A, y, x0, st, bar); });
+        return;
     }
-    cp_async_commit();
-    unsigned phase = 0; // bit b: parity of stage b's next completion
-    int b = 0;          // stage of the current segment
-    bool ok = true;
-    while (it.valid()) {
-        it.next();
-        const NodeIdx nxt = it.valid() ? it.node(C) : no_node();
-        T* const sn = b ? st0 : st1;
-        if (it.valid()) { // stage b^1 is free: every thread passed the barrier that ended its last use
-            if (threadIdx.x == 0) adj_issue_rows<T, Q, NT>(C, A, it.y, it.seg * NT, sn, &bar[b ^ 1]);
-            adj_stage_ctrl<T, Q, NT>(C, A, nxt, sn);
-        }
-        cp_async_commit();
-        cp_async_wait<1>();
-        ok = mbar_wait(&bar[b], (phase >> b) & 1u);
-        phase ^= 1u << b;
-        if (ok) adj_compute<T, Q, NT, AdjArgs<T>>(C, KC, A, cur, RW{(b ? st1 : st0) + threadIdx.x}, acc);
-        if (__syncthreads_or(!ok)) { // all threads leave together when a stage never completed
-            ok = false;
-            break;
-        }
-        cur = nxt;
-        b ^= 1;
-    }
-    if (!ok) {
-        // bounded waits for the copies still in flight, then report
-        if (it.valid()) mbar_wait(&bar[b ^ 1], (phase >> (b ^ 1)) & 1u);
-        mbar_wait(&bar[b], ((phase >> b) & 1u) ^ 1u);
-        if (threadIdx.x == 0 && A.status) atomicOr(A.status, ST_TIMEOUT);
-    }
-    cp_async_wait<0>();
+    typename SqAccT<T>::type acc;
+    pipe.consume(
+        C, A.status, [&](const NodeIdx& nd, T* st) { adj_stage_ctrl<T, Q, NT>(C, A, nd, st); },
+        [&](const NodeIdx& nd, T* st) {
+            if constexpr (SB) {
+                const unsigned bits = reinterpret_cast<const uint8_t*>(st + 2 * Q * RW::W + 6 * NT)[threadIdx.x];
+                adj_compute<T, Q, NT, AdjArgs<T>>(C, KC, A, nd, RowWindowSolid<T, Q, NT>{{st + threadIdx.x}, bits},
+                                                  acc);
+            } else {
+                adj_compute<T, Q, NT, AdjArgs<T>>(C, KC, A, nd, RW{st + threadIdx.x}, acc);
+            }
+        });
     const int w = blockIdx.x * (NT >> 5) + (threadIdx.x >> 5);
     acc.flush(A.e2_part + w, A.emax_part + w);
 }
@@ -200,7 +179,8 @@ __global__ void __launch_bounds__(NT) k_adjoint_rows(const CxConst C, const KCon
 template <typename T> static bool rows_eligible(const CxConst& C, const AdjArgs<T>& A, const Launch& L) {
     constexpr int H = 16 / (int)sizeof(T);
     auto al = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; };
-    if (!L.row_windows || A.terminal || C.has_solid || C.nx % H != 0) return false;
+    if (!L.row_windows || A.terminal || C.nx % H != 0) return false;
+    if (C.has_solid && (!C.bounce || C.nx % 16 != 0 || !al(C.bounce))) return false;
     if (!rows_pipelined(C, L, L.rows_grid ? std::min(L.rows_grid, L.grid.x) : L.grid.x)) return false;
     if (L.block.x != 128 && L.block.x != 256) return false;
     for (int j = 0; j < 2 * C.Q; ++j)
@@ -211,20 +191,20 @@ template <typename T> static bool rows_eligible(const CxConst& C, const AdjArgs<
     return true;
 }
 
-template <typename T, int Q, int NT>
+template <typename T, int Q, int NT, bool SB>
 static cudaError_t launch_rows_qn(const CxConst& C, const KConst<T>& K, const AdjArgs<T>& A, const Launch& L,
                                   cudaStream_t s) {
     constexpr size_t smem = adj_rows_smem<T, Q, NT>();
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e =
-            cudaFuncSetAttribute(k_adjoint_rows<T, Q, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(k_adjoint_rows<T, Q, NT, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(L.rows_grid ? std::min(L.rows_grid, L.grid.x) : L.grid.x);
-    cfg.blockDim = L.block;
+    cfg.blockDim = dim3(L.block.x + 32); // compute threads + the producer warp
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -234,13 +214,17 @@ static cudaError_t launch_rows_qn(const CxConst& C, const KConst<T>& K, const Ad
     cfg.numAttrs = 1;
     AdjArgs<T> A2 = A;
     A2.tx_pad = L.row_windows == 2 ? 16u : 0u; // test mode: no stage ever completes
-    return cudaLaunchKernelEx(&cfg, k_adjoint_rows<T, Q, NT>, C, K, A2);
+    return cudaLaunchKernelEx(&cfg, k_adjoint_rows<T, Q, NT, SB>, C, K, A2);
 }
 
 template <typename T, int Q>
 static cudaError_t launch_rows_q(const CxConst& C, const KConst<T>& K, const AdjArgs<T>& A, const Launch& L,
                                  cudaStream_t s) {
-    return L.block.x == 128 ? launch_rows_qn<T, Q, 128>(C, K, A, L, s) : launch_rows_qn<T, Q, 256>(C, K, A, L, s);
+    if (C.has_solid)
+        return L.block.x == 128 ? launch_rows_qn<T, Q, 128, true>(C, K, A, L, s)
+                                : launch_rows_qn<T, Q, 256, true>(C, K, A, L, s);
+    return L.block.x == 128 ? launch_rows_qn<T, Q, 128, false>(C, K, A, L, s)
+                            : launch_rows_qn<T, Q, 256, false>(C, K, A, L, s);
 }
 
 template <typename T>
@@ -273,12 +257,18 @@ template <typename T> int adjoint_occupancy(int Q, int threads) {
 template int adjoint_occupancy<float>(int, int);
 template int adjoint_occupancy<double>(int, int);
 
-template <typename T, int Q, int NT> static int rows_occ_qn() {
+template <typename T, int Q, int NT, bool SB> static int rows_occ_qnb() {
     constexpr size_t smem = adj_rows_smem<T, Q, NT>();
-    cudaFuncSetAttribute(k_adjoint_rows<T, Q, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_adjoint_rows<T, Q, NT, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adjoint_rows<T, Q, NT>, NT, smem) != cudaSuccess) return 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adjoint_rows<T, Q, NT, SB>, NT + 32, smem) !=
+        cudaSuccess)
+        return 1;
     return nb > 0 ? nb : 1;
+}
+// the smaller residency of the two forms (the persistent grid serves both)
+template <typename T, int Q, int NT> static int rows_occ_qn() {
+    return std::min(rows_occ_qnb<T, Q, NT, false>(), rows_occ_qnb<T, Q, NT, true>());
 }
 template <typename T, int Q> static int rows_occ_q(int threads) {
     return threads == 128 ? rows_occ_qn<T, Q, 128>() : rows_occ_qn<T, Q, 256>();

@@ -95,6 +95,7 @@ Layout cx::make_layout(const cx_problem_desc* d) {
     L.off_a = take(d->adv == CX_ADV_FIELD ? 2 * fld : (d->adv == CX_ADV_ROW ? 2 * (size_t)d->ny * L.esz : 0));
     L.off_ut = take(fld);
     L.off_solid = take(d->solid ? L.plane : 0);
+    L.off_bounce = take(d->solid ? L.plane : 0);
     L.off_cmask = take((d->solid || d->ctrl_mask) ? L.nctrl : 0);
     L.off_part = take(sizeof(double) * 4 * (size_t)L.nparts);
     L.off_scal = take(sizeof(double) * 16);
@@ -194,13 +195,15 @@ template <typename T> static cx_status run_forward(cx_problem* p, const T* g, co
         CX_CUDA(launch_forward<T>(C, p->kc((T*)nullptr), A, p->Lf, p->stream));
         in = out;
     }
+    range_end(p, r, Ly.N);
+    range_begin(p, PH_OTHER, &r); // u^N, v^N, the terminal seed and the FP64 cost
     double* cost = part;
     CX_CUDA(launch_final<T>(C, in, p->at<T>(Ly.off_ut), p->at<T>(Ly.off_uN), p->at<T>(Ly.off_vN), p->at<T>(Ly.off_wu),
                             cost, p->L, p->stream));
     double* scal = p->at<double>(Ly.off_scal);
     CX_CUDA(launch_finalize(cost, p->nblocks, gsq, fw, C.alpha, scal, p->at<int>(Ly.off_status),
                             flag_unstable ? ST_UNSTABLE : 0, 0, p->stream));
-    range_end(p, r, Ly.N);
+    range_end(p, r, 2);
     if (J_dev) CX_CUDA(cudaMemcpyAsync(J_dev, scal, sizeof(double), cudaMemcpyDeviceToDevice, p->stream));
     p->fwd_valid = true;
     p->adj_valid = false;
@@ -821,6 +824,7 @@ cx_status cx_create(const cx_problem_desc* desc, void* workspace, size_t bytes, 
     C.Kfield = desc->aniso == CX_ANISO_FIELD ? ws + Ly.off_K : nullptr;
     C.a = desc->adv != CX_ADV_NONE ? ws + Ly.off_a : nullptr;
     C.solid = desc->solid ? reinterpret_cast<uint8_t*>(ws + Ly.off_solid) : nullptr;
+    C.bounce = desc->solid ? reinterpret_cast<uint8_t*>(ws + Ly.off_bounce) : nullptr;
     C.cmask = (desc->solid || desc->ctrl_mask) ? reinterpret_cast<uint8_t*>(ws + Ly.off_cmask) : nullptr;
     p->C = C;
     p->Kf = make_kconst<float>(C, C.Q);
@@ -842,11 +846,11 @@ cx_status cx_create(const cx_problem_desc* desc, void* workspace, size_t bytes, 
     if (desc->precision == 64)
         e = launch_setup_fields<double>(C, *desc, (double*)C.theta, (double*)C.Kfield, (double*)C.a,
                                         reinterpret_cast<double*>(ws + Ly.off_ut), (uint8_t*)C.solid,
-                                        (uint8_t*)C.cmask, stream);
+                                        (uint8_t*)C.cmask, (uint8_t*)C.bounce, stream);
     else
         e = launch_setup_fields<float>(C, *desc, (float*)C.theta, (float*)C.Kfield, (float*)C.a,
                                        reinterpret_cast<float*>(ws + Ly.off_ut), (uint8_t*)C.solid,
-                                       (uint8_t*)C.cmask, stream);
+                                       (uint8_t*)C.cmask, (uint8_t*)C.bounce, stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ws + Ly.off_status, 0, sizeof(int) * 4, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) {

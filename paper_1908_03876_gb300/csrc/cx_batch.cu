@@ -338,6 +338,8 @@ template <typename T, int Q> struct TileWindow {
     int pw, nt;
     __device__ __forceinline__ T pop(int j, int sx) const { return pops[j * pw + H + sx]; }
     __device__ __forceinline__ T val(int v) const { return loc[(v - 2 * Q) * nt]; }
+    static constexpr bool fwd_bounce(int) { return false; } // grids with solid nodes use per-thread staging
+    static constexpr bool adj_bounce(int) { return false; }
 };
 
 // population part of a stage: 2Q planes of at most NT / 32 windows (tx >= 32)

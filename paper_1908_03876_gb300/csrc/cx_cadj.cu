@@ -33,11 +33,12 @@ __device__ __forceinline__ void cadj_stage(const CxConst& C, const CadjArgs<T>& 
     } else {
         const int xm = x == 0 ? C.nx - 1 : x - 1, xp = x == C.nx - 1 ? 0 : x + 1;
         const int rm = (y == 0 ? C.ny - 1 : y - 1) * C.nx, r0 = y * C.nx, rp = (y == C.ny - 1 ? 0 : y + 1) * C.nx;
+        const unsigned bb = C.has_solid ? C.bounce[k] : 0u; // pulls that bounce back
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const int xs = L::ex(i) > 0 ? xm : (L::ex(i) < 0 ? xp : x);
             const int ks = (L::ey(i) > 0 ? rm : (L::ey(i) < 0 ? rp : r0)) + xs;
-            if (C.has_solid && i != 0 && C.solid[ks]) {
+            if (i != 0 && ((bb >> (i - 1)) & 1u)) {
                 cp_async(s + i * NT, A.in(L::opp(i)) + k);
                 cp_async(s + (Q + i) * NT, A.in(Q + L::opp(i)) + k);
             } else {

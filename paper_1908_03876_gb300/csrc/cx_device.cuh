@@ -467,10 +467,16 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
 //
 // ThreadSlots: per-thread staging; value v of the thread's own node at
 // s[v NT] (s already offset by threadIdx.x); the staging copy resolved sx.
+// fwd_bounce(i) / adj_bounce(i): whether the pull of direction i bounces back
+// and must be read from the node's own opposite population instead (forward:
+// x - e_i solid; adjoint: x + e_i solid).  The per-thread staging resolves
+// bounce-back while copying, so it never reports one.
 template <typename T, int NT> struct ThreadSlots {
     const T* s;
     __device__ __forceinline__ T pop(int j, int) const { return s[j * NT]; }
     __device__ __forceinline__ T val(int v) const { return s[v * NT]; }
+    static constexpr bool fwd_bounce(int) { return false; }
+    static constexpr bool adj_bounce(int) { return false; }
 };
 // RowWindow: per-block staging of a row segment [x0, x0 + NT): plane j as a
 // window of the source row starting at x0 - H (H = 16 bytes of values),
@@ -482,6 +488,19 @@ template <typename T, int Q, int NT> struct RowWindow {
     const T* s;
     __device__ __forceinline__ T pop(int j, int sx) const { return s[j * W + H + sx]; }
     __device__ __forceinline__ T val(int v) const { return s[2 * Q * W + (v - 2 * Q) * NT]; }
+    static constexpr bool fwd_bounce(int) { return false; }
+    static constexpr bool adj_bounce(int) { return false; }
+};
+// RowWindowSolid: a RowWindow on a grid with solid nodes, with the node's
+// bounce-back flags (bit i-1: x - e_i is solid), staged as one byte per node.
+// A window entry whose source is solid holds no population the node may use;
+// the node reads its own opposite population from global memory instead.
+template <typename T, int Q, int NT> struct RowWindowSolid : RowWindow<T, Q, NT> {
+    unsigned bits;
+    __device__ __forceinline__ bool fwd_bounce(int i) const { return i != 0 && ((bits >> (i - 1)) & 1u); }
+    __device__ __forceinline__ bool adj_bounce(int i) const {
+        return i != 0 && ((bits >> (Lat<Q>::opp(i) - 1)) & 1u);
+    }
 };
 
 // Row windows pay when each block of the persistent grid walks several row
@@ -635,22 +654,34 @@ template <int NT> struct ChunkIter {
             ++y;
         }
     }
-    __device__ __forceinline__ NodeIdx node(const CxConst& C) const {
+    // control-vector index of node (x, y), or -1
+    __device__ __forceinline__ int ctrl_index(const CxConst& C, int x, int k) const {
+        if (C.ctrl_full) return k;
+        const int cx = x - C.cx0, cy = y - C.cy0;
+        return (cx >= 0 && cy >= 0 && cx < C.cnx && cy < C.cny) ? cy * C.cnx + cx : -1;
+    }
+    // the global bytes the node description needs: bit 0 solid, bit 1 control mask set
+    __device__ __forceinline__ unsigned flags(const CxConst& C) const {
+        const int x = seg * NT + (int)threadIdx.x;
+        if (x >= C.nx) return 0u;
+        const int k = y * C.nx + x;
+        unsigned f = (C.has_solid && C.solid[k]) ? 1u : 0u;
+        const int c = ctrl_index(C, x, k);
+        if (C.cmask && c >= 0 && C.cmask[c]) f |= 2u;
+        return f;
+    }
+    // the node description from its flags (no memory access)
+    __device__ __forceinline__ NodeIdx node_from(const CxConst& C, unsigned f) const {
         NodeIdx r;
         r.x = seg * NT + (int)threadIdx.x;
         r.y = y;
         r.k = r.y * C.nx + r.x;
-        r.fluid = r.x < C.nx && !(C.has_solid && C.solid[r.k]);
-        if (C.ctrl_full) {
-            r.c = r.k;
-        } else {
-            const int cx = r.x - C.cx0, cy = r.y - C.cy0;
-            r.c = (r.x < C.nx && cx >= 0 && cy >= 0 && cx < C.cnx && cy < C.cny) ? cy * C.cnx + cx : -1;
-        }
-        r.ctrl = r.fluid && r.c >= 0 && (!C.cmask || C.cmask[r.c]);
-        if (r.x >= C.nx) r.c = -1;
+        r.fluid = r.x < C.nx && !(f & 1u);
+        r.c = r.x < C.nx ? ctrl_index(C, r.x, r.k) : -1;
+        r.ctrl = r.fluid && r.c >= 0 && (!C.cmask || (f & 2u));
         return r;
     }
+    __device__ __forceinline__ NodeIdx node(const CxConst& C) const { return node_from(C, flags(C)); }
 };
 __device__ __forceinline__ NodeIdx no_node() {
     NodeIdx r;

@@ -36,6 +36,7 @@
 #include <algorithm>
 
 #include "cx_fwd_body.cuh"
+#include "cx_rows.cuh"
 
 namespace cx {
 
@@ -104,7 +105,8 @@ static cudaError_t launch_q(const CxConst& C, const KConst<T>& K, const FwdArgs<
 
 // Bulk copies of one row segment's stage (issued by one thread): the 2Q
 // population windows, the angle (rotated tensors), g and E (whole-grid
-// control) and Phi^{n-1}.
+// control), Phi^{n-1} and, on grids with solid nodes, the bounce-back flags
+// (one byte per node).
 template <typename T, int Q, int NT>
 __device__ __forceinline__ void fwd_issue_rows(const CxConst& C, const FwdArgs<T>& A, int y, int x0, T* st,
                                                uint64_t* bar) {
@@ -114,7 +116,8 @@ __device__ __forceinline__ void fwd_issue_rows(const CxConst& C, const FwdArgs<T
     const int rm = y == 0 ? C.ny - 1 : y - 1, rp = y == C.ny - 1 ? 0 : y + 1;
     const bool rot = C.aniso == CX_ANISO_ROTATED, gb = A.g && C.ctrl_full, eb = A.E && C.ctrl_full;
     const uint32_t nb = (uint32_t)nv * sizeof(T);
-    mbar_expect_tx(bar, (uint32_t)(2 * Q * (nv + 2 * RW::H)) * sizeof(T) + nb * (1u + rot + gb + eb) + A.tx_pad);
+    mbar_expect_tx(bar, (uint32_t)(2 * Q * (nv + 2 * RW::H)) * sizeof(T) + nb * (1u + rot + gb + eb) +
+                            (C.has_solid ? (uint32_t)nv : 0u) + A.tx_pad);
 #pragma unroll
     for (int j = 0; j < 2 * Q; ++j) {
         const int i = j < Q ? j : j - Q;
@@ -127,6 +130,7 @@ __device__ __forceinline__ void fwd_issue_rows(const CxConst& C, const FwdArgs<T
     if (gb) bulk_g2s(loc + NT, A.g + k0, nb, bar);
     if (eb) bulk_g2s(loc + 2 * NT, A.E + k0, nb, bar);
     bulk_g2s(loc + 3 * NT, A.phi + k0, nb, bar);
+    if (C.has_solid) bulk_g2s(loc + 4 * NT, C.bounce + k0, (uint32_t)nv, bar);
 }
 
 // g and E of a controlled node when the control window is not the whole grid:
@@ -141,75 +145,52 @@ __device__ __forceinline__ void fwd_stage_ctrl(const CxConst& C, const FwdArgs<T
 }
 
 template <typename T, int Q, int NT> constexpr int fwd_rows_stage_values() {
-    return 2 * Q * RowWindow<T, Q, NT>::W + 4 * NT;
+    return 2 * Q * RowWindow<T, Q, NT>::W + 4 * NT + NT / (int)sizeof(T); // + one flag byte per node
 }
 template <typename T, int Q, int NT> constexpr size_t fwd_rows_smem() {
-    return (size_t)2 * fwd_rows_stage_values<T, Q, NT>() * sizeof(T) + 2 * sizeof(uint64_t);
+    return rows_pipe_smem<T>(fwd_rows_stage_values<T, Q, NT>());
 }
 
-template <typename T, int Q, int NT>
-__global__ void __launch_bounds__(NT) k_forward_rows(const CxConst C, const KConst<T> KC, const FwdArgs<T> A) {
+// SB: the grid has solid nodes (bounce-back flags staged with each segment).
+// Block: NT compute threads and one producer warp (see cx_rows.cuh).
+template <typename T, int Q, int NT, bool SB>
+__global__ void __launch_bounds__(NT + 32, sizeof(T) == 4 ? (NT == 256 ? 3 : 5) : 1)
+    k_forward_rows(const CxConst C, const KConst<T> KC, const FwdArgs<T> A) {
     using RW = RowWindow<T, Q, NT>;
-    constexpr int SV = fwd_rows_stage_values<T, Q, NT>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* const st0 = reinterpret_cast<T*>(smem_raw);
-    T* const st1 = st0 + SV;
-    uint64_t* const bar = reinterpret_cast<uint64_t*>(st1 + SV);
-    if (threadIdx.x == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        mbar_init_fence();
-    }
-    typename SqAccT<T>::type acc;
-    ChunkIter<NT> it(C);
-    NodeIdx cur = it.valid() ? it.node(C) : no_node();
+    RowsPipe<T, NT> pipe(smem_raw, fwd_rows_stage_values<T, Q, NT>());
+    pipe.init();
     allow_next_grid();
     wait_prior_grid(); // the previous step's populations and node state are complete
     if (block_sees_timeout(A.status)) return;
-    if (it.valid()) {
-        if (threadIdx.x == 0) fwd_issue_rows<T, Q, NT>(C, A, it.y, it.seg * NT, st0, &bar[0]);
-        fwd_stage_ctrl<T, Q, NT>(C, A, cur, st0);
+    if (threadIdx.x >= NT) {
+        pipe.produce(C, A.status,
+                     [&](int y, int x0, T* st, uint64_t* bar) { fwd_issue_rows<T, Q, NT>(C, A, y, x0, st, bar); });
+        return;
     }
-    cp_async_commit();
-    unsigned phase = 0; // bit b: parity of stage b's next completion
-    int b = 0;          // stage of the current segment
-    bool ok = true;
-    while (it.valid()) {
-        it.next();
-        const NodeIdx nxt = it.valid() ? it.node(C) : no_node();
-        T* const sn = b ? st0 : st1;
-        if (it.valid()) { // stage b^1 is free: every thread passed the barrier that ended its last use
-            if (threadIdx.x == 0) fwd_issue_rows<T, Q, NT>(C, A, it.y, it.seg * NT, sn, &bar[b ^ 1]);
-            fwd_stage_ctrl<T, Q, NT>(C, A, nxt, sn);
-        }
-        cp_async_commit();
-        cp_async_wait<1>();
-        ok = mbar_wait(&bar[b], (phase >> b) & 1u);
-        phase ^= 1u << b;
-        if (ok) fwd_compute<T, Q, NT, FwdArgs<T>>(C, KC, A, cur, RW{(b ? st1 : st0) + threadIdx.x}, acc);
-        if (__syncthreads_or(!ok)) { // all threads leave together when a stage never completed
-            ok = false;
-            break;
-        }
-        cur = nxt;
-        b ^= 1;
-    }
-    if (!ok) {
-        // bounded waits for the copies still in flight, then report
-        if (it.valid()) mbar_wait(&bar[b ^ 1], (phase >> (b ^ 1)) & 1u);
-        mbar_wait(&bar[b], ((phase >> b) & 1u) ^ 1u);
-        if (threadIdx.x == 0 && A.status) atomicOr(A.status, ST_TIMEOUT);
-    }
-    cp_async_wait<0>();
+    typename SqAccT<T>::type acc;
+    pipe.consume(
+        C, A.status, [&](const NodeIdx& nd, T* st) { fwd_stage_ctrl<T, Q, NT>(C, A, nd, st); },
+        [&](const NodeIdx& nd, T* st) {
+            if constexpr (SB) {
+                const unsigned bits = reinterpret_cast<const uint8_t*>(st + 2 * Q * RW::W + 4 * NT)[threadIdx.x];
+                fwd_compute<T, Q, NT, FwdArgs<T>>(C, KC, A, nd, RowWindowSolid<T, Q, NT>{{st + threadIdx.x}, bits},
+                                                  acc);
+            } else {
+                fwd_compute<T, Q, NT, FwdArgs<T>>(C, KC, A, nd, RW{st + threadIdx.x}, acc);
+            }
+        });
     if (A.gsq_part) acc.flush(A.gsq_part + blockIdx.x * (NT >> 5) + (threadIdx.x >> 5), nullptr);
 }
 
-// a step the row-window kernel can take: pulled populations (n >= 1), no
-// solid nodes, rows a whole number of 16-byte units, 16-byte aligned planes
+// a step the row-window kernel can take: pulled populations (n >= 1), rows a
+// whole number of 16-byte units (of flag bytes too when there are solid
+// nodes), 16-byte aligned planes
 template <typename T> static bool rows_eligible(const CxConst& C, const FwdArgs<T>& A, const Launch& L) {
     constexpr int H = 16 / (int)sizeof(T);
     auto al = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; };
-    if (!L.row_windows || A.n == 0 || C.has_solid || C.nx % H != 0 || !al(A.phi)) return false;
+    if (!L.row_windows || A.n == 0 || C.nx % H != 0 || !al(A.phi)) return false;
+    if (C.has_solid && (!C.bounce || C.nx % 16 != 0 || !al(C.bounce))) return false;
     if (!rows_pipelined(C, L, L.rows_grid ? std::min(L.rows_grid, L.grid.x) : L.grid.x)) return false;
     if (L.block.x != 128 && L.block.x != 256) return false;
     for (int j = 0; j < 2 * C.Q; ++j)
@@ -219,20 +200,20 @@ template <typename T> static bool rows_eligible(const CxConst& C, const FwdArgs<
     return true;
 }
 
-template <typename T, int Q, int NT>
+template <typename T, int Q, int NT, bool SB>
 static cudaError_t launch_rows_qn(const CxConst& C, const KConst<T>& K, const FwdArgs<T>& A, const Launch& L,
                                   cudaStream_t s) {
     constexpr size_t smem = fwd_rows_smem<T, Q, NT>();
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e =
-            cudaFuncSetAttribute(k_forward_rows<T, Q, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(k_forward_rows<T, Q, NT, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(L.rows_grid ? std::min(L.rows_grid, L.grid.x) : L.grid.x);
-    cfg.blockDim = L.block;
+    cfg.blockDim = dim3(L.block.x + 32); // compute threads + the producer warp
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -242,13 +223,17 @@ static cudaError_t launch_rows_qn(const CxConst& C, const KConst<T>& K, const Fw
     cfg.numAttrs = 1;
     FwdArgs<T> A2 = A;
     A2.tx_pad = L.row_windows == 2 ? 16u : 0u; // test mode: no stage ever completes
-    return cudaLaunchKernelEx(&cfg, k_forward_rows<T, Q, NT>, C, K, A2);
+    return cudaLaunchKernelEx(&cfg, k_forward_rows<T, Q, NT, SB>, C, K, A2);
 }
 
 template <typename T, int Q>
 static cudaError_t launch_rows_q(const CxConst& C, const KConst<T>& K, const FwdArgs<T>& A, const Launch& L,
                                  cudaStream_t s) {
-    return L.block.x == 128 ? launch_rows_qn<T, Q, 128>(C, K, A, L, s) : launch_rows_qn<T, Q, 256>(C, K, A, L, s);
+    if (C.has_solid)
+        return L.block.x == 128 ? launch_rows_qn<T, Q, 128, true>(C, K, A, L, s)
+                                : launch_rows_qn<T, Q, 256, true>(C, K, A, L, s);
+    return L.block.x == 128 ? launch_rows_qn<T, Q, 128, false>(C, K, A, L, s)
+                            : launch_rows_qn<T, Q, 256, false>(C, K, A, L, s);
 }
 
 template <typename T>
@@ -283,12 +268,18 @@ template int forward_occupancy<float>(int, int);
 template int forward_occupancy<double>(int, int);
 
 
-template <typename T, int Q, int NT> static int rows_occ_qn() {
+template <typename T, int Q, int NT, bool SB> static int rows_occ_qnb() {
     constexpr size_t smem = fwd_rows_smem<T, Q, NT>();
-    cudaFuncSetAttribute(k_forward_rows<T, Q, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_forward_rows<T, Q, NT, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_forward_rows<T, Q, NT>, NT, smem) != cudaSuccess) return 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_forward_rows<T, Q, NT, SB>, NT + 32, smem) !=
+        cudaSuccess)
+        return 1;
     return nb > 0 ? nb : 1;
+}
+// the smaller residency of the two forms (the persistent grid serves both)
+template <typename T, int Q, int NT> static int rows_occ_qn() {
+    return std::min(rows_occ_qnb<T, Q, NT, false>(), rows_occ_qnb<T, Q, NT, true>());
 }
 template <typename T, int Q> static int rows_occ_q(int threads) {
     return threads == 128 ? rows_occ_qn<T, Q, 128>() : rows_occ_qn<T, Q, 256>();

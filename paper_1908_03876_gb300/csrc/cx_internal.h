@@ -26,6 +26,8 @@ struct CxConst {
     const void* Kfield;               // T [6][plane]        (FIELD)
     const void* a;                    // T [ny][2] or [2][plane]
     const uint8_t* solid;             // [plane] or null
+    const uint8_t* bounce;            // [plane] with solid nodes: at a fluid node bit i-1 is set when x - e_i is
+                                      // solid (the pull of direction i bounces back); 0 at solid nodes; or null
     const uint8_t* cmask;             // [cny*cnx] window & mask & fluid, or null
 };
 
@@ -158,6 +160,6 @@ template <typename T>
 cudaError_t launch_convert(const double* in, T* out, size_t n, cudaStream_t s);
 template <typename T>
 cudaError_t launch_setup_fields(const CxConst& C, const cx_problem_desc& d, T* theta, T* Kfield, T* a, T* u_tgt,
-                                uint8_t* solid, uint8_t* cmask, cudaStream_t s);
+                                uint8_t* solid, uint8_t* cmask, uint8_t* bounce, cudaStream_t s);
 
 } // namespace cx

@@ -235,7 +235,7 @@ template <typename T> cudaError_t launch_convert(const double* in, T* out, size_
 template <typename T>
 __global__ void k_setup(const CxConst C, const double* theta_in, const double* Du_in, const double* Dv_in,
                         const double* a_in, const double* ut_in, const uint8_t* solid_in, const uint8_t* cmask_in,
-                        T* theta, T* Kfield, T* a, T* u_tgt, uint8_t* solid, uint8_t* cmask) {
+                        T* theta, T* Kfield, T* a, T* u_tgt, uint8_t* solid, uint8_t* cmask, uint8_t* bounce) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= C.nx || y >= C.ny) return;
@@ -264,6 +264,19 @@ __global__ void k_setup(const CxConst C, const double* theta_in, const double* D
     }
     u_tgt[k] = T(ut_in[k]);
     if (solid) solid[k] = solid_in[k] ? 1 : 0;
+    if (bounce) { // which pulls of this fluid node bounce back (halfway bounce-back, periodic neighbours)
+        unsigned bits = 0;
+        if (!solid_in[k]) {
+            const int xm = x == 0 ? C.nx - 1 : x - 1, xp = x == C.nx - 1 ? 0 : x + 1;
+            const int ym = y == 0 ? C.ny - 1 : y - 1, yp = y == C.ny - 1 ? 0 : y + 1;
+            for (int i = 1; i < C.Q; ++i) {
+                const int ex = Lat<9>::ex(i), ey = Lat<9>::ey(i); // D2Q5 uses the first five D2Q9 velocities
+                const int xs = ex > 0 ? xm : (ex < 0 ? xp : x), ys = ey > 0 ? ym : (ey < 0 ? yp : y);
+                if (solid_in[ys * C.nx + xs]) bits |= 1u << (i - 1);
+            }
+        }
+        bounce[k] = (uint8_t)bits;
+    }
     if (cmask) {
         const int cx = x - C.cx0, cy = y - C.cy0;
         if (cx >= 0 && cy >= 0 && cx < C.cnx && cy < C.cny) {
@@ -278,10 +291,10 @@ __global__ void k_setup(const CxConst C, const double* theta_in, const double* D
 
 template <typename T>
 cudaError_t launch_setup_fields(const CxConst& C, const cx_problem_desc& d, T* theta, T* Kfield, T* a, T* u_tgt,
-                                uint8_t* solid, uint8_t* cmask, cudaStream_t s) {
+                                uint8_t* solid, uint8_t* cmask, uint8_t* bounce, cudaStream_t s) {
     dim3 block(32, 8), grid((C.nx + 31) / 32, (C.ny + 7) / 8);
     k_setup<T><<<grid, block, 0, s>>>(C, d.theta, d.D_u_field, d.D_v_field, d.a, d.u_target, d.solid, d.ctrl_mask,
-                                      theta, Kfield, a, u_tgt, solid, cmask);
+                                      theta, Kfield, a, u_tgt, solid, cmask, bounce);
     return cudaGetLastError();
 }
 
@@ -342,7 +355,7 @@ template <typename T> KConst<T> make_kconst(const CxConst& C, int Q) {
                                         cudaStream_t);                                                               \
     template cudaError_t launch_convert<T>(const double*, T*, size_t, cudaStream_t);                                 \
     template cudaError_t launch_setup_fields<T>(const CxConst&, const cx_problem_desc&, T*, T*, T*, T*, uint8_t*,    \
-                                                uint8_t*, cudaStream_t);
+                                                uint8_t*, uint8_t*, cudaStream_t);
 CX_INST(float)
 CX_INST(double)
 

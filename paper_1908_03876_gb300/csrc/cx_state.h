@@ -21,8 +21,8 @@ struct Layout {
     int Q, N, k, S, nparts;
     int nwin, win_len;   // control windows W and steps per window N / W
     size_t off_popA, off_popB, off_adjA, off_adjB, off_ckpt, off_ckpt_phi, off_phi, off_sigma, off_tape;
-    size_t off_uN, off_vN, off_wu, off_theta, off_K, off_a, off_ut, off_solid, off_cmask, off_part, off_scal,
-        off_status, off_tlm, total; // off_tlm: 4 planes for the tangent-linear pass (zero, du, dv, scratch)
+    size_t off_uN, off_vN, off_wu, off_theta, off_K, off_a, off_ut, off_solid, off_bounce, off_cmask, off_part,
+        off_scal, off_status, off_tlm, total; // off_tlm: 4 planes for the tangent-linear pass (zero, du, dv, scratch)
 };
 
 struct TimedRange {

@@ -30,7 +30,7 @@ struct StaticLayout {
     size_t plane, nctrl, esz, total;
     int nparts;
     size_t off_P0, off_PA, off_PB, off_phi, off_uN, off_vN, off_wu, off_theta, off_K, off_a, off_ut, off_solid,
-        off_cmask, off_part, off_scal, off_status;
+        off_bounce, off_cmask, off_part, off_scal, off_status;
 };
 
 StaticLayout static_layout(const cx_problem_desc* d) {
@@ -60,6 +60,7 @@ StaticLayout static_layout(const cx_problem_desc* d) {
     L.off_a = take(d->adv == CX_ADV_FIELD ? 2 * fld : (d->adv == CX_ADV_ROW ? 2 * (size_t)d->ny * L.esz : 0));
     L.off_ut = take(fld);
     L.off_solid = take(d->solid ? L.plane : 0);
+    L.off_bounce = take(d->solid ? L.plane : 0);
     L.off_cmask = take((d->solid || d->ctrl_mask) ? L.nctrl : 0);
     L.off_part = take(sizeof(double) * 2 * (size_t)L.nparts);
     L.off_scal = take(sizeof(double) * 16);
@@ -125,7 +126,7 @@ cx_status run_static(const cx_problem_desc* d, const CxConst& C, const StaticLay
     if (cudaMemsetAsync(gsq, 0, sizeof(double) * fw, s) != cudaSuccess) return CX_ERR_CUDA;
     if (cudaMemsetAsync(status, 0, sizeof(int) * 4, s) != cudaSuccess) return CX_ERR_CUDA;
     if (launch_setup_fields<T>(C, *d, (T*)C.theta, (T*)C.Kfield, (T*)C.a, reinterpret_cast<T*>(ws + Ly.off_ut),
-                               (uint8_t*)C.solid, (uint8_t*)C.cmask, s) != cudaSuccess)
+                               (uint8_t*)C.solid, (uint8_t*)C.cmask, (uint8_t*)C.bounce, s) != cudaSuccess)
         return CX_ERR_CUDA;
     if (launch_init<T>(C, nullptr, nullptr, u0, v0, P0, L2, s) != cudaSuccess) return CX_ERR_CUDA;
     const T* in = P0;
@@ -231,6 +232,7 @@ extern "C" cx_status cx_forward_static(const cx_problem_desc* desc, const void* 
     C.Kfield = desc->aniso == CX_ANISO_FIELD ? ws + Ly.off_K : nullptr;
     C.a = desc->adv != CX_ADV_NONE ? ws + Ly.off_a : nullptr;
     C.solid = desc->solid ? reinterpret_cast<uint8_t*>(ws + Ly.off_solid) : nullptr;
+    C.bounce = desc->solid ? reinterpret_cast<uint8_t*>(ws + Ly.off_bounce) : nullptr;
     C.cmask = (desc->solid || desc->ctrl_mask) ? reinterpret_cast<uint8_t*>(ws + Ly.off_cmask) : nullptr;
     if (desc->precision == 64)
         return run_static<double>(desc, C, Ly, ws, (const double*)u0, (const double*)v0, (const double*)g, J_dev,

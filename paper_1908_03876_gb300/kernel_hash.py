@@ -9,8 +9,8 @@ CSRC = os.path.join(os.path.dirname(os.path.abspath(__file__)), "csrc")
 KERNEL_SOURCES = {
     "k_forward": ("cx_device.cuh", "cx_fwd_body.cuh", "cx_internal.h", "cx_forward.cu"),
     "k_adjoint": ("cx_device.cuh", "cx_adj_body.cuh", "cx_internal.h", "cx_adjoint.cu"),
-    "k_forward_rows": ("cx_device.cuh", "cx_fwd_body.cuh", "cx_internal.h", "cx_forward.cu"),
-    "k_adjoint_rows": ("cx_device.cuh", "cx_adj_body.cuh", "cx_internal.h", "cx_adjoint.cu"),
+    "k_forward_rows": ("cx_device.cuh", "cx_fwd_body.cuh", "cx_internal.h", "cx_rows.cuh", "cx_forward.cu"),
+    "k_adjoint_rows": ("cx_device.cuh", "cx_adj_body.cuh", "cx_internal.h", "cx_rows.cuh", "cx_adjoint.cu"),
     "k_batch": ("cx_device.cuh", "cx_fwd_body.cuh", "cx_adj_body.cuh", "cx_internal.h", "cx_state.h",
                 "cx_batch.cu"),
     "k_batch_rows": ("cx_device.cuh", "cx_fwd_body.cuh", "cx_adj_body.cuh", "cx_internal.h", "cx_state.h",
