@@ -95,6 +95,10 @@ typedef struct {
     int ctrl_windows;         /* W: g piecewise constant in time over W equal windows
                                  (g^n = G_{n/(N/W)}, W divides N); 0: one value per
                                  step (W = N).  Controls and gradients are [W][ctrl]. */
+    int halo;                 /* 1: this grid is one sub-domain of a larger problem and
+                                 its outer one-node frame is a halo (see cx_set_halo_exchange):
+                                 frame nodes are pulled from but never updated, costed or
+                                 controlled.  0: the grid is the whole (periodic) problem. */
 } cx_problem_desc;
 
 typedef struct cx_problem cx_problem; /* opaque, library-owned host object */
@@ -512,6 +516,62 @@ cx_status cx_nn_cast_bf16(const float* in, uint16_t* out, size_t n, cudaStream_t
 #define CX_STATIC_SCRATCH_BYTES (64u << 20)
 cx_status cx_forward_static(const cx_problem_desc* desc, const void* u0, const void* v0, const void* g,
                             double* J_dev, void* uN, void* vN, int* status_dev, cudaStream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Domain decomposition of one problem (2-D blocks over several devices or
+ * processes).  Collision is local and streaming reaches only the nearest
+ * neighbours (Sec. 3.1; the adjoint of Sec. 3.2.1 streams along -e_i), so a
+ * block needs, before each step, the populations that cross its faces and
+ * corners.  A block of lx x ly nodes is created as an (lx + 2) x (ly + 2)
+ * problem with halo = 1 whose descriptor fields are the global fields over
+ * the block and its one-node frame (periodic images at the edges of the
+ * global grid); its frame nodes are ghosts, filled from the neighbouring
+ * blocks.  The cost, gradient norms and control penalty of a block cover its
+ * interior only; the sum over blocks is the problem's.
+ *
+ * Kinds of exchanged data: */
+enum { CX_HALO_FWD = 0,  /* forward (and recompute) populations, [2][Q][plane] */
+       CX_HALO_ADJ = 1,  /* adjoint populations, [2][Q][plane]                 */
+       CX_HALO_SEED = 2  /* a node field [plane]: the terminal adjoint seed     */ };
+/* Exchange callback: called on the calling host thread after every lattice
+ * step of cx_forward / cx_forward_trial / cx_adjoint / cx_adjoint_vjp (kind
+ * FWD or ADJ, `field` = the populations the step wrote) and after the
+ * forward's terminal moments (kind SEED, `field` = the terminal seed
+ * u^N - u_target).  Before returning it must queue on `stream` the work that
+ * fills the ghost frame of `field` from the neighbouring blocks, usually
+ * cx_halo_pack, a transfer of the slots, and cx_halo_unpack.  A non-zero
+ * return ends the call with that status. */
+typedef cx_status (*cx_halo_fn)(void* user, int kind, void* field, cudaStream_t stream);
+/* Install (fn != NULL) or remove the callback of a problem created with
+ * halo = 1.  On such a problem cx_step, cx_cg_step, cx_lma_step, cx_tlm and
+ * cx_cadjoint return CX_ERR_INVALID_ARG: their line searches and dot
+ * products need sums over all blocks (the caller's). */
+cx_status cx_set_halo_exchange(cx_problem* p, cx_halo_fn fn, void* user);
+/* Slots: direction d = 1..8 is the neighbour at offset e_d (E, N, W, S, NE,
+ * NW, SW, SE).  Send slot d holds the interior cells along side d (a column
+ * of ly, a row of lx, or one corner cell) for the planes the neighbour pulls
+ * across that side: forward populations moving toward d (3 + 3 per face and
+ * 1 + 1 per corner on D2Q9, 1 + 1 per face on D2Q5), adjoint populations
+ * moving away from d, or the node field itself (SEED); each slot is
+ * [planes][cells] of T.  The neighbour at e_d receives it as its receive slot
+ * opp(d).  Byte offsets of the send slots (send_off[0..7], d = 1..8), of the
+ * receive slots (recv_off[0..7]) and the bytes of either buffer (*bytes);
+ * any pointer may be NULL.  Host call.  Errors: CX_ERR_INVALID_ARG (halo = 0
+ * or an unknown kind). */
+cx_status cx_halo_layout(const cx_problem* p, int kind, size_t* send_off, size_t* recv_off, size_t* bytes);
+/* Gather the send slots of `field` (device, the kind's layout) into `send`
+ * (device, cx_halo_layout bytes); scatter the receive slots of `recv` into
+ * the ghost frame of `field`.  Asynchronous on the problem's stream. */
+cx_status cx_halo_pack(cx_problem* p, int kind, const void* field, void* send);
+cx_status cx_halo_unpack(cx_problem* p, int kind, const void* recv, void* field);
+/* Forward solve at the trial control g - lam E (E device T [W][ctrl], each
+ * value rounded as cx_control_axpy rounds it), as a line-search trial of
+ * cx_step computes it; J_dev as for cx_forward.  The state is then that of
+ * the trial control. */
+cx_status cx_forward_trial(cx_problem* p, const void* g, const void* E, double lam, double* J_dev);
+/* g <- g - lam E on the device (T [W][ctrl]), the accepted update of a line
+ * search.  Asynchronous. */
+cx_status cx_control_axpy(cx_problem* p, void* g, const void* E, double lam);
 
 /* Release the host object (the workspace stays the caller's). */
 cx_status cx_destroy(cx_problem* p);

@@ -11,6 +11,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libcxlbm.so")
 
 CX_ANISO_CONST, CX_ANISO_ROTATED, CX_ANISO_FIELD = 0, 1, 2
+CX_HALO_FWD, CX_HALO_ADJ, CX_HALO_SEED = 0, 1, 2
+# the exchange callback type of cx_set_halo_exchange
+HALO_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p)
 CX_ADV_NONE, CX_ADV_ROW, CX_ADV_FIELD = 0, 1, 2
 
 STATUS = {
@@ -29,6 +32,8 @@ EXPORTS = [
     "cx_batch_forward", "cx_batch_gradient", "cx_batch_get_fields", "cx_batch_get_status", "cx_batch_destroy",
     "cx_batch_set_enabled", "cx_batch_step", "cx_batch_adjoint", "cx_batch_axpy", "cx_batch_prepare",
     "cx_batch_autotune", "cx_batch_set_staging",
+    "cx_set_halo_exchange", "cx_halo_layout", "cx_halo_pack", "cx_halo_unpack", "cx_forward_trial",
+    "cx_control_axpy",
     "cx_nn_conv_forward", "cx_nn_conv_backward_data", "cx_nn_conv_backward_weight_scratch",
     "cx_nn_conv_backward_weight", "cx_nn_relu_backward", "cx_nn_add", "cx_nn_pool2", "cx_nn_up2", "cx_nn_mse",
     "cx_nn_adam", "cx_nn_cast_bf16", "cx_nn_conv_forward_f32", "cx_nn_smooth", "cx_nn_packed_weights",
@@ -61,6 +66,7 @@ class Desc(ctypes.Structure):
         ("s", ctypes.c_double * 7),
         ("source_order", ctypes.c_int),
         ("ctrl_windows", ctypes.c_int),
+        ("halo", ctypes.c_int),
     ]
 
 
@@ -116,6 +122,12 @@ def load():
         "cx_lma_step": [vp, vp, vp, ctypes.POINTER(StepInfo)],
         "cx_cadjoint": [vp, vp, vp],
         "cx_set_staging": [vp, cint],
+        "cx_set_halo_exchange": [vp, vp, vp],
+        "cx_halo_layout": [vp, cint, vp, vp, ctypes.POINTER(ctypes.c_size_t)],
+        "cx_halo_pack": [vp, cint, vp, vp],
+        "cx_halo_unpack": [vp, cint, vp, vp],
+        "cx_forward_trial": [vp, vp, vp, ctypes.c_double, vp],
+        "cx_control_axpy": [vp, vp, vp, ctypes.c_double],
         "cx_batch_workspace_size": [D, cint, ctypes.POINTER(ctypes.c_size_t)],
         "cx_batch_create": [D, cint, vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)],
         "cx_batch_set_initial": [vp, vp, vp],

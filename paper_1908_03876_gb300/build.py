@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcxlbm.so")
-SOURCES = ["cx_forward.cu", "cx_adjoint.cu", "cx_tlm.cu", "cx_cadj.cu", "cx_misc.cu", "cx_api.cu", "cx_static.cu", "cx_batch.cu",
+SOURCES = ["cx_forward.cu", "cx_adjoint.cu", "cx_tlm.cu", "cx_cadj.cu", "cx_misc.cu", "cx_api.cu", "cx_static.cu", "cx_halo.cu", "cx_batch.cu",
            "nn_kernels.cu", "nn_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # Per-source flags.  The continuous adjoint is compiled without multiply-add

@@ -15,6 +15,10 @@
 //               lambda_Phi^n = c_n sigma^n + c'_{n+1} sigma^{n+1} + (G path),
 //               sigma^n = sum_i rho_v,i w~_i.
 // The tape (u^n, G^n) comes from the forward recompute of the segment.
+// In FP32, sums sum_i c_i rho_i with c_i = w_i (a + b.e_i) (sigma, and the
+// weights of the chemotactic coupling) are taken from the moments m = M0 rho
+// the collision needs anyway: sum_i c_i rho_i = sum_k (M0 c)_k m_k / |row_k|^2;
+// FP64 (the parity mode) sums them per direction as written.
 //
 // Execution: the persistent, two-stage cp.async pipeline of the forward
 // kernel (see cx_forward.cu), staging the pulled adjoint populations, the tape,
@@ -95,6 +99,22 @@ __device__ __forceinline__ void adj_compute(const CxConst& C, const KConst<T>& K
     T psu[Q], psv[Q];
     meq_unit<T, Q>(nc.ax, nc.ay, KC.d_u, mh);
     Transform<T, Q>::moments(ru, mom);
+    // Y = sum_i 3 w_i e_i rho_u,i (the weights of tau S_u)
+    constexpr bool fold = sizeof(T) == 4; // from the moments (FP32)
+    T Yx = T(0), Yy = T(0);
+    if constexpr (fold) {
+#pragma unroll
+        for (int kk = 0; kk < Q; ++kk) {
+            if (L::src_Bx(kk) != 0.0) Yx += T(3.0 * L::inv_n(kk) * L::src_Bx(kk)) * mom[kk];
+            if (L::src_By(kk) != 0.0) Yy += T(3.0 * L::inv_n(kk) * L::src_By(kk)) * mom[kk];
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            Yx += T(3.0 * L::w(i) * L::ex(i)) * ru[i];
+            Yy += T(3.0 * L::w(i) * L::ey(i)) * ru[i];
+        }
+    }
     relax_n<T, Q>(KC, nc.Ku0, nc.Ku1, nc.Ku2, mom, z);
     T Tc = T(0);
 #pragma unroll
@@ -103,8 +123,26 @@ __device__ __forceinline__ void adj_compute(const CxConst& C, const KConst<T>& K
 #pragma unroll
     for (int i = 0; i < Q; ++i) psu[i] = ru[i] - mt[i] + Tc;
 
+    // sigma = sum_i w~_i rho_v,i with w~_i = w_i (1 + 3 V.e_i), V = (I - K_v/2) a
+    const T Kax = nc.Kv0 * nc.ax + nc.Kv1 * nc.ay, Kay = nc.Kv1 * nc.ax + nc.Kv2 * nc.ay;
+    const T Vx = nc.ax - T(0.5) * Kax, Vy = nc.ay - T(0.5) * Kay;
     meq_unit<T, Q>(nc.ax, nc.ay, KC.d_v, mh);
     Transform<T, Q>::moments(rv, mom);
+    T sigma = T(0);
+    if constexpr (fold) {
+        T sA = T(0), sBx = T(0), sBy = T(0);
+#pragma unroll
+        for (int kk = 0; kk < Q; ++kk) {
+            if (L::src_A(kk) != 0.0) sA += T(L::inv_n(kk) * L::src_A(kk)) * mom[kk];
+            if (L::src_Bx(kk) != 0.0) sBx += T(3.0 * L::inv_n(kk) * L::src_Bx(kk)) * mom[kk];
+            if (L::src_By(kk) != 0.0) sBy += T(3.0 * L::inv_n(kk) * L::src_By(kk)) * mom[kk];
+        }
+        sigma = sA + Vx * sBx + Vy * sBy;
+    } else {
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+            sigma += T(L::w(i)) * (T(1) + T(3) * (Vx * T(L::ex(i)) + Vy * T(L::ey(i)))) * rv[i];
+    }
     relax_n<T, Q>(KC, nc.Kv0, nc.Kv1, nc.Kv2, mom, z);
     Tc = T(0);
 #pragma unroll
@@ -114,12 +152,6 @@ __device__ __forceinline__ void adj_compute(const CxConst& C, const KConst<T>& K
     for (int i = 0; i < Q; ++i) psv[i] = rv[i] - mt[i] + Tc;
 
     // --- coupling through tau S_u,i = 3 w_i chi u e_i . (K_u G)
-    T Yx = T(0), Yy = T(0);
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        Yx += T(3.0 * L::w(i) * L::ex(i)) * ru[i];
-        Yy += T(3.0 * L::w(i) * L::ey(i)) * ru[i];
-    }
     const T chi = KC.chi;
     T adj_Tu = chi * (Yx * (nc.Ku0 * Gx + nc.Ku1 * Gy) + Yy * (nc.Ku1 * Gx + nc.Ku2 * Gy));
     const T aGx = chi * Tu * (nc.Ku0 * Yx + nc.Ku1 * Yy);
@@ -133,12 +165,6 @@ __device__ __forceinline__ void adj_compute(const CxConst& C, const KConst<T>& K
     T adj_Phi = T(-0.5) * aKG * sc;
 
     // --- reaction/control source: sigma^n and the use of Phi^n at step n+1
-    const T Kax = nc.Kv0 * nc.ax + nc.Kv1 * nc.ay, Kay = nc.Kv1 * nc.ax + nc.Kv2 * nc.ay;
-    const T Vx = nc.ax - T(0.5) * Kax, Vy = nc.ay - T(0.5) * Kay;
-    T sigma = T(0);
-#pragma unroll
-    for (int i = 0; i < Q; ++i)
-        sigma += T(L::w(i)) * (T(1) + T(3) * (Vx * T(L::ex(i)) + Vy * T(L::ey(i)))) * rv[i];
     adj_Phi += ((A.n == 0) ? KC.c_first : KC.c_now) * sigma;
     if (!A.terminal) adj_Phi += KC.c_prev * sig_next; // Phi^n feeds step n+1 with c'_{n+1}
     A.sigma[k] = sigma;

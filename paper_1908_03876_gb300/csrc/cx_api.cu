@@ -38,6 +38,7 @@ static cx_status validate(const cx_problem_desc* d) {
     for (int i = 0; i < 7; ++i)
         if (!(d->s[i] > 0.0 && d->s[i] < 2.0)) return CX_ERR_INVALID_ARG;
     if (d->source_order != 1 && d->source_order != 2) return CX_ERR_INVALID_ARG;
+    if (d->halo != 0 && d->halo != 1) return CX_ERR_INVALID_ARG;
     if (d->ctrl_windows < 0 || d->ctrl_windows > d->n_steps ||
         (d->ctrl_windows > 0 && d->n_steps % d->ctrl_windows != 0))
         return CX_ERR_INVALID_ARG;
@@ -193,6 +194,10 @@ template <typename T> static cx_status run_forward(cx_problem* p, const T* g, co
         A.gsq_part = gsq;
         A.n = n;
         CX_CUDA(launch_forward<T>(C, p->kc((T*)nullptr), A, p->Lf, p->stream));
+        if (p->halo_fn) {
+            const cx_status hs = p->halo_fn(p->halo_user, CX_HALO_FWD, out, p->stream);
+            if (hs) return hs;
+        }
         in = out;
     }
     range_end(p, r, Ly.N);
@@ -204,6 +209,10 @@ template <typename T> static cx_status run_forward(cx_problem* p, const T* g, co
     CX_CUDA(launch_finalize(cost, p->nblocks, gsq, fw, C.alpha, scal, p->at<int>(Ly.off_status),
                             flag_unstable ? ST_UNSTABLE : 0, 0, p->stream));
     range_end(p, r, 2);
+    if (p->halo_fn) { // the terminal adjoint step pulls the seed from the frame too
+        const cx_status hs = p->halo_fn(p->halo_user, CX_HALO_SEED, p->at<T>(Ly.off_wu), p->stream);
+        if (hs) return hs;
+    }
     if (J_dev) CX_CUDA(cudaMemcpyAsync(J_dev, scal, sizeof(double), cudaMemcpyDeviceToDevice, p->stream));
     p->fwd_valid = true;
     p->adj_valid = false;
@@ -251,6 +260,10 @@ static cx_status run_adjoint(cx_problem* p, const T* g, const T* seed_u, const T
                 A.gsq_part = nullptr;
                 A.n = n;
                 CX_CUDA(launch_forward<T>(C, p->kc((T*)nullptr), A, p->Lf, p->stream));
+                if (p->halo_fn) {
+                    const cx_status hs = p->halo_fn(p->halo_user, CX_HALO_FWD, out, p->stream);
+                    if (hs) return hs;
+                }
                 in = out;
             }
             range_end(p, r, n1 - n0);
@@ -276,6 +289,10 @@ static cx_status run_adjoint(cx_problem* p, const T* g, const T* seed_u, const T
             A.emax_part = emax;
             A.n = n;
             CX_CUDA(launch_adjoint<T>(C, KA, A, p->La, p->stream));
+            if (p->halo_fn && n > 0) {
+                const cx_status hs = p->halo_fn(p->halo_user, CX_HALO_ADJ, out, p->stream);
+                if (hs) return hs;
+            }
             psi_in = out;
         }
         range_end(p, r, n1 - n0);
@@ -777,6 +794,7 @@ cx_status cx_create(const cx_problem_desc* desc, void* workspace, size_t bytes, 
     C.aniso = desc->aniso;
     C.adv = desc->adv;
     C.has_solid = desc->solid ? 1 : 0;
+    C.halo = desc->halo;
     C.ctrl_full = (desc->ctrl_nx == 0 || (desc->ctrl_x0 == 0 && desc->ctrl_y0 == 0 && desc->ctrl_nx == desc->nx &&
                                           desc->ctrl_ny == desc->ny)) &&
                   !desc->ctrl_mask && !desc->solid;
@@ -909,6 +927,28 @@ cx_status cx_adjoint_vjp(cx_problem* p, const void* g, const void* seed_u, const
     return run_adjoint<float>(p, (const float*)g, (const float*)seed_u, (const float*)seed_v, (float*)vjp, false);
 }
 
+cx_status cx_set_halo_exchange(cx_problem* p, cx_halo_fn fn, void* user) {
+    if (!p || !p->d.halo) return CX_ERR_INVALID_ARG;
+    p->halo_fn = fn;
+    p->halo_user = fn ? user : nullptr;
+    return CX_OK;
+}
+
+cx_status cx_forward_trial(cx_problem* p, const void* g, const void* E, double lam, double* J_dev) {
+    if (!p || !E || !std::isfinite(lam)) return CX_ERR_INVALID_ARG;
+    if (!p->has_init) return CX_ERR_STATE;
+    if (p->lay.esz == 8) return run_forward<double>(p, (const double*)g, (const double*)E, lam, J_dev, true);
+    return run_forward<float>(p, (const float*)g, (const float*)E, lam, J_dev, true);
+}
+
+cx_status cx_control_axpy(cx_problem* p, void* g, const void* E, double lam) {
+    if (!p || !g || !E || !std::isfinite(lam)) return CX_ERR_INVALID_ARG;
+    const size_t n = (size_t)p->lay.nwin * p->lay.nctrl;
+    if (p->lay.esz == 8) CX_CUDA(launch_axpy<double>((double*)g, (const double*)E, lam, n, p->stream));
+    else CX_CUDA(launch_axpy<float>((float*)g, (const float*)E, (float)lam, n, p->stream));
+    return CX_OK;
+}
+
 cx_status cx_gradient(cx_problem* p, const void* g, void* dJdg, double* J_dev) {
     cx_status rc = cx_forward(p, g, J_dev);
     if (rc) return rc;
@@ -916,14 +956,14 @@ cx_status cx_gradient(cx_problem* p, const void* g, void* dJdg, double* J_dev) {
 }
 
 cx_status cx_cg_step(cx_problem* p, void* g_inout, void* work, int variant, cx_cg_info* info) {
-    if (!p || !g_inout || !work || variant < CX_CG_FR || variant > CX_CG_DY) return CX_ERR_INVALID_ARG;
+    if (!p || !g_inout || !work || variant < CX_CG_FR || variant > CX_CG_DY || p->d.halo) return CX_ERR_INVALID_ARG;
     if (!p->has_init) return CX_ERR_STATE;
     if (p->lay.esz == 8) return run_cg_step<double>(p, (double*)g_inout, (double*)work, variant, info);
     return run_cg_step<float>(p, (float*)g_inout, (float*)work, variant, info);
 }
 
 cx_status cx_tlm(cx_problem* p, const void* g, const void* dg, void* du_out, void* dv_out, double* du_sq) {
-    if (!p || !dg) return CX_ERR_INVALID_ARG;
+    if (!p || !dg || p->d.halo) return CX_ERR_INVALID_ARG;
     if (!p->fwd_valid) return CX_ERR_STATE;
     if (p->lay.esz == 8)
         return run_tlm<double>(p, (const double*)g, (const double*)dg, (double*)du_out, (double*)dv_out, du_sq);
@@ -931,14 +971,14 @@ cx_status cx_tlm(cx_problem* p, const void* g, const void* dg, void* du_out, voi
 }
 
 cx_status cx_cadjoint(cx_problem* p, const void* g, void* dJdg) {
-    if (!p || !dJdg) return CX_ERR_INVALID_ARG;
+    if (!p || !dJdg || p->d.halo) return CX_ERR_INVALID_ARG;
     if (!p->fwd_valid) return CX_ERR_STATE;
     if (p->lay.esz == 8) return run_cadj<double>(p, (const double*)g, (double*)dJdg);
     return run_cadj<float>(p, (const float*)g, (float*)dJdg);
 }
 
 cx_status cx_lma_step(cx_problem* p, void* g_inout, void* E_work, cx_step_info* info) {
-    if (!p || !g_inout || !E_work) return CX_ERR_INVALID_ARG;
+    if (!p || !g_inout || !E_work || p->d.halo) return CX_ERR_INVALID_ARG;
     if (!p->has_init) return CX_ERR_STATE;
     if (p->lay.esz == 8) return run_lma_step<double>(p, (double*)g_inout, (double*)E_work, info);
     return run_lma_step<float>(p, (float*)g_inout, (float*)E_work, info);
@@ -951,7 +991,7 @@ cx_status cx_cg_reset(cx_problem* p) {
 }
 
 cx_status cx_step(cx_problem* p, void* g_inout, void* E_work, cx_step_info* info) {
-    if (!p || !g_inout || !E_work) return CX_ERR_INVALID_ARG;
+    if (!p || !g_inout || !E_work || p->d.halo) return CX_ERR_INVALID_ARG;
     if (!p->has_init) return CX_ERR_STATE;
     if (p->lay.esz == 8) return run_step<double>(p, (double*)g_inout, (double*)E_work, info);
     return run_step<float>(p, (float*)g_inout, (float*)E_work, info);

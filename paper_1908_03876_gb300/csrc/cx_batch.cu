@@ -1150,6 +1150,7 @@ cx_status batch_layout(const cx_problem_desc* d, int count, std::vector<size_t>*
     if (!d || count < 1 || count > MAX_BATCH) return CX_ERR_INVALID_ARG;
     size_t o = 0;
     for (int i = 0; i < count; ++i) {
+        if (d[i].halo) return CX_ERR_INVALID_ARG; // sub-domains of one problem are not independent problems
         if (d[i].n_steps != d[0].n_steps || d[i].lattice != d[0].lattice || d[i].precision != d[0].precision ||
             (d[i].ckpt_every ? d[i].ckpt_every : d[i].n_steps) != (d[0].ckpt_every ? d[0].ckpt_every : d[0].n_steps))
             return CX_ERR_INVALID_ARG;

@@ -50,6 +50,20 @@ template <> struct Lat<9> {
     }
     // indices of the two flux moments j_x, j_y inside the moment vector
     static constexpr int JX = 3, JY = 5;
+    // moment images of the source shapes (M0 applied to w_i, w_i e_x,i and w_i e_y,i):
+    // a source s_i = w_i (a + b.e_i) has moments a src_A(k) + b_x src_Bx(k) + b_y src_By(k)
+    __host__ __device__ static constexpr double src_A(int k) {
+        constexpr double t[9] = {1, -2, 1, 0, 0, 0, 0, 0, 0};
+        return t[k];
+    }
+    __host__ __device__ static constexpr double src_Bx(int k) {
+        constexpr double t[9] = {0, 0, 0, 1.0 / 3, -1.0 / 3, 0, 0, 0, 0};
+        return t[k];
+    }
+    __host__ __device__ static constexpr double src_By(int k) {
+        constexpr double t[9] = {0, 0, 0, 0, 0, 1.0 / 3, -1.0 / 3, 0, 0};
+        return t[k];
+    }
 };
 
 template <> struct Lat<5> {
@@ -67,6 +81,18 @@ template <> struct Lat<5> {
         return t[k];
     }
     static constexpr int JX = 1, JY = 2;
+    __host__ __device__ static constexpr double src_A(int k) {
+        constexpr double t[5] = {1, 0, 0, -2.0 / 3, 0};
+        return t[k];
+    }
+    __host__ __device__ static constexpr double src_Bx(int k) {
+        constexpr double t[5] = {0, 1.0 / 3, 0, 0, 0};
+        return t[k];
+    }
+    __host__ __device__ static constexpr double src_By(int k) {
+        constexpr double t[5] = {0, 0, 1.0 / 3, 0, 0};
+        return t[k];
+    }
 };
 
 // Moment transforms.  m = M f and its transpose out = M^T r, written for D2Q9
@@ -676,7 +702,7 @@ template <int NT> struct ChunkIter {
         r.x = seg * NT + (int)threadIdx.x;
         r.y = y;
         r.k = r.y * C.nx + r.x;
-        r.fluid = r.x < C.nx && !(f & 1u);
+        r.fluid = r.x < C.nx && !(f & 1u) && !(C.halo && (r.x == 0 || r.y == 0 || r.x == C.nx - 1 || r.y == C.ny - 1));
         r.c = r.x < C.nx ? ctrl_index(C, r.x, r.k) : -1;
         r.ctrl = r.fluid && r.c >= 0 && (!C.cmask || (f & 2u));
         return r;

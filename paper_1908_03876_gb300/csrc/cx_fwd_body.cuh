@@ -14,6 +14,11 @@
 //   P_v,i   += w~_i [c_n Phi^n + c'_n Phi^{n-1}]                    (eq. PhiS with
 //              V = (I - K_v/2) a, kappa_x = 0; c_n = 3 tau/2, c'_n = -tau/2;
 //              c_0 = tau, c'_0 = 0 because Phi^{-1} := Phi^0)
+// Both sources have the shape w_i (a + b.e_i).  In FP32 they join the
+// collision in moment space: with s^ = M0 s (a few nonzero moments) and
+// M0^-1 = M0^T N^-1, P = f - M0^T N^-1 (Pi (m - m^eq) - s^), one transform per
+// species and fewer instructions.  FP64 (the parity mode) adds them per
+// direction, in the order of operations of the equations as written.
 // The node also writes Phi^n (node-local state for the next step), optionally
 // the adjoint tape (u, G_x, G_y), and accumulates (g^n)^2 for the penalty.
 //
@@ -112,14 +117,26 @@ __device__ __forceinline__ void fwd_compute(const CxConst& C, const KConst<T>& K
 #pragma unroll
     for (int kk = 0; kk < Q; ++kk) dm[kk] = mu[kk] - Tu * mh[kk];
     relax_n<T, Q>(KC, nc.Ku0, nc.Ku1, nc.Ku2, dm, rl);
-    // (w_i/Cs^2) chi u e_i.(K_u G) = 3 w_i e_i . F
+    // (w_i/Cs^2) chi u e_i.(K_u G) = 3 w_i e_i . F: moments 3 (F_x src_Bx + F_y src_By)
     const T Fx = KC.chi * Tu * (nc.Ku0 * Gx + nc.Ku1 * Gy);
     const T Fy = KC.chi * Tu * (nc.Ku1 * Gx + nc.Ku2 * Gy);
-    Transform<T, Q>::transpose(rl, bt); // M^-1 Pi (m - m^eq) = M^T N^-1 Pi (m - m^eq)
+    constexpr bool fold = sizeof(T) == 4; // sources in moment space (FP32)
+    if constexpr (fold) {
+#pragma unroll
+        for (int kk = 0; kk < Q; ++kk) {
+            if (L::src_Bx(kk) != 0.0) rl[kk] -= T(3.0 * L::inv_n(kk) * L::src_Bx(kk)) * Fx;
+            if (L::src_By(kk) != 0.0) rl[kk] -= T(3.0 * L::inv_n(kk) * L::src_By(kk)) * Fy;
+        }
+    }
+    Transform<T, Q>::transpose(rl, bt); // M^-1 (Pi (m - m^eq) - s^) = M^T N^-1 (...)
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const T src = T(3.0 * L::w(i)) * (T(L::ex(i)) * Fx + T(L::ey(i)) * Fy);
-        A.out(i)[k] = fu[i] - bt[i] + src;
+        if constexpr (fold) {
+            A.out(i)[k] = fu[i] - bt[i];
+        } else {
+            const T src = T(3.0 * L::w(i)) * (T(L::ex(i)) * Fx + T(L::ey(i)) * Fy);
+            A.out(i)[k] = fu[i] - bt[i] + src;
+        }
     }
 
     // --- species v: MRT collision + reaction/control source with the tau/2
@@ -130,11 +147,25 @@ __device__ __forceinline__ void fwd_compute(const CxConst& C, const KConst<T>& K
     relax_n<T, Q>(KC, nc.Kv0, nc.Kv1, nc.Kv2, dm, rl);
     const T Vx = nc.ax - T(0.5) * Kax, Vy = nc.ay - T(0.5) * Kay; // V = (I - K_v/2) a
     const T srcv = (A.n == 0) ? KC.c_first * Phi : KC.c_now * Phi + KC.c_prev * Phi_prev;
+    // w~_i srcv = w_i (srcv + 3 srcv V.e_i): moments srcv src_A + 3 srcv (V_x src_Bx + V_y src_By)
+    if constexpr (fold) {
+        const T sVx = srcv * Vx, sVy = srcv * Vy;
+#pragma unroll
+        for (int kk = 0; kk < Q; ++kk) {
+            if (L::src_A(kk) != 0.0) rl[kk] -= T(L::inv_n(kk) * L::src_A(kk)) * srcv;
+            if (L::src_Bx(kk) != 0.0) rl[kk] -= T(3.0 * L::inv_n(kk) * L::src_Bx(kk)) * sVx;
+            if (L::src_By(kk) != 0.0) rl[kk] -= T(3.0 * L::inv_n(kk) * L::src_By(kk)) * sVy;
+        }
+    }
     Transform<T, Q>::transpose(rl, bt);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const T wt = T(L::w(i)) * (T(1) + T(3) * (Vx * T(L::ex(i)) + Vy * T(L::ey(i))));
-        A.out(Q + i)[k] = fv[i] - bt[i] + wt * srcv;
+        if constexpr (fold) {
+            A.out(Q + i)[k] = fv[i] - bt[i];
+        } else {
+            const T wt = T(L::w(i)) * (T(1) + T(3) * (Vx * T(L::ex(i)) + Vy * T(L::ey(i))));
+            A.out(Q + i)[k] = fv[i] - bt[i] + wt * srcv;
+        }
     }
     A.phi[k] = Phi;
     if (A.phi_ckpt) A.phi_ckpt[k] = Phi;

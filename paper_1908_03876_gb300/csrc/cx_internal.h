@@ -16,6 +16,7 @@ struct CxConst {
     int Q, n_steps;
     int aniso, adv, has_solid;
     int ctrl_full;                    // control window = whole grid, no mask
+    int halo;                         // outer one-node frame is a halo of ghost nodes (sub-domain)
     int cx0, cy0, cnx, cny;
     int source_order;
     double tau, d_u, d_v, chi, r_vu, r_vv, alpha;

@@ -64,7 +64,8 @@ __global__ void __launch_bounds__(256) k_final(const CxConst C, const T* Pin, co
         const int k = y * C.nx + x;
         const size_t pl = (size_t)C.plane;
         T su = T(0), sv = T(0), w = T(0);
-        if (!(C.has_solid && C.solid[k])) {
+        const bool ghost = C.halo && (x == 0 || y == 0 || x == C.nx - 1 || y == C.ny - 1);
+        if (!(C.has_solid && C.solid[k]) && !ghost) {
             const int xm = x == 0 ? C.nx - 1 : x - 1, xp = x == C.nx - 1 ? 0 : x + 1;
             const int ym = y == 0 ? C.ny - 1 : y - 1, yp = y == C.ny - 1 ? 0 : y + 1;
 #pragma unroll

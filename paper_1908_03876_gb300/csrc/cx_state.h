@@ -61,6 +61,8 @@ struct cx_problem {
     void* psi0 = nullptr;
     bool timing = false;
     std::vector<cx::TimedRange> ranges;
+    cx_halo_fn halo_fn = nullptr; // sub-domain: fills the halo frame after every lattice step
+    void* halo_user = nullptr;
     size_t n_ranges = 0;
 
     template <typename P> P* at(size_t off) const { return reinterpret_cast<P*>(ws + off); }

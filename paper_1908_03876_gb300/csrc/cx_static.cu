@@ -176,7 +176,7 @@ extern "C" cx_status cx_forward_static(const cx_problem_desc* desc, const void* 
     size_t check = 0;
     cx_status rc = cx_workspace_size(desc, &check); // same descriptor validation as cx_create
     if (rc) return rc;
-    if (!u0 || !v0) return CX_ERR_INVALID_ARG;
+    if (!u0 || !v0 || desc->halo) return CX_ERR_INVALID_ARG;
     const StaticLayout Ly = static_layout(desc);
     if (Ly.total > (size_t)CX_STATIC_SCRATCH_BYTES) return CX_ERR_WORKSPACE; // problem too large for the array
     // the array's device address on the current device (looked up on every call)

@@ -270,4 +270,5 @@ def make_desc(w: Workload, dev, precision=None):
     d.s = (ctypes.c_double * 7)(*w.s)
     d.source_order = w.source_order
     d.ctrl_windows = w.windows
+    d.halo = w.halo
     return d, keep

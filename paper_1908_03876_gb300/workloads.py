@@ -71,6 +71,7 @@ class Workload:
     source_order: int = 2
     ckpt_every: int = 0
     windows: int = 0          # W > 0: control piecewise constant over W equal time windows
+    halo: int = 0             # 1: a sub-domain whose outer one-node frame holds ghost copies of its neighbours
     extra: dict = field(default_factory=dict)
 
     # ---- views of the same inputs in per-node form (input shaping only)
