@@ -408,3 +408,122 @@ def lma_step(p: Problem, g, c1=1e-4, max_trials=30):
             return gt, dict(J0=J0, J=Jt, lam=lam, trials=t + 1, E2=e2)
         lam *= 0.5
     raise RuntimeError("line search failed")
+
+
+# ---------------------------------------------------------------- three species
+
+class _Problem3(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("N", ctypes.c_int), ("tau", ctypes.c_double),
+        ("Du", ctypes.c_void_p), ("Dv", ctypes.c_void_p), ("Dw", ctypes.c_void_p), ("d", ctypes.c_double),
+        ("a", ctypes.c_void_p), ("chi1", ctypes.c_double), ("chi2", ctypes.c_double),
+        ("a1", ctypes.c_double), ("a2", ctypes.c_double),
+        ("b1", ctypes.c_double), ("b2", ctypes.c_double), ("b3", ctypes.c_double),
+        ("c1", ctypes.c_double), ("c2", ctypes.c_double), ("ctrl_species", ctypes.c_int),
+        ("u_tgt", ctypes.c_void_p), ("alpha", ctypes.c_double), ("s", ctypes.c_double * 7),
+        ("source_order", ctypes.c_int), ("u0", ctypes.c_void_p), ("v0", ctypes.c_void_p), ("w0", ctypes.c_void_p),
+    ]
+
+
+@dataclass
+class Problem3:
+    """Three-species (attraction-repulsion chemotaxis, logistic source) problem
+    in the oracle's layout (see mrt_oracle.h, or3_problem)."""
+
+    nx: int
+    ny: int
+    N: int
+    Du: np.ndarray
+    Dv: np.ndarray
+    Dw: np.ndarray
+    u0: np.ndarray
+    v0: np.ndarray
+    w0: np.ndarray
+    u_tgt: np.ndarray
+    d: float = 1.0
+    a: np.ndarray | None = None
+    chi1: float = 0.0
+    chi2: float = 0.0
+    a1: float = 0.0
+    a2: float = 0.0
+    b1: float = 0.0
+    b2: float = 0.0
+    b3: float = 0.0
+    c1: float = 0.0
+    c2: float = 0.0
+    ctrl_species: int = 2
+    alpha: float = 0.0
+    s: tuple = (1.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0)
+    source_order: int = 2
+    tau: float = 1.0
+    _keep: list = field(default_factory=list, repr=False)
+
+    def _struct(self):
+        arrs = dict(Du=_f64(self.Du), Dv=_f64(self.Dv), Dw=_f64(self.Dw), a=_f64(self.a), u_tgt=_f64(self.u_tgt),
+                    u0=_f64(self.u0), v0=_f64(self.v0), w0=_f64(self.w0))
+        self._keep = list(arrs.values())
+        st = _Problem3()
+        st.nx, st.ny, st.N, st.tau = self.nx, self.ny, self.N, self.tau
+        for k in ("Du", "Dv", "Dw", "a", "u_tgt", "u0", "v0", "w0"):
+            setattr(st, k, _ptr(arrs[k]))
+        for k in ("d", "chi1", "chi2", "a1", "a2", "b1", "b2", "b3", "c1", "c2", "alpha"):
+            setattr(st, k, float(getattr(self, k)))
+        st.ctrl_species = self.ctrl_species
+        st.s = (ctypes.c_double * 7)(*self.s)
+        st.source_order = self.source_order
+        return st
+
+
+def _load3():
+    lib = _load()
+    if not hasattr(lib, "_or3_ready"):
+        P = ctypes.POINTER(_Problem3)
+        vp, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)
+        lib.or3_forward.argtypes = [P, vp, dp, vp]
+        lib.or3_forward_trace.argtypes = [P, vp, vp]
+        lib.or3_tlm.argtypes = [P, vp, vp, vp, vp, dp]
+        lib.or3_adjoint.argtypes = [P, vp, vp, vp, vp, dp]
+        lib._or3_ready = True
+    return lib
+
+
+def forward3(p: Problem3, g=None):
+    """Three-species forward solve.  Returns (J, uvw^N [3][ny][nx])."""
+    lib = _load3()
+    st = p._struct()
+    J = ctypes.c_double(0.0)
+    uvw = np.zeros((3, p.ny, p.nx))
+    _check(lib.or3_forward(ctypes.byref(st), _ptr(_f64(g)), ctypes.byref(J), _ptr(uvw)), "forward3")
+    return J.value, uvw
+
+
+def forward3_trace(p: Problem3, g=None):
+    """Per step: (masses of u, v, w before collision [N][3], sums of Phi_u, Phi_v, Phi_w [N][3])."""
+    lib = _load3()
+    st = p._struct()
+    tr = np.zeros((p.N, 6))
+    _check(lib.or3_forward_trace(ctypes.byref(st), _ptr(_f64(g)), _ptr(tr)), "forward3_trace")
+    return tr[:, :3], tr[:, 3:]
+
+
+def tlm3(p: Problem3, g, dg, df0=None):
+    """Tangent-linear model.  Returns (dJ, duvw^N [3][ny][nx])."""
+    lib = _load3()
+    st = p._struct()
+    dJ = ctypes.c_double(0.0)
+    d = np.zeros((3, p.ny, p.nx))
+    _check(lib.or3_tlm(ctypes.byref(st), _ptr(_f64(g)), _ptr(_f64(dg)), _ptr(_f64(df0)), _ptr(d), ctypes.byref(dJ)),
+           "tlm3")
+    return dJ.value, d
+
+
+def adjoint3(p: Problem3, g=None, seeds=None, want_psi0=False):
+    """Exact discrete adjoint.  Returns (J, dJ/dg [N][ny][nx], psi0 [ny][nx][3][9] or None)."""
+    lib = _load3()
+    st = p._struct()
+    J = ctypes.c_double(0.0)
+    E = np.zeros((p.N, p.ny, p.nx))
+    psi0 = np.zeros((p.ny, p.nx, 3, 9)) if want_psi0 else None
+    _check(lib.or3_adjoint(ctypes.byref(st), _ptr(_f64(g)), _ptr(_f64(seeds)), _ptr(E), _ptr(psi0),
+                           ctypes.byref(J)), "adjoint3")
+    return J.value, E, psi0

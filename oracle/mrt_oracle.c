@@ -968,3 +968,438 @@ int or_cadjoint(const or_problem* p, const double* g, double* dJdg, double* J) {
     free(u);
     return 0;
 }
+
+/* ===================================================================
+ * Three species (u, v, w): the attraction-repulsion chemotaxis model with
+ * a logistic source (the ARC example of Sec. 2.2, a case of the paper's
+ * three-equation system eq. ReacDiff), solved by the same coupled MRT
+ * scheme of Sec. 3.1 (eq. LBE with S, PhiS, phieq) and differentiated by the
+ * exact discrete adjoint of Sec. 3.2.1.  See mrt_oracle.h (or3_problem).
+ *   Phi_u = a1 u - a2 u^2, Phi_v = b1 u - b2 v - b3 u v, Phi_w = c1 u - c2 w,
+ *   and the control g added to Phi_v or Phi_w;
+ *   S_u,i = (w_i/Cs^2) e_i . (K_u (chi1 u G_v + chi2 u G_w)) (eq. S with
+ *   D_{u,1} = chi1 u I toward v and D_{u,2} = chi2 u I toward w);
+ *   G_Theta the local gradient of Theta = v, w from its non-equilibrium flux
+ *   (the reading of C146 used for v in the two-species model).
+ * Populations [ny][nx][3][Q] (species u, v, w), periodic grid, D2Q9.
+ * =================================================================== */
+
+typedef struct {
+    double K[3][2][2];   /* relaxation blocks of u, v, w */
+    double a[2];
+    double aleph[3][9];  /* adjoint-equilibrium weights per species */
+    double wt[3][9];     /* w~_i = w_i (1 + V_Theta.e_i / Cs^2), V_Theta = (I - K_Theta/2) a */
+} node3_t;
+
+static void Pi_rates(const double s[7], const double K[2][2], double Pi[9][9]) {
+    memset(Pi, 0, sizeof(double) * 81);
+    Pi[0][0] = s[0];
+    Pi[1][1] = s[1];
+    Pi[2][2] = s[2];
+    Pi[3][3] = K[0][0];
+    Pi[3][5] = K[0][1];
+    Pi[4][4] = s[3];
+    Pi[5][3] = K[1][0];
+    Pi[5][5] = K[1][1];
+    Pi[6][6] = s[4];
+    Pi[7][7] = s[5];
+    Pi[8][8] = s[6];
+}
+
+static void node3_params(const lattice_t* L, const or3_problem* p, int x, int y, node3_t* nd) {
+    int k = y * p->nx + x;
+    const double* D[3] = {p->Du, p->Dv, p->Dw};
+    nd->a[0] = p->a ? p->a[2 * k] : 0.0;
+    nd->a[1] = p->a ? p->a[2 * k + 1] : 0.0;
+    for (int sp = 0; sp < 3; ++sp) {
+        K_from_D(D[sp] + 3 * k, p->d, p->tau, nd->K[sp]);
+        aleph_lat(L, nd->a, p->d, nd->aleph[sp]);
+        double V[2];
+        for (int c = 0; c < 2; ++c)
+            V[c] = nd->a[c] - 0.5 * (nd->K[sp][c][0] * nd->a[0] + nd->K[sp][c][1] * nd->a[1]);
+        for (int i = 0; i < L->Q; ++i)
+            nd->wt[sp][i] = L->w[i] * (1.0 + (V[0] * L->e[i][0] + V[1] * L->e[i][1]) / CS2);
+    }
+}
+
+static double c3_now(const or3_problem* p, int n) { return (p->source_order == 1 || n == 0) ? p->tau : 1.5 * p->tau; }
+static double c3_prev(const or3_problem* p, int n) { return (p->source_order == 1 || n == 0) ? 0.0 : -0.5 * p->tau; }
+
+/* reaction/control sources (the kinetics of the ARC example) */
+static void phi3(const or3_problem* p, double Tu, double Tv, double Tw, double g, double Phi[3]) {
+    Phi[0] = p->a1 * Tu - p->a2 * Tu * Tu;
+    Phi[1] = p->b1 * Tu - p->b2 * Tv - p->b3 * Tu * Tv + (p->ctrl_species == 1 ? g : 0.0);
+    Phi[2] = p->c1 * Tu - p->c2 * Tw + (p->ctrl_species == 2 ? g : 0.0);
+}
+
+/* local gradient of a species from its first non-equilibrium moment (C146 reading) */
+static void grad3(const or3_problem* p, const double K[2][2], const double a[2], double T, const double j[2],
+                  double Phi, double G[2]) {
+    double r[2] = {(j[0] - a[0] * T) / p->tau, (j[1] - a[1] * T) / p->tau};
+    for (int c = 0; c < 2; ++c)
+        G[c] = -(K[c][0] * r[0] + K[c][1] * r[1] + 0.5 * (K[c][0] * a[0] + K[c][1] * a[1]) * Phi) / (p->d * CS2);
+}
+
+typedef struct {
+    double T[3], Phi[3], Gv[2], Gw[2];
+} state3_t;
+
+/* one collision of the three species at a node: f[3][Q] -> P[3][Q] */
+static void collide3(const lattice_t* L, const or3_problem* p, const node3_t* nd, int n, const double* f,
+                     double g, const double Phi_prev[3], double* P, state3_t* st) {
+    int Q = L->Q;
+    double T[3] = {0, 0, 0}, j[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+    for (int sp = 0; sp < 3; ++sp)
+        for (int i = 0; i < Q; ++i) {
+            T[sp] += f[sp * Q + i];
+            j[sp][0] += L->e[i][0] * f[sp * Q + i];
+            j[sp][1] += L->e[i][1] * f[sp * Q + i];
+        }
+    double Phi[3], Pp[3];
+    phi3(p, T[0], T[1], T[2], g, Phi);
+    for (int sp = 0; sp < 3; ++sp) Pp[sp] = (n == 0) ? Phi[sp] : Phi_prev[sp];
+    double Gv[2], Gw[2];
+    grad3(p, nd->K[1], nd->a, T[1], j[1], Phi[1], Gv);
+    grad3(p, nd->K[2], nd->a, T[2], j[2], Phi[2], Gw);
+    double Pi[9][9], feq[9];
+    for (int sp = 0; sp < 3; ++sp) {
+        Pi_rates(p->s, nd->K[sp], Pi);
+        feq_lat(L, T[sp], nd->a, p->d, feq);
+        mrt_collide(L, Pi, f + sp * Q, feq, P + sp * Q);
+        for (int i = 0; i < Q; ++i) {
+            double src = p->tau * nd->wt[sp][i] * Phi[sp];
+            if (p->source_order != 1) src += 0.5 * p->tau * nd->wt[sp][i] * (Phi[sp] - Pp[sp]);
+            P[sp * Q + i] += src;
+        }
+    }
+    /* tau S_u: chemotactic fluxes toward v (chi1) and w (chi2) */
+    double F[2];
+    for (int c = 0; c < 2; ++c) F[c] = p->chi1 * T[0] * Gv[c] + p->chi2 * T[0] * Gw[c];
+    double KF[2] = {nd->K[0][0][0] * F[0] + nd->K[0][0][1] * F[1], nd->K[0][1][0] * F[0] + nd->K[0][1][1] * F[1]};
+    for (int i = 0; i < Q; ++i) P[i] += L->w[i] / CS2 * (L->e[i][0] * KF[0] + L->e[i][1] * KF[1]);
+    if (st) {
+        for (int sp = 0; sp < 3; ++sp) {
+            st->T[sp] = T[sp];
+            st->Phi[sp] = Phi[sp];
+        }
+        st->Gv[0] = Gv[0];
+        st->Gv[1] = Gv[1];
+        st->Gw[0] = Gw[0];
+        st->Gw[1] = Gw[1];
+    }
+}
+
+static void stream3(const lattice_t* L, const or3_problem* p, const double* P, double* f, int adjoint) {
+    int Q = L->Q, nx = p->nx, ny = p->ny;
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x)
+            for (int sp = 0; sp < 3; ++sp)
+                for (int i = 0; i < Q; ++i) {
+                    int sx = adjoint ? L->e[i][0] : -L->e[i][0], sy = adjoint ? L->e[i][1] : -L->e[i][1];
+                    int xs = (x + sx + nx) % nx, ys = (y + sy + ny) % ny;
+                    f[((size_t)(y * nx + x) * 3 + sp) * Q + i] = P[((size_t)(ys * nx + xs) * 3 + sp) * Q + i];
+                }
+}
+
+static int run3_forward(const or3_problem* p, const double* g, double* fN, double* traj, double* Phi_traj,
+                        double* trace) {
+    lattice_t L;
+    if (lattice_init(&L, 9)) return -1;
+    int Q = 9, nx = p->nx, ny = p->ny;
+    size_t nn = (size_t)nx * ny, npop = nn * 3 * Q;
+    double* f = calloc(npop, sizeof(double));
+    double* P = calloc(npop, sizeof(double));
+    double* Phi = calloc(nn * 3, sizeof(double));
+    double* Th = calloc(nn * 3, sizeof(double));
+    node3_t* nodes = malloc(sizeof(node3_t) * nn);
+    if (!f || !P || !Phi || !Th || !nodes) return -2;
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) node3_params(&L, p, x, y, &nodes[y * nx + x]);
+    const double* init[3] = {p->u0, p->v0, p->w0};
+    for (size_t k = 0; k < nn; ++k)
+        for (int sp = 0; sp < 3; ++sp) feq_lat(&L, init[sp][k], nodes[k].a, p->d, f + (k * 3 + sp) * Q);
+    for (int n = 0; n < p->N; ++n) {
+        if (traj) memcpy(traj + (size_t)n * npop, f, sizeof(double) * npop);
+#pragma omp parallel for schedule(static)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                size_t k = (size_t)y * nx + x;
+                state3_t st;
+                double gv = g ? g[(size_t)n * nn + k] : 0.0;
+                collide3(&L, p, &nodes[k], n, f + k * 3 * Q, gv, Phi + 3 * k, P + k * 3 * Q, &st);
+                for (int sp = 0; sp < 3; ++sp) {
+                    Phi[3 * k + sp] = st.Phi[sp];
+                    Th[3 * k + sp] = st.T[sp];
+                }
+            }
+        if (Phi_traj) memcpy(Phi_traj + (size_t)n * nn * 3, Phi, sizeof(double) * nn * 3);
+        if (trace) /* per step: mass of u, v, w before collision, then sum of Phi_u, Phi_v, Phi_w */
+            for (int sp = 0; sp < 3; ++sp) {
+                double m = 0.0, s = 0.0;
+                for (size_t k = 0; k < nn; ++k) {
+                    m += Th[3 * k + sp];
+                    s += Phi[3 * k + sp];
+                }
+                trace[(size_t)n * 6 + sp] = m;
+                trace[(size_t)n * 6 + 3 + sp] = s;
+            }
+        stream3(&L, p, P, f, 0);
+    }
+    memcpy(fN, f, sizeof(double) * npop);
+    free(f);
+    free(P);
+    free(Phi);
+    free(Th);
+    free(nodes);
+    return 0;
+}
+
+static double cost3(const or3_problem* p, const double* fN, const double* g, double* uvw) {
+    size_t nn = (size_t)p->nx * p->ny;
+    double s = 0.0, pen = 0.0;
+    for (size_t k = 0; k < nn; ++k) {
+        double T[3] = {0, 0, 0};
+        for (int sp = 0; sp < 3; ++sp)
+            for (int i = 0; i < 9; ++i) T[sp] += fN[(k * 3 + sp) * 9 + i];
+        if (uvw)
+            for (int sp = 0; sp < 3; ++sp) uvw[sp * nn + k] = T[sp];
+        double d = T[0] - p->u_tgt[k];
+        s += 0.5 * d * d;
+    }
+    if (g)
+        for (size_t q = 0; q < (size_t)p->N * nn; ++q) pen += g[q] * g[q];
+    return s + p->alpha * pen;
+}
+
+int or3_forward(const or3_problem* p, const double* g, double* J, double* uvwN) {
+    size_t nn = (size_t)p->nx * p->ny;
+    double* fN = malloc(sizeof(double) * nn * 27);
+    if (!fN) return -2;
+    int rc = run3_forward(p, g, fN, NULL, NULL, NULL);
+    if (rc) return rc;
+    double c = cost3(p, fN, g, uvwN);
+    if (J) *J = c;
+    free(fN);
+    return 0;
+}
+
+int or3_forward_trace(const or3_problem* p, const double* g, double* trace) {
+    size_t nn = (size_t)p->nx * p->ny;
+    double* fN = malloc(sizeof(double) * nn * 27);
+    if (!fN) return -2;
+    int rc = run3_forward(p, g, fN, NULL, NULL, trace);
+    free(fN);
+    return rc;
+}
+
+/* Tangent-linear model of the three-species forward solve along dg (and df0,
+ * [ny][nx][3][Q], may be NULL): duvwN [3][ny][nx] and the derivative dJ. */
+int or3_tlm(const or3_problem* p, const double* g, const double* dg, const double* df0, double* duvwN, double* dJ) {
+    lattice_t L;
+    if (lattice_init(&L, 9)) return -1;
+    int Q = 9, nx = p->nx, ny = p->ny;
+    size_t nn = (size_t)nx * ny, npop = nn * 3 * Q;
+    double *f = calloc(npop, sizeof(double)), *P = calloc(npop, sizeof(double));
+    double *df = calloc(npop, sizeof(double)), *dP = calloc(npop, sizeof(double));
+    double *Phi = calloc(nn * 3, sizeof(double)), *dPhi = calloc(nn * 3, sizeof(double));
+    node3_t* nodes = malloc(sizeof(node3_t) * nn);
+    if (!f || !P || !df || !dP || !Phi || !dPhi || !nodes) return -2;
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) node3_params(&L, p, x, y, &nodes[y * nx + x]);
+    const double* init[3] = {p->u0, p->v0, p->w0};
+    for (size_t k = 0; k < nn; ++k)
+        for (int sp = 0; sp < 3; ++sp) feq_lat(&L, init[sp][k], nodes[k].a, p->d, f + (k * 3 + sp) * Q);
+    if (df0) memcpy(df, df0, sizeof(double) * npop);
+    for (int n = 0; n < p->N; ++n) {
+#pragma omp parallel for schedule(static)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                size_t k = (size_t)y * nx + x;
+                const node3_t* nd = &nodes[k];
+                state3_t st;
+                double gv = g ? g[(size_t)n * nn + k] : 0.0;
+                double dgv = dg ? dg[(size_t)n * nn + k] : 0.0;
+                collide3(&L, p, nd, n, f + k * 3 * Q, gv, Phi + 3 * k, P + k * 3 * Q, &st);
+                /* tangent of the local map */
+                const double* dfk = df + k * 3 * Q;
+                double* dPk = dP + k * 3 * Q;
+                double dT[3] = {0, 0, 0}, dj[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+                for (int sp = 0; sp < 3; ++sp)
+                    for (int i = 0; i < Q; ++i) {
+                        dT[sp] += dfk[sp * Q + i];
+                        dj[sp][0] += L.e[i][0] * dfk[sp * Q + i];
+                        dj[sp][1] += L.e[i][1] * dfk[sp * Q + i];
+                    }
+                const double Tu = st.T[0], Tv = st.T[1];
+                double dPh[3];
+                dPh[0] = (p->a1 - 2.0 * p->a2 * Tu) * dT[0];
+                dPh[1] = (p->b1 - p->b3 * Tv) * dT[0] - (p->b2 + p->b3 * Tu) * dT[1] + (p->ctrl_species == 1 ? dgv : 0.0);
+                dPh[2] = p->c1 * dT[0] - p->c2 * dT[2] + (p->ctrl_species == 2 ? dgv : 0.0);
+                double dPp[3];
+                for (int sp = 0; sp < 3; ++sp) dPp[sp] = (n == 0) ? dPh[sp] : dPhi[3 * k + sp];
+                double dGv[2], dGw[2];
+                grad3(p, nd->K[1], nd->a, dT[1], dj[1], dPh[1], dGv); /* G is linear in (j, T, Phi) */
+                grad3(p, nd->K[2], nd->a, dT[2], dj[2], dPh[2], dGw);
+                double Pi[9][9], dfeq[9];
+                for (int sp = 0; sp < 3; ++sp) {
+                    Pi_rates(p->s, nd->K[sp], Pi);
+                    feq_lat(&L, dT[sp], nd->a, p->d, dfeq);
+                    mrt_collide(&L, Pi, dfk + sp * Q, dfeq, dPk + sp * Q);
+                    for (int i = 0; i < Q; ++i) {
+                        double src = p->tau * nd->wt[sp][i] * dPh[sp];
+                        if (p->source_order != 1) src += 0.5 * p->tau * nd->wt[sp][i] * (dPh[sp] - dPp[sp]);
+                        dPk[sp * Q + i] += src;
+                    }
+                }
+                double dF[2];
+                for (int c = 0; c < 2; ++c)
+                    dF[c] = (p->chi1 * st.Gv[c] + p->chi2 * st.Gw[c]) * dT[0] +
+                            Tu * (p->chi1 * dGv[c] + p->chi2 * dGw[c]);
+                double dKF[2] = {nd->K[0][0][0] * dF[0] + nd->K[0][0][1] * dF[1],
+                                 nd->K[0][1][0] * dF[0] + nd->K[0][1][1] * dF[1]};
+                for (int i = 0; i < Q; ++i) dPk[i] += L.w[i] / CS2 * (L.e[i][0] * dKF[0] + L.e[i][1] * dKF[1]);
+                for (int sp = 0; sp < 3; ++sp) {
+                    Phi[3 * k + sp] = st.Phi[sp];
+                    dPhi[3 * k + sp] = dPh[sp];
+                }
+            }
+        stream3(&L, p, P, f, 0);
+        stream3(&L, p, dP, df, 0);
+    }
+    double s = 0.0;
+    for (size_t k = 0; k < nn; ++k) {
+        double T[3] = {0, 0, 0}, dT[3] = {0, 0, 0};
+        for (int sp = 0; sp < 3; ++sp)
+            for (int i = 0; i < Q; ++i) {
+                T[sp] += f[(k * 3 + sp) * Q + i];
+                dT[sp] += df[(k * 3 + sp) * Q + i];
+            }
+        if (duvwN)
+            for (int sp = 0; sp < 3; ++sp) duvwN[sp * nn + k] = dT[sp];
+        s += (T[0] - p->u_tgt[k]) * dT[0];
+    }
+    if (g && dg)
+        for (size_t q = 0; q < (size_t)p->N * nn; ++q) s += 2.0 * p->alpha * g[q] * dg[q];
+    if (dJ) *dJ = s;
+    free(f); free(P); free(df); free(dP); free(Phi); free(dPhi); free(nodes);
+    return 0;
+}
+
+/* Exact discrete adjoint of the three-species forward solve.  seeds [3][ny][nx]
+ * (adjoints of u^N, v^N, w^N), NULL meaning (u^N - u_tgt, 0, 0); with seeds the
+ * gradient is that of sum(seed . uvw^N) + alpha ||g||^2.  dJdg [N][ny][nx];
+ * psi0 [ny][nx][3][Q] (may be NULL); J (may be NULL). */
+int or3_adjoint(const or3_problem* p, const double* g, const double* seeds, double* dJdg, double* psi0, double* J) {
+    lattice_t L;
+    if (lattice_init(&L, 9)) return -1;
+    int Q = 9, nx = p->nx, ny = p->ny, N = p->N;
+    size_t nn = (size_t)nx * ny, npop = nn * 3 * Q;
+    double* traj = malloc(sizeof(double) * npop * (size_t)N);
+    double* Phi_traj = malloc(sizeof(double) * nn * 3 * (size_t)N);
+    double* fN = malloc(sizeof(double) * npop);
+    double* psi = calloc(npop, sizeof(double));
+    double* rho = calloc(npop, sizeof(double));
+    double* sig_next = calloc(nn * 3, sizeof(double));
+    double* sig_now = calloc(nn * 3, sizeof(double));
+    double* uvw = malloc(sizeof(double) * nn * 3);
+    node3_t* nodes = malloc(sizeof(node3_t) * nn);
+    if (!traj || !Phi_traj || !fN || !psi || !rho || !sig_next || !sig_now || !uvw || !nodes) return -2;
+    int rc = run3_forward(p, g, fN, traj, Phi_traj, NULL);
+    if (rc) return rc;
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) node3_params(&L, p, x, y, &nodes[y * nx + x]);
+    double c = cost3(p, fN, g, uvw);
+    if (J) *J = c;
+    /* final condition: psi_Theta,i(T) = d I0 / d f_Theta,i */
+    for (size_t k = 0; k < nn; ++k)
+        for (int sp = 0; sp < 3; ++sp) {
+            double wseed = seeds ? seeds[sp * nn + k] : (sp == 0 ? uvw[k] - p->u_tgt[k] : 0.0);
+            for (int i = 0; i < Q; ++i) psi[(k * 3 + sp) * Q + i] = wseed;
+        }
+    if (dJdg) memset(dJdg, 0, sizeof(double) * nn * (size_t)N);
+    for (int n = N - 1; n >= 0; --n) {
+        stream3(&L, p, psi, rho, 1); /* streaming along -e_i, backward in time */
+        const double* f = traj + (size_t)n * npop;
+#pragma omp parallel for schedule(static)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                size_t k = (size_t)y * nx + x;
+                const node3_t* nd = &nodes[k];
+                const double* fk = f + k * 3 * Q;
+                const double* rk = rho + k * 3 * Q;
+                /* forward state at (x, n) */
+                double T[3] = {0, 0, 0}, j[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+                for (int sp = 0; sp < 3; ++sp)
+                    for (int i = 0; i < Q; ++i) {
+                        T[sp] += fk[sp * Q + i];
+                        j[sp][0] += L.e[i][0] * fk[sp * Q + i];
+                        j[sp][1] += L.e[i][1] * fk[sp * Q + i];
+                    }
+                const double* Ph = Phi_traj + ((size_t)n * nn + k) * 3;
+                double Gv[2], Gw[2];
+                grad3(p, nd->K[1], nd->a, T[1], j[1], Ph[1], Gv);
+                grad3(p, nd->K[2], nd->a, T[2], j[2], Ph[2], Gw);
+                /* transposed MRT collisions with the adjoint equilibrium broadcast */
+                double out[27], Pi[9][9], mt[9];
+                for (int sp = 0; sp < 3; ++sp) {
+                    Pi_rates(p->s, nd->K[sp], Pi);
+                    mrt_collide_T(&L, Pi, rk + sp * Q, mt);
+                    double Tcal = 0.0;
+                    for (int i = 0; i < Q; ++i) Tcal += L.w[i] * nd->aleph[sp][i] * mt[i];
+                    for (int i = 0; i < Q; ++i) out[sp * Q + i] = rk[sp * Q + i] - mt[i] + Tcal;
+                }
+                /* adjoint of tau S_u = (w_i/Cs^2) e_i . K_u F,  F = u (chi1 G_v + chi2 G_w) */
+                double Y[2] = {0.0, 0.0};
+                for (int i = 0; i < Q; ++i) {
+                    Y[0] += rk[i] * L.w[i] / CS2 * L.e[i][0];
+                    Y[1] += rk[i] * L.w[i] / CS2 * L.e[i][1];
+                }
+                double aF[2] = {nd->K[0][0][0] * Y[0] + nd->K[0][1][0] * Y[1], nd->K[0][0][1] * Y[0] + nd->K[0][1][1] * Y[1]};
+                double aT[3] = {0, 0, 0}, aPhi[3] = {0, 0, 0}, aj[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+                for (int c2 = 0; c2 < 2; ++c2) aT[0] += (p->chi1 * Gv[c2] + p->chi2 * Gw[c2]) * aF[c2];
+                double aG[3][2];
+                for (int c2 = 0; c2 < 2; ++c2) {
+                    aG[1][c2] = p->chi1 * T[0] * aF[c2];
+                    aG[2][c2] = p->chi2 * T[0] * aF[c2];
+                }
+                /* G_Theta = -(K (j - a T)/tau + K a Phi / 2) / (d Cs^2), Theta = v, w */
+                for (int sp = 1; sp < 3; ++sp) {
+                    double KtG[2] = {nd->K[sp][0][0] * aG[sp][0] + nd->K[sp][1][0] * aG[sp][1],
+                                     nd->K[sp][0][1] * aG[sp][0] + nd->K[sp][1][1] * aG[sp][1]};
+                    double sc = 1.0 / (p->d * CS2);
+                    aj[sp][0] = -KtG[0] * sc / p->tau;
+                    aj[sp][1] = -KtG[1] * sc / p->tau;
+                    aT[sp] += (nd->a[0] * KtG[0] + nd->a[1] * KtG[1]) * sc / p->tau;
+                    aPhi[sp] += -0.5 * (nd->a[0] * KtG[0] + nd->a[1] * KtG[1]) * sc;
+                }
+                /* sources w~ (c_n Phi^n + c'_n Phi^{n-1}) and the use of Phi^n at step n+1 */
+                for (int sp = 0; sp < 3; ++sp) {
+                    double sig = 0.0;
+                    for (int i = 0; i < Q; ++i) sig += rk[sp * Q + i] * nd->wt[sp][i];
+                    aPhi[sp] += c3_now(p, n) * sig;
+                    if (n + 1 <= N - 1) aPhi[sp] += c3_prev(p, n + 1) * sig_next[3 * k + sp];
+                    sig_now[3 * k + sp] = sig;
+                }
+                /* Phi_u = a1 u - a2 u^2, Phi_v = b1 u - b2 v - b3 u v (+ g), Phi_w = c1 u - c2 w (+ g) */
+                aT[0] += (p->a1 - 2.0 * p->a2 * T[0]) * aPhi[0] + (p->b1 - p->b3 * T[1]) * aPhi[1] + p->c1 * aPhi[2];
+                aT[1] += -(p->b2 + p->b3 * T[0]) * aPhi[1];
+                aT[2] += -p->c2 * aPhi[2];
+                if (dJdg) {
+                    double gv = g ? g[(size_t)n * nn + k] : 0.0;
+                    dJdg[(size_t)n * nn + k] = aPhi[p->ctrl_species] + 2.0 * p->alpha * gv;
+                }
+                for (int sp = 0; sp < 3; ++sp)
+                    for (int i = 0; i < Q; ++i)
+                        psi[(k * 3 + sp) * Q + i] =
+                            out[sp * Q + i] + aT[sp] + L.e[i][0] * aj[sp][0] + L.e[i][1] * aj[sp][1];
+            }
+        double* t = sig_next;
+        sig_next = sig_now;
+        sig_now = t;
+    }
+    if (psi0) memcpy(psi0, psi, sizeof(double) * npop);
+    free(traj); free(Phi_traj); free(fN); free(psi); free(rho); free(sig_next); free(sig_now); free(uvw); free(nodes);
+    return 0;
+}

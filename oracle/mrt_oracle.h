@@ -104,6 +104,42 @@ int or_adjoint(const or_problem* p, const double* g, const double* seed_u,
  * NULL). */
 int or_cadjoint(const or_problem* p, const double* g, double* dJdg, double* J);
 
+/* ---- three species: the attraction-repulsion chemotaxis model with a logistic
+ * source (the ARC example of Sec. 2.2 of the paper, a case of its
+ * three-equation system), D2Q9, periodic grid, control on the whole grid:
+ *   du/dt = div(D_u grad u) - div(a u) - div(chi1 u grad v) - div(chi2 u grad w) + a1 u - a2 u^2
+ *   dv/dt = div(D_v grad v) - div(a v) + b1 u - b2 v - b3 u v   (+ g if ctrl_species == 1)
+ *   dw/dt = div(D_w grad w) - div(a w) + c1 u - c2 w            (+ g if ctrl_species == 2)
+ *   J = 1/2 sum (u^N - u_tgt)^2 + alpha sum_{n<N} sum g^2.
+ * Populations [ny][nx][3][Q]; fields [3][ny][nx] (u, v, w); controls [N][ny][nx]. */
+typedef struct {
+    int nx, ny, N;
+    double tau;
+    const double* Du;            /* [ny][nx][3] */
+    const double* Dv;
+    const double* Dw;
+    double d;                    /* d_Theta of the equilibrium, all species */
+    const double* a;             /* [ny][nx][2] or NULL */
+    double chi1, chi2;           /* D_{u,1} = chi1 u I (toward v), D_{u,2} = chi2 u I (toward w) */
+    double a1, a2;               /* logistic source of u */
+    double b1, b2, b3;           /* kinetics of v */
+    double c1, c2;               /* kinetics of w */
+    int ctrl_species;            /* 1: g acts on v, 2: g acts on w */
+    const double* u_tgt;
+    double alpha;
+    double s[7];
+    int source_order;
+    const double* u0;
+    const double* v0;
+    const double* w0;
+} or3_problem;
+
+int or3_forward(const or3_problem* p, const double* g, double* J, double* uvwN);
+/* per step n: [n][6] = mass of u, v, w before collision, sum of Phi_u, Phi_v, Phi_w */
+int or3_forward_trace(const or3_problem* p, const double* g, double* trace);
+int or3_tlm(const or3_problem* p, const double* g, const double* dg, const double* df0, double* duvwN, double* dJ);
+int or3_adjoint(const or3_problem* p, const double* g, const double* seeds, double* dJdg, double* psi0, double* J);
+
 #ifdef __cplusplus
 }
 #endif
