@@ -96,13 +96,22 @@ __global__ void __launch_bounds__(NTHR) k_conv(const bf16* __restrict__ X, const
     const int nchunks = (IC + KC - 1) / KC;
     const bf16 zero = __float2bfloat16(0.0f);
     for (int c = 0; c < nchunks; ++c) {
-        for (int e = tid; e < KC * PP; e += NTHR) {
-            const int j = e / PP, r = e - j * PP;
+        // one thread per (8-channel group, patch position): eight loads, one 16-byte store
+        for (int e = tid; e < (KC / 8) * PP; e += NTHR) {
+            const int gq = e / PP, r = e - gq * PP;
             const int py = r / PW, px = r - py * PW;
-            const int ic = c * KC + j, y = y0 - OFF + py, x = x0 - OFF + px;
-            bf16 v = zero;
-            if (ic < IC && y >= 0 && y < H && x >= 0 && x < W) v = X[((size_t)b * IC + ic) * hw + (size_t)y * W + x];
-            Ps[r][j] = v;
+            const int y = y0 - OFF + py, x = x0 - OFF + px;
+            const bool inb = y >= 0 && y < H && x >= 0 && x < W;
+            const int ic0 = c * KC + gq * 8;
+            const bf16* src = X + ((size_t)b * IC + ic0) * hw + (size_t)(inb ? y : 0) * W + (inb ? x : 0);
+            uint32_t wv[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const bf16 lo = (inb && ic0 + 2 * q < IC) ? src[(size_t)(2 * q) * hw] : zero;
+                const bf16 hi = (inb && ic0 + 2 * q + 1 < IC) ? src[(size_t)(2 * q + 1) * hw] : zero;
+                wv[q] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+            }
+            *reinterpret_cast<uint4*>(&Ps[r][gq * 8]) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
         }
         for (int e = tid; e < TAPS * CT * 2; e += NTHR) {
             const int t = e / (CT * 2), rem = e - t * CT * 2, o = rem >> 1, h = rem & 1;
@@ -186,11 +195,20 @@ __global__ void __launch_bounds__(NTHR) k_wgrad(const bf16* __restrict__ X, cons
     for (int tile = t_beg; tile < t_end; ++tile) {
         const int b = tile / (tiles_x * tiles_y), bt = tile - b * tiles_x * tiles_y;
         const int y0 = (bt / tiles_x) * 8, x0 = (bt % tiles_x) * 8;
-        for (int e = tid; e < CT * 64; e += NTHR) {
-            const int o = e >> 6, p = e & 63, y = y0 + (p >> 3), x = x0 + (p & 7);
-            bf16 v = zero;
-            if (oc0 + o < OC && y < H && x < W) v = dY[((size_t)b * OC + oc0 + o) * hw + (size_t)y * W + x];
-            As[o][p] = v;
+        // dY tile: one 16-byte row of 8 pixels per (channel, tile row) when the row is whole and
+        // aligned (widths that are multiples of 8), else element by element
+        const bool rows16 = (W & 7) == 0 && x0 + 8 <= W && (reinterpret_cast<uintptr_t>(dY) & 15u) == 0;
+        for (int e = tid; e < CT * 8; e += NTHR) {
+            const int o = e >> 3, ry = e & 7, y = y0 + ry;
+            const bool ok = oc0 + o < OC && y < H;
+            const bf16* src = dY + ((size_t)b * OC + oc0 + o) * hw + (size_t)y * W + x0;
+            if (rows16) {
+                *reinterpret_cast<uint4*>(&As[o][ry * 8]) =
+                    ok ? *reinterpret_cast<const uint4*>(src) : make_uint4(0, 0, 0, 0);
+            } else {
+#pragma unroll
+                for (int px = 0; px < 8; ++px) As[o][ry * 8 + px] = (ok && x0 + px < W) ? src[px] : zero;
+            }
         }
         for (int e = tid; e < KC * PW * PW; e += NTHR) {
             const int j = e / (PW * PW), r = e - j * PW * PW, py = r / PW, px = r - py * PW;

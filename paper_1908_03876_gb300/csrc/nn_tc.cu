@@ -194,14 +194,24 @@ __global__ void __launch_bounds__(NTHR) k_conv_tc(const bf16* __restrict__ X, co
             bulk_copy(Bm, Wp + (size_t)c * TAPS * 2 * OC * 8, b_bytes, &lbar[buf]);
             ++n_copy[buf];
         }
-        // A: [ci/8][pos][8]
-        for (int e = tid; e < 16 * PP; e += NTHR) {
-            const int j = e / PP, r = e - j * PP;
+        // A: [ci/8][pos][8].  One thread per (8-channel group, patch position): eight
+        // loads from the channel planes (coalesced along x across the warp), one
+        // 16-byte store of the position's core-matrix row (no bank conflicts)
+        for (int e = tid; e < 2 * PP; e += NTHR) {
+            const int gq = e / PP, r = e - gq * PP;
             const int py = r / PW, px = r - py * PW;
-            const int ic = c * 16 + j, y = y0 - OFF + py, x = x0 - OFF + px;
-            bf16 v = zero;
-            if (ic < IC && y >= 0 && y < H && x >= 0 && x < W) v = X[((size_t)b * IC + ic) * hw + (size_t)y * W + x];
-            reinterpret_cast<bf16*>(A)[((j >> 3) * PP + r) * 8 + (j & 7)] = v;
+            const int y = y0 - OFF + py, x = x0 - OFF + px;
+            const bool inb = y >= 0 && y < H && x >= 0 && x < W;
+            const int ic0 = c * 16 + gq * 8;
+            const bf16* src = X + ((size_t)b * IC + ic0) * hw + (size_t)(inb ? y : 0) * W + (inb ? x : 0);
+            uint32_t wv[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const bf16 lo = (inb && ic0 + 2 * q < IC) ? src[(size_t)(2 * q) * hw] : zero;
+                const bf16 hi = (inb && ic0 + 2 * q + 1 < IC) ? src[(size_t)(2 * q + 1) * hw] : zero;
+                wv[q] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+            }
+            reinterpret_cast<uint4*>(A)[gq * PP + r] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
         }
         // B: [tap][ci/8][oc][8] (thread copies when the tile is a part of the output channels)
         if (!bulk)
