@@ -624,6 +624,106 @@ def run_fp64(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+# algorithmic bytes per node and step of the three-species kernels (FP32, D2Q9):
+#   forward   27 pulls + 27 stores (216) + angle (4) + g (4) + Phi in/out for 3 species (24) = 248
+#   recompute forward + tape (u, v, G_v, G_w) store (24)                                       = 272
+#   adjoint   216 + tape read (24) + angle (4) + sigma in/out (24) + g (4) + dJ/dg (4)         = 276
+BYTES3 = dict(forward=248, recompute=272, adjoint=276)
+
+
+def run_arc(args, rank, world, local):
+    """Three-species attraction-repulsion chemotaxis (logistic source) on the
+    1024x1024 D2Q9 FP32 lattice, 2000 steps, checkpoint every 100: gradient
+    evaluations (forward + recompute + exact discrete adjoint) with per-phase
+    kernel times and HBM fractions, FP32 error against the FP64 oracle on a
+    reduced-size run, and the CPU oracle on a bounded sample."""
+    import numpy as np
+    import torch
+
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1908_03876_gb300.build import build
+
+    build()
+    from paper_1908_03876_gb300 import workloads as W
+    from paper_1908_03876_gb300.arc import ArcProblem
+
+    nx = ny = 256 if args.profile else 1024
+    N, k = (20, 10) if args.profile else (2000, 100)
+    w = W.arc(nx, ny, N, seed=5, precision=32, ckpt_every=k)
+    p = ArcProblem(w, device=dev)
+    g = torch.as_tensor(w.random_control(100, 0.01), dtype=torch.float32, device=dev).contiguous()
+    E = torch.empty_like(g)
+    for _ in range(args.warmup):
+        p.gradient(g, out=E)
+    torch.cuda.synchronize()
+    if args.profile:
+        print(json.dumps({"profile": f"arc {nx}x{ny}, {N} steps: gradient evaluations"}))
+        return
+    clocks = Clocks()
+    clocks.start()
+    p.set_timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(p.stream)
+    for _ in range(args.steps):
+        p.gradient(g, out=E)
+    e1.record(p.stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop(local)
+    ms = e0.elapsed_time(e1) / args.steps
+    phases = p.timing()
+    p.set_timing(False)
+    J, gsq, _ = p.norms()
+    nodes = nx * ny
+    hbm, peak_kind = _peaks()
+    kern = {}
+    for ph in ("forward", "recompute", "adjoint"):
+        t, n = phases[ph]
+        if n > 0:
+            us = t * 1e3 / n
+            ach = BYTES3[ph] * nodes / (us * 1e-6) / 1e9
+            kern[ph] = {"us_per_launch": us, "achieved": ach, "frac": ach / hbm, "launches": n,
+                        "bytes_per_node": BYTES3[ph]}
+    dom = max(kern, key=lambda q: kern[q]["us_per_launch"] * kern[q]["launches"])
+    kname = {"forward": "k3_forward", "recompute": "k3_forward", "adjoint": "k3_adjoint"}[dom]
+    roof = {"bound": "hbm", "achieved": kern[dom]["achieved"], "peak": hbm, "unit": "GB/s",
+            "frac": kern[dom]["frac"], "traffic": _traffic(kname), "kernel": kname, "peak_source": peak_kind,
+            "bytes_per_launch": BYTES3[dom] * nodes}
+    # FP32 against the FP64 oracle at the same horizon on a 64x64 grid
+    err = None
+    try:
+        import oracle
+
+        oracle.build()
+        ws = W.arc(64, 64, N, seed=5, precision=32, ckpt_every=k)
+        ps = ArcProblem(ws, device=dev)
+        gs = ws.random_control(101, 0.01)
+        Js, Es = ps.gradient(gs)
+        fs = [t.cpu().numpy() for t in ps.fields()]
+        po = oracle.from_workload3(ws)
+        Jo, uvw = oracle.forward3(po, gs)
+        _, Eo, _ = oracle.adjoint3(po, gs)
+        rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+        err = {"grid": "64x64", "steps": N, "u": rel(fs[0], uvw[0]), "v": rel(fs[1], uvw[1]), "w": rel(fs[2], uvw[2]),
+               "dJdg": rel(Es.cpu().numpy(), Eo), "J": abs(float(Js.item()) - Jo) / abs(Jo)}
+        ps.close()
+    except Exception as exc:
+        err = {"error": str(exc)[:200]}
+    line = {"metric": "fwd+adjoint MLUPS (three species)", "value": nodes * N / (ms * 1e-3) / 1e6, "unit": "MLUPS",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "replicas only", "vs_baseline": None, "dtype": "f32 (FP64 reductions)",
+            "data": "synthetic (seeded)",
+            "config": {"workload": f"arc{nx}: {nx}x{ny} D2Q9 FP32, three species (attraction to v, repulsion "
+                                   f"from w, logistic growth), {N} steps, checkpoint every {k}",
+                       "step": "one gradient evaluation (forward + recompute + exact discrete adjoint)",
+                       "l2": "inputs larger than L2 (8.4 GB control per step)"},
+            "roofline": roof, "kernels": kern, "fp32_err_vs_oracle": err, "clocks": clk,
+            "gpu_launches": (3 * N - k + 3) * args.steps, "J": J, "grad_norm": float(np.sqrt(gsq))}
+    print(json.dumps(line), flush=True)
+
+
 def run_unet_layers(args, rank, world, local):
     """Forward time of each 3x3 layer shape of the 4-level U-Net at 128x128,
     batch 16, on the tcgen05 kernel and on the mma.sync kernel (same packed
@@ -688,7 +788,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="aniso1024",
-                    choices=["aniso1024", "batch", "warmstart", "cg", "unetlayers", "fp64", "geometry4096"],
+                    choices=["aniso1024", "batch", "warmstart", "cg", "unetlayers", "fp64", "geometry4096", "arc"],
                     help="aniso1024 (default bench line) or batch: 256 independent problems, sizes {64..512}^2, "
                          "1000 steps, one persistent launch per step replayed as a CUDA graph")
     ap.add_argument("--staging", default=None, choices=["rows", "thread"],
@@ -700,6 +800,8 @@ def main():
     ap.add_argument("--ws-train", type=int, default=2000)
     ap.add_argument("--ws-test", type=int, default=200)
     ap.add_argument("--ws-size", type=int, default=256)
+    ap.add_argument("--opt-iters", type=int, default=20,
+                    help="Armijo steepest-descent iterations of the default workload's optimisation leg (0: skip)")
     ap.add_argument("--ws-steps", type=int, default=256)
     ap.add_argument("--ws-epochs", type=int, default=40)
     ap.add_argument("--profile", action="store_true",
@@ -727,6 +829,9 @@ def main():
         return
     if args.workload == "fp64":
         return run_fp64(args, rank, world, local)
+    if args.workload == "arc":
+        run_arc(args, rank, world, local)
+        return
     if args.workload == "unetlayers":
         run_unet_layers(args, rank, world, local)
         return
@@ -892,6 +997,26 @@ def main():
         except Exception as exc:  # pinned memory can fail on small hosts
             e2e = {"value": None, "unit": "MLUPS", "error": str(exc)[:200]}
 
+    # ---- the optimisation leg of the same workload: plain steepest descent
+    # from g = 0 with the Armijo rule (one gradient and >= 1 trial forward
+    # solves per iteration), timed on the problem's stream
+    opt = None
+    if rank == 0 and not args.profile and args.opt_iters > 0:
+        g.zero_()
+        oa, ob = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        oa.record(stream)
+        its = [prob.step(g, E) for _ in range(args.opt_iters)]
+        ob.record(stream)
+        torch.cuda.synchronize()
+        trials = sum(it["trials"] for it in its)
+        sec = oa.elapsed_time(ob) * 1e-3
+        opt = {"iterations": len(its), "J0": its[0]["J0"], "J": its[-1]["J"],
+               "J_ratio": its[-1]["J"] / its[0]["J0"], "trial_forward_solves": trials,
+               "grad_norm_ratio": float(np.sqrt(its[-1]["grad_sq"] / its[0]["grad_sq"])),
+               "seconds": sec, "ms_per_iteration": sec * 1e3 / len(its),
+               "J_per_iteration": [it["J"] for it in its]}
+
     launches_per_step = 3 * w.N - wl["k"] + 3
     if rank == 0:
         cpu = None if args.no_cpu_baseline else cpu_baseline()
@@ -912,6 +1037,7 @@ def main():
             "cpu_baseline": cpu,
             "fp32_err_vs_oracle": fp32_err,
             "geometry4096": geom,
+            "optimise": opt,
             "clocks": clk,
             "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps,

@@ -527,3 +527,12 @@ def adjoint3(p: Problem3, g=None, seeds=None, want_psi0=False):
     _check(lib.or3_adjoint(ctypes.byref(st), _ptr(_f64(g)), _ptr(_f64(seeds)), _ptr(E), _ptr(psi0),
                            ctypes.byref(J)), "adjoint3")
     return J.value, E, psi0
+
+
+def from_workload3(w, N=None) -> Problem3:
+    """Three-species oracle problem from a seeded workload (per-node fields)."""
+    Du, Dv, Dw = w.D_fields()
+    return Problem3(nx=w.nx, ny=w.ny, N=w.N if N is None else N, Du=Du, Dv=Dv, Dw=Dw, u0=w.u0, v0=w.v0, w0=w.w0,
+                    u_tgt=w.u_tgt, d=w.d, a=w.a_fields(), chi1=w.chi1, chi2=w.chi2, a1=w.a1, a2=w.a2, b1=w.b1,
+                    b2=w.b2, b3=w.b3, c1=w.c1, c2=w.c2, ctrl_species=w.ctrl_species, alpha=w.alpha,
+                    s=tuple(w.s), source_order=w.source_order)

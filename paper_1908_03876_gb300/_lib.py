@@ -1,4 +1,5 @@
-"""ctypes view of the C ABI in include/cxlbm.h (argument marshalling only).
+"""ctypes view of the C ABI in include/cxlbm.h and include/cxarc.h (argument
+marshalling only).
 
 Loading fails loudly if libcxlbm.so is missing: there is no fallback path.
 """
@@ -38,6 +39,9 @@ EXPORTS = [
     "cx_nn_conv_backward_weight", "cx_nn_relu_backward", "cx_nn_add", "cx_nn_pool2", "cx_nn_up2", "cx_nn_mse",
     "cx_nn_adam", "cx_nn_cast_bf16", "cx_nn_conv_forward_f32", "cx_nn_smooth", "cx_nn_packed_weights",
     "cx_nn_pack_weights", "cx_nn_conv_tc_tile", "cx_nn_conv_forward_tc",
+    # include/cxarc.h (three species)
+    "cx3_workspace_size", "cx3_create", "cx3_set_initial", "cx3_forward", "cx3_adjoint", "cx3_gradient",
+    "cx3_step", "cx3_get_fields", "cx3_get_norms", "cx3_set_timing", "cx3_get_timing", "cx3_destroy",
 ]
 STATIC_SCRATCH_BYTES = 64 << 20  # CX_STATIC_SCRATCH_BYTES of include/cxlbm.h
 
@@ -70,6 +74,25 @@ class Desc(ctypes.Structure):
     ]
 
 
+class Desc3(ctypes.Structure):
+    """cx3_desc of include/cxarc.h."""
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("n_steps", ctypes.c_int), ("precision", ctypes.c_int),
+        ("ckpt_every", ctypes.c_int), ("tau", ctypes.c_double), ("aniso", ctypes.c_int),
+        ("D_u", ctypes.c_double * 3), ("D_v", ctypes.c_double * 3), ("D_w", ctypes.c_double * 3),
+        ("lam_u", ctypes.c_double * 2), ("lam_v", ctypes.c_double * 2), ("lam_w", ctypes.c_double * 2),
+        ("theta", ctypes.c_void_p), ("D_u_field", ctypes.c_void_p), ("D_v_field", ctypes.c_void_p),
+        ("D_w_field", ctypes.c_void_p),
+        ("d", ctypes.c_double), ("chi1", ctypes.c_double), ("chi2", ctypes.c_double),
+        ("a1", ctypes.c_double), ("a2", ctypes.c_double),
+        ("b1", ctypes.c_double), ("b2", ctypes.c_double), ("b3", ctypes.c_double),
+        ("c1", ctypes.c_double), ("c2", ctypes.c_double),
+        ("ctrl_species", ctypes.c_int), ("adv", ctypes.c_int), ("a", ctypes.c_void_p),
+        ("u_target", ctypes.c_void_p), ("alpha", ctypes.c_double), ("s", ctypes.c_double * 7),
+        ("source_order", ctypes.c_int),
+    ]
+
+
 class CGInfo(ctypes.Structure):
     _fields_ = [("J0", ctypes.c_double), ("J", ctypes.c_double), ("lam", ctypes.c_double),
                 ("grad_sq", ctypes.c_double), ("beta", ctypes.c_double), ("trials", ctypes.c_int),
@@ -99,6 +122,7 @@ def load():
     lib = ctypes.CDLL(LIB_PATH)
     vp, cint, dp = ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)
     D = ctypes.POINTER(Desc)
+    D3 = ctypes.POINTER(Desc3)
     sig = {
         "cx_workspace_size": [D, ctypes.POINTER(ctypes.c_size_t)],
         "cx_create": [D, vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)],
@@ -160,6 +184,18 @@ def load():
         "cx_nn_adam": [vp, vp, vp, vp, vp, ctypes.c_size_t, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                        ctypes.c_float, cint, vp],
         "cx_nn_cast_bf16": [vp, vp, ctypes.c_size_t, vp],
+        "cx3_workspace_size": [D3, ctypes.POINTER(ctypes.c_size_t)],
+        "cx3_create": [D3, vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)],
+        "cx3_set_initial": [vp, vp, vp, vp],
+        "cx3_forward": [vp, vp, vp],
+        "cx3_adjoint": [vp, vp, vp, vp, vp, cint, vp],
+        "cx3_gradient": [vp, vp, vp, vp],
+        "cx3_step": [vp, vp, vp, ctypes.POINTER(StepInfo)],
+        "cx3_get_fields": [vp, vp, vp, vp],
+        "cx3_get_norms": [vp, dp, dp, dp],
+        "cx3_set_timing": [vp, cint],
+        "cx3_get_timing": [vp, dp, ctypes.POINTER(ctypes.c_longlong)],
+        "cx3_destroy": [vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)

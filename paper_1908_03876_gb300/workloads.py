@@ -234,3 +234,97 @@ def batch_workloads(n_problems=256, N=1000, seed=3, sizes=(64, 128, 256, 512), c
                             u0=u0, v0=np.zeros((ny, nx)), u_tgt=u_tgt, alpha=1e-3, ckpt_every=ckpt_every,
                             extra=dict(ratio=ratio, angle=ang)))
     return out
+
+
+@dataclass
+class Workload3:
+    """Three-species (attraction-repulsion chemotaxis, logistic source) input
+    set: the same tensor/convection vocabulary as ``Workload`` with a third
+    species w, the kinetics coefficients and the controlled species."""
+    name: str
+    nx: int
+    ny: int
+    N: int
+    precision: int = 64
+    aniso: str = "rotated"
+    D_u_const: tuple = (0.05, 0.0, 0.05)
+    D_v_const: tuple = (0.2, 0.0, 0.2)
+    D_w_const: tuple = (0.15, 0.0, 0.15)
+    lam_u: tuple = (0.08, 0.02)
+    lam_v: tuple = (0.2, 0.1)
+    lam_w: tuple = (0.15, 0.05)
+    theta: np.ndarray | None = None
+    D_u_field: np.ndarray | None = None
+    D_v_field: np.ndarray | None = None
+    D_w_field: np.ndarray | None = None
+    d: float = 1.0
+    chi1: float = -0.1
+    chi2: float = 0.08
+    a1: float = 0.0
+    a2: float = 0.0
+    b1: float = 0.0
+    b2: float = 0.0
+    b3: float = 0.0
+    c1: float = 0.0
+    c2: float = 0.0
+    ctrl_species: int = 2
+    adv: str = "none"
+    a_row: np.ndarray | None = None
+    a_field: np.ndarray | None = None
+    u0: np.ndarray = None
+    v0: np.ndarray = None
+    w0: np.ndarray = None
+    u_tgt: np.ndarray = None
+    alpha: float = 1e-3
+    s: tuple = (1.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0)
+    source_order: int = 2
+    ckpt_every: int = 0
+
+    @property
+    def ctrl_shape(self):
+        return (self.N, self.ny, self.nx)
+
+    def D_fields(self):
+        """Per-node (Dxx, Dxy, Dyy) of u, v, w, [ny, nx, 3] each."""
+        if self.aniso == "field":
+            return self.D_u_field, self.D_v_field, self.D_w_field
+        if self.aniso == "const":
+            return tuple(np.broadcast_to(np.asarray(c, float), (self.ny, self.nx, 3)).copy()
+                         for c in (self.D_u_const, self.D_v_const, self.D_w_const))
+        return tuple(rotated_tensor(l, self.theta) for l in (self.lam_u, self.lam_v, self.lam_w))
+
+    def a_fields(self):
+        if self.adv == "none":
+            return None
+        if self.adv == "row":
+            return np.broadcast_to(self.a_row[:, None, :], (self.ny, self.nx, 2)).copy()
+        return self.a_field
+
+    def random_control(self, seed: int, scale: float = 0.01):
+        return scale * np.random.default_rng(seed).standard_normal(self.ctrl_shape)
+
+
+def arc(nx=1024, ny=1024, N=2000, seed=5, precision=32, ckpt_every=100, ctrl_species=2):
+    """Attraction-repulsion chemotaxis with a logistic source (D2Q9): rotated
+    anisotropic tensors for the three species along one seeded angle field,
+    shear convection a = (0.05 sin(2 pi y / L), 0), attraction toward v
+    (chi1 = -0.1), repulsion from w (chi2 = 0.08), logistic growth of u,
+    nonlinear consumption of v; u0 four seeded bumps on 1, v0 and w0 smooth
+    seeded fields, u_target one centred bump.  Rates are per lattice step."""
+    rng = np.random.default_rng(seed)
+    theta = _angle_field(nx, ny, seed)
+    y = np.arange(ny)
+    a_row = np.stack([0.05 * np.sin(2 * np.pi * y / ny), np.zeros(ny)], axis=-1)
+    sig = nx / 16.0
+    u0 = bumps(nx, ny, seed, sig)
+    x = np.arange(nx)[None, :]
+    yy = np.arange(ny)[:, None]
+    p = rng.uniform(0, 2 * np.pi, 3)
+    v0 = 0.5 + 0.1 * np.sin(2 * np.pi * (x / nx + yy / ny) + p[0])
+    w0 = 0.4 + 0.1 * np.cos(2 * np.pi * 2 * x / nx + p[1]) * np.cos(2 * np.pi * yy / ny + p[2])
+    u_tgt = 1.0 + 0.2 * _periodic_gauss(nx, ny, nx / 2, ny / 2, 2 * sig)
+    return Workload3(name="arc", nx=nx, ny=ny, N=N, precision=precision, aniso="rotated", theta=theta,
+                     lam_u=(0.08, 0.02), lam_v=(0.2, 0.1), lam_w=(0.15, 0.05), chi1=-0.1, chi2=0.08,
+                     a1=1e-3, a2=5e-4, b1=1e-3, b2=2e-3, b3=5e-4, c1=1e-3, c2=3e-3, ctrl_species=ctrl_species,
+                     adv="row", a_row=a_row, u0=u0, v0=v0, w0=np.broadcast_to(w0, (ny, nx)).copy(), u_tgt=u_tgt,
+                     alpha=1e-3, ckpt_every=ckpt_every)

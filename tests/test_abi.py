@@ -22,9 +22,13 @@ def lib():
 
 
 def _header_symbols():
-    with open(os.path.join(ROOT, "include", "cxlbm.h")) as fh:
-        text = fh.read()
-    return sorted(set(re.findall(r"^(?:cx_status|const char\*|size_t|int)\s+(cx_\w+)\s*\(", text, flags=re.M)))
+    syms = set()
+    for name in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if name.endswith(".h"):
+            with open(os.path.join(ROOT, "include", name)) as fh:
+                text = fh.read()
+            syms |= set(re.findall(r"^(?:cx_status|const char\*|size_t|int)\s+(cx\w*_\w+)\s*\(", text, flags=re.M))
+    return sorted(syms)
 
 
 def test_exports_every_declared_symbol(lib):
@@ -111,3 +115,61 @@ def test_batch_descriptors_must_share_schedule(lib):
         bad = (mod.Desc * 2)(_desc(mod), _desc(mod, **kw))
         assert so.cx_batch_workspace_size(bad, 2, ctypes.byref(n)) == 1, kw
     assert so.cx_batch_workspace_size(d, 0, ctypes.byref(n)) == 1
+
+
+def test_arc_desc_layout_matches_header(lib, tmp_path):
+    """ctypes Desc3 layout equals cx3_desc compiled from include/cxarc.h."""
+    so, mod = lib
+    fields = [f for f, _ in mod.Desc3._fields_]
+    src = tmp_path / "layout3.c"
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "cxarc.h"', "int main(void){",
+             'printf("%zu\\n", sizeof(cx3_desc));']
+    lines += [f'printf("%zu\\n", offsetof(cx3_desc, {f}));' for f in fields]
+    lines += ["return 0;}"]
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout3"
+    import subprocess
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    out = subprocess.check_output([str(exe)]).decode().split()
+    assert int(out[0]) == ctypes.sizeof(mod.Desc3)
+    for f, off in zip(fields, out[1:]):
+        assert getattr(mod.Desc3, f).offset == int(off), f
+
+
+def _desc3(mod, **kw):
+    d = mod.Desc3()
+    d.nx, d.ny, d.n_steps, d.precision, d.ckpt_every = 40, 24, 12, 32, 5
+    d.tau, d.d = 1.0, 1.0
+    d.D_u = (ctypes.c_double * 3)(0.05, 0.0, 0.05)
+    d.D_v = (ctypes.c_double * 3)(0.2, 0.0, 0.2)
+    d.D_w = (ctypes.c_double * 3)(0.1, 0.0, 0.1)
+    d.u_target = ctypes.c_void_p(0x1000)
+    d.s = (ctypes.c_double * 7)(*([1.0] * 7))
+    d.source_order = 2
+    d.ctrl_species = 2
+    for k, v in kw.items():
+        setattr(d, k, v)
+    return d
+
+
+def test_arc_workspace_size_and_validation(lib):
+    so, mod = lib
+    n = ctypes.c_size_t(0)
+    assert so.cx3_workspace_size(ctypes.byref(_desc3(mod)), ctypes.byref(n)) == 0
+    plane = 40 * 24 + 24  # rounded up to 64
+    # at least: 4 population buffers of 27 planes, 3 checkpoint slots of 30 planes, 5 tape steps of 6 planes
+    assert n.value >= (4 * 27 + 3 * 30 + 5 * 6) * plane * 4
+    n64 = ctypes.c_size_t(0)
+    assert so.cx3_workspace_size(ctypes.byref(_desc3(mod, precision=64)), ctypes.byref(n64)) == 0
+    assert n64.value > n.value
+    bad = [dict(precision=16), dict(nx=2), dict(n_steps=0), dict(d=0.0), dict(source_order=3), dict(aniso=1),
+           dict(aniso=2), dict(adv=1), dict(ctrl_species=0), dict(ctrl_species=3), dict(alpha=-1.0),
+           dict(u_target=None), dict(chi1=float("nan")), dict(ckpt_every=-1)]
+    for kw in bad:
+        assert so.cx3_workspace_size(ctypes.byref(_desc3(mod, **kw)), ctypes.byref(n)) == 1, kw
+    d = _desc3(mod)
+    d.s[2] = 2.0
+    assert so.cx3_workspace_size(ctypes.byref(d), ctypes.byref(n)) == 1
+    h = ctypes.c_void_p()
+    assert so.cx3_create(ctypes.byref(_desc3(mod)), ctypes.c_void_p(0x1001), 1 << 30, None, ctypes.byref(h)) == 2
+    assert so.cx3_create(ctypes.byref(_desc3(mod)), ctypes.c_void_p(0x1000), 16, None, ctypes.byref(h)) == 2
