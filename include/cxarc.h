@@ -8,8 +8,8 @@
  *     dw/dt = div(D_w grad w) - div(a w) + c1 u - c2 w           [+ g]
  *
  * with the distributed control g acting on v (ctrl_species = 1) or on w
- * (ctrl_species = 2).  chi1 < 0 attracts the cells toward v, chi2 > 0 repels
- * them from w.
+ * (ctrl_species = 2).  The cell flux holds + chi1 u grad v + chi2 u grad w, so
+ * chi1 > 0 attracts the cells toward v and chi2 < 0 repels them from w.
  *
  * Discrete problem (Sec. 3.1 and 3.2), the two-species scheme of cxlbm.h
  * widened to three species on D2Q9:
@@ -135,6 +135,19 @@ cx_status cx3_get_fields(cx3_problem* p, void* u_out, void* v_out, void* w_out);
  * any may be NULL); synchronises.  Errors: CX_ERR_UNSTABLE (a non-finite
  * cost or gradient was recorded), CX_ERR_CUDA. */
 cx_status cx3_get_norms(cx3_problem* p, double* J, double* grad_sq, double* grad_inf);
+
+/* Staging of the lattice kernels: 1 (default) runs the forward steps whose
+ * inputs are all pulled (n >= 1) in the row-window kernel -- a producer warp
+ * stages row segments by bulk asynchronous copies completed on mbarriers --
+ * when rows are a whole number of 16-byte units, the planes 16-byte aligned
+ * and the grid has at least two row segments per block; 0 uses the
+ * per-thread kernels everywhere; 2 takes the row-window kernels for every
+ * eligible forward and adjoint step (adjoint: below the terminal one)
+ * whatever the grid size (tests; the adjoint's row-window form measured
+ * slower).  Results agree to rounding.  A bounded wait of the pipeline that
+ * runs out is reported as CX_ERR_TIMEOUT by cx3_step / cx3_get_norms.
+ * Errors: CX_ERR_INVALID_ARG. */
+cx_status cx3_set_staging(cx3_problem* p, int mode);
 
 /* Per-phase device time (forward, recompute, adjoint: ms[3], launches[3])
  * accumulated while timing is enabled (events on the problem's stream).

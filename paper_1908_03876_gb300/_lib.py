@@ -41,7 +41,8 @@ EXPORTS = [
     "cx_nn_pack_weights", "cx_nn_conv_tc_tile", "cx_nn_conv_forward_tc",
     # include/cxarc.h (three species)
     "cx3_workspace_size", "cx3_create", "cx3_set_initial", "cx3_forward", "cx3_adjoint", "cx3_gradient",
-    "cx3_step", "cx3_get_fields", "cx3_get_norms", "cx3_set_timing", "cx3_get_timing", "cx3_destroy",
+    "cx3_step", "cx3_get_fields", "cx3_get_norms", "cx3_set_staging", "cx3_set_timing", "cx3_get_timing",
+    "cx3_destroy",
 ]
 STATIC_SCRATCH_BYTES = 64 << 20  # CX_STATIC_SCRATCH_BYTES of include/cxlbm.h
 
@@ -193,6 +194,7 @@ def load():
         "cx3_step": [vp, vp, vp, ctypes.POINTER(StepInfo)],
         "cx3_get_fields": [vp, vp, vp, vp],
         "cx3_get_norms": [vp, dp, dp, dp],
+        "cx3_set_staging": [vp, cint],
         "cx3_set_timing": [vp, cint],
         "cx3_get_timing": [vp, dp, ctypes.POINTER(ctypes.c_longlong)],
         "cx3_destroy": [vp],

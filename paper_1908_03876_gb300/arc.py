@@ -154,6 +154,12 @@ class ArcProblem:
                    "cx3_get_norms")
         return J.value, e2.value, einf.value
 
+    def set_staging(self, mode=1):
+        """1: the forward in the row-window kernel where it pays (default);
+        0: per-thread kernels only; 2: row-window forward and adjoint for
+        every eligible step (tests)."""
+        _lib.check(self.lib.cx3_set_staging(self.h, int(mode)), "cx3_set_staging")
+
     def set_timing(self, on=True):
         _lib.check(self.lib.cx3_set_timing(self.h, 1 if on else 0), "cx3_set_timing")
 

@@ -37,6 +37,7 @@
 
 #include "../../include/cxarc.h"
 #include "cx_device.cuh"
+#include "cx_rows.cuh"
 
 namespace cx {
 namespace arc {
@@ -72,10 +73,10 @@ template <typename T> struct Coef3 {
 template <typename T> __device__ __forceinline__ T ld(const T* p) { return __ldg(p); }
 
 template <typename T>
-__device__ __forceinline__ void coef3(const AC& C, const AK<T>& KC, int y, int k, Coef3<T>& c) {
+__device__ __forceinline__ void coef3_th(const AC& C, const AK<T>& KC, int y, int k, T th, Coef3<T>& c) {
     if (C.aniso == CX_ANISO_ROTATED) {
         T s2, c2;
-        sincos2(ld(reinterpret_cast<const T*>(C.theta) + k), &s2, &c2);
+        sincos2(th, &s2, &c2);
 #pragma unroll
         for (int sp = 0; sp < 3; ++sp) {
             c.K[sp][0] = KC.kbar[sp] + KC.kd[sp] * c2;
@@ -104,6 +105,11 @@ __device__ __forceinline__ void coef3(const AC& C, const AK<T>& KC, int y, int k
         c.ax = T(0);
         c.ay = T(0);
     }
+}
+
+template <typename T>
+__device__ __forceinline__ void coef3(const AC& C, const AK<T>& KC, int y, int k, Coef3<T>& c) {
+    coef3_th<T>(C, KC, y, k, C.aniso == CX_ANISO_ROTATED ? ld(reinterpret_cast<const T*>(C.theta) + k) : T(0), c);
 }
 
 // N^-1 Pi dm (Pi^T N^-1 has the same entries: K symmetric, equal flux-row norms)
@@ -155,97 +161,87 @@ template <typename T> struct F3Args {
     T lam;
     T* tape;          // [6][plane] (u, v, G_v, G_w) or null
     double* gsq_part; // per-warp partials of sum (g^n)^2, or null
+    int* status;      // status word (ST_TIMEOUT from the row-window kernels)
     int n;
 };
 
-template <typename T>
-__global__ void __launch_bounds__(256) k3_forward(const AC C, const AK<T> KC, const F3Args<T> A) {
-    const size_t pl = (size_t)C.plane;
-    const int total = C.nx * C.ny;
-    typename SqAccT<T>::type acc;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
-        const int y = k / C.nx, x = k - y * C.nx;
-        T f[3][9];
-        if (A.n == 0) {
-#pragma unroll
-            for (int s = 0; s < 3; ++s)
-#pragma unroll
-                for (int i = 0; i < 9; ++i) f[s][i] = ld(A.in + (s * 9 + i) * pl + k);
-        } else {
-            const int xm = x == 0 ? C.nx - 1 : x - 1, xp = x == C.nx - 1 ? 0 : x + 1;
-            const int rm = (y == 0 ? C.ny - 1 : y - 1) * C.nx, r0 = y * C.nx;
-            const int rp = (y == C.ny - 1 ? 0 : y + 1) * C.nx;
-#pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                const int xs = L9::ex(i) > 0 ? xm : (L9::ex(i) < 0 ? xp : x);
-                const int ks = (L9::ey(i) > 0 ? rm : (L9::ey(i) < 0 ? rp : r0)) + xs;
-#pragma unroll
-                for (int s = 0; s < 3; ++s) f[s][i] = ld(A.in + (s * 9 + i) * pl + ks);
-            }
-        }
-        T g = T(0);
-        if (A.g) g = ld(A.g + k);
-        if (A.E) g = fma(-A.lam, ld(A.E + k), g); // same rounding as the accepted update
-        if (A.gsq_part) acc.add(g);
-        Coef3<T> nc;
-        coef3<T>(C, KC, y, k, nc);
+// ------------------------------------------------------------ node bodies
+// The forward and adjoint node bodies read their inputs through a source
+// object: global memory (per-thread kernels) or a staged row window.
 
-        T m[3][9];
+template <typename T, typename Src>
+__device__ __forceinline__ void fwd3_body(const AC& C, const AK<T>& KC, const F3Args<T>& A, int y, int k,
+                                          const Src& S, typename SqAccT<T>::type& acc) {
+    const size_t pl = (size_t)C.plane;
+    T f[3][9];
 #pragma unroll
-        for (int s = 0; s < 3; ++s) Transform<T, 9>::moments(f[s], m[s]);
-        const T Tu = m[0][0], Tv = m[1][0], Tw = m[2][0];
-        T Phi[3];
-        Phi[0] = KC.a1 * Tu - KC.a2 * Tu * Tu;
-        Phi[1] = KC.b1 * Tu - KC.b2 * Tv - KC.b3 * Tu * Tv + (C.ctrl == 1 ? g : T(0));
-        Phi[2] = KC.c1 * Tu - KC.c2 * Tw + (C.ctrl == 2 ? g : T(0));
-        T src[3];
+    for (int s = 0; s < 3; ++s)
 #pragma unroll
-        for (int s = 0; s < 3; ++s) {
-            const T prev = A.n == 0 ? Phi[s] : A.phi[s * pl + k];
-            src[s] = A.n == 0 ? KC.c_first * Phi[s] : KC.c_now * Phi[s] + KC.c_prev * prev;
-        }
-        // local gradients of v and w
-        T G[2][2];
+        for (int i = 0; i < 9; ++i) f[s][i] = S.pop(s, i);
+    T prev[3];
+    if (A.n > 0) {
 #pragma unroll
-        for (int s = 1; s < 3; ++s) {
-            const T* K = nc.K[s];
-            const T Th = m[s][0];
-            const T rx = (m[s][L9::JX] - nc.ax * Th) * KC.inv_tau, ry = (m[s][L9::JY] - nc.ay * Th) * KC.inv_tau;
-            const T Kax = K[0] * nc.ax + K[1] * nc.ay, Kay = K[1] * nc.ax + K[2] * nc.ay;
-            G[s - 1][0] = KC.gsc * (K[0] * rx + K[1] * ry + T(0.5) * Kax * Phi[s]);
-            G[s - 1][1] = KC.gsc * (K[1] * rx + K[2] * ry + T(0.5) * Kay * Phi[s]);
-        }
-        T mh[9];
-        meq_unit<T, 9>(nc.ax, nc.ay, KC.d, mh);
-#pragma unroll
-        for (int s = 0; s < 3; ++s) {
-            const T(&K)[3] = nc.K[s];
-            const T Vx = nc.ax - T(0.5) * (K[0] * nc.ax + K[1] * nc.ay);
-            const T Vy = nc.ay - T(0.5) * (K[1] * nc.ax + K[2] * nc.ay);
-            T Bx = T(3) * src[s] * Vx, By = T(3) * src[s] * Vy;
-            if (s == 0) { // tau S_u = 3 w_i e_i . K_u F,  F = u (chi1 G_v + chi2 G_w)
-                const T Fx = Tu * (KC.chi1 * G[0][0] + KC.chi2 * G[1][0]);
-                const T Fy = Tu * (KC.chi1 * G[0][1] + KC.chi2 * G[1][1]);
-                Bx += T(3) * (K[0] * Fx + K[1] * Fy);
-                By += T(3) * (K[1] * Fx + K[2] * Fy);
-            }
-            collide_write<T>(KC, f[s], m[s], mh, K, src[s], Bx, By, A.out + (size_t)s * 9 * pl, pl, k);
-        }
-#pragma unroll
-        for (int s = 0; s < 3; ++s) {
-            A.phi[s * pl + k] = Phi[s];
-            if (A.phi_ckpt) A.phi_ckpt[s * pl + k] = Phi[s];
-        }
-        if (A.tape) {
-            A.tape[k] = Tu;
-            A.tape[pl + k] = Tv;
-            A.tape[2 * pl + k] = G[0][0];
-            A.tape[3 * pl + k] = G[0][1];
-            A.tape[4 * pl + k] = G[1][0];
-            A.tape[5 * pl + k] = G[1][1];
-        }
+        for (int s = 0; s < 3; ++s) prev[s] = S.phi(s);
     }
-    if (A.gsq_part) acc.flush(A.gsq_part + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5), nullptr);
+    T g = T(0);
+    if (A.g) g = S.g();
+    if (A.E) g = fma(-A.lam, S.E(), g); // same rounding as the accepted update
+    if (A.gsq_part) acc.add(g);
+    Coef3<T> nc;
+    coef3_th<T>(C, KC, y, k, C.aniso == CX_ANISO_ROTATED ? S.theta() : T(0), nc);
+
+    T m[3][9];
+#pragma unroll
+    for (int s = 0; s < 3; ++s) Transform<T, 9>::moments(f[s], m[s]);
+    const T Tu = m[0][0], Tv = m[1][0], Tw = m[2][0];
+    T Phi[3];
+    Phi[0] = KC.a1 * Tu - KC.a2 * Tu * Tu;
+    Phi[1] = KC.b1 * Tu - KC.b2 * Tv - KC.b3 * Tu * Tv + (C.ctrl == 1 ? g : T(0));
+    Phi[2] = KC.c1 * Tu - KC.c2 * Tw + (C.ctrl == 2 ? g : T(0));
+    T src[3];
+#pragma unroll
+    for (int s = 0; s < 3; ++s)
+        src[s] = A.n == 0 ? KC.c_first * Phi[s] : KC.c_now * Phi[s] + KC.c_prev * prev[s];
+    // local gradients of v and w
+    T G[2][2];
+#pragma unroll
+    for (int s = 1; s < 3; ++s) {
+        const T* K = nc.K[s];
+        const T Th = m[s][0];
+        const T rx = (m[s][L9::JX] - nc.ax * Th) * KC.inv_tau, ry = (m[s][L9::JY] - nc.ay * Th) * KC.inv_tau;
+        const T Kax = K[0] * nc.ax + K[1] * nc.ay, Kay = K[1] * nc.ax + K[2] * nc.ay;
+        G[s - 1][0] = KC.gsc * (K[0] * rx + K[1] * ry + T(0.5) * Kax * Phi[s]);
+        G[s - 1][1] = KC.gsc * (K[1] * rx + K[2] * ry + T(0.5) * Kay * Phi[s]);
+    }
+    T mh[9];
+    meq_unit<T, 9>(nc.ax, nc.ay, KC.d, mh);
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        const T(&K)[3] = nc.K[s];
+        const T Vx = nc.ax - T(0.5) * (K[0] * nc.ax + K[1] * nc.ay);
+        const T Vy = nc.ay - T(0.5) * (K[1] * nc.ax + K[2] * nc.ay);
+        T Bx = T(3) * src[s] * Vx, By = T(3) * src[s] * Vy;
+        if (s == 0) { // tau S_u = 3 w_i e_i . K_u F,  F = u (chi1 G_v + chi2 G_w)
+            const T Fx = Tu * (KC.chi1 * G[0][0] + KC.chi2 * G[1][0]);
+            const T Fy = Tu * (KC.chi1 * G[0][1] + KC.chi2 * G[1][1]);
+            Bx += T(3) * (K[0] * Fx + K[1] * Fy);
+            By += T(3) * (K[1] * Fx + K[2] * Fy);
+        }
+        collide_write<T>(KC, f[s], m[s], mh, K, src[s], Bx, By, A.out + (size_t)s * 9 * pl, pl, k);
+    }
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        A.phi[s * pl + k] = Phi[s];
+        if (A.phi_ckpt) A.phi_ckpt[s * pl + k] = Phi[s];
+    }
+    if (A.tape) {
+        A.tape[k] = Tu;
+        A.tape[pl + k] = Tv;
+        A.tape[2 * pl + k] = G[0][0];
+        A.tape[3 * pl + k] = G[0][1];
+        A.tape[4 * pl + k] = G[1][0];
+        A.tape[5 * pl + k] = G[1][1];
+    }
 }
 
 template <typename T> struct A3Args {
@@ -258,13 +254,184 @@ template <typename T> struct A3Args {
     T* dJdg;           // [ny*nx] gradient of step n
     double* e2_part;   // per-warp partials of sum E^2 and max |E| (accumulated over steps)
     double* emax_part;
+    int* status;       // status word (ST_TIMEOUT from the row-window kernels)
     int n, terminal;
 };
 
-template <typename T>
-__global__ void __launch_bounds__(256) k3_adjoint(const AC C, const AK<T> KC, const A3Args<T> A) {
+template <typename T, typename Src>
+__device__ __forceinline__ void adj3_body(const AC& C, const AK<T>& KC, const A3Args<T>& A, int y, int k,
+                                          const Src& S, typename SqAccT<T>::type& acc) {
     constexpr bool fold = sizeof(T) == 4;
     const size_t pl = (size_t)C.plane;
+    T r[3][9];
+#pragma unroll
+    for (int s = 0; s < 3; ++s)
+#pragma unroll
+        for (int i = 0; i < 9; ++i) r[s][i] = S.pop(s, i);
+    const T Tu = S.tape(0), Tv = S.tape(1);
+    const T Gv[2] = {S.tape(2), S.tape(3)};
+    const T Gw[2] = {S.tape(4), S.tape(5)};
+    const T gv = A.g ? S.g() : T(0);
+    // sigma^{n+1}: read with the other inputs, before this node's stores
+    // (which the compiler cannot prove disjoint from it)
+    T sig_next[3] = {T(0), T(0), T(0)};
+    if (!A.terminal) {
+#pragma unroll
+        for (int s = 0; s < 3; ++s) sig_next[s] = S.sig(s);
+    }
+    Coef3<T> nc;
+    coef3_th<T>(C, KC, y, k, C.aniso == CX_ANISO_ROTATED ? S.theta() : T(0), nc);
+    T mh[9];
+    meq_unit<T, 9>(nc.ax, nc.ay, KC.d, mh);
+
+    // transposed collisions, sigma per species, Y = sum_i 3 w_i e_i rho_u,i
+    T ps[3][9], sigma[3], Yx = T(0), Yy = T(0);
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        const T(&K)[3] = nc.K[s];
+        const T Vx = nc.ax - T(0.5) * (K[0] * nc.ax + K[1] * nc.ay);
+        const T Vy = nc.ay - T(0.5) * (K[1] * nc.ax + K[2] * nc.ay);
+        T mom[9], z[9], mt[9];
+        Transform<T, 9>::moments(r[s], mom);
+        if constexpr (fold) {
+            T sA = T(0), sBx = T(0), sBy = T(0);
+#pragma unroll
+            for (int q = 0; q < 9; ++q) {
+                if (L9::src_A(q) != 0.0) sA += T(L9::inv_n(q) * L9::src_A(q)) * mom[q];
+                if (L9::src_Bx(q) != 0.0) sBx += T(3.0 * L9::inv_n(q) * L9::src_Bx(q)) * mom[q];
+                if (L9::src_By(q) != 0.0) sBy += T(3.0 * L9::inv_n(q) * L9::src_By(q)) * mom[q];
+            }
+            sigma[s] = sA + Vx * sBx + Vy * sBy;
+            if (s == 0) {
+                Yx = sBx;
+                Yy = sBy;
+            }
+        } else {
+            T sg = T(0);
+#pragma unroll
+            for (int i = 0; i < 9; ++i)
+                sg += T(L9::w(i)) * (T(1) + T(3) * (Vx * T(L9::ex(i)) + Vy * T(L9::ey(i)))) * r[s][i];
+            sigma[s] = sg;
+            if (s == 0) {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    Yx += T(3.0 * L9::w(i) * L9::ex(i)) * r[0][i];
+                    Yy += T(3.0 * L9::w(i) * L9::ey(i)) * r[0][i];
+                }
+            }
+        }
+        relax3<T>(KC, K, mom, z);
+        T Tc = T(0);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) Tc += z[q] * mh[q];
+        Transform<T, 9>::transpose(z, mt);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) ps[s][i] = r[s][i] - mt[i] + Tc;
+    }
+
+    // chemotactic source of u: F = u (chi1 G_v + chi2 G_w), tau S_u = 3 w_i e_i . K_u F
+    const T(&Ku)[3] = nc.K[0];
+    const T aFx = Ku[0] * Yx + Ku[1] * Yy, aFy = Ku[1] * Yx + Ku[2] * Yy;
+    T aT[3], aPhi[3], aj[3][2];
+    aT[0] = (KC.chi1 * Gv[0] + KC.chi2 * Gw[0]) * aFx + (KC.chi1 * Gv[1] + KC.chi2 * Gw[1]) * aFy;
+    aT[1] = T(0);
+    aT[2] = T(0);
+    aj[0][0] = aj[0][1] = T(0);
+    const T chis[2] = {KC.chi1, KC.chi2};
+#pragma unroll
+    for (int s = 1; s < 3; ++s) {
+        // G = -(K (j - a Theta)/tau + K a Phi/2) / (d Cs^2)
+        const T(&K)[3] = nc.K[s];
+        const T aGx = chis[s - 1] * Tu * aFx, aGy = chis[s - 1] * Tu * aFy;
+        const T KGx = K[0] * aGx + K[1] * aGy, KGy = K[1] * aGx + K[2] * aGy;
+        aj[s][0] = -KGx * KC.asc * KC.inv_tau;
+        aj[s][1] = -KGy * KC.asc * KC.inv_tau;
+        const T aKG = nc.ax * KGx + nc.ay * KGy;
+        aT[s] = aKG * KC.asc * KC.inv_tau;
+        aPhi[s] = T(-0.5) * aKG * KC.asc;
+    }
+    aPhi[0] = T(0);
+    // sources: Phi^n at step n (c_n) and at step n + 1 (c'_{n+1})
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        aPhi[s] += (A.n == 0 ? KC.c_first : KC.c_now) * sigma[s];
+        if (!A.terminal) aPhi[s] += KC.c_prev * sig_next[s];
+        A.sigma[s * pl + k] = sigma[s];
+    }
+    // kinetics
+    aT[0] += (KC.a1 - T(2) * KC.a2 * Tu) * aPhi[0] + (KC.b1 - KC.b3 * Tv) * aPhi[1] + KC.c1 * aPhi[2];
+    aT[1] += -(KC.b2 + KC.b3 * Tu) * aPhi[1];
+    aT[2] += -KC.c2 * aPhi[2];
+    const T E = aPhi[C.ctrl] + KC.two_alpha * gv;
+    A.dJdg[k] = E;
+    if (A.e2_part) acc.add(E);
+#pragma unroll
+    for (int s = 0; s < 3; ++s)
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+            A.out[(s * 9 + i) * pl + k] = ps[s][i] + aT[s] + T(L9::ex(i)) * aj[s][0] + T(L9::ey(i)) * aj[s][1];
+}
+
+// ------------------------------------------------------ per-thread kernels
+// One node per thread and iteration of a grid-stride loop; inputs straight
+// from global memory.
+
+template <typename T> struct GFwd {
+    const AC& C;
+    const F3Args<T>& A;
+    size_t pl;
+    int k, ks[9];
+    __device__ __forceinline__ T pop(int s, int i) const { return ld(A.in + (s * 9 + i) * pl + ks[i]); }
+    __device__ __forceinline__ T phi(int s) const { return A.phi[s * pl + k]; }
+    __device__ __forceinline__ T g() const { return ld(A.g + k); }
+    __device__ __forceinline__ T E() const { return ld(A.E + k); }
+    __device__ __forceinline__ T theta() const { return ld(reinterpret_cast<const T*>(C.theta) + k); }
+};
+
+// FP32: 256 threads, at least 3 blocks per SM (<= 85 registers), measured faster
+// than 2 blocks with more registers and than 4 blocks with heavier spilling.
+template <typename T>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k3_forward(const AC C, const AK<T> KC, const F3Args<T> A) {
+    const int total = C.nx * C.ny;
+    typename SqAccT<T>::type acc;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
+        const int y = k / C.nx, x = k - y * C.nx;
+        GFwd<T> S{C, A, (size_t)C.plane, k, {}};
+        if (A.n == 0) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) S.ks[i] = k;
+        } else {
+            const int xm = x == 0 ? C.nx - 1 : x - 1, xp = x == C.nx - 1 ? 0 : x + 1;
+            const int rm = (y == 0 ? C.ny - 1 : y - 1) * C.nx, r0 = y * C.nx;
+            const int rp = (y == C.ny - 1 ? 0 : y + 1) * C.nx;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const int xs = L9::ex(i) > 0 ? xm : (L9::ex(i) < 0 ? xp : x);
+                S.ks[i] = (L9::ey(i) > 0 ? rm : (L9::ey(i) < 0 ? rp : r0)) + xs;
+            }
+        }
+        fwd3_body<T>(C, KC, A, y, k, S, acc);
+    }
+    if (A.gsq_part) acc.flush(A.gsq_part + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5), nullptr);
+}
+
+template <typename T> struct GAdj {
+    const AC& C;
+    const A3Args<T>& A;
+    size_t pl;
+    int k, kd[9];
+    __device__ __forceinline__ T pop(int s, int i) const {
+        if (A.terminal) return A.seed[s] ? ld(A.seed[s] + kd[i]) : T(0);
+        return ld(A.in + (s * 9 + i) * pl + kd[i]);
+    }
+    __device__ __forceinline__ T tape(int c) const { return ld(A.tape + c * pl + k); }
+    __device__ __forceinline__ T sig(int s) const { return A.sigma[s * pl + k]; }
+    __device__ __forceinline__ T g() const { return ld(A.g + k); }
+    __device__ __forceinline__ T theta() const { return ld(reinterpret_cast<const T*>(C.theta) + k); }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k3_adjoint(const AC C, const AK<T> KC, const A3Args<T> A) {
     const int total = C.nx * C.ny;
     typename SqAccT<T>::type acc;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
@@ -272,118 +439,149 @@ __global__ void __launch_bounds__(256) k3_adjoint(const AC C, const AK<T> KC, co
         const int xm = x == 0 ? C.nx - 1 : x - 1, xp = x == C.nx - 1 ? 0 : x + 1;
         const int rm = (y == 0 ? C.ny - 1 : y - 1) * C.nx, r0 = y * C.nx;
         const int rp = (y == C.ny - 1 ? 0 : y + 1) * C.nx;
-        T r[3][9];
+        GAdj<T> S{C, A, (size_t)C.plane, k, {}};
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const int xd = L9::ex(i) > 0 ? xp : (L9::ex(i) < 0 ? xm : x);
-            const int kd = (L9::ey(i) > 0 ? rp : (L9::ey(i) < 0 ? rm : r0)) + xd;
-#pragma unroll
-            for (int s = 0; s < 3; ++s) {
-                if (A.terminal)
-                    r[s][i] = A.seed[s] ? ld(A.seed[s] + kd) : T(0);
-                else
-                    r[s][i] = ld(A.in + (s * 9 + i) * pl + kd);
-            }
+            S.kd[i] = (L9::ey(i) > 0 ? rp : (L9::ey(i) < 0 ? rm : r0)) + xd;
         }
-        const T Tu = ld(A.tape + k), Tv = ld(A.tape + pl + k);
-        const T Gv[2] = {ld(A.tape + 2 * pl + k), ld(A.tape + 3 * pl + k)};
-        const T Gw[2] = {ld(A.tape + 4 * pl + k), ld(A.tape + 5 * pl + k)};
-        const T gv = A.g ? ld(A.g + k) : T(0);
-        Coef3<T> nc;
-        coef3<T>(C, KC, y, k, nc);
-        T mh[9];
-        meq_unit<T, 9>(nc.ax, nc.ay, KC.d, mh);
-
-        // transposed collisions, sigma per species, Y = sum_i 3 w_i e_i rho_u,i
-        T ps[3][9], sigma[3], Yx = T(0), Yy = T(0);
-#pragma unroll
-        for (int s = 0; s < 3; ++s) {
-            const T(&K)[3] = nc.K[s];
-            const T Vx = nc.ax - T(0.5) * (K[0] * nc.ax + K[1] * nc.ay);
-            const T Vy = nc.ay - T(0.5) * (K[1] * nc.ax + K[2] * nc.ay);
-            T mom[9], z[9], mt[9];
-            Transform<T, 9>::moments(r[s], mom);
-            if constexpr (fold) {
-                T sA = T(0), sBx = T(0), sBy = T(0);
-#pragma unroll
-                for (int q = 0; q < 9; ++q) {
-                    if (L9::src_A(q) != 0.0) sA += T(L9::inv_n(q) * L9::src_A(q)) * mom[q];
-                    if (L9::src_Bx(q) != 0.0) sBx += T(3.0 * L9::inv_n(q) * L9::src_Bx(q)) * mom[q];
-                    if (L9::src_By(q) != 0.0) sBy += T(3.0 * L9::inv_n(q) * L9::src_By(q)) * mom[q];
-                }
-                sigma[s] = sA + Vx * sBx + Vy * sBy;
-                if (s == 0) {
-                    Yx = sBx;
-                    Yy = sBy;
-                }
-            } else {
-                T sg = T(0);
-#pragma unroll
-                for (int i = 0; i < 9; ++i)
-                    sg += T(L9::w(i)) * (T(1) + T(3) * (Vx * T(L9::ex(i)) + Vy * T(L9::ey(i)))) * r[s][i];
-                sigma[s] = sg;
-                if (s == 0) {
-#pragma unroll
-                    for (int i = 0; i < 9; ++i) {
-                        Yx += T(3.0 * L9::w(i) * L9::ex(i)) * r[0][i];
-                        Yy += T(3.0 * L9::w(i) * L9::ey(i)) * r[0][i];
-                    }
-                }
-            }
-            relax3<T>(KC, K, mom, z);
-            T Tc = T(0);
-#pragma unroll
-            for (int q = 0; q < 9; ++q) Tc += z[q] * mh[q];
-            Transform<T, 9>::transpose(z, mt);
-#pragma unroll
-            for (int i = 0; i < 9; ++i) ps[s][i] = r[s][i] - mt[i] + Tc;
-        }
-
-        // chemotactic source of u: F = u (chi1 G_v + chi2 G_w), tau S_u = 3 w_i e_i . K_u F
-        const T(&Ku)[3] = nc.K[0];
-        const T aFx = Ku[0] * Yx + Ku[1] * Yy, aFy = Ku[1] * Yx + Ku[2] * Yy;
-        T aT[3], aPhi[3], aj[3][2];
-        aT[0] = (KC.chi1 * Gv[0] + KC.chi2 * Gw[0]) * aFx + (KC.chi1 * Gv[1] + KC.chi2 * Gw[1]) * aFy;
-        aT[1] = T(0);
-        aT[2] = T(0);
-        aj[0][0] = aj[0][1] = T(0);
-        const T chis[2] = {KC.chi1, KC.chi2};
-#pragma unroll
-        for (int s = 1; s < 3; ++s) {
-            // G = -(K (j - a Theta)/tau + K a Phi/2) / (d Cs^2)
-            const T(&K)[3] = nc.K[s];
-            const T aGx = chis[s - 1] * Tu * aFx, aGy = chis[s - 1] * Tu * aFy;
-            const T KGx = K[0] * aGx + K[1] * aGy, KGy = K[1] * aGx + K[2] * aGy;
-            aj[s][0] = -KGx * KC.asc * KC.inv_tau;
-            aj[s][1] = -KGy * KC.asc * KC.inv_tau;
-            const T aKG = nc.ax * KGx + nc.ay * KGy;
-            aT[s] = aKG * KC.asc * KC.inv_tau;
-            aPhi[s] = T(-0.5) * aKG * KC.asc;
-        }
-        aPhi[0] = T(0);
-        // sources: Phi^n at step n (c_n) and at step n + 1 (c'_{n+1})
-#pragma unroll
-        for (int s = 0; s < 3; ++s) {
-            aPhi[s] += (A.n == 0 ? KC.c_first : KC.c_now) * sigma[s];
-            if (!A.terminal) aPhi[s] += KC.c_prev * A.sigma[s * pl + k];
-            A.sigma[s * pl + k] = sigma[s];
-        }
-        // kinetics
-        aT[0] += (KC.a1 - T(2) * KC.a2 * Tu) * aPhi[0] + (KC.b1 - KC.b3 * Tv) * aPhi[1] + KC.c1 * aPhi[2];
-        aT[1] += -(KC.b2 + KC.b3 * Tu) * aPhi[1];
-        aT[2] += -KC.c2 * aPhi[2];
-        const T E = aPhi[C.ctrl] + KC.two_alpha * gv;
-        A.dJdg[k] = E;
-        if (A.e2_part) acc.add(E);
-#pragma unroll
-        for (int s = 0; s < 3; ++s)
-#pragma unroll
-            for (int i = 0; i < 9; ++i)
-                A.out[(s * 9 + i) * pl + k] =
-                    ps[s][i] + aT[s] + T(L9::ex(i)) * aj[s][0] + T(L9::ey(i)) * aj[s][1];
+        adj3_body<T>(C, KC, A, y, k, S, acc);
     }
     if (A.e2_part) {
         const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+        acc.flush(A.e2_part + w, A.emax_part + w);
+    }
+}
+
+// ------------------------------------------------------ row-window kernels
+// Steps whose inputs are all pulled (forward n >= 1, adjoint below the
+// terminal step) on grids whose rows are a whole number of 16-byte units:
+// the warp-specialised pipeline of cx_rows.cuh.  A producer warp issues, per
+// row segment of RNT nodes, one bulk copy per population plane of the source
+// row window (the segment widened by 16 bytes on each side; periodic ends from
+// the other end of the row) and of the node-local planes, completing on the
+// stage's mbarrier; the compute warps read everything from shared memory.
+
+constexpr int RNT = 128;
+template <typename T> struct RW3 {
+    static constexpr int H = 16 / (int)sizeof(T);
+    static constexpr int W = RNT + 2 * H;
+};
+// stage layout: 27 population windows, then per-node planes of RNT values
+template <typename T> constexpr int fwd3_stage_values() { return 27 * RW3<T>::W + 6 * RNT; } // theta, g, E, Phi x3
+template <typename T> constexpr int adj3_stage_values() {
+    return 27 * RW3<T>::W + 11 * RNT; // tape x6, sigma x3, g, theta
+}
+
+template <typename T> struct SFwd {
+    const T* s; // stage + threadIdx.x
+    __device__ __forceinline__ T pop(int sp, int i) const { return s[(sp * 9 + i) * RW3<T>::W + RW3<T>::H - L9::ex(i)]; }
+    __device__ __forceinline__ T theta() const { return s[27 * RW3<T>::W]; }
+    __device__ __forceinline__ T g() const { return s[27 * RW3<T>::W + RNT]; }
+    __device__ __forceinline__ T E() const { return s[27 * RW3<T>::W + 2 * RNT]; }
+    __device__ __forceinline__ T phi(int sp) const { return s[27 * RW3<T>::W + (3 + sp) * RNT]; }
+};
+template <typename T> struct SAdj {
+    const T* s;
+    __device__ __forceinline__ T pop(int sp, int i) const { return s[(sp * 9 + i) * RW3<T>::W + RW3<T>::H + L9::ex(i)]; }
+    __device__ __forceinline__ T tape(int c) const { return s[27 * RW3<T>::W + c * RNT]; }
+    __device__ __forceinline__ T sig(int sp) const { return s[27 * RW3<T>::W + (6 + sp) * RNT]; }
+    __device__ __forceinline__ T g() const { return s[27 * RW3<T>::W + 9 * RNT]; }
+    __device__ __forceinline__ T theta() const { return s[27 * RW3<T>::W + 10 * RNT]; }
+};
+
+template <typename T>
+__device__ __forceinline__ void fwd3_issue(const AC& C, const F3Args<T>& A, int y, int x0, T* st, uint64_t* bar) {
+    constexpr int H = RW3<T>::H, W = RW3<T>::W;
+    const int nx = C.nx, nv = min(RNT, nx - x0);
+    const int rm = y == 0 ? C.ny - 1 : y - 1, rp = y == C.ny - 1 ? 0 : y + 1;
+    const bool rot = C.aniso == CX_ANISO_ROTATED;
+    const uint32_t nb = (uint32_t)nv * sizeof(T);
+    const size_t pl = (size_t)C.plane, k0 = (size_t)y * nx + x0;
+    mbar_expect_tx(bar, (uint32_t)(27 * (nv + 2 * H)) * sizeof(T) + nb * (3u + rot + (A.g ? 1u : 0u) + (A.E ? 1u : 0u)));
+#pragma unroll
+    for (int j = 0; j < 27; ++j) {
+        const int i = j % 9;
+        const int ys = L9::ey(i) > 0 ? rm : (L9::ey(i) < 0 ? rp : y); // pull from x - e_i
+        bulk_row_window<T, RNT>(st + j * W, A.in + j * pl + (size_t)ys * nx, x0, nv, nx, bar);
+    }
+    T* const loc = st + 27 * W;
+    if (rot) bulk_g2s(loc, reinterpret_cast<const T*>(C.theta) + k0, nb, bar);
+    if (A.g) bulk_g2s(loc + RNT, A.g + k0, nb, bar);
+    if (A.E) bulk_g2s(loc + 2 * RNT, A.E + k0, nb, bar);
+#pragma unroll
+    for (int s = 0; s < 3; ++s) bulk_g2s(loc + (3 + s) * RNT, A.phi + s * pl + k0, nb, bar);
+}
+
+template <typename T>
+__device__ __forceinline__ void adj3_issue(const AC& C, const A3Args<T>& A, int y, int x0, T* st, uint64_t* bar) {
+    constexpr int H = RW3<T>::H, W = RW3<T>::W;
+    const int nx = C.nx, nv = min(RNT, nx - x0);
+    const int rm = y == 0 ? C.ny - 1 : y - 1, rp = y == C.ny - 1 ? 0 : y + 1;
+    const bool rot = C.aniso == CX_ANISO_ROTATED;
+    const uint32_t nb = (uint32_t)nv * sizeof(T);
+    const size_t pl = (size_t)C.plane, k0 = (size_t)y * nx + x0;
+    mbar_expect_tx(bar, (uint32_t)(27 * (nv + 2 * H)) * sizeof(T) + nb * (9u + rot + (A.g ? 1u : 0u)));
+#pragma unroll
+    for (int j = 0; j < 27; ++j) {
+        const int i = j % 9;
+        const int ys = L9::ey(i) > 0 ? rp : (L9::ey(i) < 0 ? rm : y); // pull from x + e_i
+        bulk_row_window<T, RNT>(st + j * W, A.in + j * pl + (size_t)ys * nx, x0, nv, nx, bar);
+    }
+    T* const loc = st + 27 * W;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) bulk_g2s(loc + c * RNT, A.tape + c * pl + k0, nb, bar);
+#pragma unroll
+    for (int s = 0; s < 3; ++s) bulk_g2s(loc + (6 + s) * RNT, A.sigma + s * pl + k0, nb, bar);
+    if (A.g) bulk_g2s(loc + 9 * RNT, A.g + k0, nb, bar);
+    if (rot) bulk_g2s(loc + 10 * RNT, reinterpret_cast<const T*>(C.theta) + k0, nb, bar);
+}
+
+// Block: RNT compute threads and one producer warp.  CC describes the grid to
+// the pipeline's segment walk (no solid nodes, whole-grid control).
+template <typename T>
+__global__ void __launch_bounds__(RNT + 32, sizeof(T) == 4 ? 4 : 2)
+    k3_forward_rows(const CxConst CC, const AC C, const AK<T> KC, const F3Args<T> A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    RowsPipe<T, RNT> pipe(smem_raw, fwd3_stage_values<T>());
+    pipe.init();
+    allow_next_grid();
+    wait_prior_grid(); // the previous step's populations and node state are complete
+    if (block_sees_timeout(A.status)) return;
+    if (threadIdx.x >= RNT) {
+        pipe.produce(CC, A.status, [&](int y, int x0, T* st, uint64_t* bar) { fwd3_issue<T>(C, A, y, x0, st, bar); });
+        return;
+    }
+    typename SqAccT<T>::type acc;
+    pipe.consume(
+        CC, A.status, [&](const NodeIdx&, T*) {},
+        [&](const NodeIdx& nd, T* st) {
+            if (nd.fluid) fwd3_body<T>(C, KC, A, nd.y, nd.k, SFwd<T>{st + threadIdx.x}, acc);
+        });
+    if (A.gsq_part) acc.flush(A.gsq_part + blockIdx.x * (RNT >> 5) + (threadIdx.x >> 5), nullptr);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(RNT + 32, sizeof(T) == 4 ? 3 : 2)
+    k3_adjoint_rows(const CxConst CC, const AC C, const AK<T> KC, const A3Args<T> A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    RowsPipe<T, RNT> pipe(smem_raw, adj3_stage_values<T>());
+    pipe.init();
+    allow_next_grid();
+    wait_prior_grid();
+    if (block_sees_timeout(A.status)) return;
+    if (threadIdx.x >= RNT) {
+        pipe.produce(CC, A.status, [&](int y, int x0, T* st, uint64_t* bar) { adj3_issue<T>(C, A, y, x0, st, bar); });
+        return;
+    }
+    typename SqAccT<T>::type acc;
+    pipe.consume(
+        CC, A.status, [&](const NodeIdx&, T*) {},
+        [&](const NodeIdx& nd, T* st) {
+            if (nd.fluid) adj3_body<T>(C, KC, A, nd.y, nd.k, SAdj<T>{st + threadIdx.x}, acc);
+        });
+    if (A.e2_part) {
+        const int w = blockIdx.x * (RNT >> 5) + (threadIdx.x >> 5);
         acc.flush(A.e2_part + w, A.emax_part + w);
     }
 }
@@ -636,6 +834,9 @@ struct cx3_problem {
     const AK<float>& kc(float*) const { return Kf; }
     const AK<double>& kc(double*) const { return Kd; }
     int grid_f = 1, grid_a = 1, nblk = 1; // persistent grids (forward, adjoint), blocks of k3_final
+    int grid_fr = 1, grid_ar = 1;          // persistent grids of the row-window kernels
+    int rows_mode = 1;                     // cx3_set_staging
+    CxConst CC{};                          // the grid as the row-window pipeline walks it
     bool has_init = false, fwd_valid = false, adj_valid = false, tape_last_valid = false;
     bool have_lam = false;
     double lam_prev = 0.0;
@@ -680,13 +881,64 @@ void rend(cx3_problem* p, Range3* r, long long launches) {
     r->launches = launches;
 }
 
+// Row-window kernels for a step whose inputs are all pulled, on rows of whole
+// 16-byte units with 16-byte aligned planes; mode 1 also asks for at least
+// two row segments per block (else nothing overlaps the copies).
+bool aligned16(const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; }
+
+template <typename T> bool rows_ok(const cx3_problem* p, const T* in, const T* g, const T* extra) {
+    if (p->rows_mode == 0 || p->C.nx % (16 / (int)sizeof(T)) != 0) return false;
+    if (!aligned16(in) || !aligned16(p->ws) || (g && !aligned16(g)) || (extra && !aligned16(extra))) return false;
+    const long long segs = (long long)((p->C.nx + RNT - 1) / RNT) * p->C.ny;
+    return p->rows_mode == 2 || segs >= 2LL * std::max(p->grid_fr, p->grid_ar);
+}
+
+template <typename T> cudaError_t launch_rows(const void* kern, int grid, size_t smem, cudaStream_t s, void** args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(RNT + 32);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, kern, args);
+}
+
+template <typename T> cudaError_t launch_fwd3(cx3_problem* p, const F3Args<T>& A) {
+    const AK<T>& K = p->kc((T*)nullptr);
+    if (A.n > 0 && rows_ok<T>(p, A.in, A.g, A.E)) {
+        void* args[] = {(void*)&p->CC, (void*)&p->C, (void*)&K, (void*)&A};
+        return launch_rows<T>((const void*)k3_forward_rows<T>, p->grid_fr, rows_pipe_smem<T>(fwd3_stage_values<T>()),
+                              p->stream, args);
+    }
+    k3_forward<T><<<p->grid_f, 256, 0, p->stream>>>(p->C, K, A);
+    return cudaGetLastError();
+}
+
+// The adjoint takes the row-window kernel only when asked to (mode 2): at
+// 1024^2 it measured slower than the per-thread kernel (57.7 against 53.8 us
+// per step; 127 registers and 61 KB of stages leave 12 compute warps per SM
+// to a body that issues on 60% of the cycles, against 24 warps).
+template <typename T> cudaError_t launch_adj3(cx3_problem* p, const AK<T>& K, const A3Args<T>& A) {
+    if (!A.terminal && p->rows_mode == 2 && rows_ok<T>(p, A.in, A.g, nullptr)) {
+        void* args[] = {(void*)&p->CC, (void*)&p->C, (void*)&K, (void*)&A};
+        return launch_rows<T>((const void*)k3_adjoint_rows<T>, p->grid_ar, rows_pipe_smem<T>(adj3_stage_values<T>()),
+                              p->stream, args);
+    }
+    k3_adjoint<T><<<p->grid_a, 256, 0, p->stream>>>(p->C, K, A);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cx_status run3_forward(cx3_problem* p, const T* g, const T* E, double lam, double* J_dev, bool flag_unstable) {
     const Lay3& Ly = p->lay;
     const size_t nn = (size_t)p->d.nx * p->d.ny; // control and gradient planes are unpadded [N][ny][nx]
     double* part = p->at<double>(Ly.off_part);
     double* gsq = part + Ly.nparts;
-    const int fw = p->grid_f * 8;
+    const int fw = std::max(p->grid_f * 8, p->grid_fr * (RNT / 32));
     CX3_CUDA(cudaMemsetAsync(gsq, 0, sizeof(double) * fw, p->stream));
     Range3* r;
     rbegin(p, R_FWD, &r);
@@ -710,9 +962,9 @@ cx_status run3_forward(cx3_problem* p, const T* g, const T* E, double lam, doubl
         A.lam = T(lam);
         A.tape = (seg == Ly.S - 1) ? reinterpret_cast<T*>(p->tape(n - seg * Ly.k)) : nullptr;
         A.gsq_part = gsq;
+        A.status = p->at<int>(Ly.off_status);
         A.n = n;
-        k3_forward<T><<<p->grid_f, 256, 0, p->stream>>>(p->C, p->kc((T*)nullptr), A);
-        CX3_CUDA(cudaGetLastError());
+        CX3_CUDA(launch_fwd3<T>(p, A));
         in = out;
     }
     rend(p, r, Ly.N);
@@ -740,7 +992,7 @@ cx_status run3_adjoint(cx3_problem* p, const T* g, const T* const (&seeds)[3], b
     double* e2 = part + 2 * (size_t)Ly.nparts;
     double* emax = part + 3 * (size_t)Ly.nparts;
     CX3_CUDA(cudaMemsetAsync(e2, 0, sizeof(double) * 2 * Ly.nparts, p->stream));
-    const int aw = p->grid_a * 8;
+    const int aw = std::max(p->grid_a * 8, p->grid_ar * (RNT / 32));
     T* sigma = p->at<T>(Ly.off_sigma);
     T* phi = p->at<T>(Ly.off_phi);
     const bool cost_seed = !seeds[0] && !seeds[1] && !seeds[2];
@@ -762,9 +1014,9 @@ cx_status run3_adjoint(cx3_problem* p, const T* g, const T* const (&seeds)[3], b
                 A.phi = phi;
                 A.g = g ? g + (size_t)n * nn : nullptr;
                 A.tape = reinterpret_cast<T*>(p->tape(n - n0));
+                A.status = p->at<int>(Ly.off_status);
                 A.n = n;
-                k3_forward<T><<<p->grid_f, 256, 0, p->stream>>>(p->C, p->kc((T*)nullptr), A);
-                CX3_CUDA(cudaGetLastError());
+                CX3_CUDA(launch_fwd3<T>(p, A));
                 in = out;
             }
             rend(p, r, n1 - n0);
@@ -784,9 +1036,9 @@ cx_status run3_adjoint(cx3_problem* p, const T* g, const T* const (&seeds)[3], b
             A.dJdg = dJdg + (size_t)n * nn;
             A.e2_part = e2;
             A.emax_part = emax;
+            A.status = p->at<int>(Ly.off_status);
             A.n = n;
-            k3_adjoint<T><<<p->grid_a, 256, 0, p->stream>>>(p->C, KA, A);
-            CX3_CUDA(cudaGetLastError());
+            CX3_CUDA(launch_adj3<T>(p, KA, A));
             psi_in = out;
         }
         rend(p, r, n1 - n0);
@@ -822,6 +1074,7 @@ template <typename T> cx_status run3_step(cx3_problem* p, T* g, T* E, cx_step_in
     int st = 0;
     rc = read3(p, s4, &st);
     if (rc) return rc;
+    if (st & ST_TIMEOUT) return CX_ERR_TIMEOUT;
     if (st & ST_UNSTABLE) return CX_ERR_UNSTABLE;
     const double J0 = s4[0], e2 = s4[2], einf = s4[3];
     double lam = p->have_lam ? 2.0 * p->lam_prev : std::min(1.0, einf > 0.0 ? 1.0 / einf : 1.0);
@@ -913,6 +1166,36 @@ cx_status cx3_create(const cx3_desc* desc, void* workspace, size_t bytes, cudaSt
     const bool f64 = desc->precision == 64;
     p->grid_f = persistent_grid(f64 ? (const void*)k3_forward<double> : (const void*)k3_forward<float>, nsm, total);
     p->grid_a = persistent_grid(f64 ? (const void*)k3_adjoint<double> : (const void*)k3_adjoint<float>, nsm, total);
+    {
+        const void* kf = f64 ? (const void*)k3_forward_rows<double> : (const void*)k3_forward_rows<float>;
+        const void* ka = f64 ? (const void*)k3_adjoint_rows<double> : (const void*)k3_adjoint_rows<float>;
+        const size_t sf = f64 ? rows_pipe_smem<double>(fwd3_stage_values<double>())
+                              : rows_pipe_smem<float>(fwd3_stage_values<float>());
+        const size_t sa = f64 ? rows_pipe_smem<double>(adj3_stage_values<double>())
+                              : rows_pipe_smem<float>(adj3_stage_values<float>());
+        int of = 1, oa = 1;
+        if (cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf) != cudaSuccess ||
+            cudaFuncSetAttribute(ka, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&of, kf, RNT + 32, sf) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oa, ka, RNT + 32, sa) != cudaSuccess) {
+            delete p;
+            return CX_ERR_CUDA;
+        }
+        const long long segs = (long long)((desc->nx + RNT - 1) / RNT) * desc->ny;
+        p->grid_fr = (int)std::max(1LL, std::min<long long>((long long)std::max(of, 1) * nsm, segs));
+        p->grid_ar = (int)std::max(1LL, std::min<long long>((long long)std::max(oa, 1) * nsm, segs));
+        p->grid_fr = std::min(p->grid_fr, MAXW / (RNT / 32));
+        p->grid_ar = std::min(p->grid_ar, MAXW / (RNT / 32));
+    }
+    CxConst& CC = p->CC;
+    CC.nx = desc->nx;
+    CC.ny = desc->ny;
+    CC.plane = (long long)L.plane;
+    CC.Q = 9;
+    CC.n_steps = desc->n_steps;
+    CC.ctrl_full = 1;
+    CC.cnx = desc->nx;
+    CC.cny = desc->ny;
     cudaError_t e = cudaMemsetAsync(p->at<int>(L.off_status), 0, sizeof(int) * 4, stream);
     const int sb = std::min(p->nblk, nsm * 8);
     if (e == cudaSuccess) {
@@ -1012,7 +1295,14 @@ cx_status cx3_get_norms(cx3_problem* p, double* J, double* grad_sq, double* grad
     if (J) *J = s4[0];
     if (grad_sq) *grad_sq = s4[2];
     if (grad_inf) *grad_inf = s4[3];
+    if (st & ST_TIMEOUT) return CX_ERR_TIMEOUT;
     return (st & ST_UNSTABLE) ? CX_ERR_UNSTABLE : CX_OK;
+}
+
+cx_status cx3_set_staging(cx3_problem* p, int mode) {
+    if (!p || mode < 0 || mode > 2) return CX_ERR_INVALID_ARG;
+    p->rows_mode = mode;
+    return CX_OK;
 }
 
 cx_status cx3_set_timing(cx3_problem* p, int enable) {

@@ -19,8 +19,9 @@ KERNEL_SOURCES = {
     "k_cadj": ("cx_device.cuh", "cx_internal.h", "cx_cadj.cu"),
     "k_tlm_rows": ("cx_device.cuh", "cx_internal.h", "cx_tlm.cu"),
     "k_cadj_rows": ("cx_device.cuh", "cx_internal.h", "cx_cadj.cu"),
-    "k3_forward": ("cx_device.cuh", "cx_internal.h", "cx_arc.cu"),
-    "k3_adjoint": ("cx_device.cuh", "cx_internal.h", "cx_arc.cu"),
+    "k3_forward": ("cx_device.cuh", "cx_internal.h", "cx_rows.cuh", "cx_arc.cu"),
+    "k3_forward_rows": ("cx_device.cuh", "cx_internal.h", "cx_rows.cuh", "cx_arc.cu"),
+    "k3_adjoint": ("cx_device.cuh", "cx_internal.h", "cx_rows.cuh", "cx_arc.cu"),
     "nn": ("nn_kernels.cu",),
 }
 

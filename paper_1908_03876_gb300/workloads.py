@@ -258,8 +258,8 @@ class Workload3:
     D_v_field: np.ndarray | None = None
     D_w_field: np.ndarray | None = None
     d: float = 1.0
-    chi1: float = -0.1
-    chi2: float = 0.08
+    chi1: float = 0.1
+    chi2: float = -0.08
     a1: float = 0.0
     a2: float = 0.0
     b1: float = 0.0
@@ -308,7 +308,7 @@ def arc(nx=1024, ny=1024, N=2000, seed=5, precision=32, ckpt_every=100, ctrl_spe
     """Attraction-repulsion chemotaxis with a logistic source (D2Q9): rotated
     anisotropic tensors for the three species along one seeded angle field,
     shear convection a = (0.05 sin(2 pi y / L), 0), attraction toward v
-    (chi1 = -0.1), repulsion from w (chi2 = 0.08), logistic growth of u,
+    (chi1 = 0.1), repulsion from w (chi2 = -0.08), logistic growth of u,
     nonlinear consumption of v; u0 four seeded bumps on 1, v0 and w0 smooth
     seeded fields, u_target one centred bump.  Rates are per lattice step."""
     rng = np.random.default_rng(seed)
@@ -324,7 +324,7 @@ def arc(nx=1024, ny=1024, N=2000, seed=5, precision=32, ckpt_every=100, ctrl_spe
     w0 = 0.4 + 0.1 * np.cos(2 * np.pi * 2 * x / nx + p[1]) * np.cos(2 * np.pi * yy / ny + p[2])
     u_tgt = 1.0 + 0.2 * _periodic_gauss(nx, ny, nx / 2, ny / 2, 2 * sig)
     return Workload3(name="arc", nx=nx, ny=ny, N=N, precision=precision, aniso="rotated", theta=theta,
-                     lam_u=(0.08, 0.02), lam_v=(0.2, 0.1), lam_w=(0.15, 0.05), chi1=-0.1, chi2=0.08,
+                     lam_u=(0.08, 0.02), lam_v=(0.2, 0.1), lam_w=(0.15, 0.05), chi1=0.1, chi2=-0.08,
                      a1=1e-3, a2=5e-4, b1=1e-3, b2=2e-3, b3=5e-4, c1=1e-3, c2=3e-3, ctrl_species=ctrl_species,
                      adv="row", a_row=a_row, u0=u0, v0=v0, w0=np.broadcast_to(w0, (ny, nx)).copy(), u_tgt=u_tgt,
                      alpha=1e-3, ckpt_every=ckpt_every)

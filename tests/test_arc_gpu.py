@@ -39,9 +39,11 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-def _problem(w):
+def _problem(w, staging=1):
     from paper_1908_03876_gb300.arc import ArcProblem
-    return ArcProblem(w)
+    p = ArcProblem(w)
+    p.set_staging(staging)
+    return p
 
 
 CASES = [
@@ -52,10 +54,13 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("staging", [0, 2], ids=["per-thread", "row-window"])
 @pytest.mark.parametrize("case", CASES, ids=[str(i) for i in range(len(CASES))])
-def test_arc_fp64_forward_and_gradient_match_oracle(case):
+def test_arc_fp64_forward_and_gradient_match_oracle(case, staging):
+    """Both kernel forms (the row-window kernels take every step they can:
+    rows of whole 16-byte units, pulled inputs) against the oracle."""
     w = _arc(**case)
-    p = _problem(w)
+    p = _problem(w, staging)
     g = w.random_control(11, 0.05)
     J = float(p.forward(g).item())
     u, v, ww = (t.cpu().numpy() for t in p.fields())
@@ -99,7 +104,7 @@ def test_arc_fp64_armijo_step():
     """The accepted cost equals the oracle's cost at the updated control, and
     descends; the next step reuses the accepted trial's forward."""
     w = _arc(40, 36, 9, 4)
-    p = _problem(w)
+    p = _problem(w, 2)
     g = p.zeros_control()
     po = oracle.from_workload3(w)
     J_prev = None
@@ -114,13 +119,13 @@ def test_arc_fp64_armijo_step():
         J_prev = info["J"]
 
 
-@pytest.mark.parametrize("ctrl", [1, 2])
-def test_arc_fp32_against_fp64_oracle(ctrl):
+@pytest.mark.parametrize("ctrl,staging", [(1, 0), (2, 0), (1, 2), (2, 2)])
+def test_arc_fp32_against_fp64_oracle(ctrl, staging):
     """FP32 lattices against the FP64 oracle over 200 steps: fields within
     1e-4 and the gradient within 1e-3 (relative L2)."""
     w = _arc(64, 48, 200, 50, precision=32, ctrl=ctrl)
     w.a1, w.a2, w.b1, w.b2, w.b3, w.c1, w.c2 = 2e-3, 1e-3, 2e-3, 3e-3, 1e-3, 2e-3, 4e-3
-    p = _problem(w)
+    p = _problem(w, staging)
     g = w.random_control(13, 0.01)
     J, E = p.gradient(g)
     u, v, ww = (t.cpu().numpy() for t in p.fields())
@@ -163,3 +168,23 @@ def test_arc_errors():
     w2.lam_u = (-0.5, 0.02)  # a negative diffusivity gives a K eigenvalue outside (0, 2)
     with pytest.raises(_lib.CxError):
         _problem(w2)
+
+
+def test_arc_fp32_staging_forms_agree_at_1024():
+    """At the benchmark's grid (1024^2, the row-window kernels' default
+    launch), 20 steps: the row-window and per-thread forms give the same
+    fields and gradient to FP32 rounding, and the FP32 gradient is finite."""
+    w = _arc(1024, 1024, 20, 10, precision=32)
+    g = torch.as_tensor(w.random_control(15, 0.01), dtype=torch.float32, device="cuda")
+    out = []
+    for staging in (1, 0):
+        p = _problem(w, staging)
+        J, E = p.gradient(g)
+        out.append((float(J.item()), E.clone(), [t.clone() for t in p.fields()]))
+        p.close()
+    (J1, E1, F1), (J0, E0, F0) = out
+    assert abs(J1 - J0) <= 1e-6 * abs(J0)
+    assert bool(torch.isfinite(E1).all())
+    assert float(torch.linalg.norm(E1 - E0) / torch.linalg.norm(E0)) <= 1e-5
+    for a, b in zip(F1, F0):
+        assert float(torch.linalg.norm(a - b) / torch.linalg.norm(b)) <= 1e-6
