@@ -488,36 +488,20 @@ def run_warmstart(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
-def run_cg(args, rank, world, local):
+def cg_block():
     """Nonlinear CG (Polak-Ribiere, Wolfe-Powell search) and steepest descent
     with the linearised (sensitivity) line search against Armijo steepest
-    descent on one problem: wall time and iterations until J <= J* (1 + 1e-6),
+    descent on one problem (256x256 D2Q9 FP32, 200 steps, control constant
+    over 8 windows): wall time and iterations until J <= J* (1 + 1e-6),
     J* = the lowest cost any method reaches in its iteration budget."""
-    import numpy as np
     import torch
 
-    if rank != 0:
-        return
-    torch.cuda.set_device(local)
-    from paper_1908_03876_gb300.build import build
-
-    build()
     from paper_1908_03876_gb300 import workloads as W
     from paper_1908_03876_gb300._lib import CxError
     from paper_1908_03876_gb300.problem import Problem
 
     w = W.aniso(256, 256, 200, seed=1, precision=32, ckpt_every=50)
     w.windows = 8
-    if args.profile:  # one forward, sensitivity pass and continuous adjoint (profiling case)
-        p = Problem(w)
-        g = p.zeros_control()
-        p.forward(g)
-        p.tlm(g, torch.ones_like(g))
-        p.forward(g)
-        p.cadjoint(g)
-        torch.cuda.synchronize()
-        print(json.dumps({"profile": "aniso 256x256, 200 steps: forward, sensitivity, continuous adjoint"}))
-        return
 
     def run(method, n_iter, target=None):
         p = Problem(w)
@@ -548,17 +532,46 @@ def run_cg(args, rank, world, local):
     _, t_cg, it_cg = run("cg", 150, target)
     _, t_sd, it_sd = run("sd", 600, target)
     _, t_lm, it_lm = run("lma", 600, target)
+    return {"workload": "aniso 256x256 D2Q9 FP32, 200 steps, k = 50, control constant over 8 windows",
+            "J_star": Jstar, "iteration_budgets": {"cg": 150, "steepest_descent": 600, "lma": 600},
+            "cg_seconds": t_cg, "cg_iterations": it_cg, "steepest_descent_seconds": t_sd,
+            "steepest_descent_iterations": it_sd, "lma_seconds": t_lm, "lma_iterations": it_lm,
+            "speedup_vs_steepest_descent": None if (t_cg is None or t_sd is None) else t_sd / t_cg,
+            "J_final": {"cg": Jcg[-1], "steepest_descent": Jsd[-1], "lma": Jlm[-1]}}
+
+
+def run_cg(args, rank, world, local):
+    """The CG comparison of cg_block as its own bench line."""
+    import torch
+
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    from paper_1908_03876_gb300.build import build
+
+    build()
+    if args.profile:  # one forward, sensitivity pass and continuous adjoint (profiling case)
+        from paper_1908_03876_gb300 import workloads as W
+        from paper_1908_03876_gb300.problem import Problem
+
+        w = W.aniso(256, 256, 200, seed=1, precision=32, ckpt_every=50)
+        w.windows = 8
+        p = Problem(w)
+        g = p.zeros_control()
+        p.forward(g)
+        p.tlm(g, torch.ones_like(g))
+        p.forward(g)
+        p.cadjoint(g)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": "aniso 256x256, 200 steps: forward, sensitivity, continuous adjoint"}))
+        return
+    cg = cg_block()
     line = {
         "metric": "wall time to J* (1e-6 rel): nonlinear CG (Polak-Ribiere, Wolfe-Powell) vs Armijo steepest descent",
-        "value": t_cg, "unit": "s", "n_gpus": 1, "steps": 1, "warmup": 0,
-        "ms_per_step": None if t_cg is None else t_cg * 1e3, "higher_is_better": False, "scaling": "replicas only",
-        "vs_baseline": None, "dtype": "f32 (FP64 reductions)", "data": "synthetic (seeded)",
-        "config": {"workload": "aniso 256x256 D2Q9 FP32, 200 steps, k = 50, control constant over 8 windows",
-                   "J_star": Jstar, "iteration budgets": {"cg": 150, "steepest_descent": 600}},
-        "steepest_descent_seconds": t_sd, "cg_iterations": it_cg, "steepest_descent_iterations": it_sd,
-        "lma_seconds": t_lm, "lma_iterations": it_lm,
-        "speedup_vs_steepest_descent": None if (t_cg is None or t_sd is None) else t_sd / t_cg,
-        "J_final": {"cg": Jcg[-1], "steepest_descent": Jsd[-1], "lma": Jlm[-1]},
+        "value": cg["cg_seconds"], "unit": "s", "n_gpus": 1, "steps": 1, "warmup": 0,
+        "ms_per_step": None if cg["cg_seconds"] is None else cg["cg_seconds"] * 1e3, "higher_is_better": False,
+        "scaling": "replicas only", "vs_baseline": None, "dtype": "f32 (FP64 reductions)",
+        "data": "synthetic (seeded)", "config": {"workload": cg["workload"]}, **cg,
     }
     print(json.dumps(line), flush=True)
 
@@ -774,6 +787,33 @@ def run_unet_layers(args, rank, world, local):
             e1.record()
             torch.cuda.synchronize()
             res[name] = e0.elapsed_time(e1) / 20 * 1e3
+        # weight gradient of the same layer (dY random), both kernels, the splits the surrogate uses
+        dy = torch.randn(B, cout, hw, hw, device="cuda").to(BF)
+        wg = {}
+        ntiles = B * ((hw + 7) // 8) ** 2
+        for name, base in (("wgrad_tcgen05", ((cin + 15) // 16) * ((cout + 127) // 128)),
+                           ("wgrad_mma_sync", ((cin + 15) // 16) * ((cout + 63) // 64))):
+            splits = int(max(1, min(ntiles, -(-304 // base))))
+            scr = torch.empty(lib.cx_nn_conv_backward_weight_scratch(B, cin, cout, hw, hw, 3, splits) // 4 + 1,
+                              device="cuda")
+            dw = torch.empty(cout, cin, 3, 3, device="cuda")
+            db = torch.empty(cout, device="cuda")
+            if name == "wgrad_tcgen05":
+                fn = lambda: lib.cx_nn_conv_backward_weight_tc(p(x), p(dy), p(dw), p(db), p(scr), splits, B, cin,
+                                                               cout, hw, hw, 3, None, s)
+            else:
+                fn = lambda: lib.cx_nn_conv_backward_weight(p(x), p(dy), p(dw), p(db), p(scr), splits, B, cin, cout,
+                                                            hw, hw, 3, s)
+            for _ in range(3):
+                fn()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(20):
+                fn()
+            e1.record()
+            torch.cuda.synchronize()
+            wg[name] = e0.elapsed_time(e1) / 20 * 1e3
+        res.update(wg)
         fl = 2 * B * hw * hw * cout * cin * 9
         out.append({"layer": f"{cin}->{cout}@{hw}", **{k + "_us": round(v, 1) for k, v in res.items()},
                     **{k + "_tflops": round(fl / v / 1e6, 1) for k, v in res.items()}})
@@ -800,6 +840,7 @@ def main():
     ap.add_argument("--ws-train", type=int, default=2000)
     ap.add_argument("--ws-test", type=int, default=200)
     ap.add_argument("--ws-size", type=int, default=256)
+    ap.add_argument("--no-cg", action="store_true", help="leave the CG comparison out of the default bench line")
     ap.add_argument("--opt-iters", type=int, default=20,
                     help="Armijo steepest-descent iterations of the default workload's optimisation leg (0: skip)")
     ap.add_argument("--ws-steps", type=int, default=256)
@@ -1022,6 +1063,12 @@ def main():
         cpu = None if args.no_cpu_baseline else cpu_baseline()
         fp32_err = None if args.profile else fp32_error_vs_oracle(dev)
         geom = None if args.profile else geometry_block(dev, args.staging)
+        cgb = None
+        if not args.profile and not args.no_cg:
+            try:
+                cgb = cg_block()
+            except Exception as exc:
+                cgb = {"error": str(exc)[:200]}
         line = {
             "metric": "fwd+adjoint MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -1038,6 +1085,7 @@ def main():
             "fp32_err_vs_oracle": fp32_err,
             "geometry4096": geom,
             "optimise": opt,
+            "cg256": cgb,
             "clocks": clk,
             "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps,

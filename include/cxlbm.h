@@ -455,6 +455,17 @@ size_t cx_nn_conv_backward_weight_scratch(int B, int Cin, int Cout, int H, int W
 cx_status cx_nn_conv_backward_weight(const uint16_t* x, const uint16_t* dy, float* dw, float* db, float* scratch,
                                      int splits, int B, int Cin, int Cout, int H, int W, int ks,
                                      cudaStream_t stream);
+/* The same weight and bias gradients (3x3 only) on the tcgen05 tensor cores:
+ * per block 128 output channels x 16 input channels x 9 taps accumulated in
+ * tensor memory over 8 x 8 pixel tiles (K = pixels; the tap shifts of the
+ * input are materialised in shared memory).  Same scratch size and partial
+ * layout as cx_nn_conv_backward_weight, then the same fixed-order sum over
+ * splits.  Needs H and W multiples of 8 and 16-byte aligned x, dy.  status
+ * (device int, may be NULL) is set non-zero if a bounded wait ran out (dw, db
+ * then hold no result).  Errors: CX_ERR_INVALID_ARG. */
+cx_status cx_nn_conv_backward_weight_tc(const uint16_t* x, const uint16_t* dy, float* dw, float* db, float* scratch,
+                                        int splits, int B, int Cin, int Cout, int H, int W, int ks, int* status,
+                                        cudaStream_t stream);
 /* dz = dy where y > 0, else 0 (y = ReLU output). */
 cx_status cx_nn_relu_backward(const uint16_t* y, const uint16_t* dy, uint16_t* dz, size_t n, cudaStream_t stream);
 cx_status cx_nn_add(const uint16_t* a, const uint16_t* b, uint16_t* out, size_t n, cudaStream_t stream);

@@ -38,7 +38,7 @@ EXPORTS = [
     "cx_nn_conv_forward", "cx_nn_conv_backward_data", "cx_nn_conv_backward_weight_scratch",
     "cx_nn_conv_backward_weight", "cx_nn_relu_backward", "cx_nn_add", "cx_nn_pool2", "cx_nn_up2", "cx_nn_mse",
     "cx_nn_adam", "cx_nn_cast_bf16", "cx_nn_conv_forward_f32", "cx_nn_smooth", "cx_nn_packed_weights",
-    "cx_nn_pack_weights", "cx_nn_conv_tc_tile", "cx_nn_conv_forward_tc",
+    "cx_nn_pack_weights", "cx_nn_conv_tc_tile", "cx_nn_conv_forward_tc", "cx_nn_conv_backward_weight_tc",
     # include/cxarc.h (three species)
     "cx3_workspace_size", "cx3_create", "cx3_set_initial", "cx3_forward", "cx3_adjoint", "cx3_gradient",
     "cx3_step", "cx3_get_fields", "cx3_get_norms", "cx3_set_staging", "cx3_set_timing", "cx3_get_timing",
@@ -177,6 +177,7 @@ def load():
         "cx_nn_pack_weights": [vp, cint, cint, cint, vp, vp, vp],
         "cx_nn_conv_forward_tc": [vp, vp, vp, vp, cint, cint, cint, cint, cint, cint, cint, vp, vp],
         "cx_nn_conv_backward_weight": [vp, vp, vp, vp, vp, cint, cint, cint, cint, cint, cint, cint, vp],
+        "cx_nn_conv_backward_weight_tc": [vp, vp, vp, vp, vp, cint, cint, cint, cint, cint, cint, cint, vp, vp],
         "cx_nn_relu_backward": [vp, vp, vp, ctypes.c_size_t, vp],
         "cx_nn_add": [vp, vp, vp, ctypes.c_size_t, vp],
         "cx_nn_pool2": [vp, vp, cint, cint, cint, cint, vp],

@@ -101,17 +101,31 @@ class UNet:
                                                1 if relu else 0, self._s()), "cx_nn_conv_forward")
         return y
 
+    @staticmethod
+    def wgrad_on_tcgen05(cin, H, W, ks):
+        """Whether the 3x3 weight gradient runs on the tcgen05 kernel: measured
+        faster from 64x64 pixels up (up to 2x), and at 32x32 with 128 or more
+        input channels; the mma.sync kernel wins on the small deep levels
+        (fewer pixel tiles than the tensor-core pipeline needs to fill)."""
+        return ks == 3 and H % 8 == 0 and W % 8 == 0 and (H * W >= 4096 or (H * W >= 1024 and cin >= 128))
+
     def _conv_back(self, c: Conv, x, dy, need_dx=True):
         B, _, H, W = x.shape
         # split the pixel tiles so that about 2 blocks per SM run (fewer partials to reduce)
         ntiles = B * ((H + 7) // 8) * ((W + 7) // 8)
-        base = ((c.cin + 15) // 16) * ((c.cout + 63) // 64)
+        tc = self.wgrad_on_tcgen05(c.cin, H, W, c.ks)
+        base = ((c.cin + 15) // 16) * ((c.cout + 127) // 128 if tc else (c.cout + 63) // 64)
         splits = int(max(1, min(ntiles, -(-304 // base))))
         nbytes = self.lib.cx_nn_conv_backward_weight_scratch(B, c.cin, c.cout, H, W, c.ks, splits)
         scratch = torch.empty(max(1, nbytes // 4), dtype=torch.float32, device=self.device)
-        _lib.check(self.lib.cx_nn_conv_backward_weight(_p(x), _p(dy), _p(c.gw), _p(c.gb), _p(scratch), splits, B,
-                                                       c.cin, c.cout, H, W, c.ks, self._s()),
-                   "cx_nn_conv_backward_weight")
+        if tc:
+            _lib.check(self.lib.cx_nn_conv_backward_weight_tc(_p(x), _p(dy), _p(c.gw), _p(c.gb), _p(scratch), splits,
+                                                              B, c.cin, c.cout, H, W, c.ks, None, self._s()),
+                       "cx_nn_conv_backward_weight_tc")
+        else:
+            _lib.check(self.lib.cx_nn_conv_backward_weight(_p(x), _p(dy), _p(c.gw), _p(c.gb), _p(scratch), splits, B,
+                                                           c.cin, c.cout, H, W, c.ks, self._s()),
+                       "cx_nn_conv_backward_weight")
         if not need_dx:
             return None
         dx = self._new(B, c.cin, H, W)

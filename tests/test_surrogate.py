@@ -303,3 +303,45 @@ def test_conv_forward_tcgen05(B, Cin, Cout, H, W, ks, relu):
     d = (y.double() - y2.double()).abs().max().item()
     print(f"tcgen05 vs mma.sync max |diff| {d:.3e}")
     assert d <= 2.0 ** -7 * y2.double().abs().max().item()
+
+
+@pytest.mark.parametrize("B,Cin,Cout,H,W", [
+    (2, 40, 72, 16, 24),    # ragged input chunk, fewer than 128 output channels
+    (1, 6, 32, 32, 32),     # the first layer (6 inputs, one chunk mostly padding)
+    (2, 64, 256, 16, 16),   # two 128-channel output tiles
+    (1, 256, 128, 8, 8),    # deep level: one pixel tile, 16 input chunks
+    (3, 32, 32, 24, 40),    # tiles at every image border
+])
+def test_conv_backward_weight_tcgen05(B, Cin, Cout, H, W):
+    """3x3 weight and bias gradients on the tcgen05 tensor cores against the
+    FP64 reference and the mma.sync kernel, with 1, a few and more splits
+    than pixel tiles (empty splits write zeros)."""
+    lib, check = _lib()
+    x = bf16_data((B, Cin, H, W), 41)
+    dy = bf16_data((B, Cout, H, W), 42)
+    xd, dyd = x.cuda(), dy.cuda()
+    w = torch.zeros((Cout, Cin, 3, 3), dtype=torch.float64)
+    xr = x.double().requires_grad_(True)
+    wr = w.requires_grad_(True)
+    br = torch.zeros(Cout, dtype=torch.float64, requires_grad=True)
+    (R.conv(xr, wr, br) * dy.double()).sum().backward()
+    ntiles = B * (H // 8) * (W // 8)
+    for splits in (1, 5, ntiles + 3):
+        nbytes = lib.cx_nn_conv_backward_weight_scratch(B, Cin, Cout, H, W, 3, splits)
+        scratch = torch.full((nbytes // 4,), float("nan"), dtype=torch.float32, device="cuda")
+        dw = torch.empty((Cout, Cin, 3, 3), dtype=torch.float32, device="cuda")
+        db = torch.empty(Cout, dtype=torch.float32, device="cuda")
+        st = torch.zeros(1, dtype=torch.int32, device="cuda")
+        check(lib.cx_nn_conv_backward_weight_tc(_p(xd), _p(dyd), _p(dw), _p(db), _p(scratch), splits, B, Cin, Cout, H,
+                                                W, 3, _p(st), _s()), "bwd weight tc")
+        dw2 = torch.empty_like(dw)
+        db2 = torch.empty_like(db)
+        scratch2 = torch.empty_like(scratch)
+        check(lib.cx_nn_conv_backward_weight(_p(xd), _p(dyd), _p(dw2), _p(db2), _p(scratch2), splits, B, Cin, Cout, H,
+                                             W, 3, _s()), "bwd weight")
+        torch.cuda.synchronize()
+        assert int(st.item()) == 0
+        e_w, e_b = rel_l2(dw, wr.grad), rel_l2(db, br.grad)
+        d_w = rel_l2(dw, dw2)
+        print(f"[wgrad tcgen05 {Cin}->{Cout} {H}x{W} splits {splits}] dW {e_w:.2e} db {e_b:.2e} vs mma.sync {d_w:.2e}")
+        assert e_w < 1e-5 and e_b < 1e-5 and d_w < 1e-5
