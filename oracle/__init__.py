@@ -25,6 +25,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liboracle.so")
 _SRC = os.path.join(_HERE, "mrt_oracle.c")
+_SRC3D = os.path.join(_HERE, "d3q19_oracle.c")
 _lib = None
 
 
@@ -32,12 +33,12 @@ def build(force: bool = False) -> str:
     """Compile the oracle with gcc (portable flags: x86_64 and aarch64; the
     per-node loops run on OpenMP threads, bitwise independent of their count)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < max(
-        os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "mrt_oracle.h"))
-    ):
+    deps = [_SRC, _SRC3D, os.path.join(_HERE, "mrt_oracle.h"), os.path.join(_HERE, "d3q19_oracle.h")]
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < max(os.path.getmtime(f) for f in deps):
         tmp = _SO + f".{os.getpid()}.tmp"
         subprocess.check_call(
-            ["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-ffp-contract=off", "-fopenmp", "-o", tmp, _SRC, "-lm"]
+            ["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-ffp-contract=off", "-fopenmp", "-o", tmp, _SRC, _SRC3D,
+             "-lm"]
         )
         os.replace(tmp, _SO)
     return _SO
@@ -536,3 +537,126 @@ def from_workload3(w, N=None) -> Problem3:
                     u_tgt=w.u_tgt, d=w.d, a=w.a_fields(), chi1=w.chi1, chi2=w.chi2, a1=w.a1, a2=w.a2, b1=w.b1,
                     b2=w.b2, b3=w.b3, c1=w.c1, c2=w.c2, ctrl_species=w.ctrl_species, alpha=w.alpha,
                     s=tuple(w.s), source_order=w.source_order)
+
+
+# ------------------------------------------------------------------ D3Q19
+class _Problem3D(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("N", ctypes.c_int),
+        ("tau", ctypes.c_double),
+        ("Du", ctypes.c_void_p), ("Dv", ctypes.c_void_p), ("a", ctypes.c_void_p),
+        ("u0", ctypes.c_void_p), ("v0", ctypes.c_void_p), ("u_tgt", ctypes.c_void_p),
+        ("d_u", ctypes.c_double), ("d_v", ctypes.c_double), ("chi", ctypes.c_double),
+        ("r_vu", ctypes.c_double), ("r_vv", ctypes.c_double), ("alpha", ctypes.c_double),
+        ("s", ctypes.c_double * 7), ("source_order", ctypes.c_int),
+    ]
+
+
+@dataclass
+class Problem3D:
+    """Two-species problem on the D3Q19 lattice in the oracle's layout (see
+    d3q19_oracle.h): node fields [nz][ny][nx], tensors [nz][ny][nx][6]
+    (Dxx, Dxy, Dxz, Dyy, Dyz, Dzz), velocity [nz][ny][nx][3] or None."""
+
+    nx: int
+    ny: int
+    nz: int
+    N: int
+    Du: np.ndarray
+    Dv: np.ndarray
+    u0: np.ndarray
+    v0: np.ndarray
+    u_tgt: np.ndarray
+    a: np.ndarray | None = None
+    d_u: float = 1.0
+    d_v: float = 1.0
+    chi: float = 0.0
+    r_vu: float = 0.0
+    r_vv: float = 0.0
+    alpha: float = 0.0
+    s: tuple = (1.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0)
+    source_order: int = 2
+    tau: float = 1.0
+    _keep: list = field(default_factory=list, repr=False)
+
+    def _struct(self):
+        arrs = dict(Du=_f64(self.Du), Dv=_f64(self.Dv), a=_f64(self.a), u0=_f64(self.u0), v0=_f64(self.v0),
+                    u_tgt=_f64(self.u_tgt))
+        self._keep = list(arrs.values())
+        st = _Problem3D()
+        st.nx, st.ny, st.nz, st.N, st.tau = self.nx, self.ny, self.nz, self.N, self.tau
+        for k, v in arrs.items():
+            setattr(st, k, _ptr(v))
+        for k in ("d_u", "d_v", "chi", "r_vu", "r_vv", "alpha"):
+            setattr(st, k, float(getattr(self, k)))
+        st.s = (ctypes.c_double * 7)(*self.s)
+        st.source_order = self.source_order
+        return st
+
+
+def _load3d():
+    lib = _load()
+    if not hasattr(lib, "_od3_ready"):
+        P = ctypes.POINTER(_Problem3D)
+        vp, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)
+        lib.od3_lattice.argtypes = [vp, vp, vp]
+        lib.od3_forward.argtypes = [P, vp, dp, vp, vp]
+        lib.od3_forward_trace.argtypes = [P, vp, vp, vp, vp]
+        lib.od3_tlm.argtypes = [P, vp, vp, vp, vp, vp]
+        lib.od3_adjoint.argtypes = [P, vp, vp, vp, vp, vp, dp]
+        lib.od3_set_threads.argtypes = [ctypes.c_int]
+        lib._od3_ready = True
+    return lib
+
+
+def lattice3d():
+    """D3Q19 tables of the oracle: e [19][3], w [19], M [19][19]."""
+    lib = _load3d()
+    e = np.zeros((19, 3), dtype=np.int32)
+    w = np.zeros(19)
+    M = np.zeros((19, 19))
+    _check(lib.od3_lattice(_ptr(e), _ptr(w), _ptr(M)), "lattice3d")
+    return e, w, M
+
+
+def forward3d(p: Problem3D, g=None):
+    """D3Q19 forward solve.  Returns (J, u^N, v^N), fields [nz][ny][nx]."""
+    lib = _load3d()
+    st = p._struct()
+    J = ctypes.c_double(0.0)
+    u = np.zeros((p.nz, p.ny, p.nx))
+    v = np.zeros_like(u)
+    _check(lib.od3_forward(ctypes.byref(st), _ptr(_f64(g)), ctypes.byref(J), _ptr(u), _ptr(v)), "forward3d")
+    return J.value, u, v
+
+
+def forward3d_trace(p: Problem3D, g=None):
+    """Per step: mass of u, mass of v (before collision), sum of Phi_v."""
+    lib = _load3d()
+    st = p._struct()
+    mu, mv, sp = np.zeros(p.N), np.zeros(p.N), np.zeros(p.N)
+    _check(lib.od3_forward_trace(ctypes.byref(st), _ptr(_f64(g)), _ptr(mu), _ptr(mv), _ptr(sp)), "forward3d_trace")
+    return mu, mv, sp
+
+
+def tlm3d(p: Problem3D, g, dg, df0=None):
+    """Tangent-linear model.  Returns (du^N, dv^N)."""
+    lib = _load3d()
+    st = p._struct()
+    du = np.zeros((p.nz, p.ny, p.nx))
+    dv = np.zeros_like(du)
+    _check(lib.od3_tlm(ctypes.byref(st), _ptr(_f64(g)), _ptr(_f64(dg)), _ptr(_f64(df0)), _ptr(du), _ptr(dv)),
+           "tlm3d")
+    return du, dv
+
+
+def adjoint3d(p: Problem3D, g=None, seed_u=None, seed_v=None, want_psi0=False):
+    """Exact discrete adjoint.  Returns (J, dJ/dg [N][nz][ny][nx], psi0 [nz][ny][nx][2][19] or None)."""
+    lib = _load3d()
+    st = p._struct()
+    J = ctypes.c_double(0.0)
+    E = np.zeros((p.N, p.nz, p.ny, p.nx))
+    psi0 = np.zeros((p.nz, p.ny, p.nx, 2, 19)) if want_psi0 else None
+    _check(lib.od3_adjoint(ctypes.byref(st), _ptr(_f64(g)), _ptr(_f64(seed_u)), _ptr(_f64(seed_v)), _ptr(E),
+                           _ptr(psi0), ctypes.byref(J)), "adjoint3d")
+    return J.value, E, psi0
