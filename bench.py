@@ -737,6 +737,104 @@ def run_arc(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+# algorithmic bytes per node and step of the D3Q19 kernels (FP32, two species):
+#   forward   38 pulls + 38 stores (304) + g (4) + Phi in/out (8)                       = 316
+#   recompute forward + tape (u, G_x, G_y, G_z) store (16)                               = 332
+#   adjoint   304 + tape read (16) + sigma in/out (8) + g (4) + dJ/dg (4)                = 336
+BYTES3D = dict(forward=316, recompute=332, adjoint=336)
+
+
+def run_d3q19(args, rank, world, local):
+    """The two-species problem on a 128^3 D3Q19 lattice (FP32, 500 steps,
+    checkpoint every 50, constant rotated tensors, shear convection):
+    gradient evaluations with per-phase kernel times and HBM fractions, and
+    the FP32 error against the FP64 oracle on a 24^3 run of the same physics."""
+    import numpy as np
+    import torch
+
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1908_03876_gb300.build import build
+
+    build()
+    from paper_1908_03876_gb300 import workloads as W
+    from paper_1908_03876_gb300.d3 import D3Problem
+
+    n = 128
+    N, k = (10, 5) if args.profile else (500, 50)
+    w = W.aniso3d(n, N, seed=6, precision=32, ckpt_every=k)
+    p = D3Problem(w, device=dev)
+    g = torch.as_tensor(w.random_control(100, 0.01), dtype=torch.float32, device=dev).contiguous()
+    E = torch.empty_like(g)
+    for _ in range(args.warmup):
+        p.gradient(g, out=E)
+    torch.cuda.synchronize()
+    if args.profile:
+        print(json.dumps({"profile": f"d3q19 {n}^3, {N} steps: gradient evaluations"}))
+        return
+    clocks = Clocks()
+    clocks.start()
+    p.set_timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(p.stream)
+    for _ in range(args.steps):
+        p.gradient(g, out=E)
+    e1.record(p.stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop(local)
+    ms = e0.elapsed_time(e1) / args.steps
+    phases = p.timing()
+    p.set_timing(False)
+    J, gsq, _ = p.norms()
+    nodes = n ** 3
+    hbm, peak_kind = _peaks()
+    kern = {}
+    for ph in ("forward", "recompute", "adjoint"):
+        t, c = phases[ph]
+        if c > 0:
+            us = t * 1e3 / c
+            ach = BYTES3D[ph] * nodes / (us * 1e-6) / 1e9
+            kern[ph] = {"us_per_launch": us, "achieved": ach, "frac": ach / hbm, "launches": c,
+                        "bytes_per_node": BYTES3D[ph]}
+    dom = max(kern, key=lambda q: kern[q]["us_per_launch"] * kern[q]["launches"])
+    kname = {"forward": "k3d_forward", "recompute": "k3d_forward", "adjoint": "k3d_adjoint"}[dom]
+    roof = {"bound": "hbm", "achieved": kern[dom]["achieved"], "peak": hbm, "unit": "GB/s",
+            "frac": kern[dom]["frac"], "traffic": _traffic(kname), "kernel": kname, "peak_source": peak_kind,
+            "bytes_per_launch": BYTES3D[dom] * nodes}
+    err = None
+    try:
+        import oracle
+
+        oracle.build()
+        ws = W.aniso3d(24, 100, seed=6, precision=32, ckpt_every=25)
+        ps = D3Problem(ws, device=dev)
+        gs = ws.random_control(101, 0.01)
+        Js, Es = ps.gradient(gs)
+        us, vs = (t.cpu().numpy() for t in ps.fields())
+        po = oracle.from_workload3d(ws)
+        Jo, uo, vo = oracle.forward3d(po, gs)
+        _, Eo, _ = oracle.adjoint3d(po, gs)
+        rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+        err = {"grid": "24^3", "steps": 100, "u": rel(us, uo), "v": rel(vs, vo), "dJdg": rel(Es.cpu().numpy(), Eo),
+               "J": abs(float(Js.item()) - Jo) / abs(Jo)}
+        ps.close()
+    except Exception as exc:
+        err = {"error": str(exc)[:200]}
+    line = {"metric": "fwd+adjoint MLUPS (D3Q19)", "value": nodes * N / (ms * 1e-3) / 1e6, "unit": "MLUPS",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "replicas only", "vs_baseline": None, "dtype": "f32 (FP64 reductions)",
+            "data": "synthetic (seeded)",
+            "config": {"workload": f"aniso3d{n}: {n}^3 D3Q19 FP32, two species, {N} steps, checkpoint every {k}, "
+                                   "rotated constant tensors, shear convection, chi = -0.1",
+                       "step": "one gradient evaluation (forward + recompute + exact discrete adjoint)",
+                       "l2": "inputs larger than L2 (4.2 GB control per step)"},
+            "roofline": roof, "kernels": kern, "fp32_err_vs_oracle": err, "clocks": clk,
+            "gpu_launches": (3 * N - k + 3) * args.steps, "J": J, "grad_norm": float(np.sqrt(gsq))}
+    print(json.dumps(line), flush=True)
+
+
 def run_unet_layers(args, rank, world, local):
     """Forward time of each 3x3 layer shape of the 4-level U-Net at 128x128,
     batch 16, on the tcgen05 kernel and on the mma.sync kernel (same packed
@@ -828,7 +926,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="aniso1024",
-                    choices=["aniso1024", "batch", "warmstart", "cg", "unetlayers", "fp64", "geometry4096", "arc"],
+                    choices=["aniso1024", "batch", "warmstart", "cg", "unetlayers", "fp64", "geometry4096", "arc", "d3q19"],
                     help="aniso1024 (default bench line) or batch: 256 independent problems, sizes {64..512}^2, "
                          "1000 steps, one persistent launch per step replayed as a CUDA graph")
     ap.add_argument("--staging", default=None, choices=["rows", "thread"],
@@ -872,6 +970,9 @@ def main():
         return run_fp64(args, rank, world, local)
     if args.workload == "arc":
         run_arc(args, rank, world, local)
+        return
+    if args.workload == "d3q19":
+        run_d3q19(args, rank, world, local)
         return
     if args.workload == "unetlayers":
         run_unet_layers(args, rank, world, local)

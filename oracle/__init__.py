@@ -660,3 +660,11 @@ def adjoint3d(p: Problem3D, g=None, seed_u=None, seed_v=None, want_psi0=False):
     _check(lib.od3_adjoint(ctypes.byref(st), _ptr(_f64(g)), _ptr(_f64(seed_u)), _ptr(_f64(seed_v)), _ptr(E),
                            _ptr(psi0), ctypes.byref(J)), "adjoint3d")
     return J.value, E, psi0
+
+
+def from_workload3d(w, N=None) -> Problem3D:
+    """D3Q19 oracle problem from a seeded workload (per-node fields)."""
+    Du, Dv = w.D_fields()
+    return Problem3D(nx=w.nx, ny=w.ny, nz=w.nz, N=w.N if N is None else N, Du=Du, Dv=Dv, u0=w.u0, v0=w.v0,
+                     u_tgt=w.u_tgt, a=w.a_fields(), d_u=w.d_u, d_v=w.d_v, chi=w.chi, r_vu=w.r_vu, r_vv=w.r_vv,
+                     alpha=w.alpha, s=tuple(w.s), source_order=w.source_order)

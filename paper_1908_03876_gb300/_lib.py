@@ -1,5 +1,5 @@
-"""ctypes view of the C ABI in include/cxlbm.h and include/cxarc.h (argument
-marshalling only).
+"""ctypes view of the C ABI in include/cxlbm.h, include/cxarc.h and
+include/cx3d.h (argument marshalling only).
 
 Loading fails loudly if libcxlbm.so is missing: there is no fallback path.
 """
@@ -43,6 +43,9 @@ EXPORTS = [
     "cx3_workspace_size", "cx3_create", "cx3_set_initial", "cx3_forward", "cx3_adjoint", "cx3_gradient",
     "cx3_step", "cx3_get_fields", "cx3_get_norms", "cx3_set_staging", "cx3_set_timing", "cx3_get_timing",
     "cx3_destroy",
+    # include/cx3d.h (D3Q19)
+    "cx3d_workspace_size", "cx3d_create", "cx3d_set_initial", "cx3d_forward", "cx3d_adjoint", "cx3d_gradient",
+    "cx3d_step", "cx3d_get_fields", "cx3d_get_norms", "cx3d_set_timing", "cx3d_get_timing", "cx3d_destroy",
 ]
 STATIC_SCRATCH_BYTES = 64 << 20  # CX_STATIC_SCRATCH_BYTES of include/cxlbm.h
 
@@ -94,6 +97,20 @@ class Desc3(ctypes.Structure):
     ]
 
 
+class Desc3D(ctypes.Structure):
+    """cx3d_desc of include/cx3d.h."""
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("n_steps", ctypes.c_int),
+        ("precision", ctypes.c_int), ("ckpt_every", ctypes.c_int), ("tau", ctypes.c_double), ("aniso", ctypes.c_int),
+        ("D_u", ctypes.c_double * 6), ("D_v", ctypes.c_double * 6),
+        ("D_u_field", ctypes.c_void_p), ("D_v_field", ctypes.c_void_p),
+        ("d_u", ctypes.c_double), ("d_v", ctypes.c_double),
+        ("chi", ctypes.c_double), ("r_vu", ctypes.c_double), ("r_vv", ctypes.c_double),
+        ("adv", ctypes.c_int), ("a", ctypes.c_void_p), ("u_target", ctypes.c_void_p), ("alpha", ctypes.c_double),
+        ("s", ctypes.c_double * 7), ("source_order", ctypes.c_int),
+    ]
+
+
 class CGInfo(ctypes.Structure):
     _fields_ = [("J0", ctypes.c_double), ("J", ctypes.c_double), ("lam", ctypes.c_double),
                 ("grad_sq", ctypes.c_double), ("beta", ctypes.c_double), ("trials", ctypes.c_int),
@@ -124,6 +141,7 @@ def load():
     vp, cint, dp = ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)
     D = ctypes.POINTER(Desc)
     D3 = ctypes.POINTER(Desc3)
+    DD = ctypes.POINTER(Desc3D)
     sig = {
         "cx_workspace_size": [D, ctypes.POINTER(ctypes.c_size_t)],
         "cx_create": [D, vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)],
@@ -199,6 +217,18 @@ def load():
         "cx3_set_timing": [vp, cint],
         "cx3_get_timing": [vp, dp, ctypes.POINTER(ctypes.c_longlong)],
         "cx3_destroy": [vp],
+        "cx3d_workspace_size": [DD, ctypes.POINTER(ctypes.c_size_t)],
+        "cx3d_create": [DD, vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)],
+        "cx3d_set_initial": [vp, vp, vp],
+        "cx3d_forward": [vp, vp, vp],
+        "cx3d_adjoint": [vp, vp, vp, vp, cint, vp],
+        "cx3d_gradient": [vp, vp, vp, vp],
+        "cx3d_step": [vp, vp, vp, ctypes.POINTER(StepInfo)],
+        "cx3d_get_fields": [vp, vp, vp],
+        "cx3d_get_norms": [vp, dp, dp, dp],
+        "cx3d_set_timing": [vp, cint],
+        "cx3d_get_timing": [vp, dp, ctypes.POINTER(ctypes.c_longlong)],
+        "cx3d_destroy": [vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcxlbm.so")
 SOURCES = ["cx_forward.cu", "cx_adjoint.cu", "cx_tlm.cu", "cx_cadj.cu", "cx_misc.cu", "cx_api.cu", "cx_static.cu", "cx_halo.cu", "cx_batch.cu",
-           "cx_arc.cu", "nn_kernels.cu", "nn_tc.cu"]
+           "cx_arc.cu", "cx_d3q19.cu", "nn_kernels.cu", "nn_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # Per-source flags.  The continuous adjoint is compiled without multiply-add
 # contraction: its per-thread and row-window kernels inline the same node body

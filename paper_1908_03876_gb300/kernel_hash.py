@@ -22,6 +22,8 @@ KERNEL_SOURCES = {
     "k3_forward": ("cx_device.cuh", "cx_internal.h", "cx_rows.cuh", "cx_arc.cu"),
     "k3_forward_rows": ("cx_device.cuh", "cx_internal.h", "cx_rows.cuh", "cx_arc.cu"),
     "k3_adjoint": ("cx_device.cuh", "cx_internal.h", "cx_rows.cuh", "cx_arc.cu"),
+    "k3d_forward": ("cx_device.cuh", "cx_internal.h", "cx_d3q19.cuh", "cx_d3q19_kernels.cuh", "cx_d3q19.cu"),
+    "k3d_adjoint": ("cx_device.cuh", "cx_internal.h", "cx_d3q19.cuh", "cx_d3q19_kernels.cuh", "cx_d3q19.cu"),
     "nn": ("nn_kernels.cu",),
 }
 

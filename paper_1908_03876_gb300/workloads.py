@@ -328,3 +328,102 @@ def arc(nx=1024, ny=1024, N=2000, seed=5, precision=32, ckpt_every=100, ctrl_spe
                      a1=1e-3, a2=5e-4, b1=1e-3, b2=2e-3, b3=5e-4, c1=1e-3, c2=3e-3, ctrl_species=ctrl_species,
                      adv="row", a_row=a_row, u0=u0, v0=v0, w0=np.broadcast_to(w0, (ny, nx)).copy(), u_tgt=u_tgt,
                      alpha=1e-3, ckpt_every=ckpt_every)
+
+
+def rotated_tensor3(lam, ax, ay):
+    """(Dxx, Dxy, Dxz, Dyy, Dyz, Dzz) of R diag(lam) R^T, R a rotation by ay
+    about y after ax about x (constant angles)."""
+    cx, sx, cy, sy = np.cos(ax), np.sin(ax), np.cos(ay), np.sin(ay)
+    Rx = np.array([[1, 0, 0], [0, cx, -sx], [0, sx, cx]])
+    Ry = np.array([[cy, 0, sy], [0, 1, 0], [-sy, 0, cy]])
+    R = Ry @ Rx
+    D = R @ np.diag(np.asarray(lam, float)) @ R.T
+    return (D[0, 0], D[0, 1], D[0, 2], D[1, 1], D[1, 2], D[2, 2])
+
+
+@dataclass
+class Workload3D:
+    """Two-species problem on a periodic nx x ny x nz D3Q19 lattice: constant
+    ("const") or per-node ("field") tensors as (Dxx, Dxy, Dxz, Dyy, Dyz, Dzz),
+    convection none / "row" (a function of y, [ny][3]) / "field"
+    ([nz][ny][nx][3]); node fields [nz][ny][nx]; control [N][nz][ny][nx]."""
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    N: int
+    precision: int = 64
+    aniso: str = "const"
+    D_u_const: tuple = (0.05, 0.0, 0.0, 0.05, 0.0, 0.05)
+    D_v_const: tuple = (0.2, 0.0, 0.0, 0.2, 0.0, 0.2)
+    D_u_field: np.ndarray | None = None
+    D_v_field: np.ndarray | None = None
+    d_u: float = 1.0
+    d_v: float = 1.0
+    chi: float = -0.1
+    r_vu: float = 0.5
+    r_vv: float = -0.1
+    adv: str = "none"
+    a_row: np.ndarray | None = None
+    a_field: np.ndarray | None = None
+    u0: np.ndarray = None
+    v0: np.ndarray = None
+    u_tgt: np.ndarray = None
+    alpha: float = 1e-3
+    s: tuple = (1.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0)
+    source_order: int = 2
+    ckpt_every: int = 0
+
+    @property
+    def ctrl_shape(self):
+        return (self.N, self.nz, self.ny, self.nx)
+
+    def D_fields(self):
+        """Per-node tensors of u and v, [nz, ny, nx, 6] each."""
+        if self.aniso == "field":
+            return self.D_u_field, self.D_v_field
+        shape = (self.nz, self.ny, self.nx, 6)
+        return (np.broadcast_to(np.asarray(self.D_u_const, float), shape).copy(),
+                np.broadcast_to(np.asarray(self.D_v_const, float), shape).copy())
+
+    def a_fields(self):
+        if self.adv == "none":
+            return None
+        if self.adv == "row":
+            return np.broadcast_to(self.a_row[None, :, None, :], (self.nz, self.ny, self.nx, 3)).copy()
+        return self.a_field
+
+    def random_control(self, seed: int, scale: float = 0.01):
+        return scale * np.random.default_rng(seed).standard_normal(self.ctrl_shape)
+
+
+def aniso3d(n=128, N=500, seed=6, precision=32, ckpt_every=50, nx=None, ny=None, nz=None):
+    """Anisotropic three-dimensional problem (D3Q19): constant rotated tensors
+    D_u = R diag(0.08, 0.04, 0.02) R^T, D_v = R' diag(0.12, 0.08, 0.04) R'^T
+    (seeded angles), shear convection a = (0.05 sin(2 pi y / L), 0, 0),
+    chi = -0.1, Phi_v = 0.5 u - 0.1 v + g; u0 = 1 + 0.2 * four seeded
+    periodic Gaussian bumps (sigma L/16), v0 = 0, target one centred bump
+    (sigma L/8)."""
+    nx, ny, nz = nx or n, ny or n, nz or n
+    rng = np.random.default_rng(seed)
+    angs = rng.uniform(0, np.pi, 4)
+    y = np.arange(ny)
+    a_row = np.stack([0.05 * np.sin(2 * np.pi * y / ny), np.zeros(ny), np.zeros(ny)], axis=-1)
+    sig = nx / 16.0
+
+    def g3(c, s):
+        X = np.arange(nx)[None, None, :]
+        Y = np.arange(ny)[None, :, None]
+        Z = np.arange(nz)[:, None, None]
+        d = [np.minimum(np.abs(q - cq), L - np.abs(q - cq)) for q, cq, L in ((X, c[0], nx), (Y, c[1], ny), (Z, c[2], nz))]
+        return np.exp(-(d[0] ** 2 + d[1] ** 2 + d[2] ** 2) / (2 * s * s))
+
+    u0 = np.ones((nz, ny, nx))
+    for c in rng.uniform(0, 1, size=(4, 3)):
+        u0 = u0 + 0.2 * g3((c[0] * nx, c[1] * ny, c[2] * nz), sig)
+    u_tgt = 1.0 + 0.2 * g3((nx / 2, ny / 2, nz / 2), 2 * sig)
+    return Workload3D(name="aniso3d", nx=nx, ny=ny, nz=nz, N=N, precision=precision, aniso="const",
+                      D_u_const=rotated_tensor3((0.08, 0.04, 0.02), angs[0], angs[1]),
+                      D_v_const=rotated_tensor3((0.12, 0.08, 0.04), angs[2], angs[3]),
+                      chi=-0.1, r_vu=0.5, r_vv=-0.1, adv="row", a_row=a_row, u0=u0, v0=np.zeros((nz, ny, nx)),
+                      u_tgt=u_tgt, alpha=1e-3, ckpt_every=ckpt_every)

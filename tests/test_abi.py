@@ -173,3 +173,51 @@ def test_arc_workspace_size_and_validation(lib):
     h = ctypes.c_void_p()
     assert so.cx3_create(ctypes.byref(_desc3(mod)), ctypes.c_void_p(0x1001), 1 << 30, None, ctypes.byref(h)) == 2
     assert so.cx3_create(ctypes.byref(_desc3(mod)), ctypes.c_void_p(0x1000), 16, None, ctypes.byref(h)) == 2
+
+
+def test_d3q19_desc_layout_and_validation(lib, tmp_path):
+    """ctypes Desc3D layout equals cx3d_desc of include/cx3d.h; host-side
+    validation and workspace sizing of the D3Q19 solver."""
+    so, mod = lib
+    fields = [f for f, _ in mod.Desc3D._fields_]
+    src = tmp_path / "layout3d.c"
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "cx3d.h"', "int main(void){",
+             'printf("%zu\\n", sizeof(cx3d_desc));']
+    lines += [f'printf("%zu\\n", offsetof(cx3d_desc, {f}));' for f in fields]
+    lines += ["return 0;}"]
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout3d"
+    import subprocess
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    out = subprocess.check_output([str(exe)]).decode().split()
+    assert int(out[0]) == ctypes.sizeof(mod.Desc3D)
+    for f, off in zip(fields, out[1:]):
+        assert getattr(mod.Desc3D, f).offset == int(off), f
+
+    def desc(**kw):
+        d = mod.Desc3D()
+        d.nx, d.ny, d.nz, d.n_steps, d.precision, d.ckpt_every = 12, 10, 8, 9, 32, 4
+        d.tau, d.d_u, d.d_v = 1.0, 1.0, 1.0
+        d.D_u = (ctypes.c_double * 6)(0.05, 0, 0, 0.05, 0, 0.05)
+        d.D_v = (ctypes.c_double * 6)(0.2, 0, 0, 0.2, 0, 0.2)
+        d.u_target = ctypes.c_void_p(0x1000)
+        d.s = (ctypes.c_double * 7)(*([1.0] * 7))
+        d.source_order = 2
+        for k, v in kw.items():
+            setattr(d, k, v)
+        return d
+
+    n = ctypes.c_size_t(0)
+    assert so.cx3d_workspace_size(ctypes.byref(desc()), ctypes.byref(n)) == 0
+    plane = 12 * 10 * 8
+    assert n.value >= (4 * 38 + 3 * 39 + 4 * 4) * plane * 4
+    for kw in (dict(nz=2), dict(precision=16), dict(n_steps=0), dict(d_v=0.0), dict(aniso=1), dict(aniso=2),
+               dict(adv=1), dict(adv=3, a=ctypes.c_void_p(8)), dict(alpha=-1.0), dict(u_target=None),
+               dict(source_order=0)):
+        assert so.cx3d_workspace_size(ctypes.byref(desc(**kw)), ctypes.byref(n)) == 1, kw
+    h = ctypes.c_void_p()
+    assert so.cx3d_create(ctypes.byref(desc()), ctypes.c_void_p(0x1001), 1 << 30, None, ctypes.byref(h)) == 2
+    # a tensor that is not positive definite is refused before any device work
+    bad = desc()
+    bad.D_u = (ctypes.c_double * 6)(0.05, 0.2, 0, 0.05, 0, 0.05)
+    assert so.cx3d_create(ctypes.byref(bad), ctypes.c_void_p(0x1000), 1 << 30, None, ctypes.byref(h)) == 5
