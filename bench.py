@@ -1099,7 +1099,7 @@ def main():
             J_hosts = [J_host, torch.empty_like(J_host, pin_memory=True)]
             Jb = [torch.empty(1, dtype=torch.float64, device=dev) for _ in range(2)]  # J of step i, kept per buffer
             ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            ne = max(1, min(args.steps, 3))
+            ne = max(1, args.steps)  # every timed step; the first upload and the last read-back are not overlapped
             h2d_done = [torch.cuda.Event() for _ in range(2)]
             used = [torch.cuda.Event() for _ in range(2)]     # gradient i done with gb[i%2] / wrote Eb[i%2]
             d2h_done = [torch.cuda.Event() for _ in range(2)]

@@ -188,3 +188,21 @@ def test_arc_fp32_staging_forms_agree_at_1024():
     assert float(torch.linalg.norm(E1 - E0) / torch.linalg.norm(E0)) <= 1e-5
     for a, b in zip(F1, F0):
         assert float(torch.linalg.norm(a - b) / torch.linalg.norm(b)) <= 1e-6
+
+
+def test_arc_fp64_full_grid_against_oracle():
+    """The bench's full 1024^2 grid (its physics, FP64), three steps: fields,
+    J and the gradient at every node against the oracle on the same grid."""
+    w = W.arc(1024, 1024, 3, seed=5, precision=64, ckpt_every=3)
+    p = _problem(w)
+    g = w.random_control(22, 0.01)
+    _, E = p.gradient(g)
+    J = float(p.norms()[0])
+    fields = [t.cpu().numpy() for t in p.fields()]
+    po = oracle.from_workload3(w)
+    Jo, uvw = oracle.forward3(po, g)
+    assert abs(J - Jo) <= 1e-12 * abs(Jo)
+    for a, b in zip(fields, uvw):
+        assert _rel(a, b) <= 1e-12
+    _, Eo, _ = oracle.adjoint3(po, g)
+    assert _rel(E.cpu().numpy(), Eo) <= 1e-12

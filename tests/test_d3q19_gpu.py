@@ -139,3 +139,21 @@ def test_d3q19_fp64_directional_derivative_64():
     fd = (float(p.forward(g + h * d).item()) - float(p.forward(g - h * d).item())) / (2 * h)
     print("directional", dd, fd)
     assert abs(dd - fd) <= 1e-5 * abs(dd)
+
+
+def test_d3q19_fp64_full_grid_against_oracle():
+    """The bench's full 128^3 grid (its physics, FP64), three steps: fields and
+    J against the oracle run on the same grid, and the gradient of the first
+    step at every node."""
+    w = W.aniso3d(128, 3, seed=6, precision=64, ckpt_every=3)
+    p = _problem(w)
+    g = w.random_control(21, 0.01)
+    _, E = p.gradient(g)
+    J = float(p.norms()[0])
+    u, v = (t.cpu().numpy() for t in p.fields())
+    po = oracle.from_workload3d(w)
+    Jo, uo, vo = oracle.forward3d(po, g)
+    assert abs(J - Jo) <= 1e-12 * abs(Jo)
+    assert _rel(u, uo) <= 1e-12 and _rel(v, vo) <= 1e-12
+    _, Eo, _ = oracle.adjoint3d(po, g)
+    assert _rel(E.cpu().numpy(), Eo) <= 1e-12
