@@ -274,11 +274,100 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def run_batch(args, rank, world, local):
-    """Aggregate MLUPS of many independent problems in one persistent launch per
-    step, replayed as a CUDA graph; problems are sharded over ranks (no
-    collective on the data path)."""
+def batch_block(dev, problems=256, N=1000, steps=2, warmup=1, staging="thread", profile=False, rank=0, world=1,
+                dist=None):
+    """Many independent problems in one persistent launch per step, replayed
+    as a CUDA graph (problems {64..512}^2, N steps, checkpoint every 100),
+    sharded over ranks with no collective on the data path: aggregate MLUPS of
+    gradient evaluations, the HBM fraction of all lattice launches, and the
+    per-problem FP32 gradient error against the FP64 oracle on a sample."""
     import numpy as np
+    import torch
+
+    from paper_1908_03876_gb300 import autotune, sharding
+    from paper_1908_03876_gb300 import workloads as W
+    from paper_1908_03876_gb300.batch import Batch
+
+    if profile:  # small profiling case: 20 steps, k = 10, default tiles
+        allw = W.batch_workloads(problems, N=20, seed=3, ckpt_every=10)
+    else:
+        allw = W.batch_workloads(problems, N=N, seed=3)
+    mine = sharding.my_problems(allw, rank, world)
+    b = Batch(mine, device=dev)
+    b.set_staging(staging == "rows")
+    # seeded controls drawn on the device (N x nodes values per problem)
+    gs = []
+    for i, w in enumerate(mine):
+        gen = torch.Generator(device=dev).manual_seed(500 + i)
+        gs.append(0.01 * torch.randn(w.ctrl_shape, generator=gen, dtype=torch.float32, device=dev))
+    b.bind(gs)
+    t0 = time.perf_counter()
+    if profile:
+        cfg = {"threads": 256, "tile_x": {s: 256 for s in (64, 128, 256, 512)}, "rows": {}}
+        autotune.apply(b, cfg)
+    else:
+        cfg = autotune.autotune(b, probe_steps=12)
+    t_tune = time.perf_counter() - t0
+    nodes = sum(w.nx * w.ny for w in mine)
+    Nn = mine[0].N
+    for _ in range(warmup):
+        b.gradient()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(b.stream)
+    for _ in range(steps):
+        b.gradient()
+    e1.record(b.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    b.status()
+    ms, all_nodes = sharding.aggregate(ms, float(nodes))
+    mlups = all_nodes * Nn / (ms * 1e-3) / 1e6
+    hbm, peak_kind = _peaks()
+    k = mine[0].ckpt_every
+    byts = all_nodes * (Nn * BYTES["forward"] + (Nn - k) * BYTES["recompute"] + Nn * BYTES["adjoint"])
+    ach = byts / (ms * 1e-3) / world / 1e9
+    b.close()
+    del gs
+    torch.cuda.empty_cache()
+    err = [float("nan")]
+    if rank == 0 and not profile:
+        err = []
+        import oracle
+
+        oracle.build()
+        sample = [W.batch_workloads(problems, N=6, seed=3, ckpt_every=3)[i] for i in (0, 1, 2, 3, 5, 8)]
+        sb = Batch(sample, device=dev)
+        sg = [torch.as_tensor(w.random_control(700 + i, 0.01), dtype=torch.float32, device=dev)
+              for i, w in enumerate(sample)]
+        sb.bind(sg)
+        autotune.apply(sb, {"threads": cfg["threads"], "tile_x": {w.nx: cfg["tile_x"].get(w.nx, 64) for w in sample},
+                            "rows": cfg.get("rows", {})})
+        sb.gradient()
+        torch.cuda.synchronize()
+        for i, w in enumerate(sample):
+            _, Eo, _ = oracle.adjoint(oracle.from_workload(w), sg[i].double().cpu().numpy())
+            E = sb.E[i].double().cpu().numpy()
+            err.append(float(np.linalg.norm(E - Eo) / np.linalg.norm(Eo)))
+        sb.close()
+    kern = "k_batch_rows" if staging == "rows" else "k_batch"
+    return {"workload": f"batch: {problems} problems, nx, ny in {{64,128,256,512}}, {Nn} steps, checkpoint every "
+                        f"{k}, one persistent launch per step, CUDA graph",
+            "mlups": mlups, "ms_per_gradient": ms, "nodes": all_nodes, "steps": steps, "warmup": warmup,
+            "tiles": cfg, "autotune_s": t_tune, "staging": staging,
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                         "traffic": _batch_traffic(all_nodes / world, kern),
+                         "kernel": kern + " (all lattice launches of the step)", "peak_source": peak_kind},
+            "per_problem_grad_rel_err_fp32_vs_oracle": {"sample": "6 problems, 6 steps", "max": max(err),
+                                                        "values": err},
+            "gpu_launches": steps * (Nn + len(mine) + 1 + 1 + max(0, Nn // k - 2) + (Nn - k) + Nn + 1)}
+
+
+def run_batch(args, rank, world, local):
+    """The batched workload (batch_block) as its own bench line."""
     import torch
 
     dist = None
@@ -294,99 +383,26 @@ def run_batch(args, rank, world, local):
         build()
     if dist:
         dist.barrier()
-    from paper_1908_03876_gb300 import autotune
-    from paper_1908_03876_gb300 import workloads as W
-    from paper_1908_03876_gb300.batch import Batch
-
-    from paper_1908_03876_gb300 import sharding
-
-    if args.profile:  # small profiling case: 20 steps, k = 10, default tiles
-        allw = W.batch_workloads(args.problems, N=20, seed=3, ckpt_every=10)
-    else:
-        allw = W.batch_workloads(args.problems, N=1000, seed=3)
-    mine = sharding.my_problems(allw, rank, world)
-    b = Batch(mine, device=dev)
-    args.staging = args.staging or "thread"
-    b.set_staging(args.staging == "rows")
-    gs = [torch.as_tensor(w.random_control(500 + i, 0.01), dtype=torch.float32, device=dev) for i, w in enumerate(mine)]
-    b.bind(gs)
-    t0 = time.perf_counter()
-    if args.profile:
-        cfg = {"threads": 256, "tile_x": {s: 256 for s in (64, 128, 256, 512)}, "rows": {}}
-        autotune.apply(b, cfg)
-    else:
-        cfg = autotune.autotune(b, probe_steps=12)
-    t_tune = time.perf_counter() - t0
-    nodes = sum(w.nx * w.ny for w in mine)
-    N = mine[0].N
-    for _ in range(args.warmup):
-        b.gradient()
-    torch.cuda.synchronize()
     clocks = Clocks()
     if rank == 0:
         clocks.start()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(b.stream)
-    for _ in range(args.steps):
-        b.gradient()
-    e1.record(b.stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
+    res = batch_block(dev, problems=args.problems, steps=args.steps, warmup=args.warmup,
+                      staging=args.staging or "thread", profile=args.profile, rank=rank, world=world, dist=dist)
     clk = clocks.stop(local) if rank == 0 else None
-    b.status()
-    ms, all_nodes = sharding.aggregate(ms, float(nodes))
-    mlups = all_nodes * N / (ms * 1e-3) / 1e6
-    hbm, peak_kind = _peaks()
-    k = mine[0].ckpt_every
-    byts = all_nodes * (N * BYTES["forward"] + (N - k) * BYTES["recompute"] + N * BYTES["adjoint"])
-    ach = byts / (ms * 1e-3) / world / 1e9
-    b.close()
-    del gs
-    torch.cuda.empty_cache()
-    # per-problem gradient error against the FP64 oracle on a sample
-    err = [float("nan")]
-    if rank == 0 and not args.profile:
-        err = []
-        import oracle
-
-        oracle.build()
-        sample = [W.batch_workloads(args.problems, N=6, seed=3, ckpt_every=3)[i] for i in (0, 1, 2, 3, 5, 8)]
-        sb = Batch(sample, device=dev)
-        sg = [torch.as_tensor(w.random_control(700 + i, 0.01), dtype=torch.float32, device=dev)
-              for i, w in enumerate(sample)]
-        sb.bind(sg)
-        autotune.apply(sb, {"threads": cfg["threads"], "tile_x": {w.nx: cfg["tile_x"].get(w.nx, 64) for w in sample},
-                            "rows": cfg.get("rows", {})})
-        sb.gradient()
-        torch.cuda.synchronize()
-        for i, w in enumerate(sample):
-            _, Eo, _ = oracle.adjoint(oracle.from_workload(w), sg[i].double().cpu().numpy())
-            E = sb.E[i].double().cpu().numpy()
-            err.append(float(np.linalg.norm(E - Eo) / np.linalg.norm(Eo)))
     if rank == 0:
         line = {
-            "metric": "fwd+adjoint MLUPS (batched)", "value": mlups, "unit": "MLUPS", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 reductions)", "data": "synthetic (seeded)",
-            "config": {"workload": f"batch: {args.problems} problems, nx, ny in {{64,128,256,512}}, 1000 steps, "
-                                   "checkpoint every 100, one persistent launch per step, CUDA graph",
-                       "nodes": all_nodes, "tiles": cfg, "autotune_s": t_tune, "staging": args.staging,
-                       "l2": "inputs larger than L2"},
-            "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                         "traffic": _batch_traffic(all_nodes / world,
-                                                   "k_batch_rows" if args.staging == "rows" else "k_batch"),
-                         "kernel": ("k_batch_rows" if args.staging == "rows" else "k_batch")
-                                   + " (all lattice launches of the step)",
-                         "peak_source": peak_kind},
-            "per_problem_grad_rel_err_fp32_vs_oracle": {"sample": "6 problems, 6 steps", "max": max(err),
-                                                        "values": err},
+            "metric": "fwd+adjoint MLUPS (batched)", "value": res["mlups"], "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_per_gradient"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 reductions)",
+            "data": "synthetic (seeded)",
+            "config": {"workload": res["workload"], "nodes": res["nodes"], "tiles": res["tiles"],
+                       "autotune_s": res["autotune_s"], "staging": res["staging"], "l2": "inputs larger than L2"},
+            "roofline": res["roofline"],
+            "per_problem_grad_rel_err_fp32_vs_oracle": res["per_problem_grad_rel_err_fp32_vs_oracle"],
             "clocks": clk, "e2e": None,
             # per gradient: N forward + one final per problem + finalize, zero sigma, S-2 Phi restores,
             # N-k recompute, N adjoint, finalize
-            "gpu_launches": args.steps * (N + len(mine) + 1 + 1 + max(0, N // k - 2) + (N - k) + N + 1),
+            "gpu_launches": res["gpu_launches"],
         }
         print(json.dumps(line), flush=True)
     if dist:
@@ -939,6 +955,8 @@ def main():
     ap.add_argument("--ws-test", type=int, default=200)
     ap.add_argument("--ws-size", type=int, default=256)
     ap.add_argument("--no-cg", action="store_true", help="leave the CG comparison out of the default bench line")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="leave the batched workload (256 problems) out of the default bench line")
     ap.add_argument("--opt-iters", type=int, default=20,
                     help="Armijo steepest-descent iterations of the default workload's optimisation leg (0: skip)")
     ap.add_argument("--ws-steps", type=int, default=256)
@@ -1164,6 +1182,12 @@ def main():
         cpu = None if args.no_cpu_baseline else cpu_baseline()
         fp32_err = None if args.profile else fp32_error_vs_oracle(dev)
         geom = None if args.profile else geometry_block(dev, args.staging)
+        bb = None
+        if not args.profile and not args.no_batch:
+            try:
+                bb = batch_block(dev)
+            except Exception as exc:
+                bb = {"error": str(exc)[:200]}
         cgb = None
         if not args.profile and not args.no_cg:
             try:
@@ -1187,6 +1211,7 @@ def main():
             "geometry4096": geom,
             "optimise": opt,
             "cg256": cgb,
+            "batch256": bb,
             "clocks": clk,
             "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps,
