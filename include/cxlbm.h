@@ -253,7 +253,9 @@ cx_status cx_cg_reset(cx_problem* p);
 cx_status cx_get_fields(cx_problem* p, void* u_out, void* v_out);
 
 /* Adjoint populations psi^0 of the last cx_adjoint: the sensitivity of the
- * seeded functional to the initial populations (device T [2][Q][ny][nx]). */
+ * seeded functional to the initial populations (device T [2][Q][ny][nx]).
+ * Solid nodes have no populations: their entries carry no meaning (on grids
+ * with solid nodes they hold the bounce-back copies of the adjoint step). */
 cx_status cx_get_psi0(cx_problem* p, void* out);
 
 /* Synchronising: cost of the last forward, ||dJ/dg||^2 and max |dJ/dg| of the

@@ -15,6 +15,9 @@
 //               lambda_Phi^n = c_n sigma^n + c'_{n+1} sigma^{n+1} + (G path),
 //               sigma^n = sum_i rho_v,i w~_i.
 // The tape (u^n, G^n) comes from the forward recompute of the segment.
+// On grids whose solid nodes carry bounce-back copies (C.bb_copy), psi_i(x)
+// with x - e_i solid is also written into plane opp(i) at x - e_i, where the
+// next adjoint step's pull of direction opp(i) at x looks.
 // In FP32, sums sum_i c_i rho_i with c_i = w_i (a + b.e_i) (sigma, and the
 // weights of the chemotactic coupling) are taken from the moments m = M0 rho
 // the collision needs anyway: sum_i c_i rho_i = sum_k (M0 c)_k m_k / |row_k|^2;
@@ -64,6 +67,19 @@ __device__ __forceinline__ void adj_stage(const CxConst& C, const Args& A, const
     if (!A.terminal) cp_async(s + (2 * Q + 3) * NT, A.sigma + k);
     if (nd.ctrl && A.g) cp_async(s + (2 * Q + 4) * NT, A.g + nd.c);
     if (C.aniso == CX_ANISO_ROTATED) cp_async(s + (2 * Q + 5) * NT, reinterpret_cast<const T*>(C.theta) + k);
+}
+
+// Bounce-back copies of one species (planes base .. base + Q - 1): psi_i(x)
+// to plane opp(i) at x - e_i for every i whose x - e_i is solid (flag bit
+// i - 1).  Each solid slot has one writer: the fluid node x = s + e_i.
+template <typename T, int Q, typename Args>
+__device__ __forceinline__ void adj_bb_copies(const CxConst& C, const Args& A, int base, int k, unsigned bits,
+                                              const T (&psi)[Q]) {
+    using L = Lat<Q>;
+    const int y = k / C.nx, x = k - y * C.nx; // rare (nodes next to a wall): recomputed, not kept in registers
+#pragma unroll
+    for (int i = 1; i < Q; ++i)
+        if ((bits >> (i - 1)) & 1u) A.out(base + L::opp(i))[nbr_index(C, x, y, -L::ex(i), -L::ey(i))] = psi[i];
 }
 
 template <typename T, int Q, int NT, typename Args, typename Stage>
@@ -179,10 +195,17 @@ __device__ __forceinline__ void adj_compute(const CxConst& C, const KConst<T>& K
     } else if (nd.c >= 0) {
         A.dJdg[nd.c] = T(0);
     }
+    const unsigned bbc = (Stage::copies && C.bb_copy) ? S.bb_bits(C, k) : 0u;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        A.out(i)[k] = psu[i] + adj_Tu;
-        A.out(Q + i)[k] = psv[i] + adj_Tv + T(L::ex(i)) * ajx + T(L::ey(i)) * ajy;
+        psu[i] = psu[i] + adj_Tu;
+        psv[i] = psv[i] + adj_Tv + T(L::ex(i)) * ajx + T(L::ey(i)) * ajy;
+        A.out(i)[k] = psu[i];
+        A.out(Q + i)[k] = psv[i];
+    }
+    if (Stage::copies && bbc) {
+        adj_bb_copies<T, Q>(C, A, 0, k, bbc, psu);
+        adj_bb_copies<T, Q>(C, A, Q, k, bbc, psv);
     }
 }
 

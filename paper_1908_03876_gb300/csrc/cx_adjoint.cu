@@ -31,7 +31,9 @@
 
 namespace cx {
 
-template <typename T, int Q, int NT>
+// BB: the grid's solid nodes carry bounce-back copies (C.bb_copy), which the
+// kernel writes; a separate instantiation keeps the other grids' code as it is.
+template <typename T, int Q, int NT, bool BB>
 __global__ void __launch_bounds__(NT) k_adjoint(const CxConst C, const KConst<T> KC, const AdjArgs<T> A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int NV = adj_stage_values<Q>();
@@ -51,7 +53,7 @@ __global__ void __launch_bounds__(NT) k_adjoint(const CxConst C, const KConst<T>
         if (it.valid()) adj_stage<T, Q, NT, AdjArgs<T>>(C, A, nxt, odd ? s0 : s1);
         cp_async_commit();
         cp_async_wait<1>();
-        adj_compute<T, Q, NT, AdjArgs<T>>(C, KC, A, cur, ThreadSlots<T, NT>{odd ? s1 : s0}, acc);
+        adj_compute<T, Q, NT, AdjArgs<T>>(C, KC, A, cur, ThreadSlots<T, NT, BB>{odd ? s1 : s0}, acc);
         cur = nxt;
         odd = !odd;
     }
@@ -60,14 +62,14 @@ __global__ void __launch_bounds__(NT) k_adjoint(const CxConst C, const KConst<T>
     acc.flush(A.e2_part + w, A.emax_part + w);
 }
 
-template <typename T, int Q, int NT>
-static cudaError_t launch_qn(const CxConst& C, const KConst<T>& K, const AdjArgs<T>& A, const Launch& L,
-                             cudaStream_t s) {
+template <typename T, int Q, int NT, bool BB>
+static cudaError_t launch_qnb(const CxConst& C, const KConst<T>& K, const AdjArgs<T>& A, const Launch& L,
+                              cudaStream_t s) {
     const size_t smem = (size_t)2 * adj_stage_values<Q>() * NT * sizeof(T);
     static bool attr_set = false; // the attribute belongs to the function, once per process
     if (!attr_set) {
         cudaError_t e =
-            cudaFuncSetAttribute(k_adjoint<T, Q, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 112 * 1024);
+            cudaFuncSetAttribute(k_adjoint<T, Q, NT, BB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 112 * 1024);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
@@ -81,7 +83,12 @@ static cudaError_t launch_qn(const CxConst& C, const KConst<T>& K, const AdjArgs
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_adjoint<T, Q, NT>, C, K, A);
+    return cudaLaunchKernelEx(&cfg, k_adjoint<T, Q, NT, BB>, C, K, A);
+}
+template <typename T, int Q, int NT>
+static cudaError_t launch_qn(const CxConst& C, const KConst<T>& K, const AdjArgs<T>& A, const Launch& L,
+                             cudaStream_t s) {
+    return C.bb_copy ? launch_qnb<T, Q, NT, true>(C, K, A, L, s) : launch_qnb<T, Q, NT, false>(C, K, A, L, s);
 }
 
 template <typename T, int Q>
@@ -142,9 +149,12 @@ template <typename T, int Q, int NT> constexpr size_t adj_rows_smem() {
     return rows_pipe_smem<T>(adj_rows_stage_values<T, Q, NT>());
 }
 
-// SB: the grid has solid nodes (bounce-back flags staged with each segment).
+// SB: 0 no solid nodes; 1 solid nodes, bounced pulls read from global memory;
+// 2 solid nodes carrying bounce-back copies (C.bb_copy), so every pull reads
+// the windows.  With solid nodes the bounce-back flags are staged with each
+// segment.
 // Block: NT compute threads and one producer warp (see cx_rows.cuh).
-template <typename T, int Q, int NT, bool SB>
+template <typename T, int Q, int NT, int SB>
 __global__ void __launch_bounds__(NT + 32, sizeof(T) == 4 ? (NT == 256 ? 3 : 5) : 1)
     k_adjoint_rows(const CxConst C, const KConst<T> KC, const AdjArgs<T> A) {
     using RW = RowWindow<T, Q, NT>;
@@ -163,9 +173,9 @@ __global__ void __launch_bounds__(NT + 32, sizeof(T) == 4 ? (NT == 256 ? 3 : 5) 
     pipe.consume(
         C, A.status, [&](const NodeIdx& nd, T* st) { adj_stage_ctrl<T, Q, NT>(C, A, nd, st); },
         [&](const NodeIdx& nd, T* st) {
-            if constexpr (SB) {
+            if constexpr (SB > 0) {
                 const unsigned bits = reinterpret_cast<const uint8_t*>(st + 2 * Q * RW::W + 6 * NT)[threadIdx.x];
-                adj_compute<T, Q, NT, AdjArgs<T>>(C, KC, A, nd, RowWindowSolid<T, Q, NT>{{st + threadIdx.x}, bits},
+                adj_compute<T, Q, NT, AdjArgs<T>>(C, KC, A, nd, RowWindowSolid<T, Q, NT, SB == 2>{{st + threadIdx.x}, bits},
                                                   acc);
             } else {
                 adj_compute<T, Q, NT, AdjArgs<T>>(C, KC, A, nd, RW{st + threadIdx.x}, acc);
@@ -191,7 +201,7 @@ template <typename T> static bool rows_eligible(const CxConst& C, const AdjArgs<
     return true;
 }
 
-template <typename T, int Q, int NT, bool SB>
+template <typename T, int Q, int NT, int SB>
 static cudaError_t launch_rows_qn(const CxConst& C, const KConst<T>& K, const AdjArgs<T>& A, const Launch& L,
                                   cudaStream_t s) {
     constexpr size_t smem = adj_rows_smem<T, Q, NT>();
@@ -220,11 +230,14 @@ static cudaError_t launch_rows_qn(const CxConst& C, const KConst<T>& K, const Ad
 template <typename T, int Q>
 static cudaError_t launch_rows_q(const CxConst& C, const KConst<T>& K, const AdjArgs<T>& A, const Launch& L,
                                  cudaStream_t s) {
+    if (C.has_solid && C.bb_copy)
+        return L.block.x == 128 ? launch_rows_qn<T, Q, 128, 2>(C, K, A, L, s)
+                                : launch_rows_qn<T, Q, 256, 2>(C, K, A, L, s);
     if (C.has_solid)
-        return L.block.x == 128 ? launch_rows_qn<T, Q, 128, true>(C, K, A, L, s)
-                                : launch_rows_qn<T, Q, 256, true>(C, K, A, L, s);
-    return L.block.x == 128 ? launch_rows_qn<T, Q, 128, false>(C, K, A, L, s)
-                            : launch_rows_qn<T, Q, 256, false>(C, K, A, L, s);
+        return L.block.x == 128 ? launch_rows_qn<T, Q, 128, 1>(C, K, A, L, s)
+                                : launch_rows_qn<T, Q, 256, 1>(C, K, A, L, s);
+    return L.block.x == 128 ? launch_rows_qn<T, Q, 128, 0>(C, K, A, L, s)
+                            : launch_rows_qn<T, Q, 256, 0>(C, K, A, L, s);
 }
 
 template <typename T>
@@ -240,24 +253,27 @@ template cudaError_t launch_adjoint<float>(const CxConst&, const KConst<float>&,
 template cudaError_t launch_adjoint<double>(const CxConst&, const KConst<double>&, const AdjArgs<double>&,
                                             const Launch&, cudaStream_t);
 
-template <typename T, int Q, int NT> static int occ_qn() {
-    cudaFuncSetAttribute(k_adjoint<T, Q, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 112 * 1024);
+template <typename T, int Q, int NT, bool BB> static int occ_qnb() {
+    cudaFuncSetAttribute(k_adjoint<T, Q, NT, BB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 112 * 1024);
     int nb = 0;
     const size_t smem = (size_t)2 * adj_stage_values<Q>() * NT * sizeof(T);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adjoint<T, Q, NT>, NT, smem) != cudaSuccess) return 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adjoint<T, Q, NT, BB>, NT, smem) != cudaSuccess) return 1;
     return nb > 0 ? nb : 1;
 }
-template <typename T, int Q> static int occ_q(int threads) {
-    return threads == 64 ? occ_qn<T, Q, 64>() : (threads == 128 ? occ_qn<T, Q, 128>() : occ_qn<T, Q, 256>());
+template <typename T, int Q, int NT> static int occ_qn(bool bb) {
+    return bb ? occ_qnb<T, Q, NT, true>() : occ_qnb<T, Q, NT, false>();
+}
+template <typename T, int Q> static int occ_q(int threads, bool bb) {
+    return threads == 64 ? occ_qn<T, Q, 64>(bb) : (threads == 128 ? occ_qn<T, Q, 128>(bb) : occ_qn<T, Q, 256>(bb));
 }
 
-template <typename T> int adjoint_occupancy(int Q, int threads) {
-    return Q == 9 ? occ_q<T, 9>(threads) : occ_q<T, 5>(threads);
+template <typename T> int adjoint_occupancy(int Q, int threads, bool bb) {
+    return Q == 9 ? occ_q<T, 9>(threads, bb) : occ_q<T, 5>(threads, bb);
 }
-template int adjoint_occupancy<float>(int, int);
-template int adjoint_occupancy<double>(int, int);
+template int adjoint_occupancy<float>(int, int, bool);
+template int adjoint_occupancy<double>(int, int, bool);
 
-template <typename T, int Q, int NT, bool SB> static int rows_occ_qnb() {
+template <typename T, int Q, int NT, int SB> static int rows_occ_qnb() {
     constexpr size_t smem = adj_rows_smem<T, Q, NT>();
     cudaFuncSetAttribute(k_adjoint_rows<T, Q, NT, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int nb = 0;
@@ -266,9 +282,9 @@ template <typename T, int Q, int NT, bool SB> static int rows_occ_qnb() {
         return 1;
     return nb > 0 ? nb : 1;
 }
-// the smaller residency of the two forms (the persistent grid serves both)
+// the smallest residency of the three forms (the persistent grid serves all)
 template <typename T, int Q, int NT> static int rows_occ_qn() {
-    return std::min(rows_occ_qnb<T, Q, NT, false>(), rows_occ_qnb<T, Q, NT, true>());
+    return std::min(rows_occ_qnb<T, Q, NT, 0>(), std::min(rows_occ_qnb<T, Q, NT, 1>(), rows_occ_qnb<T, Q, NT, 2>()));
 }
 template <typename T, int Q> static int rows_occ_q(int threads) {
     return threads == 128 ? rows_occ_qn<T, Q, 128>() : rows_occ_qn<T, Q, 256>();

@@ -749,8 +749,9 @@ static cx_status set_persistent(cx_problem* p, Launch& L, int threads, int block
 cx_status cx_set_launch(cx_problem* p, int threads, int blocks) {
     if (!p || (threads != 64 && threads != 128 && threads != 256) || blocks < 0) return CX_ERR_INVALID_ARG;
     const bool dbl = p->lay.esz == 8;
+    const bool bb = p->C.bb_copy != 0;
     const int of = dbl ? forward_occupancy<double>(p->lay.Q, threads) : forward_occupancy<float>(p->lay.Q, threads);
-    const int oa = dbl ? adjoint_occupancy<double>(p->lay.Q, threads) : adjoint_occupancy<float>(p->lay.Q, threads);
+    const int oa = dbl ? adjoint_occupancy<double>(p->lay.Q, threads, bb) : adjoint_occupancy<float>(p->lay.Q, threads, bb);
     Launch f, a;
     cx_status rc = set_persistent(p, f, threads, blocks, of);
     if (rc) return rc;
@@ -795,6 +796,7 @@ cx_status cx_create(const cx_problem_desc* desc, void* workspace, size_t bytes, 
     C.adv = desc->adv;
     C.has_solid = desc->solid ? 1 : 0;
     C.halo = desc->halo;
+    C.bb_copy = (desc->solid && !desc->halo) ? 1 : 0;
     C.ctrl_full = (desc->ctrl_nx == 0 || (desc->ctrl_x0 == 0 && desc->ctrl_y0 == 0 && desc->ctrl_nx == desc->nx &&
                                           desc->ctrl_ny == desc->ny)) &&
                   !desc->ctrl_mask && !desc->solid;

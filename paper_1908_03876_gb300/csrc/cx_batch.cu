@@ -340,6 +340,8 @@ template <typename T, int Q> struct TileWindow {
     __device__ __forceinline__ T val(int v) const { return loc[(v - 2 * Q) * nt]; }
     static constexpr bool fwd_bounce(int) { return false; } // grids with solid nodes use per-thread staging
     static constexpr bool adj_bounce(int) { return false; }
+    static constexpr bool copies = false;
+    static constexpr unsigned bb_bits(const CxConst&, int) { return 0u; }
 };
 
 // population part of a stage: 2Q planes of at most NT / 32 windows (tx >= 32)
@@ -704,6 +706,7 @@ template <typename T> cx_status upload_table(BatchHost& h) {
         BRec<T>& R = recs[i];
         std::memset(&R, 0, sizeof(R));
         R.C = p->C;
+        R.C.bb_copy = 0; // the batched kernels resolve bounce-back while staging
         R.K = p->kc((T*)nullptr);
         R.pop[ROLE_POPA] = p->at<T>(p->lay.off_popA);
         R.pop[ROLE_POPB] = p->at<T>(p->lay.off_popB);

@@ -496,13 +496,19 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
 // fwd_bounce(i) / adj_bounce(i): whether the pull of direction i bounces back
 // and must be read from the node's own opposite population instead (forward:
 // x - e_i solid; adjoint: x + e_i solid).  The per-thread staging resolves
-// bounce-back while copying, so it never reports one.
-template <typename T, int NT> struct ThreadSlots {
+// bounce-back while copying, so it never reports one.  bb_bits(C, k): the
+// node's bounce-back flags (bit i-1: x - e_i solid), which the adjoint body
+// needs to write the bounce-back copies of a grid with C.bb_copy set; copies:
+// whether the kernel writes them at all (BB: the single-problem adjoint,
+// whose output row-window kernels may read).
+template <typename T, int NT, bool BB = false> struct ThreadSlots {
     const T* s;
     __device__ __forceinline__ T pop(int j, int) const { return s[j * NT]; }
     __device__ __forceinline__ T val(int v) const { return s[v * NT]; }
     static constexpr bool fwd_bounce(int) { return false; }
     static constexpr bool adj_bounce(int) { return false; }
+    static constexpr bool copies = BB;
+    __device__ __forceinline__ unsigned bb_bits(const CxConst& C, int k) const { return __ldg(C.bounce + k); }
 };
 // RowWindow: per-block staging of a row segment [x0, x0 + NT): plane j as a
 // window of the source row starting at x0 - H (H = 16 bytes of values),
@@ -516,18 +522,36 @@ template <typename T, int Q, int NT> struct RowWindow {
     __device__ __forceinline__ T val(int v) const { return s[2 * Q * W + (v - 2 * Q) * NT]; }
     static constexpr bool fwd_bounce(int) { return false; }
     static constexpr bool adj_bounce(int) { return false; }
+    static constexpr bool copies = false;
+    static constexpr unsigned bb_bits(const CxConst&, int) { return 0u; }
 };
 // RowWindowSolid: a RowWindow on a grid with solid nodes, with the node's
 // bounce-back flags (bit i-1: x - e_i is solid), staged as one byte per node.
-// A window entry whose source is solid holds no population the node may use;
-// the node reads its own opposite population from global memory instead.
-template <typename T, int Q, int NT> struct RowWindowSolid : RowWindow<T, Q, NT> {
+// COPIES (the adjoint on a grid with C.bb_copy): the solid source of a
+// bounced pull holds the node's own opposite population, written there by the
+// previous step, so the window entry is the value to use.  Otherwise a window
+// entry whose source is solid holds no population the node may use, and the
+// node reads its own opposite population from global memory instead (the
+// forward, and sub-domains, whose halo frame the exchange overwrites).
+template <typename T, int Q, int NT, bool COPIES = false> struct RowWindowSolid : RowWindow<T, Q, NT> {
     unsigned bits;
-    __device__ __forceinline__ bool fwd_bounce(int i) const { return i != 0 && ((bits >> (i - 1)) & 1u); }
-    __device__ __forceinline__ bool adj_bounce(int i) const {
-        return i != 0 && ((bits >> (Lat<Q>::opp(i) - 1)) & 1u);
+    __device__ __forceinline__ bool fwd_bounce(int i) const {
+        return !COPIES && i != 0 && ((bits >> (i - 1)) & 1u);
     }
+    __device__ __forceinline__ bool adj_bounce(int i) const {
+        return !COPIES && i != 0 && ((bits >> (Lat<Q>::opp(i) - 1)) & 1u);
+    }
+    static constexpr bool copies = COPIES;
+    __device__ __forceinline__ unsigned bb_bits(const CxConst&, int) const { return bits; }
 };
+
+// Index of the periodic neighbour x + (dx, dy) (|dx|, |dy| <= 1) of node (x, y).
+__device__ __forceinline__ int nbr_index(const CxConst& C, int x, int y, int dx, int dy) {
+    int xn = x + dx, yn = y + dy;
+    xn = xn < 0 ? C.nx - 1 : (xn == C.nx ? 0 : xn);
+    yn = yn < 0 ? C.ny - 1 : (yn == C.ny ? 0 : yn);
+    return yn * C.nx + xn;
+}
 
 // Row windows pay when each block of the persistent grid walks several row
 // segments, so that one segment's copies run while the previous one is

@@ -17,6 +17,10 @@ struct CxConst {
     int aniso, adv, has_solid;
     int ctrl_full;                    // control window = whole grid, no mask
     int halo;                         // outer one-node frame is a halo of ghost nodes (sub-domain)
+    int bb_copy;                      // the adjoint's solid nodes carry bounce-back copies: every adjoint step
+                                      // also writes each psi_i(x) whose next pull comes back to x (x - e_i
+                                      // solid) into plane opp(i) at the solid node x - e_i, where the next
+                                      // step's row windows hold it (solid grids without a halo)
     int cx0, cy0, cnx, cny;
     int source_order;
     double tau, d_u, d_v, chi, r_vu, r_vv, alpha;
@@ -144,12 +148,15 @@ cudaError_t launch_final(const CxConst& C, const T* Pin, const T* u_tgt, T* uN, 
                          const Launch& L, cudaStream_t s);
 cudaError_t launch_finalize(const double* part_a, int na, const double* part_b, int nb, double scale_b, double* out,
                             int* status, int status_bit, int mode, cudaStream_t s);
+// resident blocks per SM of the per-thread forward kernel
 template <typename T> int forward_occupancy(int Q, int threads);
 template <typename T>
 cudaError_t launch_cadj(const CxConst& C, const KConst<T>& K, const CadjArgs<T>& A, const Launch& L, cudaStream_t s);
 template <typename T>
 cudaError_t launch_tlm(const CxConst& C, const KConst<T>& K, const TlmArgs<T>& A, const Launch& L, cudaStream_t s);
-template <typename T> int adjoint_occupancy(int Q, int threads);
+// resident blocks per SM of the per-thread adjoint kernel (bb: the form that
+// writes bounce-back copies)
+template <typename T> int adjoint_occupancy(int Q, int threads, bool bb = false);
 template <typename T>
 cudaError_t launch_axpy(T* g, const T* E, T lam, size_t n, cudaStream_t s);
 template <typename T>

@@ -156,13 +156,24 @@ def _staging_case(case):
         w = W.geometry(160, 48, 12, seed=5, precision=64, ckpt_every=4, win=40, rmin=3, rmax=7)
     elif case == "geometry32":  # 208 columns: a partial last segment for 128 and 256 threads
         w = W.geometry(208, 56, 14, seed=6, precision=32, ckpt_every=5, win=48, rmin=3, rmax=8)
+    elif case == "geometry64_periodic":  # no solid frame: fluid runs and walls across the periodic ends
+        from dataclasses import replace
+
+        w = W.geometry(160, 48, 12, seed=5, precision=64, ckpt_every=4, win=40, rmin=3, rmax=7)
+        solid = w.solid.copy()
+        solid[:, 0] = solid[:, -1] = 0
+        solid[0, :] = solid[-1, :] = 0
+        solid[10:14, 156:160] = 1  # a wall on the right end whose neighbours wrap to column 0
+        solid[20:22, 0:3] = 1
+        x0, y0, cnx, cny = w.window
+        w = replace(w, solid=solid, cmask=(1 - solid[y0:y0 + cny, x0:x0 + cnx]).astype(np.uint8))
     else:  # one 16-byte unit per row (nx = 4): every segment touches both periodic ends
         w = W.aniso(4, 24, 10, seed=13, precision=32, ckpt_every=5)
     return w
 
 
 @pytest.mark.parametrize("case", ["aniso32_ragged", "aniso64_window", "plain64_q5_windows", "aniso32_nx4",
-                                  "geometry64", "geometry32"])
+                                  "geometry64", "geometry32", "geometry64_periodic"])
 @pytest.mark.parametrize("threads", [128, 256])
 def test_row_window_staging_bitwise(case, threads):
     """Bulk row-window staging (cp.async.bulk + mbarrier per row segment) and
