@@ -457,43 +457,47 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k3_adjoint(const 
 // Steps whose inputs are all pulled (forward n >= 1, adjoint below the
 // terminal step) on grids whose rows are a whole number of 16-byte units:
 // the warp-specialised pipeline of cx_rows.cuh.  A producer warp issues, per
-// row segment of RNT nodes, one bulk copy per population plane of the source
+// row segment (FNT or ANT nodes), one bulk copy per population plane of the source
 // row window (the segment widened by 16 bytes on each side; periodic ends from
 // the other end of the row) and of the node-local planes, completing on the
 // stage's mbarrier; the compute warps read everything from shared memory.
 
-constexpr int RNT = 128;
-template <typename T> struct RW3 {
+// Row segments of FNT nodes (forward) and ANT nodes (adjoint): the forward's
+// FP32 stages of 256 nodes leave two blocks per SM, which measured faster
+// than four blocks of 128; FP64 (the parity mode) and the adjoint keep 128.
+template <typename T> constexpr int FNT = sizeof(T) == 4 ? 256 : 128;
+constexpr int ANT = 128;
+template <typename T, int NT> struct RW3 {
     static constexpr int H = 16 / (int)sizeof(T);
-    static constexpr int W = RNT + 2 * H;
+    static constexpr int W = NT + 2 * H;
 };
-// stage layout: 27 population windows, then per-node planes of RNT values
-template <typename T> constexpr int fwd3_stage_values() { return 27 * RW3<T>::W + 6 * RNT; } // theta, g, E, Phi x3
+// stage layout: 27 population windows, then per-node planes of NT values
+template <typename T> constexpr int fwd3_stage_values() { return 27 * RW3<T, FNT<T>>::W + 6 * FNT<T>; } // theta, g, E, Phi x3
 template <typename T> constexpr int adj3_stage_values() {
-    return 27 * RW3<T>::W + 11 * RNT; // tape x6, sigma x3, g, theta
+    return 27 * RW3<T, ANT>::W + 11 * ANT; // tape x6, sigma x3, g, theta
 }
 
 template <typename T> struct SFwd {
     const T* s; // stage + threadIdx.x
-    __device__ __forceinline__ T pop(int sp, int i) const { return s[(sp * 9 + i) * RW3<T>::W + RW3<T>::H - L9::ex(i)]; }
-    __device__ __forceinline__ T theta() const { return s[27 * RW3<T>::W]; }
-    __device__ __forceinline__ T g() const { return s[27 * RW3<T>::W + RNT]; }
-    __device__ __forceinline__ T E() const { return s[27 * RW3<T>::W + 2 * RNT]; }
-    __device__ __forceinline__ T phi(int sp) const { return s[27 * RW3<T>::W + (3 + sp) * RNT]; }
+    __device__ __forceinline__ T pop(int sp, int i) const { return s[(sp * 9 + i) * RW3<T, FNT<T>>::W + RW3<T, FNT<T>>::H - L9::ex(i)]; }
+    __device__ __forceinline__ T theta() const { return s[27 * RW3<T, FNT<T>>::W]; }
+    __device__ __forceinline__ T g() const { return s[27 * RW3<T, FNT<T>>::W + FNT<T>]; }
+    __device__ __forceinline__ T E() const { return s[27 * RW3<T, FNT<T>>::W + 2 * FNT<T>]; }
+    __device__ __forceinline__ T phi(int sp) const { return s[27 * RW3<T, FNT<T>>::W + (3 + sp) * FNT<T>]; }
 };
 template <typename T> struct SAdj {
     const T* s;
-    __device__ __forceinline__ T pop(int sp, int i) const { return s[(sp * 9 + i) * RW3<T>::W + RW3<T>::H + L9::ex(i)]; }
-    __device__ __forceinline__ T tape(int c) const { return s[27 * RW3<T>::W + c * RNT]; }
-    __device__ __forceinline__ T sig(int sp) const { return s[27 * RW3<T>::W + (6 + sp) * RNT]; }
-    __device__ __forceinline__ T g() const { return s[27 * RW3<T>::W + 9 * RNT]; }
-    __device__ __forceinline__ T theta() const { return s[27 * RW3<T>::W + 10 * RNT]; }
+    __device__ __forceinline__ T pop(int sp, int i) const { return s[(sp * 9 + i) * RW3<T, ANT>::W + RW3<T, ANT>::H + L9::ex(i)]; }
+    __device__ __forceinline__ T tape(int c) const { return s[27 * RW3<T, ANT>::W + c * ANT]; }
+    __device__ __forceinline__ T sig(int sp) const { return s[27 * RW3<T, ANT>::W + (6 + sp) * ANT]; }
+    __device__ __forceinline__ T g() const { return s[27 * RW3<T, ANT>::W + 9 * ANT]; }
+    __device__ __forceinline__ T theta() const { return s[27 * RW3<T, ANT>::W + 10 * ANT]; }
 };
 
 template <typename T>
 __device__ __forceinline__ void fwd3_issue(const AC& C, const F3Args<T>& A, int y, int x0, T* st, uint64_t* bar) {
-    constexpr int H = RW3<T>::H, W = RW3<T>::W;
-    const int nx = C.nx, nv = min(RNT, nx - x0);
+    constexpr int H = RW3<T, FNT<T>>::H, W = RW3<T, FNT<T>>::W;
+    const int nx = C.nx, nv = min(FNT<T>, nx - x0);
     const int rm = y == 0 ? C.ny - 1 : y - 1, rp = y == C.ny - 1 ? 0 : y + 1;
     const bool rot = C.aniso == CX_ANISO_ROTATED;
     const uint32_t nb = (uint32_t)nv * sizeof(T);
@@ -503,20 +507,20 @@ __device__ __forceinline__ void fwd3_issue(const AC& C, const F3Args<T>& A, int 
     for (int j = 0; j < 27; ++j) {
         const int i = j % 9;
         const int ys = L9::ey(i) > 0 ? rm : (L9::ey(i) < 0 ? rp : y); // pull from x - e_i
-        bulk_row_window<T, RNT>(st + j * W, A.in + j * pl + (size_t)ys * nx, x0, nv, nx, bar);
+        bulk_row_window<T, FNT<T>>(st + j * W, A.in + j * pl + (size_t)ys * nx, x0, nv, nx, bar);
     }
     T* const loc = st + 27 * W;
     if (rot) bulk_g2s(loc, reinterpret_cast<const T*>(C.theta) + k0, nb, bar);
-    if (A.g) bulk_g2s(loc + RNT, A.g + k0, nb, bar);
-    if (A.E) bulk_g2s(loc + 2 * RNT, A.E + k0, nb, bar);
+    if (A.g) bulk_g2s(loc + FNT<T>, A.g + k0, nb, bar);
+    if (A.E) bulk_g2s(loc + 2 * FNT<T>, A.E + k0, nb, bar);
 #pragma unroll
-    for (int s = 0; s < 3; ++s) bulk_g2s(loc + (3 + s) * RNT, A.phi + s * pl + k0, nb, bar);
+    for (int s = 0; s < 3; ++s) bulk_g2s(loc + (3 + s) * FNT<T>, A.phi + s * pl + k0, nb, bar);
 }
 
 template <typename T>
 __device__ __forceinline__ void adj3_issue(const AC& C, const A3Args<T>& A, int y, int x0, T* st, uint64_t* bar) {
-    constexpr int H = RW3<T>::H, W = RW3<T>::W;
-    const int nx = C.nx, nv = min(RNT, nx - x0);
+    constexpr int H = RW3<T, ANT>::H, W = RW3<T, ANT>::W;
+    const int nx = C.nx, nv = min(ANT, nx - x0);
     const int rm = y == 0 ? C.ny - 1 : y - 1, rp = y == C.ny - 1 ? 0 : y + 1;
     const bool rot = C.aniso == CX_ANISO_ROTATED;
     const uint32_t nb = (uint32_t)nv * sizeof(T);
@@ -526,29 +530,31 @@ __device__ __forceinline__ void adj3_issue(const AC& C, const A3Args<T>& A, int 
     for (int j = 0; j < 27; ++j) {
         const int i = j % 9;
         const int ys = L9::ey(i) > 0 ? rp : (L9::ey(i) < 0 ? rm : y); // pull from x + e_i
-        bulk_row_window<T, RNT>(st + j * W, A.in + j * pl + (size_t)ys * nx, x0, nv, nx, bar);
+        bulk_row_window<T, ANT>(st + j * W, A.in + j * pl + (size_t)ys * nx, x0, nv, nx, bar);
     }
     T* const loc = st + 27 * W;
 #pragma unroll
-    for (int c = 0; c < 6; ++c) bulk_g2s(loc + c * RNT, A.tape + c * pl + k0, nb, bar);
+    for (int c = 0; c < 6; ++c) bulk_g2s(loc + c * ANT, A.tape + c * pl + k0, nb, bar);
 #pragma unroll
-    for (int s = 0; s < 3; ++s) bulk_g2s(loc + (6 + s) * RNT, A.sigma + s * pl + k0, nb, bar);
-    if (A.g) bulk_g2s(loc + 9 * RNT, A.g + k0, nb, bar);
-    if (rot) bulk_g2s(loc + 10 * RNT, reinterpret_cast<const T*>(C.theta) + k0, nb, bar);
+    for (int s = 0; s < 3; ++s) bulk_g2s(loc + (6 + s) * ANT, A.sigma + s * pl + k0, nb, bar);
+    if (A.g) bulk_g2s(loc + 9 * ANT, A.g + k0, nb, bar);
+    if (rot) bulk_g2s(loc + 10 * ANT, reinterpret_cast<const T*>(C.theta) + k0, nb, bar);
 }
 
-// Block: RNT compute threads and one producer warp.  CC describes the grid to
+// Block: FNT (ANT) compute threads and one producer warp.  CC describes the grid to
 // the pipeline's segment walk (no solid nodes, whole-grid control).
 template <typename T>
-__global__ void __launch_bounds__(RNT + 32, sizeof(T) == 4 ? 4 : 2)
+// (register cap: two blocks of FNT + 32 threads per SM, which is what shared
+// memory allows, without spills in FP32)
+__global__ void __maxnreg__(sizeof(T) == 4 ? 104 : 224)
     k3_forward_rows(const CxConst CC, const AC C, const AK<T> KC, const F3Args<T> A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    RowsPipe<T, RNT> pipe(smem_raw, fwd3_stage_values<T>());
+    RowsPipe<T, FNT<T>> pipe(smem_raw, fwd3_stage_values<T>());
     pipe.init();
     allow_next_grid();
     wait_prior_grid(); // the previous step's populations and node state are complete
     if (block_sees_timeout(A.status)) return;
-    if (threadIdx.x >= RNT) {
+    if (threadIdx.x >= FNT<T>) {
         pipe.produce(CC, A.status, [&](int y, int x0, T* st, uint64_t* bar) { fwd3_issue<T>(C, A, y, x0, st, bar); });
         return;
     }
@@ -558,19 +564,19 @@ __global__ void __launch_bounds__(RNT + 32, sizeof(T) == 4 ? 4 : 2)
         [&](const NodeIdx& nd, T* st) {
             if (nd.fluid) fwd3_body<T>(C, KC, A, nd.y, nd.k, SFwd<T>{st + threadIdx.x}, acc);
         });
-    if (A.gsq_part) acc.flush(A.gsq_part + blockIdx.x * (RNT >> 5) + (threadIdx.x >> 5), nullptr);
+    if (A.gsq_part) acc.flush(A.gsq_part + blockIdx.x * (FNT<T> >> 5) + (threadIdx.x >> 5), nullptr);
 }
 
 template <typename T>
-__global__ void __launch_bounds__(RNT + 32, sizeof(T) == 4 ? 3 : 2)
+__global__ void __launch_bounds__(ANT + 32, sizeof(T) == 4 ? 3 : 2)
     k3_adjoint_rows(const CxConst CC, const AC C, const AK<T> KC, const A3Args<T> A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    RowsPipe<T, RNT> pipe(smem_raw, adj3_stage_values<T>());
+    RowsPipe<T, ANT> pipe(smem_raw, adj3_stage_values<T>());
     pipe.init();
     allow_next_grid();
     wait_prior_grid();
     if (block_sees_timeout(A.status)) return;
-    if (threadIdx.x >= RNT) {
+    if (threadIdx.x >= ANT) {
         pipe.produce(CC, A.status, [&](int y, int x0, T* st, uint64_t* bar) { adj3_issue<T>(C, A, y, x0, st, bar); });
         return;
     }
@@ -581,7 +587,7 @@ __global__ void __launch_bounds__(RNT + 32, sizeof(T) == 4 ? 3 : 2)
             if (nd.fluid) adj3_body<T>(C, KC, A, nd.y, nd.k, SAdj<T>{st + threadIdx.x}, acc);
         });
     if (A.e2_part) {
-        const int w = blockIdx.x * (RNT >> 5) + (threadIdx.x >> 5);
+        const int w = blockIdx.x * (ANT >> 5) + (threadIdx.x >> 5);
         acc.flush(A.e2_part + w, A.emax_part + w);
     }
 }
@@ -889,14 +895,16 @@ bool aligned16(const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15u) ==
 template <typename T> bool rows_ok(const cx3_problem* p, const T* in, const T* g, const T* extra) {
     if (p->rows_mode == 0 || p->C.nx % (16 / (int)sizeof(T)) != 0) return false;
     if (!aligned16(in) || !aligned16(p->ws) || (g && !aligned16(g)) || (extra && !aligned16(extra))) return false;
-    const long long segs = (long long)((p->C.nx + RNT - 1) / RNT) * p->C.ny;
-    return p->rows_mode == 2 || segs >= 2LL * std::max(p->grid_fr, p->grid_ar);
+    const long long segf = (long long)((p->C.nx + FNT<T> - 1) / FNT<T>) * p->C.ny;
+    const long long sega = (long long)((p->C.nx + ANT - 1) / ANT) * p->C.ny;
+    return p->rows_mode == 2 || (segf >= 2LL * p->grid_fr && sega >= 2LL * p->grid_ar);
 }
 
-template <typename T> cudaError_t launch_rows(const void* kern, int grid, size_t smem, cudaStream_t s, void** args) {
+template <typename T> cudaError_t launch_rows(const void* kern, int grid, int threads, size_t smem, cudaStream_t s,
+                                               void** args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3(RNT + 32);
+    cfg.blockDim = dim3((unsigned)threads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -911,7 +919,7 @@ template <typename T> cudaError_t launch_fwd3(cx3_problem* p, const F3Args<T>& A
     const AK<T>& K = p->kc((T*)nullptr);
     if (A.n > 0 && rows_ok<T>(p, A.in, A.g, A.E)) {
         void* args[] = {(void*)&p->CC, (void*)&p->C, (void*)&K, (void*)&A};
-        return launch_rows<T>((const void*)k3_forward_rows<T>, p->grid_fr, rows_pipe_smem<T>(fwd3_stage_values<T>()),
+        return launch_rows<T>((const void*)k3_forward_rows<T>, p->grid_fr, FNT<T> + 32, rows_pipe_smem<T>(fwd3_stage_values<T>()),
                               p->stream, args);
     }
     k3_forward<T><<<p->grid_f, 256, 0, p->stream>>>(p->C, K, A);
@@ -925,7 +933,7 @@ template <typename T> cudaError_t launch_fwd3(cx3_problem* p, const F3Args<T>& A
 template <typename T> cudaError_t launch_adj3(cx3_problem* p, const AK<T>& K, const A3Args<T>& A) {
     if (!A.terminal && p->rows_mode == 2 && rows_ok<T>(p, A.in, A.g, nullptr)) {
         void* args[] = {(void*)&p->CC, (void*)&p->C, (void*)&K, (void*)&A};
-        return launch_rows<T>((const void*)k3_adjoint_rows<T>, p->grid_ar, rows_pipe_smem<T>(adj3_stage_values<T>()),
+        return launch_rows<T>((const void*)k3_adjoint_rows<T>, p->grid_ar, ANT + 32, rows_pipe_smem<T>(adj3_stage_values<T>()),
                               p->stream, args);
     }
     k3_adjoint<T><<<p->grid_a, 256, 0, p->stream>>>(p->C, K, A);
@@ -938,7 +946,7 @@ cx_status run3_forward(cx3_problem* p, const T* g, const T* E, double lam, doubl
     const size_t nn = (size_t)p->d.nx * p->d.ny; // control and gradient planes are unpadded [N][ny][nx]
     double* part = p->at<double>(Ly.off_part);
     double* gsq = part + Ly.nparts;
-    const int fw = std::max(p->grid_f * 8, p->grid_fr * (RNT / 32));
+    const int fw = std::max(p->grid_f * 8, p->grid_fr * (FNT<T> / 32));
     CX3_CUDA(cudaMemsetAsync(gsq, 0, sizeof(double) * fw, p->stream));
     Range3* r;
     rbegin(p, R_FWD, &r);
@@ -992,7 +1000,7 @@ cx_status run3_adjoint(cx3_problem* p, const T* g, const T* const (&seeds)[3], b
     double* e2 = part + 2 * (size_t)Ly.nparts;
     double* emax = part + 3 * (size_t)Ly.nparts;
     CX3_CUDA(cudaMemsetAsync(e2, 0, sizeof(double) * 2 * Ly.nparts, p->stream));
-    const int aw = std::max(p->grid_a * 8, p->grid_ar * (RNT / 32));
+    const int aw = std::max(p->grid_a * 8, p->grid_ar * (ANT / 32));
     T* sigma = p->at<T>(Ly.off_sigma);
     T* phi = p->at<T>(Ly.off_phi);
     const bool cost_seed = !seeds[0] && !seeds[1] && !seeds[2];
@@ -1176,16 +1184,18 @@ cx_status cx3_create(const cx3_desc* desc, void* workspace, size_t bytes, cudaSt
         int of = 1, oa = 1;
         if (cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf) != cudaSuccess ||
             cudaFuncSetAttribute(ka, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&of, kf, RNT + 32, sf) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oa, ka, RNT + 32, sa) != cudaSuccess) {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&of, kf, f64 ? FNT<double> + 32 : FNT<float> + 32, sf) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oa, ka, ANT + 32, sa) != cudaSuccess) {
             delete p;
             return CX_ERR_CUDA;
         }
-        const long long segs = (long long)((desc->nx + RNT - 1) / RNT) * desc->ny;
-        p->grid_fr = (int)std::max(1LL, std::min<long long>((long long)std::max(of, 1) * nsm, segs));
-        p->grid_ar = (int)std::max(1LL, std::min<long long>((long long)std::max(oa, 1) * nsm, segs));
-        p->grid_fr = std::min(p->grid_fr, MAXW / (RNT / 32));
-        p->grid_ar = std::min(p->grid_ar, MAXW / (RNT / 32));
+        const int fnt = f64 ? FNT<double> : FNT<float>;
+        const long long segf = (long long)((desc->nx + fnt - 1) / fnt) * desc->ny;
+        const long long sega = (long long)((desc->nx + ANT - 1) / ANT) * desc->ny;
+        p->grid_fr = (int)std::max(1LL, std::min<long long>((long long)std::max(of, 1) * nsm, segf));
+        p->grid_ar = (int)std::max(1LL, std::min<long long>((long long)std::max(oa, 1) * nsm, sega));
+        p->grid_fr = std::min(p->grid_fr, MAXW / (fnt / 32));
+        p->grid_ar = std::min(p->grid_ar, MAXW / (ANT / 32));
     }
     CxConst& CC = p->CC;
     CC.nx = desc->nx;
