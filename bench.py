@@ -1105,55 +1105,26 @@ def main():
             g_host = torch.empty(g.shape, dtype=g.dtype, pin_memory=True)
             g_host.copy_(g.cpu())
             E_host = torch.empty_like(g_host, pin_memory=True)
-            J_host = torch.empty(1, dtype=torch.float64, pin_memory=True)
             torch.cuda.synchronize()
-            # Copies run on their own streams (one per direction, so the host link
-            # carries both at once), double-buffered: step i+1's control arrives
-            # and step i-1's gradient leaves while step i computes.  Every step's
-            # H2D and D2H lie inside the timed region [ea, eb].
-            cs = torch.cuda.Stream()   # host -> device
-            ds = torch.cuda.Stream()   # device -> host
-            gb, Eb = [g, torch.empty_like(g)], [E, torch.empty_like(E)]
-            J_hosts = [J_host, torch.empty_like(J_host, pin_memory=True)]
-            Jb = [torch.empty(1, dtype=torch.float64, device=dev) for _ in range(2)]  # J of step i, kept per buffer
+            # Every step goes through the C ABI's host-buffer call
+            # (cx_gradient_host): the control is copied in chunk by chunk, each
+            # forward step waiting only for its own chunk, and the gradient
+            # leaves chunk by chunk during the reverse sweep; the call returns
+            # with J and dJ/dg in host memory.
             ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            ne = max(1, args.steps)  # every timed step; the first upload and the last read-back are not overlapped
-            h2d_done = [torch.cuda.Event() for _ in range(2)]
-            used = [torch.cuda.Event() for _ in range(2)]     # gradient i done with gb[i%2] / wrote Eb[i%2]
-            d2h_done = [torch.cuda.Event() for _ in range(2)]
-            ea.record(cs)
-            with torch.cuda.stream(cs):
-                gb[0].copy_(g_host, non_blocking=True)
-            h2d_done[0].record(cs)
-            for i in range(ne):
-                b = i % 2
-                if i + 1 < ne:  # prefetch step i+1's control into the other buffer
-                    if i >= 1:
-                        cs.wait_event(used[1 - b])
-                    with torch.cuda.stream(cs):
-                        gb[1 - b].copy_(g_host, non_blocking=True)
-                    h2d_done[1 - b].record(cs)
-                stream.wait_event(h2d_done[b])
-                if i >= 2:
-                    stream.wait_event(d2h_done[b])  # Eb[b] read back before it is overwritten
-                Jd, _ = prob.gradient(gb[b], out=Eb[b])
-                with torch.cuda.stream(stream):
-                    Jb[b].copy_(Jd)  # the problem's J buffer is rewritten by the next step
-                used[b].record(stream)
-                ds.wait_event(used[b])
-                with torch.cuda.stream(ds):
-                    E_host.copy_(Eb[b], non_blocking=True)
-                    J_hosts[b].copy_(Jb[b], non_blocking=True)
-                d2h_done[b].record(ds)
-            stream.wait_stream(cs)
-            stream.wait_stream(ds)
+            ne = max(1, args.steps)
+            ea.record(stream)
+            for _ in range(ne):
+                prob.gradient_host(g_host, E_host, g, E)
             eb.record(stream)
             torch.cuda.synchronize()
             ms_e2e = ea.elapsed_time(eb) / ne
             e2e = {"value": nodes * w.N / (ms_e2e * 1e-3) / 1e6, "unit": "MLUPS",
                    "h2d_bytes_per_step": g.numel() * g.element_size(),
-                   "d2h_bytes_per_step": E.numel() * E.element_size() + 8, "ms_per_step": ms_e2e,
-                   "overlap": "one copy stream per direction, double-buffered control and gradient"}
+                   "d2h_bytes_per_step": E.numel() * E.element_size() + 36, "ms_per_step": ms_e2e,
+                   "call": "cx_gradient_host (host control in, host gradient and cost out)",
+                   "overlap": "control copied in 16 chunks, each forward step waiting for its own chunk; "
+                              "gradient chunks read back during the reverse sweep"}
         except Exception as exc:  # pinned memory can fail on small hosts
             e2e = {"value": None, "unit": "MLUPS", "error": str(exc)[:200]}
 

@@ -168,6 +168,23 @@ cx_status cx_adjoint_vjp(cx_problem* p, const void* g, const void* seed_u, const
  * NULL) and dJ/dg. */
 cx_status cx_gradient(cx_problem* p, const void* g, void* dJdg, double* J_dev);
 
+/* cx_gradient with the control and the gradient in HOST memory: g_host (host
+ * T [W][ctrl_ny][ctrl_nx], page-locked for the copies to overlap) is copied
+ * into g_dev, the gradient computed into dJdg_dev (both device T of the same
+ * size, caller-owned, not aliasing) and copied back into dJdg_host (host T,
+ * same size); J goes to *J_host (host double, may be NULL).  The control
+ * moves in chunks of windows on a copy stream of the problem's own, each
+ * forward step waiting only for the chunk that holds its control; each
+ * gradient chunk leaves on a second copy stream as soon as the reverse sweep
+ * has finished it.  So the copies overlap the kernels except the first chunk
+ * in and the last chunk out.  Synchronises before it returns (the host
+ * buffers may be reused at once).  The two copy streams are created on the
+ * first call and destroyed with the problem.  Errors: CX_ERR_INVALID_ARG (a
+ * NULL buffer, or a sub-domain), CX_ERR_STATE (no initial state),
+ * CX_ERR_CUDA, CX_ERR_UNSTABLE, CX_ERR_TIMEOUT. */
+cx_status cx_gradient_host(cx_problem* p, const void* g_host, void* dJdg_host, double* J_host, void* g_dev,
+                           void* dJdg_dev);
+
 /* One steepest-descent iteration with Armijo backtracking (step 5 of the
  * algorithm; first trial min(1, 1/||E||_inf), the heuristic of the remark
  * after the continuous gradient algorithm, then twice the previous step).

@@ -25,7 +25,7 @@ STATUS = {
 # every exported symbol of include/cxlbm.h
 EXPORTS = [
     "cx_workspace_size", "cx_create", "cx_set_initial", "cx_forward", "cx_adjoint", "cx_adjoint_vjp",
-    "cx_gradient", "cx_step",
+    "cx_gradient", "cx_gradient_host", "cx_step",
     "cx_get_fields", "cx_get_psi0", "cx_get_norms", "cx_set_launch", "cx_set_timing", "cx_get_timing",
     "cx_destroy", "cx_status_string", "cx_forward_static", "cx_cg_step", "cx_cg_reset",
     "cx_tlm", "cx_lma_step", "cx_cadjoint", "cx_set_staging",
@@ -150,6 +150,7 @@ def load():
         "cx_adjoint": [vp, vp, vp, vp, vp],
         "cx_adjoint_vjp": [vp, vp, vp, vp, vp],
         "cx_gradient": [vp, vp, vp, vp],
+        "cx_gradient_host": [vp, vp, vp, vp, vp, vp],
         "cx_step": [vp, vp, vp, ctypes.POINTER(StepInfo)],
         "cx_get_fields": [vp, vp, vp],
         "cx_get_psi0": [vp, vp],

@@ -193,6 +193,8 @@ template <typename T> static cx_status run_forward(cx_problem* p, const T* g, co
         A.tape = (seg == Ly.S - 1) ? reinterpret_cast<T*>(p->tape_slot(n - seg * Ly.k)) : nullptr;
         A.gsq_part = gsq;
         A.n = n;
+        if (p->io_cw > 0 && n % Ly.win_len == 0 && (n / Ly.win_len) % p->io_cw == 0) // a control chunk's first step
+            CX_CUDA(cudaStreamWaitEvent(p->stream, p->io_ev[(n / Ly.win_len) / p->io_cw], 0));
         CX_CUDA(launch_forward<T>(C, p->kc((T*)nullptr), A, p->Lf, p->stream));
         if (p->halo_fn) {
             const cx_status hs = p->halo_fn(p->halo_user, CX_HALO_FWD, out, p->stream);
@@ -289,6 +291,16 @@ static cx_status run_adjoint(cx_problem* p, const T* g, const T* seed_u, const T
             A.emax_part = emax;
             A.n = n;
             CX_CUDA(launch_adjoint<T>(C, KA, A, p->La, p->stream));
+            if (p->io_cw > 0 && p->io_E_host && n % Ly.win_len == 0 && (n / Ly.win_len) % p->io_cw == 0) {
+                // the chunk's lowest window is final: read the chunk back while the adjoint goes on
+                const size_t w0 = (size_t)(n / Ly.win_len), w1 = std::min(w0 + (size_t)p->io_cw, (size_t)Ly.nwin);
+                const size_t off = w0 * Ly.nctrl * sizeof(T), bytes = (w1 - w0) * Ly.nctrl * sizeof(T);
+                cudaEvent_t ev = p->io_ev[(size_t)p->io_nch + w0 / (size_t)p->io_cw];
+                CX_CUDA(cudaEventRecord(ev, p->stream));
+                CX_CUDA(cudaStreamWaitEvent(p->io_d2h, ev, 0));
+                CX_CUDA(cudaMemcpyAsync(static_cast<char*>(p->io_E_host) + off, reinterpret_cast<const char*>(dJdg) + off,
+                                        bytes, cudaMemcpyDeviceToHost, p->io_d2h));
+            }
             if (p->halo_fn && n > 0) {
                 const cx_status hs = p->halo_fn(p->halo_user, CX_HALO_ADJ, out, p->stream);
                 if (hs) return hs;
@@ -957,6 +969,66 @@ cx_status cx_gradient(cx_problem* p, const void* g, void* dJdg, double* J_dev) {
     return cx_adjoint(p, g, nullptr, nullptr, dJdg);
 }
 
+// One gradient evaluation from and to host memory.  The control arrives in
+// chunks of io_cw windows on the upload stream, and the forward waits for a
+// chunk only at the chunk's first step; the gradient leaves chunk by chunk on
+// the read-back stream as soon as the reverse sweep has finished the chunk's
+// lowest window.  So both copies overlap the kernels except the first chunk
+// in and the last chunk out.
+constexpr int HOST_CHUNKS = 16; // chunks per direction (the first in and the last out are not overlapped)
+
+cx_status cx_gradient_host(cx_problem* p, const void* g_host, void* dJdg_host, double* J_host, void* g_dev,
+                           void* dJdg_dev) {
+    if (!p || !g_host || !dJdg_host || !g_dev || !dJdg_dev || p->d.halo) return CX_ERR_INVALID_ARG;
+    if (!p->has_init) return CX_ERR_STATE;
+    const Layout& Ly = p->lay;
+    const int cw = std::max(1, Ly.nwin / HOST_CHUNKS);
+    const int nch = (Ly.nwin + cw - 1) / cw;
+    if (!p->io_h2d) {
+        CX_CUDA(cudaStreamCreateWithFlags(&p->io_h2d, cudaStreamNonBlocking));
+        CX_CUDA(cudaStreamCreateWithFlags(&p->io_d2h, cudaStreamNonBlocking));
+    }
+    while ((int)p->io_ev.size() < 2 * nch + 1) {
+        cudaEvent_t e;
+        CX_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        p->io_ev.push_back(e);
+    }
+    // the copies must not overtake work already queued on the problem's stream
+    // (a previous call's kernels may still read g_dev or write dJdg_dev)
+    cudaEvent_t start = p->io_ev[2 * nch];
+    CX_CUDA(cudaEventRecord(start, p->stream));
+    CX_CUDA(cudaStreamWaitEvent(p->io_h2d, start, 0));
+    const size_t wbytes = Ly.nctrl * Ly.esz;
+    for (int c = 0; c < nch; ++c) {
+        const size_t w0 = (size_t)c * cw, w1 = std::min(w0 + (size_t)cw, (size_t)Ly.nwin);
+        CX_CUDA(cudaMemcpyAsync(static_cast<char*>(g_dev) + w0 * wbytes, static_cast<const char*>(g_host) + w0 * wbytes,
+                                (w1 - w0) * wbytes, cudaMemcpyHostToDevice, p->io_h2d));
+        CX_CUDA(cudaEventRecord(p->io_ev[c], p->io_h2d));
+    }
+    // the read-back stream waits, per chunk, for the adjoint (queued inside)
+    p->io_cw = cw;
+    p->io_nch = nch;
+    p->io_E_host = dJdg_host;
+    cx_status rc = cx_gradient(p, g_dev, dJdg_dev, nullptr);
+    p->io_cw = 0;
+    p->io_E_host = nullptr;
+    if (rc) {
+        cudaStreamSynchronize(p->io_h2d);
+        cudaStreamSynchronize(p->io_d2h);
+        return rc;
+    }
+    double s4[4];
+    int st = 0;
+    rc = read_scalars(p, s4, &st);
+    CX_CUDA(cudaStreamSynchronize(p->io_h2d));
+    CX_CUDA(cudaStreamSynchronize(p->io_d2h));
+    if (rc) return rc;
+    if (J_host) *J_host = s4[0];
+    if (st & ST_TIMEOUT) return CX_ERR_TIMEOUT;
+    if (st & ST_UNSTABLE) return CX_ERR_UNSTABLE;
+    return CX_OK;
+}
+
 cx_status cx_cg_step(cx_problem* p, void* g_inout, void* work, int variant, cx_cg_info* info) {
     if (!p || !g_inout || !work || variant < CX_CG_FR || variant > CX_CG_DY || p->d.halo) return CX_ERR_INVALID_ARG;
     if (!p->has_init) return CX_ERR_STATE;
@@ -1063,6 +1135,9 @@ cx_status cx_destroy(cx_problem* p) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
     }
+    for (cudaEvent_t e : p->io_ev) cudaEventDestroy(e);
+    if (p->io_h2d) cudaStreamDestroy(p->io_h2d);
+    if (p->io_d2h) cudaStreamDestroy(p->io_d2h);
     delete p;
     return CX_OK;
 }

@@ -61,6 +61,16 @@ struct cx_problem {
     void* psi0 = nullptr;
     bool timing = false;
     std::vector<cx::TimedRange> ranges;
+    // cx_gradient_host: copy streams (created on first use) and per-chunk
+    // events ([0, n) control chunk landed, [n, 2n) gradient chunk final, 2n
+    // the call's start; n = io_nch chunks of io_cw windows); while
+    // io_cw > 0 the forward waits for each chunk's event before the chunk's
+    // first step, and the adjoint queues each gradient chunk's read-back to
+    // io_E_host once the chunk is final
+    cudaStream_t io_h2d = nullptr, io_d2h = nullptr;
+    std::vector<cudaEvent_t> io_ev;
+    int io_cw = 0, io_nch = 0;
+    void* io_E_host = nullptr;
     cx_halo_fn halo_fn = nullptr; // sub-domain: fills the halo frame after every lattice step
     void* halo_user = nullptr;
     size_t n_ranges = 0;

@@ -113,6 +113,25 @@ class Problem:
         self.generation += 1
         return self._J, out
 
+    def gradient_host(self, g_host, out_host, g_dev=None, E_dev=None):
+        """J and dJ/dg with the control and the gradient in host memory
+        (cx_gradient_host): g_host and out_host are CPU tensors of the control's
+        shape and dtype (pinned for the copies to overlap the kernels); g_dev
+        and E_dev are the device buffers the call works in (allocated here
+        when not given).  Returns J (float)."""
+        for t in (g_host, out_host):
+            if t.device.type != "cpu" or t.dtype != self.dtype or not t.is_contiguous() or \
+                    tuple(t.shape) != tuple(self.ctrl_shape):
+                raise ValueError("host buffers must be contiguous CPU tensors of the control's shape and dtype")
+        g_dev = g_dev if g_dev is not None else torch.empty(self.ctrl_shape, dtype=self.dtype, device=self.device)
+        E_dev = E_dev if E_dev is not None else torch.empty(self.ctrl_shape, dtype=self.dtype, device=self.device)
+        J = ctypes.c_double(0.0)
+        _lib.check(self.lib.cx_gradient_host(self.h, ctypes.c_void_p(g_host.data_ptr()),
+                                             ctypes.c_void_p(out_host.data_ptr()), ctypes.byref(J), _ptr(g_dev),
+                                             _ptr(E_dev)), "cx_gradient_host")
+        self.generation += 1
+        return J.value
+
     def step(self, g, E=None):
         """One Armijo steepest-descent iteration, g updated in place."""
         if g.dtype != self.dtype or not g.is_contiguous() or g.device != self.device or \
