@@ -1123,7 +1123,7 @@ def main():
                    "h2d_bytes_per_step": g.numel() * g.element_size(),
                    "d2h_bytes_per_step": E.numel() * E.element_size() + 36, "ms_per_step": ms_e2e,
                    "call": "cx_gradient_host (host control in, host gradient and cost out)",
-                   "overlap": "control copied in 16 chunks, each forward step waiting for its own chunk; "
+                   "overlap": "control copied in 32 chunks, each forward step waiting for its own chunk; "
                               "gradient chunks read back during the reverse sweep"}
         except Exception as exc:  # pinned memory can fail on small hosts
             e2e = {"value": None, "unit": "MLUPS", "error": str(exc)[:200]}

@@ -975,7 +975,7 @@ cx_status cx_gradient(cx_problem* p, const void* g, void* dJdg, double* J_dev) {
 // the read-back stream as soon as the reverse sweep has finished the chunk's
 // lowest window.  So both copies overlap the kernels except the first chunk
 // in and the last chunk out.
-constexpr int HOST_CHUNKS = 16; // chunks per direction (the first in and the last out are not overlapped)
+constexpr int HOST_CHUNKS = 32; // chunks per direction (the first in and the last out are not overlapped)
 
 cx_status cx_gradient_host(cx_problem* p, const void* g_host, void* dJdg_host, double* J_host, void* g_dev,
                            void* dJdg_dev) {
