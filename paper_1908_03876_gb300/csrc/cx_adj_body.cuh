@@ -132,12 +132,14 @@ __device__ __forceinline__ void adj_compute(const CxConst& C, const KConst<T>& K
         }
     }
     relax_n<T, Q>(KC, nc.Ku0, nc.Ku1, nc.Ku2, mom, z);
-    T Tc = T(0);
+    T Tcu = T(0);
 #pragma unroll
-    for (int kk = 0; kk < Q; ++kk) Tc += z[kk] * mh[kk];
+    for (int kk = 0; kk < Q; ++kk) Tcu += z[kk] * mh[kk];
     Transform<T, Q>::transpose(z, mt);
+    // FP32 adds the node's scalar terms (Tcal, the coupling) once per
+    // direction at the end; FP64 adds them in the order written above
 #pragma unroll
-    for (int i = 0; i < Q; ++i) psu[i] = ru[i] - mt[i] + Tc;
+    for (int i = 0; i < Q; ++i) psu[i] = fold ? ru[i] - mt[i] : ru[i] - mt[i] + Tcu;
 
     // sigma = sum_i w~_i rho_v,i with w~_i = w_i (1 + 3 V.e_i), V = (I - K_v/2) a
     const T Kax = nc.Kv0 * nc.ax + nc.Kv1 * nc.ay, Kay = nc.Kv1 * nc.ax + nc.Kv2 * nc.ay;
@@ -160,12 +162,12 @@ __device__ __forceinline__ void adj_compute(const CxConst& C, const KConst<T>& K
             sigma += T(L::w(i)) * (T(1) + T(3) * (Vx * T(L::ex(i)) + Vy * T(L::ey(i)))) * rv[i];
     }
     relax_n<T, Q>(KC, nc.Kv0, nc.Kv1, nc.Kv2, mom, z);
-    Tc = T(0);
+    T Tcv = T(0);
 #pragma unroll
-    for (int kk = 0; kk < Q; ++kk) Tc += z[kk] * mh[kk];
+    for (int kk = 0; kk < Q; ++kk) Tcv += z[kk] * mh[kk];
     Transform<T, Q>::transpose(z, mt);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) psv[i] = rv[i] - mt[i] + Tc;
+    for (int i = 0; i < Q; ++i) psv[i] = fold ? rv[i] - mt[i] : rv[i] - mt[i] + Tcv;
 
     // --- coupling through tau S_u,i = 3 w_i chi u e_i . (K_u G)
     const T chi = KC.chi;
@@ -196,12 +198,27 @@ __device__ __forceinline__ void adj_compute(const CxConst& C, const KConst<T>& K
         A.dJdg[nd.c] = T(0);
     }
     const unsigned bbc = (Stage::copies && C.bb_copy) ? S.bb_bits(C, k) : 0u;
+    if constexpr (fold) {
+        // psi_i = (rho_i - mt_i) + c(e_i), c(e) = Tcal + adj_T + e.aj: three
+        // x-classes, then +-aj_y
+        const T cu = Tcu + adj_Tu, cv = Tcv + adj_Tv;
+        const T cvx[3] = {cv - ajx, cv, cv + ajx};
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        psu[i] = psu[i] + adj_Tu;
-        psv[i] = psv[i] + adj_Tv + T(L::ex(i)) * ajx + T(L::ey(i)) * ajy;
-        A.out(i)[k] = psu[i];
-        A.out(Q + i)[k] = psv[i];
+        for (int i = 0; i < Q; ++i) {
+            const T cxi = cvx[L::ex(i) + 1];
+            psu[i] = psu[i] + cu;
+            psv[i] = psv[i] + (L::ey(i) == 0 ? cxi : (L::ey(i) > 0 ? cxi + ajy : cxi - ajy));
+            A.out(i)[k] = psu[i];
+            A.out(Q + i)[k] = psv[i];
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            psu[i] = psu[i] + adj_Tu;
+            psv[i] = psv[i] + adj_Tv + T(L::ex(i)) * ajx + T(L::ey(i)) * ajy;
+            A.out(i)[k] = psu[i];
+            A.out(Q + i)[k] = psv[i];
+        }
     }
     if (Stage::copies && bbc) {
         adj_bb_copies<T, Q>(C, A, 0, k, bbc, psu);
