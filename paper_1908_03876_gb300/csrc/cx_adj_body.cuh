@@ -132,10 +132,15 @@ __device__ __forceinline__ void adj_compute(const CxConst& C, const KConst<T>& K
         }
     }
     relax_n<T, Q>(KC, nc.Ku0, nc.Ku1, nc.Ku2, mom, z);
+    // (FP32: the mass moment's term, z_0 in both mt and Tcal, cancels exactly
+    // in psi = rho - mt + Tcal, so it is left out)
     T Tcu = T(0);
 #pragma unroll
-    for (int kk = 0; kk < Q; ++kk) Tcu += z[kk] * mh[kk];
-    Transform<T, Q>::transpose(z, mt);
+    for (int kk = fold ? 1 : 0; kk < Q; ++kk) Tcu += z[kk] * mh[kk];
+    if constexpr (fold)
+        Transform<T, Q>::transpose0(z, mt);
+    else
+        Transform<T, Q>::transpose(z, mt);
     // FP32 adds the node's scalar terms (Tcal, the coupling) once per
     // direction at the end; FP64 adds them in the order written above
 #pragma unroll
@@ -164,8 +169,11 @@ __device__ __forceinline__ void adj_compute(const CxConst& C, const KConst<T>& K
     relax_n<T, Q>(KC, nc.Kv0, nc.Kv1, nc.Kv2, mom, z);
     T Tcv = T(0);
 #pragma unroll
-    for (int kk = 0; kk < Q; ++kk) Tcv += z[kk] * mh[kk];
-    Transform<T, Q>::transpose(z, mt);
+    for (int kk = fold ? 1 : 0; kk < Q; ++kk) Tcv += z[kk] * mh[kk];
+    if constexpr (fold)
+        Transform<T, Q>::transpose0(z, mt);
+    else
+        Transform<T, Q>::transpose(z, mt);
 #pragma unroll
     for (int i = 0; i < Q; ++i) psv[i] = fold ? rv[i] - mt[i] : rv[i] - mt[i] + Tcv;
 

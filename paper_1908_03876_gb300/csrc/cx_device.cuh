@@ -120,6 +120,17 @@ template <typename T, int Q> struct Transform {
             o[i] = s;
         }
     }
+    // transpose of (0, r_1, ..., r_{Q-1}): r[0] is not read
+    __host__ __device__ static inline void transpose0(const T (&r)[Q], T (&o)[Q]) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            T s = T(0);
+#pragma unroll
+            for (int k = 1; k < Q; ++k)
+                if (Lat<Q>::M(k, i) != 0) s += T(Lat<Q>::M(k, i)) * r[k];
+            o[i] = s;
+        }
+    }
 };
 template <typename T> struct Transform<T, 9> {
     __host__ __device__ static inline void moments(const T (&f)[9], T (&m)[9]) {
@@ -145,6 +156,24 @@ template <typename T> struct Transform<T, 9> {
         const T E = base2 + r[8], G = base2 - r[8];
         const T F = r[3] + r[4] + r[5] + r[6], H = r[5] + r[6] - r[3] - r[4];
         o[0] = r[0] - T(4) * r[1] + T(4) * r[2];
+        o[1] = A + B;
+        o[3] = A - B;
+        o[2] = C + D;
+        o[4] = C - D;
+        o[5] = E + F;
+        o[7] = E - F;
+        o[6] = G + H;
+        o[8] = G - H;
+    }
+    // transpose of (0, r_1, ..., r_8): r[0] is not read
+    __host__ __device__ static inline void transpose0(const T (&r)[9], T (&o)[9]) {
+        const T base1 = -r[1] - T(2) * r[2];
+        const T base2 = T(2) * r[1] + r[2];
+        const T A = base1 + r[7], C = base1 - r[7];
+        const T B = r[3] - T(2) * r[4], D = r[5] - T(2) * r[6];
+        const T E = base2 + r[8], G = base2 - r[8];
+        const T F = r[3] + r[4] + r[5] + r[6], H = r[5] + r[6] - r[3] - r[4];
+        o[0] = T(4) * (r[2] - r[1]);
         o[1] = A + B;
         o[3] = A - B;
         o[2] = C + D;

@@ -128,7 +128,13 @@ __device__ __forceinline__ void fwd_compute(const CxConst& C, const KConst<T>& K
             if (L::src_By(kk) != 0.0) rl[kk] -= T(3.0 * L::inv_n(kk) * L::src_By(kk)) * Fy;
         }
     }
-    Transform<T, Q>::transpose(rl, bt); // M^-1 (Pi (m - m^eq) - s^) = M^T N^-1 (...)
+    // M^-1 (Pi (m - m^eq) - s^) = M^T N^-1 (...); FP32: the mass moment of u's
+    // non-equilibrium part is exactly zero (m_0 - Theta m^eq_0 = Theta - Theta)
+    // and u has no mass source, so its row is left out
+    if constexpr (fold)
+        Transform<T, Q>::transpose0(rl, bt);
+    else
+        Transform<T, Q>::transpose(rl, bt);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         if constexpr (fold) {
