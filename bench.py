@@ -1106,6 +1106,20 @@ def main():
             g_host.copy_(g.cpu())
             E_host = torch.empty_like(g_host, pin_memory=True)
             torch.cuda.synchronize()
+            # the host link as this process sees it (the whole pinned buffers,
+            # one copy each way, alone), so that a slow link shows beside the
+            # figure: the rate of these buffers' pages can differ from a short
+            # probe's
+            link = {}
+            for name, dst, src in (("h2d_gbs", g, g_host), ("d2h_gbs", E_host, E)):
+                la, lb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                la.record()
+                dst.copy_(src, non_blocking=True)
+                lb.record()
+                torch.cuda.synchronize()
+                link[name] = g.numel() * g.element_size() / (la.elapsed_time(lb) * 1e-3) / 1e9
+            g.copy_(g_host, non_blocking=True)
+            torch.cuda.synchronize()
             # Every step goes through the C ABI's host-buffer call
             # (cx_gradient_host): the control is copied in chunk by chunk, each
             # forward step waiting only for its own chunk, and the gradient
@@ -1123,6 +1137,7 @@ def main():
                    "h2d_bytes_per_step": g.numel() * g.element_size(),
                    "d2h_bytes_per_step": E.numel() * E.element_size() + 36, "ms_per_step": ms_e2e,
                    "call": "cx_gradient_host (host control in, host gradient and cost out)",
+                   "host_link": {k: round(v, 1) for k, v in link.items()},
                    "overlap": "control copied in 32 chunks, each forward step waiting for its own chunk; "
                               "gradient chunks read back during the reverse sweep"}
         except Exception as exc:  # pinned memory can fail on small hosts
