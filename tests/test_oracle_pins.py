@@ -99,6 +99,64 @@ def _problem(n=12, N=10, Q=9, chi=-0.1, adv=True, solid=False, seed=0, source_or
     return w, oracle.from_workload(w)
 
 
+# ------------------------------------------------- one node, one collision
+
+@pytest.mark.parametrize("n", [0, 5])
+def test_single_node_collision_moments(n):
+    """The local collision at one node against the moment conditions the
+    scheme is built on (Sec. 3.1: TF0, the K block acting on the fluxes, the
+    source moments of eq. PhiS with V chosen after PC13), for arbitrary
+    pre-collision populations and K from D by K = (D/(d Cs^2 tau) + I/2)^-1:
+      Phi^n       = r_vu u + r_vv v + g                     (u, v the moments of f)
+      sum P_u     = u                                       (no source for u; sum_i S_i = 0)
+      sum P_v     = v + c_n Phi^n + c'_n Phi^{n-1}          (c_0 = tau, c'_0 = 0; else 3tau/2, -tau/2)
+      sum e P_u   = j_u - K_u (j_u - a u)                   (chi = 0)
+      sum e P_v   = j_v - K_v (j_v - a v) + V (c_n Phi^n + c'_n Phi^{n-1}),  V = (I - K_v/2) a
+    and chi (the chemotactic cross-diffusion source of u) changes u's flux in
+    proportion to chi and neither u's mass nor species v.  (The direction of
+    that change, K_u G with G from v's non-equilibrium flux, is pinned by the
+    pseudo-spectral PDE comparisons.)"""
+    from dataclasses import replace
+
+    w = W.aniso(12, 12, 8, seed=4, precision=64, chi=0.0)
+    p0 = oracle.from_workload(w)
+    e, _, _, _ = oracle.lattice(9)
+    rng = np.random.default_rng(11 + n)
+    tau = p0.tau
+    c_now, c_prev = (tau, 0.0) if n == 0 else (1.5 * tau, -0.5 * tau)
+    for _ in range(4):
+        x, y = (int(v) for v in rng.integers(0, 12, 2))
+        a = p0.a[y, x]
+        fu = oracle.feq(9, rng.uniform(0.8, 1.2), a, p0.d_u) + rng.normal(0, 0.01, 9)
+        fv = oracle.feq(9, rng.uniform(0.1, 0.5), a, p0.d_v) + rng.normal(0, 0.01, 9)
+        g, phi_prev = rng.normal(0, 0.05), rng.normal(0, 0.05)
+        u, v = fu.sum(), fv.sum()
+        ju, jv = e.T @ fu, e.T @ fv
+        Pu, Pv, Phi = oracle.collide_node(p0, x, y, n, fu, fv, g, phi_prev)
+
+        def K_of(D, d):
+            Dm = np.array([[D[0], D[1]], [D[1], D[2]]])
+            return np.linalg.inv(Dm / (d * CS2 * tau) + 0.5 * np.eye(2))
+
+        Ku, Kv = K_of(p0.Du[y, x], p0.d_u), K_of(p0.Dv[y, x], p0.d_v)
+        src = c_now * Phi + c_prev * phi_prev
+        assert abs(Phi - (p0.r_vu * u + p0.r_vv * v + g)) < 1e-14
+        assert abs(Pu.sum() - u) < 1e-13
+        assert abs(Pv.sum() - (v + src)) < 1e-13
+        assert np.allclose(e.T @ Pu, ju - Ku @ (ju - a * u), rtol=0, atol=1e-13)
+        V = (np.eye(2) - 0.5 * Kv) @ a
+        assert np.allclose(e.T @ Pv, jv - Kv @ (jv - a * v) + V * src, rtol=0, atol=1e-13)
+
+        per_chi = []
+        for chi in (0.3, -0.7):
+            Pu_c, Pv_c, _ = oracle.collide_node(replace(p0, chi=chi), x, y, n, fu, fv, g, phi_prev)
+            assert abs(Pu_c.sum() - u) < 1e-13
+            assert np.array_equal(Pv_c, Pv)  # chemotaxis acts on u only
+            per_chi.append(e.T @ (Pu_c - Pu) / chi)
+        assert np.allclose(per_chi[0], per_chi[1], rtol=1e-9, atol=1e-13)
+        assert np.linalg.norm(per_chi[0]) > 1e-6
+
+
 # ----------------------------------------------------------- special cases
 
 def _bgk_numpy(p, s):
