@@ -78,6 +78,8 @@ def _load():
         lib.or_feq.argtypes = [ctypes.c_int, ctypes.c_double, vp, ctypes.c_double, vp]
         lib.or_collide_node.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp,
                                         ctypes.c_double, ctypes.c_double, vp, vp, dp]
+        lib.or_adjoint_node.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_double,
+                                        vp, vp, ctypes.c_int, ctypes.c_double, vp, vp, dp, dp]
         _lib = lib
     return _lib
 
@@ -271,6 +273,22 @@ def collide_node(p: Problem, x, y, n, f_u, f_v, g=0.0, phi_prev=0.0):
     _check(lib.or_collide_node(ctypes.byref(st), x, y, n, _ptr(fu), _ptr(fv), float(g), float(phi_prev),
                                _ptr(Pu), _ptr(Pv), ctypes.byref(phi)), "collide_node")
     return Pu, Pv, phi.value
+
+
+def adjoint_node(p: Problem, x, y, n, f_u, f_v, rho_u, rho_v, g=0.0, sigma_next=None):
+    """Local AMRT adjoint step at node (x, y), step n: the transpose of
+    collide_node applied to the pulled adjoint populations (rho_u, rho_v) and,
+    when sigma_next is given, to the adjoint c'_{n+1} sigma^{n+1} of Phi^n's
+    use at step n + 1.  Returns (psi_u, psi_v, sigma^n, lambda_Phi)."""
+    lib = _load()
+    st = p._struct()
+    fu, fv, ru, rv = _f64(f_u), _f64(f_v), _f64(rho_u), _f64(rho_v)
+    psu, psv = np.zeros(p.Q), np.zeros(p.Q)
+    sig, lam = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(lib.or_adjoint_node(ctypes.byref(st), x, y, n, _ptr(fu), _ptr(fv), float(g), _ptr(ru), _ptr(rv),
+                               0 if sigma_next is None else 1, 0.0 if sigma_next is None else float(sigma_next),
+                               _ptr(psu), _ptr(psv), ctypes.byref(sig), ctypes.byref(lam)), "adjoint_node")
+    return psu, psv, sig.value, lam.value
 
 
 def gd_step(p: Problem, g, lam_prev=None, c1=1e-4, max_trials=30):

@@ -685,6 +685,79 @@ int or_tlm(const or_problem* p, const double* g, const double* dg, const double*
 
 /* ------------------------------------------------------- AMRT adjoint */
 
+/* One node of the AMRT adjoint step at step n (Sec. 3.2.1, eqs. CAE, AEDs,
+ * CAE-L), the exact transpose of collide_local: from the pulled adjoint
+ * populations rho (rho_i(x) = psi^{n+1}_i(x + e_i)) and the node's forward
+ * state at step n (pre-collision populations f, Phi = Phi^n), the adjoint
+ * populations psi^n of the node, sigma^n = sum_i rho_v,i w~_i, and lambda_Phi,
+ * the adjoint of Phi^n (its use at step n and, when has_next, with
+ * c'_{n+1} sigma^{n+1} at step n + 1), which is dJ/dg^n without the penalty. */
+static void adjoint_local(const lattice_t* L, const or_problem* p, const node_t* nd, int n, const double* fu,
+                          const double* fv, double Phi, const double* ru, const double* rv, int has_next,
+                          double sigma_next, double* psi_u_out, double* psi_v_out, double* sigma_out,
+                          double* adj_Phi_out) {
+    const int Q = L->Q;
+    double Pi[9][9], mt[9], psi_u[9], psi_v[9];
+    /* forward state at (x, n) */
+    double Tu = 0.0, Tv = 0.0, jv[2] = {0.0, 0.0};
+    for (int i = 0; i < Q; ++i) {
+        Tu += fu[i];
+        Tv += fv[i];
+        jv[0] += L->e[i][0] * fv[i];
+        jv[1] += L->e[i][1] * fv[i];
+    }
+    double G[2];
+    grad_v(p, nd, Tv, jv, Phi, G);
+
+    /* AMRT collision: psi - Lambda^T (psi - psi^eq), with the
+     * moment-space adjoint equilibrium m~^eq_i = T = sum_j w_j aleph_j m~_j */
+    Pi_matrix(L, p, nd->Ku, Pi);
+    mrt_collide_T(L, Pi, ru, mt);
+    double Tcal = 0.0;
+    for (int j = 0; j < Q; ++j) Tcal += L->w[j] * nd->aleph_u[j] * mt[j];
+    for (int i = 0; i < Q; ++i) psi_u[i] = ru[i] - mt[i] + Tcal;
+    Pi_matrix(L, p, nd->Kv, Pi);
+    mrt_collide_T(L, Pi, rv, mt);
+    Tcal = 0.0;
+    for (int j = 0; j < Q; ++j) Tcal += L->w[j] * nd->aleph_v[j] * mt[j];
+    for (int i = 0; i < Q; ++i) psi_v[i] = rv[i] - mt[i] + Tcal;
+
+    /* coupling terms sum_k psi_k dR_k/dphi_i (CAE-L) */
+    double adj_Tu = 0.0, adj_Tv = 0.0, adj_Phi = 0.0, adj_jv[2];
+    /* R_u = tau S_u,  tau S_u,k = tau w_k/Cs^2 e_k . (K_u G) chi Tu / tau */
+    double Y[2] = {0.0, 0.0};
+    for (int i = 0; i < Q; ++i) {
+        Y[0] += ru[i] * L->w[i] / CS2 * L->e[i][0];
+        Y[1] += ru[i] * L->w[i] / CS2 * L->e[i][1];
+    }
+    double KG[2] = {nd->Ku[0][0] * G[0] + nd->Ku[0][1] * G[1], nd->Ku[1][0] * G[0] + nd->Ku[1][1] * G[1]};
+    adj_Tu += p->chi * (Y[0] * KG[0] + Y[1] * KG[1]);
+    double adj_G[2] = {p->chi * Tu * (nd->Ku[0][0] * Y[0] + nd->Ku[1][0] * Y[1]),
+                       p->chi * Tu * (nd->Ku[0][1] * Y[0] + nd->Ku[1][1] * Y[1])};
+    /* G = -(K_v (j_v - a v)/tau + K_v a Phi / 2) / (d_v Cs^2) */
+    double KtG[2] = {nd->Kv[0][0] * adj_G[0] + nd->Kv[1][0] * adj_G[1],
+                     nd->Kv[0][1] * adj_G[0] + nd->Kv[1][1] * adj_G[1]};
+    double sc = 1.0 / (p->d_v * CS2);
+    adj_jv[0] = -KtG[0] * sc / p->tau;
+    adj_jv[1] = -KtG[1] * sc / p->tau;
+    adj_Tv += (nd->a[0] * KtG[0] + nd->a[1] * KtG[1]) * sc / p->tau;
+    adj_Phi += -0.5 * (nd->a[0] * KtG[0] + nd->a[1] * KtG[1]) * sc;
+    /* R_v = w~ (c_n Phi^n + c'_n Phi^{n-1}) and the use of Phi^n at step n+1 */
+    double sigma = 0.0;
+    for (int i = 0; i < Q; ++i) sigma += rv[i] * nd->wt_v[i];
+    adj_Phi += c_now(p, n) * sigma;
+    if (has_next) adj_Phi += c_prev(p, n + 1) * sigma_next;
+    *sigma_out = sigma;
+    /* Phi = r_vu u + r_vv v + g */
+    adj_Tu += p->r_vu * adj_Phi;
+    adj_Tv += p->r_vv * adj_Phi;
+    *adj_Phi_out = adj_Phi;
+    for (int i = 0; i < Q; ++i) {
+        psi_u_out[i] = psi_u[i] + adj_Tu;
+        psi_v_out[i] = psi_v[i] + adj_Tv + L->e[i][0] * adj_jv[0] + L->e[i][1] * adj_jv[1];
+    }
+}
+
 int or_adjoint(const or_problem* p, const double* g, const double* seed_u, const double* seed_v,
                double* dJdg, double* psi0, double* J) {
     lattice_t L;
@@ -732,73 +805,16 @@ int or_adjoint(const or_problem* p, const double* g, const double* seed_u, const
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x) {
                 if (is_solid(p, x, y)) continue;
-                double Pi[9][9], mt[9], psi_u[9], psi_v[9];
                 size_t k = (size_t)y * nx + x;
-                const node_t* nd = &nodes[k];
                 const double *fu = f + (k * 2) * Q, *fv = f + (k * 2 + 1) * Q;
                 const double *ru = rho + (k * 2) * Q, *rv = rho + (k * 2 + 1) * Q;
-                /* forward state at (x, n) */
-                double Tu = 0.0, Tv = 0.0, jv[2] = {0.0, 0.0};
-                for (int i = 0; i < Q; ++i) {
-                    Tu += fu[i];
-                    Tv += fv[i];
-                    jv[0] += L.e[i][0] * fv[i];
-                    jv[1] += L.e[i][1] * fv[i];
-                }
-                double Phi = Phi_traj[(size_t)n * nn + k];
-                double G[2];
-                grad_v(p, nd, Tv, jv, Phi, G);
-
-                /* AMRT collision: psi - Lambda^T (psi - psi^eq), with the
-                 * moment-space adjoint equilibrium m~^eq_i = T = sum_j w_j aleph_j m~_j */
-                Pi_matrix(&L, p, nd->Ku, Pi);
-                mrt_collide_T(&L, Pi, ru, mt);
-                double Tcal = 0.0;
-                for (int j = 0; j < Q; ++j) Tcal += L.w[j] * nd->aleph_u[j] * mt[j];
-                for (int i = 0; i < Q; ++i) psi_u[i] = ru[i] - mt[i] + Tcal;
-                Pi_matrix(&L, p, nd->Kv, Pi);
-                mrt_collide_T(&L, Pi, rv, mt);
-                Tcal = 0.0;
-                for (int j = 0; j < Q; ++j) Tcal += L.w[j] * nd->aleph_v[j] * mt[j];
-                for (int i = 0; i < Q; ++i) psi_v[i] = rv[i] - mt[i] + Tcal;
-
-                /* coupling terms sum_k psi_k dR_k/dphi_i (CAE-L) */
-                double adj_Tu = 0.0, adj_Tv = 0.0, adj_Phi = 0.0, adj_jv[2];
-                /* R_u = tau S_u,  tau S_u,k = tau w_k/Cs^2 e_k . (K_u G) chi Tu / tau */
-                double Y[2] = {0.0, 0.0};
-                for (int i = 0; i < Q; ++i) {
-                    Y[0] += ru[i] * L.w[i] / CS2 * L.e[i][0];
-                    Y[1] += ru[i] * L.w[i] / CS2 * L.e[i][1];
-                }
-                double KG[2] = {nd->Ku[0][0] * G[0] + nd->Ku[0][1] * G[1], nd->Ku[1][0] * G[0] + nd->Ku[1][1] * G[1]};
-                adj_Tu += p->chi * (Y[0] * KG[0] + Y[1] * KG[1]);
-                double adj_G[2] = {p->chi * Tu * (nd->Ku[0][0] * Y[0] + nd->Ku[1][0] * Y[1]),
-                                   p->chi * Tu * (nd->Ku[0][1] * Y[0] + nd->Ku[1][1] * Y[1])};
-                /* G = -(K_v (j_v - a v)/tau + K_v a Phi / 2) / (d_v Cs^2) */
-                double KtG[2] = {nd->Kv[0][0] * adj_G[0] + nd->Kv[1][0] * adj_G[1],
-                                 nd->Kv[0][1] * adj_G[0] + nd->Kv[1][1] * adj_G[1]};
-                double sc = 1.0 / (p->d_v * CS2);
-                adj_jv[0] = -KtG[0] * sc / p->tau;
-                adj_jv[1] = -KtG[1] * sc / p->tau;
-                adj_Tv += (nd->a[0] * KtG[0] + nd->a[1] * KtG[1]) * sc / p->tau;
-                adj_Phi += -0.5 * (nd->a[0] * KtG[0] + nd->a[1] * KtG[1]) * sc;
-                /* R_v = w~ (c_n Phi^n + c'_n Phi^{n-1}) and the use of Phi^n at step n+1 */
-                double sigma = 0.0;
-                for (int i = 0; i < Q; ++i) sigma += rv[i] * nd->wt_v[i];
-                adj_Phi += c_now(p, n) * sigma;
-                if (n + 1 <= N - 1) adj_Phi += c_prev(p, n + 1) * sigma_next[k];
-                sigma_now[k] = sigma;
-                /* Phi = r_vu u + r_vv v + g */
-                adj_Tu += p->r_vu * adj_Phi;
-                adj_Tv += p->r_vv * adj_Phi;
+                double adj_Phi;
+                adjoint_local(&L, p, &nodes[k], n, fu, fv, Phi_traj[(size_t)n * nn + k], ru, rv, n + 1 <= N - 1,
+                              sigma_next[k], psi + (k * 2) * Q, psi + (k * 2 + 1) * Q, &sigma_now[k], &adj_Phi);
                 int c = ctrl_index(p, x, y);
                 if (c >= 0 && dJdg) {
                     double gv = g ? g[(size_t)n * nc + c] : 0.0;
                     dJdg[(size_t)n * nc + c] = adj_Phi + 2.0 * p->alpha * gv;
-                }
-                for (int i = 0; i < Q; ++i) {
-                    psi[(k * 2) * Q + i] = psi_u[i] + adj_Tu;
-                    psi[(k * 2 + 1) * Q + i] = psi_v[i] + adj_Tv + L.e[i][0] * adj_jv[0] + L.e[i][1] * adj_jv[1];
                 }
             }
         double* t = sigma_next;
@@ -812,6 +828,25 @@ int or_adjoint(const or_problem* p, const double* g, const double* seed_u, const
 }
 
 /* ------------------------------------------------------ unit-test access */
+
+int or_adjoint_node(const or_problem* p, int x, int y, int n, const double* f_u, const double* f_v, double g,
+                    const double* rho_u, const double* rho_v, int has_next, double sigma_next, double* psi_u,
+                    double* psi_v, double* sigma_out, double* lam_Phi) {
+    lattice_t L;
+    if (lattice_init(&L, p->Q)) return -1;
+    if (x < 0 || y < 0 || x >= p->nx || y >= p->ny) return -3;
+    node_t nd;
+    node_params(&L, p, x, y, &nd);
+    double Tu = 0.0, Tv = 0.0;
+    for (int i = 0; i < p->Q; ++i) {
+        Tu += f_u[i];
+        Tv += f_v[i];
+    }
+    const double Phi = p->r_vu * Tu + p->r_vv * Tv + g; /* as collide_local forms Phi^n */
+    adjoint_local(&L, p, &nd, n, f_u, f_v, Phi, rho_u, rho_v, has_next, sigma_next, psi_u, psi_v, sigma_out,
+                  lam_Phi);
+    return 0;
+}
 
 int or_set_threads(int n) {
 #ifdef _OPENMP

@@ -71,6 +71,17 @@ int or_collide_node(const or_problem* p, int x, int y, int n,
                     const double* f_u, const double* f_v, double g, double Phi_prev,
                     double* P_u, double* P_v, double* Phi_out);
 
+/* One node of the AMRT adjoint step at step n, exposing the local transposed
+ * map for unit tests: given the node's pre-collision populations f_u, f_v and
+ * control g at step n, and the pulled adjoint populations rho_u, rho_v, it
+ * returns psi_u, psi_v (the node's adjoint populations psi^n), sigma^n =
+ * sum_i rho_v,i w~_i and lam_Phi, the adjoint of Phi^n (dJ/dg^n without the
+ * penalty term).  has_next: Phi^n is also used at step n + 1, whose
+ * sigma^{n+1} is sigma_next.  All arrays are [Q]. */
+int or_adjoint_node(const or_problem* p, int x, int y, int n, const double* f_u, const double* f_v, double g,
+                    const double* rho_u, const double* rho_v, int has_next, double sigma_next, double* psi_u,
+                    double* psi_v, double* sigma_out, double* lam_Phi);
+
 /* Forward solve; uN, vN may be NULL.  Returns 0 on success. */
 int or_forward(const or_problem* p, const double* g, double* J, double* uN, double* vN);
 

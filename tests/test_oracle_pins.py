@@ -157,6 +157,54 @@ def test_single_node_collision_moments(n):
         assert np.linalg.norm(per_chi[0]) > 1e-6
 
 
+@pytest.mark.parametrize("n", [0, 5])
+def test_local_adjoint_is_the_transposed_local_jacobian(n):
+    """One node of the AMRT step against the dense Jacobian of one forward
+    collision at that node, by central differences (the unit-level form of
+    the adjoint checks; Sec. 3.2.1: transposed collision, scalar adjoint
+    equilibrium, coupling terms CAE-L).  With L = rho_u.P_u + rho_v.P_v +
+    lam Phi^n (lam = c'_{n+1} sigma^{n+1}, the adjoint of Phi^n's use at step
+    n + 1): psi_u = dL/df_u, psi_v = dL/df_v, lambda_Phi = dL/dg and
+    c'_n sigma^n = dL/dPhi^{n-1}, for every input of the 18 + 2."""
+    w = W.aniso(12, 12, 8, seed=4, precision=64, chi=-0.4)
+    w.r_vu, w.r_vv = 0.3, -0.2
+    p = oracle.from_workload(w)
+    e, _, _, _ = oracle.lattice(9)
+    rng = np.random.default_rng(21 + n)
+    tau = p.tau
+    c_prev_n = 0.0 if n == 0 else -0.5 * tau
+    c_prev_next = -0.5 * tau
+    h = 1e-6
+    for _ in range(3):
+        x, y = (int(v) for v in rng.integers(0, 12, 2))
+        a = p.a[y, x]
+        fu = oracle.feq(9, rng.uniform(0.8, 1.2), a, p.d_u) + rng.normal(0, 0.01, 9)
+        fv = oracle.feq(9, rng.uniform(0.1, 0.5), a, p.d_v) + rng.normal(0, 0.01, 9)
+        g, phi_prev = rng.normal(0, 0.05), rng.normal(0, 0.05)
+        ru, rv, sig_next = rng.normal(size=9), rng.normal(size=9), rng.normal()
+        lam_next = c_prev_next * sig_next
+
+        def L(fu_, fv_, g_, pp_):
+            Pu, Pv, Phi = oracle.collide_node(p, x, y, n, fu_, fv_, g_, pp_)
+            return ru @ Pu + rv @ Pv + lam_next * Phi
+
+        dfu, dfv = np.zeros(9), np.zeros(9)
+        for i in range(9):
+            d = np.zeros(9)
+            d[i] = h
+            dfu[i] = (L(fu + d, fv, g, phi_prev) - L(fu - d, fv, g, phi_prev)) / (2 * h)
+            dfv[i] = (L(fu, fv + d, g, phi_prev) - L(fu, fv - d, g, phi_prev)) / (2 * h)
+        dg = (L(fu, fv, g + h, phi_prev) - L(fu, fv, g - h, phi_prev)) / (2 * h)
+        dpp = (L(fu, fv, g, phi_prev + h) - L(fu, fv, g, phi_prev - h)) / (2 * h)
+
+        psu, psv, sigma, lam_phi = oracle.adjoint_node(p, x, y, n, fu, fv, ru, rv, g=g, sigma_next=sig_next)
+        scale = max(np.abs(dfu).max(), np.abs(dfv).max(), 1.0)
+        assert np.allclose(psu, dfu, rtol=0, atol=1e-8 * scale)
+        assert np.allclose(psv, dfv, rtol=0, atol=1e-8 * scale)
+        assert abs(lam_phi - dg) < 1e-8 * scale
+        assert abs(c_prev_n * sigma - dpp) < 1e-8 * scale
+
+
 # ----------------------------------------------------------- special cases
 
 def _bgk_numpy(p, s):
