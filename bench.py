@@ -1165,9 +1165,15 @@ def main():
 
     launches_per_step = 3 * w.N - wl["k"] + 3
     if rank == 0:
-        cpu = None if args.no_cpu_baseline else cpu_baseline()
-        fp32_err = None if args.profile else fp32_error_vs_oracle(dev)
-        geom = None if args.profile else geometry_block(dev, args.staging)
+        def guarded(fn, *a):  # a block that fails reports its error; the bench line still prints
+            try:
+                return fn(*a)
+            except Exception as exc:
+                return {"error": str(exc)[:200]}
+
+        cpu = None if args.no_cpu_baseline else guarded(cpu_baseline)
+        fp32_err = None if args.profile else guarded(fp32_error_vs_oracle, dev)
+        geom = None if args.profile else guarded(geometry_block, dev, args.staging)
         bb = None
         if not args.profile and not args.no_batch:
             try:
