@@ -502,6 +502,10 @@ def _load3():
         lib.or3_forward_trace.argtypes = [P, vp, vp]
         lib.or3_tlm.argtypes = [P, vp, vp, vp, vp, dp]
         lib.or3_adjoint.argtypes = [P, vp, vp, vp, vp, dp]
+        lib.or3_collide_node.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ctypes.c_double, vp, vp,
+                                         vp]
+        lib.or3_adjoint_node.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ctypes.c_double, vp,
+                                         ctypes.c_int, vp, vp, vp, vp]
         lib._or3_ready = True
     return lib
 
@@ -546,6 +550,31 @@ def adjoint3(p: Problem3, g=None, seeds=None, want_psi0=False):
     _check(lib.or3_adjoint(ctypes.byref(st), _ptr(_f64(g)), _ptr(_f64(seeds)), _ptr(E), _ptr(psi0),
                            ctypes.byref(J)), "adjoint3")
     return J.value, E, psi0
+
+
+def collide3_node(p: Problem3, x, y, n, f, g=0.0, phi_prev=(0.0, 0.0, 0.0)):
+    """One three-species collision at node (x, y), step n: f [3][9] ->
+    (P [3][9], Phi^n [3])."""
+    lib = _load3()
+    st = p._struct()
+    P, phi = np.zeros((3, 9)), np.zeros(3)
+    _check(lib.or3_collide_node(ctypes.byref(st), x, y, n, _ptr(_f64(f)), float(g), _ptr(_f64(phi_prev)), _ptr(P),
+                                _ptr(phi)), "collide3_node")
+    return P, phi
+
+
+def adjoint3_node(p: Problem3, x, y, n, f, rho, g=0.0, sigma_next=None):
+    """Local three-species AMRT step at node (x, y), step n, the transpose of
+    collide3_node applied to rho [3][9] and, when sigma_next [3] is given, to
+    the adjoint c'_{n+1} sigma^{n+1} of each Phi^n's use at step n + 1.
+    Returns (psi [3][9], sigma^n [3], lambda_Phi [3])."""
+    lib = _load3()
+    st = p._struct()
+    psi, sig, lam = np.zeros((3, 9)), np.zeros(3), np.zeros(3)
+    _check(lib.or3_adjoint_node(ctypes.byref(st), x, y, n, _ptr(_f64(f)), float(g), _ptr(_f64(rho)),
+                                0 if sigma_next is None else 1, _ptr(_f64(sigma_next)), _ptr(psi), _ptr(sig),
+                                _ptr(lam)), "adjoint3_node")
+    return psi, sig, lam
 
 
 def from_workload3(w, N=None) -> Problem3:

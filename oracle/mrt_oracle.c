@@ -1326,6 +1326,79 @@ int or3_tlm(const or3_problem* p, const double* g, const double* dg, const doubl
  * (adjoints of u^N, v^N, w^N), NULL meaning (u^N - u_tgt, 0, 0); with seeds the
  * gradient is that of sum(seed . uvw^N) + alpha ||g||^2.  dJdg [N][ny][nx];
  * psi0 [ny][nx][3][Q] (may be NULL); J (may be NULL). */
+/* One node of the three-species AMRT step at step n, the exact transpose of
+ * collide3: from the pulled adjoint populations rho ([3][Q], rho_i(x) =
+ * psi^{n+1}_i(x + e_i)) and the node's forward state at step n (pre-collision
+ * populations f [3][Q], Phi = Phi^n [3]), the node's adjoint populations psi
+ * [3][Q], sigma^n [3] and aPhi [3], the adjoint of each species' Phi^n (its
+ * use at step n and, when has_next, with c'_{n+1} sigma^{n+1} at step n + 1). */
+static void adjoint3_local(const lattice_t* L, const or3_problem* p, const node3_t* nd, int n, const double* fk,
+                           const double* Ph, const double* rk, int has_next, const double* sig_next,
+                           double* psi_out, double* sig_out, double* aPhi) {
+    const int Q = L->Q;
+    /* forward state at (x, n) */
+    double T[3] = {0, 0, 0}, j[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+    for (int sp = 0; sp < 3; ++sp)
+        for (int i = 0; i < Q; ++i) {
+            T[sp] += fk[sp * Q + i];
+            j[sp][0] += L->e[i][0] * fk[sp * Q + i];
+            j[sp][1] += L->e[i][1] * fk[sp * Q + i];
+        }
+    double Gv[2], Gw[2];
+    grad3(p, nd->K[1], nd->a, T[1], j[1], Ph[1], Gv);
+    grad3(p, nd->K[2], nd->a, T[2], j[2], Ph[2], Gw);
+    /* transposed MRT collisions with the adjoint equilibrium broadcast */
+    double out[27], Pi[9][9], mt[9];
+    for (int sp = 0; sp < 3; ++sp) {
+        Pi_rates(p->s, nd->K[sp], Pi);
+        mrt_collide_T(L, Pi, rk + sp * Q, mt);
+        double Tcal = 0.0;
+        for (int i = 0; i < Q; ++i) Tcal += L->w[i] * nd->aleph[sp][i] * mt[i];
+        for (int i = 0; i < Q; ++i) out[sp * Q + i] = rk[sp * Q + i] - mt[i] + Tcal;
+    }
+    /* adjoint of tau S_u = (w_i/Cs^2) e_i . K_u F,  F = u (chi1 G_v + chi2 G_w) */
+    double Y[2] = {0.0, 0.0};
+    for (int i = 0; i < Q; ++i) {
+        Y[0] += rk[i] * L->w[i] / CS2 * L->e[i][0];
+        Y[1] += rk[i] * L->w[i] / CS2 * L->e[i][1];
+    }
+    double aF[2] = {nd->K[0][0][0] * Y[0] + nd->K[0][1][0] * Y[1], nd->K[0][0][1] * Y[0] + nd->K[0][1][1] * Y[1]};
+    double aT[3] = {0, 0, 0}, aj[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+    for (int sp = 0; sp < 3; ++sp) aPhi[sp] = 0.0;
+    for (int c2 = 0; c2 < 2; ++c2) aT[0] += (p->chi1 * Gv[c2] + p->chi2 * Gw[c2]) * aF[c2];
+    double aG[3][2];
+    for (int c2 = 0; c2 < 2; ++c2) {
+        aG[1][c2] = p->chi1 * T[0] * aF[c2];
+        aG[2][c2] = p->chi2 * T[0] * aF[c2];
+    }
+    /* G_Theta = -(K (j - a T)/tau + K a Phi / 2) / (d Cs^2), Theta = v, w */
+    for (int sp = 1; sp < 3; ++sp) {
+        double KtG[2] = {nd->K[sp][0][0] * aG[sp][0] + nd->K[sp][1][0] * aG[sp][1],
+                         nd->K[sp][0][1] * aG[sp][0] + nd->K[sp][1][1] * aG[sp][1]};
+        double sc = 1.0 / (p->d * CS2);
+        aj[sp][0] = -KtG[0] * sc / p->tau;
+        aj[sp][1] = -KtG[1] * sc / p->tau;
+        aT[sp] += (nd->a[0] * KtG[0] + nd->a[1] * KtG[1]) * sc / p->tau;
+        aPhi[sp] += -0.5 * (nd->a[0] * KtG[0] + nd->a[1] * KtG[1]) * sc;
+    }
+    /* sources w~ (c_n Phi^n + c'_n Phi^{n-1}) and the use of Phi^n at step n+1 */
+    for (int sp = 0; sp < 3; ++sp) {
+        double sig = 0.0;
+        for (int i = 0; i < Q; ++i) sig += rk[sp * Q + i] * nd->wt[sp][i];
+        aPhi[sp] += c3_now(p, n) * sig;
+        if (has_next) aPhi[sp] += c3_prev(p, n + 1) * sig_next[sp];
+        sig_out[sp] = sig;
+    }
+    /* Phi_u = a1 u - a2 u^2, Phi_v = b1 u - b2 v - b3 u v (+ g), Phi_w = c1 u - c2 w (+ g) */
+    aT[0] += (p->a1 - 2.0 * p->a2 * T[0]) * aPhi[0] + (p->b1 - p->b3 * T[1]) * aPhi[1] + p->c1 * aPhi[2];
+    aT[1] += -(p->b2 + p->b3 * T[0]) * aPhi[1];
+    aT[2] += -p->c2 * aPhi[2];
+    for (int sp = 0; sp < 3; ++sp)
+        for (int i = 0; i < Q; ++i)
+            psi_out[sp * Q + i] =
+                out[sp * Q + i] + aT[sp] + L->e[i][0] * aj[sp][0] + L->e[i][1] * aj[sp][1];
+}
+
 int or3_adjoint(const or3_problem* p, const double* g, const double* seeds, double* dJdg, double* psi0, double* J) {
     lattice_t L;
     if (lattice_init(&L, 9)) return -1;
@@ -1361,74 +1434,14 @@ int or3_adjoint(const or3_problem* p, const double* g, const double* seeds, doub
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x) {
                 size_t k = (size_t)y * nx + x;
-                const node3_t* nd = &nodes[k];
-                const double* fk = f + k * 3 * Q;
-                const double* rk = rho + k * 3 * Q;
-                /* forward state at (x, n) */
-                double T[3] = {0, 0, 0}, j[3][2] = {{0, 0}, {0, 0}, {0, 0}};
-                for (int sp = 0; sp < 3; ++sp)
-                    for (int i = 0; i < Q; ++i) {
-                        T[sp] += fk[sp * Q + i];
-                        j[sp][0] += L.e[i][0] * fk[sp * Q + i];
-                        j[sp][1] += L.e[i][1] * fk[sp * Q + i];
-                    }
-                const double* Ph = Phi_traj + ((size_t)n * nn + k) * 3;
-                double Gv[2], Gw[2];
-                grad3(p, nd->K[1], nd->a, T[1], j[1], Ph[1], Gv);
-                grad3(p, nd->K[2], nd->a, T[2], j[2], Ph[2], Gw);
-                /* transposed MRT collisions with the adjoint equilibrium broadcast */
-                double out[27], Pi[9][9], mt[9];
-                for (int sp = 0; sp < 3; ++sp) {
-                    Pi_rates(p->s, nd->K[sp], Pi);
-                    mrt_collide_T(&L, Pi, rk + sp * Q, mt);
-                    double Tcal = 0.0;
-                    for (int i = 0; i < Q; ++i) Tcal += L.w[i] * nd->aleph[sp][i] * mt[i];
-                    for (int i = 0; i < Q; ++i) out[sp * Q + i] = rk[sp * Q + i] - mt[i] + Tcal;
-                }
-                /* adjoint of tau S_u = (w_i/Cs^2) e_i . K_u F,  F = u (chi1 G_v + chi2 G_w) */
-                double Y[2] = {0.0, 0.0};
-                for (int i = 0; i < Q; ++i) {
-                    Y[0] += rk[i] * L.w[i] / CS2 * L.e[i][0];
-                    Y[1] += rk[i] * L.w[i] / CS2 * L.e[i][1];
-                }
-                double aF[2] = {nd->K[0][0][0] * Y[0] + nd->K[0][1][0] * Y[1], nd->K[0][0][1] * Y[0] + nd->K[0][1][1] * Y[1]};
-                double aT[3] = {0, 0, 0}, aPhi[3] = {0, 0, 0}, aj[3][2] = {{0, 0}, {0, 0}, {0, 0}};
-                for (int c2 = 0; c2 < 2; ++c2) aT[0] += (p->chi1 * Gv[c2] + p->chi2 * Gw[c2]) * aF[c2];
-                double aG[3][2];
-                for (int c2 = 0; c2 < 2; ++c2) {
-                    aG[1][c2] = p->chi1 * T[0] * aF[c2];
-                    aG[2][c2] = p->chi2 * T[0] * aF[c2];
-                }
-                /* G_Theta = -(K (j - a T)/tau + K a Phi / 2) / (d Cs^2), Theta = v, w */
-                for (int sp = 1; sp < 3; ++sp) {
-                    double KtG[2] = {nd->K[sp][0][0] * aG[sp][0] + nd->K[sp][1][0] * aG[sp][1],
-                                     nd->K[sp][0][1] * aG[sp][0] + nd->K[sp][1][1] * aG[sp][1]};
-                    double sc = 1.0 / (p->d * CS2);
-                    aj[sp][0] = -KtG[0] * sc / p->tau;
-                    aj[sp][1] = -KtG[1] * sc / p->tau;
-                    aT[sp] += (nd->a[0] * KtG[0] + nd->a[1] * KtG[1]) * sc / p->tau;
-                    aPhi[sp] += -0.5 * (nd->a[0] * KtG[0] + nd->a[1] * KtG[1]) * sc;
-                }
-                /* sources w~ (c_n Phi^n + c'_n Phi^{n-1}) and the use of Phi^n at step n+1 */
-                for (int sp = 0; sp < 3; ++sp) {
-                    double sig = 0.0;
-                    for (int i = 0; i < Q; ++i) sig += rk[sp * Q + i] * nd->wt[sp][i];
-                    aPhi[sp] += c3_now(p, n) * sig;
-                    if (n + 1 <= N - 1) aPhi[sp] += c3_prev(p, n + 1) * sig_next[3 * k + sp];
-                    sig_now[3 * k + sp] = sig;
-                }
-                /* Phi_u = a1 u - a2 u^2, Phi_v = b1 u - b2 v - b3 u v (+ g), Phi_w = c1 u - c2 w (+ g) */
-                aT[0] += (p->a1 - 2.0 * p->a2 * T[0]) * aPhi[0] + (p->b1 - p->b3 * T[1]) * aPhi[1] + p->c1 * aPhi[2];
-                aT[1] += -(p->b2 + p->b3 * T[0]) * aPhi[1];
-                aT[2] += -p->c2 * aPhi[2];
+                double aPhi[3];
+                adjoint3_local(&L, p, &nodes[k], n, f + k * 3 * Q, Phi_traj + ((size_t)n * nn + k) * 3,
+                               rho + k * 3 * Q, n + 1 <= N - 1, sig_next + 3 * k, psi + k * 3 * Q,
+                               sig_now + 3 * k, aPhi);
                 if (dJdg) {
                     double gv = g ? g[(size_t)n * nn + k] : 0.0;
                     dJdg[(size_t)n * nn + k] = aPhi[p->ctrl_species] + 2.0 * p->alpha * gv;
                 }
-                for (int sp = 0; sp < 3; ++sp)
-                    for (int i = 0; i < Q; ++i)
-                        psi[(k * 3 + sp) * Q + i] =
-                            out[sp * Q + i] + aT[sp] + L.e[i][0] * aj[sp][0] + L.e[i][1] * aj[sp][1];
             }
         double* t = sig_next;
         sig_next = sig_now;
@@ -1436,5 +1449,35 @@ int or3_adjoint(const or3_problem* p, const double* g, const double* seeds, doub
     }
     if (psi0) memcpy(psi0, psi, sizeof(double) * npop);
     free(traj); free(Phi_traj); free(fN); free(psi); free(rho); free(sig_next); free(sig_now); free(uvw); free(nodes);
+    return 0;
+}
+
+int or3_collide_node(const or3_problem* p, int x, int y, int n, const double* f, double g, const double* Phi_prev,
+                     double* P, double* Phi_out) {
+    lattice_t L;
+    if (lattice_init(&L, 9)) return -1;
+    if (x < 0 || y < 0 || x >= p->nx || y >= p->ny) return -3;
+    node3_t nd;
+    node3_params(&L, p, x, y, &nd);
+    state3_t st;
+    collide3(&L, p, &nd, n, f, g, Phi_prev, P, &st);
+    for (int sp = 0; sp < 3; ++sp) Phi_out[sp] = st.Phi[sp];
+    return 0;
+}
+
+int or3_adjoint_node(const or3_problem* p, int x, int y, int n, const double* f, double g, const double* rho,
+                     int has_next, const double* sigma_next, double* psi, double* sigma_out, double* lam_Phi) {
+    lattice_t L;
+    if (lattice_init(&L, 9)) return -1;
+    if (x < 0 || y < 0 || x >= p->nx || y >= p->ny) return -3;
+    node3_t nd;
+    node3_params(&L, p, x, y, &nd);
+    double T[3] = {0, 0, 0};
+    for (int sp = 0; sp < 3; ++sp)
+        for (int i = 0; i < 9; ++i) T[sp] += f[sp * 9 + i];
+    double Phi[3];
+    phi3(p, T[0], T[1], T[2], g, Phi); /* as collide3 forms Phi^n */
+    const double zero[3] = {0, 0, 0};
+    adjoint3_local(&L, p, &nd, n, f, Phi, rho, has_next, sigma_next ? sigma_next : zero, psi, sigma_out, lam_Phi);
     return 0;
 }

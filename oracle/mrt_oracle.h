@@ -150,6 +150,18 @@ int or3_forward(const or3_problem* p, const double* g, double* J, double* uvwN);
 int or3_forward_trace(const or3_problem* p, const double* g, double* trace);
 int or3_tlm(const or3_problem* p, const double* g, const double* dg, const double* df0, double* duvwN, double* dJ);
 int or3_adjoint(const or3_problem* p, const double* g, const double* seeds, double* dJdg, double* psi0, double* J);
+/* One collision of the three species at one node (pre-collision f [3][Q] ->
+ * post-collision P [3][Q], Phi^n [3]), for unit tests; Phi_prev [3] is
+ * Phi^{n-1} (ignored at n = 0). */
+int or3_collide_node(const or3_problem* p, int x, int y, int n, const double* f, double g, const double* Phi_prev,
+                     double* P, double* Phi_out);
+/* One node of the three-species AMRT step, the transpose of or3_collide_node:
+ * from the pulled adjoint populations rho [3][Q] (and, when has_next, the
+ * species' sigma^{n+1} [3] for Phi^n's use at step n + 1) it returns psi
+ * [3][Q], sigma^n [3] and lam_Phi [3], the adjoint of each species' Phi^n
+ * (lam_Phi of the controlled species is dJ/dg^n without the penalty). */
+int or3_adjoint_node(const or3_problem* p, int x, int y, int n, const double* f, double g, const double* rho,
+                     int has_next, const double* sigma_next, double* psi, double* sigma_out, double* lam_Phi);
 
 #ifdef __cplusplus
 }

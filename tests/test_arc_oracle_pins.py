@@ -219,3 +219,47 @@ def test_arc_system_against_pde():
     for c in range(3):
         r1, r2 = errs[0][c] / errs[1][c], errs[1][c] / errs[2][c]
         assert 3.5 < r1 < 4.6 and 3.5 < r2 < 4.6, errs
+
+
+@pytest.mark.parametrize("n,ctrl", [(0, 1), (4, 2)])
+def test_local_adjoint_is_the_transposed_local_jacobian(n, ctrl):
+    """One node of the three-species AMRT step against the dense Jacobian of
+    one collision at that node by central differences (27 populations, the
+    control and the three Phi^{n-1}).  With L = rho.P + sum_s lam_s Phi_s^n
+    (lam_s = c'_{n+1} sigma_s^{n+1}): psi = dL/df, lambda_Phi of the
+    controlled species = dL/dg and c'_n sigma_s^n = dL/dPhi_s^{n-1}.  The maps
+    are at most quadratic (chemotaxis u G, logistic u^2, consumption u v), so
+    central differences are exact up to rounding."""
+    p = _arc(n=8, N=6, seed=3, ctrl_species=ctrl)
+    e, _, _, _ = oracle.lattice(9)
+    rng = np.random.default_rng(40 + n)
+    tau = p.tau
+    c_prev_n = 0.0 if n == 0 else -0.5 * tau
+    h = 1e-6
+    for _ in range(2):
+        x, y = (int(v) for v in rng.integers(0, 8, 2))
+        a = p.a[y, x]
+        f = np.stack([oracle.feq(9, rng.uniform(lo, hi), a, p.d) for lo, hi in ((0.8, 1.2), (0.3, 0.6), (0.2, 0.5))])
+        f = f + rng.normal(0, 0.01, (3, 9))
+        g, pp = rng.normal(0, 0.05), rng.normal(0, 0.05, 3)
+        rho, sig_next = rng.normal(size=(3, 9)), rng.normal(size=3)
+        lam_next = -0.5 * tau * sig_next
+
+        def L(f_, g_, pp_):
+            P, phi = oracle.collide3_node(p, x, y, n, f_, g_, pp_)
+            return float(np.sum(rho * P) + lam_next @ phi)
+
+        dfd = np.zeros((3, 9))
+        for s in range(3):
+            for i in range(9):
+                d = np.zeros((3, 9))
+                d[s, i] = h
+                dfd[s, i] = (L(f + d, g, pp) - L(f - d, g, pp)) / (2 * h)
+        dg = (L(f, g + h, pp) - L(f, g - h, pp)) / (2 * h)
+        dpp = np.array([(L(f, g, pp + h * np.eye(3)[s]) - L(f, g, pp - h * np.eye(3)[s])) / (2 * h) for s in range(3)])
+
+        psi, sigma, lam_phi = oracle.adjoint3_node(p, x, y, n, f, rho, g=g, sigma_next=sig_next)
+        scale = max(np.abs(dfd).max(), 1.0)
+        assert np.allclose(psi, dfd, rtol=0, atol=1e-8 * scale)
+        assert abs(lam_phi[ctrl] - dg) < 1e-8 * scale
+        assert np.allclose(c_prev_n * sigma, dpp, rtol=0, atol=1e-8 * scale)
