@@ -651,6 +651,10 @@ def _load3d():
         lib.od3_forward_trace.argtypes = [P, vp, vp, vp, vp]
         lib.od3_tlm.argtypes = [P, vp, vp, vp, vp, vp]
         lib.od3_adjoint.argtypes = [P, vp, vp, vp, vp, vp, dp]
+        ci = ctypes.c_int
+        lib.od3_collide_node.argtypes = [P, ci, ci, ci, ci, vp, ctypes.c_double, ctypes.c_double, vp, dp]
+        lib.od3_adjoint_node.argtypes = [P, ci, ci, ci, ci, vp, ctypes.c_double, vp, ci, ctypes.c_double, vp, dp,
+                                         dp]
         lib.od3_set_threads.argtypes = [ctypes.c_int]
         lib._od3_ready = True
     return lib
@@ -707,6 +711,30 @@ def adjoint3d(p: Problem3D, g=None, seed_u=None, seed_v=None, want_psi0=False):
     _check(lib.od3_adjoint(ctypes.byref(st), _ptr(_f64(g)), _ptr(_f64(seed_u)), _ptr(_f64(seed_v)), _ptr(E),
                            _ptr(psi0), ctypes.byref(J)), "adjoint3d")
     return J.value, E, psi0
+
+
+def collide3d_node(p: Problem3D, x, y, z, n, f, g=0.0, phi_prev=0.0):
+    """One D3Q19 collision at node (x, y, z), step n: f [2][19] -> (P [2][19], Phi^n)."""
+    lib = _load3d()
+    st = p._struct()
+    P, phi = np.zeros((2, 19)), ctypes.c_double(0.0)
+    _check(lib.od3_collide_node(ctypes.byref(st), x, y, z, n, _ptr(_f64(f)), float(g), float(phi_prev), _ptr(P),
+                                ctypes.byref(phi)), "collide3d_node")
+    return P, phi.value
+
+
+def adjoint3d_node(p: Problem3D, x, y, z, n, f, rho, g=0.0, sigma_next=None):
+    """Local D3Q19 AMRT step at node (x, y, z), step n, the transpose of
+    collide3d_node applied to rho [2][19] and, when sigma_next is given, to
+    the adjoint c'_{n+1} sigma^{n+1} of Phi^n's use at step n + 1.
+    Returns (psi [2][19], sigma^n, lambda_Phi)."""
+    lib = _load3d()
+    st = p._struct()
+    psi, sig, lam = np.zeros((2, 19)), ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(lib.od3_adjoint_node(ctypes.byref(st), x, y, z, n, _ptr(_f64(f)), float(g), _ptr(_f64(rho)),
+                                0 if sigma_next is None else 1, 0.0 if sigma_next is None else float(sigma_next),
+                                _ptr(psi), ctypes.byref(sig), ctypes.byref(lam)), "adjoint3d_node")
+    return psi, sig.value, lam.value
 
 
 def from_workload3d(w, N=None) -> Problem3D:

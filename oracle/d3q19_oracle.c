@@ -459,6 +459,75 @@ int od3_tlm(const od3_problem* p, const double* g, const double* dg, const doubl
     return 0;
 }
 
+/* One node of the AMRT step at step n, the exact transpose of collide_node:
+ * from the pulled adjoint populations rho [2][Q] and the node's forward state
+ * at step n (pre-collision f [2][Q], Phi = Phi^n), the node's adjoint
+ * populations psi [2][Q], sigma^n and the adjoint of Phi^n (its use at step n
+ * and, when has_next, with c'_{n+1} sigma^{n+1} at step n + 1). */
+static void adjoint_local(const lat3_t* L, const od3_problem* p, const node3d_t* nd, int n, const double* fk,
+                          double Phi, const double* rk, int has_next, double sig_next, double* psi_out,
+                          double* sig_out, double* aPhi_out) {
+    const double sc = 1.0 / (p->d_v * CS2);
+    double Tu = 0.0, Tv = 0.0, jv[3] = {0, 0, 0};
+    for (int i = 0; i < Q; ++i) {
+        Tu += fk[i];
+        Tv += fk[Q + i];
+        for (int cc = 0; cc < 3; ++cc) jv[cc] += E[i][cc] * fk[Q + i];
+    }
+    double G[3];
+    grad_v(p, nd, Tv, jv, Phi, G);
+    /* transposed collisions with the adjoint-equilibrium broadcast */
+    double out[2 * Q], Pi[Q][Q], mt[Q];
+    for (int s = 0; s < 2; ++s) {
+        Pi3(p->s, s == 0 ? nd->Ku : nd->Kv, Pi);
+        collide_T(L, Pi, rk + s * Q, mt);
+        const double* al = s == 0 ? nd->aleph_u : nd->aleph_v;
+        double Tcal = 0.0;
+        for (int i = 0; i < Q; ++i) Tcal += L->w[i] * al[i] * mt[i];
+        for (int i = 0; i < Q; ++i) out[s * Q + i] = rk[s * Q + i] - mt[i] + Tcal;
+    }
+    /* adjoint of tau S_u = (w_i / Cs^2) e_i . K_u F, F = chi u G */
+    double Y[3] = {0, 0, 0};
+    for (int i = 0; i < Q; ++i)
+        for (int cc = 0; cc < 3; ++cc) Y[cc] += rk[i] * L->w[i] / CS2 * E[i][cc];
+    double aF[3];
+    for (int cc = 0; cc < 3; ++cc) {
+        aF[cc] = 0.0;
+        for (int r = 0; r < 3; ++r) aF[cc] += nd->Ku[r][cc] * Y[r];
+    }
+    double aTu = 0.0, aTv = 0.0, aPhi = 0.0, aG[3], aj[3];
+    for (int cc = 0; cc < 3; ++cc) {
+        aTu += p->chi * G[cc] * aF[cc];
+        aG[cc] = p->chi * Tu * aF[cc];
+    }
+    /* G = -(K_v (j_v - a v)/tau + K_v a Phi/2) / (d_v Cs^2) */
+    double KtG[3];
+    for (int cc = 0; cc < 3; ++cc) {
+        KtG[cc] = 0.0;
+        for (int r = 0; r < 3; ++r) KtG[cc] += nd->Kv[r][cc] * aG[r];
+    }
+    double aKG = 0.0;
+    for (int cc = 0; cc < 3; ++cc) {
+        aj[cc] = -KtG[cc] * sc / p->tau;
+        aKG += nd->a[cc] * KtG[cc];
+    }
+    aTv += aKG * sc / p->tau;
+    aPhi += -0.5 * aKG * sc;
+    /* the source w~ (c_n Phi^n + c'_n Phi^{n-1}) and the use of Phi^n at step n+1 */
+    double sig = 0.0;
+    for (int i = 0; i < Q; ++i) sig += rk[Q + i] * nd->wt_v[i];
+    aPhi += c_now(p, n) * sig;
+    if (has_next) aPhi += c_prev(p, n + 1) * sig_next;
+    *sig_out = sig;
+    aTu += p->r_vu * aPhi;
+    aTv += p->r_vv * aPhi;
+    *aPhi_out = aPhi;
+    for (int i = 0; i < Q; ++i) {
+        psi_out[i] = out[i] + aTu;
+        psi_out[Q + i] = out[Q + i] + aTv + E[i][0] * aj[0] + E[i][1] * aj[1] + E[i][2] * aj[2];
+    }
+}
+
 int od3_adjoint(const od3_problem* p, const double* g, const double* seed_u, const double* seed_v, double* dJdg,
                 double* psi0, double* J) {
     lat3_t L;
@@ -486,76 +555,18 @@ int od3_adjoint(const od3_problem* p, const double* g, const double* seed_u, con
             psi[k * 2 * Q + i] = seed_u ? seed_u[k] : wu[k];
             psi[k * 2 * Q + Q + i] = seed_v ? seed_v[k] : 0.0;
         }
-    const double sc = 1.0 / (p->d_v * CS2);
     for (int n = N - 1; n >= 0; --n) {
         stream(p, psi, rho, 1); /* along -e_i, backward in time */
         const double* f = traj + (size_t)n * npop;
 #pragma omp parallel for schedule(static)
         for (long long kk = 0; kk < (long long)nn; ++kk) {
             const size_t k = (size_t)kk;
-            const node3d_t* nd = &nodes[k];
-            const double* fk = f + k * 2 * Q;
-            const double* rk = rho + k * 2 * Q;
-            double Tu = 0.0, Tv = 0.0, jv[3] = {0, 0, 0};
-            for (int i = 0; i < Q; ++i) {
-                Tu += fk[i];
-                Tv += fk[Q + i];
-                for (int cc = 0; cc < 3; ++cc) jv[cc] += E[i][cc] * fk[Q + i];
-            }
-            double G[3];
-            grad_v(p, nd, Tv, jv, Phi_traj[(size_t)n * nn + k], G);
-            /* transposed collisions with the adjoint-equilibrium broadcast */
-            double out[2 * Q], Pi[Q][Q], mt[Q];
-            for (int s = 0; s < 2; ++s) {
-                Pi3(p->s, s == 0 ? nd->Ku : nd->Kv, Pi);
-                collide_T(&L, Pi, rk + s * Q, mt);
-                const double* al = s == 0 ? nd->aleph_u : nd->aleph_v;
-                double Tcal = 0.0;
-                for (int i = 0; i < Q; ++i) Tcal += L.w[i] * al[i] * mt[i];
-                for (int i = 0; i < Q; ++i) out[s * Q + i] = rk[s * Q + i] - mt[i] + Tcal;
-            }
-            /* adjoint of tau S_u = (w_i / Cs^2) e_i . K_u F, F = chi u G */
-            double Y[3] = {0, 0, 0};
-            for (int i = 0; i < Q; ++i)
-                for (int cc = 0; cc < 3; ++cc) Y[cc] += rk[i] * L.w[i] / CS2 * E[i][cc];
-            double aF[3];
-            for (int cc = 0; cc < 3; ++cc) {
-                aF[cc] = 0.0;
-                for (int r = 0; r < 3; ++r) aF[cc] += nd->Ku[r][cc] * Y[r];
-            }
-            double aTu = 0.0, aTv = 0.0, aPhi = 0.0, aG[3], aj[3];
-            for (int cc = 0; cc < 3; ++cc) {
-                aTu += p->chi * G[cc] * aF[cc];
-                aG[cc] = p->chi * Tu * aF[cc];
-            }
-            /* G = -(K_v (j_v - a v)/tau + K_v a Phi/2) / (d_v Cs^2) */
-            double KtG[3];
-            for (int cc = 0; cc < 3; ++cc) {
-                KtG[cc] = 0.0;
-                for (int r = 0; r < 3; ++r) KtG[cc] += nd->Kv[r][cc] * aG[r];
-            }
-            double aKG = 0.0;
-            for (int cc = 0; cc < 3; ++cc) {
-                aj[cc] = -KtG[cc] * sc / p->tau;
-                aKG += nd->a[cc] * KtG[cc];
-            }
-            aTv += aKG * sc / p->tau;
-            aPhi += -0.5 * aKG * sc;
-            /* the source w~ (c_n Phi^n + c'_n Phi^{n-1}) and the use of Phi^n at step n+1 */
-            double sig = 0.0;
-            for (int i = 0; i < Q; ++i) sig += rk[Q + i] * nd->wt_v[i];
-            aPhi += c_now(p, n) * sig;
-            if (n + 1 <= N - 1) aPhi += c_prev(p, n + 1) * sig_next[k];
-            sig_now[k] = sig;
-            aTu += p->r_vu * aPhi;
-            aTv += p->r_vv * aPhi;
+            double aPhi;
+            adjoint_local(&L, p, &nodes[k], n, f + k * 2 * Q, Phi_traj[(size_t)n * nn + k], rho + k * 2 * Q,
+                          n + 1 <= N - 1, sig_next[k], psi + k * 2 * Q, &sig_now[k], &aPhi);
             if (dJdg) {
                 const double gv = g ? g[(size_t)n * nn + k] : 0.0;
                 dJdg[(size_t)n * nn + k] = aPhi + 2.0 * p->alpha * gv;
-            }
-            for (int i = 0; i < Q; ++i) {
-                psi[k * 2 * Q + i] = out[i] + aTu;
-                psi[k * 2 * Q + Q + i] = out[Q + i] + aTv + E[i][0] * aj[0] + E[i][1] * aj[1] + E[i][2] * aj[2];
             }
         }
         double* t = sig_next;
@@ -572,5 +583,36 @@ int od3_adjoint(const od3_problem* p, const double* g, const double* seed_u, con
     free(sig_now);
     free(wu);
     free(nodes);
+    return 0;
+}
+
+int od3_collide_node(const od3_problem* p, int x, int y, int z, int n, const double* f, double g,
+                     double Phi_prev, double* P, double* Phi_out) {
+    lat3_t L;
+    lat_init(&L);
+    if (x < 0 || y < 0 || z < 0 || x >= p->nx || y >= p->ny || z >= p->nz) return -3;
+    node3d_t nd;
+    node_params(&L, p, nidx(p, x, y, z), &nd);
+    st3d_t st;
+    collide_node(&L, p, &nd, n, f, g, Phi_prev, P, &st);
+    *Phi_out = st.Phi;
+    return 0;
+}
+
+int od3_adjoint_node(const od3_problem* p, int x, int y, int z, int n, const double* f, double g,
+                     const double* rho, int has_next, double sigma_next, double* psi, double* sigma_out,
+                     double* lam_Phi) {
+    lat3_t L;
+    lat_init(&L);
+    if (x < 0 || y < 0 || z < 0 || x >= p->nx || y >= p->ny || z >= p->nz) return -3;
+    node3d_t nd;
+    node_params(&L, p, nidx(p, x, y, z), &nd);
+    double Tu = 0.0, Tv = 0.0;
+    for (int i = 0; i < Q; ++i) {
+        Tu += f[i];
+        Tv += f[Q + i];
+    }
+    const double Phi = p->r_vu * Tu + p->r_vv * Tv + g; /* as collide_node forms Phi^n */
+    adjoint_local(&L, p, &nd, n, f, Phi, rho, has_next, sigma_next, psi, sigma_out, lam_Phi);
     return 0;
 }

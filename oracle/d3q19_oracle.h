@@ -69,6 +69,17 @@ int od3_tlm(const od3_problem* p, const double* g, const double* dg, const doubl
  * otherwise the gradient of sum(seed . (u^N, v^N)) + alpha ||g||^2); dJdg [N][...]; psi0 (may be NULL) */
 int od3_adjoint(const od3_problem* p, const double* g, const double* seed_u, const double* seed_v, double* dJdg,
                 double* psi0, double* J);
+/* One collision at node (x, y, z), step n (f [2][Q] -> P [2][Q], Phi^n), for
+ * unit tests; Phi_prev is Phi^{n-1} (ignored at n = 0). */
+int od3_collide_node(const od3_problem* p, int x, int y, int z, int n, const double* f, double g,
+                     double Phi_prev, double* P, double* Phi_out);
+/* One node of the AMRT step, the transpose of od3_collide_node: from the
+ * pulled adjoint populations rho [2][Q] (and, when has_next, sigma^{n+1} for
+ * Phi^n's use at step n + 1) it returns psi [2][Q], sigma^n and lam_Phi, the
+ * adjoint of Phi^n (dJ/dg^n without the penalty term). */
+int od3_adjoint_node(const od3_problem* p, int x, int y, int z, int n, const double* f, double g,
+                     const double* rho, int has_next, double sigma_next, double* psi, double* sigma_out,
+                     double* lam_Phi);
 int od3_set_threads(int n);
 
 #ifdef __cplusplus

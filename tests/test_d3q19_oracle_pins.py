@@ -292,3 +292,44 @@ def test_chemotaxis_coupling_against_pde():
     print("D3Q19 vs pseudo-spectral", errs)
     for c in range(2):
         assert 3.3 < errs[0][c] / errs[1][c] < 4.7, errs
+
+
+@pytest.mark.parametrize("n", [0, 3])
+def test_local_adjoint_is_the_transposed_local_jacobian(n):
+    """One node of the D3Q19 AMRT step against the dense Jacobian of one
+    collision at that node by central differences (38 populations, the
+    control and Phi^{n-1}).  With L = rho.P + lam Phi^n (lam = c'_{n+1}
+    sigma^{n+1}): psi = dL/df, lambda_Phi = dL/dg and c'_n sigma^n =
+    dL/dPhi^{n-1}.  The map is at most quadratic (chemotaxis u G), so central
+    differences are exact up to rounding."""
+    p = _problem()
+    _, wts, _ = oracle.lattice3d()
+    rng = np.random.default_rng(50 + n)
+    tau = 1.0
+    c_prev_n = 0.0 if n == 0 else -0.5 * tau
+    h = 1e-6
+    for _ in range(2):
+        x, y, z = int(rng.integers(0, 6)), int(rng.integers(0, 5)), int(rng.integers(0, 4))
+        f = np.stack([wts * rng.uniform(0.8, 1.2), wts * rng.uniform(0.3, 0.6)]) + rng.normal(0, 0.005, (2, 19))
+        g, pp = rng.normal(0, 0.05), rng.normal(0, 0.05)
+        rho, sig_next = rng.normal(size=(2, 19)), rng.normal()
+        lam_next = -0.5 * tau * sig_next
+
+        def L(f_, g_, pp_):
+            P, phi = oracle.collide3d_node(p, x, y, z, n, f_, g_, pp_)
+            return float(np.sum(rho * P) + lam_next * phi)
+
+        dfd = np.zeros((2, 19))
+        for s in range(2):
+            for i in range(19):
+                d = np.zeros((2, 19))
+                d[s, i] = h
+                dfd[s, i] = (L(f + d, g, pp) - L(f - d, g, pp)) / (2 * h)
+        dg = (L(f, g + h, pp) - L(f, g - h, pp)) / (2 * h)
+        dpp = (L(f, g, pp + h) - L(f, g, pp - h)) / (2 * h)
+
+        psi, sigma, lam_phi = oracle.adjoint3d_node(p, x, y, z, n, f, rho, g=g, sigma_next=sig_next)
+        scale = max(np.abs(dfd).max(), 1.0)
+        assert np.allclose(psi, dfd, rtol=0, atol=1e-8 * scale)
+        assert abs(lam_phi - dg) < 1e-8 * scale
+        assert abs(c_prev_n * sigma - dpp) < 1e-8 * scale
